@@ -1,0 +1,223 @@
+"""CPU oracle for Picard-iteration FO policy simulation -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg may import this package.  It shares no code with the CUDA implementation:
+the arithmetic lives in ``fo_oracle.c`` (plain C, compiled with
+``-ffp-contract=off``) and, for the policy gradient, in ``pg.py`` (numpy FP64).
+
+Inputs are duck-typed: an instance needs attributes T, N, K, R, prod, reg, x0,
+cost, lam; a policy needs kind ('greedy' | 'dual' | 'mlp' | 'gumbel'), mlp (with
+W1, b1, W2, b2, E as BF16 uint16 arrays and H), seed and traj.
+
+Parity status per function (see each docstring for its pins): every function
+here is pinned by tests under ``tests/test_oracle_*.py``; none is unpinned.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fo_oracle.c")
+_LIB = os.path.join(_HERE, "libfo_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+KINDS = {"greedy": 0, "dual": 1, "mlp": 2, "gumbel": 3}
+OK, ERR_ARG, ERR_NOT_CONVERGED = 0, 1, 4
+
+
+def build(force: bool = False) -> str:
+    """Compile fo_oracle.c with gcc (IEEE FP32, no contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c99",
+                               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            P = C.c_void_p
+            i32, i64, u64 = C.c_int32, C.c_int64, C.c_uint64
+            common = [i32, i32, i32, i32, P, P, P, P, P, i32, i32, P, P, P, P, P, u64, i32]
+            lib.orc_seq_sim.argtypes = common + [P, P, P, P]
+            lib.orc_seq_sim.restype = C.c_int
+            lib.orc_picard_literal.argtypes = common + [i32, i32, P, P, P, P]
+            lib.orc_picard_literal.restype = C.c_int
+            lib.orc_picard_chunked.argtypes = common + [i32, i32, P, P, P, P, P, P]
+            lib.orc_picard_chunked.restype = C.c_int
+            lib.orc_mlp_scores.argtypes = [C.c_int, C.c_int, P, P, P, P, P, P, i32, P, P]
+            lib.orc_mlp_scores.restype = None
+            lib.orc_philox4x32_10.argtypes = [P, P, P]
+            lib.orc_philox4x32_10.restype = None
+            lib.orc_uniform.argtypes = [u64, i32, i64, i32]
+            lib.orc_uniform.restype = C.c_float
+            lib.orc_log.argtypes = [C.c_float]
+            lib.orc_log.restype = C.c_float
+            lib.orc_gumbel.argtypes = [u64, i32, i64, i32]
+            lib.orc_gumbel.restype = C.c_float
+            lib.orc_state_before.argtypes = [i32, i32, P, P, P, i64, P]
+            lib.orc_state_before.restype = C.c_int
+            lib.orc_policy_call.argtypes = [i32, i32, P, P, i32, i32, P, P, P, P, P, u64, i32,
+                                            P, i32, i32, i64]
+            lib.orc_policy_call.restype = C.c_int
+            _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _c(a, dt):
+    return None if a is None else np.ascontiguousarray(a, dtype=dt)
+
+
+def _args(inst, pol):
+    kind = KINDS[pol.kind]
+    m = pol.mlp
+    keep = [
+        _c(inst.prod, np.int32), _c(inst.reg, np.int32), _c(inst.x0, np.int32),
+        _c(inst.cost, np.int32), _c(inst.lam, np.int32) if kind == 1 else None,
+    ]
+    if kind >= 2:
+        mk = [_c(m.W1, np.uint16), _c(m.b1, np.uint16), _c(m.W2, np.uint16), _c(m.b2, np.uint16),
+              _c(m.E, np.uint16)]
+        H = int(m.H)
+    else:
+        mk, H = [None] * 5, 0
+    keep += mk
+    args = [inst.T, inst.N, inst.K, inst.R] + [_p(a) for a in keep[:5]] + [kind, H] + \
+        [_p(a) for a in mk] + [int(pol.seed) & 0xFFFFFFFFFFFFFFFF, int(pol.traj)]
+    return args, keep
+
+
+def seq_sim(inst, pol):
+    """Sequential simulation a_t = pi(s_t, w_t), s_{t+1} = f(s_t, a_t, w_t)
+    (Sec. 2 problem statement, Sec. 3 inventory dynamics).
+
+    Pins: brute-force argmin/argmax per step on tiny inputs, conservation
+    (units shipped = x0 - x_final), non-negative stock, a^phi iff no stock,
+    textbook special cases (ample stock => unconstrained argmin)."""
+    lib = _load()
+    args, keep = _args(inst, pol)
+    act = np.empty(inst.T, np.int8)
+    xf = np.empty((inst.K, inst.N), np.int32)
+    tc, lost = C.c_int64(0), C.c_int64(0)
+    rc = lib.orc_seq_sim(*args, _p(act), _p(xf), C.byref(tc), C.byref(lost))
+    if rc != OK:
+        raise ValueError(f"orc_seq_sim failed rc={rc}")
+    return {"actions": act, "x_final": xf, "total_cost": tc.value, "lost": lost.value}
+
+
+def _picard(fn, inst, pol, M, max_iters, alpha_init, record, extra):
+    lib = _load()
+    args, keep = _args(inst, pol)
+    if max_iters is None:
+        max_iters = M + 1
+    act = np.empty(inst.T, np.int8)
+    iters = C.c_int32(0)
+    its = np.empty((max_iters, inst.T), np.int8) if record else None
+    ai = _c(alpha_init, np.int8)
+    out = {}
+    tail = [_p(ai), _p(act), C.byref(iters), _p(its)]
+    if extra:
+        chg = np.zeros(max_iters, np.int64)
+        fst = np.zeros(max_iters, np.int64)
+        tail += [_p(chg), _p(fst)]
+    rc = fn(*args, int(M), int(max_iters), *tail)
+    if rc not in (OK, ERR_NOT_CONVERGED):
+        raise ValueError(f"picard oracle failed rc={rc}")
+    k = iters.value
+    out.update(actions=act, iters=k, converged=(rc == OK))
+    if record:
+        out["iterates"] = its[:k].copy()
+    if extra:
+        out["changed"] = chg[:k].copy()
+        out["first_changed"] = fst[:k].copy()
+    return out
+
+
+def picard_literal(inst, pol, M, max_iters=None, alpha_init=None, record=False):
+    """Algorithm 1 verbatim on M contiguous time blocks: every process restarts
+    from s_1, evaluates pi on its block, applies feasible cached actions elsewhere.
+
+    Pins: equals seq_sim (Prop. 1); alpha^k exact on blocks 0..k-1 after pass k
+    (proof of Prop. 1); M=1 and ample stock converge in 2 passes; iteration bound
+    of Sec. 3.1 for greedy; brute force over tiny instances."""
+    return _picard(_load().orc_picard_literal, inst, pol, M, max_iters, alpha_init, record, False)
+
+
+def picard_chunked(inst, pol, M, max_iters=None, alpha_init=None, record=False):
+    """Algorithm 1 on the same blocks with the cached-prefix replay in closed form
+    max(0, x0 - d).  Pins: identical iterates alpha^k to picard_literal for every
+    k on exhaustive tiny instances and random small ones; fixed point = seq_sim."""
+    return _picard(_load().orc_picard_chunked, inst, pol, M, max_iters, alpha_init, record, True)
+
+
+def mlp_scores(N, mlp, cost_row, r, stock_row):
+    """Fixed-order FP32 MLP scores.  Pins: agrees with an FP64 matrix product of
+    the same parameters to within the FP32 accumulation bound."""
+    lib = _load()
+    keep = [_c(mlp.W1, np.uint16), _c(mlp.b1, np.uint16), _c(mlp.W2, np.uint16),
+            _c(mlp.b2, np.uint16), _c(mlp.E, np.uint16), _c(cost_row, np.int32),
+            _c(stock_row, np.int32)]
+    out = np.empty(N, np.float32)
+    lib.orc_mlp_scores(N, int(mlp.H), *[_p(a) for a in keep[:6]], int(r), _p(keep[6]), _p(out))
+    return out
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 block (Salmon et al., SC'11).  Pin: published known-answer
+    vectors (tests/golden/philox4x32_10_kat.txt)."""
+    lib = _load()
+    c = np.ascontiguousarray(ctr, np.uint32)
+    k = np.ascontiguousarray(key, np.uint32)
+    o = np.empty(4, np.uint32)
+    lib.orc_philox4x32_10(_p(c), _p(k), _p(o))
+    return o
+
+
+def log32(x):
+    """IEEE-only FP32 natural log.  Pin: within 2 ulp of FP64 log."""
+    return np.float32(_load().orc_log(float(x)))
+
+
+def uniform(seed, traj, t, n):
+    return np.float32(_load().orc_uniform(seed, traj, t, n))
+
+
+def gumbel(seed, traj, t, n):
+    return np.float32(_load().orc_gumbel(seed, traj, t, n))
+
+
+def state_before(inst, actions, t):
+    """Stock row seen by the order at time t under an action path."""
+    lib = _load()
+    prod = _c(inst.prod, np.int32)
+    act = _c(actions, np.int8)
+    x0 = _c(inst.x0, np.int32)
+    out = np.empty(inst.N, np.int32)
+    rc = lib.orc_state_before(inst.T, inst.N, _p(prod), _p(act), _p(x0), int(t), _p(out))
+    if rc != OK:
+        raise ValueError("bad t")
+    return out
+
+
+def policy_call(inst, pol, stock_row, k, r, t):
+    """One policy decision pi(s, w) for product k, region r, time t."""
+    lib = _load()
+    args, keep = _args(inst, pol)
+    # args layout: T,N,K,R,prod,reg,x0,cost,lam,kind,H,W1,b1,W2,b2,E,seed,traj
+    sr = _c(stock_row, np.int32)
+    return lib.orc_policy_call(inst.N, inst.R, args[7], args[8], args[9], args[10], *args[11:16],
+                               args[16], args[17], _p(sr), int(k), int(r), int(t))

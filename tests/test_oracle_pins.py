@@ -1,0 +1,387 @@
+"""Pins for the CPU oracle: facts fixed by the paper and by mathematics, not by
+the oracle itself.  All CPU-only (no GPU marker)."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_01939_b300 import synth
+from paper_2406_01939_b300.synth import Instance, Policy
+
+
+def tiny(rng, T=None, N=None, K=None, R=None, xmax=4, cmax=5, lam=False):
+    T = int(rng.integers(0, 41)) if T is None else T
+    N = int(rng.integers(1, 6)) if N is None else N
+    K = int(rng.integers(1, 5)) if K is None else K
+    R = int(rng.integers(1, 4)) if R is None else R
+    return Instance(
+        T, N, K, R,
+        rng.integers(0, K, T).astype(np.int32), rng.integers(0, R, T).astype(np.int32),
+        rng.integers(0, xmax + 1, (K, N)).astype(np.int32),
+        rng.integers(1, cmax + 1, (R, N)).astype(np.int32),
+        rng.integers(0, 4, (K, N)).astype(np.int32) if lam else None)
+
+
+def policies(inst, seed):
+    mlp = synth.make_mlp(inst.N, inst.R, seed=seed)
+    return [Policy("greedy"), Policy("dual") if inst.lam is not None else Policy("greedy"),
+            Policy("mlp", mlp=mlp), Policy("gumbel", mlp=mlp, seed=seed * 7 + 1, traj=seed % 5)]
+
+
+def state_path(inst, actions):
+    """Stock rows before every t under an action path (plain replay)."""
+    x = inst.x0.astype(np.int64).copy()
+    rows = []
+    for t in range(inst.T):
+        k = inst.prod[t]
+        rows.append(x[k].copy())
+        a = actions[t]
+        if a >= 0:
+            x[k, a] -= 1
+    return rows, x
+
+
+# ----------------------------------------------------------------------------- sequential sim
+def test_seq_invariants_random():
+    """Dynamics of Sec. 3 (x_{t+1} = x_t - e_{i,a}): stock never negative, every
+    action feasible, a^phi iff no stock, units shipped = x0 - x_final, cost =
+    sum of cost[r_t][a_t] over fulfilled orders."""
+    rng = np.random.default_rng(1)
+    for trial in range(150):
+        inst = tiny(rng, lam=True)
+        for pol in policies(inst, trial):
+            out = oracle.seq_sim(inst, pol)
+            a = out["actions"]
+            rows, xf = state_path(inst, a)
+            for t in range(inst.T):
+                row = rows[t]
+                assert (row >= 0).all()
+                if a[t] >= 0:
+                    assert row[a[t]] > 0
+                else:
+                    assert (row <= 0).all()
+            assert (xf >= 0).all()
+            np.testing.assert_array_equal(out["x_final"], xf)
+            shipped = np.zeros_like(inst.x0)
+            for t in range(inst.T):
+                if a[t] >= 0:
+                    shipped[inst.prod[t], a[t]] += 1
+            np.testing.assert_array_equal(shipped, inst.x0 - out["x_final"])
+            cost = sum(int(inst.cost[inst.reg[t], a[t]]) for t in range(inst.T) if a[t] >= 0)
+            assert cost == out["total_cost"]
+            assert out["lost"] == int((a < 0).sum())
+
+
+def test_seq_greedy_brute_force_unique_path():
+    """Brute force: among ALL feasible action paths of a tiny instance exactly one
+    picks, at every step, a cheapest stocked node with the lowest index (a^phi only
+    when nothing is stocked) -- and it is the oracle's path.  Same for the
+    bid-price policy (score cost - lambda)."""
+    rng = np.random.default_rng(2)
+    for trial in range(60):
+        inst = tiny(rng, T=int(rng.integers(1, 6)), N=int(rng.integers(1, 4)),
+                    K=int(rng.integers(1, 3)), R=2, xmax=2, cmax=3, lam=True)
+        for kind in ("greedy", "dual"):
+            def score(k, r, n):
+                v = int(inst.cost[r, n])
+                return v - int(inst.lam[k, n]) if kind == "dual" else v
+            good = []
+            for path in itertools.product(range(-1, inst.N), repeat=inst.T):
+                x = inst.x0.astype(int).copy()
+                ok = True
+                for t, a in enumerate(path):
+                    k, r = inst.prod[t], inst.reg[t]
+                    stocked = [n for n in range(inst.N) if x[k, n] > 0]
+                    if a == -1:
+                        ok = not stocked
+                    else:
+                        ok = a in stocked and all(
+                            (score(k, r, a), a) <= (score(k, r, n), n) for n in stocked)
+                    if not ok:
+                        break
+                    if a >= 0:
+                        x[k, a] -= 1
+                if ok:
+                    good.append(path)
+            assert len(good) == 1
+            out = oracle.seq_sim(inst, Policy(kind))
+            assert tuple(out["actions"].tolist()) == good[0]
+
+
+def test_seq_ample_stock_is_unconstrained_argmin():
+    """Special case (Sec. 3.1 with x_1 = T*1): with stock never binding, greedy
+    takes the unconstrained argmin of the cost row (numpy argmin = lowest index)."""
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        inst = tiny(rng, T=200, N=6, K=3, R=5, cmax=9, lam=True)
+        inst.x0[:] = 10_000
+        g = oracle.seq_sim(inst, Policy("greedy"))["actions"]
+        np.testing.assert_array_equal(g, np.argmin(inst.cost[inst.reg], axis=1))
+        d = oracle.seq_sim(inst, Policy("dual"))["actions"]
+        np.testing.assert_array_equal(
+            d, np.argmin(inst.cost[inst.reg] - inst.lam[inst.prod], axis=1))
+
+
+def test_seq_single_node_closed_form():
+    """N = 1: the first x0[k] orders of product k are fulfilled, the rest lost."""
+    rng = np.random.default_rng(4)
+    inst = tiny(rng, T=300, N=1, K=7, R=3, xmax=60)
+    a = oracle.seq_sim(inst, Policy("greedy"))["actions"]
+    for k in range(inst.K):
+        idx = np.flatnonzero(inst.prod == k)
+        want = np.where(np.arange(len(idx)) < inst.x0[k, 0], 0, -1)
+        np.testing.assert_array_equal(a[idx], want)
+
+
+def test_seq_no_stock_all_lost():
+    rng = np.random.default_rng(5)
+    inst = tiny(rng, T=50, N=4, K=2, R=2)
+    inst.x0[:] = 0
+    mlp = synth.make_mlp(4, 2)
+    for pol in (Policy("greedy"), Policy("mlp", mlp=mlp)):
+        out = oracle.seq_sim(inst, pol)
+        assert (out["actions"] == -1).all() and out["total_cost"] == 0 and out["lost"] == 50
+
+
+# ----------------------------------------------------------------------------- Algorithm 1
+def test_hand_worked_example():
+    """Algorithm 1 by hand.  One product, nodes {0, 1}, cost row [1, 5], stock
+    [2, 1], four orders, M = 4 (one order per process).
+      pass 1: every process starts from [2,1] and picks node 0 -> alpha^1 = 0 0 0 0
+      pass 2: p1 replays cached 0 -> [1,1], picks 0; p2 replays 0,0 -> [0,1], picks 1;
+              p3 replays 0,0 then cached 0 is infeasible (a^phi) -> [0,1], picks 1
+              -> alpha^2 = 0 0 1 1
+      pass 3: p3 replays 0,0,1 -> [0,0] -> a^phi   -> alpha^3 = 0 0 1 -1
+      pass 4: no change -> returns after 4 passes; equals the sequential path."""
+    inst = Instance(4, 2, 1, 1, np.zeros(4, np.int32), np.zeros(4, np.int32),
+                    np.array([[2, 1]], np.int32), np.array([[1, 5]], np.int32))
+    want = [[0, 0, 0, 0], [0, 0, 1, 1], [0, 0, 1, -1], [0, 0, 1, -1]]
+    for fn in (oracle.picard_literal, oracle.picard_chunked):
+        out = fn(inst, Policy("greedy"), 4, record=True)
+        assert out["iters"] == 4
+        assert out["iterates"].tolist() == want
+    assert oracle.seq_sim(inst, Policy("greedy"))["actions"].tolist() == [0, 0, 1, -1]
+
+
+def _check_prop1(inst, pol, M, seq):
+    lit = oracle.picard_literal(inst, pol, M, record=True)
+    chk = oracle.picard_chunked(inst, pol, M, record=True)
+    assert lit["converged"] and chk["converged"]
+    # closed-form prefix == verbatim replay, pass by pass
+    assert lit["iters"] == chk["iters"]
+    np.testing.assert_array_equal(lit["iterates"], chk["iterates"])
+    # Prop. 1: the fixed point is the sequential path, within M + 1 passes
+    np.testing.assert_array_equal(lit["actions"], seq)
+    assert lit["iters"] <= M + 1
+    # proof of Prop. 1 on contiguous blocks: after pass k, blocks 0..k-1 are exact
+    L = -(-inst.T // M) if inst.T else 1
+    for k in range(1, lit["iters"] + 1):
+        hi = min(k * L, inst.T)
+        np.testing.assert_array_equal(lit["iterates"][k - 1][:hi], seq[:hi])
+
+
+def test_prop1_random_all_policies_all_M():
+    rng = np.random.default_rng(6)
+    for trial in range(40):
+        inst = tiny(rng, T=int(rng.integers(0, 24)), lam=True)
+        for pol in policies(inst, trial):
+            seq = oracle.seq_sim(inst, pol)["actions"]
+            for M in sorted({1, 2, 3, max(1, inst.T // 2), max(1, inst.T)}):
+                _check_prop1(inst, pol, M, seq)
+
+
+def test_exhaustive_family_literal_equals_chunked():
+    """Exhaustive: one product, N=2, R=2, T=4, every region pattern, every stock
+    vector in {0,1,2}^2, a strict and a tied cost table, every M in 1..4."""
+    for costs in (np.array([[1, 2], [2, 1]], np.int32), np.array([[1, 1], [1, 1]], np.int32)):
+        for regs in itertools.product(range(2), repeat=4):
+            for x0 in itertools.product(range(3), repeat=2):
+                inst = Instance(4, 2, 1, 2, np.zeros(4, np.int32), np.array(regs, np.int32),
+                                np.array([x0], np.int32), costs)
+                seq = oracle.seq_sim(inst, Policy("greedy"))["actions"]
+                for M in range(1, 5):
+                    _check_prop1(inst, Policy("greedy"), M, seq)
+
+
+def test_warm_start_cache_still_converges_to_seq():
+    """The induction behind Prop. 1 does not use alpha^0, so any initial cache
+    (e.g. a previous policy's actions, Sec. 5) reaches the sequential path."""
+    rng = np.random.default_rng(7)
+    for trial in range(30):
+        inst = tiny(rng, T=30, lam=True)
+        for pol in policies(inst, trial)[:3]:
+            seq = oracle.seq_sim(inst, pol)["actions"]
+            init = rng.integers(-1, inst.N, inst.T).astype(np.int8)
+            for M in (1, 4, 30):
+                a = oracle.picard_literal(inst, pol, M, alpha_init=init)
+                b = oracle.picard_chunked(inst, pol, M, alpha_init=init)
+                assert a["iters"] == b["iters"] and a["iters"] <= M + 1
+                np.testing.assert_array_equal(a["actions"], seq)
+                np.testing.assert_array_equal(b["actions"], seq)
+
+
+def test_single_process_and_ample_stock_converge_in_two_passes():
+    """M = 1 reproduces sequential simulation in one pass (+1 to confirm, unless
+    the path is all a^phi, which the initial cache already holds); with ample
+    stock greedy does not depend on the state, so any M needs 1 (+1)."""
+    rng = np.random.default_rng(8)
+    for trial in range(20):
+        inst = tiny(rng, T=40, lam=True)
+        for pol in policies(inst, trial):
+            seq = oracle.seq_sim(inst, pol)["actions"]
+            # one pass suffices to confirm when the sequential path is the initial cache
+            want = 1 if (seq == -1).all() else 2
+            assert oracle.picard_chunked(inst, pol, 1)["iters"] == want
+        inst.x0[:] = 1000
+        for M in (2, 7, 40):
+            assert oracle.picard_chunked(inst, Policy("greedy"), M)["iters"] == 2
+            assert oracle.picard_chunked(inst, Policy("dual"), M)["iters"] == 2
+
+
+def _depleted_before(inst, seq):
+    """Q_t of Sec. 3.1 per order: nodes of the order's product with zero stock just
+    before t in the sequential run."""
+    rows, xf = state_path(inst, seq)
+    return rows, xf
+
+
+def test_greedy_lemma_and_iteration_bound():
+    """Sec. 3.1, applied per product (inventory independence, Assumption 1, makes
+    every product its own FO system with 'capacity' = its stock):
+    Lemma 3.2: alpha^k_t in {a^seq_t} U Q_t for every pass k and every t;
+    theorem: at most |Q_T| + 1 changing passes, so passes <= min(M, max_k |Q_k| + 1) + 1."""
+    rng = np.random.default_rng(9)
+    for trial in range(60):
+        inst = tiny(rng, T=int(rng.integers(5, 60)), N=int(rng.integers(2, 6)), K=2, R=3,
+                    xmax=5, cmax=6, lam=True)
+        for kind in ("greedy", "dual"):
+            pol = Policy(kind)
+            seq = oracle.seq_sim(inst, pol)
+            rows, xf = _depleted_before(inst, seq["actions"])
+            qmax = int((xf == 0).sum(axis=1).max())
+            for M in (2, 5, inst.T):
+                out = oracle.picard_literal(inst, pol, M, record=True)
+                assert out["iters"] <= min(M, qmax + 1) + 1
+                for it in out["iterates"]:
+                    for t in range(inst.T):
+                        a = it[t]
+                        if a == seq["actions"][t]:
+                            continue
+                        assert a >= 0 and rows[t][a] == 0, (trial, kind, M, t)
+
+
+def test_large_dual_iteration_bound_and_fixed_point():
+    """At the large benchmark shape (reduced T): fixed point = sequential path and
+    the per-product greedy bound holds for several block counts."""
+    inst = synth.dual_large(0, T=1 << 16, K=2000, R=200)
+    pol = Policy("dual")
+    seq = oracle.seq_sim(inst, pol)
+    qmax = int((seq["x_final"] == 0).sum(axis=1).max())
+    for M in (64, 1024, 1 << 16):
+        out = oracle.picard_chunked(inst, pol, M)
+        np.testing.assert_array_equal(out["actions"], seq["actions"])
+        assert out["iters"] <= min(M, qmax + 1) + 1
+
+
+# ----------------------------------------------------------------------------- MLP scorer
+def test_mlp_scores_match_fp64_matmul():
+    """The fixed-order FP32 scorer agrees with an FP64 matrix product of the same
+    BF16 parameters to within the FP32 accumulation bound (n u sum|terms|); a
+    swapped row block, a wrong feature scale or a dropped bias fails this."""
+    rng = np.random.default_rng(10)
+    for N, R in ((8, 5), (64, 7), (32, 3)):
+        mlp = synth.make_mlp(N, R, seed=N)
+        f = mlp.as_float()
+        W1, b1, W2, b2, E = (f[k].astype(np.float64) for k in ("W1", "b1", "W2", "b2", "E"))
+        for _ in range(10):
+            cost = rng.integers(1, 101, N).astype(np.int32)
+            stock = rng.integers(0, 60, N).astype(np.int32)
+            r = int(rng.integers(0, R))
+            x = np.concatenate([cost / 128.0, np.minimum(stock, 32) / 32.0, E[r]])
+            z = x @ W1 + b1
+            h = np.maximum(z, 0)
+            s = h @ W2 + b2
+            got = oracle.mlp_scores(N, mlp, cost, r, stock).astype(np.float64)
+            zb = np.abs(x) @ np.abs(W1) + np.abs(b1)
+            bound = (2 * N + 17) * 2.0 ** -24 * (np.abs(W2).T @ zb) \
+                + 257 * 2.0 ** -24 * (np.abs(h) @ np.abs(W2) + np.abs(b2))
+            assert (np.abs(got - s) <= 2 * bound + 1e-12).all()
+
+
+# ----------------------------------------------------------------------------- Philox / log / Gumbel
+def _kat():
+    import os
+    p = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    rows = []
+    for line in open(p):
+        if line.startswith("#") or not line.strip():
+            continue
+        w = [int(v, 16) for v in line.split()]
+        rows.append((w[0:4], w[4:6], w[6:10]))
+    return rows
+
+
+def test_philox_known_answers():
+    for ctr, key, want in _kat():
+        assert oracle.philox4x32_10(ctr, key).tolist() == want
+
+
+def test_log32_accuracy():
+    """Own FP32 log within 2 ulp of the FP64 log (rounded), across the range the
+    Gumbel transform feeds it, and exactly 0 at 1."""
+    rng = np.random.default_rng(11)
+    xs = np.concatenate([rng.uniform(2.0 ** -24, 1.0, 3000), rng.uniform(1e-8, 20.0, 3000),
+                         np.exp(rng.uniform(-40, 40, 3000))]).astype(np.float32)
+    assert oracle.log32(1.0) == 0.0
+    for x in xs:
+        got = oracle.log32(x)
+        want = math.log(float(x))
+        ulp = np.spacing(np.float32(abs(want))) if want != 0 else np.float32(2.0 ** -149)
+        assert abs(float(got) - want) <= 2 * float(ulp), (x, got, want)
+
+
+def test_uniform_and_gumbel_distribution():
+    """u = ((w >> 9) + 1/2) 2^-23 lies in (0,1); Gumbel(0,1) has mean Euler's gamma
+    and variance pi^2/6; argmax(s + g) samples softmax(s) (Gumbel-max)."""
+    us, gs = [], []
+    for t in range(4000):
+        for n in range(4):
+            u = oracle.uniform(123, 1, t, n)
+            w = oracle.philox4x32_10([t, 1, 0, 0], [123, 0])[n]
+            assert u == np.float32(((int(w) >> 9) + 0.5) * 2.0 ** -23)
+            us.append(u)
+            gs.append(oracle.gumbel(123, 1, t, n))
+    us, gs = np.array(us), np.array(gs, np.float64)
+    assert us.min() > 0 and us.max() < 1
+    assert abs(gs.mean() - 0.5772156649) < 0.03
+    assert abs(gs.var() - math.pi ** 2 / 6) < 0.08
+    s = np.array([0.3, -0.2, 1.0, 0.0], np.float32)
+    p = np.exp(s) / np.exp(s).sum()
+    cnt = np.zeros(4)
+    for t in range(6000):
+        v = [s[n] + oracle.gumbel(9, 2, t, n) for n in range(4)]
+        cnt[int(np.argmax(v))] += 1
+    assert np.abs(cnt / cnt.sum() - p).max() < 0.025
+
+
+def test_gumbel_policy_is_chunk_invariant():
+    """Noise keyed by (seed, trajectory, t, node) gives the same sequential path
+    and Picard fixed point for every block count."""
+    rng = np.random.default_rng(12)
+    inst = tiny(rng, T=40, N=5, K=3, R=3)
+    mlp = synth.make_mlp(5, 3)
+    pol = Policy("gumbel", mlp=mlp, seed=77, traj=3)
+    seq = oracle.seq_sim(inst, pol)["actions"]
+    for M in (1, 3, 8, 40):
+        np.testing.assert_array_equal(oracle.picard_chunked(inst, pol, M)["actions"], seq)
+    other = oracle.seq_sim(inst, Policy("gumbel", mlp=mlp, seed=78, traj=3))["actions"]
+    assert (other != seq).any()
+
+
+def test_bad_arguments_rejected():
+    inst = Instance(3, 2, 1, 1, np.array([0, 1, 0], np.int32), np.zeros(3, np.int32),
+                    np.ones((1, 2), np.int32), np.ones((1, 2), np.int32))
+    with pytest.raises(ValueError):
+        oracle.seq_sim(inst, Policy("greedy"))

@@ -1,0 +1,329 @@
+#!/usr/bin/env python
+"""Benchmark: orders simulated per second by Picard iteration (Algorithm 1) on
+one B300, against the sequential GPU simulator, bit-exact.
+
+A step is one whole simulation of one synthetic trajectory from its order
+stream resident in HBM: the product-major order tables (sort, runs, segments),
+every Picard pass to the fixed point, and the outputs (actions in time order,
+total cost).  Workload (bid-price FO, the large single-trajectory shape):
+T = 2^20 orders, N = 64 warehouses, K = 10,000 products (Zipf 1.1 demand),
+R = 1,000 regions, stock ~ Poisson(1.05 T p_k / N), M = 4,096 time chunks.
+
+Prints one JSON line (rank 0).  Under torchrun every rank simulates its own
+trajectory (weak scaling, no collective on the data path).  --impl reference
+times the CPU oracle (plain C sequential simulator) on the host instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "orders simulated/sec on 1 B300, Picard vs sequential GPU sim, bit-exact; iters"
+UNIT = "orders/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--chunks", type=int, default=4096)
+    p.add_argument("--seg-window", type=int, default=0)
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--seq-steps", type=int, default=3)
+    p.add_argument("--e2e-steps", type=int, default=20)
+    p.add_argument("--cpu-seconds", type=float, default=10.0)
+    return p.parse_args()
+
+
+def workload_config(args, inst):
+    return {
+        "workload": "dual_large",
+        "desc": (f"bid-price FO, T={inst.T} orders, N={inst.N} warehouses, K={inst.K} products "
+                 f"(Zipf 1.1), R={inst.R} regions, x0~Poisson(1.05 T p_k/N), lambda~U{{0..30}}, "
+                 f"cost~U{{1..100}}"),
+        "T": inst.T, "N": inst.N, "K": inst.K, "R": inst.R,
+        "chunks": args.chunks, "policy": "dual",
+        "l2": "flushed between timed steps (256 MiB write)",
+    }
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("pic_int.cu", "pic_device.cuh", "pic_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2406_01939_b300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the Picard kernel from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "picard_int_dual_large.md")
+    if not os.path.exists(p):
+        return None
+    src = kernel_source_hash()
+    hash_ok, traffic = False, None
+    for line in open(p):
+        if line.startswith("kernel_source_hash:") and line.split(":", 1)[1].strip() == src:
+            hash_ok = True
+        if line.startswith("dram_bytes_per_launch:"):
+            try:
+                traffic = float(line.split(":", 1)[1].strip())
+            except ValueError:
+                traffic = None
+    return traffic if hash_ok else None
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle_rate(inst, seconds):
+    """The CPU oracle's sequential simulator on the host (1 thread), repeated on
+    the full trajectory for about `seconds`."""
+    import oracle
+    from paper_2406_01939_b300.synth import Policy
+    pol = Policy("dual")
+    oracle.seq_sim(inst, pol)  # build + warm
+    n, t0 = 0, time.perf_counter()
+    out = None
+    while True:
+        out = oracle.seq_sim(inst, pol)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return n * inst.T / el, n, el, out
+
+
+def run_reference(args):
+    from paper_2406_01939_b300 import synth
+    inst = synth.dual_large(args.seed)
+    per = max(1, int(args.steps))
+    import oracle
+    from paper_2406_01939_b300.synth import Policy
+    pol = Policy("dual")
+    for _ in range(max(0, args.warmup)):
+        oracle.seq_sim(inst, pol)
+    t0 = time.perf_counter()
+    for _ in range(per):
+        oracle.seq_sim(inst, pol)
+    el = time.perf_counter() - t0
+    value = per * inst.T / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": per, "warmup": args.warmup, "ms_per_step": 1000 * el / per,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic", "config": workload_config(args, inst),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"full {inst.T}-order trajectory per step, sequential C oracle"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    import paper_2406_01939_b300 as pic
+    from paper_2406_01939_b300 import synth
+    from paper_2406_01939_b300.session import DeviceInstance, DevicePolicy
+    from paper_2406_01939_b300.synth import Policy
+
+    inst = synth.dual_large(args.seed + rank)
+    di = DeviceInstance(inst, device=dev)
+    pol = DevicePolicy(Policy("dual"), dev)
+    T = inst.T
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(out):
+        return di.simulate(pol, "picard", num_chunks=args.chunks, seg_window=args.seg_window,
+                           flags=pic.PIC_FLAG_TIMING, want_stock=False, out=out)
+
+    act = torch.empty(T, dtype=torch.int8, device=dev)
+    for _ in range(max(3, args.warmup)):
+        r = step(act)
+    stream = torch.cuda.current_stream(dev)
+    clocks = Clocks(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    evs = []
+    results = []
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1)  # evict the previous step's working set from L2 (untimed)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        results.append(step(act))
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    t_ms = sum(step_ms)
+    if world > 1:
+        tt = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    value = world * T * args.steps / (t_ms / 1000.0)
+    last = results[-1]
+    sim_ms = statistics.median(r["sim_ms"] for r in results)
+    prep_ms = statistics.median(r["prep_ms"] for r in results)
+    iters = last["iters"]
+
+    # sequential GPU simulator (the speedup denominator), same instance
+    seq_act = torch.empty(T, dtype=torch.int8, device=dev)
+    seq_ms = []
+    for i in range(max(1, args.seq_steps) + 1):
+        r = di.simulate(pol, "sequential", flags=pic.PIC_FLAG_TIMING, want_stock=False, out=seq_act)
+        if i:
+            seq_ms.append(r["total_ms"])
+        seq_res = r
+    seq_ms = statistics.median(seq_ms)
+    bit_exact_gpu = bool(torch.equal(seq_act, act)) and seq_res["total_cost"] == last["total_cost"]
+
+    # end to end through host buffers: H2D of the inputs, simulate, D2H of the actions
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).pin_memory()
+    host = {k: pin(getattr(inst, k)) for k in ("prod", "reg", "x0", "cost", "lam")}
+    host_np = {k: v.numpy() for k, v in host.items()}
+    host_act = torch.empty(T, dtype=torch.int8).pin_memory().numpy()
+    opts = pic.make_opts("picard", args.chunks, out_mem=pic.PIC_MEM_HOST, seg_window=args.seg_window)
+    h2d = sum(host_np[k].nbytes for k in host_np)
+    d2h = host_act.nbytes + 64  # actions + the result record
+    e2e_t = []
+    for i in range(args.e2e_steps + 2):
+        flush.fill_(1)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        di.load_host(host_np)
+        st, res = pic.pic_simulate(di.handle, pol.struct, opts, host_act)
+        t1 = time.perf_counter()
+        if i >= 2:
+            e2e_t.append(t1 - t0)
+    e2e_value = world * T / statistics.median(e2e_t)
+    bit_exact_e2e = bool(np.array_equal(host_act, act.cpu().numpy()))
+
+    # roofline of the dominant kernel (the persistent Picard kernel)
+    N = inst.N
+    alg_bytes = last["policy_calls"] * 6 + last["seg_replays"] * 16 * N
+    achieved = alg_bytes / (sim_ms / 1000.0) / 1e9
+    peak, peak_kind = load_peaks()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": workload_config(args, inst),
+        "iters": iters,
+        "seq_gpu": {"value": T / (seq_ms / 1000.0), "unit": UNIT, "ms": seq_ms},
+        "speedup_vs_seq_gpu": seq_ms / (t_ms / args.steps),
+        "bit_exact_vs_seq_gpu": bit_exact_gpu,
+        "phases_ms": {"tables": prep_ms, "picard_kernel": sim_ms,
+                      "step_device": t_ms / args.steps},
+        "policy_calls": last["policy_calls"], "segment_replays": last["seg_replays"],
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": profiled_traffic(),
+                     "kernel": "k_picard_int (persistent, all passes)",
+                     "peak_kind": peak_kind,
+                     "algorithmic_bytes": alg_bytes},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "bit_exact": bit_exact_e2e},
+        "gpu_launches": int(last["launches"]) * args.steps,
+        "clocks": clk,
+        "wall_s_timed_loop": wall,
+    }
+    if rank == 0 and world == 1:
+        rate, n, el, out = cpu_oracle_rate(inst, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"full {T}-order trajectory x{n} ({el:.1f} s), "
+                                          f"sequential C oracle, 1 thread"}
+        line["bit_exact_vs_oracle"] = bool(np.array_equal(out["actions"], act.cpu().numpy())) and \
+            out["total_cost"] == last["total_cost"]
+    elif rank == 0:
+        line["cpu_baseline"] = None
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    di.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

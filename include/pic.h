@@ -1,0 +1,160 @@
+/*
+ * pic.h -- C ABI of the B300 Picard-iteration policy simulator for the
+ * fulfillment-optimization (FO) problem ("Speeding up Policy Simulation in
+ * Supply Chain RL", Farias, Gijsbrechts, Khojandi, Peng, Zheng, ICML 2025).
+ *
+ * Problem (Sec. 2, policy simulation): given an initial state s_1, a horizon T
+ * and disturbances w_1..w_T, compute the sample path of actions
+ * a_t = pi(s_t, w_t), s_{t+1} = f(s_t, a_t, w_t).  Here (Sec. 3, FO model with
+ * the node-capacity part left out) the state is the inventory x[K][N] of K
+ * products at N warehouses (nodes), an order w_t = (product k_t, region r_t),
+ * the action is a warehouse holding stock of k_t or a^phi (-1, do not fulfil),
+ * and f decrements x[k_t][a_t].  Algorithm 1 (the Picard iteration) computes the
+ * same path by iterating M parallel processes over a cache of actions.
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns a pic_status; on failure it writes no output and
+ *    pic_last_error() returns a message (thread-local, valid until the next
+ *    call on the same thread).
+ *  - Array layouts are row-major, C-contiguous; sizes are element counts.
+ *  - The caller owns every buffer it passes.  An instance owns the device
+ *    copies it makes of its inputs (made at create / load time).
+ *  - Device work is ordered on the CUDA stream given in the call (NULL = the
+ *    legacy default stream); calls return after that work completed.
+ *  - Actions: -1 = a^phi (no fulfilment), otherwise a 0-based warehouse index.
+ *  - Limits: 1 <= N <= 127 (an action fits int8), 1 <= K <= 65535,
+ *    1 <= R <= 65535, 0 <= T <= 2^31-1; x0 >= 0; for the integer policies
+ *    |cost[r][n] - lam[k][n]| < 2^23.  Violations return PIC_ERR_INVALID_ARG.
+ */
+#ifndef PIC_H_
+#define PIC_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PIC_OK = 0,
+    PIC_ERR_INVALID_ARG = 1,   /* bad size, pointer, enum or value range */
+    PIC_ERR_CUDA = 2,          /* a CUDA runtime call failed (message says which) */
+    PIC_ERR_OOM = 3,           /* device allocation failed */
+    PIC_ERR_NOT_CONVERGED = 4, /* max_iters passes without a fixed point */
+    PIC_ERR_TIMEOUT = 5,       /* a device-side wait exceeded opts.timeout_ns */
+    PIC_ERR_UNSUPPORTED = 6    /* valid request this build does not implement */
+} pic_status;
+
+/* Policy kinds (pic_policy.kind). */
+enum {
+    PIC_POLICY_GREEDY = 0, /* argmin_{n: x[k][n]>0} cost[r][n]; Sec. 3.1 greedy */
+    PIC_POLICY_DUAL = 1,   /* argmin_{n: x[k][n]>0} cost[r][n] - lam[k][n]; bid-price, Sec. 4.2 */
+    PIC_POLICY_MLP = 2,    /* argmax over stocked n of an MLP score, Sec. 4.1 */
+    PIC_POLICY_GUMBEL = 3  /* argmax over stocked n of MLP score + Gumbel noise */
+};
+
+/* Simulation modes (pic_sim_opts.mode). */
+enum {
+    PIC_MODE_PICARD = 0,    /* Algorithm 1 on contiguous time chunks */
+    PIC_MODE_SEQUENTIAL = 1 /* one order at a time on the GPU (the baseline of Sec. 4) */
+};
+
+/* Where a pointer lives. */
+enum { PIC_MEM_HOST = 0, PIC_MEM_DEVICE = 1 };
+
+/* pic_sim_opts.flags bits */
+enum {
+    PIC_FLAG_NO_RESET = 1,   /* recompute every chunk on every pass (no t_reset skipping) */
+    PIC_FLAG_REUSE_TABLES = 2, /* keep the order/run tables of the previous call if its
+                                 chunking matches (skip the per-call preprocessing) */
+    PIC_FLAG_TIMING = 4        /* time the phases with CUDA events (pic_sim_result *_ms) */
+};
+
+typedef struct pic_instance pic_instance;
+
+/* One FO trajectory's inputs. */
+typedef struct {
+    int32_t T, N, K, R;
+    const int32_t* prod; /* [T] product k_t of order t, 0 <= k_t < K */
+    const int32_t* reg;  /* [T] region r_t of order t, 0 <= r_t < R */
+    const int32_t* x0;   /* [K][N] initial inventory s_1, >= 0 */
+    const int32_t* cost; /* [R][N] fulfilment cost (the paper's reward is -cost) */
+    const int32_t* lam;  /* [K][N] dual prices for PIC_POLICY_DUAL, or NULL */
+    int32_t mem;         /* PIC_MEM_HOST or PIC_MEM_DEVICE: where the arrays above live */
+    void* stream;        /* cudaStream_t for the copies and preprocessing, or NULL */
+} pic_instance_desc;
+
+/* Policy.  MLP parameters are BF16 bit patterns in DEVICE memory, borrowed for
+ * the duration of the call: W1[2N+16][H] with rows [cost (N) | stock (N) |
+ * region embedding (16)], b1[H], W2[H][N], b2[N], E[R][16]; H must be 256.
+ * Features: cost[r][n]/128, min(x[k][n],32)/32, E[r][0..16). */
+typedef struct {
+    int32_t kind;   /* PIC_POLICY_* */
+    int32_t hidden; /* H (MLP kinds only) */
+    const uint16_t *W1, *b1, *W2, *b2, *E;
+    uint64_t seed;  /* Gumbel noise key (PIC_POLICY_GUMBEL) */
+    int32_t traj;   /* trajectory id in the noise counter (PIC_POLICY_GUMBEL) */
+} pic_policy;
+
+typedef struct {
+    int32_t mode;             /* PIC_MODE_* */
+    int32_t num_chunks;       /* M >= 1 time chunks (Picard); 0 = pick automatically */
+    int32_t max_iters;        /* cap on passes; 0 = M + 1 (Prop. 1 bound plus the confirming pass) */
+    int32_t flags;            /* PIC_FLAG_* */
+    const int8_t* alpha_init; /* DEVICE [T] initial action cache, or NULL = all a^phi (Alg. 1) */
+    uint64_t timeout_ns;      /* bound on any device-side wait; 0 = 10 s */
+    int32_t out_mem;          /* PIC_MEM_HOST / PIC_MEM_DEVICE for the output arrays */
+    int32_t seg_window;       /* tuning: orders of one product per warp work unit; 0 = 64 */
+    void* stream;             /* cudaStream_t or NULL */
+} pic_sim_opts;
+
+typedef struct {
+    int64_t total_cost;   /* sum of cost[r_t][a_t] over fulfilled orders */
+    int64_t lost;         /* number of a^phi actions */
+    int64_t policy_calls; /* policy evaluations performed, over all passes */
+    int32_t iters;        /* passes of Algorithm 1's loop, including the confirming one
+                             (1 for PIC_MODE_SEQUENTIAL) */
+    int32_t num_chunks;   /* M used */
+    int64_t rescored;     /* MLP decisions re-scored in FP32 after the BF16 pass */
+    int64_t seg_replays;  /* warp work units (segments) replayed, over all passes */
+    int32_t launches;     /* kernels this call launched */
+    float prep_ms;        /* PIC_FLAG_TIMING: order tables (sort, runs, segments) */
+    float sim_ms;         /* PIC_FLAG_TIMING: the simulation kernel (all passes) */
+    float total_ms;       /* PIC_FLAG_TIMING: whole call on the device, first to last kernel */
+} pic_sim_result;
+
+/* Create an instance: validates and copies desc's arrays to the device, sized
+ * for (T, N, K, R).  *out receives an owned handle (free with
+ * pic_destroy_instance).  Errors: INVALID_ARG, OOM, CUDA. */
+pic_status pic_create_instance(const pic_instance_desc* desc, pic_instance** out);
+
+/* Replace an instance's inputs with new arrays of the same T, N, K, R (and lam
+ * present iff it was at create time), reusing its device memory.  Used to stream
+ * new trajectories through one instance.  Errors: INVALID_ARG, CUDA. */
+pic_status pic_instance_load(pic_instance* inst, const pic_instance_desc* desc);
+
+/* Release an instance and its device memory (NULL is a no-op). */
+void pic_destroy_instance(pic_instance* inst);
+
+/* Simulate one trajectory (Sec. 2 policy simulation).  PIC_MODE_PICARD runs
+ * Algorithm 1 with process m owning the contiguous orders
+ * [m*L, min((m+1)*L, T)), L = ceil(T/M), the cache initialised to a^phi (or
+ * opts.alpha_init), and stops at the first pass that changes no cached action;
+ * the result equals the sequential path (Prop. 1).  PIC_MODE_SEQUENTIAL runs the
+ * sequential definition directly.
+ *   actions_out  [T] int8 in opts.out_mem memory (required);
+ *   final_stock  [K][N] int32 in opts.out_mem memory, or NULL;
+ *   res          host struct, or NULL.
+ * Errors: INVALID_ARG, UNSUPPORTED, NOT_CONVERGED (actions_out then holds the
+ * last cache), TIMEOUT, CUDA. */
+pic_status pic_simulate(pic_instance* inst, const pic_policy* pol, const pic_sim_opts* opts,
+                        int8_t* actions_out, int32_t* final_stock, pic_sim_result* res);
+
+/* Message for the last non-OK status on this thread ("" if none). */
+const char* pic_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIC_H_ */

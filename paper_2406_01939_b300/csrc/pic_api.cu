@@ -1,0 +1,398 @@
+// C ABI entry points (include/pic.h): instance management and the simulate call.
+#include <cstdarg>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "pic_device.cuh"
+
+using namespace pic;
+
+struct pic_instance {
+    Instance I;
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+pic_status fail(pic_status s, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+#define CU(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(e_ == cudaErrorMemoryAllocation ? PIC_ERR_OOM : PIC_ERR_CUDA,   \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                      \
+    } while (0)
+
+// Validation of the value ranges the kernels rely on (one pass over the inputs).
+__global__ void k_validate(int T, int N, int K, int R, const int32_t* __restrict__ prod,
+                           const int32_t* __restrict__ reg, const int32_t* __restrict__ x0,
+                           const int32_t* __restrict__ cost, const int32_t* __restrict__ lam,
+                           int* bad) {
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    int b = 0;
+    for (long long t = gid; t < T; t += stride) {
+        if ((unsigned)prod[t] >= (unsigned)K) b |= 1;
+        if ((unsigned)reg[t] >= (unsigned)R) b |= 2;
+    }
+    for (long long i = gid; i < (long long)K * N; i += stride)
+        if (x0[i] < 0) b |= 4;
+    const int lim = 1 << 23;
+    for (long long i = gid; i < (long long)R * N; i += stride) {
+        const int c = cost[i];
+        if (c <= -lim || c >= lim) b |= 8;
+    }
+    if (lam)
+        for (long long i = gid; i < (long long)K * N; i += stride) {
+            const int l = lam[i];
+            if (l <= -lim || l >= lim) b |= 16;
+        }
+    if (b) atomicOr(bad, b);
+}
+
+// Exact check of |cost[r][n] - lam[k][n]| < 2^23 via per-warehouse extremes.
+__global__ void k_validate_dual(int N, int K, int R, const int32_t* __restrict__ cost,
+                                const int32_t* __restrict__ lam, int* bad) {
+    const int n = blockIdx.x;
+    long long cmin = LLONG_MAX, cmax = LLONG_MIN, lmin = LLONG_MAX, lmax = LLONG_MIN;
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        cmin = min(cmin, (long long)cost[(size_t)r * N + n]);
+        cmax = max(cmax, (long long)cost[(size_t)r * N + n]);
+    }
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        lmin = min(lmin, (long long)lam[(size_t)k * N + n]);
+        lmax = max(lmax, (long long)lam[(size_t)k * N + n]);
+    }
+    __shared__ long long red[4][32];
+    for (int o = 16; o > 0; o >>= 1) {
+        cmin = min(cmin, __shfl_xor_sync(kFull, cmin, o));
+        cmax = max(cmax, __shfl_xor_sync(kFull, cmax, o));
+        lmin = min(lmin, __shfl_xor_sync(kFull, lmin, o));
+        lmax = max(lmax, __shfl_xor_sync(kFull, lmax, o));
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { red[0][w] = cmin; red[1][w] = cmax; red[2][w] = lmin; red[3][w] = lmax; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+            cmin = min(cmin, red[0][i]); cmax = max(cmax, red[1][i]);
+            lmin = min(lmin, red[2][i]); lmax = max(lmax, red[3][i]);
+        }
+        const long long lim = 1 << 23;
+        if (cmax - lmin >= lim || cmin - lmax <= -lim) atomicOr(bad, 32);
+    }
+}
+
+__global__ void k_gather_alpha(const int8_t* __restrict__ alpha_t, const int32_t* __restrict__ perm,
+                               int T, int N, int8_t* __restrict__ alpha_s, int* bad) {
+    long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= T) return;
+    int a = alpha_t[perm[j]];
+    if (a < -1 || a >= N) { atomicOr(bad, 64); a = -1; }
+    alpha_s[j] = (int8_t)a;
+}
+
+// Histogram of the cache per segment (used when the cache starts from alpha_init).
+__global__ void k_seg_hist(const int8_t* __restrict__ alpha_s, const int32_t* __restrict__ run_start,
+                           const int32_t* __restrict__ seg_run, const Ctrl* ctrl, int NP,
+                           int32_t* __restrict__ agg) {
+    extern __shared__ int sh[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int* h = sh + w * NP;
+    const int nseg = ctrl->nseg;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int s = gw; s < nseg; s += nw) {
+        for (int i = lane; i < NP; i += 32) h[i] = 0;
+        __syncwarp();
+        const int j0 = run_start[seg_run[s]], j1 = run_start[seg_run[s + 1]];
+        for (int j = j0 + lane; j < j1; j += 32) {
+            const int a = alpha_s[j];
+            if (a >= 0) atomicAdd(&h[a], 1);
+        }
+        __syncwarp();
+        for (int i = lane; i < NP; i += 32) agg[(size_t)s * NP + i] = h[i];
+        __syncwarp();
+    }
+}
+
+bool valid_desc(const pic_instance_desc* d) {
+    return d && d->T >= 0 && d->N >= 1 && d->N <= 127 && d->K >= 1 && d->K <= 65535 && d->R >= 1 &&
+           d->R <= 65535 && (d->T == 0 || (d->prod && d->reg)) && d->x0 && d->cost &&
+           (d->mem == PIC_MEM_HOST || d->mem == PIC_MEM_DEVICE);
+}
+
+template <typename T>
+cudaError_t dmalloc(T** p, size_t n) {
+    return cudaMalloc((void**)p, sizeof(T) * (n ? n : 1));
+}
+
+void free_instance(Instance& I) {
+    void* ptrs[] = {I.prod, I.reg, I.x0, I.cost, I.lam, I.perm, I.prod_s, I.reg_s, I.pcount,
+                    I.pstart, I.run_start, I.run_of, I.seg_run, I.seg_of_run, I.seg_prod, I.seg_cf,
+                    I.seg_ce, I.alpha_s, I.agg, I.carry, I.sbtot, I.fc, I.seg_cost, I.seg_lost,
+                    I.xfin, I.xwork, I.act_t, I.tmp_a, I.tmp_b, I.tmp_c, I.scan_blk, I.hist,
+                    I.ctrl};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (int i = 0; i < 4; ++i)
+        if (I.ev[i]) cudaEventDestroy(I.ev[i]);
+}
+
+pic_status copy_inputs(Instance& I, const pic_instance_desc* d, cudaStream_t st) {
+    const cudaMemcpyKind kind = d->mem == PIC_MEM_HOST ? cudaMemcpyHostToDevice
+                                                       : cudaMemcpyDeviceToDevice;
+    if (I.T) {
+        CU(cudaMemcpyAsync(I.prod, d->prod, sizeof(int32_t) * I.T, kind, st));
+        CU(cudaMemcpyAsync(I.reg, d->reg, sizeof(int32_t) * I.T, kind, st));
+    }
+    CU(cudaMemcpyAsync(I.x0, d->x0, sizeof(int32_t) * I.K * I.N, kind, st));
+    CU(cudaMemcpyAsync(I.cost, d->cost, sizeof(int32_t) * I.R * I.N, kind, st));
+    if (I.has_lam) CU(cudaMemcpyAsync(I.lam, d->lam, sizeof(int32_t) * I.K * I.N, kind, st));
+    // validate on the device
+    int* bad = &I.ctrl->pad0;
+    CU(cudaMemsetAsync(bad, 0, sizeof(int), st));
+    k_validate<<<2 * I.num_sms, 256, 0, st>>>(I.T, I.N, I.K, I.R, I.prod, I.reg, I.x0, I.cost,
+                                              I.has_lam ? I.lam : nullptr, bad);
+    if (I.has_lam) k_validate_dual<<<I.N, 256, 0, st>>>(I.N, I.K, I.R, I.cost, I.lam, bad);
+    CU(cudaGetLastError());
+    int hb = 0;
+    CU(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (hb & 1) return fail(PIC_ERR_INVALID_ARG, "prod[t] outside [0, K)");
+    if (hb & 2) return fail(PIC_ERR_INVALID_ARG, "reg[t] outside [0, R)");
+    if (hb & 4) return fail(PIC_ERR_INVALID_ARG, "x0 has a negative entry");
+    if (hb & (8 | 16 | 32))
+        return fail(PIC_ERR_INVALID_ARG, "|cost|, |lam| or |cost - lam| not below 2^23");
+    return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pic_last_error(void) { return g_err; }
+
+pic_status pic_create_instance(const pic_instance_desc* d, pic_instance** out) {
+    g_err[0] = 0;
+    if (!out) return fail(PIC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!valid_desc(d)) return fail(PIC_ERR_INVALID_ARG, "invalid instance descriptor (sizes, pointers or mem)");
+    pic_instance* h = new (std::nothrow) pic_instance();
+    if (!h) return fail(PIC_ERR_OOM, "host allocation failed");
+    Instance& I = h->I;
+    memset(&I, 0, sizeof(I));
+    I.T = d->T; I.N = d->N; I.K = d->K; I.R = d->R;
+    I.NP = ((d->N + 31) / 32) * 32;
+    I.has_lam = d->lam != nullptr;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (!e) e = cudaDeviceGetAttribute(&I.num_sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t T = (size_t)I.T, K = I.K, N = I.N;
+    // segments <= runs <= T for any window; per-segment histograms are sized per window later
+    I.smax = (int64_t)T + (int64_t)K + 2;
+    const size_t nblk_radix = (T + 4095) / 4096 + 1;
+    const size_t nscan = (T > 256 * nblk_radix ? T : 256 * nblk_radix) + K + 2;
+    I.hist_cap = 256 * nblk_radix;
+    const size_t S = (size_t)I.smax;
+    if (!e) e = dmalloc(&I.prod, T);
+    if (!e) e = dmalloc(&I.reg, T);
+    if (!e) e = dmalloc(&I.x0, K * N);
+    if (!e) e = dmalloc(&I.cost, (size_t)I.R * N);
+    if (!e && I.has_lam) e = dmalloc(&I.lam, K * N);
+    if (!e) e = dmalloc(&I.perm, T);
+    if (!e) e = dmalloc(&I.prod_s, T);
+    if (!e) e = dmalloc(&I.reg_s, T);
+    if (!e) e = dmalloc(&I.pcount, K + 1);
+    if (!e) e = dmalloc(&I.pstart, K + 1);
+    if (!e) e = dmalloc(&I.run_start, T + 2);
+    if (!e) e = dmalloc(&I.run_of, T + 1);
+    if (!e) e = dmalloc(&I.seg_run, S + 1);
+    if (!e) e = dmalloc(&I.seg_of_run, T + 1);
+    if (!e) e = dmalloc(&I.seg_prod, S);
+    if (!e) e = dmalloc(&I.seg_cf, S);
+    if (!e) e = dmalloc(&I.seg_ce, S);
+    if (!e) e = dmalloc(&I.alpha_s, T);
+    if (!e) e = dmalloc(&I.fc, 2 * K);
+    if (!e) e = dmalloc(&I.seg_cost, S);
+    if (!e) e = dmalloc(&I.seg_lost, S);
+    if (!e) e = dmalloc(&I.xfin, K * N);
+    if (!e) e = dmalloc(&I.xwork, K * N);
+    if (!e) e = dmalloc(&I.act_t, T);
+    if (!e) e = dmalloc(&I.tmp_a, T);
+    if (!e) e = dmalloc(&I.tmp_b, T);
+    if (!e) e = dmalloc(&I.scan_blk, nscan / 2048 + 2);
+    if (!e) e = dmalloc(&I.hist, (size_t)I.hist_cap);
+    if (!e) e = cudaMalloc((void**)&I.ctrl, sizeof(Ctrl));
+    for (int i = 0; i < 4 && !e; ++i) e = cudaEventCreate(&I.ev[i]);
+    // per-segment histograms: allocated lazily at the first simulate (size depends on W)
+    if (e) {
+        free_instance(I);
+        delete h;
+        return fail(e == cudaErrorMemoryAllocation ? PIC_ERR_OOM : PIC_ERR_CUDA,
+                    "allocation failed: %s", cudaGetErrorString(e));
+    }
+    cudaStream_t st = (cudaStream_t)d->stream;
+    if (cudaMemsetAsync(I.ctrl, 0, sizeof(Ctrl), st) != cudaSuccess) {
+        free_instance(I);
+        delete h;
+        return fail(PIC_ERR_CUDA, "memset failed");
+    }
+    pic_status s = copy_inputs(I, d, st);
+    if (s != PIC_OK) {
+        free_instance(I);
+        delete h;
+        return s;
+    }
+    *out = h;
+    return PIC_OK;
+}
+
+pic_status pic_instance_load(pic_instance* h, const pic_instance_desc* d) {
+    g_err[0] = 0;
+    if (!h) return fail(PIC_ERR_INVALID_ARG, "instance is NULL");
+    if (!valid_desc(d)) return fail(PIC_ERR_INVALID_ARG, "invalid instance descriptor");
+    Instance& I = h->I;
+    if (d->T != I.T || d->N != I.N || d->K != I.K || d->R != I.R || (d->lam != nullptr) != (I.has_lam != 0))
+        return fail(PIC_ERR_INVALID_ARG, "shape differs from the instance's");
+    I.tables_m = 0;  // the order tables describe the old stream
+    return copy_inputs(I, d, (cudaStream_t)d->stream);
+}
+
+void pic_destroy_instance(pic_instance* h) {
+    if (!h) return;
+    free_instance(h->I);
+    delete h;
+}
+
+pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_opts* opts,
+                        int8_t* actions_out, int32_t* final_stock, pic_sim_result* res) {
+    g_err[0] = 0;
+    if (!h || !pol || !opts || !actions_out)
+        return fail(PIC_ERR_INVALID_ARG, "instance, policy, opts and actions_out are required");
+    Instance& I = h->I;
+    if (opts->mode != PIC_MODE_PICARD && opts->mode != PIC_MODE_SEQUENTIAL)
+        return fail(PIC_ERR_INVALID_ARG, "unknown mode %d", opts->mode);
+    if (opts->out_mem != PIC_MEM_HOST && opts->out_mem != PIC_MEM_DEVICE)
+        return fail(PIC_ERR_INVALID_ARG, "unknown out_mem %d", opts->out_mem);
+    if (pol->kind < PIC_POLICY_GREEDY || pol->kind > PIC_POLICY_GUMBEL)
+        return fail(PIC_ERR_INVALID_ARG, "unknown policy kind %d", pol->kind);
+    if (pol->kind == PIC_POLICY_DUAL && !I.has_lam)
+        return fail(PIC_ERR_INVALID_ARG, "bid-price policy needs an instance created with lam");
+    if (pol->kind >= PIC_POLICY_MLP)
+        return fail(PIC_ERR_UNSUPPORTED, "MLP policies are not built into this library yet");
+    if (opts->num_chunks < 0 || opts->max_iters < 0 || opts->seg_window < 0)
+        return fail(PIC_ERR_INVALID_ARG, "negative num_chunks, max_iters or seg_window");
+    cudaStream_t st = (cudaStream_t)opts->stream;
+    const size_t T = I.T, K = I.K, N = I.N;
+    const bool host_out = opts->out_mem == PIC_MEM_HOST;
+    const cudaMemcpyKind okind = host_out ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    const bool timing = (opts->flags & PIC_FLAG_TIMING) != 0;
+    I.launches = 0;
+    if (timing) CU(cudaEventRecord(I.ev[0], st));
+    CU(cudaMemsetAsync(I.ctrl, 0, offsetof(Ctrl, nruns), st));
+    int M = 1, iters_cap = 1;
+    if (opts->mode == PIC_MODE_SEQUENTIAL) {
+        CU(cudaMemcpyAsync(I.xwork, I.x0, sizeof(int32_t) * K * N, cudaMemcpyDeviceToDevice, st));
+        if (timing) CU(cudaEventRecord(I.ev[1], st));
+        if (T) CU(sequential_int(&I, pol->kind, st));
+        if (timing) CU(cudaEventRecord(I.ev[2], st));
+        if (T) CU(cudaMemcpyAsync(actions_out, I.act_t, T, okind, st));
+        if (final_stock)
+            CU(cudaMemcpyAsync(final_stock, I.xwork, sizeof(int32_t) * K * N, okind, st));
+    } else {
+        M = opts->num_chunks ? opts->num_chunks : (int)((T + 255) / 256);
+        if (M < 1) M = 1;
+        if (T && M > (int)T) M = (int)T;
+        const int W = opts->seg_window ? opts->seg_window : kSegWindow;
+        iters_cap = opts->max_iters ? opts->max_iters : M + 1;
+        // tables + per-segment state (capacity for this window)
+        const int64_t smax = (int64_t)2 * K + (int64_t)(T + W - 1) / W + 2;
+        if (!I.agg || smax > I.smax_agg) {
+            if (I.agg) { cudaFree(I.agg); cudaFree(I.carry); cudaFree(I.sbtot); }
+            I.agg = I.carry = I.sbtot = nullptr;
+            I.smax_agg = 0;
+            CU(dmalloc(&I.agg, (size_t)smax * I.NP));
+            CU(dmalloc(&I.carry, (size_t)smax * I.NP));
+            CU(dmalloc(&I.sbtot, (size_t)smax * I.NP));
+            I.smax_agg = smax;
+        }
+        const bool reuse = (opts->flags & PIC_FLAG_REUSE_TABLES) && I.tables_m == M && I.tables_w == W;
+        if (!reuse) {
+            CU(build_tables(&I, M, W, st));
+            I.tables_m = M;
+            I.tables_w = W;
+        }
+        CU(cudaMemsetAsync(I.agg, 0, sizeof(int32_t) * (size_t)smax * I.NP, st));
+        CU(cudaMemsetAsync(I.carry, 0, sizeof(int32_t) * (size_t)smax * I.NP, st));
+        CU(cudaMemsetAsync(I.sbtot, 0, sizeof(int32_t) * (size_t)smax * I.NP, st));
+        CU(cudaMemsetAsync(I.fc, 0xFF, sizeof(int32_t) * K, st));  // pass 0: everything "changed"
+        CU(cudaMemcpyAsync(I.xfin, I.x0, sizeof(int32_t) * K * N, cudaMemcpyDeviceToDevice, st));
+        if (T) {
+            if (opts->alpha_init) {
+                int* bad = &I.ctrl->pad0;
+                k_gather_alpha<<<(int)((T + 255) / 256), 256, 0, st>>>(opts->alpha_init, I.perm, (int)T,
+                                                                     (int)N, I.alpha_s, bad);
+                k_seg_hist<<<2 * I.num_sms, 256, 8 * I.NP * sizeof(int), st>>>(
+                    I.alpha_s, I.run_start, I.seg_run, I.ctrl, I.NP, I.agg);
+                CU(cudaGetLastError());
+                I.launches += 2;
+            } else {
+                CU(cudaMemsetAsync(I.alpha_s, 0xFF, T, st));  // a^phi everywhere (Alg. 1 line 1)
+            }
+            if (timing) CU(cudaEventRecord(I.ev[1], st));
+            CU(picard_int(&I, pol->kind, iters_cap, opts->flags, opts->alpha_init,
+                          opts->timeout_ns ? opts->timeout_ns : 10000000000ull, st));
+            if (timing) CU(cudaEventRecord(I.ev[2], st));
+            CU(finish_outputs(&I, st));
+            CU(cudaMemcpyAsync(actions_out, I.act_t, T, okind, st));
+        }
+        if (final_stock)
+            CU(cudaMemcpyAsync(final_stock, I.xfin, sizeof(int32_t) * K * N, okind, st));
+    }
+    if (timing) {
+        if (!T) {
+            CU(cudaEventRecord(I.ev[1], st));
+            CU(cudaEventRecord(I.ev[2], st));
+        }
+        CU(cudaEventRecord(I.ev[3], st));
+    }
+    Ctrl hc;
+    CU(cudaMemcpyAsync(&hc, I.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (hc.pad0 & 64) return fail(PIC_ERR_INVALID_ARG, "alpha_init holds a value outside [-1, N)");
+    if (hc.err) return fail((pic_status)hc.err, "device wait exceeded timeout (%llu ns)",
+                            (unsigned long long)opts->timeout_ns);
+    if (res) {
+        res->total_cost = hc.total_cost;
+        res->lost = hc.lost;
+        res->policy_calls = (int64_t)hc.policy_calls;
+        res->iters = T ? hc.iters : 1;
+        res->num_chunks = M;
+        res->rescored = (int64_t)hc.rescored;
+        res->seg_replays = (int64_t)hc.seg_replays;
+        res->launches = I.launches;
+        res->prep_ms = res->sim_ms = res->total_ms = 0.0f;
+        if (timing) {
+            CU(cudaEventElapsedTime(&res->prep_ms, I.ev[0], I.ev[1]));
+            CU(cudaEventElapsedTime(&res->sim_ms, I.ev[1], I.ev[2]));
+            CU(cudaEventElapsedTime(&res->total_ms, I.ev[0], I.ev[3]));
+        }
+    }
+    if (T && opts->mode == PIC_MODE_PICARD && !hc.converged)
+        return fail(PIC_ERR_NOT_CONVERGED, "no fixed point within %d passes", iters_cap);
+    return PIC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,343 @@
+// Per-call preprocessing of one trajectory's order stream.
+//
+// Algorithm 1 assigns process m the contiguous orders [m*L, (m+1)*L).  Under
+// inventory independence (Assumption 1 of Sec. 3.2) the orders of different
+// products inside a process never interact, so a process splits into "runs":
+// its orders of one product, replayed in time order.  The cached prefix that a
+// run must apply before its first order involves only orders of the same
+// product, so the kernels work in product-major order:
+//   sorted position j  ->  (product, time) ascending (stable radix sort by product),
+//   run   = maximal range of sorted positions with one product and one chunk,
+//   segment = consecutive runs of one product whose first order falls in one
+//             window of W sorted positions of that product (the unit one warp
+//             replays), chain = all segments of one product.
+// Everything here is rebuilt from the raw order stream on the device.
+#include <cstdio>
+
+#include "pic_device.cuh"
+
+namespace pic {
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+constexpr int kRadixThreads = 256;           // 8 warps
+constexpr int kRadixPerWarp = 512;           // 16 rounds of 32
+constexpr int kRadixTile = 8 * kRadixPerWarp; // 4096 keys per CTA
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int* total) {
+    __shared__ int warp_sums[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int s = lane < kScanThreads / 32 ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(kFull, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < kScanThreads / 32) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    int before = w ? warp_sums[w - 1] : 0;
+    *total = warp_sums[kScanThreads / 32 - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void k_scan_reduce(const int32_t* __restrict__ in, int n, int32_t* __restrict__ blk) {
+    const long long base = (long long)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    int s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i)
+        if (base + i < n) s += in[base + i];
+    int tot;
+    block_exclusive_scan(s, &tot);
+    if (threadIdx.x == 0) blk[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_blocks(int32_t* blk, int nb, int32_t* total) {
+    int carry = 0;
+    for (int b0 = 0; b0 < nb; b0 += kScanThreads) {
+        int i = b0 + threadIdx.x;
+        int v = i < nb ? blk[i] : 0;
+        int tot;
+        int ex = block_exclusive_scan(v, &tot);
+        if (i < nb) blk[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__global__ void k_scan_down(const int32_t* __restrict__ in, int32_t* __restrict__ out, int n,
+                            const int32_t* __restrict__ blk) {
+    const long long base = (long long)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = base + i < n ? in[base + i] : 0;
+        s += v[i];
+    }
+    int tot;
+    int ex = block_exclusive_scan(s, &tot) + blk[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        if (base + i < n) out[base + i] = ex;
+        ex += v[i];
+    }
+}
+
+// --------------------------------------------------------------------------- radix sort
+__global__ void k_radix_hist(const int32_t* __restrict__ keys, int n, int shift, int32_t* hist,
+                             int nblk) {
+    __shared__ int h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const long long base = (long long)blockIdx.x * kRadixTile;
+    for (int i = threadIdx.x; i < kRadixTile; i += kRadixThreads) {
+        long long idx = base + i;
+        if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 255], 1);
+    }
+    __syncthreads();
+    hist[(long long)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter: ranks inside the tile follow (warp, round, lane) = index order.
+__global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
+    const int32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in, int n, int shift,
+    const int32_t* __restrict__ offs, int nblk, int32_t* __restrict__ keys_out,
+    int32_t* __restrict__ vals_out) {
+    __shared__ int wh[8][256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < 8 * 256; i += kRadixThreads) (&wh[0][0])[i] = 0;
+    __syncthreads();
+    const long long base = (long long)blockIdx.x * kRadixTile + (long long)w * kRadixPerWarp;
+    int local[16];
+    int dig[16];
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int rd = 0; rd < 16; ++rd) {
+        long long idx = base + rd * 32 + lane;
+        bool valid = idx < n;
+        int d = valid ? (keys_in[idx] >> shift) & 255 : 256 + lane;  // unique for invalid lanes
+        unsigned peers = __match_any_sync(kFull, d);
+        int rank = __popc(peers & lt);
+        int off = valid ? wh[w][d] : 0;
+        __syncwarp();
+        if (valid && (__ffs(peers) - 1) == lane) wh[w][d] += __popc(peers);
+        __syncwarp();
+        local[rd] = off + rank;
+        dig[rd] = d;
+    }
+    __syncthreads();
+    if (threadIdx.x < 256) {
+        int run = 0;
+#pragma unroll
+        for (int ww = 0; ww < 8; ++ww) {
+            int tmp = wh[ww][threadIdx.x];
+            wh[ww][threadIdx.x] = run;
+            run += tmp;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int rd = 0; rd < 16; ++rd) {
+        long long idx = base + rd * 32 + lane;
+        if (idx < n) {
+            int d = dig[rd];
+            long long pos = (long long)offs[(long long)d * nblk + blockIdx.x] + wh[w][d] + local[rd];
+            keys_out[pos] = keys_in[idx];
+            vals_out[pos] = vals_in ? vals_in[idx] : (int32_t)idx;
+        }
+    }
+}
+
+// --------------------------------------------------------------------------- tables
+__global__ void k_hist_prod(const int32_t* __restrict__ prod, int n, int32_t* cnt) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool valid = idx < n;
+    int k = valid ? prod[idx] : -1 - (int)(threadIdx.x & 31);
+    unsigned peers = __match_any_sync(kFull, k);
+    if (valid && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) atomicAdd(&cnt[k], __popc(peers));
+}
+
+// Region gather and run-start flags: a run starts where the product or the
+// chunk (t / L) changes between consecutive sorted positions.
+__global__ void k_run_flags(const int32_t* __restrict__ perm, const int32_t* __restrict__ prod_s,
+                            const int32_t* __restrict__ reg, int32_t* __restrict__ reg_s, int T,
+                            int L, int32_t* __restrict__ flag) {
+    long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= T) return;
+    int t = perm[j];
+    reg_s[j] = reg[t];
+    int f = 1;
+    if (j > 0) f = (prod_s[j] != prod_s[j - 1]) || (t / L != perm[j - 1] / L);
+    flag[j] = f;
+}
+
+__global__ void k_runs(const int32_t* __restrict__ flag, const int32_t* __restrict__ ex, int T,
+                       int32_t* __restrict__ run_of, int32_t* __restrict__ run_start, Ctrl* ctrl) {
+    long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= T) return;
+    int r = ex[j] + flag[j] - 1;
+    run_of[j] = r;
+    if (flag[j]) run_start[r] = (int)j;
+    if (j == T - 1) {
+        run_start[r + 1] = T;
+        ctrl->nruns = r + 1;
+    }
+}
+
+__global__ void k_seg_flags(const int32_t* __restrict__ run_start, const int32_t* __restrict__ prod_s,
+                            const int32_t* __restrict__ pstart, int W, int T, const Ctrl* ctrl,
+                            int32_t* __restrict__ flag) {
+    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= T) return;
+    const int nruns = ctrl->nruns;
+    if (r >= nruns) { flag[r] = 0; return; }
+    int j = run_start[r];
+    int k = prod_s[j];
+    int f = 1;
+    if (r > 0) {
+        int jp = run_start[r - 1];
+        int kp = prod_s[jp];
+        f = (k != kp) || ((j - pstart[k]) / W != (jp - pstart[kp]) / W);
+    }
+    flag[r] = f;
+}
+
+__global__ void k_segs(const int32_t* __restrict__ flag, const int32_t* __restrict__ ex, int T,
+                       const int32_t* __restrict__ run_start, const int32_t* __restrict__ prod_s,
+                       int32_t* __restrict__ seg_of_run, int32_t* __restrict__ seg_run,
+                       int32_t* __restrict__ seg_prod, Ctrl* ctrl) {
+    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nruns = ctrl->nruns;
+    if (r >= nruns) return;
+    int s = ex[r] + flag[r] - 1;
+    seg_of_run[r] = s;
+    if (flag[r]) {
+        seg_run[s] = (int)r;
+        seg_prod[s] = prod_s[run_start[r]];
+    }
+    if (r == nruns - 1) {
+        seg_run[s + 1] = nruns;
+        ctrl->nseg = s + 1;
+    }
+}
+
+__global__ void k_chains(const int32_t* __restrict__ seg_prod, const int32_t* __restrict__ pstart,
+                         const int32_t* __restrict__ run_of, const int32_t* __restrict__ seg_of_run,
+                         int T, const Ctrl* ctrl, int32_t* __restrict__ cf, int32_t* __restrict__ ce) {
+    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= ctrl->nseg) return;
+    int k = seg_prod[s];
+    cf[s] = seg_of_run[run_of[pstart[k]]];
+    ce[s] = seg_of_run[run_of[pstart[k + 1] - 1]] + 1;
+}
+
+__global__ void k_scatter_actions(const int8_t* __restrict__ alpha_s, const int32_t* __restrict__ perm,
+                                  int T, int8_t* __restrict__ act_t) {
+    long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < T) act_t[perm[j]] = alpha_s[j];
+}
+
+__global__ void k_reduce_costs(const long long* __restrict__ seg_cost,
+                               const int32_t* __restrict__ seg_lost, Ctrl* ctrl) {
+    const int nseg = ctrl->nseg;
+    long long c = 0, l = 0;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < nseg;
+         s += (long long)gridDim.x * blockDim.x) {
+        c += seg_cost[s];
+        l += seg_lost[s];
+    }
+    c = warp_sum_i64(c);
+    l = warp_sum_i64(l);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd((unsigned long long*)&ctrl->total_cost, (unsigned long long)c);
+        atomicAdd((unsigned long long*)&ctrl->lost, (unsigned long long)l);
+    }
+}
+
+inline int nblocks(long long n, int per) { return (int)((n + per - 1) / per); }
+
+}  // namespace
+
+cudaError_t scan_exclusive(const int32_t* in, int32_t* out, int n, int32_t* total_dev, int32_t* blk,
+                           cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    int nb = nblocks(n, kScanTile);
+    k_scan_reduce<<<nb, kScanThreads, 0, st>>>(in, n, blk);
+    k_scan_blocks<<<1, kScanThreads, 0, st>>>(blk, nb, total_dev);
+    k_scan_down<<<nb, kScanThreads, 0, st>>>(in, out, n, blk);
+    return cudaGetLastError();
+}
+
+cudaError_t build_tables(Instance* I, int M, int W, cudaStream_t st) {
+    const int T = I->T, K = I->K;
+    cudaError_t e;
+    if (T == 0) {
+        e = cudaMemsetAsync(I->ctrl, 0, sizeof(Ctrl), st);
+        return e;
+    }
+    // kernel launches made below: per radix pass 2 + a 3-kernel scan; then
+    // product histogram + scan, run flags + scan + runs, segment flags + scan +
+    // segments + chains
+    I->launches += (K <= 256 ? 1 : 2) * 5 + 4 + 5 + 6;
+    // 1. stable sort of (product, time) by product: LSD radix, 8-bit digits
+    const int nblk = nblocks(T, kRadixTile);
+    const int passes = K <= 256 ? 1 : 2;
+    const int32_t* kin = I->prod;
+    const int32_t* vin = nullptr;
+    int32_t* kout = passes == 2 ? I->tmp_a : I->prod_s;
+    int32_t* vout = passes == 2 ? I->tmp_b : I->perm;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        k_radix_hist<<<nblk, kRadixThreads, 0, st>>>(kin, T, shift, I->hist, nblk);
+        if ((e = scan_exclusive(I->hist, I->hist, 256 * nblk, nullptr, I->scan_blk, st))) return e;
+        k_radix_scatter<<<nblk, kRadixThreads, 0, st>>>(kin, vin, T, shift, I->hist, nblk, kout, vout);
+        kin = kout;
+        vin = vout;
+        kout = I->prod_s;
+        vout = I->perm;
+    }
+    // 2. per-product counts and first positions
+    cudaMemsetAsync(I->pcount, 0, sizeof(int32_t) * (K + 1), st);
+    k_hist_prod<<<nblocks(T, 256), 256, 0, st>>>(I->prod, T, I->pcount);
+    if ((e = scan_exclusive(I->pcount, I->pstart, K + 1, nullptr, I->scan_blk, st))) return e;
+    // 3. runs for M chunks of L orders
+    const long long L = ((long long)T + M - 1) / M;
+    k_run_flags<<<nblocks(T, 256), 256, 0, st>>>(I->perm, I->prod_s, I->reg, I->reg_s, T, (int)L,
+                                                  I->tmp_a);
+    if ((e = scan_exclusive(I->tmp_a, I->tmp_b, T, nullptr, I->scan_blk, st))) return e;
+    k_runs<<<nblocks(T, 256), 256, 0, st>>>(I->tmp_a, I->tmp_b, T, I->run_of, I->run_start, I->ctrl);
+    // 4. segments (window W per product) and chains
+    k_seg_flags<<<nblocks(T, 256), 256, 0, st>>>(I->run_start, I->prod_s, I->pstart, W, T, I->ctrl,
+                                                  I->tmp_a);
+    if ((e = scan_exclusive(I->tmp_a, I->tmp_b, T, nullptr, I->scan_blk, st))) return e;
+    k_segs<<<nblocks(T, 256), 256, 0, st>>>(I->tmp_a, I->tmp_b, T, I->run_start, I->prod_s,
+                                             I->seg_of_run, I->seg_run, I->seg_prod, I->ctrl);
+    k_chains<<<nblocks(I->smax, 256), 256, 0, st>>>(I->seg_prod, I->pstart, I->run_of,
+                                                     I->seg_of_run, T, I->ctrl, I->seg_cf, I->seg_ce);
+    return cudaGetLastError();
+}
+
+cudaError_t finish_outputs(Instance* I, cudaStream_t st) {
+    if (I->T == 0) return cudaSuccess;
+    I->launches += 2;
+    k_scatter_actions<<<nblocks(I->T, 256), 256, 0, st>>>(I->alpha_s, I->perm, I->T, I->act_t);
+    k_reduce_costs<<<2 * I->num_sms, 256, 0, st>>>(I->seg_cost, I->seg_lost, I->ctrl);
+    return cudaGetLastError();
+}
+
+}  // namespace pic

@@ -1,0 +1,51 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point
+that include/pic.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2406_01939_b300 import build as pic_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*[\w\s\*]*?\b(pic_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for want in ("pic_create_instance", "pic_instance_load", "pic_destroy_instance",
+                 "pic_simulate", "pic_last_error"):
+        assert want in names
+
+
+def test_library_loads_and_exports_every_declared_symbol():
+    path = pic_build.build()
+    lib = ctypes.CDLL(path)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_last_error_is_empty_string_initially():
+    lib = ctypes.CDLL(pic_build.build())
+    lib.pic_last_error.restype = ctypes.c_char_p
+    assert lib.pic_last_error() == b""
+
+
+def test_null_arguments_rejected_without_gpu():
+    """Argument checks run before any device work."""
+    import paper_2406_01939_b300 as pic
+    L = pic.lib()
+    h = ctypes.c_void_p()
+    assert L.pic_create_instance(None, ctypes.byref(h)) == pic.PIC_ERR_INVALID_ARG
+    assert "descriptor" in pic.pic_last_error()
+    assert L.pic_simulate(None, None, None, None, None, None) == pic.PIC_ERR_INVALID_ARG

@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--seq-steps", type=int, default=3)
     p.add_argument("--e2e-steps", type=int, default=20)
     p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--T", type=int, default=1 << 20, help="orders (smaller only for profiling)")
     return p.parse_args()
 
 
@@ -155,7 +156,7 @@ def cpu_oracle_rate(inst, seconds):
 
 def run_reference(args):
     from paper_2406_01939_b300 import synth
-    inst = synth.dual_large(args.seed)
+    inst = synth.dual_large(args.seed, T=args.T)
     per = max(1, int(args.steps))
     import oracle
     from paper_2406_01939_b300.synth import Policy
@@ -201,7 +202,7 @@ def main():
     from paper_2406_01939_b300.session import DeviceInstance, DevicePolicy
     from paper_2406_01939_b300.synth import Policy
 
-    inst = synth.dual_large(args.seed + rank)
+    inst = synth.dual_large(args.seed + rank, T=args.T)
     di = DeviceInstance(inst, device=dev)
     pol = DevicePolicy(Policy("dual"), dev)
     T = inst.T
@@ -243,20 +244,33 @@ def main():
         t_ms = float(tt.item())
     value = world * T * args.steps / (t_ms / 1000.0)
     last = results[-1]
+    # one extra (untimed) call with the per-pass trace
+    tr = np.zeros((4096, 4), np.int64)
+    di.simulate(pol, "picard", num_chunks=args.chunks, seg_window=args.seg_window,
+                want_stock=False, out=act, trace=tr)
+    ntr = min(last["iters"], 4096)
+    ts, tr_end = tr[:ntr, 0], tr[:ntr, 1]
+    prev = np.r_[0, tr_end[:-1]]
+    pass_trace = {"prefix_us": ((ts - prev) / 1e3).round(1).tolist(),
+                  "replay_us": ((tr_end - ts) / 1e3).round(1).tolist(),
+                  "policy_calls": tr[:ntr, 2].tolist(), "units": tr[:ntr, 3].tolist()}
     sim_ms = statistics.median(r["sim_ms"] for r in results)
     prep_ms = statistics.median(r["prep_ms"] for r in results)
     iters = last["iters"]
 
     # sequential GPU simulator (the speedup denominator), same instance
-    seq_act = torch.empty(T, dtype=torch.int8, device=dev)
-    seq_ms = []
-    for i in range(max(1, args.seq_steps) + 1):
-        r = di.simulate(pol, "sequential", flags=pic.PIC_FLAG_TIMING, want_stock=False, out=seq_act)
-        if i:
-            seq_ms.append(r["total_ms"])
-        seq_res = r
-    seq_ms = statistics.median(seq_ms)
-    bit_exact_gpu = bool(torch.equal(seq_act, act)) and seq_res["total_cost"] == last["total_cost"]
+    seq_ms, bit_exact_gpu = None, None
+    if args.seq_steps > 0:
+        seq_act = torch.empty(T, dtype=torch.int8, device=dev)
+        seq_ms = []
+        for i in range(args.seq_steps + 1):
+            r = di.simulate(pol, "sequential", flags=pic.PIC_FLAG_TIMING, want_stock=False,
+                            out=seq_act)
+            if i:
+                seq_ms.append(r["total_ms"])
+            seq_res = r
+        seq_ms = statistics.median(seq_ms)
+        bit_exact_gpu = bool(torch.equal(seq_act, act)) and seq_res["total_cost"] == last["total_cost"]
 
     # end to end through host buffers: H2D of the inputs, simulate, D2H of the actions
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).pin_memory()
@@ -267,7 +281,7 @@ def main():
     h2d = sum(host_np[k].nbytes for k in host_np)
     d2h = host_act.nbytes + 64  # actions + the result record
     e2e_t = []
-    for i in range(args.e2e_steps + 2):
+    for i in range(args.e2e_steps + 2 if args.e2e_steps > 0 else 0):
         flush.fill_(1)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -276,8 +290,8 @@ def main():
         t1 = time.perf_counter()
         if i >= 2:
             e2e_t.append(t1 - t0)
-    e2e_value = world * T / statistics.median(e2e_t)
-    bit_exact_e2e = bool(np.array_equal(host_act, act.cpu().numpy()))
+    e2e_value = world * T / statistics.median(e2e_t) if e2e_t else None
+    bit_exact_e2e = bool(np.array_equal(host_act, act.cpu().numpy())) if e2e_t else None
 
     # roofline of the dominant kernel (the persistent Picard kernel)
     N = inst.N
@@ -291,12 +305,13 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": workload_config(args, inst),
         "iters": iters,
-        "seq_gpu": {"value": T / (seq_ms / 1000.0), "unit": UNIT, "ms": seq_ms},
-        "speedup_vs_seq_gpu": seq_ms / (t_ms / args.steps),
+        "seq_gpu": {"value": T / (seq_ms / 1000.0), "unit": UNIT, "ms": seq_ms} if seq_ms else None,
+        "speedup_vs_seq_gpu": seq_ms / (t_ms / args.steps) if seq_ms else None,
         "bit_exact_vs_seq_gpu": bit_exact_gpu,
         "phases_ms": {"tables": prep_ms, "picard_kernel": sim_ms,
                       "step_device": t_ms / args.steps},
         "policy_calls": last["policy_calls"], "segment_replays": last["seg_replays"],
+        "pass_trace": pass_trace,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": profiled_traffic(),
                      "kernel": "k_picard_int (persistent, all passes)",
@@ -308,7 +323,7 @@ def main():
         "clocks": clk,
         "wall_s_timed_loop": wall,
     }
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and args.cpu_seconds > 0:
         rate, n, el, out = cpu_oracle_rate(inst, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"full {T}-order trajectory x{n} ({el:.1f} s), "

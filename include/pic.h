@@ -67,7 +67,9 @@ enum {
     PIC_FLAG_NO_RESET = 1,   /* recompute every chunk on every pass (no t_reset skipping) */
     PIC_FLAG_REUSE_TABLES = 2, /* keep the order/run tables of the previous call if its
                                  chunking matches (skip the per-call preprocessing) */
-    PIC_FLAG_TIMING = 4        /* time the phases with CUDA events (pic_sim_result *_ms) */
+    PIC_FLAG_TIMING = 4,       /* time the phases with CUDA events (pic_sim_result *_ms) */
+    PIC_FLAG_WARP_KERNEL = 8   /* tuning: replay each work unit with a whole warp instead of
+                                  a group of lanes (integer policies) */
 };
 
 typedef struct pic_instance pic_instance;
@@ -106,6 +108,11 @@ typedef struct {
     int32_t out_mem;          /* PIC_MEM_HOST / PIC_MEM_DEVICE for the output arrays */
     int32_t seg_window;       /* tuning: orders of one product per warp work unit; 0 = 64 */
     void* stream;             /* cudaStream_t or NULL */
+    int64_t* trace;           /* HOST [trace_cap][4] per-pass record, or NULL: ns from the
+                                 simulation kernel's start to the end of the pass's prefix
+                                 phase, ns to the end of its replay phase, policy calls in the
+                                 pass, work units replayed in the pass */
+    int32_t trace_cap;        /* rows available in trace */
 } pic_sim_opts;
 
 typedef struct {
@@ -113,7 +120,8 @@ typedef struct {
     int64_t lost;         /* number of a^phi actions */
     int64_t policy_calls; /* policy evaluations performed, over all passes */
     int32_t iters;        /* passes of Algorithm 1's loop, including the confirming one
-                             (1 for PIC_MODE_SEQUENTIAL) */
+                             (1 for PIC_MODE_SEQUENTIAL); also the rows written to opts.trace
+                             (at most trace_cap) */
     int32_t num_chunks;   /* M used */
     int64_t rescored;     /* MLP decisions re-scored in FP32 after the BF16 pass */
     int64_t seg_replays;  /* warp work units (segments) replayed, over all passes */

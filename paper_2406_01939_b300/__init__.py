@@ -23,7 +23,7 @@ PIC_ERR_NOT_CONVERGED, PIC_ERR_TIMEOUT, PIC_ERR_UNSUPPORTED = 4, 5, 6
 PIC_POLICY_GREEDY, PIC_POLICY_DUAL, PIC_POLICY_MLP, PIC_POLICY_GUMBEL = 0, 1, 2, 3
 PIC_MODE_PICARD, PIC_MODE_SEQUENTIAL = 0, 1
 PIC_MEM_HOST, PIC_MEM_DEVICE = 0, 1
-PIC_FLAG_NO_RESET, PIC_FLAG_REUSE_TABLES, PIC_FLAG_TIMING = 1, 2, 4
+PIC_FLAG_NO_RESET, PIC_FLAG_REUSE_TABLES, PIC_FLAG_TIMING, PIC_FLAG_WARP_KERNEL = 1, 2, 4, 8
 
 POLICY_KINDS = {"greedy": PIC_POLICY_GREEDY, "dual": PIC_POLICY_DUAL, "mlp": PIC_POLICY_MLP,
                 "gumbel": PIC_POLICY_GUMBEL}
@@ -52,7 +52,8 @@ class pic_policy(C.Structure):
 class pic_sim_opts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("num_chunks", C.c_int32), ("max_iters", C.c_int32),
                 ("flags", C.c_int32), ("alpha_init", C.c_void_p), ("timeout_ns", C.c_uint64),
-                ("out_mem", C.c_int32), ("seg_window", C.c_int32), ("stream", C.c_void_p)]
+                ("out_mem", C.c_int32), ("seg_window", C.c_int32), ("stream", C.c_void_p),
+                ("trace", C.c_void_p), ("trace_cap", C.c_int32)]
 
 
 class pic_sim_result(C.Structure):
@@ -146,10 +147,12 @@ def make_policy(kind="greedy", W1=None, b1=None, W2=None, b2=None, E=None, hidde
 
 
 def make_opts(mode="picard", num_chunks=0, max_iters=0, flags=0, alpha_init=None, timeout_ns=0,
-              out_mem=PIC_MEM_DEVICE, seg_window=0, stream=None) -> pic_sim_opts:
+              out_mem=PIC_MEM_DEVICE, seg_window=0, stream=None, trace=None) -> pic_sim_opts:
+    """trace: optional host int64 numpy array [cap, 4] receiving the per-pass record."""
     m = MODES[mode] if isinstance(mode, str) else int(mode)
     return pic_sim_opts(m, int(num_chunks), int(max_iters), int(flags), _ptr(alpha_init),
-                        int(timeout_ns), int(out_mem), int(seg_window), _stream_handle(stream))
+                        int(timeout_ns), int(out_mem), int(seg_window), _stream_handle(stream),
+                        _ptr(trace), 0 if trace is None else int(trace.shape[0]))
 
 
 def pic_simulate(handle: int, policy: pic_policy, opts: pic_sim_opts, actions_out,

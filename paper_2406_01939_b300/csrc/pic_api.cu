@@ -52,6 +52,7 @@ __global__ void k_validate(int T, int N, int K, int R, const int32_t* __restrict
     for (long long i = gid; i < (long long)R * N; i += stride) {
         const int c = cost[i];
         if (c <= -lim || c >= lim) b |= 8;
+        if (c < -32768 || c > 32767) b |= 128;  // not representable in int16
     }
     if (lam)
         for (long long i = gid; i < (long long)K * N; i += stride) {
@@ -141,9 +142,10 @@ cudaError_t dmalloc(T** p, size_t n) {
 void free_instance(Instance& I) {
     void* ptrs[] = {I.prod, I.reg, I.x0, I.cost, I.lam, I.perm, I.prod_s, I.reg_s, I.pcount,
                     I.pstart, I.run_start, I.run_of, I.seg_run, I.seg_of_run, I.seg_prod, I.seg_cf,
-                    I.seg_ce, I.alpha_s, I.agg, I.carry, I.sbtot, I.fc, I.seg_cost, I.seg_lost,
+                    I.seg_ce, I.seg_meta, I.seg_lpt, I.len_hist, I.alpha_s, I.agg, I.carry, I.sbagg, I.sbincl,
+                    I.fc,
                     I.xfin, I.xwork, I.act_t, I.tmp_a, I.tmp_b, I.tmp_c, I.scan_blk, I.hist,
-                    I.ctrl};
+                    I.ctrl, I.trace};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < 4; ++i)
@@ -175,6 +177,7 @@ pic_status copy_inputs(Instance& I, const pic_instance_desc* d, cudaStream_t st)
     if (hb & 4) return fail(PIC_ERR_INVALID_ARG, "x0 has a negative entry");
     if (hb & (8 | 16 | 32))
         return fail(PIC_ERR_INVALID_ARG, "|cost|, |lam| or |cost - lam| not below 2^23");
+    I.cost16 = (hb & 128) ? 0 : 1;
     return PIC_OK;
 }
 
@@ -223,10 +226,11 @@ pic_status pic_create_instance(const pic_instance_desc* d, pic_instance** out) {
     if (!e) e = dmalloc(&I.seg_prod, S);
     if (!e) e = dmalloc(&I.seg_cf, S);
     if (!e) e = dmalloc(&I.seg_ce, S);
+    if (!e) e = dmalloc(&I.seg_meta, S);
+    if (!e) e = dmalloc(&I.seg_lpt, S);
+    if (!e) e = dmalloc(&I.len_hist, kLenBuckets);
     if (!e) e = dmalloc(&I.alpha_s, T);
     if (!e) e = dmalloc(&I.fc, 2 * K);
-    if (!e) e = dmalloc(&I.seg_cost, S);
-    if (!e) e = dmalloc(&I.seg_lost, S);
     if (!e) e = dmalloc(&I.xfin, K * N);
     if (!e) e = dmalloc(&I.xwork, K * N);
     if (!e) e = dmalloc(&I.act_t, T);
@@ -235,6 +239,7 @@ pic_status pic_create_instance(const pic_instance_desc* d, pic_instance** out) {
     if (!e) e = dmalloc(&I.scan_blk, nscan / 2048 + 2);
     if (!e) e = dmalloc(&I.hist, (size_t)I.hist_cap);
     if (!e) e = cudaMalloc((void**)&I.ctrl, sizeof(Ctrl));
+    if (!e) e = cudaMalloc((void**)&I.trace, sizeof(long long) * 4 * kTraceCap);
     for (int i = 0; i < 4 && !e; ++i) e = cudaEventCreate(&I.ev[i]);
     // per-segment histograms: allocated lazily at the first simulate (size depends on W)
     if (e) {
@@ -279,7 +284,7 @@ void pic_destroy_instance(pic_instance* h) {
 pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_opts* opts,
                         int8_t* actions_out, int32_t* final_stock, pic_sim_result* res) {
     g_err[0] = 0;
-    if (!h || !pol || !opts || !actions_out)
+    if (!h || !pol || !opts || (!actions_out && h->I.T > 0))
         return fail(PIC_ERR_INVALID_ARG, "instance, policy, opts and actions_out are required");
     Instance& I = h->I;
     if (opts->mode != PIC_MODE_PICARD && opts->mode != PIC_MODE_SEQUENTIAL)
@@ -320,12 +325,16 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
         // tables + per-segment state (capacity for this window)
         const int64_t smax = (int64_t)2 * K + (int64_t)(T + W - 1) / W + 2;
         if (!I.agg || smax > I.smax_agg) {
-            if (I.agg) { cudaFree(I.agg); cudaFree(I.carry); cudaFree(I.sbtot); }
-            I.agg = I.carry = I.sbtot = nullptr;
+            if (I.agg) {
+                cudaFree(I.agg); cudaFree(I.carry); cudaFree(I.sbagg); cudaFree(I.sbincl);
+            }
+            I.agg = I.carry = nullptr;
+            I.sbagg = I.sbincl = nullptr;
             I.smax_agg = 0;
             CU(dmalloc(&I.agg, (size_t)smax * I.NP));
             CU(dmalloc(&I.carry, (size_t)smax * I.NP));
-            CU(dmalloc(&I.sbtot, (size_t)smax * I.NP));
+            CU(dmalloc(&I.sbagg, (size_t)smax * I.NP));
+            CU(dmalloc(&I.sbincl, (size_t)smax * I.NP));
             I.smax_agg = smax;
         }
         const bool reuse = (opts->flags & PIC_FLAG_REUSE_TABLES) && I.tables_m == M && I.tables_w == W;
@@ -336,7 +345,9 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
         }
         CU(cudaMemsetAsync(I.agg, 0, sizeof(int32_t) * (size_t)smax * I.NP, st));
         CU(cudaMemsetAsync(I.carry, 0, sizeof(int32_t) * (size_t)smax * I.NP, st));
-        CU(cudaMemsetAsync(I.sbtot, 0, sizeof(int32_t) * (size_t)smax * I.NP, st));
+        // look-back words of earlier calls carry pass tags that this call reuses
+        CU(cudaMemsetAsync(I.sbagg, 0, sizeof(unsigned long long) * (size_t)smax * I.NP, st));
+        CU(cudaMemsetAsync(I.sbincl, 0, sizeof(unsigned long long) * (size_t)smax * I.NP, st));
         CU(cudaMemsetAsync(I.fc, 0xFF, sizeof(int32_t) * K, st));  // pass 0: everything "changed"
         CU(cudaMemcpyAsync(I.xfin, I.x0, sizeof(int32_t) * K * N, cudaMemcpyDeviceToDevice, st));
         if (T) {
@@ -352,8 +363,10 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
                 CU(cudaMemsetAsync(I.alpha_s, 0xFF, T, st));  // a^phi everywhere (Alg. 1 line 1)
             }
             if (timing) CU(cudaEventRecord(I.ev[1], st));
+            const bool trace = opts->trace && opts->trace_cap > 0;
+            if (trace) CU(cudaMemsetAsync(I.trace, 0, sizeof(long long) * 4 * kTraceCap, st));
             CU(picard_int(&I, pol->kind, iters_cap, opts->flags, opts->alpha_init,
-                          opts->timeout_ns ? opts->timeout_ns : 10000000000ull, st));
+                          opts->timeout_ns ? opts->timeout_ns : 10000000000ull, trace, st));
             if (timing) CU(cudaEventRecord(I.ev[2], st));
             CU(finish_outputs(&I, st));
             CU(cudaMemcpyAsync(actions_out, I.act_t, T, okind, st));
@@ -374,6 +387,12 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
     if (hc.pad0 & 64) return fail(PIC_ERR_INVALID_ARG, "alpha_init holds a value outside [-1, N)");
     if (hc.err) return fail((pic_status)hc.err, "device wait exceeded timeout (%llu ns)",
                             (unsigned long long)opts->timeout_ns);
+    if (T && opts->mode == PIC_MODE_PICARD && opts->trace && opts->trace_cap > 0) {
+        int rows = hc.iters < opts->trace_cap ? hc.iters : opts->trace_cap;
+        if (rows > kTraceCap) rows = kTraceCap;
+        if (rows > 0)
+            CU(cudaMemcpy(opts->trace, I.trace, sizeof(long long) * 4 * rows, cudaMemcpyDeviceToHost));
+    }
     if (res) {
         res->total_cost = hc.total_cost;
         res->lost = hc.lost;

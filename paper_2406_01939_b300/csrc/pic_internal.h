@@ -13,6 +13,10 @@ constexpr int kHidden = 256;       // MLP hidden width
 constexpr int kSegWindow = 64;     // default segment window (orders of one product)
 constexpr int kSuperBlock = 32;    // segments per carry super-block
 constexpr int kThreads = 256;      // threads per CTA of the persistent kernels
+constexpr size_t kSmemCostMax = 200 * 1024;  // largest int16 cost table staged in shared memory
+constexpr int kTraceCap = 4096;    // passes recorded by the device-side trace
+constexpr int kLenBuckets = 1024;  // segment-length buckets of the longest-first order
+constexpr size_t kGrpSmemMax = 150 * 1024;  // cost table budget of the group-per-segment kernel
 
 // Device-side control block of one simulate call (zeroed before each launch).
 struct Ctrl {
@@ -34,11 +38,18 @@ struct Ctrl {
     int pad1;
 };
 
+// Per-segment metadata packed for one 32-byte load: product, run range, sorted
+// position range, first order of the last run, chain (product) segment range.
+struct __align__(32) SegMeta {
+    int k, r0, r1, j0, jend, last_start, cf, ce;
+};
+
 // All device buffers of one instance.  Sizes: T orders, K products, N warehouses,
 // R regions; NP = N rounded up to a multiple of 32.
 struct Instance {
     int T, N, K, R, NP;
     int has_lam;
+    int cost16;         // every cost fits int16 (the cost table can be staged in shared memory)
     cudaStream_t create_stream;
     // inputs
     int32_t *prod, *reg, *x0, *cost, *lam;
@@ -55,6 +66,9 @@ struct Instance {
     int32_t *seg_prod;  // [SMAX]
     int32_t *seg_cf;    // [SMAX] first segment of the segment's product (chain)
     int32_t *seg_ce;    // [SMAX] one past the last segment of the chain
+    SegMeta *seg_meta;  // [SMAX] packed copy of the above for the simulation kernels
+    int32_t *seg_lpt;   // [SMAX] segments in decreasing order of length (replay assignment)
+    int32_t *len_hist;  // [kLenBuckets] counting-sort buckets
     int64_t smax;       // capacity of the segment tables (>= any segment count)
     int64_t smax_agg;   // capacity (segments) of agg/carry/sbtot
     int tables_m, tables_w;  // chunking the current tables were built for (0 = none)
@@ -62,10 +76,9 @@ struct Instance {
     int8_t *alpha_s;    // [T]  action cache in sorted order
     int32_t *agg;       // [SMAX][NP] histogram of cached actions per segment
     int32_t *carry;     // [SMAX][NP] in-super-block exclusive prefix of agg
-    int32_t *sbtot;     // [SMAX][NP] super-block totals (at the block's first segment)
+    unsigned long long *sbagg;   // [SMAX][NP] super-block totals, (pass << 32) | value
+    unsigned long long *sbincl;  // [SMAX][NP] inclusive chain prefix, (pass << 32) | value
     int32_t *fc;        // [2][K] first changed sorted position per product and pass parity
-    long long *seg_cost;// [SMAX]
-    int32_t *seg_lost;  // [SMAX]
     int32_t *xfin;      // [K][N] final stock
     int32_t *xwork;     // [K][N] working stock of the sequential simulator
     int8_t *act_t;      // [T]  actions in time order (device staging)
@@ -75,6 +88,7 @@ struct Instance {
     int32_t *hist;                    // radix histograms
     int64_t hist_cap;
     Ctrl *ctrl;
+    long long *trace;                 // [kTraceCap][4] device-side per-pass record
     int num_sms;
     int coop_blocks;                  // persistent grid size (integer kernel)
     int launches;                     // kernels launched by the current call
@@ -88,13 +102,10 @@ cudaError_t build_tables(Instance* I, int M, int W, cudaStream_t st);
 cudaError_t finish_outputs(Instance* I, cudaStream_t st);
 
 // Integer policies (pic_int.cu).
-struct IntPolicyArgs {
-    int kind;  // PIC_POLICY_GREEDY / DUAL
-};
 cudaError_t picard_int(Instance* I, int kind, int max_iters, int flags, const int8_t* alpha_init,
-                       unsigned long long timeout_ns, cudaStream_t st);
+                       unsigned long long timeout_ns, bool trace, cudaStream_t st);
 cudaError_t sequential_int(Instance* I, int kind, cudaStream_t st);
-int picard_int_grid(Instance* I);
+bool smem_cost_ok(const Instance* I);
 
 // Simple device-wide exclusive scan of int32 (n elements); total written to *total_dev.
 cudaError_t scan_exclusive(const int32_t* in, int32_t* out, int n, int32_t* total_dev,

@@ -164,12 +164,17 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
 }
 
 // --------------------------------------------------------------------------- tables
-__global__ void k_hist_prod(const int32_t* __restrict__ prod, int n, int32_t* cnt) {
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    bool valid = idx < n;
-    int k = valid ? prod[idx] : -1 - (int)(threadIdx.x & 31);
-    unsigned peers = __match_any_sync(kFull, k);
-    if (valid && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) atomicAdd(&cnt[k], __popc(peers));
+// First sorted position of every product (K+1 entries, pstart[K] = T): a
+// lower-bound search in the sorted product column.
+__global__ void k_pstart(const int32_t* __restrict__ prod_s, int T, int K, int32_t* __restrict__ pstart) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > K) return;
+    int lo = 0, hi = T;
+    while (lo < hi) {
+        const int mid = (int)(((unsigned)lo + (unsigned)hi) >> 1);
+        if (prod_s[mid] < k) lo = mid + 1; else hi = mid;
+    }
+    pstart[k] = lo;
 }
 
 // Region gather and run-start flags: a run starts where the product or the
@@ -236,14 +241,55 @@ __global__ void k_segs(const int32_t* __restrict__ flag, const int32_t* __restri
     }
 }
 
-__global__ void k_chains(const int32_t* __restrict__ seg_prod, const int32_t* __restrict__ pstart,
+__global__ void k_chains(const int32_t* __restrict__ seg_prod, const int32_t* __restrict__ seg_run,
+                         const int32_t* __restrict__ run_start, const int32_t* __restrict__ pstart,
                          const int32_t* __restrict__ run_of, const int32_t* __restrict__ seg_of_run,
-                         int T, const Ctrl* ctrl, int32_t* __restrict__ cf, int32_t* __restrict__ ce) {
+                         int T, const Ctrl* ctrl, int32_t* __restrict__ cf, int32_t* __restrict__ ce,
+                         SegMeta* __restrict__ meta) {
     long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= ctrl->nseg) return;
-    int k = seg_prod[s];
-    cf[s] = seg_of_run[run_of[pstart[k]]];
-    ce[s] = seg_of_run[run_of[pstart[k + 1] - 1]] + 1;
+    const int k = seg_prod[s];
+    const int c0 = seg_of_run[run_of[pstart[k]]];
+    const int c1 = seg_of_run[run_of[pstart[k + 1] - 1]] + 1;
+    cf[s] = c0;
+    ce[s] = c1;
+    SegMeta m;
+    m.k = k;
+    m.r0 = seg_run[s];
+    m.r1 = seg_run[s + 1];
+    m.j0 = run_start[m.r0];
+    m.jend = run_start[m.r1];
+    m.last_start = run_start[m.r1 - 1];
+    m.cf = c0;
+    m.ce = c1;
+    meta[s] = m;
+}
+
+// Longest-first order of the segments (counting sort on min(length, 1023),
+// descending; order inside a bucket is arbitrary).  Warps take segments from
+// this order so that the long ones start first and the work evens out.
+__global__ void k_len_hist(const SegMeta* __restrict__ meta, const Ctrl* ctrl, int32_t* hist) {
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = s < ctrl->nseg;
+    int b = -1 - (int)(threadIdx.x & 31);
+    if (valid) b = kLenBuckets - 1 - min(meta[s].jend - meta[s].j0, kLenBuckets - 1);
+    const unsigned peers = __match_any_sync(kFull, b);
+    if (valid && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) atomicAdd(&hist[b], __popc(peers));
+}
+
+__global__ void k_len_scatter(const SegMeta* __restrict__ meta, const Ctrl* ctrl, int32_t* offs,
+                              int32_t* __restrict__ lpt) {
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = s < ctrl->nseg;
+    const int lane = threadIdx.x & 31;
+    int b = -1 - lane;
+    if (valid) b = kLenBuckets - 1 - min(meta[s].jend - meta[s].j0, kLenBuckets - 1);
+    const unsigned peers = __match_any_sync(kFull, b);
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (valid && leader == lane) base = atomicAdd(&offs[b], __popc(peers));
+    base = __shfl_sync(kFull, base, leader);
+    if (valid) lpt[base + __popc(peers & ((1u << lane) - 1u))] = (int)s;
 }
 
 __global__ void k_scatter_actions(const int8_t* __restrict__ alpha_s, const int32_t* __restrict__ perm,
@@ -252,14 +298,16 @@ __global__ void k_scatter_actions(const int8_t* __restrict__ alpha_s, const int3
     if (j < T) act_t[perm[j]] = alpha_s[j];
 }
 
-__global__ void k_reduce_costs(const long long* __restrict__ seg_cost,
-                               const int32_t* __restrict__ seg_lost, Ctrl* ctrl) {
-    const int nseg = ctrl->nseg;
+// Total cost sum_t cost[r_t][a_t] over fulfilled orders and the a^phi count,
+// from the converged cache (in sorted order).
+__global__ void k_reduce_costs(const int8_t* __restrict__ alpha_s, const int32_t* __restrict__ reg_s,
+                               const int32_t* __restrict__ cost, int T, int N, Ctrl* ctrl) {
     long long c = 0, l = 0;
-    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < nseg;
-         s += (long long)gridDim.x * blockDim.x) {
-        c += seg_cost[s];
-        l += seg_lost[s];
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < T;
+         j += (long long)gridDim.x * blockDim.x) {
+        const int a = alpha_s[j];
+        if (a >= 0) c += __ldg(cost + (size_t)reg_s[j] * N + a);
+        else l += 1;
     }
     c = warp_sum_i64(c);
     l = warp_sum_i64(l);
@@ -291,9 +339,9 @@ cudaError_t build_tables(Instance* I, int M, int W, cudaStream_t st) {
         return e;
     }
     // kernel launches made below: per radix pass 2 + a 3-kernel scan; then
-    // product histogram + scan, run flags + scan + runs, segment flags + scan +
+    // product offsets, run flags + scan + runs, segment flags + scan +
     // segments + chains
-    I->launches += (K <= 256 ? 1 : 2) * 5 + 4 + 5 + 6;
+    I->launches += (K <= 256 ? 1 : 2) * 5 + 1 + 5 + 6 + 5;
     // 1. stable sort of (product, time) by product: LSD radix, 8-bit digits
     const int nblk = nblocks(T, kRadixTile);
     const int passes = K <= 256 ? 1 : 2;
@@ -311,10 +359,8 @@ cudaError_t build_tables(Instance* I, int M, int W, cudaStream_t st) {
         kout = I->prod_s;
         vout = I->perm;
     }
-    // 2. per-product counts and first positions
-    cudaMemsetAsync(I->pcount, 0, sizeof(int32_t) * (K + 1), st);
-    k_hist_prod<<<nblocks(T, 256), 256, 0, st>>>(I->prod, T, I->pcount);
-    if ((e = scan_exclusive(I->pcount, I->pstart, K + 1, nullptr, I->scan_blk, st))) return e;
+    // 2. first sorted position of every product
+    k_pstart<<<nblocks(K + 1, 256), 256, 0, st>>>(I->prod_s, T, K, I->pstart);
     // 3. runs for M chunks of L orders
     const long long L = ((long long)T + M - 1) / M;
     k_run_flags<<<nblocks(T, 256), 256, 0, st>>>(I->perm, I->prod_s, I->reg, I->reg_s, T, (int)L,
@@ -327,8 +373,15 @@ cudaError_t build_tables(Instance* I, int M, int W, cudaStream_t st) {
     if ((e = scan_exclusive(I->tmp_a, I->tmp_b, T, nullptr, I->scan_blk, st))) return e;
     k_segs<<<nblocks(T, 256), 256, 0, st>>>(I->tmp_a, I->tmp_b, T, I->run_start, I->prod_s,
                                              I->seg_of_run, I->seg_run, I->seg_prod, I->ctrl);
-    k_chains<<<nblocks(I->smax, 256), 256, 0, st>>>(I->seg_prod, I->pstart, I->run_of,
-                                                     I->seg_of_run, T, I->ctrl, I->seg_cf, I->seg_ce);
+    k_chains<<<nblocks(I->smax, 256), 256, 0, st>>>(I->seg_prod, I->seg_run, I->run_start,
+                                                     I->pstart, I->run_of, I->seg_of_run, T, I->ctrl,
+                                                     I->seg_cf, I->seg_ce, I->seg_meta);
+    // 5. longest-first order of the segments
+    cudaMemsetAsync(I->len_hist, 0, sizeof(int32_t) * kLenBuckets, st);
+    const int sb = nblocks(I->smax, 256);
+    k_len_hist<<<sb, 256, 0, st>>>(I->seg_meta, I->ctrl, I->len_hist);
+    if ((e = scan_exclusive(I->len_hist, I->len_hist, kLenBuckets, nullptr, I->scan_blk, st))) return e;
+    k_len_scatter<<<sb, 256, 0, st>>>(I->seg_meta, I->ctrl, I->len_hist, I->seg_lpt);
     return cudaGetLastError();
 }
 
@@ -336,7 +389,7 @@ cudaError_t finish_outputs(Instance* I, cudaStream_t st) {
     if (I->T == 0) return cudaSuccess;
     I->launches += 2;
     k_scatter_actions<<<nblocks(I->T, 256), 256, 0, st>>>(I->alpha_s, I->perm, I->T, I->act_t);
-    k_reduce_costs<<<2 * I->num_sms, 256, 0, st>>>(I->seg_cost, I->seg_lost, I->ctrl);
+    k_reduce_costs<<<4 * I->num_sms, 256, 0, st>>>(I->alpha_s, I->reg_s, I->cost, I->T, I->N, I->ctrl);
     return cudaGetLastError();
 }
 

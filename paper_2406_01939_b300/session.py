@@ -67,7 +67,8 @@ class DeviceInstance:
         pic_instance_load(self.handle, self._desc(host_arrays, self.stream, mem=PIC_MEM_HOST))
 
     def simulate(self, policy, mode="picard", num_chunks=0, max_iters=0, flags=0, alpha_init=None,
-                 timeout_ns=0, seg_window=0, want_stock=True, raise_on_error=True, out=None):
+                 timeout_ns=0, seg_window=0, want_stock=True, raise_on_error=True, out=None,
+                 trace=None):
         i = self.inst
         dp = policy if isinstance(policy, DevicePolicy) else DevicePolicy(policy, self.device)
         act = out if out is not None else torch.empty(i.T, dtype=torch.int8, device=self.device)
@@ -77,7 +78,7 @@ class DeviceInstance:
             ai = torch.as_tensor(np.ascontiguousarray(alpha_init, dtype=np.int8)).to(self.device) \
                 if not torch.is_tensor(alpha_init) else alpha_init
         opts = make_opts(mode, num_chunks, max_iters, flags, ai, timeout_ns, PIC_MEM_DEVICE,
-                         seg_window, self.stream)
+                         seg_window, self.stream, trace)
         st, res = pic_simulate(self.handle, dp.struct, opts, act, stock, raise_on_error)
         return {"status": st, "actions": act, "final_stock": stock, "total_cost": res.total_cost,
                 "lost": res.lost, "iters": res.iters, "policy_calls": res.policy_calls,

@@ -78,7 +78,21 @@ def test_random_shapes_and_ragged_lanes(N):
         for kind in ("greedy", "dual"):
             for M in sorted({1, 7, max(1, T)}):
                 for W in (1, 3, 64):
-                    check_against_oracle(inst, kind, M, dev=dev, seg_window=W)
+                    for flags in (0, pic.PIC_FLAG_WARP_KERNEL):
+                        check_against_oracle(inst, kind, M, dev=dev, seg_window=W, flags=flags)
+
+
+def test_wide_costs_use_global_table():
+    """Costs beyond int16 (no shared-memory table): same bit-exact results."""
+    rng = np.random.default_rng(11)
+    for N in (8, 40, 64):
+        inst = rand_inst(rng, 3000, N, 20, 9, xmax=8, cmax=9)
+        inst.cost = (inst.cost.astype(np.int64) * 100_003 - 300_000).astype(np.int32)
+        inst.lam = (inst.lam.astype(np.int64) * 99_991).astype(np.int32)
+        dev = DeviceInstance(inst)
+        for kind in ("greedy", "dual"):
+            for M in (1, 30, 3000):
+                check_against_oracle(inst, kind, M, dev=dev)
 
 
 def test_sequential_mode_bit_exact():
@@ -86,7 +100,7 @@ def test_sequential_mode_bit_exact():
     for inst in (synth.greedy_small(3), rand_inst(rng, 3000, 64, 50, 20), rand_inst(rng, 777, 100, 9, 3),
                  rand_inst(rng, 1, 1, 1, 1)):
         d = DeviceInstance(inst)
-        for kind in ("greedy", "dual"):
+        for kind in ("greedy", "dual") if inst.lam is not None else ("greedy",):
             seq = oracle.seq_sim(inst, Policy(kind))
             got = d.simulate(Policy(kind), "sequential")
             np.testing.assert_array_equal(got["actions"].cpu().numpy(), seq["actions"])
@@ -169,6 +183,24 @@ def test_host_buffers_end_to_end():
 @pytest.mark.parametrize("M", [256, 4096, 65536])
 def test_dual_large_full_size(M):
     """T=2^20, N=64, K=10,000, R=1,000 bid-price workload (the benchmark's
-    shape): bit-exact fixed point and the oracle's pass count."""
+    shape): bit-exact fixed point and the oracle's pass count, both layouts."""
     inst = synth.dual_large(0)
-    check_against_oracle(inst, "dual", M)
+    dev = DeviceInstance(inst)
+    check_against_oracle(inst, "dual", M, dev=dev)
+    check_against_oracle(inst, "dual", M, dev=dev, flags=pic.PIC_FLAG_WARP_KERNEL)
+
+
+def test_pass_trace_records_every_pass():
+    """The per-pass trace has one row per pass: increasing timestamps, and its
+    policy-call column sums to the call's total."""
+    inst = synth.greedy_small(5)
+    d = DeviceInstance(inst)
+    tr = np.zeros((100, 4), np.int64)
+    got = d.simulate(Policy("greedy"), num_chunks=64, trace=tr)
+    n = got["iters"]
+    assert (tr[n:] == 0).all()
+    stamps = tr[:n, :2].reshape(-1)
+    assert (np.diff(stamps) >= 0).all() and stamps[0] > 0
+    assert tr[:n, 2].sum() == got["policy_calls"]
+    assert tr[:n, 3].sum() == got["seg_replays"]
+    assert tr[0, 2] == inst.T  # every order is evaluated in the first pass

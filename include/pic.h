@@ -68,8 +68,9 @@ enum {
     PIC_FLAG_REUSE_TABLES = 2, /* keep the order/run tables of the previous call if its
                                  chunking matches (skip the per-call preprocessing) */
     PIC_FLAG_TIMING = 4,       /* time the phases with CUDA events (pic_sim_result *_ms) */
-    PIC_FLAG_WARP_KERNEL = 8   /* tuning: replay each work unit with a whole warp instead of
-                                  a group of lanes (integer policies) */
+    PIC_FLAG_GROUP_KERNEL = 8  /* tuning: replay each work unit with a group of 8 warehouses
+                                  per lane instead of a whole warp (integer policies, costs
+                                  that fit int16) */
 };
 
 typedef struct pic_instance pic_instance;

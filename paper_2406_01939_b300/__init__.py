@@ -23,7 +23,7 @@ PIC_ERR_NOT_CONVERGED, PIC_ERR_TIMEOUT, PIC_ERR_UNSUPPORTED = 4, 5, 6
 PIC_POLICY_GREEDY, PIC_POLICY_DUAL, PIC_POLICY_MLP, PIC_POLICY_GUMBEL = 0, 1, 2, 3
 PIC_MODE_PICARD, PIC_MODE_SEQUENTIAL = 0, 1
 PIC_MEM_HOST, PIC_MEM_DEVICE = 0, 1
-PIC_FLAG_NO_RESET, PIC_FLAG_REUSE_TABLES, PIC_FLAG_TIMING, PIC_FLAG_WARP_KERNEL = 1, 2, 4, 8
+PIC_FLAG_NO_RESET, PIC_FLAG_REUSE_TABLES, PIC_FLAG_TIMING, PIC_FLAG_GROUP_KERNEL = 1, 2, 4, 8
 
 POLICY_KINDS = {"greedy": PIC_POLICY_GREEDY, "dual": PIC_POLICY_DUAL, "mlp": PIC_POLICY_MLP,
                 "gumbel": PIC_POLICY_GUMBEL}
@@ -165,3 +165,4 @@ def pic_simulate(handle: int, policy: pic_policy, opts: pic_sim_opts, actions_ou
     if raise_on_error and st != PIC_OK:
         raise PicError(st, pic_last_error())
     return st, res
+

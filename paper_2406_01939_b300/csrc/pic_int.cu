@@ -473,7 +473,7 @@ cudaError_t picard_int(Instance* I, int kind, int max_iters, int flags, const in
     a.first_dirty = alpha_init != nullptr; a.timeout_ns = timeout_ns;
     a.trace = trace ? I->trace : nullptr;
     const bool dual = kind == PIC_POLICY_DUAL;
-    if (!(flags & PIC_FLAG_WARP_KERNEL) && grp_ok(I)) return picard_grp(I, a, dual, st);
+    if ((flags & PIC_FLAG_GROUP_KERNEL) && grp_ok(I)) return picard_grp(I, a, dual, st);
     const int npl = (I->N + 31) / 32;
     if (npl == 1) return dual ? picard_dispatch<1, true>(I, a, st) : picard_dispatch<1, false>(I, a, st);
     if (npl == 2) return dual ? picard_dispatch<2, true>(I, a, st) : picard_dispatch<2, false>(I, a, st);

@@ -78,7 +78,7 @@ def test_random_shapes_and_ragged_lanes(N):
         for kind in ("greedy", "dual"):
             for M in sorted({1, 7, max(1, T)}):
                 for W in (1, 3, 64):
-                    for flags in (0, pic.PIC_FLAG_WARP_KERNEL):
+                    for flags in (0, pic.PIC_FLAG_GROUP_KERNEL):
                         check_against_oracle(inst, kind, M, dev=dev, seg_window=W, flags=flags)
 
 
@@ -187,7 +187,7 @@ def test_dual_large_full_size(M):
     inst = synth.dual_large(0)
     dev = DeviceInstance(inst)
     check_against_oracle(inst, "dual", M, dev=dev)
-    check_against_oracle(inst, "dual", M, dev=dev, flags=pic.PIC_FLAG_WARP_KERNEL)
+    check_against_oracle(inst, "dual", M, dev=dev, flags=pic.PIC_FLAG_GROUP_KERNEL)
 
 
 def test_pass_trace_records_every_pass():

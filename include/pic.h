@@ -159,6 +159,29 @@ void pic_destroy_instance(pic_instance* inst);
 pic_status pic_simulate(pic_instance* inst, const pic_policy* pol, const pic_sim_opts* opts,
                         int8_t* actions_out, int32_t* final_stock, pic_sim_result* res);
 
+/* Sequential simulation that allocates no device memory.  The paper has no
+ * counterpart: this is a deployment variant of PIC_MODE_SEQUENTIAL for callers
+ * that may not allocate device memory (a process whose own allocator owns all
+ * device memory after start-up, or a latency-critical path that cannot absorb
+ * cudaMalloc's implicit device synchronisation).  Instead of an instance it
+ * reads the caller's DEVICE arrays in desc (desc->mem must be PIC_MEM_DEVICE)
+ * and keeps its working stock and control block in a fixed 4 MiB array owned by
+ * the library (a static device variable, held on every GPU that loads the
+ * library until the process exits).
+ *   kind         PIC_POLICY_GREEDY or PIC_POLICY_DUAL;
+ *   actions_out  DEVICE [T] int8 (required when T > 0);
+ *   final_stock  DEVICE [K][N] int32, or NULL;
+ *   total_cost, lost  HOST, or NULL.
+ * Limits: K*N <= 1,048,512 (else PIC_ERR_INVALID_ARG naming the limit);
+ * |cost|, |lam| < 2^22.  The first call on each device resolves the array's
+ * device address (with that device current) and should come before any stream
+ * capture on it.  All calls share the array: calls whose work overlaps on the
+ * same GPU race.  Synchronous on desc->stream.  Errors: INVALID_ARG,
+ * UNSUPPORTED, CUDA. */
+pic_status pic_simulate_sequential_static(const pic_instance_desc* desc, int32_t kind,
+                                          int8_t* actions_out, int32_t* final_stock,
+                                          int64_t* total_cost, int64_t* lost);
+
 /* Message for the last non-OK status on this thread ("" if none). */
 const char* pic_last_error(void);
 

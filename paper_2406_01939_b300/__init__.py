@@ -7,7 +7,8 @@ kernels.  There is no CPU fallback: if the library or a CUDA device is missing,
 calls raise.
 
 Names follow the C ABI: ``pic_create_instance``, ``pic_instance_load``,
-``pic_destroy_instance``, ``pic_simulate``, ``pic_last_error``.
+``pic_destroy_instance``, ``pic_simulate``, ``pic_simulate_sequential_static``,
+``pic_last_error``.
 """
 from __future__ import annotations
 
@@ -85,6 +86,10 @@ def lib():
             L.pic_simulate.argtypes = [P, C.POINTER(pic_policy), C.POINTER(pic_sim_opts), P, P,
                                        C.POINTER(pic_sim_result)]
             L.pic_simulate.restype = C.c_int
+            L.pic_simulate_sequential_static.argtypes = [C.POINTER(pic_instance_desc), C.c_int32, P,
+                                                         P, C.POINTER(C.c_int64),
+                                                         C.POINTER(C.c_int64)]
+            L.pic_simulate_sequential_static.restype = C.c_int
             L.pic_last_error.argtypes = []
             L.pic_last_error.restype = C.c_char_p
             _lib = L
@@ -166,3 +171,15 @@ def pic_simulate(handle: int, policy: pic_policy, opts: pic_sim_opts, actions_ou
         raise PicError(st, pic_last_error())
     return st, res
 
+
+def pic_simulate_sequential_static(desc: pic_instance_desc, kind, actions_out, final_stock=None,
+                                   raise_on_error=True):
+    """Sequential simulation with library-owned scratch (no device allocation).
+    desc must describe DEVICE arrays.  Returns (status, total_cost, lost)."""
+    k = POLICY_KINDS[kind] if isinstance(kind, str) else int(kind)
+    tc, lost = C.c_int64(0), C.c_int64(0)
+    st = lib().pic_simulate_sequential_static(C.byref(desc), k, _ptr(actions_out),
+                                              _ptr(final_stock), C.byref(tc), C.byref(lost))
+    if raise_on_error and st != PIC_OK:
+        raise PicError(st, pic_last_error())
+    return st, tc.value, lost.value

@@ -183,6 +183,16 @@ pic_status copy_inputs(Instance& I, const pic_instance_desc* d, cudaStream_t st)
 
 }  // namespace
 
+namespace pic {
+// Record the message pic_last_error() returns on this thread (for entry points
+// defined in other translation units).
+pic_status record_error(pic_status s, const char* msg) {
+    snprintf(g_err, sizeof(g_err), "%s", msg);
+    return s;
+}
+void clear_error() { g_err[0] = 0; }
+}  // namespace pic
+
 extern "C" {
 
 const char* pic_last_error(void) { return g_err; }

@@ -107,6 +107,10 @@ cudaError_t picard_int(Instance* I, int kind, int max_iters, int flags, const in
 cudaError_t sequential_int(Instance* I, int kind, cudaStream_t st);
 bool smem_cost_ok(const Instance* I);
 
+// Error message plumbing shared by the entry points (pic_api.cu).
+pic_status record_error(pic_status s, const char* msg);
+void clear_error();
+
 // Simple device-wide exclusive scan of int32 (n elements); total written to *total_dev.
 cudaError_t scan_exclusive(const int32_t* in, int32_t* out, int n, int32_t* total_dev,
                            int32_t* blk, cudaStream_t st);

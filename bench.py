@@ -72,7 +72,7 @@ def load_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("pic_int.cu", "pic_device.cuh", "pic_internal.h"):
+    for f in ("pic_int.cu", "pic_picard.cuh", "pic_device.cuh", "pic_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_2406_01939_b300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

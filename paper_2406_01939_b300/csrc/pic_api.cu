@@ -145,7 +145,7 @@ void free_instance(Instance& I) {
                     I.seg_ce, I.seg_meta, I.seg_lpt, I.len_hist, I.alpha_s, I.agg, I.carry, I.sbagg, I.sbincl,
                     I.fc,
                     I.xfin, I.xwork, I.act_t, I.tmp_a, I.tmp_b, I.tmp_c, I.scan_blk, I.hist,
-                    I.ctrl, I.trace};
+                    I.ctrl, I.trace, I.mlp_P, I.mlp_W1s, I.mlp_W2, I.mlp_b2};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < 4; ++i)
@@ -305,8 +305,11 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
         return fail(PIC_ERR_INVALID_ARG, "unknown policy kind %d", pol->kind);
     if (pol->kind == PIC_POLICY_DUAL && !I.has_lam)
         return fail(PIC_ERR_INVALID_ARG, "bid-price policy needs an instance created with lam");
-    if (pol->kind >= PIC_POLICY_MLP)
-        return fail(PIC_ERR_UNSUPPORTED, "MLP policies are not built into this library yet");
+    const bool mlp = pol->kind == PIC_POLICY_MLP || pol->kind == PIC_POLICY_GUMBEL;
+    if (mlp && pol->hidden != kHidden)
+        return fail(PIC_ERR_UNSUPPORTED, "MLP hidden width must be %d", kHidden);
+    if (mlp && (!pol->W1 || !pol->b1 || !pol->W2 || !pol->b2 || !pol->E))
+        return fail(PIC_ERR_INVALID_ARG, "MLP policy needs W1, b1, W2, b2 and E (device pointers)");
     if (opts->num_chunks < 0 || opts->max_iters < 0 || opts->seg_window < 0)
         return fail(PIC_ERR_INVALID_ARG, "negative num_chunks, max_iters or seg_window");
     cudaStream_t st = (cudaStream_t)opts->stream;
@@ -315,13 +318,25 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
     const cudaMemcpyKind okind = host_out ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     const bool timing = (opts->flags & PIC_FLAG_TIMING) != 0;
     I.launches = 0;
+    if (mlp && !I.mlp_P) {  // per-region chain prefixes and FP32 weights, sized once
+        CU(dmalloc(&I.mlp_P, (size_t)I.R * kHidden));
+        CU(dmalloc(&I.mlp_W1s, N * kHidden));
+        CU(dmalloc(&I.mlp_W2, N * kHidden));
+        CU(dmalloc(&I.mlp_b2, N));
+    }
     if (timing) CU(cudaEventRecord(I.ev[0], st));
     CU(cudaMemsetAsync(I.ctrl, 0, offsetof(Ctrl, nruns), st));
+    if (mlp) CU(mlp_prepare(&I, pol, st));
     int M = 1, iters_cap = 1;
     if (opts->mode == PIC_MODE_SEQUENTIAL) {
         CU(cudaMemcpyAsync(I.xwork, I.x0, sizeof(int32_t) * K * N, cudaMemcpyDeviceToDevice, st));
         if (timing) CU(cudaEventRecord(I.ev[1], st));
-        if (T) CU(sequential_int(&I, pol->kind, st));
+        if (T && mlp) {
+            CU(sequential_mlp(&I, pol, st));
+            CU(reduce_costs(&I, I.act_t, I.reg, st));
+        } else if (T) {
+            CU(sequential_int(&I, pol->kind, st));
+        }
         if (timing) CU(cudaEventRecord(I.ev[2], st));
         if (T) CU(cudaMemcpyAsync(actions_out, I.act_t, T, okind, st));
         if (final_stock)
@@ -375,7 +390,7 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
             if (timing) CU(cudaEventRecord(I.ev[1], st));
             const bool trace = opts->trace && opts->trace_cap > 0;
             if (trace) CU(cudaMemsetAsync(I.trace, 0, sizeof(long long) * 4 * kTraceCap, st));
-            CU(picard_int(&I, pol->kind, iters_cap, opts->flags, opts->alpha_init,
+            CU(picard_run(&I, pol, iters_cap, opts->flags, opts->alpha_init,
                           opts->timeout_ns ? opts->timeout_ns : 10000000000ull, trace, st));
             if (timing) CU(cudaEventRecord(I.ev[2], st));
             CU(finish_outputs(&I, st));

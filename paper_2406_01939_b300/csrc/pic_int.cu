@@ -459,8 +459,10 @@ bool smem_cost_ok(const Instance* I) {
     return I->cost16 && (size_t)I->R * I->N * sizeof(int16_t) <= kSmemCostMax;
 }
 
-cudaError_t picard_int(Instance* I, int kind, int max_iters, int flags, const int8_t* alpha_init,
-                       unsigned long long timeout_ns, bool trace, cudaStream_t st) {
+cudaError_t picard_run(Instance* I, const pic_policy* pol, int max_iters, int flags,
+                       const int8_t* alpha_init, unsigned long long timeout_ns, bool trace,
+                       cudaStream_t st) {
+    const int kind = pol->kind;
     KArgs a;
     a.T = I->T; a.N = I->N; a.K = I->K; a.NP = I->NP; a.R = I->R;
     a.reg_s = I->reg_s; a.run_start = I->run_start; a.seg_run = I->seg_run;
@@ -472,6 +474,7 @@ cudaError_t picard_int(Instance* I, int kind, int max_iters, int flags, const in
     a.ctrl = I->ctrl; a.max_iters = max_iters; a.flags = flags;
     a.first_dirty = alpha_init != nullptr; a.timeout_ns = timeout_ns;
     a.trace = trace ? I->trace : nullptr;
+    if (kind == PIC_POLICY_MLP || kind == PIC_POLICY_GUMBEL) return picard_mlp(I, a, pol, st);
     const bool dual = kind == PIC_POLICY_DUAL;
     if ((flags & PIC_FLAG_GROUP_KERNEL) && grp_ok(I)) return picard_grp(I, a, dual, st);
     const int npl = (I->N + 31) / 32;

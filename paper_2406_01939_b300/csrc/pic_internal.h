@@ -82,6 +82,11 @@ struct Instance {
     int32_t *xfin;      // [K][N] final stock
     int32_t *xwork;     // [K][N] working stock of the sequential simulator
     int8_t *act_t;      // [T]  actions in time order (device staging)
+    // MLP policy, per call: chain prefix per region and FP32 copies of the weights
+    float *mlp_P;       // [R][256]
+    float *mlp_W1s;     // [N][256] stock rows of W1
+    float *mlp_W2;      // [256][N]
+    float *mlp_b2;      // [N]
     // scratch for the sort and scans
     int32_t *tmp_a, *tmp_b, *tmp_c;   // [T] each
     int32_t *scan_blk;                // block sums
@@ -101,9 +106,15 @@ cudaError_t build_tables(Instance* I, int M, int W, cudaStream_t st);
 // Scatter the sorted cache to time order and reduce segment costs.
 cudaError_t finish_outputs(Instance* I, cudaStream_t st);
 
-// Integer policies (pic_int.cu).
-cudaError_t picard_int(Instance* I, int kind, int max_iters, int flags, const int8_t* alpha_init,
-                       unsigned long long timeout_ns, bool trace, cudaStream_t st);
+// Picard passes for any policy (pic_int.cu dispatches to the integer or MLP kernels).
+cudaError_t picard_run(Instance* I, const pic_policy* pol, int max_iters, int flags,
+                       const int8_t* alpha_init, unsigned long long timeout_ns, bool trace,
+                       cudaStream_t st);
+// MLP policies (pic_mlp.cu).
+cudaError_t mlp_prepare(Instance* I, const pic_policy* pol, cudaStream_t st);
+cudaError_t sequential_mlp(Instance* I, const pic_policy* pol, cudaStream_t st);
+// Total cost and a^phi count of an action array (any order) with its regions.
+cudaError_t reduce_costs(Instance* I, const int8_t* alpha, const int32_t* reg, cudaStream_t st);
 cudaError_t sequential_int(Instance* I, int kind, cudaStream_t st);
 bool smem_cost_ok(const Instance* I);
 

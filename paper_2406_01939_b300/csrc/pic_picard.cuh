@@ -199,6 +199,9 @@ __device__ __forceinline__ void superblock_prefix(const KArgs& a, int s, const S
 
 }  // namespace picard
 
+// MLP Picard kernel (pic_mlp.cu).
+cudaError_t picard_mlp(Instance* I, const picard::KArgs& a, const pic_policy* pol, cudaStream_t st);
+
 // Group-per-segment Picard kernel (pic_grp.cu).
 int grp_lanes(int N);
 bool grp_ok(const Instance* I);

@@ -385,12 +385,18 @@ cudaError_t build_tables(Instance* I, int M, int W, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+cudaError_t reduce_costs(Instance* I, const int8_t* alpha, const int32_t* reg, cudaStream_t st) {
+    if (I->T == 0) return cudaSuccess;
+    I->launches += 1;
+    k_reduce_costs<<<4 * I->num_sms, 256, 0, st>>>(alpha, reg, I->cost, I->T, I->N, I->ctrl);
+    return cudaGetLastError();
+}
+
 cudaError_t finish_outputs(Instance* I, cudaStream_t st) {
     if (I->T == 0) return cudaSuccess;
-    I->launches += 2;
+    I->launches += 1;
     k_scatter_actions<<<nblocks(I->T, 256), 256, 0, st>>>(I->alpha_s, I->perm, I->T, I->act_t);
-    k_reduce_costs<<<4 * I->num_sms, 256, 0, st>>>(I->alpha_s, I->reg_s, I->cost, I->T, I->N, I->ctrl);
-    return cudaGetLastError();
+    return reduce_costs(I, I->alpha_s, I->reg_s, st);
 }
 
 }  // namespace pic

@@ -1,0 +1,87 @@
+"""GPU parity of the MLP policies (argmax and Gumbel-max) against the CPU oracle
+through the C ABI.  Scores use a fixed FP32 operation order on both sides, so
+actions, pass counts, final stock and total cost must be identical."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2406_01939_b300 as pic
+from paper_2406_01939_b300 import synth
+from paper_2406_01939_b300.session import DeviceInstance
+from paper_2406_01939_b300.synth import Policy
+
+pytestmark = pytest.mark.gpu
+
+
+def small(seed, T, N, K, R, fill=0.9):
+    inst = synth.make_instance(T, N, K, R, seed=seed, stock="poisson", fill=fill)
+    return inst, synth.make_mlp(N, R, seed=seed)
+
+
+def policies(mlp, seed):
+    return [Policy("mlp", mlp=mlp), Policy("gumbel", mlp=mlp, seed=1000 + seed, traj=seed % 3)]
+
+
+@pytest.mark.parametrize("N", [8, 33, 64, 100])
+def test_sequential_mlp_bit_exact(N):
+    inst, mlp = small(N, 1500, N, 30, 11)
+    d = DeviceInstance(inst)
+    for pol in policies(mlp, N):
+        want = oracle.seq_sim(inst, pol)
+        got = d.simulate(pol, "sequential")
+        np.testing.assert_array_equal(got["actions"].cpu().numpy(), want["actions"])
+        np.testing.assert_array_equal(got["final_stock"].cpu().numpy(), want["x_final"])
+        assert got["total_cost"] == want["total_cost"] and got["lost"] == want["lost"]
+
+
+@pytest.mark.parametrize("N", [8, 64])
+def test_picard_mlp_iterates_and_fixed_point(N):
+    """Pass count, fixed point and every intermediate cache alpha^k equal the
+    oracle's (Algorithm 1 with the same blocks)."""
+    inst, mlp = small(7 * N, 1200, N, 20, 9)
+    d = DeviceInstance(inst)
+    for pol in policies(mlp, N):
+        M = 40
+        want = oracle.picard_chunked(inst, pol, M, record=True)
+        seq = oracle.seq_sim(inst, pol)
+        got = d.simulate(pol, "picard", num_chunks=M)
+        np.testing.assert_array_equal(got["actions"].cpu().numpy(), seq["actions"])
+        assert got["iters"] == want["iters"]
+        assert got["total_cost"] == seq["total_cost"]
+        np.testing.assert_array_equal(got["final_stock"].cpu().numpy(), seq["x_final"])
+        for k in (1, 2, want["iters"] // 2):
+            g = d.simulate(pol, "picard", num_chunks=M, max_iters=k, raise_on_error=False)
+            np.testing.assert_array_equal(g["actions"].cpu().numpy(), want["iterates"][k - 1])
+
+
+def test_picard_mlp_windows_and_chunk_counts():
+    inst, mlp = small(3, 2000, 32, 15, 6)
+    d = DeviceInstance(inst)
+    pol = Policy("mlp", mlp=mlp)
+    seq = oracle.seq_sim(inst, pol)["actions"]
+    for M in (1, 13, 2000):
+        want = oracle.picard_chunked(inst, pol, M)
+        for W in (1, 5, 64):
+            got = d.simulate(pol, "picard", num_chunks=M, seg_window=W)
+            np.testing.assert_array_equal(got["actions"].cpu().numpy(), seq)
+            assert got["iters"] == want["iters"]
+
+
+def test_mlp_full_size_sampled_against_oracle():
+    """T=2^18, N=64, K=2,000, R=500 MLP workload: the Picard fixed point equals the
+    GPU sequential simulation, and at sampled orders the oracle's decision from
+    the state implied by the GPU path's earlier actions is the GPU's action."""
+    inst, mlp = synth.mlp_medium(0)
+    d = DeviceInstance(inst)
+    pol = Policy("mlp", mlp=mlp)
+    got = d.simulate(pol, "picard", num_chunks=1024)
+    seq = d.simulate(pol, "sequential")
+    a = got["actions"].cpu().numpy()
+    assert torch.equal(got["actions"], seq["actions"])
+    assert got["total_cost"] == seq["total_cost"]
+    rng = np.random.default_rng(0)
+    for t in np.concatenate([rng.integers(0, inst.T, 24), [0, inst.T - 1]]):
+        row = oracle.state_before(inst, a, int(t))
+        want = oracle.policy_call(inst, pol, row, inst.prod[t], inst.reg[t], int(t))
+        assert want == a[t], (t, want, a[t])

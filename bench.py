@@ -46,18 +46,33 @@ def parse():
     p.add_argument("--seq-steps", type=int, default=3)
     p.add_argument("--e2e-steps", type=int, default=20)
     p.add_argument("--cpu-seconds", type=float, default=10.0)
-    p.add_argument("--T", type=int, default=1 << 20, help="orders (smaller only for profiling)")
+    p.add_argument("--T", type=int, default=0, help="orders (0 = the workload's own size)")
+    p.add_argument("--workload", default="dual_large", choices=["dual_large", "mlp_medium"])
+    p.add_argument("--flags", type=int, default=0, help="extra pic_sim_opts flags (tuning)")
     return p.parse_args()
 
 
+def make_workload(args, seed):
+    """(instance, policy, policy-kind name) of the named synthetic workload."""
+    from paper_2406_01939_b300 import synth
+    from paper_2406_01939_b300.synth import Policy
+    if args.workload == "mlp_medium":
+        inst, mlp = synth.mlp_medium(seed, **({"T": args.T} if args.T else {}))
+        return inst, Policy("mlp", mlp=mlp), "mlp"
+    inst = synth.dual_large(seed, **({"T": args.T} if args.T else {}))
+    return inst, Policy("dual"), "dual"
+
+
 def workload_config(args, inst):
+    pol = "MLP Linear(2N+16,256)-ReLU-Linear(256,N), BF16 N(0,0.02)" \
+        if args.workload == "mlp_medium" else "bid-price, lambda~U{0..30}"
     return {
-        "workload": "dual_large",
-        "desc": (f"bid-price FO, T={inst.T} orders, N={inst.N} warehouses, K={inst.K} products "
-                 f"(Zipf 1.1), R={inst.R} regions, x0~Poisson(1.05 T p_k/N), lambda~U{{0..30}}, "
-                 f"cost~U{{1..100}}"),
+        "workload": args.workload,
+        "desc": (f"FO, T={inst.T} orders, N={inst.N} warehouses, K={inst.K} products "
+                 f"(Zipf 1.1), R={inst.R} regions, x0~Poisson(1.05 T p_k/N), cost~U{{1..100}}, "
+                 f"{pol}"),
         "T": inst.T, "N": inst.N, "K": inst.K, "R": inst.R,
-        "chunks": args.chunks, "policy": "dual",
+        "chunks": args.chunks, "policy": args.workload == "mlp_medium" and "mlp" or "dual",
         "l2": "flushed between timed steps (256 MiB write)",
     }
 
@@ -136,45 +151,69 @@ class Clocks:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_oracle_rate(inst, seconds):
-    """The CPU oracle's sequential simulator on the host (1 thread), repeated on
-    the full trajectory for about `seconds`."""
+def prefix_instance(inst, T):
+    """The first T orders of a trajectory (sequential simulation is causal, so its
+    actions are the first T actions of the full trajectory)."""
+    from paper_2406_01939_b300.synth import Instance
+    return Instance(T, inst.N, inst.K, inst.R, inst.prod[:T].copy(), inst.reg[:T].copy(), inst.x0,
+                    inst.cost, inst.lam)
+
+
+def cpu_oracle_rate(inst, pol, seconds):
+    """The CPU oracle's sequential simulator on the host (1 thread) for about
+    `seconds`: the full trajectory repeated, or, when one full run would take
+    longer, a prefix of the trajectory sized to the budget.
+    Returns (orders/s, sample description, oracle output, orders covered)."""
     import oracle
-    from paper_2406_01939_b300.synth import Policy
-    pol = Policy("dual")
-    oracle.seq_sim(inst, pol)  # build + warm
+    probe_T = min(inst.T, 2048)
+    t0 = time.perf_counter()
+    oracle.seq_sim(prefix_instance(inst, probe_T), pol)
+    per_order = max((time.perf_counter() - t0) / probe_T, 1e-9)
+    if per_order * inst.T > seconds:
+        Ts = max(probe_T, min(inst.T, int(seconds / per_order)))
+        sub = prefix_instance(inst, Ts)
+        t0 = time.perf_counter()
+        out = oracle.seq_sim(sub, pol)
+        el = time.perf_counter() - t0
+        return Ts / el, f"first {Ts} of {inst.T} orders, sequential C oracle, 1 thread ({el:.1f} s)", out, Ts
     n, t0 = 0, time.perf_counter()
-    out = None
     while True:
         out = oracle.seq_sim(inst, pol)
         n += 1
         el = time.perf_counter() - t0
         if el >= seconds:
             break
-    return n * inst.T / el, n, el, out
+    return (n * inst.T / el, f"full {inst.T}-order trajectory x{n} ({el:.1f} s), sequential C oracle, "
+            f"1 thread", out, inst.T)
 
 
 def run_reference(args):
-    from paper_2406_01939_b300 import synth
-    inst = synth.dual_large(args.seed, T=args.T)
+    inst, pol, _ = make_workload(args, args.seed)
     per = max(1, int(args.steps))
     import oracle
-    from paper_2406_01939_b300.synth import Policy
-    pol = Policy("dual")
+    # each step: the full trajectory, or a prefix of it when a full run exceeds ~10 s
+    probe = prefix_instance(inst, min(inst.T, 2048))
+    t0 = time.perf_counter()
+    oracle.seq_sim(probe, pol)
+    per_order = max((time.perf_counter() - t0) / probe.T, 1e-9)
+    Ts = inst.T if per_order * inst.T <= 10.0 else max(probe.T, int(10.0 / per_order))
+    sub = inst if Ts == inst.T else prefix_instance(inst, Ts)
     for _ in range(max(0, args.warmup)):
-        oracle.seq_sim(inst, pol)
+        oracle.seq_sim(sub, pol)
     t0 = time.perf_counter()
     for _ in range(per):
-        oracle.seq_sim(inst, pol)
+        oracle.seq_sim(sub, pol)
     el = time.perf_counter() - t0
-    value = per * inst.T / el
+    value = per * sub.T / el
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": per, "warmup": args.warmup, "ms_per_step": 1000 * el / per,
+        "steps": per, "warmup": args.warmup, "ms_per_step": 1000 * el / per * inst.T / sub.T,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic", "config": workload_config(args, inst),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"full {inst.T}-order trajectory per step, sequential C oracle"},
+                         "sample": (f"full {inst.T}-order trajectory per step" if sub.T == inst.T else
+                                    f"first {sub.T} of {inst.T} orders per step") +
+                                   ", sequential C oracle, 1 thread"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -202,15 +241,15 @@ def main():
     from paper_2406_01939_b300.session import DeviceInstance, DevicePolicy
     from paper_2406_01939_b300.synth import Policy
 
-    inst = synth.dual_large(args.seed + rank, T=args.T)
+    inst, hpol, _ = make_workload(args, args.seed + rank)
     di = DeviceInstance(inst, device=dev)
-    pol = DevicePolicy(Policy("dual"), dev)
+    pol = DevicePolicy(hpol, dev)
     T = inst.T
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def step(out):
         return di.simulate(pol, "picard", num_chunks=args.chunks, seg_window=args.seg_window,
-                           flags=pic.PIC_FLAG_TIMING, want_stock=False, out=out)
+                           flags=pic.PIC_FLAG_TIMING | args.flags, want_stock=False, out=out)
 
     act = torch.empty(T, dtype=torch.int8, device=dev)
     for _ in range(max(3, args.warmup)):
@@ -247,7 +286,7 @@ def main():
     # one extra (untimed) call with the per-pass trace
     tr = np.zeros((4096, 4), np.int64)
     di.simulate(pol, "picard", num_chunks=args.chunks, seg_window=args.seg_window,
-                want_stock=False, out=act, trace=tr)
+                flags=args.flags, want_stock=False, out=act, trace=tr)
     ntr = min(last["iters"], 4096)
     ts, tr_end = tr[:ntr, 0], tr[:ntr, 1]
     prev = np.r_[0, tr_end[:-1]]
@@ -274,11 +313,13 @@ def main():
 
     # end to end through host buffers: H2D of the inputs, simulate, D2H of the actions
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).pin_memory()
-    host = {k: pin(getattr(inst, k)) for k in ("prod", "reg", "x0", "cost", "lam")}
-    host_np = {k: v.numpy() for k, v in host.items()}
+    host = {k: pin(getattr(inst, k)) for k in ("prod", "reg", "x0", "cost")}
+    host["lam"] = pin(inst.lam) if inst.lam is not None else None
+    host_np = {k: (v.numpy() if v is not None else None) for k, v in host.items()}
     host_act = torch.empty(T, dtype=torch.int8).pin_memory().numpy()
-    opts = pic.make_opts("picard", args.chunks, out_mem=pic.PIC_MEM_HOST, seg_window=args.seg_window)
-    h2d = sum(host_np[k].nbytes for k in host_np)
+    opts = pic.make_opts("picard", args.chunks, out_mem=pic.PIC_MEM_HOST, seg_window=args.seg_window,
+                         flags=args.flags)
+    h2d = sum(v.nbytes for v in host_np.values() if v is not None)
     d2h = host_act.nbytes + 64  # actions + the result record
     e2e_t = []
     for i in range(args.e2e_steps + 2 if args.e2e_steps > 0 else 0):
@@ -324,12 +365,14 @@ def main():
         "wall_s_timed_loop": wall,
     }
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
-        rate, n, el, out = cpu_oracle_rate(inst, args.cpu_seconds)
+        rate, sample, out, covered = cpu_oracle_rate(inst, hpol, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"full {T}-order trajectory x{n} ({el:.1f} s), "
-                                          f"sequential C oracle, 1 thread"}
-        line["bit_exact_vs_oracle"] = bool(np.array_equal(out["actions"], act.cpu().numpy())) and \
-            out["total_cost"] == last["total_cost"]
+                                "sample": sample}
+        same = bool(np.array_equal(out["actions"], act.cpu().numpy()[:covered]))
+        if covered == T:
+            same = same and out["total_cost"] == last["total_cost"]
+        line["bit_exact_vs_oracle"] = same
+        line["oracle_orders_checked"] = covered
     elif rank == 0:
         line["cpu_baseline"] = None
     if rank == 0:

@@ -107,7 +107,8 @@ typedef struct {
     const int8_t* alpha_init; /* DEVICE [T] initial action cache, or NULL = all a^phi (Alg. 1) */
     uint64_t timeout_ns;      /* bound on any device-side wait; 0 = 10 s */
     int32_t out_mem;          /* PIC_MEM_HOST / PIC_MEM_DEVICE for the output arrays */
-    int32_t seg_window;       /* tuning: orders of one product per warp work unit; 0 = 64 */
+    int32_t seg_window;       /* tuning: orders of one product per warp work unit; 0 = 64
+                                 (greedy, bid-price) or 8 (MLP policies) */
     void* stream;             /* cudaStream_t or NULL */
     int64_t* trace;           /* HOST [trace_cap][4] per-pass record, or NULL: ns from the
                                  simulation kernel's start to the end of the pass's prefix

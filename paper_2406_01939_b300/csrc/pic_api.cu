@@ -345,7 +345,9 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
         M = opts->num_chunks ? opts->num_chunks : (int)((T + 255) / 256);
         if (M < 1) M = 1;
         if (T && M > (int)T) M = (int)T;
-        const int W = opts->seg_window ? opts->seg_window : kSegWindow;
+        // default window: long work units amortise the cheap integer policy; the MLP
+        // policy's per-order cost makes short units (short critical paths) better
+        const int W = opts->seg_window ? opts->seg_window : (mlp ? kSegWindowMlp : kSegWindow);
         iters_cap = opts->max_iters ? opts->max_iters : M + 1;
         // tables + per-segment state (capacity for this window)
         const int64_t smax = (int64_t)2 * K + (int64_t)(T + W - 1) / W + 2;

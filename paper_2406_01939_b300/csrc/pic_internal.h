@@ -10,7 +10,8 @@ namespace pic {
 
 constexpr int kEmb = 16;           // region-embedding width of the MLP policy
 constexpr int kHidden = 256;       // MLP hidden width
-constexpr int kSegWindow = 64;     // default segment window (orders of one product)
+constexpr int kSegWindow = 64;     // default segment window (orders of one product), integer policies
+constexpr int kSegWindowMlp = 8;   // default segment window, MLP policies
 constexpr int kSuperBlock = 32;    // segments per carry super-block
 constexpr int kThreads = 256;      // threads per CTA of the persistent kernels
 constexpr size_t kSmemCostMax = 200 * 1024;  // largest int16 cost table staged in shared memory

@@ -132,9 +132,15 @@ struct MlpPolicy {
 // The warp evaluates the policy for stock row S (lane l holds warehouses l + 32 i)
 // of an order in region r at time t; fs/hs: per-warp shared scratch (N and H
 // floats).  Returns the action (warp-uniform).
-template <int NPL>
-__device__ __forceinline__ int mlp_decide(const MlpPolicy& p, const int S[NPL], int r, int t,
-                                          float* fs, float* hs) {
+template <bool SMEMW>
+__device__ __forceinline__ float wld(const float* p) {
+    if (SMEMW) return *p;  // shared-memory copy of the weights
+    return __ldg(p);
+}
+
+template <int NPL, bool SMEMW>
+__device__ __forceinline__ int mlp_decide(const MlpPolicy& p, const float* W1s, const float* W2f,
+                                          const int S[NPL], int r, int t, float* fs, float* hs) {
     const int lane = lane_id();
     const int N = p.N, H = p.H;
 #pragma unroll
@@ -147,11 +153,12 @@ __device__ __forceinline__ int mlp_decide(const MlpPolicy& p, const int S[NPL], 
     float acc[kJ];
 #pragma unroll
     for (int u = 0; u < kJ; ++u) acc[u] = __ldg(p.P + (size_t)r * H + lane + 32 * u);
+#pragma unroll 2
     for (int n = 0; n < N; ++n) {
         const float f = fs[n];
-        const float* w = p.W1s + (size_t)n * H + lane;
+        const float* w = W1s + (size_t)n * H + lane;
 #pragma unroll
-        for (int u = 0; u < kJ; ++u) acc[u] = fmaf(__ldg(w + 32 * u), f, acc[u]);
+        for (int u = 0; u < kJ; ++u) acc[u] = fmaf(wld<SMEMW>(w + 32 * u), f, acc[u]);
     }
 #pragma unroll
     for (int u = 0; u < kJ; ++u) hs[lane + 32 * u] = acc[u] > 0.0f ? acc[u] : 0.0f;
@@ -164,7 +171,8 @@ __device__ __forceinline__ int mlp_decide(const MlpPolicy& p, const int S[NPL], 
         const int n = lane + 32 * i;
         if (n < N && S[i] > 0) {
             float s = __ldg(p.b2f + n);
-            for (int j = 0; j < H; ++j) s = fmaf(__ldg(p.W2f + (size_t)j * N + n), hs[j], s);
+#pragma unroll 8
+            for (int j = 0; j < H; ++j) s = fmaf(wld<SMEMW>(W2f + (size_t)j * N + n), hs[j], s);
             if (p.gumbel) s = __fadd_rn(s, gumbel1(p.seed, p.traj, t, n));
             const unsigned kk = ord_key(s);
             if (!any || kk > best_key) { best_key = kk; best_n = n; any = true; }
@@ -177,13 +185,27 @@ __device__ __forceinline__ int mlp_decide(const MlpPolicy& p, const int S[NPL], 
     return stocked ? n : -1;
 }
 
+// Copy the FP32 weights (W1 stock rows, then W2) into shared memory.
+__device__ __forceinline__ void stage_weights(const MlpPolicy& p, float* sw) {
+    const int n = 2 * p.N * p.H;
+    const float* src0 = p.W1s;
+    const float* src1 = p.W2f;
+    const int half = p.N * p.H;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sw[i] = i < half ? src0[i] : src1[i - half];
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------- sequential simulator
-template <int NPL>
+template <int NPL, bool SMEMW>
 __global__ void __launch_bounds__(32) k_seq_mlp(int T, int N, const int32_t* __restrict__ prod,
                                                 const int32_t* __restrict__ reg, int32_t* xw,
                                                 int8_t* __restrict__ act_t, MlpPolicy p, Ctrl* ctrl) {
     __shared__ float fs[128];
     __shared__ float hs[kHidden];
+    extern __shared__ float s_w[];
+    if (SMEMW) stage_weights(p, s_w);
+    const float* W1s = SMEMW ? s_w : p.W1s;
+    const float* W2f = SMEMW ? s_w + (size_t)p.N * p.H : p.W2f;
     const int lane = lane_id();
     int my_act = -1;
     for (int t = 0; t < T; ++t) {
@@ -194,7 +216,7 @@ __global__ void __launch_bounds__(32) k_seq_mlp(int T, int N, const int32_t* __r
             const int n = lane + 32 * i;
             S[i] = n < N ? xw[(size_t)k * N + n] : 0;
         }
-        const int act = mlp_decide<NPL>(p, S, r, t, fs, hs);
+        const int act = mlp_decide<NPL, SMEMW>(p, W1s, W2f, S, r, t, fs, hs);
 #pragma unroll
         for (int i = 0; i < NPL; ++i)
             if (act == lane + 32 * i) xw[(size_t)k * N + act] = S[i] - 1;
@@ -213,9 +235,10 @@ __global__ void __launch_bounds__(32) k_seq_mlp(int T, int N, const int32_t* __r
 }
 
 // ---------------------------------------------------------------- Picard, one warp per segment
-template <int NPL>
-__device__ bool replay_segment_mlp(const KArgs& a, const MlpPolicy& p, const int32_t* __restrict__ perm,
-                                   int s, const SegMeta& m, int fcp, int* fc_cur,
+template <int NPL, bool SMEMW>
+__device__ bool replay_segment_mlp(const KArgs& a, const MlpPolicy& p, const float* W1s,
+                                   const float* W2f, const int32_t* __restrict__ perm, int s,
+                                   const SegMeta& m, int fcp, int* fc_cur,
                                    unsigned long long& calls, float* fs, float* hs) {
     const int lane = lane_id();
     const int N = a.N, NP = a.NP;
@@ -261,7 +284,7 @@ __device__ bool replay_segment_mlp(const KArgs& a, const MlpPolicy& p, const int
             const int tt = __shfl_sync(kFull, my_t, q);
             int act = ao;
             if (eval) {
-                act = mlp_decide<NPL>(p, S, rr, tt, fs, hs);
+                act = mlp_decide<NPL, SMEMW>(p, W1s, W2f, S, rr, tt, fs, hs);
                 ++evals;
             }
 #pragma unroll
@@ -296,9 +319,13 @@ __device__ bool replay_segment_mlp(const KArgs& a, const MlpPolicy& p, const int
 
 constexpr int kMlpThreads = 256;
 
-template <int NPL>
+template <int NPL, bool SMEMW>
 __global__ void __launch_bounds__(kMlpThreads, 1) k_picard_mlp(KArgs a, MlpPolicy p,
                                                               const int32_t* __restrict__ perm) {
+    extern __shared__ float s_w[];
+    if (SMEMW) stage_weights(p, s_w);
+    const float* W1s = SMEMW ? s_w : p.W1s;
+    const float* W2f = SMEMW ? s_w + (size_t)p.N * p.H : p.W2f;
     __shared__ int s_changed;
     __shared__ SegMeta s_meta[kMlpThreads / 32][32];
     __shared__ int s_fcp[kMlpThreads / 32][32];
@@ -376,8 +403,8 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_picard_mlp(KArgs a, MlpPolic
                 todo &= todo - 1;
                 const SegMeta mm = smem_meta(&s_meta[wib][src]);
                 const int seg = __shfl_sync(kFull, sl, src);
-                chg |= replay_segment_mlp<NPL>(a, p, perm, seg, mm, s_fcp[wib][src], fc_cur, calls,
-                                               s_fs[wib], s_hs[wib]);
+                chg |= replay_segment_mlp<NPL, SMEMW>(a, p, W1s, W2f, perm, seg, mm, s_fcp[wib][src],
+                                                      fc_cur, calls, s_fs[wib], s_hs[wib]);
                 if (lane == 0) replays += 1;
             }
             __syncwarp();
@@ -420,11 +447,18 @@ MlpPolicy make_policy_view(const Instance* I, const pic_policy* pol) {
     return p;
 }
 
-template <int NPL>
+// Weights fit in shared memory next to the kernels' static buffers.
+bool smem_weights_ok(int N) { return (size_t)2 * N * kHidden * sizeof(float) <= 180 * 1024; }
+
+template <int NPL, bool SMEMW>
 cudaError_t launch_picard_mlp(Instance* I, const KArgs& a, const MlpPolicy& p, cudaStream_t st) {
-    auto kern = k_picard_mlp<NPL>;
+    auto kern = k_picard_mlp<NPL, SMEMW>;
+    const size_t smem = SMEMW ? (size_t)2 * I->N * kHidden * sizeof(float) : 0;
+    cudaError_t e;
+    if (SMEMW && (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+        return e;
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kMlpThreads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kMlpThreads, smem);
     if (e) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const int grid = I->num_sms * (occ < 2 ? occ : 2);
@@ -433,7 +467,19 @@ cudaError_t launch_picard_mlp(Instance* I, const KArgs& a, const MlpPolicy& p, c
     const int32_t* perm = I->perm;
     void* params[] = {&args, &pp, &perm};
     I->launches += 1;
-    return cudaLaunchCooperativeKernel((const void*)kern, grid, kMlpThreads, params, 0, st);
+    return cudaLaunchCooperativeKernel((const void*)kern, grid, kMlpThreads, params, smem, st);
+}
+
+template <int NPL, bool SMEMW>
+cudaError_t launch_seq_mlp(Instance* I, const MlpPolicy& p, cudaStream_t st) {
+    auto kern = k_seq_mlp<NPL, SMEMW>;
+    const size_t smem = SMEMW ? (size_t)2 * I->N * kHidden * sizeof(float) : 0;
+    cudaError_t e;
+    if (SMEMW && (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+        return e;
+    I->launches += 1;
+    kern<<<1, 32, smem, st>>>(I->T, I->N, I->prod, I->reg, I->xwork, I->act_t, p, I->ctrl);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -452,23 +498,20 @@ cudaError_t mlp_prepare(Instance* I, const pic_policy* pol, cudaStream_t st) {
 
 cudaError_t sequential_mlp(Instance* I, const pic_policy* pol, cudaStream_t st) {
     const MlpPolicy p = make_policy_view(I, pol);
-    I->launches += 1;
     const int npl = (I->N + 31) / 32;
-    if (npl == 1)
-        k_seq_mlp<1><<<1, 32, 0, st>>>(I->T, I->N, I->prod, I->reg, I->xwork, I->act_t, p, I->ctrl);
-    else if (npl == 2)
-        k_seq_mlp<2><<<1, 32, 0, st>>>(I->T, I->N, I->prod, I->reg, I->xwork, I->act_t, p, I->ctrl);
-    else
-        k_seq_mlp<4><<<1, 32, 0, st>>>(I->T, I->N, I->prod, I->reg, I->xwork, I->act_t, p, I->ctrl);
-    return cudaGetLastError();
+    const bool sw = smem_weights_ok(I->N);
+    if (npl == 1) return sw ? launch_seq_mlp<1, true>(I, p, st) : launch_seq_mlp<1, false>(I, p, st);
+    if (npl == 2) return sw ? launch_seq_mlp<2, true>(I, p, st) : launch_seq_mlp<2, false>(I, p, st);
+    return sw ? launch_seq_mlp<4, true>(I, p, st) : launch_seq_mlp<4, false>(I, p, st);
 }
 
 cudaError_t picard_mlp(Instance* I, const KArgs& a, const pic_policy* pol, cudaStream_t st) {
     const MlpPolicy p = make_policy_view(I, pol);
     const int npl = (I->N + 31) / 32;
-    if (npl == 1) return launch_picard_mlp<1>(I, a, p, st);
-    if (npl == 2) return launch_picard_mlp<2>(I, a, p, st);
-    return launch_picard_mlp<4>(I, a, p, st);
+    const bool sw = smem_weights_ok(I->N);
+    if (npl == 1) return sw ? launch_picard_mlp<1, true>(I, a, p, st) : launch_picard_mlp<1, false>(I, a, p, st);
+    if (npl == 2) return sw ? launch_picard_mlp<2, true>(I, a, p, st) : launch_picard_mlp<2, false>(I, a, p, st);
+    return sw ? launch_picard_mlp<4, true>(I, a, p, st) : launch_picard_mlp<4, false>(I, a, p, st);
 }
 
 }  // namespace pic

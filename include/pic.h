@@ -68,9 +68,13 @@ enum {
     PIC_FLAG_REUSE_TABLES = 2, /* keep the order/run tables of the previous call if its
                                  chunking matches (skip the per-call preprocessing) */
     PIC_FLAG_TIMING = 4,       /* time the phases with CUDA events (pic_sim_result *_ms) */
-    PIC_FLAG_GROUP_KERNEL = 8  /* tuning: replay each work unit with a group of 8 warehouses
+    PIC_FLAG_GROUP_KERNEL = 8, /* tuning: replay each work unit with a group of 8 warehouses
                                   per lane instead of a whole warp (integer policies, costs
                                   that fit int16) */
+    PIC_FLAG_GRAPH = 16        /* pic_simulate_batch: run the per-call device work as a CUDA
+                                  graph, captured at the first call and relaunched while the
+                                  chunking, CTA shape, MLP weight pointers, alpha_init, trace,
+                                  max_iters, timeout and flags stay the same */
 };
 
 typedef struct pic_instance pic_instance;
@@ -105,7 +109,8 @@ typedef struct {
     int32_t max_iters;        /* cap on passes; 0 = M + 1 (Prop. 1 bound plus the confirming pass) */
     int32_t flags;            /* PIC_FLAG_* */
     const int8_t* alpha_init; /* DEVICE [T] initial action cache, or NULL = all a^phi (Alg. 1) */
-    uint64_t timeout_ns;      /* bound on any device-side wait; 0 = 10 s */
+    uint64_t timeout_ns;      /* bound on the device-side waits of the simulation kernel,
+                                 measured from its start; 0 = 10 s (60 s for a batch) */
     int32_t out_mem;          /* PIC_MEM_HOST / PIC_MEM_DEVICE for the output arrays */
     int32_t seg_window;       /* tuning: orders of one product per warp work unit; 0 = 64
                                  (greedy, bid-price) or 8 (MLP policies) */
@@ -131,7 +136,20 @@ typedef struct {
     float prep_ms;        /* PIC_FLAG_TIMING: order tables (sort, runs, segments) */
     float sim_ms;         /* PIC_FLAG_TIMING: the simulation kernel (all passes) */
     float total_ms;       /* PIC_FLAG_TIMING: whole call on the device, first to last kernel */
+    int32_t seg_window;   /* segment window used (Picard) */
+    int32_t cta_threads;  /* threads per CTA of the Picard launch */
+    int32_t ctas_per_sm;  /* CTAs per SM of the Picard launch */
 } pic_sim_result;
+
+/* Per-trajectory result of pic_simulate_batch. */
+typedef struct {
+    int64_t total_cost; /* sum of cost[r_t][a_t] over the trajectory's fulfilled orders */
+    int64_t lost;       /* a^phi actions of the trajectory */
+    int32_t iters;      /* passes after which the trajectory's cache stopped changing, plus
+                           the confirming pass: what pic_simulate with min(M, T_b) chunks
+                           reports for this trajectory alone (1 in PIC_MODE_SEQUENTIAL) */
+    int32_t converged;  /* 1 if the trajectory reached its fixed point within the passes run */
+} pic_traj_result;
 
 /* Create an instance: validates and copies desc's arrays to the device, sized
  * for (T, N, K, R).  *out receives an owned handle (free with
@@ -182,6 +200,40 @@ pic_status pic_simulate(pic_instance* inst, const pic_policy* pol, const pic_sim
 pic_status pic_simulate_sequential_static(const pic_instance_desc* desc, int32_t kind,
                                           int8_t* actions_out, int32_t* final_stock,
                                           int64_t* total_cost, int64_t* lost);
+
+/* Create a batch instance from B trajectories' inputs (Sec. 4 simulates many
+ * trajectories of one policy; each is its own FO instance).  All descs must
+ * have the same N; T, K, R, lam presence and memory kind may differ per
+ * trajectory; the work is ordered on descs[0].stream.  The batch is stored as
+ * one combined instance: trajectory b's orders, products and regions occupy
+ * their own index ranges in the order given, so trajectories never share state.
+ * Limits: sum of T < 2^31, sum of K < 2^31, sum of R < 2^31.  Release with
+ * pic_destroy_instance.  Errors: INVALID_ARG (names the trajectory), OOM, CUDA. */
+pic_status pic_create_batch(const pic_instance_desc* descs, int32_t B, pic_instance** out);
+
+/* Simulate every trajectory of a batch instance, each under its own policy,
+ * in one persistent launch (PIC_MODE_PICARD) or one warp per trajectory
+ * (PIC_MODE_SEQUENTIAL).
+ *   pols         HOST [B]: policy of each trajectory.  Kinds may be mixed; every
+ *                MLP / Gumbel policy of one call must use the same W1, b1, W2, b2,
+ *                E pointers (seed and traj may differ), and E must then have
+ *                max_b R_b rows (region r of trajectory b reads row r); bid-price
+ *                needs the trajectory to have been created with lam.
+ *   opts         as for pic_simulate, with num_chunks = M chunks per trajectory:
+ *                trajectory b runs Algorithm 1 with min(M, T_b) contiguous chunks,
+ *                exactly as pic_simulate would on it alone.  num_chunks = 0 runs
+ *                the built-in autotuner (chunk count, CTA shape, segment window;
+ *                timed trial launches on this batch, cached per batch and policy
+ *                mix) and uses its choice; max_iters = 0 means (largest chunk
+ *                count) + 1; alpha_init is DEVICE [sum T] in batch order.
+ *   actions_out  [sum T] int8, trajectory b at offset T_0 + ... + T_{b-1};
+ *   final_stock  [sum K][N] int32 in the same trajectory order, or NULL;
+ *   traj         HOST [B] per-trajectory results, or NULL;
+ *   res          HOST totals over the batch, or NULL (iters = passes run).
+ * Errors: INVALID_ARG, UNSUPPORTED, NOT_CONVERGED, TIMEOUT, CUDA. */
+pic_status pic_simulate_batch(pic_instance* batch, const pic_policy* pols,
+                              const pic_sim_opts* opts, int8_t* actions_out, int32_t* final_stock,
+                              pic_traj_result* traj, pic_sim_result* res);
 
 /* Message for the last non-OK status on this thread ("" if none). */
 const char* pic_last_error(void);

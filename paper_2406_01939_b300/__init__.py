@@ -7,8 +7,8 @@ kernels.  There is no CPU fallback: if the library or a CUDA device is missing,
 calls raise.
 
 Names follow the C ABI: ``pic_create_instance``, ``pic_instance_load``,
-``pic_destroy_instance``, ``pic_simulate``, ``pic_simulate_sequential_static``,
-``pic_last_error``.
+``pic_destroy_instance``, ``pic_simulate``, ``pic_create_batch``,
+``pic_simulate_batch``, ``pic_simulate_sequential_static``, ``pic_last_error``.
 """
 from __future__ import annotations
 
@@ -25,6 +25,7 @@ PIC_POLICY_GREEDY, PIC_POLICY_DUAL, PIC_POLICY_MLP, PIC_POLICY_GUMBEL = 0, 1, 2,
 PIC_MODE_PICARD, PIC_MODE_SEQUENTIAL = 0, 1
 PIC_MEM_HOST, PIC_MEM_DEVICE = 0, 1
 PIC_FLAG_NO_RESET, PIC_FLAG_REUSE_TABLES, PIC_FLAG_TIMING, PIC_FLAG_GROUP_KERNEL = 1, 2, 4, 8
+PIC_FLAG_GRAPH = 16
 
 POLICY_KINDS = {"greedy": PIC_POLICY_GREEDY, "dual": PIC_POLICY_DUAL, "mlp": PIC_POLICY_MLP,
                 "gumbel": PIC_POLICY_GUMBEL}
@@ -61,7 +62,13 @@ class pic_sim_result(C.Structure):
     _fields_ = [("total_cost", C.c_int64), ("lost", C.c_int64), ("policy_calls", C.c_int64),
                 ("iters", C.c_int32), ("num_chunks", C.c_int32), ("rescored", C.c_int64),
                 ("seg_replays", C.c_int64), ("launches", C.c_int32), ("prep_ms", C.c_float),
-                ("sim_ms", C.c_float), ("total_ms", C.c_float)]
+                ("sim_ms", C.c_float), ("total_ms", C.c_float), ("seg_window", C.c_int32),
+                ("cta_threads", C.c_int32), ("ctas_per_sm", C.c_int32)]
+
+
+class pic_traj_result(C.Structure):
+    _fields_ = [("total_cost", C.c_int64), ("lost", C.c_int64), ("iters", C.c_int32),
+                ("converged", C.c_int32)]
 
 
 _lib = None
@@ -86,6 +93,11 @@ def lib():
             L.pic_simulate.argtypes = [P, C.POINTER(pic_policy), C.POINTER(pic_sim_opts), P, P,
                                        C.POINTER(pic_sim_result)]
             L.pic_simulate.restype = C.c_int
+            L.pic_create_batch.argtypes = [C.POINTER(pic_instance_desc), C.c_int32, C.POINTER(P)]
+            L.pic_create_batch.restype = C.c_int
+            L.pic_simulate_batch.argtypes = [P, C.POINTER(pic_policy), C.POINTER(pic_sim_opts), P, P,
+                                             C.POINTER(pic_traj_result), C.POINTER(pic_sim_result)]
+            L.pic_simulate_batch.restype = C.c_int
             L.pic_simulate_sequential_static.argtypes = [C.POINTER(pic_instance_desc), C.c_int32, P,
                                                          P, C.POINTER(C.c_int64),
                                                          C.POINTER(C.c_int64)]
@@ -170,6 +182,30 @@ def pic_simulate(handle: int, policy: pic_policy, opts: pic_sim_opts, actions_ou
     if raise_on_error and st != PIC_OK:
         raise PicError(st, pic_last_error())
     return st, res
+
+
+def pic_create_batch(descs) -> int:
+    """Batch instance from a list of pic_instance_desc (all with the same N)."""
+    arr = (pic_instance_desc * len(descs))(*descs)
+    h = C.c_void_p()
+    _check(lib().pic_create_batch(arr, len(descs), C.byref(h)))
+    return h.value
+
+
+def pic_simulate_batch(handle: int, policies, opts: pic_sim_opts, actions_out, final_stock=None,
+                       raise_on_error=True):
+    """Simulate every trajectory of a batch instance; policies is a list of
+    pic_policy (one per trajectory).  Returns (status, pic_sim_result,
+    [pic_traj_result])."""
+    B = len(policies)
+    pols = (pic_policy * B)(*policies)
+    traj = (pic_traj_result * B)()
+    res = pic_sim_result()
+    st = lib().pic_simulate_batch(C.c_void_p(handle), pols, C.byref(opts), _ptr(actions_out),
+                                  _ptr(final_stock), traj, C.byref(res))
+    if raise_on_error and st != PIC_OK:
+        raise PicError(st, pic_last_error())
+    return st, res, list(traj)
 
 
 def pic_simulate_sequential_static(desc: pic_instance_desc, kind, actions_out, final_stock=None,

@@ -9,10 +9,6 @@
 
 using namespace pic;
 
-struct pic_instance {
-    Instance I;
-};
-
 namespace {
 
 thread_local char g_err[512] = "";
@@ -128,6 +124,13 @@ __global__ void k_seg_hist(const int8_t* __restrict__ alpha_s, const int32_t* __
     }
 }
 
+__global__ void k_set_tag(Ctrl* c, unsigned v) { c->tag_next = v; }
+
+__global__ void k_take_tags(Ctrl* c, unsigned n) {
+    c->tag_base = c->tag_next;
+    c->tag_next += n;
+}
+
 bool valid_desc(const pic_instance_desc* d) {
     return d && d->T >= 0 && d->N >= 1 && d->N <= 127 && d->K >= 1 && d->K <= 65535 && d->R >= 1 &&
            d->R <= 65535 && (d->T == 0 || (d->prod && d->reg)) && d->x0 && d->cost &&
@@ -137,19 +140,6 @@ bool valid_desc(const pic_instance_desc* d) {
 template <typename T>
 cudaError_t dmalloc(T** p, size_t n) {
     return cudaMalloc((void**)p, sizeof(T) * (n ? n : 1));
-}
-
-void free_instance(Instance& I) {
-    void* ptrs[] = {I.prod, I.reg, I.x0, I.cost, I.lam, I.perm, I.prod_s, I.reg_s, I.pcount,
-                    I.pstart, I.run_start, I.run_of, I.seg_run, I.seg_of_run, I.seg_prod, I.seg_cf,
-                    I.seg_ce, I.seg_meta, I.seg_lpt, I.len_hist, I.alpha_s, I.agg, I.carry, I.sbagg, I.sbincl,
-                    I.fc,
-                    I.xfin, I.xwork, I.act_t, I.tmp_a, I.tmp_b, I.tmp_c, I.scan_blk, I.hist,
-                    I.ctrl, I.trace, I.mlp_P, I.mlp_W1s, I.mlp_W2, I.mlp_b2};
-    for (void* p : ptrs)
-        if (p) cudaFree(p);
-    for (int i = 0; i < 4; ++i)
-        if (I.ev[i]) cudaEventDestroy(I.ev[i]);
 }
 
 pic_status copy_inputs(Instance& I, const pic_instance_desc* d, cudaStream_t st) {
@@ -162,13 +152,8 @@ pic_status copy_inputs(Instance& I, const pic_instance_desc* d, cudaStream_t st)
     CU(cudaMemcpyAsync(I.x0, d->x0, sizeof(int32_t) * I.K * I.N, kind, st));
     CU(cudaMemcpyAsync(I.cost, d->cost, sizeof(int32_t) * I.R * I.N, kind, st));
     if (I.has_lam) CU(cudaMemcpyAsync(I.lam, d->lam, sizeof(int32_t) * I.K * I.N, kind, st));
-    // validate on the device
+    CU(launch_validate(I, st));
     int* bad = &I.ctrl->pad0;
-    CU(cudaMemsetAsync(bad, 0, sizeof(int), st));
-    k_validate<<<2 * I.num_sms, 256, 0, st>>>(I.T, I.N, I.K, I.R, I.prod, I.reg, I.x0, I.cost,
-                                              I.has_lam ? I.lam : nullptr, bad);
-    if (I.has_lam) k_validate_dual<<<I.N, 256, 0, st>>>(I.N, I.K, I.R, I.cost, I.lam, bad);
-    CU(cudaGetLastError());
     int hb = 0;
     CU(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
@@ -191,24 +176,51 @@ pic_status record_error(pic_status s, const char* msg) {
     return s;
 }
 void clear_error() { g_err[0] = 0; }
-}  // namespace pic
 
-extern "C" {
+bool desc_ok(const pic_instance_desc* d) { return valid_desc(d); }
 
-const char* pic_last_error(void) { return g_err; }
+cudaError_t launch_validate(Instance& I, cudaStream_t st) {
+    int* bad = &I.ctrl->pad0;
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int), st);
+    if (e) return e;
+    k_validate<<<2 * I.num_sms, 256, 0, st>>>(I.T, I.N, I.K, I.R, I.prod, I.reg, I.x0, I.cost,
+                                              I.has_lam ? I.lam : nullptr, bad);
+    if (I.has_lam) k_validate_dual<<<I.N, 256, 0, st>>>(I.N, I.K, I.R, I.cost, I.lam, bad);
+    return cudaGetLastError();
+}
 
-pic_status pic_create_instance(const pic_instance_desc* d, pic_instance** out) {
-    g_err[0] = 0;
-    if (!out) return fail(PIC_ERR_INVALID_ARG, "out is NULL");
-    *out = nullptr;
-    if (!valid_desc(d)) return fail(PIC_ERR_INVALID_ARG, "invalid instance descriptor (sizes, pointers or mem)");
-    pic_instance* h = new (std::nothrow) pic_instance();
-    if (!h) return fail(PIC_ERR_OOM, "host allocation failed");
-    Instance& I = h->I;
-    memset(&I, 0, sizeof(I));
-    I.T = d->T; I.N = d->N; I.K = d->K; I.R = d->R;
-    I.NP = ((d->N + 31) / 32) * 32;
-    I.has_lam = d->lam != nullptr;
+void free_instance(Instance& I) {
+    void* ptrs[] = {I.prod, I.reg, I.x0, I.cost, I.lam, I.perm, I.prod_s, I.reg_s, I.pcount,
+                    I.pstart, I.run_start, I.run_of, I.seg_run, I.seg_of_run, I.seg_prod, I.seg_cf,
+                    I.seg_ce, I.seg_meta, I.seg_lpt, I.len_hist, I.alpha_s, I.agg, I.carry, I.sbagg,
+                    I.sbincl, I.fc, I.xfin, I.xwork, I.act_t, I.tmp_a, I.tmp_b, I.tmp_c, I.scan_blk,
+                    I.hist, I.ctrl, I.trace, I.mlp_P, I.mlp_W1p, I.mlp_W2p, I.mlp_b2};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (int i = 0; i < 4; ++i)
+        if (I.ev[i]) cudaEventDestroy(I.ev[i]);
+    if (Batch* b = I.batch) {
+        void* dp[] = {b->toff, b->koff, b->roff, b->traj_of_prod, b->reg_local, b->chunk_len,
+                      b->pol, b->last_chg, b->tres};
+        for (void* p : dp)
+            if (p) cudaFree(p);
+        if (b->h_pol) cudaFreeHost(b->h_pol);
+        if (b->h_out) cudaFreeHost(b->h_out);
+        if (b->gexec) cudaGraphExecDestroy(b->gexec);
+        if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+        delete[] b->h_toff;
+        delete[] b->h_koff;
+        delete[] b->h_roff;
+        delete[] b->h_has_lam;
+        delete b;
+        I.batch = nullptr;
+    }
+}
+
+cudaError_t alloc_instance(Instance& I, int T_, int N_, int K_, int R_, bool has_lam) {
+    I.T = T_; I.N = N_; I.K = K_; I.R = R_;
+    I.NP = ((N_ + 31) / 32) * 32;
+    I.has_lam = has_lam;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (!e) e = cudaDeviceGetAttribute(&I.num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -251,6 +263,86 @@ pic_status pic_create_instance(const pic_instance_desc* d, pic_instance** out) {
     if (!e) e = cudaMalloc((void**)&I.ctrl, sizeof(Ctrl));
     if (!e) e = cudaMalloc((void**)&I.trace, sizeof(long long) * 4 * kTraceCap);
     for (int i = 0; i < 4 && !e; ++i) e = cudaEventCreate(&I.ev[i]);
+    return e;
+}
+
+cudaError_t prepare_picard_state(Instance& I, int W, int iters_cap, cudaStream_t st) {
+    const int64_t smax = (int64_t)2 * I.K + (int64_t)((int64_t)I.T + W - 1) / W + 2;
+    cudaError_t e;
+    if (!I.agg || smax > I.smax_agg) {
+        if (I.agg) {
+            cudaFree(I.agg); cudaFree(I.carry); cudaFree(I.sbagg); cudaFree(I.sbincl);
+        }
+        I.agg = I.carry = nullptr;
+        I.sbagg = I.sbincl = nullptr;
+        I.smax_agg = 0;
+        if ((e = dmalloc(&I.agg, (size_t)smax * I.NP))) return e;
+        if ((e = dmalloc(&I.carry, (size_t)smax * I.NP))) return e;
+        if ((e = dmalloc(&I.sbagg, (size_t)smax * I.NP))) return e;
+        if ((e = dmalloc(&I.sbincl, (size_t)smax * I.NP))) return e;
+        I.smax_agg = smax;
+        I.tag_next = 0;  // forces the clear below
+    }
+    // Look-back words carry tags that are never reused on this instance, so the
+    // words of earlier calls need no clearing; they are cleared only for fresh
+    // memory and when the 32-bit tag space runs out.  agg and carry need no
+    // clearing either: pass 1 replays every segment (writing agg) and reads no
+    // carry unless the cache starts from alpha_init, whose histograms and
+    // prefixes are computed before use.
+    if (I.tag_next == 0 || (unsigned long long)I.tag_next + iters_cap + 1 >= 0x7FFFFFFFull) {
+        const size_t bytes = sizeof(unsigned long long) * (size_t)I.smax_agg * I.NP;
+        if ((e = cudaMemsetAsync(I.sbagg, 0, bytes, st))) return e;
+        if ((e = cudaMemsetAsync(I.sbincl, 0, bytes, st))) return e;
+        k_set_tag<<<1, 1, 0, st>>>(I.ctrl, 1u);
+        I.launches += 1;
+        if ((e = cudaGetLastError())) return e;
+        I.tag_next = 1;
+    }
+    // the host mirror runs ahead by one call; take_tags advances the device copy
+    I.tag_next += (unsigned)iters_cap + 1;
+    return cudaSuccess;
+}
+
+cudaError_t take_tags(Instance& I, int iters_cap, cudaStream_t st) {
+    k_take_tags<<<1, 1, 0, st>>>(I.ctrl, (unsigned)iters_cap + 1);
+    I.launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t init_cache(Instance& I, const int8_t* alpha_init, cudaStream_t st) {
+    const size_t T = I.T, K = I.K, N = I.N;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(I.fc, 0xFF, sizeof(int32_t) * K, st))) return e;  // pass 0: all "changed"
+    if ((e = cudaMemcpyAsync(I.xfin, I.x0, sizeof(int32_t) * K * N, cudaMemcpyDeviceToDevice, st)))
+        return e;
+    if (!T) return cudaSuccess;
+    if (alpha_init) {
+        int* bad = &I.ctrl->pad0;
+        k_gather_alpha<<<(int)((T + 255) / 256), 256, 0, st>>>(alpha_init, I.perm, (int)T, (int)N,
+                                                             I.alpha_s, bad);
+        k_seg_hist<<<2 * I.num_sms, 256, 8 * I.NP * sizeof(int), st>>>(I.alpha_s, I.run_start,
+                                                                       I.seg_run, I.ctrl, I.NP, I.agg);
+        I.launches += 2;
+        return cudaGetLastError();
+    }
+    return cudaMemsetAsync(I.alpha_s, 0xFF, T, st);  // a^phi everywhere (Alg. 1 line 1)
+}
+}  // namespace pic
+
+extern "C" {
+
+const char* pic_last_error(void) { return g_err; }
+
+pic_status pic_create_instance(const pic_instance_desc* d, pic_instance** out) {
+    g_err[0] = 0;
+    if (!out) return fail(PIC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!valid_desc(d)) return fail(PIC_ERR_INVALID_ARG, "invalid instance descriptor (sizes, pointers or mem)");
+    pic_instance* h = new (std::nothrow) pic_instance();
+    if (!h) return fail(PIC_ERR_OOM, "host allocation failed");
+    Instance& I = h->I;
+    memset(&I, 0, sizeof(I));
+    cudaError_t e = alloc_instance(I, d->T, d->N, d->K, d->R, d->lam != nullptr);
     // per-segment histograms: allocated lazily at the first simulate (size depends on W)
     if (e) {
         free_instance(I);
@@ -279,6 +371,7 @@ pic_status pic_instance_load(pic_instance* h, const pic_instance_desc* d) {
     if (!h) return fail(PIC_ERR_INVALID_ARG, "instance is NULL");
     if (!valid_desc(d)) return fail(PIC_ERR_INVALID_ARG, "invalid instance descriptor");
     Instance& I = h->I;
+    if (I.batch) return fail(PIC_ERR_INVALID_ARG, "batch instance: inputs are fixed at pic_create_batch");
     if (d->T != I.T || d->N != I.N || d->K != I.K || d->R != I.R || (d->lam != nullptr) != (I.has_lam != 0))
         return fail(PIC_ERR_INVALID_ARG, "shape differs from the instance's");
     I.tables_m = 0;  // the order tables describe the old stream
@@ -297,6 +390,7 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
     if (!h || !pol || !opts || (!actions_out && h->I.T > 0))
         return fail(PIC_ERR_INVALID_ARG, "instance, policy, opts and actions_out are required");
     Instance& I = h->I;
+    if (I.batch) return fail(PIC_ERR_INVALID_ARG, "batch instance: use pic_simulate_batch");
     if (opts->mode != PIC_MODE_PICARD && opts->mode != PIC_MODE_SEQUENTIAL)
         return fail(PIC_ERR_INVALID_ARG, "unknown mode %d", opts->mode);
     if (opts->out_mem != PIC_MEM_HOST && opts->out_mem != PIC_MEM_DEVICE)
@@ -318,12 +412,7 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
     const cudaMemcpyKind okind = host_out ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     const bool timing = (opts->flags & PIC_FLAG_TIMING) != 0;
     I.launches = 0;
-    if (mlp && !I.mlp_P) {  // per-region chain prefixes and FP32 weights, sized once
-        CU(dmalloc(&I.mlp_P, (size_t)I.R * kHidden));
-        CU(dmalloc(&I.mlp_W1s, N * kHidden));
-        CU(dmalloc(&I.mlp_W2, N * kHidden));
-        CU(dmalloc(&I.mlp_b2, N));
-    }
+    if (mlp) CU(mlp_alloc(&I));
     if (timing) CU(cudaEventRecord(I.ev[0], st));
     CU(cudaMemsetAsync(I.ctrl, 0, offsetof(Ctrl, nruns), st));
     if (mlp) CU(mlp_prepare(&I, pol, st));
@@ -349,46 +438,16 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
         // policy's per-order cost makes short units (short critical paths) better
         const int W = opts->seg_window ? opts->seg_window : (mlp ? kSegWindowMlp : kSegWindow);
         iters_cap = opts->max_iters ? opts->max_iters : M + 1;
-        // tables + per-segment state (capacity for this window)
-        const int64_t smax = (int64_t)2 * K + (int64_t)(T + W - 1) / W + 2;
-        if (!I.agg || smax > I.smax_agg) {
-            if (I.agg) {
-                cudaFree(I.agg); cudaFree(I.carry); cudaFree(I.sbagg); cudaFree(I.sbincl);
-            }
-            I.agg = I.carry = nullptr;
-            I.sbagg = I.sbincl = nullptr;
-            I.smax_agg = 0;
-            CU(dmalloc(&I.agg, (size_t)smax * I.NP));
-            CU(dmalloc(&I.carry, (size_t)smax * I.NP));
-            CU(dmalloc(&I.sbagg, (size_t)smax * I.NP));
-            CU(dmalloc(&I.sbincl, (size_t)smax * I.NP));
-            I.smax_agg = smax;
-        }
+        CU(prepare_picard_state(I, W, iters_cap, st));
         const bool reuse = (opts->flags & PIC_FLAG_REUSE_TABLES) && I.tables_m == M && I.tables_w == W;
         if (!reuse) {
             CU(build_tables(&I, M, W, st));
             I.tables_m = M;
             I.tables_w = W;
         }
-        CU(cudaMemsetAsync(I.agg, 0, sizeof(int32_t) * (size_t)smax * I.NP, st));
-        CU(cudaMemsetAsync(I.carry, 0, sizeof(int32_t) * (size_t)smax * I.NP, st));
-        // look-back words of earlier calls carry pass tags that this call reuses
-        CU(cudaMemsetAsync(I.sbagg, 0, sizeof(unsigned long long) * (size_t)smax * I.NP, st));
-        CU(cudaMemsetAsync(I.sbincl, 0, sizeof(unsigned long long) * (size_t)smax * I.NP, st));
-        CU(cudaMemsetAsync(I.fc, 0xFF, sizeof(int32_t) * K, st));  // pass 0: everything "changed"
-        CU(cudaMemcpyAsync(I.xfin, I.x0, sizeof(int32_t) * K * N, cudaMemcpyDeviceToDevice, st));
+        CU(take_tags(I, iters_cap, st));
+        CU(init_cache(I, opts->alpha_init, st));
         if (T) {
-            if (opts->alpha_init) {
-                int* bad = &I.ctrl->pad0;
-                k_gather_alpha<<<(int)((T + 255) / 256), 256, 0, st>>>(opts->alpha_init, I.perm, (int)T,
-                                                                     (int)N, I.alpha_s, bad);
-                k_seg_hist<<<2 * I.num_sms, 256, 8 * I.NP * sizeof(int), st>>>(
-                    I.alpha_s, I.run_start, I.seg_run, I.ctrl, I.NP, I.agg);
-                CU(cudaGetLastError());
-                I.launches += 2;
-            } else {
-                CU(cudaMemsetAsync(I.alpha_s, 0xFF, T, st));  // a^phi everywhere (Alg. 1 line 1)
-            }
             if (timing) CU(cudaEventRecord(I.ev[1], st));
             const bool trace = opts->trace && opts->trace_cap > 0;
             if (trace) CU(cudaMemsetAsync(I.trace, 0, sizeof(long long) * 4 * kTraceCap, st));
@@ -426,6 +485,9 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
         res->policy_calls = (int64_t)hc.policy_calls;
         res->iters = T ? hc.iters : 1;
         res->num_chunks = M;
+        res->seg_window = opts->mode == PIC_MODE_PICARD ? I.tables_w : 0;
+        res->cta_threads = opts->mode == PIC_MODE_PICARD ? I.cta_threads : 32;
+        res->ctas_per_sm = opts->mode == PIC_MODE_PICARD ? I.ctas_per_sm : 1;
         res->rescored = (int64_t)hc.rescored;
         res->seg_replays = (int64_t)hc.seg_replays;
         res->launches = I.launches;

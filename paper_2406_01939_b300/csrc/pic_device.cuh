@@ -23,6 +23,9 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 }
 
 __device__ __forceinline__ int ld_volatile(const int* p) { return *(volatile const int*)p; }
+__device__ __forceinline__ unsigned ld_volatile(const unsigned* p) {
+    return *(volatile const unsigned*)p;
+}
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 

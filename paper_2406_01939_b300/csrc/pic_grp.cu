@@ -47,7 +47,7 @@ __device__ __forceinline__ bool replay_group(const KArgs& a, const int16_t* __re
                                              int NP8, int s, const SegMeta& m, int fcp,
                                              int* fc_cur, int2* ord, int* runend,
                                              signed char* newa, unsigned gmask, int j,
-                                             unsigned long long& calls) {
+                                             int it, unsigned long long& calls) {
     using Lay = GrpLayout<G>;
     const int N = a.N, NP = a.NP;
     const int k = m.k;
@@ -55,7 +55,8 @@ __device__ __forceinline__ bool replay_group(const KArgs& a, const int16_t* __re
     // D: counts of cached actions of product k before the current run; S: stock;
     // hist: new actions of this segment; corr: (cached - new) counts in the run
     int S[kWpl], D[kWpl], x0v[kWpl], adj[kWpl], hist[kWpl], corr[kWpl];
-    const bool chained = m.ce - m.cf > 1;
+    // prefix counts of earlier segments; none before pass 1 of an all-a^phi cache
+    const bool chained = m.ce - m.cf > 1 && (it > 1 || a.first_dirty);
 #pragma unroll
     for (int i = 0; i < kWpl; ++i) {
         const int n = nb + i;
@@ -211,6 +212,7 @@ __global__ void __launch_bounds__(kGrpThreads, 1) k_picard_grp(KArgs a, int NP8)
     const unsigned long long deadline = globaltimer_ns() + a.timeout_ns;
     const int nseg = a.ctrl->nseg;
     const bool no_reset = (a.flags & PIC_FLAG_NO_RESET) != 0;
+    const unsigned tag_base = ld_volatile(&a.ctrl->tag_base);
     unsigned long long calls = 0, replays = 0;
     const unsigned long long t_start = globaltimer_ns();
     int it = 1;
@@ -243,8 +245,8 @@ __global__ void __launch_bounds__(kGrpThreads, 1) k_picard_grp(KArgs a, int NP8)
                     const int src = __ffs(todo) - 1;
                     todo &= todo - 1;
                     const SegMeta mm = smem_meta(&s_meta[wib][src]);
-                    superblock_prefix<NPL>(a, gwarp + (j0 + src) * nwarps, mm, it, s_fcp[wib][src],
-                                           deadline);
+                    superblock_prefix<NPL>(a, gwarp + (j0 + src) * nwarps, mm, it,
+                                           tag_base + (unsigned)it, s_fcp[wib][src], deadline);
                 }
                 __syncwarp();
             }
@@ -279,7 +281,7 @@ __global__ void __launch_bounds__(kGrpThreads, 1) k_picard_grp(KArgs a, int NP8)
                 const SegMeta mm = smem_meta(&s_meta[wib][e]);
                 chg |= replay_group<G, DUAL>(a, s_cost, NP8, s_seg[wib][e], mm, s_fcp[wib][e],
                                              fc_cur, s_ord[gib], s_runend[gib], s_new[gib], gmask,
-                                             jg, calls);
+                                             jg, it, calls);
                 if (jg == 0) replays += 1;
             }
             __syncwarp();
@@ -332,6 +334,8 @@ cudaError_t launch_grp(Instance* I, const KArgs& a, cudaStream_t st) {
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const int grid = I->num_sms;  // one CTA per SM: every SM stages the cost table once
     I->coop_blocks = grid;
+    I->cta_threads = kGrpThreads;
+    I->ctas_per_sm = 1;
     KArgs args = a;
     int np8 = NP8;
     void* params[] = {&args, &np8};

@@ -18,6 +18,7 @@ constexpr size_t kSmemCostMax = 200 * 1024;  // largest int16 cost table staged 
 constexpr int kTraceCap = 4096;    // passes recorded by the device-side trace
 constexpr int kLenBuckets = 1024;  // segment-length buckets of the longest-first order
 constexpr size_t kGrpSmemMax = 150 * 1024;  // cost table budget of the group-per-segment kernel
+constexpr int kMlpLptWeight = 64;  // work of an MLP order relative to an integer-policy order
 
 // Device-side control block of one simulate call (zeroed before each launch).
 struct Ctrl {
@@ -37,12 +38,55 @@ struct Ctrl {
     int nseg;
     int last_m;              // chunk count the tables were built for
     int pad1;
+    // look-back tags (kept across calls): a call's passes use tag_base + pass,
+    // taken on the device by the call's first kernel from tag_next
+    unsigned tag_base;
+    unsigned tag_next;
 };
 
 // Per-segment metadata packed for one 32-byte load: product, run range, sorted
 // position range, first order of the last run, chain (product) segment range.
 struct __align__(32) SegMeta {
     int k, r0, r1, j0, jend, last_start, cf, ce;
+};
+
+// Per-trajectory policy selector of a batch call (device copy of pic_policy's
+// kind, trajectory id and noise seed).
+struct __align__(16) BatchPol {
+    int kind;
+    int traj;
+    unsigned long long seed;
+};
+
+// A batch of trajectories held as one instance (pic_create_batch).  Trajectory
+// b owns orders [toff[b], toff[b+1]), products [koff[b], koff[b+1]) and regions
+// [roff[b], roff[b+1]) of the combined arrays: its product and region ids are
+// shifted into those ranges at creation, so no two trajectories share state and
+// one Picard launch over the combined instance runs every trajectory's own
+// iteration (products never interact, Assumption 1 of Sec. 3.2).
+struct Batch {
+    int B;
+    int64_t *h_toff, *h_koff, *h_roff;  // host [B+1]
+    int8_t* h_has_lam;                  // host [B]: trajectory b was created with lam
+    int32_t *toff, *koff, *roff;        // device [B+1]
+    int32_t* traj_of_prod;              // [K] trajectory of each product
+    int32_t* reg_local;                 // [R] region id within its trajectory
+    int32_t* chunk_len;                 // [B] chunk length L_b of the current tables
+    BatchPol* pol;                      // [B] policies of the current call
+    BatchPol* h_pol;                    // pinned host staging of pol
+    int32_t* last_chg;                  // [B] last pass that changed a cached action of b
+    long long* tres;                    // [B][2] cost, a^phi count of trajectory b
+    unsigned char* h_out;               // pinned host staging: Ctrl, tres, last_chg
+    int max_t;                          // longest trajectory
+    // graph of the per-call work (PIC_FLAG_GRAPH), the signature it was captured
+    // for, the kernels it launches, and the stream captures are recorded on
+    cudaGraphExec_t gexec;
+    unsigned long long gsig;
+    int glaunches;
+    cudaStream_t cap_stream;
+    // autotuner result and the policy signature it was tuned for
+    unsigned long long tune_sig;
+    int tune_m, tune_w, tune_shape;
 };
 
 // All device buffers of one instance.  Sizes: T orders, K products, N warehouses,
@@ -73,6 +117,7 @@ struct Instance {
     int64_t smax;       // capacity of the segment tables (>= any segment count)
     int64_t smax_agg;   // capacity (segments) of agg/carry/sbtot
     int tables_m, tables_w;  // chunking the current tables were built for (0 = none)
+    unsigned tag_next;  // host mirror of ctrl->tag_next (0: look-back words not cleared yet)
     // iteration state
     int8_t *alpha_s;    // [T]  action cache in sorted order
     int32_t *agg;       // [SMAX][NP] histogram of cached actions per segment
@@ -85,8 +130,8 @@ struct Instance {
     int8_t *act_t;      // [T]  actions in time order (device staging)
     // MLP policy, per call: chain prefix per region and FP32 copies of the weights
     float *mlp_P;       // [R][256]
-    float *mlp_W1s;     // [N][256] stock rows of W1
-    float *mlp_W2;      // [256][N]
+    uint4 *mlp_W1p;     // [N][32] packed BF16 stock rows of W1
+    uint4 *mlp_W2p;     // [32][N] packed BF16 W2
     float *mlp_b2;      // [N]
     // scratch for the sort and scans
     int32_t *tmp_a, *tmp_b, *tmp_c;   // [T] each
@@ -96,22 +141,33 @@ struct Instance {
     Ctrl *ctrl;
     long long *trace;                 // [kTraceCap][4] device-side per-pass record
     int num_sms;
-    int coop_blocks;                  // persistent grid size (integer kernel)
+    int coop_blocks;                  // persistent grid size of the last Picard launch
+    int cta_threads, ctas_per_sm;     // its CTA shape
     int launches;                     // kernels launched by the current call
     cudaEvent_t ev[4];                // phase timing events (created with the instance)
+    Batch* batch;                     // non-null for a batch instance
 };
 
 // Preprocessing (pic_prep.cu): sort orders by product (stable in time), region
-// gather, per-product offsets, runs for M chunks and segments of window W.
+// gather, per-product offsets, runs for M chunks and segments of window W (a
+// batch instance chunks every trajectory by its own chunk_len), then the
+// longest-first order of the segments.
 cudaError_t build_tables(Instance* I, int M, int W, cudaStream_t st);
-// Scatter the sorted cache to time order and reduce segment costs.
+// Longest-first order of the segments by estimated work: length, times
+// mlp_weight for segments of trajectories whose policy (pol, batch only) is an
+// MLP kind.
+cudaError_t build_lpt(Instance* I, const BatchPol* pol, int mlp_weight, cudaStream_t st);
+// Scatter the sorted cache to time order (act_t), and also reduce the costs.
+cudaError_t scatter_actions(Instance* I, cudaStream_t st);
 cudaError_t finish_outputs(Instance* I, cudaStream_t st);
 
 // Picard passes for any policy (pic_int.cu dispatches to the integer or MLP kernels).
 cudaError_t picard_run(Instance* I, const pic_policy* pol, int max_iters, int flags,
                        const int8_t* alpha_init, unsigned long long timeout_ns, bool trace,
                        cudaStream_t st);
-// MLP policies (pic_mlp.cu).
+// MLP policies (pic_mlp.cu).  mlp_prepare evaluates the per-region chain
+// prefix (E rows through reg_local for a batch) and the FP32 weight copies.
+cudaError_t mlp_alloc(Instance* I);
 cudaError_t mlp_prepare(Instance* I, const pic_policy* pol, cudaStream_t st);
 cudaError_t sequential_mlp(Instance* I, const pic_policy* pol, cudaStream_t st);
 // Total cost and a^phi count of an action array (any order) with its regions.
@@ -122,9 +178,33 @@ bool smem_cost_ok(const Instance* I);
 // Error message plumbing shared by the entry points (pic_api.cu).
 pic_status record_error(pic_status s, const char* msg);
 void clear_error();
+// Sizes, pointers and memory kind of an instance descriptor are acceptable.
+bool desc_ok(const pic_instance_desc* d);
+
+// Instance memory (pic_api.cu): device buffers for T orders, K products, N
+// warehouses, R regions; free_instance releases whatever is allocated.
+cudaError_t alloc_instance(Instance& I, int T, int N, int K, int R, bool has_lam);
+void free_instance(Instance& I);
+// Range checks of an instance's device inputs (bits: 1 prod, 2 reg, 4 x0,
+// 8/16/32 cost, lam, cost - lam beyond 2^23, 128 a cost outside int16); the
+// result is left in ctrl->pad0.
+cudaError_t launch_validate(Instance& I, cudaStream_t st);
+// Per-segment Picard state sized for window W, with the look-back words cleared
+// when fresh or when a call of at most iters_cap passes would exhaust the tags.
+cudaError_t prepare_picard_state(Instance& I, int W, int iters_cap, cudaStream_t st);
+// First kernel of a call's per-call work: takes iters_cap + 1 tags on the device.
+cudaError_t take_tags(Instance& I, int iters_cap, cudaStream_t st);
+// Cache start (a^phi, or alpha_init gathered to sorted order with its segment
+// histograms) and the per-call resets of fc and xfin.
+cudaError_t init_cache(Instance& I, const int8_t* alpha_init, cudaStream_t st);
 
 // Simple device-wide exclusive scan of int32 (n elements); total written to *total_dev.
 cudaError_t scan_exclusive(const int32_t* in, int32_t* out, int n, int32_t* total_dev,
                            int32_t* blk, cudaStream_t st);
 
 }  // namespace pic
+
+// The opaque handle of the C ABI: a single trajectory, or a batch (I.batch set).
+struct pic_instance {
+    pic::Instance I;
+};

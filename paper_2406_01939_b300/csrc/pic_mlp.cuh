@@ -1,0 +1,336 @@
+// MLP and Gumbel-max policies on one warp: the fixed-order FP32 scorer, the
+// replay of one Picard segment and the sequential simulation, shared by the
+// single-trajectory and batch kernels.
+//
+// MLP policies (Sec. 4.1: an MLP scores the warehouses; the order goes to the
+// best-scoring warehouse that holds stock) in a fixed FP32 operation order, and
+// their Gumbel-max sampling variant.
+//
+// Score of warehouse n for an order of product k in region r with stock row S:
+//   h_j = b1_j, then one fmaf per input: cost[r][n]/128 (n = 0..N-1), E[r][e]
+//         (e = 0..15), min(S_n, 32)/32 (n = 0..N-1), weights W1 rows in that
+//         input's position; h_j = max(h_j, 0);
+//   s_n = b2_n, then one fmaf per hidden unit j = 0..255 with W2[j][n].
+// Parameters are BF16 (exact in FP32).  The part of the h chain before the stock
+// inputs depends only on the region, so it is evaluated once per call into
+// P[r][j] (the same operations in the same order).  Argmax over stocked
+// warehouses, ties to the lowest index; a^phi when nothing is stocked.
+//
+// Gumbel: s_n + g_n with g_n = -log(-log u), u = ((w >> 9) + 1/2) 2^-23 from
+// Philox4x32-10 (Salmon et al., SC'11) with key = seed and counter = (t,
+// trajectory, n / 4, 0), word n mod 4; log from IEEE operations only (x = m 2^e,
+// log m = 2 atanh((m-1)/(m+1)) by its series to the 11th power, ln 2 split in
+// two).  All floating-point steps use explicit round-to-nearest intrinsics so
+// that no contraction changes the bits.
+#pragma once
+
+#include "pic_picard.cuh"
+
+namespace pic {
+namespace mlp {
+
+using namespace picard;
+
+__device__ __forceinline__ float bf16f(uint16_t b) { return __uint_as_float((unsigned)b << 16); }
+
+// ---------------------------------------------------------------- Philox / log / Gumbel
+__device__ __forceinline__ void philox_round(unsigned c[4], unsigned k0, unsigned k1) {
+    const unsigned hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
+    const unsigned hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
+    const unsigned n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+}
+
+__device__ __forceinline__ void philox4x32_10(unsigned c[4], unsigned k0, unsigned k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        philox_round(c, k0, k1);
+    }
+}
+
+__device__ __forceinline__ float ieee_log(float x) {
+    const unsigned bits = __float_as_uint(x);
+    int e = (int)((bits >> 23) & 0xFF) - 127;
+    float m = __uint_as_float((bits & 0x007FFFFFu) | 0x3F800000u);
+    if (m > 1.41421356f) { m = __fmul_rn(m, 0.5f); e += 1; }
+    const float f = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+    const float f2 = __fmul_rn(f, f);
+    float p = 0.09090909090909091f;
+    p = fmaf(p, f2, 0.1111111111111111f);
+    p = fmaf(p, f2, 0.14285714285714285f);
+    p = fmaf(p, f2, 0.2f);
+    p = fmaf(p, f2, 0.3333333333333333f);
+    const float twof = __fmul_rn(2.0f, f);
+    const float r = __fmul_rn(twof, f2);
+    const float lm = fmaf(r, p, twof);
+    const float ef = (float)e;
+    return fmaf(ef, 0.693145751953125f, fmaf(ef, 1.4286068e-06f, lm));
+}
+
+// Gumbel noise for warehouses 4q .. 4q+3 of order t (one Philox block).
+__device__ __forceinline__ void gumbel4(unsigned long long seed, int traj, int t, int q, float g[4]) {
+    unsigned c[4] = {(unsigned)t, (unsigned)traj, (unsigned)q, 0u};
+    philox4x32_10(c, (unsigned)seed, (unsigned)(seed >> 32));
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float u = __fmul_rn(__fadd_rn((float)(c[i] >> 9), 0.5f), 1.1920928955078125e-7f);
+        g[i] = -ieee_log(-ieee_log(u));
+    }
+}
+
+__device__ __forceinline__ float gumbel1(unsigned long long seed, int traj, int t, int n) {
+    float g[4];
+    gumbel4(seed, traj, t, n >> 2, g);
+    return g[n & 3];
+}
+
+// monotone map of a float (not NaN) to unsigned; -0 is folded onto +0 first
+__device__ __forceinline__ unsigned ord_key(float v) {
+    const unsigned b = __float_as_uint(__fadd_rn(v, 0.0f));
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// ---------------------------------------------------------------- one decision, one warp
+// W1p and W2p hold the BF16 weights packed in pairs (exact in FP32 after the
+// 16-bit shift), in the order the scorer consumes them:
+//   W1p[n * 32 + l] = {W1s[n][l + 64v] | W1s[n][l + 64v + 32] << 16, v = 0..3}
+//                     (stock rows of W1; lane l's hidden units l + 32u, u = 0..7),
+//   W2p[q * N + n]  = {W2[8q + 2v][n] | W2[8q + 2v + 1][n] << 16, v = 0..3}.
+struct MlpPolicy {
+    int N, H;
+    const float* __restrict__ P;
+    const uint4* __restrict__ W1p;
+    const uint4* __restrict__ W2p;
+    const float* __restrict__ b2f;
+    bool gumbel;
+    unsigned long long seed;
+    int traj;
+};
+
+// Packed weights read from shared memory (staged copy) or global memory.
+template <bool SMEMW>
+__device__ __forceinline__ uint4 wld4(const uint4* p) {
+    if (SMEMW) return *p;
+    return __ldg(p);
+}
+__device__ __forceinline__ float lo16(unsigned w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float hi16(unsigned w) { return __uint_as_float(w & 0xFFFF0000u); }
+
+// The warp evaluates the policy for stock row S (lane l holds warehouses l + 32 i)
+// of an order in region r at time t; fs/hs: per-warp shared scratch (N and H
+// floats, hs 16-byte aligned).  Returns the action (warp-uniform).
+template <int NPL, bool SMEMW>
+__device__ __forceinline__ int mlp_decide(const MlpPolicy& p, const uint4* W1p, const uint4* W2p,
+                                          const int S[NPL], int r, int t, float* fs, float* hs) {
+    const int lane = lane_id();
+    const int N = p.N, H = p.H;
+#pragma unroll
+    for (int i = 0; i < NPL; ++i) {
+        const int n = lane + 32 * i;
+        if (n < N) fs[n] = __fdiv_rn((float)min(S[i], 32), 32.0f);
+    }
+    __syncwarp();
+    constexpr int kJ = kHidden / 32;  // hidden units per lane (l + 32u), advanced together
+    float acc[kJ];
+#pragma unroll
+    for (int u = 0; u < kJ; ++u) acc[u] = __ldg(p.P + (size_t)r * H + lane + 32 * u);
+#pragma unroll 2
+    for (int n = 0; n < N; ++n) {
+        const float f = fs[n];
+        const uint4 w = wld4<SMEMW>(W1p + n * 32 + lane);
+        acc[0] = fmaf(lo16(w.x), f, acc[0]);
+        acc[1] = fmaf(hi16(w.x), f, acc[1]);
+        acc[2] = fmaf(lo16(w.y), f, acc[2]);
+        acc[3] = fmaf(hi16(w.y), f, acc[3]);
+        acc[4] = fmaf(lo16(w.z), f, acc[4]);
+        acc[5] = fmaf(hi16(w.z), f, acc[5]);
+        acc[6] = fmaf(lo16(w.w), f, acc[6]);
+        acc[7] = fmaf(hi16(w.w), f, acc[7]);
+    }
+#pragma unroll
+    for (int u = 0; u < kJ; ++u) hs[lane + 32 * u] = acc[u] > 0.0f ? acc[u] : 0.0f;
+    __syncwarp();
+    unsigned best_key = 0;
+    int best_n = INT_MAX;
+    bool any = false;
+    const float4* h4 = reinterpret_cast<const float4*>(hs);
+#pragma unroll
+    for (int i = 0; i < NPL; ++i) {
+        const int n = lane + 32 * i;
+        if (n < N && S[i] > 0) {
+            float s = __ldg(p.b2f + n);
+#pragma unroll 4
+            for (int q = 0; q < kHidden / 8; ++q) {  // hidden units 8q .. 8q+7, in order
+                const uint4 w = wld4<SMEMW>(W2p + q * N + n);
+                const float4 ha = h4[2 * q], hb = h4[2 * q + 1];
+                s = fmaf(lo16(w.x), ha.x, s);
+                s = fmaf(hi16(w.x), ha.y, s);
+                s = fmaf(lo16(w.y), ha.z, s);
+                s = fmaf(hi16(w.y), ha.w, s);
+                s = fmaf(lo16(w.z), hb.x, s);
+                s = fmaf(hi16(w.z), hb.y, s);
+                s = fmaf(lo16(w.w), hb.z, s);
+                s = fmaf(hi16(w.w), hb.w, s);
+            }
+            if (p.gumbel) s = __fadd_rn(s, gumbel1(p.seed, p.traj, t, n));
+            const unsigned kk = ord_key(s);
+            if (!any || kk > best_key) { best_key = kk; best_n = n; any = true; }
+        }
+    }
+    __syncwarp();  // fs / hs reused by the next call
+    const unsigned kmax = __reduce_max_sync(kFull, any ? best_key : 0u);
+    const bool stocked = __any_sync(kFull, any);
+    const int n = __reduce_min_sync(kFull, (any && best_key == kmax) ? best_n : INT_MAX);
+    return stocked ? n : -1;
+}
+
+// Bytes of the packed weights (W1p then W2p).
+__host__ __device__ __forceinline__ size_t packed_weight_bytes(int N) {
+    return (size_t)2 * N * kHidden * sizeof(uint16_t);
+}
+
+// Copy the packed weights (W1p, then W2p) into shared memory.
+__device__ __forceinline__ void stage_weights(const MlpPolicy& p, uint4* sw) {
+    const int half = p.N * kHidden / 8;  // uint4 per packed matrix
+    for (int i = threadIdx.x; i < 2 * half; i += blockDim.x)
+        sw[i] = i < half ? p.W1p[i] : p.W2p[i - half];
+    __syncthreads();
+}
+
+// Sequential simulation on one warp: orders strictly one at a time (time t
+// counts from 0 within prod/reg/act_t).
+template <int NPL, bool SMEMW>
+__device__ __forceinline__ void seq_mlp_body(int T, int N, const int32_t* __restrict__ prod,
+                                             const int32_t* __restrict__ reg, int32_t* xw,
+                                             int8_t* __restrict__ act_t, const MlpPolicy& p,
+                                             const uint4* W1p, const uint4* W2p, float* fs,
+                                             float* hs) {
+    const int lane = lane_id();
+    int my_act = -1;
+    for (int t = 0; t < T; ++t) {
+        const int k = __ldg(prod + t), r = __ldg(reg + t);
+        int S[NPL];
+#pragma unroll
+        for (int i = 0; i < NPL; ++i) {
+            const int n = lane + 32 * i;
+            S[i] = n < N ? xw[(size_t)k * N + n] : 0;
+        }
+        const int act = mlp_decide<NPL, SMEMW>(p, W1p, W2p, S, r, t, fs, hs);
+#pragma unroll
+        for (int i = 0; i < NPL; ++i)
+            if (act == lane + 32 * i) xw[(size_t)k * N + act] = S[i] - 1;
+        if (lane == (t & 31)) my_act = act;
+        if ((t & 31) == 31 || t == T - 1) {
+            const int tw = (t & ~31) + lane;
+            if (tw < T) act_t[tw] = (int8_t)my_act;
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------- Picard, one warp per segment
+template <int NPL, bool SMEMW>
+__device__ bool replay_segment_mlp(const KArgs& a, const MlpPolicy& p, const uint4* W1p,
+                                   const uint4* W2p, const int32_t* __restrict__ perm, int s,
+                                   const SegMeta& m, int fcp, int* fc_cur, int it, int t_off,
+                                   unsigned long long& calls, float* fs, float* hs) {
+    const int lane = lane_id();
+    const int N = a.N, NP = a.NP;
+    const int k = m.k;
+    int D[NPL], x0v[NPL], S[NPL], S0[NPL], hist[NPL], corr[NPL];
+    // prefix counts of earlier segments; none before pass 1 of an all-a^phi cache
+    const bool chained = m.ce - m.cf > 1 && (it > 1 || a.first_dirty);
+#pragma unroll
+    for (int i = 0; i < NPL; ++i) {
+        const int n = lane + 32 * i;
+        x0v[i] = n < N ? a.x0[(size_t)k * N + n] : 0;
+        D[i] = chained ? a.carry[(size_t)s * NP + n] : 0;
+        S[i] = max(0, x0v[i] - D[i]);
+        S0[i] = S[i];
+        hist[i] = 0;
+        corr[i] = 0;
+    }
+    int r = m.r0;
+    int next_run = a.run_start[r + 1];
+    bool eval = m.j0 > fcp;
+    unsigned long long evals = 0;
+    int first_chg = INT_MAX;
+    for (int base = m.j0; base < m.jend; base += 32) {
+        const int cnt = min(32, m.jend - base);
+        const int my_reg = lane < cnt ? a.reg_s[base + lane] : 0;
+        const int my_old = lane < cnt ? a.alpha_s[base + lane] : -1;
+        const int my_t = lane < cnt ? perm[base + lane] - t_off : 0;  // time within the trajectory
+        int my_new = my_old;
+        for (int q = 0; q < cnt; ++q) {
+            if (base + q == next_run) {
+#pragma unroll
+                for (int i = 0; i < NPL; ++i) {
+                    hist[i] += S0[i] - S[i];
+                    D[i] += S0[i] - S[i] + corr[i];
+                    corr[i] = 0;
+                    S[i] = max(0, x0v[i] - D[i]);
+                    S0[i] = S[i];
+                }
+                eval = next_run > fcp;
+                ++r;
+                next_run = a.run_start[r + 1];
+            }
+            const int rr = __shfl_sync(kFull, my_reg, q);
+            const int ao = __shfl_sync(kFull, my_old, q);
+            const int tt = __shfl_sync(kFull, my_t, q);
+            int act = ao;
+            if (eval) {
+                act = mlp_decide<NPL, SMEMW>(p, W1p, W2p, S, rr, tt, fs, hs);
+                ++evals;
+            }
+#pragma unroll
+            for (int i = 0; i < NPL; ++i) S[i] -= (act == lane + 32 * i);
+            if (act != ao) {
+#pragma unroll
+                for (int i = 0; i < NPL; ++i) corr[i] += (ao == lane + 32 * i) - (act == lane + 32 * i);
+            }
+            if (lane == q) my_new = act;
+        }
+        if (lane < cnt) a.alpha_s[base + lane] = (int8_t)my_new;
+        const unsigned chg = __ballot_sync(kFull, lane < cnt && my_new != my_old);
+        if (chg && first_chg == INT_MAX) first_chg = base + __ffs(chg) - 1;
+    }
+#pragma unroll
+    for (int i = 0; i < NPL; ++i) {
+        hist[i] += S0[i] - S[i];
+        a.agg[(size_t)s * NP + lane + 32 * i] = hist[i];
+    }
+    if (lane == 0 && first_chg != INT_MAX && first_chg < ld_volatile(&fc_cur[k]))
+        atomicMin(&fc_cur[k], first_chg);
+    if (s == m.ce - 1) {
+#pragma unroll
+        for (int i = 0; i < NPL; ++i) {
+            const int n = lane + 32 * i;
+            if (n < N) a.xfin[(size_t)k * N + n] = S[i];
+        }
+    }
+    if (lane == 0) calls += evals;
+    return first_chg != INT_MAX;
+}
+
+
+inline MlpPolicy make_policy_view(const Instance* I, const pic_policy* pol) {
+    MlpPolicy p;
+    p.N = I->N;
+    p.H = kHidden;
+    p.P = I->mlp_P;
+    p.W1p = I->mlp_W1p;
+    p.W2p = I->mlp_W2p;
+    p.b2f = I->mlp_b2;
+    p.gumbel = pol->kind == PIC_POLICY_GUMBEL;
+    p.seed = pol->seed;
+    p.traj = pol->traj;
+    return p;
+}
+
+// Packed weights fit in shared memory next to the kernels' static buffers.
+inline bool smem_weights_ok(int N) { return packed_weight_bytes(N) <= 150 * 1024; }
+
+}  // namespace mlp
+}  // namespace pic

@@ -80,17 +80,19 @@ __device__ __forceinline__ SegMeta smem_meta(const SegMeta* p) {
 
 constexpr int kMaxWarpsPerCta = 32;
 
-// Look-back words carry their pass in the high half: (pass << 32) | value, so a
-// reader learns from the word itself whether it was written in this pass.  The
-// poll is a volatile relaxed load so that every spin really re-reads memory.
+// Look-back words carry a tag in the high half: (tag << 32) | value with tag =
+// ctrl->tag_base + pass, unique over the calls on one instance, so a reader
+// learns from the word itself whether it was written in this pass of this call
+// (no clearing between calls).  The poll is a volatile relaxed load so that every spin really
+// re-reads memory.
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
     unsigned long long v;
     asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
-__device__ __forceinline__ unsigned long long tagged(int it, int v) {
-    return ((unsigned long long)(unsigned)it << 32) | (unsigned)v;
+__device__ __forceinline__ unsigned long long tagged(unsigned tag, int v) {
+    return ((unsigned long long)tag << 32) | (unsigned)v;
 }
 
 // Phase S for one super-block (head segment s of a chain whose product changed):
@@ -103,18 +105,21 @@ __device__ __forceinline__ unsigned long long tagged(int it, int v) {
 // recorded and the pass is abandoned at the next grid barrier.
 template <int NPL>
 __device__ __forceinline__ void superblock_prefix(const KArgs& a, int s, const SegMeta& m, int it,
-                                                  int fcp, unsigned long long deadline) {
+                                                  unsigned tag, int fcp,
+                                                  unsigned long long deadline) {
     const int lane = lane_id();
     const int NP = a.NP;
     const int send = min(s + kSuperBlock, m.ce);
     constexpr int kRows = 8 / NPL;  // rows per round trip
-    if (send < m.ce && it > 1) {
+    // the shortcut needs last pass's prefixes: pass 1 computes none unless the
+    // cache started from alpha_init
+    if (send < m.ce && (it > 2 || (it == 2 && a.first_dirty))) {
         const int next_j0 = __ldg(&a.meta[send].j0);
         if (next_j0 <= fcp) {  // clean: aggregates and prefixes unchanged
 #pragma unroll
             for (int i = 0; i < NPL; ++i) {
                 const size_t o = (size_t)s * NP + lane + 32 * i;
-                a.sbincl[o] = tagged(it, (int)(unsigned)a.sbincl[o]);
+                a.sbincl[o] = tagged(tag, (int)(unsigned)a.sbincl[o]);
             }
             return;
         }
@@ -139,7 +144,7 @@ __device__ __forceinline__ void superblock_prefix(const KArgs& a, int s, const S
     for (int i = 0; i < NPL; ++i) acc[i] = 0;
     if (s > m.cf) {
 #pragma unroll
-        for (int i = 0; i < NPL; ++i) a.sbagg[(size_t)s * NP + lane + 32 * i] = tagged(it, tot[i]);
+        for (int i = 0; i < NPL; ++i) a.sbagg[(size_t)s * NP + lane + 32 * i] = tagged(tag, tot[i]);
         bool fail = false;
         for (int p = s - kSuperBlock; p >= m.cf && !fail; p -= kSuperBlock) {
             while (true) {
@@ -152,8 +157,8 @@ __device__ __forceinline__ void superblock_prefix(const KArgs& a, int s, const S
                 bool inc_ok = true, agg_ok = true;
 #pragma unroll
                 for (int i = 0; i < NPL; ++i) {
-                    inc_ok &= (int)(wi[i] >> 32) == it;
-                    agg_ok &= (int)(wa[i] >> 32) == it;
+                    inc_ok &= (unsigned)(wi[i] >> 32) == tag;
+                    agg_ok &= (unsigned)(wa[i] >> 32) == tag;
                 }
                 if (__all_sync(kFull, inc_ok)) {
 #pragma unroll
@@ -178,7 +183,7 @@ __device__ __forceinline__ void superblock_prefix(const KArgs& a, int s, const S
     }
 #pragma unroll
     for (int i = 0; i < NPL; ++i)
-        a.sbincl[(size_t)s * NP + lane + 32 * i] = tagged(it, acc[i] + tot[i]);
+        a.sbincl[(size_t)s * NP + lane + 32 * i] = tagged(tag, acc[i] + tot[i]);
     for (int s2 = s; s2 < send; s2 += kRows) {
         int v[kRows][NPL];
 #pragma unroll
@@ -196,6 +201,130 @@ __device__ __forceinline__ void superblock_prefix(const KArgs& a, int s, const S
     }
 }
 
+
+// Algorithm 1's passes inside one persistent cooperative launch; every thread
+// of the grid calls this.  Each pass:
+//   phase S  chain prefixes of the per-segment histograms of cached actions
+//            (superblock_prefix, one warp per super-block head of a chain whose
+//            product changed in the previous pass);
+//   phase R  active segments replayed, one warp each: positions of the
+//            longest-first order are dealt to warps in a snake (w, 2W-1-w,
+//            2W+w, ...), examined 32 at a time per warp, and
+//            replay(seg, meta, fcp, fc_cur, it) replays one of them and returns
+//            whether it changed a cached action (warp-uniform; it adds its
+//            policy calls to `calls` on lane 0);
+// separated by grid barriers.  The loop ends at the first pass that changes no
+// cached action (line 13 of Algorithm 1), or after max_iters passes.
+template <int NPL, int WARPS, class Replay>
+__device__ __forceinline__ void picard_passes(const KArgs& a, unsigned long long& calls,
+                                              Replay&& replay) {
+    __shared__ int s_changed;
+    // per warp: the 32 segments it is examining (metadata, previous-pass first change)
+    __shared__ SegMeta s_meta[WARPS][32];
+    __shared__ int s_fcp[WARPS][32];
+    const int lane = lane_id();
+    const int wib = threadIdx.x >> 5;
+    const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int gthreads = gridDim.x * blockDim.x;
+    const unsigned long long deadline = globaltimer_ns() + a.timeout_ns;
+    const int nseg = a.ctrl->nseg;
+    const bool no_reset = (a.flags & PIC_FLAG_NO_RESET) != 0;
+    const unsigned tag_base = ld_volatile(&a.ctrl->tag_base);
+    if (threadIdx.x == 0) s_changed = 0;
+    __syncthreads();
+    unsigned long long replays = 0;
+    const unsigned long long t_start = globaltimer_ns();
+    int it = 1;
+    bool ok = true, converged = false;
+    for (; it <= a.max_iters; ++it) {
+        const int parity = it & 1;
+        long long* tr = (a.trace && it <= kTraceCap) ? a.trace + 4 * (it - 1) : nullptr;
+        const unsigned long long calls0 = calls, replays0 = replays;
+        const int* fc_prev = a.fc + (size_t)(parity ^ 1) * a.K;
+        int* fc_cur = a.fc + (size_t)parity * a.K;
+        // ---- phase S: this warp's segments gwarp + j * nwarps, 32 at a time
+        for (int k = gtid; k < a.K; k += gthreads) fc_cur[k] = INT_MAX;
+        if (gtid == 0) a.ctrl->changed[parity] = 0;
+        if (it > 1 || a.first_dirty) {
+            for (int j0 = 0; gwarp + j0 * nwarps < nseg; j0 += 32) {
+                const int sl = gwarp + (j0 + lane) * nwarps;
+                bool head = false;
+                if (sl < nseg) {
+                    const SegMeta m = load_meta(a.meta + sl);
+                    head = m.ce - m.cf > 1 && (sl - m.cf) % kSuperBlock == 0;
+                    const int f = it > 1 ? fc_prev[m.k] : -1;
+                    if (head && it > 1) head = f != INT_MAX;
+                    if (head) {
+                        s_meta[wib][lane] = m;
+                        s_fcp[wib][lane] = f;
+                    }
+                }
+                unsigned todo = __ballot_sync(kFull, head);
+                while (todo) {  // increasing segment order (lane order)
+                    const int src = __ffs(todo) - 1;
+                    todo &= todo - 1;
+                    const SegMeta mm = smem_meta(&s_meta[wib][src]);
+                    superblock_prefix<NPL>(a, gwarp + (j0 + src) * nwarps, mm, it,
+                                           tag_base + (unsigned)it, s_fcp[wib][src], deadline);
+                }
+                __syncwarp();
+            }
+        }
+        if (!grid_sync(a.ctrl, deadline)) { ok = false; break; }
+        if (tr && gtid == 0) tr[0] = (long long)(globaltimer_ns() - t_start);
+        // ---- phase R
+        bool chg = false;
+        for (int j0 = 0; j0 * nwarps < nseg; j0 += 32) {
+            const int j = j0 + lane;
+            const int pos = j * nwarps + ((j & 1) ? nwarps - 1 - gwarp : gwarp);
+            int sl = nseg;
+            bool act = false;
+            if (pos < nseg) {
+                sl = a.lpt[pos];
+                const SegMeta m = load_meta(a.meta + sl);
+                const int fcp = no_reset ? -1 : fc_prev[m.k];
+                act = m.last_start > fcp;  // some run starts after the first change
+                if (act) {
+                    s_meta[wib][lane] = m;
+                    s_fcp[wib][lane] = fcp;
+                }
+            }
+            unsigned todo = __ballot_sync(kFull, act);
+            while (todo) {
+                const int src = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const SegMeta mm = smem_meta(&s_meta[wib][src]);
+                const int seg = __shfl_sync(kFull, sl, src);
+                chg |= replay(seg, mm, s_fcp[wib][src], fc_cur, it);
+                replays += 1;
+            }
+            __syncwarp();
+        }
+        if (tr && lane == 0 && replays != replays0) {
+            atomicAdd((unsigned long long*)&tr[2], calls - calls0);
+            atomicAdd((unsigned long long*)&tr[3], replays - replays0);
+        }
+        if (chg && lane == 0) s_changed = 1;  // one global write per CTA, below
+        __syncthreads();
+        if (threadIdx.x == 0 && s_changed) {
+            a.ctrl->changed[parity] = 1;
+            s_changed = 0;
+        }
+        if (!grid_sync(a.ctrl, deadline)) { ok = false; break; }
+        if (tr && gtid == 0) tr[1] = (long long)(globaltimer_ns() - t_start);
+        if (ld_volatile(&a.ctrl->changed[parity]) == 0) { converged = true; break; }
+    }
+    if (lane == 0 && replays) {
+        atomicAdd(&a.ctrl->policy_calls, calls);
+        atomicAdd(&a.ctrl->seg_replays, replays);
+    }
+    if (gtid == 0 && ok) {
+        a.ctrl->iters = converged ? it : a.max_iters;
+        a.ctrl->converged = converged ? 1 : 0;
+    }
+}
 
 }  // namespace picard
 

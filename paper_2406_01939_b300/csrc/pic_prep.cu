@@ -12,6 +12,7 @@
 //             window of W sorted positions of that product (the unit one warp
 //             replays), chain = all segments of one product.
 // Everything here is rebuilt from the raw order stream on the device.
+#include <cstddef>
 #include <cstdio>
 
 #include "pic_device.cuh"
@@ -178,16 +179,29 @@ __global__ void k_pstart(const int32_t* __restrict__ prod_s, int T, int K, int32
 }
 
 // Region gather and run-start flags: a run starts where the product or the
-// chunk (t / L) changes between consecutive sorted positions.
+// chunk changes between consecutive sorted positions.  The chunk of order t is
+// t / L, or, in a batch, (t - toff[b]) / chunk_len[b] for the trajectory b that
+// owns the product (consecutive positions of one product share b).
 __global__ void k_run_flags(const int32_t* __restrict__ perm, const int32_t* __restrict__ prod_s,
                             const int32_t* __restrict__ reg, int32_t* __restrict__ reg_s, int T,
-                            int L, int32_t* __restrict__ flag) {
+                            int L, const int32_t* __restrict__ traj_of_prod,
+                            const int32_t* __restrict__ toff, const int32_t* __restrict__ chunk_len,
+                            int32_t* __restrict__ flag) {
     long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= T) return;
     int t = perm[j];
     reg_s[j] = reg[t];
     int f = 1;
-    if (j > 0) f = (prod_s[j] != prod_s[j - 1]) || (t / L != perm[j - 1] / L);
+    if (j > 0 && prod_s[j] == prod_s[j - 1]) {
+        int tp = perm[j - 1], len = L;
+        if (traj_of_prod) {
+            const int b = traj_of_prod[prod_s[j]];
+            t -= toff[b];
+            tp -= toff[b];
+            len = chunk_len[b];
+        }
+        f = t / len != tp / len;
+    }
     flag[j] = f;
 }
 
@@ -265,25 +279,46 @@ __global__ void k_chains(const int32_t* __restrict__ seg_prod, const int32_t* __
     meta[s] = m;
 }
 
-// Longest-first order of the segments (counting sort on min(length, 1023),
-// descending; order inside a bucket is arbitrary).  Warps take segments from
-// this order so that the long ones start first and the work evens out.
-__global__ void k_len_hist(const SegMeta* __restrict__ meta, const Ctrl* ctrl, int32_t* hist) {
+// Longest-first order of the segments: a counting sort, descending, on a
+// bucket of the estimated work w = length (x mlp_weight for a segment of an MLP
+// trajectory of a batch); order inside a bucket is arbitrary.  Buckets are
+// exact below 32 and keep the leading 6 bits above (w = 1.m * 2^e with 5
+// mantissa bits), so every 32-bit work value has one of fewer than 1024
+// buckets.  Warps take segments from this order so that the long ones start
+// first and the work evens out.
+__device__ __forceinline__ int work_bucket(const SegMeta& m, const int32_t* __restrict__ traj_of_prod,
+                                           const BatchPol* __restrict__ pol, int mlp_weight) {
+    long long w = m.jend - m.j0;
+    if (pol && pol[traj_of_prod[m.k]].kind >= PIC_POLICY_MLP) w *= mlp_weight;
+    const unsigned v = (unsigned)min(w, 0x7FFFFFFFll);
+    int key = (int)v;
+    if (v >= 32) {
+        const int e = 31 - __clz(v);
+        key = (e - 4) * 32 + (int)((v >> (e - 5)) & 31);
+    }
+    return kLenBuckets - 1 - key;
+}
+
+__global__ void k_len_hist(const SegMeta* __restrict__ meta, const Ctrl* ctrl,
+                           const int32_t* __restrict__ traj_of_prod, const BatchPol* __restrict__ pol,
+                           int mlp_weight, int32_t* hist) {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = s < ctrl->nseg;
     int b = -1 - (int)(threadIdx.x & 31);
-    if (valid) b = kLenBuckets - 1 - min(meta[s].jend - meta[s].j0, kLenBuckets - 1);
+    if (valid) b = work_bucket(meta[s], traj_of_prod, pol, mlp_weight);
     const unsigned peers = __match_any_sync(kFull, b);
     if (valid && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) atomicAdd(&hist[b], __popc(peers));
 }
 
-__global__ void k_len_scatter(const SegMeta* __restrict__ meta, const Ctrl* ctrl, int32_t* offs,
+__global__ void k_len_scatter(const SegMeta* __restrict__ meta, const Ctrl* ctrl,
+                              const int32_t* __restrict__ traj_of_prod,
+                              const BatchPol* __restrict__ pol, int mlp_weight, int32_t* offs,
                               int32_t* __restrict__ lpt) {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = s < ctrl->nseg;
     const int lane = threadIdx.x & 31;
     int b = -1 - lane;
-    if (valid) b = kLenBuckets - 1 - min(meta[s].jend - meta[s].j0, kLenBuckets - 1);
+    if (valid) b = work_bucket(meta[s], traj_of_prod, pol, mlp_weight);
     const unsigned peers = __match_any_sync(kFull, b);
     const int leader = __ffs(peers) - 1;
     int base = 0;
@@ -334,37 +369,39 @@ cudaError_t scan_exclusive(const int32_t* in, int32_t* out, int n, int32_t* tota
 cudaError_t build_tables(Instance* I, int M, int W, cudaStream_t st) {
     const int T = I->T, K = I->K;
     cudaError_t e;
-    if (T == 0) {
-        e = cudaMemsetAsync(I->ctrl, 0, sizeof(Ctrl), st);
-        return e;
-    }
+    if (T == 0) return cudaMemsetAsync(I->ctrl, 0, offsetof(Ctrl, tag_base), st);
+    // 1. stable sort of (product, time) by product: LSD radix, 8-bit digits, as
+    // many passes as K - 1 has bytes; the passes alternate between (tmp_a,
+    // tmp_b) and (prod_s, perm) so that the last one lands in (prod_s, perm)
+    int passes = 1;
+    while (passes < 4 && ((unsigned)(K - 1) >> (8 * passes)) != 0) ++passes;
     // kernel launches made below: per radix pass 2 + a 3-kernel scan; then
     // product offsets, run flags + scan + runs, segment flags + scan +
     // segments + chains
-    I->launches += (K <= 256 ? 1 : 2) * 5 + 1 + 5 + 6 + 5;
-    // 1. stable sort of (product, time) by product: LSD radix, 8-bit digits
+    I->launches += passes * 5 + 1 + 5 + 6;
     const int nblk = nblocks(T, kRadixTile);
-    const int passes = K <= 256 ? 1 : 2;
     const int32_t* kin = I->prod;
     const int32_t* vin = nullptr;
-    int32_t* kout = passes == 2 ? I->tmp_a : I->prod_s;
-    int32_t* vout = passes == 2 ? I->tmp_b : I->perm;
     for (int p = 0; p < passes; ++p) {
+        const bool last_side = ((passes - 1 - p) & 1) == 0;
+        int32_t* kout = last_side ? I->prod_s : I->tmp_a;
+        int32_t* vout = last_side ? I->perm : I->tmp_b;
         const int shift = 8 * p;
         k_radix_hist<<<nblk, kRadixThreads, 0, st>>>(kin, T, shift, I->hist, nblk);
         if ((e = scan_exclusive(I->hist, I->hist, 256 * nblk, nullptr, I->scan_blk, st))) return e;
         k_radix_scatter<<<nblk, kRadixThreads, 0, st>>>(kin, vin, T, shift, I->hist, nblk, kout, vout);
         kin = kout;
         vin = vout;
-        kout = I->prod_s;
-        vout = I->perm;
     }
     // 2. first sorted position of every product
     k_pstart<<<nblocks(K + 1, 256), 256, 0, st>>>(I->prod_s, T, K, I->pstart);
     // 3. runs for M chunks of L orders
     const long long L = ((long long)T + M - 1) / M;
+    const Batch* bt = I->batch;
     k_run_flags<<<nblocks(T, 256), 256, 0, st>>>(I->perm, I->prod_s, I->reg, I->reg_s, T, (int)L,
-                                                  I->tmp_a);
+                                                  bt ? bt->traj_of_prod : nullptr,
+                                                  bt ? bt->toff : nullptr,
+                                                  bt ? bt->chunk_len : nullptr, I->tmp_a);
     if ((e = scan_exclusive(I->tmp_a, I->tmp_b, T, nullptr, I->scan_blk, st))) return e;
     k_runs<<<nblocks(T, 256), 256, 0, st>>>(I->tmp_a, I->tmp_b, T, I->run_of, I->run_start, I->ctrl);
     // 4. segments (window W per product) and chains
@@ -376,12 +413,23 @@ cudaError_t build_tables(Instance* I, int M, int W, cudaStream_t st) {
     k_chains<<<nblocks(I->smax, 256), 256, 0, st>>>(I->seg_prod, I->seg_run, I->run_start,
                                                      I->pstart, I->run_of, I->seg_of_run, T, I->ctrl,
                                                      I->seg_cf, I->seg_ce, I->seg_meta);
-    // 5. longest-first order of the segments
-    cudaMemsetAsync(I->len_hist, 0, sizeof(int32_t) * kLenBuckets, st);
+    if ((e = cudaGetLastError())) return e;
+    // 5. longest-first order of the segments (a batch rebuilds it per call, as
+    // it depends on the trajectories' policies)
+    return build_lpt(I, nullptr, 1, st);
+}
+
+cudaError_t build_lpt(Instance* I, const BatchPol* pol, int mlp_weight, cudaStream_t st) {
+    if (I->T == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(I->len_hist, 0, sizeof(int32_t) * kLenBuckets, st);
+    if (e) return e;
     const int sb = nblocks(I->smax, 256);
-    k_len_hist<<<sb, 256, 0, st>>>(I->seg_meta, I->ctrl, I->len_hist);
+    const int32_t* top = I->batch ? I->batch->traj_of_prod : nullptr;
+    I->launches += 5;
+    k_len_hist<<<sb, 256, 0, st>>>(I->seg_meta, I->ctrl, top, pol, mlp_weight, I->len_hist);
     if ((e = scan_exclusive(I->len_hist, I->len_hist, kLenBuckets, nullptr, I->scan_blk, st))) return e;
-    k_len_scatter<<<sb, 256, 0, st>>>(I->seg_meta, I->ctrl, I->len_hist, I->seg_lpt);
+    k_len_scatter<<<sb, 256, 0, st>>>(I->seg_meta, I->ctrl, top, pol, mlp_weight, I->len_hist,
+                                      I->seg_lpt);
     return cudaGetLastError();
 }
 
@@ -392,10 +440,17 @@ cudaError_t reduce_costs(Instance* I, const int8_t* alpha, const int32_t* reg, c
     return cudaGetLastError();
 }
 
-cudaError_t finish_outputs(Instance* I, cudaStream_t st) {
+cudaError_t scatter_actions(Instance* I, cudaStream_t st) {
     if (I->T == 0) return cudaSuccess;
     I->launches += 1;
     k_scatter_actions<<<nblocks(I->T, 256), 256, 0, st>>>(I->alpha_s, I->perm, I->T, I->act_t);
+    return cudaGetLastError();
+}
+
+cudaError_t finish_outputs(Instance* I, cudaStream_t st) {
+    if (I->T == 0) return cudaSuccess;
+    cudaError_t e = scatter_actions(I, st);
+    if (e) return e;
     return reduce_costs(I, I->alpha_s, I->reg_s, st);
 }
 

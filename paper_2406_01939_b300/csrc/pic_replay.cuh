@@ -1,0 +1,245 @@
+// The integer fulfilment policies (greedy and bid-price) on one warp: replay of
+// one Picard segment and the sequential simulation, shared by the
+// single-trajectory and batch kernels.
+#pragma once
+
+#include "pic_picard.cuh"
+
+namespace pic {
+namespace picard {
+
+// Replay one segment (all its runs, in order) with one warp.  Lane l owns
+// warehouses l, l+32, ..., l+32(NPL-1).  fcp: first position of product k that
+// changed in the previous pass (-1: every run is evaluated).
+//
+// Per run the state starts at max(0, x0 - D), D = counts of cached actions of
+// this product before the run.  D advances run by run: the run's own new
+// actions (S0 - S at the run's end) plus a correction for the orders whose new
+// action differs from the cached one (rare once the iteration settles).
+template <int NPL, bool DUAL, bool SMEM, bool FULL>
+__device__ __forceinline__ bool replay_segment(const KArgs& a, const CostTable<SMEM>& ct, int s,
+                                               const SegMeta& m, int fcp, int* fc_cur, int it,
+                                               bool use_lam, unsigned long long& calls) {
+    const int lane = lane_id();
+    const int N = a.N, NP = a.NP;
+    const int k = m.k;
+    // key = score * 128 + n (ties to the lowest index); adj = n - 128 * lam[k][n]
+    int D[NPL], x0v[NPL], adj[NPL], S[NPL], S0[NPL], hist[NPL], corr[NPL];
+    // prefix counts from earlier segments of this product (exclusive chain
+    // prefix); none before pass 1 of an all-a^phi cache
+    const bool chained = m.ce - m.cf > 1 && (it > 1 || a.first_dirty);
+#pragma unroll
+    for (int i = 0; i < NPL; ++i) {
+        const int n = lane + 32 * i;
+        const bool in = FULL || n < N;
+        hist[i] = 0;
+        corr[i] = 0;
+        x0v[i] = in ? a.x0[(size_t)k * N + n] : 0;
+        adj[i] = n - ((DUAL && use_lam && in) ? 128 * a.lam[(size_t)k * N + n] : 0);
+        D[i] = chained ? a.carry[(size_t)s * NP + n] : 0;
+    }
+    const int j0 = m.j0, jend = m.jend;
+    // lane i holds the end (= next start) of run rwin + i
+    int rwin = m.r0;
+    int run_end = lane < m.r1 - rwin ? a.run_start[rwin + 1 + lane] : INT_MAX;
+    int r = m.r0;
+    int next_run = __shfl_sync(kFull, run_end, 0);
+    bool eval = j0 > fcp;  // this run's prefix changed in the previous pass
+    unsigned long long evals = eval ? (unsigned long long)(next_run - j0) : 0ull;
+#pragma unroll
+    for (int i = 0; i < NPL; ++i) {
+        S[i] = max(0, x0v[i] - D[i]);
+        S0[i] = S[i];
+    }
+    int first_chg = INT_MAX;
+    int nreg = 0, nold = -1;
+    if (lane < jend - j0) {
+        nreg = a.reg_s[j0 + lane];
+        nold = a.alpha_s[j0 + lane];
+    }
+    for (int base = j0; base < jend; base += 32) {
+        const int cnt = min(32, jend - base);
+        const int my_reg = nreg, my_old = nold;
+        if (base + 32 + lane < jend) {  // prefetch the next batch of orders
+            nreg = a.reg_s[base + 32 + lane];
+            nold = a.alpha_s[base + 32 + lane];
+        }
+        int my_new = my_old;
+        for (int q = 0; q < cnt; ++q) {
+            if (base + q == next_run) {  // close run r, open run r+1
+#pragma unroll
+                for (int i = 0; i < NPL; ++i) {
+                    hist[i] += S0[i] - S[i];
+                    D[i] += S0[i] - S[i] + corr[i];
+                    corr[i] = 0;
+                    S[i] = max(0, x0v[i] - D[i]);
+                    S0[i] = S[i];
+                }
+                ++r;
+                int idx = r - rwin;
+                if (idx == 32) {  // next window of run ends
+                    rwin += 32;
+                    idx = 0;
+                    run_end = lane < m.r1 - rwin ? a.run_start[rwin + 1 + lane] : INT_MAX;
+                }
+                const int nr = __shfl_sync(kFull, run_end, idx);
+                eval = next_run > fcp;
+                if (eval) evals += (unsigned long long)(nr - next_run);
+                next_run = nr;
+            }
+            const int rr = __shfl_sync(kFull, my_reg, q);
+            const int ao = __shfl_sync(kFull, my_old, q);
+            int c[NPL];
+#pragma unroll
+            for (int i = 0; i < NPL; ++i)
+                c[i] = (FULL || lane + 32 * i < N) ? ct.at(rr, lane + 32 * i) : 0;
+            int act = ao;  // unchanged prefix: the cached action is the policy's
+            if (eval) {
+                int key = INT_MAX;
+#pragma unroll
+                for (int i = 0; i < NPL; ++i)
+                    key = min(key, S[i] > 0 ? c[i] * 128 + adj[i] : INT_MAX);
+                const int best = __reduce_min_sync(kFull, key);
+                act = best == INT_MAX ? -1 : (best & 127);
+            }
+#pragma unroll
+            for (int i = 0; i < NPL; ++i) S[i] -= (act == lane + 32 * i);
+            if (act != ao) {  // warp-uniform: the cached action was not the new one
+#pragma unroll
+                for (int i = 0; i < NPL; ++i) {
+                    corr[i] += (ao == lane + 32 * i);
+                    corr[i] -= (act == lane + 32 * i);
+                }
+            }
+            if (lane == q) my_new = act;
+        }
+        if (lane < cnt) a.alpha_s[base + lane] = (int8_t)my_new;
+        const unsigned chg = __ballot_sync(kFull, lane < cnt && my_new != my_old);
+        if (chg && first_chg == INT_MAX) first_chg = base + __ffs(chg) - 1;
+    }
+#pragma unroll
+    for (int i = 0; i < NPL; ++i) {
+        hist[i] += S0[i] - S[i];
+        a.agg[(size_t)s * NP + lane + 32 * i] = hist[i];
+    }
+    if (lane == 0) {
+        // many segments of a popular product change in the same pass: read before
+        // the atomic so that only a new minimum contends for the word
+        if (first_chg != INT_MAX && first_chg < ld_volatile(&fc_cur[k]))
+            atomicMin(&fc_cur[k], first_chg);
+    }
+    if (s == m.ce - 1) {  // last segment of the product: its end state is the final stock
+#pragma unroll
+        for (int i = 0; i < NPL; ++i) {
+            const int n = lane + 32 * i;
+            if (FULL || n < N) a.xfin[(size_t)k * N + n] = S[i];
+        }
+    }
+    calls += evals;
+    return first_chg != INT_MAX;
+}
+
+}  // namespace picard
+
+// Sequential simulation (Sec. 2 definition) on one warp: orders strictly one at
+// a time.  The ids (product, region) of order t + 2*kAhead are fetched at step
+// t; the stock row of order t + kAhead is fetched at step t and corrected, when
+// used, for the decisions of the orders in between that hit the same product.
+// cost_acc (lane-partial) and lost (warp-uniform) accumulate the order costs and
+// a^phi count; lam may be null for the greedy policy.
+constexpr int kAhead = 8;
+
+template <int NPL, bool DUAL, bool SMEM>
+__device__ __forceinline__ void seq_int_body(int T, int N, const int32_t* __restrict__ prod,
+                                             const int32_t* __restrict__ reg,
+                                             const int32_t* __restrict__ cost, const int16_t* s_cost,
+                                             const int32_t* __restrict__ lam, int32_t* xw,
+                                             int8_t* __restrict__ act_t, long long& cost_acc,
+                                             long long& lost) {
+    const int lane = lane_id();
+    // slot p: order t = p (mod kAhead).  ik/ir: ids of order t + kAhead (next
+    // occupant); rk/rr + Srow/Lrow: order t's ids and prefetched rows; dk/da:
+    // product and decision of the order that used the slot last.
+    int Srow[kAhead][NPL], Lrow[kAhead][NPL];
+    int ik[kAhead], ir[kAhead], rk[kAhead], rrg[kAhead], dk[kAhead], da[kAhead];
+#pragma unroll
+    for (int p = 0; p < kAhead; ++p) {
+        rk[p] = p < T ? __ldg(prod + p) : -1;
+        rrg[p] = p < T ? __ldg(reg + p) : 0;
+        ik[p] = p + kAhead < T ? __ldg(prod + p + kAhead) : -1;
+        ir[p] = p + kAhead < T ? __ldg(reg + p + kAhead) : 0;
+        dk[p] = -1;
+        da[p] = -1;
+#pragma unroll
+        for (int i = 0; i < NPL; ++i) {
+            const int n = lane + 32 * i;
+            Srow[p][i] = (rk[p] >= 0 && n < N) ? xw[(size_t)rk[p] * N + n] : 0;
+            Lrow[p][i] = (DUAL && lam && rk[p] >= 0 && n < N) ? __ldg(lam + (size_t)rk[p] * N + n) : 0;
+        }
+    }
+    int my_act = -1;
+    for (int t0 = 0; t0 < T; t0 += kAhead) {
+#pragma unroll
+        for (int p = 0; p < kAhead; ++p) {
+            const int t = t0 + p;
+            if (t < T) {
+                const int k = rk[p];
+                int S[NPL];
+#pragma unroll
+                for (int i = 0; i < NPL; ++i) S[i] = Srow[p][i];
+#pragma unroll
+                for (int d = 1; d < kAhead; ++d) {
+                    const int q = (p - d + kAhead) % kAhead;
+                    if (dk[q] == k) {
+#pragma unroll
+                        for (int i = 0; i < NPL; ++i) S[i] -= (da[q] == lane + 32 * i);
+                    }
+                }
+                int c[NPL];
+#pragma unroll
+                for (int i = 0; i < NPL; ++i) {
+                    const int n = lane + 32 * i;
+                    c[i] = n < N ? (SMEM ? (int)s_cost[rrg[p] * N + n]
+                                         : __ldg(cost + (size_t)rrg[p] * N + n))
+                                 : 0;
+                }
+                int key = INT_MAX;
+#pragma unroll
+                for (int i = 0; i < NPL; ++i)
+                    key = min(key, S[i] > 0 ? (c[i] - Lrow[p][i]) * 128 + lane + 32 * i : INT_MAX);
+                const int best = __reduce_min_sync(kFull, key);
+                const int act = best == INT_MAX ? -1 : (best & 127);
+#pragma unroll
+                for (int i = 0; i < NPL; ++i) {
+                    if (act == lane + 32 * i) {
+                        xw[(size_t)k * N + lane + 32 * i] = S[i] - 1;
+                        cost_acc += c[i];
+                    }
+                }
+                lost += act < 0;
+                dk[p] = k;
+                da[p] = act;
+                if (lane == (t & 31)) my_act = act;
+                if ((t & 31) == 31 || t == T - 1) {
+                    const int tw = (t & ~31) + lane;
+                    if (tw < T) act_t[tw] = (int8_t)my_act;
+                }
+                // this slot now takes order t + kAhead: row read after the store above
+                const int nk = ik[p];
+                rk[p] = nk;
+                rrg[p] = ir[p];
+#pragma unroll
+                for (int i = 0; i < NPL; ++i) {
+                    const int n = lane + 32 * i;
+                    Srow[p][i] = (nk >= 0 && n < N) ? xw[(size_t)nk * N + n] : 0;
+                    Lrow[p][i] = (DUAL && lam && nk >= 0 && n < N) ? __ldg(lam + (size_t)nk * N + n) : 0;
+                }
+                const int t2 = t + 2 * kAhead;
+                ik[p] = t2 < T ? __ldg(prod + t2) : -1;
+                ir[p] = t2 < T ? __ldg(reg + t2) : 0;
+            }
+        }
+    }
+}
+
+}  // namespace pic

@@ -6,8 +6,9 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from . import (PIC_MEM_DEVICE, PIC_MEM_HOST, make_desc, make_opts, make_policy, pic_create_instance,
-               pic_destroy_instance, pic_instance_load, pic_simulate)
+from . import (PIC_MEM_DEVICE, PIC_MEM_HOST, make_desc, make_opts, make_policy, pic_create_batch,
+               pic_create_instance, pic_destroy_instance, pic_instance_load, pic_simulate,
+               pic_simulate_batch)
 
 
 def _dev(a, device):
@@ -84,7 +85,106 @@ class DeviceInstance:
                 "lost": res.lost, "iters": res.iters, "policy_calls": res.policy_calls,
                 "num_chunks": res.num_chunks, "rescored": res.rescored,
                 "seg_replays": res.seg_replays, "launches": res.launches, "prep_ms": res.prep_ms,
-                "sim_ms": res.sim_ms, "total_ms": res.total_ms}
+                "sim_ms": res.sim_ms, "total_ms": res.total_ms, "seg_window": res.seg_window,
+                "cta_threads": res.cta_threads, "ctas_per_sm": res.ctas_per_sm}
+
+    def close(self):
+        if self.handle:
+            pic_destroy_instance(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class DeviceBatch:
+    """A batch of trajectories (list of synth.Instance, same N) as one library
+    batch instance.  Outputs of ``simulate`` are concatenated in trajectory
+    order; ``offsets`` gives each trajectory's first order."""
+
+    def __init__(self, insts, device="cuda", stream=None, mem=PIC_MEM_DEVICE):
+        self.insts = list(insts)
+        self.device = device
+        self.stream = stream
+        self.T = int(sum(i.T for i in self.insts))
+        self.K = int(sum(i.K for i in self.insts))
+        self.N = int(self.insts[0].N)
+        self.offsets = np.concatenate([[0], np.cumsum([i.T for i in self.insts])]).astype(np.int64)
+        self.koffsets = np.concatenate([[0], np.cumsum([i.K for i in self.insts])]).astype(np.int64)
+        keep, descs = [], []
+        for i in self.insts:
+            if mem == PIC_MEM_DEVICE:
+                a = {k: _dev(getattr(i, k).astype(np.int32), device) for k in ("prod", "reg", "x0", "cost")}
+                a["lam"] = None if i.lam is None else _dev(i.lam.astype(np.int32), device)
+            else:
+                a = {k: np.ascontiguousarray(getattr(i, k), dtype=np.int32)
+                     for k in ("prod", "reg", "x0", "cost")}
+                a["lam"] = None if i.lam is None else np.ascontiguousarray(i.lam, dtype=np.int32)
+            keep.append(a)
+            descs.append(make_desc(i.T, i.N, i.K, i.R, a["prod"], a["reg"], a["x0"], a["cost"],
+                                   a["lam"], mem=mem, stream=stream))
+        self.handle = pic_create_batch(descs)
+        del keep  # the batch holds its own device copies
+
+    def simulate(self, policies, mode="picard", num_chunks=0, max_iters=0, flags=0, alpha_init=None,
+                 timeout_ns=0, seg_window=0, want_stock=True, raise_on_error=True, out=None,
+                 trace=None, out_mem=PIC_MEM_DEVICE):
+        """policies: list of synth.Policy or DevicePolicy, one per trajectory (MLP
+        kinds must share one parameter set: pass the same DevicePolicy object or
+        Policies holding the same MLPParams object)."""
+        dps, cache = [], {}
+        for p in policies:
+            if isinstance(p, DevicePolicy):
+                dps.append(p)
+                continue
+            key = id(p.mlp) if p.mlp is not None else None
+            if key is not None and key in cache:
+                base = cache[key]
+            else:
+                base = DevicePolicy(p, self.device)
+                if key is not None:
+                    cache[key] = base
+            dp = DevicePolicy.__new__(DevicePolicy)
+            dp.kind, dp.tensors, dp.hidden = p.kind, base.tensors, base.hidden
+            dp.struct = make_policy(p.kind, hidden=dp.hidden, seed=p.seed, traj=p.traj, **dp.tensors)
+            dps.append(dp)
+        host = out_mem == PIC_MEM_HOST
+        if out is not None:
+            act = out
+        elif host:
+            act = np.empty(self.T, np.int8)
+        else:
+            act = torch.empty(self.T, dtype=torch.int8, device=self.device)
+        stock = None
+        if want_stock:
+            stock = (np.empty((self.K, self.N), np.int32) if host else
+                     torch.empty((self.K, self.N), dtype=torch.int32, device=self.device))
+        ai = None
+        if alpha_init is not None:
+            ai = alpha_init if torch.is_tensor(alpha_init) else \
+                torch.as_tensor(np.ascontiguousarray(alpha_init, dtype=np.int8)).to(self.device)
+        opts = make_opts(mode, num_chunks, max_iters, flags, ai, timeout_ns, out_mem, seg_window,
+                         self.stream, trace)
+        st, res, traj = pic_simulate_batch(self.handle, [d.struct for d in dps], opts, act, stock,
+                                           raise_on_error)
+        return {"status": st, "actions": act, "final_stock": stock, "total_cost": res.total_cost,
+                "lost": res.lost, "iters": res.iters, "policy_calls": res.policy_calls,
+                "num_chunks": res.num_chunks, "seg_window": res.seg_window,
+                "cta_threads": res.cta_threads, "ctas_per_sm": res.ctas_per_sm,
+                "seg_replays": res.seg_replays, "launches": res.launches, "prep_ms": res.prep_ms,
+                "sim_ms": res.sim_ms, "total_ms": res.total_ms,
+                "traj": [{"total_cost": t.total_cost, "lost": t.lost, "iters": t.iters,
+                          "converged": t.converged} for t in traj]}
+
+    def split(self, arr):
+        """Per-trajectory views of a concatenated action array."""
+        return [arr[self.offsets[b]:self.offsets[b + 1]] for b in range(len(self.insts))]
+
+    def split_stock(self, arr):
+        return [arr[self.koffsets[b]:self.koffsets[b + 1]] for b in range(len(self.insts))]
 
     def close(self):
         if self.handle:

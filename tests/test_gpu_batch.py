@@ -1,0 +1,185 @@
+"""Batched simulation (pic_create_batch / pic_simulate_batch) on the GPU against
+the CPU oracle, trajectory by trajectory: actions, final stock, cost, a^phi
+count and each trajectory's own Picard pass count must be identical to what the
+oracle computes for that trajectory alone with the same chunk count."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2406_01939_b300 as pic
+from paper_2406_01939_b300 import synth
+from paper_2406_01939_b300.session import DeviceBatch
+from paper_2406_01939_b300.synth import Policy
+
+pytestmark = pytest.mark.gpu
+
+KINDS = ("greedy", "dual", "mlp", "gumbel")
+
+
+def mixed_batch(seed, Ts, N, K=12, R=9, kinds=KINDS):
+    """Trajectories with their own sizes, stock and tables; policies cycle
+    through `kinds`; one MLP parameter set (E has R rows: every trajectory uses
+    the same R)."""
+    rng = np.random.default_rng(seed)
+    mlp = synth.make_mlp(N, R, seed=seed)
+    insts, pols = [], []
+    for b, T in enumerate(Ts):
+        Kb = int(rng.integers(1, K + 1))
+        inst = synth.make_instance(int(T), N, Kb, R, seed=1000 * seed + b, stock="poisson",
+                                   fill=0.9, with_lam=True)
+        kind = kinds[b % len(kinds)]
+        insts.append(inst)
+        pols.append(Policy(kind, mlp=mlp if kind in ("mlp", "gumbel") else None,
+                           seed=77 + b, traj=b))
+    return insts, pols
+
+
+def check_against_oracle(db, insts, pols, got, M=None):
+    acts = got["actions"]
+    acts = acts.cpu().numpy() if torch.is_tensor(acts) else acts
+    stock = got["final_stock"]
+    stock = stock.cpu().numpy() if torch.is_tensor(stock) else stock
+    tot_c = tot_l = 0
+    for b, (inst, pol) in enumerate(zip(insts, pols)):
+        want = oracle.seq_sim(inst, pol)
+        np.testing.assert_array_equal(db.split(acts)[b], want["actions"], err_msg=f"traj {b}")
+        np.testing.assert_array_equal(db.split_stock(stock)[b], want["x_final"], err_msg=f"traj {b}")
+        tr = got["traj"][b]
+        assert tr["total_cost"] == want["total_cost"] and tr["lost"] == want["lost"], b
+        assert tr["converged"] == 1
+        if M is not None and inst.T > 0:
+            assert tr["iters"] == oracle.picard_chunked(inst, pol, M)["iters"], b
+        tot_c += want["total_cost"]
+        tot_l += want["lost"]
+    assert got["total_cost"] == tot_c and got["lost"] == tot_l
+
+
+@pytest.mark.parametrize("N", [8, 32, 33])
+def test_batch_mixed_policies_match_oracle(N):
+    Ts = [0, 1, 37, 300, 1000, 1500, 64, 777, 2000]
+    insts, pols = mixed_batch(N, Ts, N)
+    db = DeviceBatch(insts)
+    for M in (1, 7, 40):
+        got = db.simulate(pols, "picard", num_chunks=M)
+        check_against_oracle(db, insts, pols, got, M)
+        assert got["iters"] == max(t["iters"] for t in got["traj"])
+
+
+def test_batch_sequential_mode_matches_oracle():
+    insts, pols = mixed_batch(5, [500, 3, 1200, 0, 900, 250, 1800], 16)
+    db = DeviceBatch(insts)
+    got = db.simulate(pols, "sequential")
+    check_against_oracle(db, insts, pols, got)
+    assert all(t["iters"] == 1 for t in got["traj"])
+
+
+def test_batch_iterates_equal_oracle_iterates():
+    """With max_iters = k every trajectory's cache equals the oracle's alpha^k."""
+    insts, pols = mixed_batch(11, [400, 900, 650, 1200], 8)
+    db = DeviceBatch(insts)
+    M = 12
+    want = [oracle.picard_chunked(i, p, M, record=True) for i, p in zip(insts, pols)]
+    for k in (1, 2, 3, 5):
+        got = db.simulate(pols, "picard", num_chunks=M, max_iters=k, raise_on_error=False)
+        a = got["actions"].cpu().numpy()
+        for b in range(len(insts)):
+            kk = min(k, want[b]["iters"])
+            np.testing.assert_array_equal(db.split(a)[b], want[b]["iterates"][kk - 1],
+                                          err_msg=f"traj {b} pass {k}")
+
+
+def test_batch_graph_relaunch_and_policy_change():
+    """PIC_FLAG_GRAPH: the captured graph is relaunched with new per-trajectory
+    policies (kinds, seeds) and still gives the oracle's paths."""
+    insts, pols = mixed_batch(3, [800, 1300, 500, 950, 1100, 60], 24)
+    db = DeviceBatch(insts)
+    M = 16
+    flags = pic.PIC_FLAG_GRAPH | pic.PIC_FLAG_TIMING
+    g1 = db.simulate(pols, "picard", num_chunks=M, flags=flags)
+    check_against_oracle(db, insts, pols, g1, M)
+    g2 = db.simulate(pols, "picard", num_chunks=M, flags=flags)  # relaunch, tables kept
+    g2b = db.simulate(pols, "picard", num_chunks=M, flags=flags)
+    assert torch.equal(g1["actions"], g2["actions"]) and torch.equal(g1["actions"], g2b["actions"])
+    assert g2["launches"] == g2b["launches"] < g1["launches"]  # g1 also built the tables
+    assert g1["iters"] == g2["iters"] == g2b["iters"]
+    mlp = next(p.mlp for p in pols if p.mlp is not None)
+    swapped = [Policy("mlp", mlp=mlp, seed=p.seed, traj=p.traj) if p.kind == "greedy" else
+               (Policy("gumbel", mlp=mlp, seed=p.seed + 5, traj=p.traj) if p.kind == "gumbel" else p)
+               for p in pols]
+    g3 = db.simulate(swapped, "picard", num_chunks=M, flags=flags)
+    check_against_oracle(db, insts, swapped, g3, M)
+    # a different chunk count is a different graph
+    g4 = db.simulate(swapped, "picard", num_chunks=M + 3, flags=flags)
+    check_against_oracle(db, insts, swapped, g4, M + 3)
+
+
+def test_batch_autotuner_choice_is_exact():
+    insts, pols = mixed_batch(8, [3000, 2500, 4000, 1000, 3500, 2000, 1800, 2600], 32)
+    db = DeviceBatch(insts)
+    got = db.simulate(pols, "picard", num_chunks=0)
+    M = got["num_chunks"]
+    assert M >= 1 and got["seg_window"] >= 1 and got["cta_threads"] in (256, 512)
+    check_against_oracle(db, insts, pols, got, M)
+    again = db.simulate(pols, "picard", num_chunks=0)  # cached choice
+    assert again["num_chunks"] == M and again["seg_window"] == got["seg_window"]
+    assert torch.equal(again["actions"], got["actions"])
+
+
+def test_batch_host_outputs_and_integer_only():
+    insts, pols = mixed_batch(21, [700, 1400, 900], 40, kinds=("greedy", "dual"))
+    db = DeviceBatch(insts, mem=pic.PIC_MEM_HOST)
+    got = db.simulate(pols, "picard", num_chunks=9, out_mem=pic.PIC_MEM_HOST)
+    assert isinstance(got["actions"], np.ndarray)
+    check_against_oracle(db, insts, pols, got, 9)
+
+
+def test_batch_invalid_inputs():
+    insts, pols = mixed_batch(2, [100, 200], 8)
+    with pytest.raises(pic.PicError) as e:
+        DeviceBatch([insts[0], synth.make_instance(50, 9, 4, 9, seed=1)])
+    assert e.value.status == pic.PIC_ERR_INVALID_ARG and "N" in str(e.value)
+    bad = synth.make_instance(50, 8, 4, 9, seed=1)
+    bad.prod = bad.prod.copy()
+    bad.prod[7] = 4  # K = 4
+    with pytest.raises(pic.PicError) as e:
+        DeviceBatch([insts[0], bad])
+    assert e.value.status == pic.PIC_ERR_INVALID_ARG and "prod" in str(e.value)
+    db = DeviceBatch(insts)
+    two = [Policy("mlp", mlp=synth.make_mlp(8, 9, seed=98)),
+           Policy("mlp", mlp=synth.make_mlp(8, 9, seed=99))]  # two weight sets
+    with pytest.raises(pic.PicError) as e:
+        db.simulate(two, "picard", num_chunks=4)
+    assert e.value.status == pic.PIC_ERR_UNSUPPORTED
+    nolam = [synth.make_instance(80, 8, 3, 9, seed=4), synth.make_instance(90, 8, 3, 9, seed=5)]
+    db2 = DeviceBatch(nolam)
+    with pytest.raises(pic.PicError) as e:
+        db2.simulate([Policy("greedy"), Policy("dual")], "picard", num_chunks=4)
+    assert e.value.status == pic.PIC_ERR_INVALID_ARG and "lam" in str(e.value)
+
+
+def test_batch_uneven_full_size():
+    """512 trajectories, T_b ~ U{16,384..262,144}, N=32, K=2,000, R=200, even
+    index greedy, odd index MLP: one persistent launch (autotuned, run as a CUDA
+    graph) equals the batched sequential simulation trajectory by trajectory, and
+    sampled orders agree with the oracle's decision from the implied state."""
+    insts, pols = synth.batch_uneven(0)
+    db = DeviceBatch(insts)
+    flags = pic.PIC_FLAG_GRAPH
+    got = db.simulate(pols, "picard", num_chunks=0, flags=flags)
+    seq = db.simulate(pols, "sequential")
+    assert torch.equal(got["actions"], seq["actions"])
+    assert torch.equal(got["final_stock"], seq["final_stock"])
+    for b in range(len(insts)):
+        assert got["traj"][b]["total_cost"] == seq["traj"][b]["total_cost"], b
+        assert got["traj"][b]["lost"] == seq["traj"][b]["lost"], b
+        assert got["traj"][b]["converged"] == 1
+    a = got["actions"].cpu().numpy()
+    rng = np.random.default_rng(0)
+    for b in rng.choice(len(insts), 6, replace=False):
+        inst, pol = insts[b], pols[b]
+        ab = db.split(a)[b]
+        for t in np.concatenate([rng.integers(0, inst.T, 4), [inst.T - 1]]):
+            row = oracle.state_before(inst, ab, int(t))
+            want = oracle.policy_call(inst, pol, row, inst.prod[t], inst.reg[t], int(t))
+            assert want == ab[t], (b, t, want, ab[t])

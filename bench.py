@@ -5,9 +5,13 @@ one B300, against the sequential GPU simulator, bit-exact.
 A step is one whole simulation of one synthetic trajectory from its order
 stream resident in HBM: the product-major order tables (sort, runs, segments),
 every Picard pass to the fixed point, and the outputs (actions in time order,
-total cost).  Workload (bid-price FO, the large single-trajectory shape):
-T = 2^20 orders, N = 64 warehouses, K = 10,000 products (Zipf 1.1 demand),
-R = 1,000 regions, stock ~ Poisson(1.05 T p_k / N), M = 4,096 time chunks.
+total cost).  Default workload (bid-price FO, the large single-trajectory
+shape): T = 2^20 orders, N = 64 warehouses, K = 10,000 products (Zipf 1.1
+demand), R = 1,000 regions, stock ~ Poisson(1.05 T p_k / N), M = 4,096 time
+chunks.  --workload mlp_medium: T = 2^18, N = 64, K = 2,000, R = 500, MLP
+policy.  --workload batch_uneven: 512 trajectories of T_b ~ U{16,384..262,144}
+orders, N = 32, K = 2,000, R = 200, even index greedy, odd index MLP, one
+persistent launch per step (autotuned chunking, CUDA graph).
 
 Prints one JSON line (rank 0).  Under torchrun every rank simulates its own
 trajectory (weak scaling, no collective on the data path).  --impl reference
@@ -40,16 +44,31 @@ def parse():
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--chunks", type=int, default=4096)
+    p.add_argument("--chunks", type=int, default=-1,
+                   help="time chunks M (-1: the workload's default; 0: autotune, batch only)")
     p.add_argument("--seg-window", type=int, default=0)
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--seq-steps", type=int, default=3)
     p.add_argument("--e2e-steps", type=int, default=20)
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--T", type=int, default=0, help="orders (0 = the workload's own size)")
-    p.add_argument("--workload", default="dual_large", choices=["dual_large", "mlp_medium"])
+    p.add_argument("--workload", default="dual_large",
+                   choices=["dual_large", "mlp_medium", "batch_uneven"])
     p.add_argument("--flags", type=int, default=0, help="extra pic_sim_opts flags (tuning)")
     return p.parse_args()
+
+
+DEFAULT_CHUNKS = {"dual_large": 4096, "mlp_medium": 1024, "batch_uneven": 0}
+
+# FP32 CUDA-core peak of the MLP scorer's arithmetic: 148 SMs x 128 FP32 lanes x
+# 2 FLOP per FMA x 2.032 GHz (maximum SM clock)
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+
+
+def mlp_flops_per_call(N):
+    """FLOPs of one MLP decision after the per-region prefix: the stock rows of
+    layer 1 (N x 256 FMA) and layer 2 (256 x N FMA), 2 FLOP per FMA."""
+    return 2 * (N * 256 + 256 * N)
 
 
 def make_workload(args, seed):
@@ -63,6 +82,25 @@ def make_workload(args, seed):
     return inst, Policy("dual"), "dual"
 
 
+def batch_config(args, insts, res):
+    Ts = [i.T for i in insts]
+    cfg = {
+        "workload": "batch_uneven",
+        "desc": (f"FO batch, B={len(insts)} trajectories, T_b~U{{16384..262144}} "
+                 f"(total {sum(Ts)} orders), N={insts[0].N}, K={insts[0].K}, R={insts[0].R} per "
+                 f"trajectory, even index greedy / odd index MLP Linear(2N+16,256)-ReLU-Linear(256,N) "
+                 f"BF16 N(0,0.02), x0~Poisson(1.05 T p_k/N), cost~U{{1..100}}"),
+        "B": len(insts), "T_total": int(sum(Ts)), "T_min": int(min(Ts)), "T_max": int(max(Ts)),
+        "N": insts[0].N, "K": insts[0].K, "R": insts[0].R,
+        "l2": "inputs (about 0.6 GB of orders) exceed L2; flushed between timed steps (256 MiB write)",
+    }
+    if res is not None:
+        cfg.update({"chunks_per_trajectory": res["num_chunks"], "seg_window": res["seg_window"],
+                    "cta_threads": res["cta_threads"], "ctas_per_sm": res["ctas_per_sm"],
+                    "tuning": "autotuned" if chunks_of(args) == 0 else "fixed", "cuda_graph": True})
+    return cfg
+
+
 def workload_config(args, inst):
     pol = "MLP Linear(2N+16,256)-ReLU-Linear(256,N), BF16 N(0,0.02)" \
         if args.workload == "mlp_medium" else "bid-price, lambda~U{0..30}"
@@ -72,9 +110,13 @@ def workload_config(args, inst):
                  f"(Zipf 1.1), R={inst.R} regions, x0~Poisson(1.05 T p_k/N), cost~U{{1..100}}, "
                  f"{pol}"),
         "T": inst.T, "N": inst.N, "K": inst.K, "R": inst.R,
-        "chunks": args.chunks, "policy": args.workload == "mlp_medium" and "mlp" or "dual",
+        "chunks": chunks_of(args), "policy": args.workload == "mlp_medium" and "mlp" or "dual",
         "l2": "flushed between timed steps (256 MiB write)",
     }
+
+
+def chunks_of(args):
+    return DEFAULT_CHUNKS[args.workload] if args.chunks < 0 else args.chunks
 
 
 def load_peaks():
@@ -187,16 +229,58 @@ def cpu_oracle_rate(inst, pol, seconds):
             f"1 thread", out, inst.T)
 
 
-def run_reference(args):
-    inst, pol, _ = make_workload(args, args.seed)
-    per = max(1, int(args.steps))
+def batch_oracle_sample(insts, pols, seconds):
+    """The CPU oracle on whole trajectories of a batch, in order, for about
+    `seconds` (1 thread).  Returns (orders/s, sample, [(b, oracle output)])."""
     import oracle
-    # each step: the full trajectory, or a prefix of it when a full run exceeds ~10 s
+    done, orders, t0 = [], 0, time.perf_counter()
+    for b, (inst, pol) in enumerate(zip(insts, pols)):
+        out = oracle.seq_sim(inst, pol)
+        done.append((b, out))
+        orders += inst.T
+        if time.perf_counter() - t0 >= seconds:
+            break
+    el = time.perf_counter() - t0
+    kinds = sorted({pols[b].kind for b, _ in done})
+    return (orders / el, f"trajectories 0..{len(done) - 1} of {len(insts)} ({orders} orders, "
+            f"{'/'.join(kinds)}), sequential C oracle, 1 thread ({el:.1f} s)", done)
+
+
+def run_reference(args):
+    import oracle
+    per = max(1, int(args.steps))
+    # each step a bounded sample, so that warm-up + timed steps take about a minute
+    budget = max(0.05, min(10.0, 60.0 / (per + max(0, args.warmup))))
+    if args.workload == "batch_uneven":
+        from paper_2406_01939_b300 import synth
+        insts, pols = synth.batch_uneven(args.seed)
+        rate, sample, _ = batch_oracle_sample(insts, pols, budget)
+        total_T = sum(i.T for i in insts)
+        t0 = time.perf_counter()
+        n_orders = 0
+        for _ in range(per):
+            r, _, done = batch_oracle_sample(insts, pols, budget)
+            n_orders += sum(insts[b].T for b, _ in done)
+        el = time.perf_counter() - t0
+        value = n_orders / el
+        line = {
+            "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": per, "warmup": args.warmup, "ms_per_step": 1000 * total_T / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32+f32",
+            "data": "synthetic", "config": batch_config(args, insts, None),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "per step: " + sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line), flush=True)
+        return
+    inst, pol, _ = make_workload(args, args.seed)
+    # each step: the full trajectory, or a prefix of it when a full run exceeds the budget
     probe = prefix_instance(inst, min(inst.T, 2048))
     t0 = time.perf_counter()
     oracle.seq_sim(probe, pol)
     per_order = max((time.perf_counter() - t0) / probe.T, 1e-9)
-    Ts = inst.T if per_order * inst.T <= 10.0 else max(probe.T, int(10.0 / per_order))
+    Ts = inst.T if per_order * inst.T <= budget else max(probe.T, int(budget / per_order))
     sub = inst if Ts == inst.T else prefix_instance(inst, Ts)
     for _ in range(max(0, args.warmup)):
         oracle.seq_sim(sub, pol)
@@ -208,7 +292,8 @@ def run_reference(args):
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": per, "warmup": args.warmup, "ms_per_step": 1000 * el / per * inst.T / sub.T,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.workload == "mlp_medium" else "int32",
         "data": "synthetic", "config": workload_config(args, inst),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": (f"full {inst.T}-order trajectory per step" if sub.T == inst.T else
@@ -217,6 +302,152 @@ def run_reference(args):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def mlp_roofline(mlp_calls, N, ms, kernel):
+    flops = mlp_calls * mlp_flops_per_call(N)
+    achieved = flops / (ms / 1000.0) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "kernel": kernel,
+            "peak_kind": "derived: 148 SMs x 128 FP32 lanes x 2 FLOP x 2.032 GHz",
+            "algorithmic_flops": flops}
+
+
+def run_batch(args, dev, world, rank):
+    """Batch workload: every step simulates all trajectories of the batch in one
+    persistent launch (CUDA graph)."""
+    import torch
+    import torch.distributed as dist
+    import paper_2406_01939_b300 as pic
+    from paper_2406_01939_b300 import synth
+    from paper_2406_01939_b300.session import DeviceBatch
+
+    insts, pols = synth.batch_uneven(args.seed + rank)
+    db = DeviceBatch(insts, device=dev)
+    T = db.T
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    act = torch.empty(T, dtype=torch.int8, device=dev)
+    flags = pic.PIC_FLAG_TIMING | pic.PIC_FLAG_GRAPH | args.flags
+
+    def step():
+        return db.simulate(pols, "picard", num_chunks=chunks_of(args), seg_window=args.seg_window,
+                           flags=flags, want_stock=False, out=act)
+
+    t_tune = time.perf_counter()
+    first = step()  # runs the autotuner when chunks = 0
+    t_tune = time.perf_counter() - t_tune
+    for _ in range(max(3, args.warmup)):
+        r = step()
+    stream = torch.cuda.current_stream(dev)
+    clocks = Clocks(int(str(dev).split(":")[-1]) if ":" in str(dev) else 0)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    evs, results = [], []
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        results.append(step())
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    t_ms = sum(a.elapsed_time(b) for a, b in evs)
+    if world > 1:
+        tt = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    value = world * T * args.steps / (t_ms / 1000.0)
+    last = results[-1]
+    sim_ms = statistics.median(r["sim_ms"] for r in results)
+
+    seq_ms, bit_exact_gpu = None, None
+    if args.seq_steps > 0:
+        seq_act = torch.empty(T, dtype=torch.int8, device=dev)
+        seq_ms = []
+        for i in range(args.seq_steps + 1):
+            rs = db.simulate(pols, "sequential", flags=pic.PIC_FLAG_TIMING, want_stock=False,
+                             out=seq_act)
+            if i:
+                seq_ms.append(rs["total_ms"])
+        seq_ms = statistics.median(seq_ms)
+        bit_exact_gpu = bool(torch.equal(seq_act, act)) and all(
+            a["total_cost"] == b["total_cost"] and a["lost"] == b["lost"]
+            for a, b in zip(rs["traj"], last["traj"]))
+
+    # end to end: the batch created from pinned host arrays (H2D inside the call),
+    # simulated with host outputs, released; chunking fixed to the tuned choice
+    e2e_t, h2d, d2h, bit_exact_e2e = [], 0, 0, None
+    if args.e2e_steps > 0:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).pin_memory().numpy()
+        host = [synth.Instance(i.T, i.N, i.K, i.R, pin(i.prod), pin(i.reg), pin(i.x0), pin(i.cost),
+                               None) for i in insts]
+        h2d = sum(i.prod.nbytes + i.reg.nbytes + i.x0.nbytes + i.cost.nbytes for i in host)
+        host_act = torch.empty(T, dtype=torch.int8).pin_memory().numpy()
+        d2h = host_act.nbytes + 24 * len(insts)
+        for i in range(args.e2e_steps + 1):
+            flush.fill_(1)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            hb = DeviceBatch(host, device=dev, mem=pic.PIC_MEM_HOST)
+            hb.simulate(pols, "picard", num_chunks=last["num_chunks"], seg_window=last["seg_window"],
+                        want_stock=False, out=host_act, out_mem=pic.PIC_MEM_HOST)
+            hb.close()
+            t1 = time.perf_counter()
+            if i:
+                e2e_t.append(t1 - t0)
+        bit_exact_e2e = bool(np.array_equal(host_act, act.cpu().numpy()))
+    e2e_value = world * T / statistics.median(e2e_t) if e2e_t else None
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32+f32", "data": "synthetic",
+        "config": batch_config(args, insts, last),
+        "iters": last["iters"],
+        "iters_per_trajectory": {"min": min(t["iters"] for t in last["traj"]),
+                                 "max": max(t["iters"] for t in last["traj"])},
+        "seq_gpu": {"value": T / (seq_ms / 1000.0), "unit": UNIT, "ms": seq_ms,
+                    "what": "one warp per trajectory, all trajectories in one launch"}
+        if seq_ms else None,
+        "speedup_vs_seq_gpu": seq_ms / (t_ms / args.steps) if seq_ms else None,
+        "bit_exact_vs_seq_gpu": bit_exact_gpu,
+        "autotune_s": t_tune,
+        "phases_ms": {"per_call_work": sim_ms, "step_device": t_ms / args.steps},
+        "policy_calls": last["policy_calls"], "mlp_calls": last["mlp_calls"],
+        "segment_replays": last["seg_replays"],
+        "roofline": mlp_roofline(last["mlp_calls"], insts[0].N, sim_ms,
+                                 "k_picard_batch (persistent, all passes; MLP scorer FP32 FMA)"),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "bit_exact": bit_exact_e2e,
+                "what": "pic_create_batch from pinned host arrays + pic_simulate_batch with host "
+                        "outputs + release, per step"},
+        "gpu_launches": int(last["launches"]) * args.steps,
+        "clocks": clk,
+        "wall_s_timed_loop": wall,
+    }
+    if rank == 0 and world == 1 and args.cpu_seconds > 0:
+        rate, sample, done = batch_oracle_sample(insts, pols, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": sample}
+        a = act.cpu().numpy()
+        same = True
+        for b, out in done:
+            same &= bool(np.array_equal(out["actions"], a[db.offsets[b]:db.offsets[b + 1]]))
+            same &= out["total_cost"] == last["traj"][b]["total_cost"]
+        line["bit_exact_vs_oracle"] = same
+        line["oracle_trajectories_checked"] = len(done)
+    elif rank == 0:
+        line["cpu_baseline"] = None
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    db.close()
 
 
 def main():
@@ -236,10 +467,15 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
 
+    if args.workload == "batch_uneven":
+        run_batch(args, dev, world, rank)
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
     import paper_2406_01939_b300 as pic
-    from paper_2406_01939_b300 import synth
     from paper_2406_01939_b300.session import DeviceInstance, DevicePolicy
-    from paper_2406_01939_b300.synth import Policy
 
     inst, hpol, _ = make_workload(args, args.seed + rank)
     di = DeviceInstance(inst, device=dev)
@@ -248,7 +484,7 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def step(out):
-        return di.simulate(pol, "picard", num_chunks=args.chunks, seg_window=args.seg_window,
+        return di.simulate(pol, "picard", num_chunks=chunks_of(args), seg_window=args.seg_window,
                            flags=pic.PIC_FLAG_TIMING | args.flags, want_stock=False, out=out)
 
     act = torch.empty(T, dtype=torch.int8, device=dev)
@@ -285,7 +521,7 @@ def main():
     last = results[-1]
     # one extra (untimed) call with the per-pass trace
     tr = np.zeros((4096, 4), np.int64)
-    di.simulate(pol, "picard", num_chunks=args.chunks, seg_window=args.seg_window,
+    di.simulate(pol, "picard", num_chunks=chunks_of(args), seg_window=args.seg_window,
                 flags=args.flags, want_stock=False, out=act, trace=tr)
     ntr = min(last["iters"], 4096)
     ts, tr_end = tr[:ntr, 0], tr[:ntr, 1]
@@ -317,7 +553,7 @@ def main():
     host["lam"] = pin(inst.lam) if inst.lam is not None else None
     host_np = {k: (v.numpy() if v is not None else None) for k, v in host.items()}
     host_act = torch.empty(T, dtype=torch.int8).pin_memory().numpy()
-    opts = pic.make_opts("picard", args.chunks, out_mem=pic.PIC_MEM_HOST, seg_window=args.seg_window,
+    opts = pic.make_opts("picard", chunks_of(args), out_mem=pic.PIC_MEM_HOST, seg_window=args.seg_window,
                          flags=args.flags)
     h2d = sum(v.nbytes for v in host_np.values() if v is not None)
     d2h = host_act.nbytes + 64  # actions + the result record
@@ -336,14 +572,22 @@ def main():
 
     # roofline of the dominant kernel (the persistent Picard kernel)
     N = inst.N
-    alg_bytes = last["policy_calls"] * 6 + last["seg_replays"] * 16 * N
-    achieved = alg_bytes / (sim_ms / 1000.0) / 1e9
-    peak, peak_kind = load_peaks()
+    if args.workload == "mlp_medium":
+        roofline = mlp_roofline(last["mlp_calls"], N, sim_ms, "k_picard_mlp (persistent, all passes)")
+    else:
+        alg_bytes = last["policy_calls"] * 6 + last["seg_replays"] * 16 * N
+        achieved = alg_bytes / (sim_ms / 1000.0) / 1e9
+        peak, peak_kind = load_peaks()
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": profiled_traffic(),
+                    "kernel": "k_picard_int (persistent, all passes)", "peak_kind": peak_kind,
+                    "algorithmic_bytes": alg_bytes}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.workload == "mlp_medium" else "int32", "data": "synthetic",
         "config": workload_config(args, inst),
         "iters": iters,
         "seq_gpu": {"value": T / (seq_ms / 1000.0), "unit": UNIT, "ms": seq_ms} if seq_ms else None,
@@ -353,11 +597,7 @@ def main():
                       "step_device": t_ms / args.steps},
         "policy_calls": last["policy_calls"], "segment_replays": last["seg_replays"],
         "pass_trace": pass_trace,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic(),
-                     "kernel": "k_picard_int (persistent, all passes)",
-                     "peak_kind": peak_kind,
-                     "algorithmic_bytes": alg_bytes},
+        "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "bit_exact": bit_exact_e2e},
         "gpu_launches": int(last["launches"]) * args.steps,

@@ -139,6 +139,7 @@ typedef struct {
     int32_t seg_window;   /* segment window used (Picard) */
     int32_t cta_threads;  /* threads per CTA of the Picard launch */
     int32_t ctas_per_sm;  /* CTAs per SM of the Picard launch */
+    int64_t mlp_calls;    /* the policy_calls that evaluated an MLP / Gumbel policy */
 } pic_sim_result;
 
 /* Per-trajectory result of pic_simulate_batch. */

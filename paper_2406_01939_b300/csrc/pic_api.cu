@@ -485,6 +485,7 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
         res->policy_calls = (int64_t)hc.policy_calls;
         res->iters = T ? hc.iters : 1;
         res->num_chunks = M;
+        res->mlp_calls = mlp ? res->policy_calls : 0;
         res->seg_window = opts->mode == PIC_MODE_PICARD ? I.tables_w : 0;
         res->cta_threads = opts->mode == PIC_MODE_PICARD ? I.cta_threads : 32;
         res->ctas_per_sm = opts->mode == PIC_MODE_PICARD ? I.ctas_per_sm : 1;

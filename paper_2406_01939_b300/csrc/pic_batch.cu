@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_picard_batch(KArgs a, MlpPoli
     const uint4* W2p = s_w + p.N * kHidden / 8;
     const CostTable<false> ct{a.cost, nullptr, a.N};
     const int wib = threadIdx.x >> 5;
-    unsigned long long calls = 0;
+    unsigned long long calls = 0, mcalls = 0;
     picard_passes<NPL, WARPS>(a, calls, [&](int seg, const SegMeta& m, int fcp, int* fc_cur, int it) {
         const int tb = __ldg(b.traj_of_prod + m.k);
         const BatchPol bp = b.pol[tb];
@@ -191,14 +191,17 @@ __global__ void __launch_bounds__(THREADS, MINB) k_picard_batch(KArgs a, MlpPoli
             q.gumbel = bp.kind == PIC_POLICY_GUMBEL;
             q.seed = bp.seed;
             q.traj = bp.traj;
+            const unsigned long long m0 = mcalls;
             chg = replay_segment_mlp<NPL, SMEMW>(a, q, W1p, W2p, b.perm, seg, m, fcp, fc_cur, it,
-                                                 __ldg(b.toff + tb), calls, s_fs[wib], s_hs[wib]);
+                                                 __ldg(b.toff + tb), mcalls, s_fs[wib], s_hs[wib]);
+            calls += mcalls - m0;
         }
         // the trajectory's last changing pass (read first: many segments of one
         // trajectory change in the same pass)
         if (chg && lane_id() == 0 && ld_volatile(&b.last_chg[tb]) < it) atomicMax(&b.last_chg[tb], it);
         return chg;
     });
+    if (lane_id() == 0 && mcalls) atomicAdd(&a.ctrl->mlp_calls, mcalls);
 }
 
 template <int NPL, int THREADS, int MINB, bool FULL>
@@ -771,6 +774,10 @@ pic_status pic_simulate_batch(pic_instance* h, const pic_policy* pols, const pic
         res->rescored = (int64_t)hc.rescored;
         res->seg_replays = (int64_t)hc.seg_replays;
         res->launches = I.launches;
+        res->mlp_calls = picard ? (int64_t)hc.mlp_calls : 0;
+        if (!picard)
+            for (int b = 0; b < B; ++b)
+                if (bt->h_pol[b].kind >= PIC_POLICY_MLP) res->mlp_calls += bt->h_toff[b + 1] - bt->h_toff[b];
         res->seg_window = picard ? c.W : 0;
         res->cta_threads = picard ? I.cta_threads : 32 * kSeqWarps;
         res->ctas_per_sm = picard ? I.ctas_per_sm : 0;

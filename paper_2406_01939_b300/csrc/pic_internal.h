@@ -34,6 +34,7 @@ struct Ctrl {
     long long lost;
     unsigned long long rescored;
     unsigned long long seg_replays;
+    unsigned long long mlp_calls;  // MLP / Gumbel policy evaluations (batch kernel)
     int nruns;               // tables built by the preprocessing kernels
     int nseg;
     int last_m;              // chunk count the tables were built for

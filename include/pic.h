@@ -236,6 +236,43 @@ pic_status pic_simulate_batch(pic_instance* batch, const pic_policy* pols,
                               const pic_sim_opts* opts, int8_t* actions_out, int32_t* final_stock,
                               pic_traj_result* traj, pic_sim_result* res);
 
+/* Parameters and buffers of pic_policy_grad.  The flat parameter layout (FP32,
+ * row-major) is W1 [(2N+16)][256] (rows: cost inputs, stock inputs, embedding
+ * inputs) | b1 [256] | W2 [256][N] | b2 [N] | E [e_rows][16]. */
+typedef struct {
+    const float* master;   /* DEVICE FP32 parameters (masters), flat layout above */
+    int32_t e_rows;        /* rows of E (>= every trajectory's R) */
+    const int8_t* actions; /* DEVICE [sum T] paths to differentiate along (batch order), or
+                              NULL to simulate them here (Picard, opts) under the policy
+                              whose parameters are BF16(master) */
+    int8_t* actions_out;   /* DEVICE [sum T] receives the paths used, or NULL */
+    float* grad;           /* DEVICE FP32, flat layout: grad_scale * dJ/dtheta, or NULL to
+                              compute the objective only */
+    double grad_scale;
+} pic_grad_args;
+
+/* REINFORCE gradient of the MLP softmax policy along simulated paths (Sec. 4.2
+ * trains its FO policy by policy gradient over simulated roll-outs):
+ *   J = sum_b sum_t log pi(a_t | s_t) G_t,  G_t = -(sum of trajectory b's order
+ *   costs cost[r_t'][a_t'] for t' >= t),
+ * pi = softmax of the MLP scores over the warehouses holding stock; orders with
+ * a_t = a^phi or fewer than 2 stocked warehouses contribute 0.  The paths are
+ * held fixed; the policy's parameters are BF16(master) (round to nearest even)
+ * and the gradient with respect to those BF16 values is returned for the
+ * masters (straight-through).  With PIC_POLICY_GUMBEL paths, a_t is a sample of
+ * pi, and dJ/dtheta is the REINFORCE estimate.  Hidden activations are
+ * recomputed per order (no T x 256 storage).
+ *   batch      a batch instance (pic_create_batch; one trajectory is a batch of 1),
+ *              N <= 64;
+ *   pols       HOST [B]: PIC_POLICY_MLP or PIC_POLICY_GUMBEL, hidden = 256, seed and
+ *              traj per trajectory; weight pointers are ignored (BF16(master) is used);
+ *   objective  HOST, or NULL: J.
+ *   res        HOST, or NULL: the simulation's result when the paths are simulated here.
+ * Errors: INVALID_ARG (also: given actions out of range or not a feasible path),
+ * UNSUPPORTED, and those of pic_simulate_batch. */
+pic_status pic_policy_grad(pic_instance* batch, const pic_policy* pols, const pic_grad_args* args,
+                           const pic_sim_opts* opts, double* objective, pic_sim_result* res);
+
 /* Message for the last non-OK status on this thread ("" if none). */
 const char* pic_last_error(void);
 

@@ -8,7 +8,8 @@ calls raise.
 
 Names follow the C ABI: ``pic_create_instance``, ``pic_instance_load``,
 ``pic_destroy_instance``, ``pic_simulate``, ``pic_create_batch``,
-``pic_simulate_batch``, ``pic_simulate_sequential_static``, ``pic_last_error``.
+``pic_simulate_batch``, ``pic_policy_grad``, ``pic_simulate_sequential_static``,
+``pic_last_error``.
 """
 from __future__ import annotations
 
@@ -71,6 +72,11 @@ class pic_traj_result(C.Structure):
                 ("converged", C.c_int32)]
 
 
+class pic_grad_args(C.Structure):
+    _fields_ = [("master", C.c_void_p), ("e_rows", C.c_int32), ("actions", C.c_void_p),
+                ("actions_out", C.c_void_p), ("grad", C.c_void_p), ("grad_scale", C.c_double)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -98,6 +104,10 @@ def lib():
             L.pic_simulate_batch.argtypes = [P, C.POINTER(pic_policy), C.POINTER(pic_sim_opts), P, P,
                                              C.POINTER(pic_traj_result), C.POINTER(pic_sim_result)]
             L.pic_simulate_batch.restype = C.c_int
+            L.pic_policy_grad.argtypes = [P, C.POINTER(pic_policy), C.POINTER(pic_grad_args),
+                                          C.POINTER(pic_sim_opts), C.POINTER(C.c_double),
+                                          C.POINTER(pic_sim_result)]
+            L.pic_policy_grad.restype = C.c_int
             L.pic_simulate_sequential_static.argtypes = [C.POINTER(pic_instance_desc), C.c_int32, P,
                                                          P, C.POINTER(C.c_int64),
                                                          C.POINTER(C.c_int64)]
@@ -206,6 +216,24 @@ def pic_simulate_batch(handle: int, policies, opts: pic_sim_opts, actions_out, f
     if raise_on_error and st != PIC_OK:
         raise PicError(st, pic_last_error())
     return st, res, list(traj)
+
+
+def pic_policy_grad(handle: int, policies, master, e_rows, opts: pic_sim_opts, actions=None,
+                    actions_out=None, grad=None, grad_scale=1.0, raise_on_error=True):
+    """REINFORCE objective (and gradient into `grad` if given) of a batch
+    instance; master / actions / actions_out / grad are device tensors.  Returns
+    (status, objective, pic_sim_result)."""
+    B = len(policies)
+    pols = (pic_policy * B)(*policies)
+    args = pic_grad_args(_ptr(master), int(e_rows), _ptr(actions), _ptr(actions_out), _ptr(grad),
+                         float(grad_scale))
+    J = C.c_double(0.0)
+    res = pic_sim_result()
+    st = lib().pic_policy_grad(C.c_void_p(handle), pols, C.byref(args), C.byref(opts), C.byref(J),
+                               C.byref(res))
+    if raise_on_error and st != PIC_OK:
+        raise PicError(st, pic_last_error())
+    return st, J.value, res
 
 
 def pic_simulate_sequential_static(desc: pic_instance_desc, kind, actions_out, final_stock=None,

@@ -190,6 +190,7 @@ cudaError_t launch_validate(Instance& I, cudaStream_t st) {
 }
 
 void free_instance(Instance& I) {
+    free_pg(I);
     void* ptrs[] = {I.prod, I.reg, I.x0, I.cost, I.lam, I.perm, I.prod_s, I.reg_s, I.pcount,
                     I.pstart, I.run_start, I.run_of, I.seg_run, I.seg_of_run, I.seg_prod, I.seg_cf,
                     I.seg_ce, I.seg_meta, I.seg_lpt, I.len_hist, I.alpha_s, I.agg, I.carry, I.sbagg,

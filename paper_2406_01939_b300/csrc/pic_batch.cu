@@ -511,6 +511,10 @@ pic_status create_fail(pic_instance* h, pic_status s) {
 
 }  // namespace
 
+namespace pic {
+pic_status batch_tables(Instance& I, int M, int W, cudaStream_t st) { return ensure_tables(I, M, W, st); }
+}  // namespace pic
+
 extern "C" {
 
 pic_status pic_create_batch(const pic_instance_desc* descs, int32_t B, pic_instance** out) {

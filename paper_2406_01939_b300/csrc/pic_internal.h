@@ -90,6 +90,8 @@ struct Batch {
     int tune_m, tune_w, tune_shape;
 };
 
+struct PgState;  // buffers of the policy gradient (pic_pg.cu)
+
 // All device buffers of one instance.  Sizes: T orders, K products, N warehouses,
 // R regions; NP = N rounded up to a multiple of 32.
 struct Instance {
@@ -147,6 +149,7 @@ struct Instance {
     int launches;                     // kernels launched by the current call
     cudaEvent_t ev[4];                // phase timing events (created with the instance)
     Batch* batch;                     // non-null for a batch instance
+    PgState* pg;                      // policy-gradient buffers (allocated at first use)
 };
 
 // Preprocessing (pic_prep.cu): sort orders by product (stable in time), region
@@ -154,6 +157,10 @@ struct Instance {
 // batch instance chunks every trajectory by its own chunk_len), then the
 // longest-first order of the segments.
 cudaError_t build_tables(Instance* I, int M, int W, cudaStream_t st);
+// Stable sort of n (key, index) pairs by key in [0, max_key] (LSD radix on the
+// instance's histogram scratch); tmp_k / tmp_v are n-element scratch arrays.
+cudaError_t sort_pairs(Instance* I, const int32_t* keys, int n, int max_key, int32_t* keys_out,
+                       int32_t* vals_out, int32_t* tmp_k, int32_t* tmp_v, cudaStream_t st);
 // Longest-first order of the segments by estimated work: length, times
 // mlp_weight for segments of trajectories whose policy (pol, batch only) is an
 // MLP kind.
@@ -176,6 +183,10 @@ cudaError_t reduce_costs(Instance* I, const int8_t* alpha, const int32_t* reg, c
 cudaError_t sequential_int(Instance* I, int kind, cudaStream_t st);
 bool smem_cost_ok(const Instance* I);
 
+// Order tables of a batch instance for M chunks per trajectory and window W
+// (built only if the current ones differ; pic_batch.cu).
+pic_status batch_tables(Instance& I, int M, int W, cudaStream_t st);
+
 // Error message plumbing shared by the entry points (pic_api.cu).
 pic_status record_error(pic_status s, const char* msg);
 void clear_error();
@@ -186,6 +197,7 @@ bool desc_ok(const pic_instance_desc* d);
 // warehouses, R regions; free_instance releases whatever is allocated.
 cudaError_t alloc_instance(Instance& I, int T, int N, int K, int R, bool has_lam);
 void free_instance(Instance& I);
+void free_pg(Instance& I);  // pic_pg.cu
 // Range checks of an instance's device inputs (bits: 1 prod, 2 reg, 4 x0,
 // 8/16/32 cost, lam, cost - lam beyond 2^23, 128 a cost outside int16); the
 // result is left in ctrl->pad0.

@@ -1,0 +1,823 @@
+// REINFORCE gradient of the softmax MLP policy along simulated trajectories
+// (pic_policy_grad).
+//
+// Objective: the policy-gradient surrogate of Sec. 4.2's training,
+//   J(theta) = sum_b sum_t log pi_theta(a_t | s_t) G_t,
+//   G_t = -(sum of trajectory b's order costs from t on)   (int64 suffix sums),
+// pi_theta the softmax of the MLP scores over the feasible set F_t = {n :
+// x_t[k_t][n] > 0}; orders with a_t = a^phi or |F_t| < 2 contribute nothing.
+// The paths (s_t, a_t, G_t) are held fixed; the parameters are the BF16
+// roundings of FP32 masters and the gradient with respect to those BF16 values
+// is returned for the masters (straight-through).  Gumbel-max sampling draws a_t
+// from exactly this softmax, so with Gumbel paths J's gradient is the REINFORCE
+// estimate.
+//
+// Pipeline (all on the device):
+//   1. BF16 rounding of the masters, the per-region prefix P[r] from them;
+//   2. the paths: given, or simulated here by the batch Picard launch;
+//   3. order costs, an int64 scan over time, G_t per order;
+//   4. stock features per order: one warp per product walks the product's
+//      orders in time order from x0 (min(x, 32) as int8; whether the order
+//      counts), checking that every fulfilled action had stock;
+//   5. the orders sorted by region;
+//   6. k_pg_grad: tiles of 32 region-sorted orders.  Per tile the hidden layer
+//      is recomputed (z = P[r] + W1s^T f; nothing of size T x 256 is stored),
+//      then scores, softmax, ds = G (e_a - p), dW2 += h^T ds, dz = (W2 ds) *
+//      [z > 0], dW1s += f^T dz (stock rows of W1), and DZ[r] = sum of dz over
+//      the orders of region r;
+//   7. the rows of dW1 for the cost and embedding inputs, db1 and dE depend on
+//      an order only through its region, so they follow from DZ:
+//      dW1[n][j] = sum_r cost[r][n]/128 DZ[r][j], dW1[2N+e][j] = sum_r
+//      E[r][e] DZ[r][j], db1 = sum_r DZ[r], dE[r] = W1_E DZ[r].
+// Products and sums are FP32 within a tile and a CTA; every sum across CTAs,
+// DZ, J and the final reductions are FP64.
+#include <cstdarg>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "pic_device.cuh"
+
+using namespace pic;
+
+namespace pic {
+
+// Device buffers of the gradient (sized at first use; see pg_alloc).
+struct PgState {
+    int64_t T, R, P;
+    int e_rows;
+    uint16_t* pbf;     // [P] BF16 parameters (flat layout of pic_grad_args.master)
+    int8_t* acts;      // [T] paths simulated here
+    long long* cost;   // [T] order costs (time order)
+    long long* pex;    // [T + 1] exclusive prefix of cost
+    long long* blk;    // scan block sums
+    float* G;          // [T] G_t in sorted order
+    int8_t* f8;        // [T][64] min(stock, 32) in sorted order
+    uint8_t* ok;       // [T] order counts (fulfilled and |F| >= 2)
+    int32_t* rq;       // [T] region of the q-th order in region order
+    int32_t* jq;       // [T] sorted position of the q-th order in region order
+    double* acc;       // [P] gradient accumulators
+    double* dz;        // [R][256] per-region sums of dz
+    double* J;         // objective
+    int* bad;
+};
+
+}  // namespace pic
+
+namespace {
+
+constexpr int kPgN = 64;         // largest N the gradient kernel handles (f8 row stride)
+constexpr int kPgT = 32;         // orders per tile
+constexpr int kPgThreads = 512;  // 16 warps
+
+__device__ __forceinline__ float lo16(unsigned w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float hi16(unsigned w) { return __uint_as_float(w & 0xFFFF0000u); }
+
+// Round-to-nearest-even of FP32 to BF16 on the bit pattern (NaN kept quiet).
+__global__ void k_round_bf16(const float* __restrict__ in, long long n, uint16_t* __restrict__ out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const unsigned u = __float_as_uint(in[i]);
+        unsigned r;
+        if ((u & 0x7F800000u) == 0x7F800000u && (u & 0x007FFFFFu)) r = (u >> 16) | 0x40u;
+        else r = (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
+        out[i] = (uint16_t)r;
+    }
+}
+
+// ---------------------------------------------------------------- returns-to-go
+__global__ void k_pg_cost(const int8_t* __restrict__ act, const int32_t* __restrict__ reg,
+                          const int32_t* __restrict__ cost, int N, int T, long long* __restrict__ c) {
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < T;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int a = act[t];
+        c[t] = a >= 0 ? (long long)cost[(size_t)reg[t] * N + a] : 0ll;
+    }
+}
+
+constexpr int kS64Threads = 256, kS64Items = 8, kS64Tile = kS64Threads * kS64Items;
+
+__device__ __forceinline__ long long block_exscan64(long long v, long long* total) {
+    __shared__ long long ws[kS64Threads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        long long s = lane < kS64Threads / 32 ? ws[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(kFull, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < kS64Threads / 32) ws[lane] = s;
+    }
+    __syncthreads();
+    const long long before = w ? ws[w - 1] : 0;
+    *total = ws[kS64Threads / 32 - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void k_scan64_reduce(const long long* __restrict__ in, int n, long long* __restrict__ blk) {
+    const long long base = (long long)blockIdx.x * kS64Tile + threadIdx.x * kS64Items;
+    long long s = 0;
+#pragma unroll
+    for (int i = 0; i < kS64Items; ++i)
+        if (base + i < n) s += in[base + i];
+    long long tot;
+    block_exscan64(s, &tot);
+    if (threadIdx.x == 0) blk[blockIdx.x] = tot;
+}
+
+// Exclusive scan of the block sums in place; the grand total goes to *total.
+__global__ void k_scan64_blocks(long long* blk, int nb, long long* total) {
+    long long carry = 0;
+    for (int b0 = 0; b0 < nb; b0 += kS64Threads) {
+        const int i = b0 + threadIdx.x;
+        const long long v = i < nb ? blk[i] : 0;
+        long long tot;
+        const long long ex = block_exscan64(v, &tot);
+        if (i < nb) blk[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_scan64_down(const long long* __restrict__ in, long long* __restrict__ out, int n,
+                              const long long* __restrict__ blk) {
+    const long long base = (long long)blockIdx.x * kS64Tile + threadIdx.x * kS64Items;
+    long long v[kS64Items];
+    long long s = 0;
+#pragma unroll
+    for (int i = 0; i < kS64Items; ++i) {
+        v[i] = base + i < n ? in[base + i] : 0;
+        s += v[i];
+    }
+    long long tot;
+    long long ex = block_exscan64(s, &tot) + blk[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < kS64Items; ++i) {
+        if (base + i < n) out[base + i] = ex;
+        ex += v[i];
+    }
+}
+
+// G_t at sorted position j: -(total cost of the trajectory from time t on).
+__global__ void k_pg_G(const int32_t* __restrict__ perm, const int32_t* __restrict__ prod_s,
+                       const int32_t* __restrict__ traj_of_prod, const int32_t* __restrict__ toff,
+                       const long long* __restrict__ pex, int T, float* __restrict__ G) {
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < T;
+         j += (long long)gridDim.x * blockDim.x) {
+        const int t = perm[j];
+        const int b = traj_of_prod[prod_s[j]];
+        G[j] = (float)(-(double)(pex[toff[b + 1]] - pex[t]));
+    }
+}
+
+// ---------------------------------------------------------------- stock features
+// One warp per product: its orders in sorted (= time) order from x0.  Writes
+// min(stock, 32) per warehouse (row stride kPgN, zero beyond N) and whether the
+// order counts; bit 1 of *bad: a fulfilled action found no stock.
+__global__ void k_pg_stock(int K, int N, const int32_t* __restrict__ pstart,
+                           const int8_t* __restrict__ alpha_s, const int32_t* __restrict__ x0,
+                           int8_t* __restrict__ f8, uint8_t* __restrict__ okf, int* bad) {
+    const int lane = lane_id();
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int k = gw; k < K; k += nw) {
+        const int j0 = pstart[k], j1 = pstart[k + 1];
+        int S0 = lane < N ? x0[(size_t)k * N + lane] : 0;
+        int S1 = lane + 32 < N ? x0[(size_t)k * N + lane + 32] : 0;
+        bool err = false;
+        for (int base = j0; base < j1; base += 32) {
+            const int cnt = min(32, j1 - base);
+            const int my_a = lane < cnt ? alpha_s[base + lane] : -1;
+            int my_ok = 0;
+            for (int q = 0; q < cnt; ++q) {
+                const int a = __shfl_sync(kFull, my_a, q);
+                int8_t* row = f8 + (size_t)(base + q) * kPgN;
+                row[lane] = (int8_t)max(-128, min(S0, 32));
+                row[lane + 32] = (int8_t)max(-128, min(S1, 32));
+                const int nf = __popc(__ballot_sync(kFull, S0 > 0)) + __popc(__ballot_sync(kFull, S1 > 0));
+                if (a >= 0) {
+                    if (a == lane) { err |= S0 <= 0; S0 -= 1; }
+                    if (a == lane + 32) { err |= S1 <= 0; S1 -= 1; }
+                }
+                if (lane == q) my_ok = (a >= 0 && nf >= 2) ? 1 : 0;
+            }
+            if (lane < cnt) okf[base + lane] = (uint8_t)my_ok;
+        }
+        if (__any_sync(kFull, err) && lane == 0) atomicOr(bad, 1);
+    }
+}
+
+// ---------------------------------------------------------------- the tile kernel
+struct PgArgs {
+    int N, Q;                                  // warehouses, orders
+    const int32_t* __restrict__ rq;            // region-sorted orders: region
+    const int32_t* __restrict__ jq;            //   and sorted position
+    const int8_t* __restrict__ alpha_s;        // action per sorted position
+    const float* __restrict__ G;               // G_t per sorted position
+    const int8_t* __restrict__ f8;             // features per sorted position
+    const uint8_t* __restrict__ ok;
+    const float* __restrict__ P;               // [R][256] prefix b1 + cost + embedding rows
+    const uint16_t* __restrict__ W1;           // BF16 [(2N+16)][256]
+    const uint16_t* __restrict__ W2;           // BF16 [256][N]
+    const uint16_t* __restrict__ b2;           // BF16 [N]
+    double* accW1;                             // FP64 [(2N+16)][256] (stock rows written here)
+    double* accW2;                             // FP64 [256][N]
+    double* accb2;                             // FP64 [N]
+    double* dz;                                // FP64 [R][256]
+    double* J;
+};
+
+struct __align__(16) PgSmem {
+    uint2 w1s[kPgN][64];     // stock rows of W1, [n][j/4] as 4 BF16
+    uint2 w2[kHidden][16];   // W2 [j][n/4]
+    uint2 w2t[kPgN][64];     // W2^T [n][j/4]
+    float h[kPgT][kHidden];  // hidden activations, then dz
+    float f[kPgT][kPgN];     // features [t][n]
+    float fT[kPgN][kPgT];    // [n][t]
+    float ds[kPgT][kPgN];    // scores, then ds [t][n]
+    float dsT[kPgN][kPgT];   // [n][t]
+    float b2[kPgN];
+    float G[kPgT];
+    int r[kPgT], a[kPgT], ok[kPgT], j[kPgT];
+    double db2[kPgN];
+};
+
+__device__ __forceinline__ void unpack4(uint2 u, float w[4]) {
+    w[0] = lo16(u.x); w[1] = hi16(u.x); w[2] = lo16(u.y); w[3] = hi16(u.y);
+}
+
+template <bool GRAD>
+__global__ void __launch_bounds__(kPgThreads, 1) k_pg_grad(PgArgs p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PgSmem& s = *reinterpret_cast<PgSmem*>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int N = p.N;
+    // ---- weights to shared memory (zero beyond N)
+    for (int i = tid; i < kPgN * 64; i += kPgThreads) {
+        const int n = i >> 6, q = i & 63;
+        uint2 v = make_uint2(0, 0);
+        if (n < N) {
+            const uint16_t* row = p.W1 + (size_t)(N + n) * kHidden + 4 * q;
+            v = make_uint2(row[0] | ((unsigned)row[1] << 16), row[2] | ((unsigned)row[3] << 16));
+        }
+        s.w1s[n][q] = v;
+        uint16_t e[4];
+        for (int c = 0; c < 4; ++c) e[c] = n < N ? p.W2[(size_t)(4 * q + c) * N + n] : 0;
+        s.w2t[n][q] = make_uint2(e[0] | ((unsigned)e[1] << 16), e[2] | ((unsigned)e[3] << 16));
+    }
+    for (int i = tid; i < kHidden * 16; i += kPgThreads) {
+        const int jj = i >> 4, q = i & 15;
+        uint16_t e[4];
+        for (int c = 0; c < 4; ++c) e[c] = 4 * q + c < N ? p.W2[(size_t)jj * N + 4 * q + c] : 0;
+        s.w2[jj][q] = make_uint2(e[0] | ((unsigned)e[1] << 16), e[2] | ((unsigned)e[3] << 16));
+    }
+    if (tid < kPgN) {
+        s.b2[tid] = tid < N ? lo16(p.b2[tid]) : 0.0f;
+        s.db2[tid] = 0.0;
+    }
+    __syncthreads();
+    // thread blocks of the two accumulated products: hidden units j0..j0+3,
+    // warehouses n0..n0+7
+    const int jq4 = tid & 63, j0 = 4 * jq4;
+    const int nb8 = tid >> 6, n0 = 8 * nb8;
+    float accW2[4][8], accW1[8][4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) accW2[c][i] = accW1[i][c] = 0.0f;
+    double Jw = 0.0;
+    int cur_r = -1;   // DZ run (threads < 256: column j = tid)
+    float run = 0.0f;
+    const int ntiles = (p.Q + kPgT - 1) / kPgT;
+    const int tb0 = (int)((long long)blockIdx.x * ntiles / gridDim.x);
+    const int tb1 = (int)((long long)(blockIdx.x + 1) * ntiles / gridDim.x);
+    for (int tile = tb0; tile < tb1; ++tile) {
+        // ---- orders of the tile
+        if (tid < kPgT) {
+            const int q = tile * kPgT + tid;
+            int jj = -1, r = -1, a = -1, okv = 0;
+            float g = 0.0f;
+            if (q < p.Q) {
+                jj = p.jq[q];
+                r = p.rq[q];
+                a = p.alpha_s[jj];
+                g = p.G[jj];
+                okv = p.ok[jj];
+            }
+            s.j[tid] = jj; s.r[tid] = r; s.a[tid] = a; s.G[tid] = g; s.ok[tid] = okv;
+        }
+        __syncthreads();
+        {  // features: 32 rows x 64 warehouses, 4 per thread
+            const int t = tid >> 4, n4 = (tid & 15) * 4;
+            const int jj = s.j[t];
+            char4 v = make_char4(0, 0, 0, 0);
+            if (jj >= 0) v = *reinterpret_cast<const char4*>(p.f8 + (size_t)jj * kPgN + n4);
+            const float f0 = v.x / 32.0f, f1 = v.y / 32.0f, f2 = v.z / 32.0f, f3 = v.w / 32.0f;
+            *reinterpret_cast<float4*>(&s.f[t][n4]) = make_float4(f0, f1, f2, f3);
+            s.fT[n4][t] = f0; s.fT[n4 + 1][t] = f1; s.fT[n4 + 2][t] = f2; s.fT[n4 + 3][t] = f3;
+        }
+        __syncthreads();
+        {  // z = P[r] + W1s^T f, h = max(z, 0): orders t0..t0+3, hidden j0..j0+3
+            const int t0 = 4 * (tid >> 6);
+            float acc[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int r = s.r[t0 + i];
+                float4 pv = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (r >= 0) pv = __ldg(reinterpret_cast<const float4*>(p.P + (size_t)r * kHidden + j0));
+                acc[i][0] = pv.x; acc[i][1] = pv.y; acc[i][2] = pv.z; acc[i][3] = pv.w;
+            }
+            for (int n = 0; n < N; ++n) {
+                const float4 fv = *reinterpret_cast<const float4*>(&s.fT[n][t0]);
+                float wv[4];
+                unpack4(s.w1s[n][jq4], wv);
+                const float fi[4] = {fv.x, fv.y, fv.z, fv.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[i][c] = fmaf(wv[c], fi[i], acc[i][c]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                *reinterpret_cast<float4*>(&s.h[t0 + i][j0]) =
+                    make_float4(fmaxf(acc[i][0], 0.f), fmaxf(acc[i][1], 0.f), fmaxf(acc[i][2], 0.f),
+                                fmaxf(acc[i][3], 0.f));
+        }
+        __syncthreads();
+        {  // scores: order t, warehouses nq..nq+3
+            const int t = tid >> 4, nq = tid & 15;
+            float acc[4] = {s.b2[4 * nq], s.b2[4 * nq + 1], s.b2[4 * nq + 2], s.b2[4 * nq + 3]};
+            for (int jj = 0; jj < kHidden; jj += 4) {
+                const float4 hv = *reinterpret_cast<const float4*>(&s.h[t][jj]);
+                const float hi[4] = {hv.x, hv.y, hv.z, hv.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    float wv[4];
+                    unpack4(s.w2[jj + u][nq], wv);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[c] = fmaf(hi[u], wv[c], acc[c]);
+                }
+            }
+            *reinterpret_cast<float4*>(&s.ds[t][4 * nq]) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        }
+        __syncthreads();
+        // ---- softmax over the feasible set, log pi(a), ds = G (e_a - p): one warp per order
+        for (int t = w; t < kPgT; t += kPgThreads / 32) {
+            const bool use = s.ok[t] != 0;
+            const int a = s.a[t];
+            const float G = s.G[t];
+            float v[2], e[2];
+            bool fe[2];
+            float mx = -INFINITY;
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int n = lane + 32 * i;
+                v[i] = s.ds[t][n];
+                fe[i] = n < N && s.f[t][n] > 0.0f;
+                if (fe[i]) mx = fmaxf(mx, v[i]);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
+            float sum = 0.0f;
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                e[i] = fe[i] ? expf(v[i] - mx) : 0.0f;
+                sum += e[i];
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
+            const float lse = mx + logf(sum);
+            // score of the taken action, from the lane that owns warehouse a
+            const float va = __shfl_sync(kFull, a >= 32 ? v[1] : v[0], a >= 0 ? (a & 31) : 0);
+            if (use && lane == 0) Jw += (double)G * (double)(va - lse);
+            if (GRAD) {
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const int n = lane + 32 * i;
+                    const float pr = e[i] / sum;
+                    const float d = (use && fe[i]) ? G * ((n == a ? 1.0f : 0.0f) - pr) : 0.0f;
+                    s.ds[t][n] = d;
+                    s.dsT[n][t] = d;
+                }
+            }
+        }
+        if (!GRAD) {
+            __syncthreads();
+            continue;
+        }
+        __syncthreads();
+        // ---- dW2 += h^T ds, db2 += sum ds
+#pragma unroll 2
+        for (int t = 0; t < kPgT; ++t) {
+            const float4 hv = *reinterpret_cast<const float4*>(&s.h[t][j0]);
+            const float4 d0 = *reinterpret_cast<const float4*>(&s.ds[t][n0]);
+            const float4 d1 = *reinterpret_cast<const float4*>(&s.ds[t][n0 + 4]);
+            const float hi[4] = {hv.x, hv.y, hv.z, hv.w};
+            const float di[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+                for (int i = 0; i < 8; ++i) accW2[c][i] = fmaf(hi[c], di[i], accW2[c][i]);
+        }
+        if (tid < kPgN) {
+            float sd = 0.0f;
+            for (int t = 0; t < kPgT; ++t) sd += s.ds[t][tid];
+            s.db2[tid] += (double)sd;
+        }
+        __syncthreads();
+        {  // dz = (W2 ds) * [z > 0], written over h: orders t0..t0+3, hidden j0..j0+3
+            const int t0 = 4 * (tid >> 6);
+            float acc[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[i][c] = 0.0f;
+            for (int n = 0; n < N; ++n) {
+                const float4 dv = *reinterpret_cast<const float4*>(&s.dsT[n][t0]);
+                float wv[4];
+                unpack4(s.w2t[n][jq4], wv);
+                const float di[4] = {dv.x, dv.y, dv.z, dv.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[i][c] = fmaf(wv[c], di[i], acc[i][c]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float4 hv = *reinterpret_cast<const float4*>(&s.h[t0 + i][j0]);
+                hv.x = hv.x > 0.f ? acc[i][0] : 0.f;
+                hv.y = hv.y > 0.f ? acc[i][1] : 0.f;
+                hv.z = hv.z > 0.f ? acc[i][2] : 0.f;
+                hv.w = hv.w > 0.f ? acc[i][3] : 0.f;
+                *reinterpret_cast<float4*>(&s.h[t0 + i][j0]) = hv;
+            }
+        }
+        __syncthreads();
+        // ---- dW1 (stock rows) += f^T dz
+#pragma unroll 2
+        for (int t = 0; t < kPgT; ++t) {
+            const float4 f0 = *reinterpret_cast<const float4*>(&s.f[t][n0]);
+            const float4 f1 = *reinterpret_cast<const float4*>(&s.f[t][n0 + 4]);
+            const float4 zv = *reinterpret_cast<const float4*>(&s.h[t][j0]);
+            const float fi[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+            const float zi[4] = {zv.x, zv.y, zv.z, zv.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) accW1[i][c] = fmaf(fi[i], zi[c], accW1[i][c]);
+        }
+        // ---- DZ[r] += dz rows of region r (the tile is region-sorted)
+        if (tid < kHidden) {
+            for (int t = 0; t < kPgT; ++t) {
+                const int r = s.r[t];
+                if (r < 0) break;  // tail of the last tile
+                if (r != cur_r) {
+                    if (cur_r >= 0) atomicAdd(p.dz + (size_t)cur_r * kHidden + tid, (double)run);
+                    cur_r = r;
+                    run = 0.0f;
+                }
+                run += s.h[t][tid];
+            }
+        }
+        __syncthreads();
+    }
+    // ---- flush
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) Jw += __shfl_xor_sync(kFull, Jw, o);
+    if (lane == 0 && Jw != 0.0) atomicAdd(p.J, Jw);
+    if (!GRAD) return;
+    if (tid < kHidden && cur_r >= 0) atomicAdd(p.dz + (size_t)cur_r * kHidden + tid, (double)run);
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int n = n0 + i;
+            if (n < N) {
+                atomicAdd(p.accW2 + (size_t)(j0 + c) * N + n, (double)accW2[c][i]);
+                atomicAdd(p.accW1 + (size_t)(N + n) * kHidden + j0 + c, (double)accW1[i][c]);
+            }
+        }
+    if (tid < N) atomicAdd(p.accb2 + tid, s.db2[tid]);
+}
+
+// ---------------------------------------------------------------- reductions over regions
+// dW1 rows of the cost inputs (n < N), of the embedding (2N + e), and db1, from
+// DZ: acc[row][j] += sum_r coef(row, r) DZ[r][j].  Block: 256 threads = one per
+// hidden unit; blockIdx.y picks a group of 16 rows; regions strided over blockIdx.x.
+__global__ void __launch_bounds__(256) k_pg_rows(int N, int R, const double* __restrict__ dz,
+                                                  const int32_t* __restrict__ cost,
+                                                  const uint16_t* __restrict__ E,
+                                                  const int32_t* __restrict__ reg_local,
+                                                  double* accW1, double* accb1) {
+    const int j = threadIdx.x;
+    const int nrows = N + kEmb + 1;  // cost rows, embedding rows, b1
+    const int row0 = blockIdx.y * 16;
+    double acc[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) acc[i] = 0.0;
+    for (int r = blockIdx.x; r < R; r += gridDim.x) {
+        const double d = dz[(size_t)r * kHidden + j];
+        const int re = reg_local[r];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int row = row0 + i;
+            double c = 0.0;
+            if (row < N) c = (double)cost[(size_t)r * N + row] / 128.0;
+            else if (row < N + kEmb) c = (double)lo16(E[(size_t)re * kEmb + (row - N)]);
+            else if (row == N + kEmb) c = 1.0;
+            acc[i] = fma(c, d, acc[i]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int row = row0 + i;
+        if (row >= nrows || acc[i] == 0.0) continue;
+        if (row < N) atomicAdd(accW1 + (size_t)row * kHidden + j, acc[i]);
+        else if (row < N + kEmb) atomicAdd(accW1 + (size_t)(2 * N + row - N) * kHidden + j, acc[i]);
+        else atomicAdd(accb1 + j, acc[i]);
+    }
+}
+
+// dE[reg_local[r]] += W1_E DZ[r]: one warp per region.
+__global__ void k_pg_dE(int N, int R, const double* __restrict__ dz, const uint16_t* __restrict__ W1,
+                        const int32_t* __restrict__ reg_local, double* accE) {
+    const int lane = lane_id();
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int r = gw; r < R; r += nw) {
+        double u[kEmb];
+#pragma unroll
+        for (int e = 0; e < kEmb; ++e) u[e] = 0.0;
+        for (int j = lane; j < kHidden; j += 32) {
+            const double d = dz[(size_t)r * kHidden + j];
+#pragma unroll
+            for (int e = 0; e < kEmb; ++e) u[e] = fma((double)lo16(W1[(size_t)(2 * N + e) * kHidden + j]), d, u[e]);
+        }
+#pragma unroll
+        for (int e = 0; e < kEmb; ++e) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) u[e] += __shfl_xor_sync(kFull, u[e], o);
+        }
+        if (lane < kEmb) {
+            double v = 0.0;
+#pragma unroll
+            for (int e = 0; e < kEmb; ++e)
+                if (e == lane) v = u[e];
+            if (v != 0.0) atomicAdd(accE + (size_t)reg_local[r] * kEmb + lane, v);
+        }
+    }
+}
+
+__global__ void k_pg_out(const double* __restrict__ acc, long long n, double scale, float* __restrict__ g) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        g[i] = (float)(scale * acc[i]);
+}
+
+__global__ void k_gather_paths(const int8_t* __restrict__ act, const int32_t* __restrict__ perm, int T,
+                               int N, int8_t* __restrict__ alpha_s, int* bad) {
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < T;
+         j += (long long)gridDim.x * blockDim.x) {
+        int a = act[perm[j]];
+        if (a < -1 || a >= N) {
+            atomicOr(bad, 2);
+            a = -1;
+        }
+        alpha_s[j] = (int8_t)a;
+    }
+}
+
+// ---------------------------------------------------------------- host side
+thread_local char t_msg[320];
+
+pic_status fail(pic_status s, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+pic_status fail(pic_status s, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(t_msg, sizeof(t_msg), fmt, ap);
+    va_end(ap);
+    return record_error(s, t_msg);
+}
+
+#define PCU(call)                                                                               \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return fail(e_ == cudaErrorMemoryAllocation ? PIC_ERR_OOM : PIC_ERR_CUDA,           \
+                        "%s failed: %s (pic_pg.cu:%d)", #call, cudaGetErrorString(e_), __LINE__); \
+    } while (0)
+
+int nblk(long long n, int per) { return (int)((n + per - 1) / per); }
+
+pic_status pg_alloc(Instance& I, int e_rows, int64_t P) {
+    PgState* g = I.pg;
+    if (g && g->P == P && g->e_rows == e_rows) return PIC_OK;
+    if (g) {
+        void* ptrs[] = {g->pbf, g->acts, g->cost, g->pex, g->blk, g->G, g->f8, g->ok, g->rq, g->jq,
+                        g->acc, g->dz, g->J, g->bad};
+        for (void* q : ptrs)
+            if (q) cudaFree(q);
+        delete g;
+        I.pg = nullptr;
+    }
+    g = new (std::nothrow) PgState();
+    if (!g) return fail(PIC_ERR_OOM, "host allocation failed");
+    memset(g, 0, sizeof(PgState));
+    I.pg = g;
+    g->T = I.T;
+    g->R = I.R;
+    g->P = P;
+    g->e_rows = e_rows;
+    const size_t T = (size_t)(I.T ? I.T : 1);
+    PCU(cudaMalloc((void**)&g->pbf, sizeof(uint16_t) * P));
+    PCU(cudaMalloc((void**)&g->acts, T));
+    PCU(cudaMalloc((void**)&g->cost, sizeof(long long) * T));
+    PCU(cudaMalloc((void**)&g->pex, sizeof(long long) * (T + 1)));
+    PCU(cudaMalloc((void**)&g->blk, sizeof(long long) * (T / kS64Tile + 2)));
+    PCU(cudaMalloc((void**)&g->G, sizeof(float) * T));
+    PCU(cudaMalloc((void**)&g->f8, (size_t)kPgN * T));
+    PCU(cudaMalloc((void**)&g->ok, T));
+    PCU(cudaMalloc((void**)&g->rq, sizeof(int32_t) * T));
+    PCU(cudaMalloc((void**)&g->jq, sizeof(int32_t) * T));
+    PCU(cudaMalloc((void**)&g->acc, sizeof(double) * P));
+    PCU(cudaMalloc((void**)&g->dz, sizeof(double) * (size_t)I.R * kHidden));
+    PCU(cudaMalloc((void**)&g->J, sizeof(double)));
+    PCU(cudaMalloc((void**)&g->bad, sizeof(int)));
+    return PIC_OK;
+}
+
+}  // namespace
+
+namespace pic {
+void free_pg(Instance& I) {
+    PgState* g = I.pg;
+    if (!g) return;
+    void* ptrs[] = {g->pbf, g->acts, g->cost, g->pex, g->blk, g->G, g->f8, g->ok, g->rq, g->jq,
+                    g->acc, g->dz, g->J, g->bad};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    delete g;
+    I.pg = nullptr;
+}
+}  // namespace pic
+
+extern "C" pic_status pic_policy_grad(pic_instance* h, const pic_policy* pols, const pic_grad_args* ga,
+                                      const pic_sim_opts* opts, double* objective,
+                                      pic_sim_result* res) {
+    clear_error();
+    if (!h || !h->I.batch)
+        return fail(PIC_ERR_INVALID_ARG, "pic_policy_grad needs a batch instance (pic_create_batch)");
+    if (!pols || !ga || !opts || !ga->master)
+        return fail(PIC_ERR_INVALID_ARG, "pols, args, args->master and opts are required");
+    Instance& I = h->I;
+    Batch* bt = I.batch;
+    const int B = bt->B, N = I.N;
+    if (N > kPgN) return fail(PIC_ERR_UNSUPPORTED, "pic_policy_grad supports N <= %d (N = %d)", kPgN, N);
+    int64_t max_r = 0;
+    for (int b = 0; b < B; ++b) {
+        if (pols[b].kind != PIC_POLICY_MLP && pols[b].kind != PIC_POLICY_GUMBEL)
+            return fail(PIC_ERR_INVALID_ARG, "trajectory %d: the gradient needs an MLP or Gumbel policy", b);
+        if (pols[b].hidden != kHidden)
+            return fail(PIC_ERR_UNSUPPORTED, "trajectory %d: MLP hidden width must be %d", b, kHidden);
+        const int64_t rb = bt->h_roff[b + 1] - bt->h_roff[b];
+        if (rb > max_r) max_r = rb;
+    }
+    if (ga->e_rows < max_r)
+        return fail(PIC_ERR_INVALID_ARG, "e_rows = %d is below the largest trajectory R = %lld", ga->e_rows,
+                    (long long)max_r);
+    const int64_t oW1 = 0, ob1 = (int64_t)(2 * N + kEmb) * kHidden, oW2 = ob1 + kHidden,
+                  ob2 = oW2 + (int64_t)kHidden * N, oE = ob2 + N;
+    const int64_t P = oE + (int64_t)ga->e_rows * kEmb;
+    pic_status s = pg_alloc(I, ga->e_rows, P);
+    if (s != PIC_OK) return s;
+    PgState* g = I.pg;
+    cudaStream_t st = (cudaStream_t)opts->stream;
+    const int T = I.T;
+    const int grid = 4 * I.num_sms;
+    // 1. BF16 parameters
+    k_round_bf16<<<grid, 256, 0, st>>>(ga->master, P, g->pbf);
+    PCU(cudaGetLastError());
+    pic_policy* pb = new (std::nothrow) pic_policy[B];
+    if (!pb) return fail(PIC_ERR_OOM, "host allocation failed");
+    for (int b = 0; b < B; ++b) {
+        pb[b] = pols[b];
+        pb[b].W1 = g->pbf + oW1;
+        pb[b].b1 = g->pbf + ob1;
+        pb[b].W2 = g->pbf + oW2;
+        pb[b].b2 = g->pbf + ob2;
+        pb[b].E = g->pbf + oE;
+    }
+    // 2. paths
+    const int8_t* acts = ga->actions;
+    pic_sim_result sr;
+    memset(&sr, 0, sizeof(sr));
+    PCU(cudaMemsetAsync(g->bad, 0, sizeof(int), st));
+    if (!acts) {
+        pic_sim_opts so = *opts;
+        so.mode = PIC_MODE_PICARD;
+        so.out_mem = PIC_MEM_DEVICE;
+        int8_t* dst = ga->actions_out ? ga->actions_out : g->acts;
+        s = pic_simulate_batch(h, pb, &so, dst, nullptr, nullptr, &sr);
+        if (s != PIC_OK) {
+            delete[] pb;
+            return s;
+        }
+        acts = dst;
+    } else {
+        if (I.tables_m == 0) {
+            s = batch_tables(I, 1, kSegWindow, st);
+            if (s != PIC_OK) {
+                delete[] pb;
+                return s;
+            }
+        }
+        if (T) k_gather_paths<<<grid, 256, 0, st>>>(acts, I.perm, T, N, I.alpha_s, g->bad);
+        PCU(cudaGetLastError());
+        if (ga->actions_out && T)
+            PCU(cudaMemcpyAsync(ga->actions_out, acts, T, cudaMemcpyDeviceToDevice, st));
+    }
+    PCU(mlp_alloc(&I));
+    cudaError_t e = mlp_prepare(&I, &pb[0], st);
+    delete[] pb;
+    PCU(e);
+    PCU(cudaMemsetAsync(g->J, 0, sizeof(double), st));
+    const bool want_grad = ga->grad != nullptr;
+    if (want_grad) {
+        PCU(cudaMemsetAsync(g->acc, 0, sizeof(double) * P, st));
+        PCU(cudaMemsetAsync(g->dz, 0, sizeof(double) * (size_t)I.R * kHidden, st));
+    }
+    int launches = 3;
+    if (T) {
+        // 3. returns-to-go
+        k_pg_cost<<<grid, 256, 0, st>>>(acts, I.reg, I.cost, N, T, g->cost);
+        const int nb = nblk(T, kS64Tile);
+        k_scan64_reduce<<<nb, kS64Threads, 0, st>>>(g->cost, T, g->blk);
+        k_scan64_blocks<<<1, kS64Threads, 0, st>>>(g->blk, nb, g->pex + T);
+        k_scan64_down<<<nb, kS64Threads, 0, st>>>(g->cost, g->pex, T, g->blk);
+        k_pg_G<<<grid, 256, 0, st>>>(I.perm, I.prod_s, bt->traj_of_prod, bt->toff, g->pex, T, g->G);
+        // 4. stock features
+        k_pg_stock<<<grid, 256, 0, st>>>(I.K, N, I.pstart, I.alpha_s, I.x0, g->f8, g->ok, g->bad);
+        PCU(cudaGetLastError());
+        // 5. region order
+        const int l0 = I.launches;
+        PCU(sort_pairs(&I, I.reg_s, T, I.R - 1, g->rq, g->jq, I.tmp_a, I.tmp_b, st));
+        launches += I.launches - l0;
+        // 6. tiles
+        PgArgs a;
+        a.N = N; a.Q = T;
+        a.rq = g->rq; a.jq = g->jq; a.alpha_s = I.alpha_s; a.G = g->G; a.f8 = g->f8; a.ok = g->ok;
+        a.P = I.mlp_P;
+        a.W1 = g->pbf + oW1; a.W2 = g->pbf + oW2; a.b2 = g->pbf + ob2;
+        a.accW1 = g->acc + oW1; a.accW2 = g->acc + oW2; a.accb2 = g->acc + ob2;
+        a.dz = g->dz; a.J = g->J;
+        const size_t smem = sizeof(PgSmem);
+        if (want_grad) {
+            PCU(cudaFuncSetAttribute(k_pg_grad<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_pg_grad<true><<<I.num_sms, kPgThreads, smem, st>>>(a);
+        } else {
+            PCU(cudaFuncSetAttribute(k_pg_grad<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_pg_grad<false><<<I.num_sms, kPgThreads, smem, st>>>(a);
+        }
+        PCU(cudaGetLastError());
+        launches += 7 + 1;
+        // 7. rows that depend on the region only
+        if (want_grad) {
+            const int groups = (N + kEmb + 1 + 15) / 16;
+            k_pg_rows<<<dim3(I.num_sms, groups), 256, 0, st>>>(N, I.R, g->dz, I.cost, g->pbf + oE,
+                                                               bt->reg_local, g->acc + oW1, g->acc + ob1);
+            k_pg_dE<<<grid, 256, 0, st>>>(N, I.R, g->dz, g->pbf + oW1, bt->reg_local, g->acc + oE);
+            PCU(cudaGetLastError());
+            launches += 2;
+        }
+    }
+    if (want_grad) {
+        k_pg_out<<<grid, 256, 0, st>>>(g->acc, P, ga->grad_scale, ga->grad);
+        PCU(cudaGetLastError());
+        launches += 1;
+    }
+    double J = 0.0;
+    int bad = 0;
+    PCU(cudaMemcpyAsync(&J, g->J, sizeof(double), cudaMemcpyDeviceToHost, st));
+    PCU(cudaMemcpyAsync(&bad, g->bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PCU(cudaStreamSynchronize(st));
+    if (bad & 2) return fail(PIC_ERR_INVALID_ARG, "actions hold a value outside [-1, N)");
+    if (bad & 1) return fail(PIC_ERR_INVALID_ARG, "actions are not a feasible path (an order took a unit "
+                                                  "from a warehouse without stock)");
+    if (objective) *objective = J;
+    if (res) {
+        *res = sr;
+        res->launches = sr.launches + launches;
+    }
+    return PIC_OK;
+}

@@ -366,33 +366,42 @@ cudaError_t scan_exclusive(const int32_t* in, int32_t* out, int n, int32_t* tota
     return cudaGetLastError();
 }
 
+cudaError_t sort_pairs(Instance* I, const int32_t* keys, int n, int max_key, int32_t* keys_out,
+                       int32_t* vals_out, int32_t* tmp_k, int32_t* tmp_v, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    // LSD radix, 8-bit digits, as many passes as max_key has bytes; the passes
+    // alternate between (tmp_k, tmp_v) and (keys_out, vals_out) so that the last
+    // one lands in (keys_out, vals_out)
+    int passes = 1;
+    while (passes < 4 && ((unsigned)max_key >> (8 * passes)) != 0) ++passes;
+    I->launches += passes * 5;  // per pass: histogram, 3-kernel scan, scatter
+    const int nblk = nblocks(n, kRadixTile);
+    const int32_t* kin = keys;
+    const int32_t* vin = nullptr;
+    cudaError_t e;
+    for (int p = 0; p < passes; ++p) {
+        const bool last_side = ((passes - 1 - p) & 1) == 0;
+        int32_t* kout = last_side ? keys_out : tmp_k;
+        int32_t* vout = last_side ? vals_out : tmp_v;
+        const int shift = 8 * p;
+        k_radix_hist<<<nblk, kRadixThreads, 0, st>>>(kin, n, shift, I->hist, nblk);
+        if ((e = scan_exclusive(I->hist, I->hist, 256 * nblk, nullptr, I->scan_blk, st))) return e;
+        k_radix_scatter<<<nblk, kRadixThreads, 0, st>>>(kin, vin, n, shift, I->hist, nblk, kout, vout);
+        kin = kout;
+        vin = vout;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t build_tables(Instance* I, int M, int W, cudaStream_t st) {
     const int T = I->T, K = I->K;
     cudaError_t e;
     if (T == 0) return cudaMemsetAsync(I->ctrl, 0, offsetof(Ctrl, tag_base), st);
-    // 1. stable sort of (product, time) by product: LSD radix, 8-bit digits, as
-    // many passes as K - 1 has bytes; the passes alternate between (tmp_a,
-    // tmp_b) and (prod_s, perm) so that the last one lands in (prod_s, perm)
-    int passes = 1;
-    while (passes < 4 && ((unsigned)(K - 1) >> (8 * passes)) != 0) ++passes;
-    // kernel launches made below: per radix pass 2 + a 3-kernel scan; then
-    // product offsets, run flags + scan + runs, segment flags + scan +
-    // segments + chains
-    I->launches += passes * 5 + 1 + 5 + 6;
-    const int nblk = nblocks(T, kRadixTile);
-    const int32_t* kin = I->prod;
-    const int32_t* vin = nullptr;
-    for (int p = 0; p < passes; ++p) {
-        const bool last_side = ((passes - 1 - p) & 1) == 0;
-        int32_t* kout = last_side ? I->prod_s : I->tmp_a;
-        int32_t* vout = last_side ? I->perm : I->tmp_b;
-        const int shift = 8 * p;
-        k_radix_hist<<<nblk, kRadixThreads, 0, st>>>(kin, T, shift, I->hist, nblk);
-        if ((e = scan_exclusive(I->hist, I->hist, 256 * nblk, nullptr, I->scan_blk, st))) return e;
-        k_radix_scatter<<<nblk, kRadixThreads, 0, st>>>(kin, vin, T, shift, I->hist, nblk, kout, vout);
-        kin = kout;
-        vin = vout;
-    }
+    // 1. stable sort of (product, time) by product
+    // kernel launches made below besides the sort: product offsets, run flags +
+    // scan + runs, segment flags + scan + segments + chains
+    I->launches += 1 + 5 + 6;
+    if ((e = sort_pairs(I, I->prod, T, K - 1, I->prod_s, I->perm, I->tmp_a, I->tmp_b, st))) return e;
     // 2. first sorted position of every product
     k_pstart<<<nblocks(K + 1, 256), 256, 0, st>>>(I->prod_s, T, K, I->pstart);
     // 3. runs for M chunks of L orders

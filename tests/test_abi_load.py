@@ -24,7 +24,8 @@ def declared_functions():
 def test_header_declares_the_entry_points():
     names = declared_functions()
     for want in ("pic_create_instance", "pic_instance_load", "pic_destroy_instance",
-                 "pic_simulate", "pic_create_batch", "pic_simulate_batch", "pic_last_error"):
+                 "pic_simulate", "pic_create_batch", "pic_simulate_batch", "pic_policy_grad",
+                 "pic_last_error"):
         assert want in names
 
 
@@ -52,3 +53,4 @@ def test_null_arguments_rejected_without_gpu():
     assert L.pic_create_batch(None, 3, ctypes.byref(h)) == pic.PIC_ERR_INVALID_ARG
     assert L.pic_simulate_batch(None, None, None, None, None, None, None) == pic.PIC_ERR_INVALID_ARG
     assert "batch" in pic.pic_last_error()
+    assert L.pic_policy_grad(None, None, None, None, None, None) == pic.PIC_ERR_INVALID_ARG

@@ -11,7 +11,10 @@ demand), R = 1,000 regions, stock ~ Poisson(1.05 T p_k / N), M = 4,096 time
 chunks.  --workload mlp_medium: T = 2^18, N = 64, K = 2,000, R = 500, MLP
 policy.  --workload batch_uneven: 512 trajectories of T_b ~ U{16,384..262,144}
 orders, N = 32, K = 2,000, R = 200, even index greedy, odd index MLP, one
-persistent launch per step (autotuned chunking, CUDA graph).
+persistent launch per step (autotuned chunking, CUDA graph).  --workload
+pg_large: a policy-gradient step over 64 trajectories of T = 2^20 orders (N = 64,
+K = 10,000, R = 1,000, Gumbel-max MLP): the batch simulated by Picard, then the
+REINFORCE gradient (hand-written backward kernel).
 
 Prints one JSON line (rank 0).  Under torchrun every rank simulates its own
 trajectory (weak scaling, no collective on the data path).  --impl reference
@@ -53,12 +56,14 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--T", type=int, default=0, help="orders (0 = the workload's own size)")
     p.add_argument("--workload", default="dual_large",
-                   choices=["dual_large", "mlp_medium", "batch_uneven"])
+                   choices=["dual_large", "mlp_medium", "batch_uneven", "pg_large"])
     p.add_argument("--flags", type=int, default=0, help="extra pic_sim_opts flags (tuning)")
+    p.add_argument("--B", type=int, default=0,
+                   help="trajectories of batch_uneven / pg_large (0 = the workload's 512 / 64)")
     return p.parse_args()
 
 
-DEFAULT_CHUNKS = {"dual_large": 4096, "mlp_medium": 1024, "batch_uneven": 0}
+DEFAULT_CHUNKS = {"dual_large": 4096, "mlp_medium": 1024, "batch_uneven": 0, "pg_large": 32}
 
 # FP32 CUDA-core peak of the MLP scorer's arithmetic: 148 SMs x 128 FP32 lanes x
 # 2 FLOP per FMA x 2.032 GHz (maximum SM clock)
@@ -129,7 +134,7 @@ def load_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("pic_int.cu", "pic_picard.cuh", "pic_device.cuh", "pic_internal.h"):
+    for f in ("pic_int.cu", "pic_replay.cuh", "pic_picard.cuh", "pic_device.cuh", "pic_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_2406_01939_b300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -322,7 +327,7 @@ def run_batch(args, dev, world, rank):
     from paper_2406_01939_b300 import synth
     from paper_2406_01939_b300.session import DeviceBatch
 
-    insts, pols = synth.batch_uneven(args.seed + rank)
+    insts, pols = synth.batch_uneven(args.seed + rank, **({"B": args.B} if args.B else {}))
     db = DeviceBatch(insts, device=dev)
     T = db.T
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -450,6 +455,102 @@ def run_batch(args, dev, world, rank):
     db.close()
 
 
+def grad_flops_per_order(N):
+    """FLOPs of the gradient kernel per order: hidden layer (stock rows), scores,
+    dW2, W2 ds and dW1 (stock rows): five N x 256 products, 2 FLOP per FMA."""
+    return 2 * 5 * N * 256
+
+
+def run_pg(args, dev, world, rank):
+    """Policy-gradient step: simulate the batch (Picard) with BF16(master), then
+    the objective and gradient along those paths."""
+    import torch
+    import torch.distributed as dist
+    from paper_2406_01939_b300 import synth
+    from paper_2406_01939_b300.reinforce import Reinforce, flat_from_mlp
+    from paper_2406_01939_b300.session import DeviceBatch
+
+    B = args.B or 64
+    insts, mlp = synth.pg_large(args.seed + rank, B=B)
+    db = DeviceBatch(insts, device=dev)
+    T, N = db.T, insts[0].N
+    rf = Reinforce(db, ["gumbel"] * B, [1000 + b for b in range(B)], list(range(B)), insts[0].R,
+                   num_chunks=chunks_of(args), seg_window=args.seg_window)
+    master = flat_from_mlp(mlp, device=dev)
+    acts = torch.empty(T, dtype=torch.int8, device=dev)
+    grad = torch.empty_like(master)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        J, res = rf.objective(master, actions_out=acts)   # simulate + J
+        e1.record(stream)
+        rf.gradient(master, acts, grad)                    # backward kernel
+        e2.record(stream)
+        return J, res, (e0, e1, e2)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    clocks = Clocks(int(str(dev).split(":")[-1]) if ":" in str(dev) else 0)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    recs = []
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        recs.append(step())
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    fwd = [a.elapsed_time(b) for _, _, (a, b, c) in recs]
+    bwd = [b.elapsed_time(c) for _, _, (a, b, c) in recs]
+    t_ms = sum(f + g for f, g in zip(fwd, bwd))
+    if world > 1:
+        tt = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    value = world * T * args.steps / (t_ms / 1000.0)
+    J, res, _ = recs[-1]
+    bwd_ms = statistics.median(bwd)
+    flops = T * grad_flops_per_order(N)
+    achieved = flops / (bwd_ms / 1000.0) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32+f32", "data": "synthetic",
+        "config": {"workload": "pg_large",
+                   "desc": (f"policy-gradient step, B={B} trajectories x T=2^20 orders, N={N}, "
+                            f"K={insts[0].K}, R={insts[0].R}, Gumbel-max MLP policy, "
+                            "BF16(master) parameters; Picard simulation + REINFORCE gradient"),
+                   "B": B, "T_total": T, "N": N, "K": insts[0].K, "R": insts[0].R,
+                   "chunks_per_trajectory": res.num_chunks, "seg_window": res.seg_window,
+                   "l2": "inputs exceed L2; flushed between timed steps (256 MiB write)"},
+        "iters": res.iters, "objective": J,
+        "phases_ms": {"simulate_and_objective": statistics.median(fwd), "gradient": bwd_ms},
+        "policy_calls": res.policy_calls,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "gradient phase (k_pg_grad dominant)",
+                     "peak_kind": "derived: 148 SMs x 128 FP32 lanes x 2 FLOP x 2.032 GHz",
+                     "algorithmic_flops": flops},
+        "e2e": None,
+        "gpu_launches": None,
+        "clocks": clk,
+        "wall_s_timed_loop": wall,
+        "cpu_baseline": None,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    db.close()
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -467,8 +568,8 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
 
-    if args.workload == "batch_uneven":
-        run_batch(args, dev, world, rank)
+    if args.workload in ("batch_uneven", "pg_large"):
+        (run_batch if args.workload == "batch_uneven" else run_pg)(args, dev, world, rank)
         if world > 1:
             dist.barrier()
             dist.destroy_process_group()

@@ -71,10 +71,20 @@ enum {
     PIC_FLAG_GROUP_KERNEL = 8, /* tuning: replay each work unit with a group of 8 warehouses
                                   per lane instead of a whole warp (integer policies, costs
                                   that fit int16) */
-    PIC_FLAG_GRAPH = 16        /* pic_simulate_batch: run the per-call device work as a CUDA
+    PIC_FLAG_GRAPH = 16,       /* pic_simulate_batch: run the per-call device work as a CUDA
                                   graph, captured at the first call and relaunched while the
                                   chunking, CTA shape, MLP weight pointers, alpha_init, trace,
                                   max_iters, timeout and flags stay the same */
+    PIC_FLAG_NO_TC = 32,       /* MLP policies: score every decision with the FP32 scorer
+                                  (no tensor-core tiles; see PIC_FLAG_TC) */
+    PIC_FLAG_TC = 64           /* MLP policies (N <= 64), the default unless PIC_FLAG_NO_TC:
+                                  inside long runs of a product whose stocked warehouses all
+                                  hold more than 32 units, score up to 16 orders at a time on
+                                  the tensor cores (BF16 inputs, FP32 accumulation) and
+                                  re-score in FP32 every order whose top-2 margin is below
+                                  max(1e-3, twice a computed error bound); same results as the
+                                  FP32 scorer.  With num_chunks = 0 the batch autotuner
+                                  decides unless one of the two flags is given */
 };
 
 typedef struct pic_instance pic_instance;
@@ -130,7 +140,7 @@ typedef struct {
                              (1 for PIC_MODE_SEQUENTIAL); also the rows written to opts.trace
                              (at most trace_cap) */
     int32_t num_chunks;   /* M used */
-    int64_t rescored;     /* MLP decisions re-scored in FP32 after the BF16 pass */
+    int64_t rescored;     /* MLP tile rows re-scored in FP32 (top-2 margin below the bound) */
     int64_t seg_replays;  /* warp work units (segments) replayed, over all passes */
     int32_t launches;     /* kernels this call launched */
     float prep_ms;        /* PIC_FLAG_TIMING: order tables (sort, runs, segments) */
@@ -140,6 +150,9 @@ typedef struct {
     int32_t cta_threads;  /* threads per CTA of the Picard launch */
     int32_t ctas_per_sm;  /* CTAs per SM of the Picard launch */
     int64_t mlp_calls;    /* the policy_calls that evaluated an MLP / Gumbel policy */
+    int64_t tc_decisions; /* MLP decisions taken from tensor-core tile scores (the rest of
+                             mlp_calls ran the FP32 scorer; rescored counts tile rows sent
+                             back to it because their top-2 margin was too small) */
 } pic_sim_result;
 
 /* Per-trajectory result of pic_simulate_batch. */

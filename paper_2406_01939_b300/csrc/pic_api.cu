@@ -195,7 +195,7 @@ void free_instance(Instance& I) {
                     I.pstart, I.run_start, I.run_of, I.seg_run, I.seg_of_run, I.seg_prod, I.seg_cf,
                     I.seg_ce, I.seg_meta, I.seg_lpt, I.len_hist, I.alpha_s, I.agg, I.carry, I.sbagg,
                     I.sbincl, I.fc, I.xfin, I.xwork, I.act_t, I.tmp_a, I.tmp_b, I.tmp_c, I.scan_blk,
-                    I.hist, I.ctrl, I.trace, I.mlp_P, I.mlp_W1p, I.mlp_W2p, I.mlp_b2};
+                    I.hist, I.ctrl, I.trace, I.mlp_P, I.mlp_W1p, I.mlp_W2p, I.mlp_b2, I.mlp_Emax, I.mlp_bnd};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < 4; ++i)
@@ -491,6 +491,7 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
         res->cta_threads = opts->mode == PIC_MODE_PICARD ? I.cta_threads : 32;
         res->ctas_per_sm = opts->mode == PIC_MODE_PICARD ? I.ctas_per_sm : 1;
         res->rescored = (int64_t)hc.rescored;
+        res->tc_decisions = (int64_t)hc.tc_rows;
         res->seg_replays = (int64_t)hc.seg_replays;
         res->launches = I.launches;
         res->prep_ms = res->sim_ms = res->total_ms = 0.0f;

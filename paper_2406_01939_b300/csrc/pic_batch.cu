@@ -166,7 +166,7 @@ struct BatchArgs {
 constexpr int kNumShapes = 3;
 constexpr int kDefaultShape = 2;
 
-template <int NPL, int THREADS, int MINB, bool FULL>
+template <int NPL, int THREADS, int MINB, bool FULL, bool SPEC>
 __global__ void __launch_bounds__(THREADS, MINB) k_picard_batch(KArgs a, MlpPolicy p, BatchArgs b) {
     constexpr bool SMEMW = true;  // the packed weights (N KB) fit in shared memory for any N
     constexpr int WARPS = THREADS / 32;
@@ -178,7 +178,8 @@ __global__ void __launch_bounds__(THREADS, MINB) k_picard_batch(KArgs a, MlpPoli
     const uint4* W2p = s_w + p.N * kHidden / 8;
     const CostTable<false> ct{a.cost, nullptr, a.N};
     const int wib = threadIdx.x >> 5;
-    unsigned long long calls = 0, mcalls = 0;
+    unsigned long long calls = 0;
+    MlpCounts mc{0, 0, 0};
     picard_passes<NPL, WARPS>(a, calls, [&](int seg, const SegMeta& m, int fcp, int* fc_cur, int it) {
         const int tb = __ldg(b.traj_of_prod + m.k);
         const BatchPol bp = b.pol[tb];
@@ -191,23 +192,27 @@ __global__ void __launch_bounds__(THREADS, MINB) k_picard_batch(KArgs a, MlpPoli
             q.gumbel = bp.kind == PIC_POLICY_GUMBEL;
             q.seed = bp.seed;
             q.traj = bp.traj;
-            const unsigned long long m0 = mcalls;
-            chg = replay_segment_mlp<NPL, SMEMW>(a, q, W1p, W2p, b.perm, seg, m, fcp, fc_cur, it,
-                                                 __ldg(b.toff + tb), mcalls, s_fs[wib], s_hs[wib]);
-            calls += mcalls - m0;
+            const unsigned long long m0 = mc.calls;
+            chg = replay_segment_mlp<NPL, SMEMW, SPEC>(a, q, W1p, W2p, b.perm, seg, m, fcp, fc_cur, it,
+                                                 __ldg(b.toff + tb), mc, s_fs[wib], s_hs[wib]);
+            calls += mc.calls - m0;
         }
         // the trajectory's last changing pass (read first: many segments of one
         // trajectory change in the same pass)
         if (chg && lane_id() == 0 && ld_volatile(&b.last_chg[tb]) < it) atomicMax(&b.last_chg[tb], it);
         return chg;
     });
-    if (lane_id() == 0 && mcalls) atomicAdd(&a.ctrl->mlp_calls, mcalls);
+    if (lane_id() == 0 && mc.calls) {
+        atomicAdd(&a.ctrl->mlp_calls, mc.calls);
+        atomicAdd(&a.ctrl->rescored, mc.rescored);
+        atomicAdd(&a.ctrl->tc_rows, mc.tc);
+    }
 }
 
-template <int NPL, int THREADS, int MINB, bool FULL>
+template <int NPL, int THREADS, int MINB, bool FULL, bool SPEC>
 cudaError_t launch_batch(Instance* I, const KArgs& a, const MlpPolicy& p, const BatchArgs& b,
                          cudaStream_t st) {
-    auto kern = k_picard_batch<NPL, THREADS, MINB, FULL>;
+    auto kern = k_picard_batch<NPL, THREADS, MINB, FULL, SPEC>;
     const size_t smem = b.has_mlp ? packed_weight_bytes(I->N) : 0;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e) return e;
@@ -233,23 +238,32 @@ cudaError_t launch_batch(Instance* I, const KArgs& a, const MlpPolicy& p, const 
     return cudaLaunchKernelEx(&cfg, kern, a, p, b);
 }
 
-template <int NPL, bool FULL>
+template <int NPL, bool FULL, bool SPEC>
 cudaError_t batch_shape(Instance* I, int shape, const KArgs& a, const MlpPolicy& p,
                         const BatchArgs& b, cudaStream_t st) {
-    if (shape == 0) return launch_batch<NPL, 256, 1, FULL>(I, a, p, b, st);
-    if (shape == 1) return launch_batch<NPL, 256, 2, FULL>(I, a, p, b, st);
-    return launch_batch<NPL, 512, 1, FULL>(I, a, p, b, st);
+    if (shape == 0) return launch_batch<NPL, 256, 1, FULL, SPEC>(I, a, p, b, st);
+    if (shape == 1) return launch_batch<NPL, 256, 2, FULL, SPEC>(I, a, p, b, st);
+    return launch_batch<NPL, 512, 1, FULL, SPEC>(I, a, p, b, st);
 }
 
-cudaError_t batch_dispatch(Instance* I, int shape, const KArgs& a, const MlpPolicy& p,
+// tc: MLP decisions through speculative tensor-core tiles (N <= 64)
+cudaError_t batch_dispatch(Instance* I, int shape, bool tc, const KArgs& a, const MlpPolicy& p,
                            const BatchArgs& b, cudaStream_t st) {
     const int npl = (I->N + 31) / 32;
     const bool full = I->N == 32 * npl;  // every lane owns real warehouses
-    if (npl == 1) return full ? batch_shape<1, true>(I, shape, a, p, b, st)
-                              : batch_shape<1, false>(I, shape, a, p, b, st);
-    if (npl == 2) return full ? batch_shape<2, true>(I, shape, a, p, b, st)
-                              : batch_shape<2, false>(I, shape, a, p, b, st);
-    return batch_shape<4, false>(I, shape, a, p, b, st);
+    if (npl == 1) {
+        if (tc) return full ? batch_shape<1, true, true>(I, shape, a, p, b, st)
+                            : batch_shape<1, false, true>(I, shape, a, p, b, st);
+        return full ? batch_shape<1, true, false>(I, shape, a, p, b, st)
+                    : batch_shape<1, false, false>(I, shape, a, p, b, st);
+    }
+    if (npl == 2) {
+        if (tc) return full ? batch_shape<2, true, true>(I, shape, a, p, b, st)
+                            : batch_shape<2, false, true>(I, shape, a, p, b, st);
+        return full ? batch_shape<2, true, false>(I, shape, a, p, b, st)
+                    : batch_shape<2, false, false>(I, shape, a, p, b, st);
+    }
+    return batch_shape<4, false, false>(I, shape, a, p, b, st);
 }
 
 template <int NPL>
@@ -294,6 +308,7 @@ pic_status cuda_fail(cudaError_t e, const char* what, int line) {
 // policy selectors (which travel through bt->h_pol).
 struct CallCfg {
     int M, W, shape, iters_cap, flags;
+    bool tc;  // speculative tensor-core tiles for the MLP decisions
     const int8_t* alpha_init;
     bool trace;
     unsigned long long timeout_ns;
@@ -312,7 +327,7 @@ unsigned long long fnv(unsigned long long h, const void* p, size_t n) {
 
 unsigned long long cfg_sig(const CallCfg& c) {
     unsigned long long h = 14695981039346656037ull;
-    const long long v[] = {c.M, c.W, c.shape, c.iters_cap, c.flags, (long long)(size_t)c.alpha_init,
+    const long long v[] = {c.M, c.W, c.shape, c.tc, c.iters_cap, c.flags, (long long)(size_t)c.alpha_init,
                            c.trace, (long long)c.timeout_ns, c.has_mlp,
                            (long long)(size_t)c.mlp.W1, (long long)(size_t)c.mlp.b1,
                            (long long)(size_t)c.mlp.W2, (long long)(size_t)c.mlp.b2,
@@ -373,7 +388,7 @@ pic_status enqueue_picard(Instance& I, const CallCfg& c, cudaStream_t st) {
     ba.perm = I.perm;
     ba.last_chg = bt->last_chg;
     ba.has_mlp = c.has_mlp ? 1 : 0;
-    BCU(batch_dispatch(&I, c.shape, a, p, ba, st));
+    BCU(batch_dispatch(&I, c.shape, c.tc && I.N <= 64, a, p, ba, st));
     BCU(scatter_actions(&I, st));
     I.launches += 1;
     k_traj_reduce<<<B, kReduceThreads, 0, st>>>(I.act_t, I.reg, I.cost, I.N, bt->toff, bt->tres, I.ctrl);
@@ -449,14 +464,16 @@ pic_status autotune(Instance& I, CallCfg& c, cudaStream_t st) {
         c.M = bt->tune_m;
         c.W = bt->tune_w;
         c.shape = bt->tune_shape;
+        c.tc = bt->tune_tc != 0;
         return PIC_OK;
     }
     const int max_t = bt->max_t > 0 ? bt->max_t : 1;
-    auto trial = [&](int M, int W, int shape, float* ms) -> pic_status {
+    auto trial = [&](int M, int W, int shape, bool tc, float* ms) -> pic_status {
         CallCfg t = c;
         t.M = M;
         t.W = W;
         t.shape = shape;
+        t.tc = tc;
         t.iters_cap = (M < max_t ? M : max_t) + 1;
         t.trace = false;
         pic_status s = run_picard(I, t, false, st);
@@ -469,19 +486,25 @@ pic_status autotune(Instance& I, CallCfg& c, cudaStream_t st) {
         return PIC_OK;
     };
     const int w_def = c.has_mlp ? kSegWindowMlp : kSegWindow;
+    // tensor-core tiles are a tuning choice unless a flag fixes them
+    const bool tc_free = c.has_mlp && I.N <= 64 && !(c.flags & (PIC_FLAG_TC | PIC_FLAG_NO_TC));
+    bool bestT = c.tc;
     int bestM = 0, bestW = w_def, bestS = kDefaultShape;
     float best = 3.4e38f;
     for (int M = 4; M <= 1024; M *= 2) {
         if (M > 4 && M / 2 >= max_t) break;  // larger M only repeats min(M, T_b) = T_b
-        float ms;
-        pic_status s = trial(M, w_def, kDefaultShape, &ms);
-        if (s != PIC_OK) return s;
-        if (ms < best) { best = ms; bestM = M; }
+        for (int tcv = 0; tcv < (tc_free ? 2 : 1); ++tcv) {
+            const bool tc = tc_free ? tcv == 1 : c.tc;
+            float ms;
+            pic_status s = trial(M, w_def, kDefaultShape, tc, &ms);
+            if (s != PIC_OK) return s;
+            if (ms < best) { best = ms; bestM = M; bestT = tc; }
+        }
     }
     for (int sh = 0; sh < kNumShapes; ++sh) {
         if (sh == kDefaultShape) continue;
         float ms;
-        pic_status s = trial(bestM, w_def, sh, &ms);
+        pic_status s = trial(bestM, w_def, sh, bestT, &ms);
         if (s != PIC_OK) return s;
         if (ms < best) { best = ms; bestS = sh; }
     }
@@ -489,7 +512,7 @@ pic_status autotune(Instance& I, CallCfg& c, cudaStream_t st) {
     for (int i = 0; i < 3; ++i) {
         const int W = c.has_mlp ? wins_mlp[i] : wins_int[i];
         float ms;
-        pic_status s = trial(bestM, W, bestS, &ms);
+        pic_status s = trial(bestM, W, bestS, bestT, &ms);
         if (s != PIC_OK) return s;
         if (ms < best) { best = ms; bestW = W; }
     }
@@ -497,9 +520,11 @@ pic_status autotune(Instance& I, CallCfg& c, cudaStream_t st) {
     bt->tune_m = bestM;
     bt->tune_w = bestW;
     bt->tune_shape = bestS;
+    bt->tune_tc = bestT ? 1 : 0;
     c.M = bestM;
     c.W = bestW;
     c.shape = bestS;
+    c.tc = bestT;
     return PIC_OK;
 }
 
@@ -717,6 +742,7 @@ pic_status pic_simulate_batch(pic_instance* h, const pic_policy* pols, const pic
                             sizeof(int32_t) * B, cudaMemcpyDeviceToHost, st));
     } else {
         c.flags = opts->flags & ~(PIC_FLAG_TIMING | PIC_FLAG_GRAPH | PIC_FLAG_REUSE_TABLES);
+        c.tc = (opts->flags & PIC_FLAG_NO_TC) == 0 && I.N <= 64;
         c.alpha_init = opts->alpha_init;
         c.trace = opts->trace && opts->trace_cap > 0;
         c.timeout_ns = opts->timeout_ns ? opts->timeout_ns : 60000000000ull;
@@ -779,6 +805,7 @@ pic_status pic_simulate_batch(pic_instance* h, const pic_policy* pols, const pic
         res->seg_replays = (int64_t)hc.seg_replays;
         res->launches = I.launches;
         res->mlp_calls = picard ? (int64_t)hc.mlp_calls : 0;
+        res->tc_decisions = picard ? (int64_t)hc.tc_rows : 0;
         if (!picard)
             for (int b = 0; b < B; ++b)
                 if (bt->h_pol[b].kind >= PIC_POLICY_MLP) res->mlp_calls += bt->h_toff[b + 1] - bt->h_toff[b];

@@ -35,6 +35,7 @@ struct Ctrl {
     unsigned long long rescored;
     unsigned long long seg_replays;
     unsigned long long mlp_calls;  // MLP / Gumbel policy evaluations (batch kernel)
+    unsigned long long tc_rows;    // MLP decisions taken from tensor-core tile scores
     int nruns;               // tables built by the preprocessing kernels
     int nseg;
     int last_m;              // chunk count the tables were built for
@@ -87,7 +88,7 @@ struct Batch {
     cudaStream_t cap_stream;
     // autotuner result and the policy signature it was tuned for
     unsigned long long tune_sig;
-    int tune_m, tune_w, tune_shape;
+    int tune_m, tune_w, tune_shape, tune_tc;
 };
 
 struct PgState;  // buffers of the policy gradient (pic_pg.cu)
@@ -136,6 +137,8 @@ struct Instance {
     uint4 *mlp_W1p;     // [N][32] packed BF16 stock rows of W1
     uint4 *mlp_W2p;     // [32][N] packed BF16 W2
     float *mlp_b2;      // [N]
+    float *mlp_Emax;    // [R] error-bound constant per region (tensor-core tiles)
+    float *mlp_bnd;     // [2] max column sum of |W2|, max |b2|
     // scratch for the sort and scans
     int32_t *tmp_a, *tmp_b, *tmp_c;   // [T] each
     int32_t *scan_blk;                // block sums

@@ -52,6 +52,53 @@ __global__ void k_mlp_prefix(MlpArgs m) {
     if (idx < N) m.b2f[idx] = bf16f(m.b2[idx]);
 }
 
+// Error-bound constants of the tensor-core tiles.  C1[j] = sum_n |W1s[n][j]| and
+// the scalars bnd = {max_n sum_j |W2[j][n]|, max_n |b2[n]|} (one block), then
+// Emax[r] = max_j (|P[r][j]| + C1[j]) (one warp per region).  Sums are rounded
+// up by a relative 2^-16 so that they bound the exact values.
+__global__ void k_mlp_consts(int N, const uint16_t* __restrict__ W1, const uint16_t* __restrict__ W2,
+                             const uint16_t* __restrict__ b2, float* __restrict__ C1,
+                             float* __restrict__ bnd) {
+    __shared__ float red[2][kHidden];
+    const int j = threadIdx.x;  // blockDim = kHidden
+    float c1 = 0.f;
+    for (int n = 0; n < N; ++n) c1 += fabsf(bf16f(W1[(size_t)(N + n) * kHidden + j]));
+    C1[j] = c1 * (1.0f + 1.0f / 65536.0f);
+    float c2 = 0.f, bb = 0.f;
+    if (j < N) {
+        for (int jj = 0; jj < kHidden; ++jj) c2 += fabsf(bf16f(W2[(size_t)jj * N + j]));
+        bb = fabsf(bf16f(b2[j]));
+    }
+    red[0][j] = c2;
+    red[1][j] = bb;
+    __syncthreads();
+    for (int o = kHidden / 2; o > 0; o >>= 1) {
+        if (j < o) {
+            red[0][j] = fmaxf(red[0][j], red[0][j + o]);
+            red[1][j] = fmaxf(red[1][j], red[1][j + o]);
+        }
+        __syncthreads();
+    }
+    if (j == 0) {
+        bnd[0] = red[0][0] * (1.0f + 1.0f / 65536.0f);
+        bnd[1] = red[1][0];
+    }
+}
+
+__global__ void k_mlp_emax(int R, const float* __restrict__ P, const float* __restrict__ C1,
+                           float* __restrict__ Emax) {
+    const int lane = lane_id();
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int r = gw; r < R; r += nw) {
+        float m = 0.f;
+        for (int j = lane; j < kHidden; j += 32) m = fmaxf(m, fabsf(P[(size_t)r * kHidden + j]) + C1[j]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
+        if (lane == 0) Emax[r] = m * (1.0f + 1.0f / 65536.0f);
+    }
+}
+
 // ---------------------------------------------------------------- sequential simulator
 template <int NPL, bool SMEMW>
 __global__ void __launch_bounds__(32) k_seq_mlp(int T, int N, const int32_t* __restrict__ prod,
@@ -73,7 +120,7 @@ __global__ void __launch_bounds__(32) k_seq_mlp(int T, int N, const int32_t* __r
 
 constexpr int kMlpThreads = 256;
 
-template <int NPL, bool SMEMW>
+template <int NPL, bool SMEMW, bool SPEC>
 __global__ void __launch_bounds__(kMlpThreads, 2) k_picard_mlp(KArgs a, MlpPolicy p,
                                                               const int32_t* __restrict__ perm) {
     extern __shared__ uint4 s_w[];
@@ -84,16 +131,24 @@ __global__ void __launch_bounds__(kMlpThreads, 2) k_picard_mlp(KArgs a, MlpPolic
     const uint4* W2p = SMEMW ? s_w + p.N * kHidden / 8 : p.W2p;
     const int wib = threadIdx.x >> 5;
     unsigned long long calls = 0;
+    MlpCounts mc{0, 0, 0};
     picard_passes<NPL, kMlpThreads / 32>(
         a, calls, [&](int seg, const SegMeta& m, int fcp, int* fc_cur, int it) {
-            return replay_segment_mlp<NPL, SMEMW>(a, p, W1p, W2p, perm, seg, m, fcp, fc_cur, it, 0,
-                                                  calls, s_fs[wib], s_hs[wib]);
+            const unsigned long long c0 = mc.calls;
+            const bool chg = replay_segment_mlp<NPL, SMEMW, SPEC>(a, p, W1p, W2p, perm, seg, m, fcp, fc_cur,
+                                                            it, 0, mc, s_fs[wib], s_hs[wib]);
+            calls += mc.calls - c0;
+            return chg;
         });
+    if (lane_id() == 0 && (mc.rescored || mc.tc)) {
+        atomicAdd(&a.ctrl->rescored, mc.rescored);
+        atomicAdd(&a.ctrl->tc_rows, mc.tc);
+    }
 }
 
-template <int NPL, bool SMEMW>
+template <int NPL, bool SMEMW, bool SPEC>
 cudaError_t launch_picard_mlp(Instance* I, const KArgs& a, const MlpPolicy& p, cudaStream_t st) {
-    auto kern = k_picard_mlp<NPL, SMEMW>;
+    auto kern = k_picard_mlp<NPL, SMEMW, SPEC>;
     const size_t smem = SMEMW ? packed_weight_bytes(I->N) : 0;
     cudaError_t e;
     if (SMEMW && (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
@@ -134,6 +189,8 @@ cudaError_t mlp_alloc(Instance* I) {
     if (!e) e = cudaMalloc((void**)&I->mlp_W1p, sizeof(uint4) * (size_t)I->N * 32);
     if (!e) e = cudaMalloc((void**)&I->mlp_W2p, sizeof(uint4) * (size_t)I->N * (kHidden / 8));
     if (!e) e = cudaMalloc((void**)&I->mlp_b2, sizeof(float) * (size_t)I->N);
+    if (!e) e = cudaMalloc((void**)&I->mlp_Emax, sizeof(float) * ((size_t)I->R + kHidden));
+    if (!e) e = cudaMalloc((void**)&I->mlp_bnd, sizeof(float) * 2);
     return e;
 }
 
@@ -145,8 +202,11 @@ cudaError_t mlp_prepare(Instance* I, const pic_policy* pol, cudaStream_t st) {
     m.reg_local = I->batch ? I->batch->reg_local : nullptr;
     m.P = I->mlp_P; m.W1p = I->mlp_W1p; m.W2p = I->mlp_W2p; m.b2f = I->mlp_b2;
     const int n = I->R * kHidden > I->N * kHidden ? I->R * kHidden : I->N * kHidden;
-    I->launches += 1;
+    I->launches += 3;
     k_mlp_prefix<<<(n + 255) / 256, 256, 0, st>>>(m);
+    float* C1 = I->mlp_Emax + I->R;  // scratch after the per-region values
+    k_mlp_consts<<<1, kHidden, 0, st>>>(I->N, pol->W1, pol->W2, pol->b2, C1, I->mlp_bnd);
+    k_mlp_emax<<<(I->R + 7) / 8, 256, 0, st>>>(I->R, I->mlp_P, C1, I->mlp_Emax);
     return cudaGetLastError();
 }
 
@@ -161,11 +221,12 @@ cudaError_t sequential_mlp(Instance* I, const pic_policy* pol, cudaStream_t st) 
 
 cudaError_t picard_mlp(Instance* I, const KArgs& a, const pic_policy* pol, cudaStream_t st) {
     const MlpPolicy p = make_policy_view(I, pol);
+    // the packed weights fit in shared memory for every N <= 127; tiles need N <= 64
+    const bool tc = (a.flags & PIC_FLAG_NO_TC) == 0 && I->N <= 64;
     const int npl = (I->N + 31) / 32;
-    const bool sw = smem_weights_ok(I->N);
-    if (npl == 1) return sw ? launch_picard_mlp<1, true>(I, a, p, st) : launch_picard_mlp<1, false>(I, a, p, st);
-    if (npl == 2) return sw ? launch_picard_mlp<2, true>(I, a, p, st) : launch_picard_mlp<2, false>(I, a, p, st);
-    return sw ? launch_picard_mlp<4, true>(I, a, p, st) : launch_picard_mlp<4, false>(I, a, p, st);
+    if (npl == 1) return tc ? launch_picard_mlp<1, true, true>(I, a, p, st) : launch_picard_mlp<1, true, false>(I, a, p, st);
+    if (npl == 2) return tc ? launch_picard_mlp<2, true, true>(I, a, p, st) : launch_picard_mlp<2, true, false>(I, a, p, st);
+    return launch_picard_mlp<4, true, false>(I, a, p, st);
 }
 
 }  // namespace pic

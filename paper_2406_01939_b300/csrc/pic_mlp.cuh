@@ -24,6 +24,8 @@
 // that no contraction changes the bits.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "pic_picard.cuh"
 
 namespace pic {
@@ -103,9 +105,20 @@ struct MlpPolicy {
     const uint4* __restrict__ W1p;
     const uint4* __restrict__ W2p;
     const float* __restrict__ b2f;
+    // error-bound constants of the tensor-core scorer (k_mlp_bounds): Emax[r] =
+    // max_j (|P[r][j]| + sum_n |W1s[n][j]|); bnd[0] = max_n sum_j |W2[j][n]|,
+    // bnd[1] = max_n |b2[n]|
+    const float* __restrict__ Emax;
+    const float* __restrict__ bnd;
     bool gumbel;
     unsigned long long seed;
     int traj;
+};
+
+// Counters of one warp's MLP decisions: evaluations, tile rows re-scored in
+// FP32, tile rows decided by the tensor-core scores.
+struct MlpCounts {
+    unsigned long long calls, rescored, tc;
 };
 
 // Packed weights read from shared memory (staged copy) or global memory.
@@ -185,6 +198,196 @@ __device__ __forceinline__ int mlp_decide(const MlpPolicy& p, const uint4* W1p, 
     return stocked ? n : -1;
 }
 
+// ---------------------------------------------------------------- speculative tensor-core tiles
+// Inside one run the stock features min(x[k][n], 32)/32 stay the same from order
+// to order until a decrement takes some warehouse below 32 units.  For the next
+// L <= 16 orders of the run the warp therefore scores all of them at once from
+// the current state: c = W1s^T f (FP32, shared by the rows), h_t = max(P[r_t] +
+// c, 0) rounded to BF16, and s_t = h_t W2 (+ b2) and u_t = h_t |W2| with
+// mma.sync m16n8k16 (BF16 inputs, FP32 accumulation).  A row's decision is the
+// FP32 scorer's exactly when its top-2 margin among stocked warehouses exceeds
+// max(1e-3, 2 B) with B a bound on |s_tc - s_fp32| for that row:
+//   |z_tc - z_fp32| <= e1 = 2^-22 (N + 2) Emax[r]      (two FP32 chains of N terms),
+//   B = 2.1e-3 max_n u_n + 1.01 e1 max_n sum_j |W2_jn| + 1.6e-5 max|b2| + 2^-21 |key|
+// (BF16 rounding of h, relative 2^-9; the two 256-term FP32 sums; the key's own
+// roundings).  Other rows are re-scored by mlp_decide.  Returns, on lane l < L,
+// the action of row l (-2: re-score), and the lanes' state is unchanged.
+constexpr int kTile = 16;
+constexpr int kSpecMin = 8;          // shortest run remainder scored by a tile
+constexpr float kTieMargin = 1e-3f;  // re-score rows whose top-2 margin is below this
+
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const unsigned*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16(float d[4], unsigned a0, unsigned a1, unsigned a2,
+                                         unsigned a3, unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// Top-2 keys (and the arg max, lowest index on ties) of one row, merged over lanes.
+struct Top2 {
+    float k1, k2, um;
+    int i1;
+    __device__ __forceinline__ void add(float key, int n, float u) {
+        if (key > k1 || (key == k1 && n < i1)) {
+            k2 = k1;
+            k1 = key;
+            i1 = n;
+        } else if (key > k2) {
+            k2 = key;
+        }
+        um = fmaxf(um, u);
+    }
+    __device__ __forceinline__ void merge_xor(int m) {
+        const float o1 = __shfl_xor_sync(kFull, k1, m), o2 = __shfl_xor_sync(kFull, k2, m);
+        const float ou = __shfl_xor_sync(kFull, um, m);
+        const int oi = __shfl_xor_sync(kFull, i1, m);
+        if (o1 > k1 || (o1 == k1 && oi < i1)) {
+            k2 = fmaxf(k1, o2);
+            k1 = o1;
+            i1 = oi;
+        } else {
+            k2 = fmaxf(k2, o1);
+        }
+        um = fmaxf(um, ou);
+    }
+};
+
+template <int NPL, bool SMEMW>
+__device__ __noinline__ int spec_tile(const MlpPolicy& p, const uint4* W1p, const uint4* W2p,
+                                      int S0, int S1, int L, const int32_t* __restrict__ reg_s,
+                                      const int32_t* __restrict__ perm, int j, int t_off, float* fs,
+                                      float* hs) {
+    const int lane = lane_id();
+    const int N = p.N;
+    const int S[2] = {S0, S1};  // warehouses lane and lane + 32 (N <= 64)
+    const unsigned m0 = __ballot_sync(kFull, lane < N && S0 > 0);
+    const unsigned m1 = NPL > 1 ? __ballot_sync(kFull, lane + 32 < N && S1 > 0) : 0u;
+    const int nfeas = __popc(m0) + __popc(m1);
+    if (nfeas <= 1)  // nothing to choose: a^phi, or the one stocked warehouse
+        return nfeas == 0 ? -1 : (m0 ? __ffs(m0) - 1 : 32 + __ffs(m1) - 1);
+    // c = W1s^T f, shared by the rows (the same chain as mlp_decide, from 0)
+#pragma unroll
+    for (int i = 0; i < (NPL < 2 ? NPL : 2); ++i) {
+        const int n = lane + 32 * i;
+        if (n < N) fs[n] = __fdiv_rn((float)min(S[i], 32), 32.0f);
+    }
+    __syncwarp();
+    {
+        float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int n = 0; n < N; ++n) {
+            const float f = fs[n];
+            const uint4 w = wld4<SMEMW>(W1p + n * 32 + lane);
+            acc[0] = fmaf(lo16(w.x), f, acc[0]);
+            acc[1] = fmaf(hi16(w.x), f, acc[1]);
+            acc[2] = fmaf(lo16(w.y), f, acc[2]);
+            acc[3] = fmaf(hi16(w.y), f, acc[3]);
+            acc[4] = fmaf(lo16(w.z), f, acc[4]);
+            acc[5] = fmaf(hi16(w.z), f, acc[5]);
+            acc[6] = fmaf(lo16(w.w), f, acc[6]);
+            acc[7] = fmaf(hi16(w.w), f, acc[7]);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) hs[lane + 32 * u] = acc[u];
+    }
+    __syncwarp();
+    // rows g and g + 8 of the fragments
+    const int g = lane >> 2, c = lane & 3;
+    const bool okA = g < L, okB = g + 8 < L;
+    const int rA = okA ? reg_s[j + g] : -1, rB = okB ? reg_s[j + g + 8] : -1;
+    const int tA = okA ? perm[j + g] - t_off : 0, tB = okB ? perm[j + g + 8] - t_off : 0;
+    const float* PA = p.P + (size_t)(rA < 0 ? 0 : rA) * kHidden;
+    const float* PB = p.P + (size_t)(rB < 0 ? 0 : rB) * kHidden;
+    const unsigned* W2u = reinterpret_cast<const unsigned*>(W2p);
+    Top2 A{-INFINITY, -INFINITY, 0.f, INT_MAX}, Bq{-INFINITY, -INFINITY, 0.f, INT_MAX};
+    const int ntiles = (N + 7) >> 3;
+    for (int nt0 = 0; nt0 < ntiles; nt0 += 4) {
+        float sacc[4][4], uacc[4][4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) sacc[t][e] = uacc[t][e] = 0.f;
+#pragma unroll 2
+        for (int kk = 0; kk < kHidden / 16; ++kk) {
+            const int k0 = 16 * kk + 2 * c;
+            const float2 c0 = *reinterpret_cast<const float2*>(hs + k0);
+            const float2 c1 = *reinterpret_cast<const float2*>(hs + k0 + 8);
+            float2 pa0 = make_float2(0.f, 0.f), pa1 = pa0, pb0 = pa0, pb1 = pa0;
+            if (okA) {
+                pa0 = __ldg(reinterpret_cast<const float2*>(PA + k0));
+                pa1 = __ldg(reinterpret_cast<const float2*>(PA + k0 + 8));
+            }
+            if (okB) {
+                pb0 = __ldg(reinterpret_cast<const float2*>(PB + k0));
+                pb1 = __ldg(reinterpret_cast<const float2*>(PB + k0 + 8));
+            }
+            const unsigned a0 = pack_bf16(fmaxf(pa0.x + c0.x, 0.f), fmaxf(pa0.y + c0.y, 0.f));
+            const unsigned a1 = pack_bf16(fmaxf(pb0.x + c0.x, 0.f), fmaxf(pb0.y + c0.y, 0.f));
+            const unsigned a2 = pack_bf16(fmaxf(pa1.x + c1.x, 0.f), fmaxf(pa1.y + c1.y, 0.f));
+            const unsigned a3 = pack_bf16(fmaxf(pb1.x + c1.x, 0.f), fmaxf(pb1.y + c1.y, 0.f));
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int n = 8 * (nt0 + t) + g;
+                unsigned b0 = 0u, b1 = 0u;
+                if (nt0 + t < ntiles && n < N) {
+                    b0 = SMEMW ? W2u[((2 * kk) * N + n) * 4 + c] : __ldg(W2u + ((2 * kk) * N + n) * 4 + c);
+                    b1 = SMEMW ? W2u[((2 * kk + 1) * N + n) * 4 + c]
+                               : __ldg(W2u + ((2 * kk + 1) * N + n) * 4 + c);
+                }
+                mma_bf16(sacc[t], a0, a1, a2, a3, b0, b1);
+                mma_bf16(uacc[t], a0, a1, a2, a3, b0 & 0x7FFF7FFFu, b1 & 0x7FFF7FFFu);
+            }
+        }
+        // candidates of this lane: warehouses 8 (nt0 + t) + 2c + {0, 1}
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int n0 = 8 * (nt0 + t) + 2 * c;
+            if (nt0 + t >= ntiles || n0 >= N) continue;
+            float gA[4], gB[4];
+            if (p.gumbel) {
+                gumbel4(p.seed, p.traj, tA, n0 >> 2, gA);
+                gumbel4(p.seed, p.traj, tB, n0 >> 2, gB);
+            }
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int n = n0 + e;
+                if (n >= N) continue;
+                const bool feas = ((n < 32 ? m0 >> n : m1 >> (n - 32)) & 1u) != 0;
+                if (!feas) continue;
+                const float b2 = __ldg(p.b2f + n);
+                float kA = __fadd_rn(sacc[t][e], b2), kB = __fadd_rn(sacc[t][2 + e], b2);
+                if (p.gumbel) {
+                    kA = __fadd_rn(kA, gA[n & 3]);
+                    kB = __fadd_rn(kB, gB[n & 3]);
+                }
+                A.add(kA, n, uacc[t][e]);
+                Bq.add(kB, n, uacc[t][2 + e]);
+            }
+        }
+    }
+    A.merge_xor(1);
+    A.merge_xor(2);
+    Bq.merge_xor(1);
+    Bq.merge_xor(2);
+    const float c2max = __ldg(p.bnd), b2max = __ldg(p.bnd + 1);
+    const float e1A = okA ? ldexpf((float)(N + 2), -22) * __ldg(p.Emax + rA) : 0.f;
+    const float e1B = okB ? ldexpf((float)(N + 2), -22) * __ldg(p.Emax + rB) : 0.f;
+    const float bA = 2.1e-3f * A.um + 1.01f * e1A * c2max + 1.6e-5f * b2max + ldexpf(fabsf(A.k1), -21);
+    const float bB = 2.1e-3f * Bq.um + 1.01f * e1B * c2max + 1.6e-5f * b2max + ldexpf(fabsf(Bq.k1), -21);
+    const int resA = (A.k1 - A.k2 > fmaxf(kTieMargin, 2.f * bA)) ? A.i1 : -2;
+    const int resB = (Bq.k1 - Bq.k2 > fmaxf(kTieMargin, 2.f * bB)) ? Bq.i1 : -2;
+    const int fromA = __shfl_sync(kFull, resA, (lane & 7) * 4);
+    const int fromB = __shfl_sync(kFull, resB, (lane & 7) * 4);
+    __syncwarp();  // hs / fs reused by the caller
+    return lane < 8 ? fromA : fromB;
+}
+
 // Bytes of the packed weights (W1p then W2p).
 __host__ __device__ __forceinline__ size_t packed_weight_bytes(int N) {
     return (size_t)2 * N * kHidden * sizeof(uint16_t);
@@ -230,11 +433,11 @@ __device__ __forceinline__ void seq_mlp_body(int T, int N, const int32_t* __rest
 }
 
 // ---------------------------------------------------------------- Picard, one warp per segment
-template <int NPL, bool SMEMW>
+template <int NPL, bool SMEMW, bool SPEC>
 __device__ bool replay_segment_mlp(const KArgs& a, const MlpPolicy& p, const uint4* W1p,
                                    const uint4* W2p, const int32_t* __restrict__ perm, int s,
                                    const SegMeta& m, int fcp, int* fc_cur, int it, int t_off,
-                                   unsigned long long& calls, float* fs, float* hs) {
+                                   MlpCounts& cnt_out, float* fs, float* hs) {
     const int lane = lane_id();
     const int N = a.N, NP = a.NP;
     const int k = m.k;
@@ -254,8 +457,9 @@ __device__ bool replay_segment_mlp(const KArgs& a, const MlpPolicy& p, const uin
     int r = m.r0;
     int next_run = a.run_start[r + 1];
     bool eval = m.j0 > fcp;
-    unsigned long long evals = 0;
+    unsigned long long evals = 0, resc = 0, tcr = 0;
     int first_chg = INT_MAX;
+    int spec_act = -2, spec_base = 0, spec_left = 0;  // current tile (rows left)
     for (int base = m.j0; base < m.jend; base += 32) {
         const int cnt = min(32, m.jend - base);
         const int my_reg = lane < cnt ? a.reg_s[base + lane] : 0;
@@ -275,17 +479,52 @@ __device__ bool replay_segment_mlp(const KArgs& a, const MlpPolicy& p, const uin
                 eval = next_run > fcp;
                 ++r;
                 next_run = a.run_start[r + 1];
+                spec_left = 0;  // the state jumps to the next run's start
             }
             const int rr = __shfl_sync(kFull, my_reg, q);
             const int ao = __shfl_sync(kFull, my_old, q);
             const int tt = __shfl_sync(kFull, my_t, q);
             int act = ao;
             if (eval) {
-                act = mlp_decide<NPL, SMEMW>(p, W1p, W2p, S, rr, tt, fs, hs);
                 ++evals;
+                // a tile needs N <= 64 (two warehouses per lane), enough orders left in
+                // the run, and every stocked warehouse above 32 units, so that no early
+                // decrement can change a feature and waste the tile
+                if (SPEC && NPL <= 2 && spec_left == 0 && next_run - (base + q) >= kSpecMin) {
+                    bool low = false;
+#pragma unroll
+                    for (int i = 0; i < NPL; ++i) low |= S[i] > 0 && S[i] <= 32;
+                    if (!__any_sync(kFull, low)) {
+                        const int L = min(kTile, next_run - (base + q));
+                        spec_act = spec_tile<NPL, SMEMW>(p, W1p, W2p, S[0], S[NPL > 1 ? 1 : 0], L,
+                                                         a.reg_s, perm, base + q, t_off, fs, hs);
+                        spec_base = base + q;
+                        spec_left = L;
+                    }
+                }
+                int sa = -3;  // -3: no tile; -2: tile row to re-score
+                if (spec_left > 0) {
+                    sa = __shfl_sync(kFull, spec_act, base + q - spec_base);
+                    --spec_left;
+                }
+                if (sa < -1) {
+                    act = mlp_decide<NPL, SMEMW>(p, W1p, W2p, S, rr, tt, fs, hs);
+                    resc += sa == -2;
+                } else {
+                    act = sa;
+                    ++tcr;
+                }
             }
 #pragma unroll
             for (int i = 0; i < NPL; ++i) S[i] -= (act == lane + 32 * i);
+            if (spec_left > 0 && act >= 0) {
+                // a warehouse below 32 units changes its feature: the tile is stale
+                int sel = S[0];
+#pragma unroll
+                for (int i = 1; i < NPL; ++i)
+                    if ((act >> 5) == i) sel = S[i];
+                if (__shfl_sync(kFull, sel, act & 31) < 32) spec_left = 0;
+            }
             if (act != ao) {
 #pragma unroll
                 for (int i = 0; i < NPL; ++i) corr[i] += (ao == lane + 32 * i) - (act == lane + 32 * i);
@@ -310,7 +549,11 @@ __device__ bool replay_segment_mlp(const KArgs& a, const MlpPolicy& p, const uin
             if (n < N) a.xfin[(size_t)k * N + n] = S[i];
         }
     }
-    if (lane == 0) calls += evals;
+    if (lane == 0) {
+        cnt_out.calls += evals;
+        cnt_out.rescored += resc;
+        cnt_out.tc += tcr;
+    }
     return first_chg != INT_MAX;
 }
 
@@ -323,6 +566,8 @@ inline MlpPolicy make_policy_view(const Instance* I, const pic_policy* pol) {
     p.W1p = I->mlp_W1p;
     p.W2p = I->mlp_W2p;
     p.b2f = I->mlp_b2;
+    p.Emax = I->mlp_Emax;
+    p.bnd = I->mlp_bnd;
     p.gumbel = pol->kind == PIC_POLICY_GUMBEL;
     p.seed = pol->seed;
     p.traj = pol->traj;

@@ -40,12 +40,13 @@ class Reinforce:
     """Policy-gradient objective over a DeviceBatch.  kinds: 'mlp' or 'gumbel'
     per trajectory; seeds / trajs key the Gumbel noise."""
 
-    def __init__(self, batch, kinds, seeds, trajs, e_rows, num_chunks=0, seg_window=0, stream=None):
+    def __init__(self, batch, kinds, seeds, trajs, e_rows, num_chunks=0, seg_window=0, stream=None,
+                 flags=0):
         self.batch = batch
         self.e_rows = int(e_rows)
         self.pols = [make_policy(k, hidden=256, seed=int(s), traj=int(t))
                      for k, s, t in zip(kinds, seeds, trajs)]
-        self.opts = make_opts("picard", num_chunks, seg_window=seg_window, stream=stream)
+        self.opts = make_opts("picard", num_chunks, seg_window=seg_window, stream=stream, flags=flags)
         self.last_actions = None
         self.last_result = None
 

@@ -87,7 +87,7 @@ class DeviceInstance:
                 "seg_replays": res.seg_replays, "launches": res.launches, "prep_ms": res.prep_ms,
                 "sim_ms": res.sim_ms, "total_ms": res.total_ms, "seg_window": res.seg_window,
                 "cta_threads": res.cta_threads, "ctas_per_sm": res.ctas_per_sm,
-                "mlp_calls": res.mlp_calls}
+                "mlp_calls": res.mlp_calls, "tc_decisions": res.tc_decisions}
 
     def close(self):
         if self.handle:
@@ -175,7 +175,8 @@ class DeviceBatch:
                 "lost": res.lost, "iters": res.iters, "policy_calls": res.policy_calls,
                 "num_chunks": res.num_chunks, "seg_window": res.seg_window,
                 "cta_threads": res.cta_threads, "ctas_per_sm": res.ctas_per_sm,
-                "mlp_calls": res.mlp_calls, "seg_replays": res.seg_replays, "launches": res.launches, "prep_ms": res.prep_ms,
+                "mlp_calls": res.mlp_calls, "tc_decisions": res.tc_decisions,
+                "rescored": res.rescored, "seg_replays": res.seg_replays, "launches": res.launches, "prep_ms": res.prep_ms,
                 "sim_ms": res.sim_ms, "total_ms": res.total_ms,
                 "traj": [{"total_cost": t.total_cost, "lost": t.lost, "iters": t.iters,
                           "converged": t.converged} for t in traj]}

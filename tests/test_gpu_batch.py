@@ -114,6 +114,19 @@ def test_batch_graph_relaunch_and_policy_change():
     check_against_oracle(db, insts, swapped, g4, M + 3)
 
 
+def test_batch_tensor_core_tiles_exact():
+    """PIC_FLAG_TC in a batch: MLP and Gumbel trajectories with long runs and
+    ample stock use the tensor-core tiles; results are the oracle's."""
+    Ts = [6000, 9000, 4000, 7000, 5000, 8000]
+    insts, pols = mixed_batch(31, Ts, 32, K=5, R=9)
+    for i in insts:
+        i.x0 = (i.x0 * 40 + 50).astype(np.int32)  # ample stock: features saturate
+    db = DeviceBatch(insts)
+    got = db.simulate(pols, "picard", num_chunks=3, flags=pic.PIC_FLAG_TC)
+    check_against_oracle(db, insts, pols, got, 3)
+    assert got["tc_decisions"] > 0
+
+
 def test_batch_autotuner_choice_is_exact():
     insts, pols = mixed_batch(8, [3000, 2500, 4000, 1000, 3500, 2000, 1800, 2600], 32)
     db = DeviceBatch(insts)

@@ -85,3 +85,51 @@ def test_mlp_full_size_sampled_against_oracle():
         row = oracle.state_before(inst, a, int(t))
         want = oracle.policy_call(inst, pol, row, inst.prod[t], inst.reg[t], int(t))
         assert want == a[t], (t, want, a[t])
+
+
+@pytest.mark.parametrize("N", [24, 32, 64])
+def test_tensor_core_tiles_bit_exact(N):
+    """PIC_FLAG_TC: long runs with ample stock are scored 16 orders at a time on
+    the tensor cores; the actions, pass counts and iterates are the oracle's
+    (rows whose top-2 margin is within the error bound are re-scored in FP32)."""
+    inst = synth.make_instance(12000, N, 6, 17, seed=N, stock="poisson", fill=1.2)
+    mlp = synth.make_mlp(N, 17, seed=N)
+    d = DeviceInstance(inst)
+    for pol in policies(mlp, N):
+        seq = oracle.seq_sim(inst, pol)
+        for M in (3, 12):
+            want = oracle.picard_chunked(inst, pol, M)
+            got = d.simulate(pol, "picard", num_chunks=M, flags=pic.PIC_FLAG_TC)
+            np.testing.assert_array_equal(got["actions"].cpu().numpy(), seq["actions"])
+            np.testing.assert_array_equal(got["final_stock"].cpu().numpy(), seq["x_final"])
+            assert got["iters"] == want["iters"] and got["total_cost"] == seq["total_cost"]
+            assert got["tc_decisions"] > 0  # the tiles were used
+            assert got["tc_decisions"] + got["rescored"] <= got["mlp_calls"]
+        want = oracle.picard_chunked(inst, pol, 12, record=True)
+        for k in (1, 2):
+            g = d.simulate(pol, "picard", num_chunks=12, max_iters=k, flags=pic.PIC_FLAG_TC,
+                           raise_on_error=False)
+            np.testing.assert_array_equal(g["actions"].cpu().numpy(), want["iterates"][k - 1])
+
+
+def test_tensor_core_tiles_with_low_stock_and_ties():
+    """Scarce stock (features change with every decrement, tiles stop early or
+    are not started) and a scorer with exact ties (W2 = 0: every stocked
+    warehouse scores b2; ties go to the lowest index, which the tiles must leave
+    to the FP32 scorer)."""
+    N = 16
+    inst = synth.make_instance(6000, N, 4, 9, seed=5, stock="poisson", fill=0.3)
+    mlp = synth.make_mlp(N, 9, seed=5)
+    d = DeviceInstance(inst)
+    pol = Policy("mlp", mlp=mlp)
+    seq = oracle.seq_sim(inst, pol)
+    got = d.simulate(pol, "picard", num_chunks=4, flags=pic.PIC_FLAG_TC)
+    np.testing.assert_array_equal(got["actions"].cpu().numpy(), seq["actions"])
+    flat = synth.MLPParams(mlp.W1, mlp.b1, np.zeros_like(mlp.W2), np.zeros_like(mlp.b2), mlp.E)
+    inst2 = synth.make_instance(6000, N, 4, 9, seed=6, stock="poisson", fill=2.0)
+    d2 = DeviceInstance(inst2)
+    pol2 = Policy("mlp", mlp=flat)
+    seq2 = oracle.seq_sim(inst2, pol2)
+    got2 = d2.simulate(pol2, "picard", num_chunks=4, flags=pic.PIC_FLAG_TC)
+    np.testing.assert_array_equal(got2["actions"].cpu().numpy(), seq2["actions"])
+    assert got2["tc_decisions"] == 0 or got2["rescored"] > 0

@@ -81,7 +81,8 @@ def test_paths_objective_and_gradient_match_oracle(N):
     a = acts.cpu().numpy()
     for b in range(len(insts)):
         np.testing.assert_array_equal(db.split(a)[b], paths[b])
-    assert abs(J - Jw) <= 1e-5 * abs(Jw) and J == J2
+    # J2 comes from the gradient kernel: FP64 partial sums in another order
+    assert abs(J - Jw) <= 1e-5 * abs(Jw) and abs(J - J2) <= 1e-12 * abs(J)
     assert_close_grad(g, gw)
 
 
@@ -178,7 +179,7 @@ def test_autograd_function_and_given_paths():
     (3.0 * J).backward()
     g_direct = torch.empty_like(m)
     Jd = rf.gradient(m.detach(), rf.last_actions, g_direct)
-    assert float(J) == Jd
+    assert abs(float(J.detach()) - Jd) <= 1e-12 * abs(Jd)
     torch.testing.assert_close(m.grad, 3.0 * g_direct, rtol=1e-6, atol=0)
     # masters that are not BF16 values: the gradient is taken at the rounded values
     m2 = (m.detach() * (1 + 1e-4)).contiguous()
@@ -194,6 +195,22 @@ def test_autograd_function_and_given_paths():
     for b in range(3):
         np.testing.assert_array_equal(db.split(a2)[b], paths[b])
     assert_close_grad(split_flat(g2.cpu().double(), 8, 7), gw)
+
+
+def test_tensor_core_tiles_in_the_simulation():
+    """Gumbel paths simulated with the tensor-core tiles (PIC_FLAG_TC) are the
+    oracle's; the gradient along them is unchanged."""
+    insts, mlp, pols = case(12, [5000, 7000], 32, K=4, R=8, fill=1.5)
+    db = DeviceBatch(insts)
+    rf = Reinforce(db, ["gumbel"] * 2, [p.seed for p in pols], [p.traj for p in pols], 8,
+                   num_chunks=3, flags=pic.PIC_FLAG_TC)
+    m = flat_from_mlp(mlp)
+    acts = torch.empty(db.T, dtype=torch.int8, device="cuda")
+    J, res = rf.objective(m, actions_out=acts)
+    assert res.tc_decisions > 0
+    a = acts.cpu().numpy()
+    for b, (inst, pol) in enumerate(zip(insts, pols)):
+        np.testing.assert_array_equal(db.split(a)[b], oracle.seq_sim(inst, pol)["actions"])
 
 
 def test_infeasible_paths_rejected():

@@ -63,7 +63,7 @@ def parse():
     return p.parse_args()
 
 
-DEFAULT_CHUNKS = {"dual_large": 4096, "mlp_medium": 1024, "batch_uneven": 0, "pg_large": 32}
+DEFAULT_CHUNKS = {"dual_large": 4096, "mlp_medium": 1024, "batch_uneven": 0, "pg_large": 0}
 
 # FP32 CUDA-core peak of the MLP scorer's arithmetic: 148 SMs x 128 FP32 lanes x
 # 2 FLOP per FMA x 2.032 GHz (maximum SM clock)
@@ -118,6 +118,13 @@ def workload_config(args, inst):
         "chunks": chunks_of(args), "policy": args.workload == "mlp_medium" and "mlp" or "dual",
         "l2": "flushed between timed steps (256 MiB write)",
     }
+
+
+def load_bf16_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p))["bf16_tflops"]), "measured"
+    return 1800.0, "fallback"
 
 
 def chunks_of(args):
@@ -456,8 +463,9 @@ def run_batch(args, dev, world, rank):
 
 
 def grad_flops_per_order(N):
-    """FLOPs of the gradient kernel per order: hidden layer (stock rows), scores,
-    dW2, W2 ds and dW1 (stock rows): five N x 256 products, 2 FLOP per FMA."""
+    """Algorithmic FLOPs of the gradient per order: hidden layer (stock rows),
+    scores, dW2, W2 ds and dW1 (stock rows): five N x 256 products, 2 FLOP per
+    FMA (the tensor-core kernel's split products and recomputation are extra)."""
     return 2 * 5 * N * 256
 
 
@@ -466,6 +474,7 @@ def run_pg(args, dev, world, rank):
     the objective and gradient along those paths."""
     import torch
     import torch.distributed as dist
+    import paper_2406_01939_b300 as pic
     from paper_2406_01939_b300 import synth
     from paper_2406_01939_b300.reinforce import Reinforce, flat_from_mlp
     from paper_2406_01939_b300.session import DeviceBatch
@@ -475,7 +484,8 @@ def run_pg(args, dev, world, rank):
     db = DeviceBatch(insts, device=dev)
     T, N = db.T, insts[0].N
     rf = Reinforce(db, ["gumbel"] * B, [1000 + b for b in range(B)], list(range(B)), insts[0].R,
-                   num_chunks=chunks_of(args), seg_window=args.seg_window)
+                   num_chunks=chunks_of(args), seg_window=args.seg_window,
+                   flags=pic.PIC_FLAG_TIMING | args.flags)
     master = flat_from_mlp(mlp, device=dev)
     acts = torch.empty(T, dtype=torch.int8, device=dev)
     grad = torch.empty_like(master)
@@ -483,15 +493,13 @@ def run_pg(args, dev, world, rank):
     stream = torch.cuda.current_stream(dev)
 
     def step():
+        # one call: simulate the paths (Picard), then J and the gradient (tile kernel)
         e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
         e2 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        J, res = rf.objective(master, actions_out=acts)   # simulate + J
-        e1.record(stream)
-        rf.gradient(master, acts, grad)                    # backward kernel
+        J, res = rf.step(master, grad, actions_out=acts)
         e2.record(stream)
-        return J, res, (e0, e1, e2)
+        return J, res, (e0, e2)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -509,18 +517,28 @@ def run_pg(args, dev, world, rank):
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    fwd = [a.elapsed_time(b) for _, _, (a, b, c) in recs]
-    bwd = [b.elapsed_time(c) for _, _, (a, b, c) in recs]
-    t_ms = sum(f + g for f, g in zip(fwd, bwd))
+    t_ms = sum(a.elapsed_time(b) for _, _, (a, b) in recs)
     if world > 1:
         tt = torch.tensor([t_ms], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_ms = float(tt.item())
     value = world * T * args.steps / (t_ms / 1000.0)
     J, res, _ = recs[-1]
-    bwd_ms = statistics.median(bwd)
+    # the gradient kernel alone, timed separately along the last step's paths
+    gts = []
+    for _ in range(3):
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        rf.gradient(master, acts, grad)
+        g1.record(stream)
+        torch.cuda.synchronize(dev)
+        gts.append(g0.elapsed_time(g1))
+    bwd_ms = statistics.median(gts)
     flops = T * grad_flops_per_order(N)
     achieved = flops / (bwd_ms / 1000.0) / 1e12
+    tc = not (args.flags & pic.PIC_FLAG_NO_TC)
+    bf16_peak, bf16_kind = load_bf16_peak()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
@@ -533,13 +551,20 @@ def run_pg(args, dev, world, rank):
                    "chunks_per_trajectory": res.num_chunks, "seg_window": res.seg_window,
                    "l2": "inputs exceed L2; flushed between timed steps (256 MiB write)"},
         "iters": res.iters, "objective": J,
-        "phases_ms": {"simulate_and_objective": statistics.median(fwd), "gradient": bwd_ms},
-        "policy_calls": res.policy_calls,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                     "kernel": "gradient phase (k_pg_grad dominant)",
-                     "peak_kind": "derived: 148 SMs x 128 FP32 lanes x 2 FLOP x 2.032 GHz",
-                     "algorithmic_flops": flops},
+        "phases_ms": {"step": t_ms / args.steps, "simulation": res.sim_ms,
+                      "gradient_call_on_given_paths": bwd_ms},
+        "policy_calls": res.policy_calls, "tc_decisions": res.tc_decisions,
+        "rescored": res.rescored,
+        "roofline": ({"bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
+                      "frac": achieved / bf16_peak, "traffic": None,
+                      "kernel": "k_pg_tc (tcgen05, BF16 split products, FP32 accumulation in TMEM)",
+                      "peak_kind": bf16_kind + " BF16 dense (burst: the gradient call timed alone)",
+                      "algorithmic_flops": flops} if tc else
+                     {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                      "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                      "kernel": "k_pg_grad (FP32 CUDA cores)",
+                      "peak_kind": "derived: 148 SMs x 128 FP32 lanes x 2 FLOP x 2.032 GHz",
+                      "algorithmic_flops": flops}),
         "e2e": None,
         "gpu_launches": None,
         "clocks": clk,

@@ -37,6 +37,8 @@
 #include <cstring>
 #include <new>
 
+#include <cuda_bf16.h>
+
 #include "pic_device.cuh"
 
 using namespace pic;
@@ -511,6 +513,413 @@ __global__ void __launch_bounds__(kPgThreads, 1) k_pg_grad(PgArgs p) {
     if (tid < N) atomicAdd(p.accb2 + tid, s.db2[tid]);
 }
 
+// ---------------------------------------------------------------- the tile kernel on tcgen05
+// The same products on the 5th-generation tensor cores: 128 region-sorted orders
+// per tile (one TMEM lane per order), the hidden layer in two halves of 128
+// units.  Per tile and half h (F = stock features, exact in BF16; weights BF16):
+//   phase 1  Z_h = F W1s_h (TMEM), h = max(Z_h + P[r], 0) split in BF16 hi + lo,
+//            SC += h_hi W2_h + h_lo W2_h;
+//            then softmax, log pi(a) G and ds = G (e_a - p) per order (FP32), ds
+//            split into BF16 hi + lo;
+//   phase 2  Z_h again, h split hi + lo; dW2_h += h_hi^T ds_hi + h_hi^T ds_lo +
+//            h_lo^T ds_hi and dH_h = ds_hi W2_h^T + ds_lo W2_h^T; dz = dH_h [h > 0]
+//            split hi + lo (over the h buffers); dW1s_h^T += dz_hi^T F + dz_lo^T F;
+//            per-region sums of dz.
+// The split products keep each term of the order sums within ~2^-16 of FP32.
+// dW2 and dW1s^T accumulate in TMEM over all tiles of the CTA and are added to
+// the FP64 accumulators once at the end.  Shared-memory operands use 8x8 core
+// matrices (8 rows of 16 bytes) without swizzle: element (r, c) of an [R][C]
+// buffer at (r/8)(C/8)128 + (c/8)128 + (r%8)16 + (c%8)2.  Read with its rows as
+// the M/N index it is a K-major operand (LBO 128 B along K, SBO (C/8)128 B along
+// M/N); read with its rows as the K index it is an MN-major operand (LBO
+// (C/8)128 B along K, SBO 128 B along M/N).
+constexpr int kTcRows = 128;     // orders per tile = TMEM lanes
+constexpr int kTcThreads = 512;  // 16 warps: four per TMEM lane quadrant
+
+struct __align__(16) TcSmem {
+    unsigned char w1s[kHidden * kPgN * 2];   // [j][n] (B of Z: K = n, N = j)
+    unsigned char w2[kPgN * kHidden * 2];    // [n][j] (B of SC: K = j, N = n; B of dH: MN-major)
+    unsigned char f[kTcRows * kPgN * 2];     // [t][n] (A of Z; B of dW1s^T: MN-major)
+    unsigned char hhi[kTcRows * 128 * 2];    // [t][j] of one half: h hi, then dz hi
+    unsigned char hlo[kTcRows * 128 * 2];    // h lo, then dz lo
+    unsigned char dshi[kTcRows * kPgN * 2];  // [t][n] ds hi (A of dH; B of dW2: MN-major)
+    unsigned char dslo[kTcRows * kPgN * 2];
+    float b2[kPgN];
+    float red[4][kTcRows];  // softmax partials of the four column quarters of a row
+    float G[kTcRows];
+    int r[kTcRows], a[kTcRows], ok[kTcRows], j[kTcRows];
+    unsigned long long mbar;
+    unsigned tmem;
+    int fail;
+};
+
+__device__ __forceinline__ int lay(int r, int c, int C) {
+    return (r >> 3) * (C >> 3) * 128 + (c >> 3) * 128 + (r & 7) * 16 + (c & 7) * 2;
+}
+
+__device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long sdesc(unsigned addr, unsigned lbo, unsigned sbo) {
+    return (unsigned long long)((addr >> 4) & 0x3FFF) | ((unsigned long long)((lbo >> 4) & 0x3FFF) << 16) |
+           ((unsigned long long)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// kind::f16 instruction descriptor: BF16 A and B, FP32 D, M = 128
+__host__ __device__ constexpr unsigned tc_idesc(int N, int a_mn, int b_mn) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)a_mn << 15) | ((unsigned)b_mn << 16) |
+           ((unsigned)(N >> 3) << 17) | ((unsigned)(kTcRows >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(unsigned d, unsigned long long a, unsigned long long b, unsigned idesc,
+                                       unsigned acc) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                 ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tc_commit(unsigned long long* mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(mbar)));
+}
+
+// Wait for the next phase of the CTA's mbarrier (bounded); false on time-out.
+__device__ __forceinline__ bool tc_wait(unsigned long long* mbar, unsigned& phase) {
+    unsigned done = 0;
+    for (int it = 0; it < (1 << 24) && !done; ++it)
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(su32(mbar)), "r"(phase));
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    return done != 0;
+}
+
+__device__ __forceinline__ void tc_ld16(unsigned addr, float v[16]) {
+    unsigned u[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+                   "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+                 : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(u[i]);
+}
+
+// Shared-memory writes by the threads become visible to the tensor cores, and
+// the threads meet (with the tcgen05 ordering fences around the barrier).
+__device__ __forceinline__ void tc_sync_operands() {
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+}
+
+__device__ __forceinline__ unsigned pack2bf(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const unsigned*>(&v);
+}
+
+// 16 BF16 values (columns c0..c0+15 of row t of a [R][C] core-matrix buffer)
+__device__ __forceinline__ void st_row16(unsigned char* buf, int t, int c0, int C, const float v[16]) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint4 q;
+        q.x = pack2bf(v[8 * h + 0], v[8 * h + 1]);
+        q.y = pack2bf(v[8 * h + 2], v[8 * h + 3]);
+        q.z = pack2bf(v[8 * h + 4], v[8 * h + 5]);
+        q.w = pack2bf(v[8 * h + 6], v[8 * h + 7]);
+        *reinterpret_cast<uint4*>(buf + lay(t, c0 + 8 * h, C)) = q;
+    }
+}
+
+constexpr unsigned kColZ = 0, kColSC = 128, kColW2 = 192, kColW1 = 320;  // TMEM column bases
+
+__device__ __forceinline__ void ld_p16(const float* Pr, int c, bool valid, float pv[16]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float4 q = valid ? __ldg(reinterpret_cast<const float4*>(Pr + c) + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        pv[4 * i] = q.x; pv[4 * i + 1] = q.y; pv[4 * i + 2] = q.z; pv[4 * i + 3] = q.w;
+    }
+}
+
+// Thread layout: 16 warps; warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile rows
+// = orders, or hidden units for the accumulators) and the column quarter w / 4.
+__global__ void __launch_bounds__(kTcThreads, 1) k_pg_tc(PgArgs p, int* err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];  // 16-byte operand addresses suffice
+    TcSmem& s = *reinterpret_cast<TcSmem*>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int t = 32 * (warp & 3) + (tid & 31);  // tile row of this thread
+    const int cq = warp >> 2;                    // column quarter
+    const int N = p.N;
+    // ---- weights (zero beyond N), control
+    for (int i = tid; i < kHidden * kPgN; i += kTcThreads) {
+        const int jj = i / kPgN, n = i % kPgN;
+        const uint16_t w1 = n < N ? p.W1[(size_t)(N + n) * kHidden + jj] : 0;
+        const uint16_t w2 = n < N ? p.W2[(size_t)jj * N + n] : 0;
+        *reinterpret_cast<uint16_t*>(s.w1s + lay(jj, n, kPgN)) = w1;
+        *reinterpret_cast<uint16_t*>(s.w2 + lay(n, jj, kHidden)) = w2;
+    }
+    if (tid < kPgN) s.b2[tid] = tid < N ? lo16(p.b2[tid]) : 0.0f;
+    double db2 = 0.0;  // thread n < N: running db2[n]
+    if (tid == 0) {
+        s.fail = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&s.mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&s.tmem)), "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_sync_operands();
+    const unsigned tm = s.tmem;
+    const unsigned lane_base = (unsigned)(32 * (warp & 3)) << 16;  // this warp's TMEM lanes
+    unsigned phase = 0;
+    bool acc_started = false;  // the TMEM accumulators hold this CTA's sums
+    double Jw = 0.0;
+    int cur_r[2] = {-1, -1};   // per-region dz sums of column tid % 128 of each half, rows of quarter tid / 128
+    float run[2] = {0.f, 0.f};
+    const unsigned aF = su32(s.f), aW1 = su32(s.w1s), aW2 = su32(s.w2), aH = su32(s.hhi), aL = su32(s.hlo);
+    const unsigned aSh = su32(s.dshi), aSl = su32(s.dslo);
+    const int ntiles = (p.Q + kTcRows - 1) / kTcRows;
+    const int tb0 = (int)((long long)blockIdx.x * ntiles / gridDim.x);
+    const int tb1 = (int)((long long)(blockIdx.x + 1) * ntiles / gridDim.x);
+    auto issue_z = [&](int h) {  // Z_h = F W1s_h into the Z columns
+        for (int kk = 0; kk < kPgN / 16; ++kk)
+            tc_mma(tm + kColZ, sdesc(aF + kk * 256, 128, 1024), sdesc(aW1 + h * 16384 + kk * 256, 128, 1024),
+                   tc_idesc(128, 0, 0), kk > 0);
+    };
+    auto issue_sc = [&](int h) {  // SC += (h_hi + h_lo) W2_h
+        for (int kk = 0; kk < 128 / 16; ++kk) {
+            const unsigned long long bw = sdesc(aW2 + h * 2048 + kk * 256, 128, 4096);
+            tc_mma(tm + kColSC, sdesc(aH + kk * 256, 128, 2048), bw, tc_idesc(kPgN, 0, 0), (h > 0 || kk > 0));
+            tc_mma(tm + kColSC, sdesc(aL + kk * 256, 128, 2048), bw, tc_idesc(kPgN, 0, 0), 1);
+        }
+    };
+    // h = max(Z + P[r], 0) of this thread's 32 columns of half h, split in BF16 hi + lo
+    auto epi_h = [&](int h, const float* Pr, bool valid) {
+        for (int c0 = 32 * cq; c0 < 32 * cq + 32; c0 += 16) {
+            float v[16], pv[16], lo[16];
+            tc_ld16(tm + lane_base + kColZ + c0, v);
+            ld_p16(Pr, 128 * h + c0, valid, pv);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const float x = valid ? fmaxf(v[i] + pv[i], 0.f) : 0.f;
+                v[i] = __bfloat162float(__float2bfloat16_rn(x));
+                lo[i] = x - v[i];
+            }
+            st_row16(s.hhi, t, c0, 128, v);
+            st_row16(s.hlo, t, c0, 128, lo);
+        }
+    };
+    bool ok_all = true;
+    for (int tile = tb0; tile < tb1 && ok_all; ++tile) {
+        // ---- the tile's orders (warps 0-3: one row each) and features (16 columns per thread)
+        {
+            const int q = tile * kTcRows + t;
+            const int jj = q < p.Q ? p.jq[q] : -1;
+            if (cq == 0) {
+                int r = -1, a = -1, okv = 0;
+                float g = 0.f;
+                if (jj >= 0) {
+                    r = p.rq[q];
+                    a = p.alpha_s[jj];
+                    g = p.G[jj];
+                    okv = p.ok[jj];
+                }
+                s.j[t] = jj; s.r[t] = r; s.a[t] = a; s.G[t] = g; s.ok[t] = okv;
+            }
+            float fv[16];
+            const int c0 = 16 * cq;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const char4 c4 = jj >= 0 ? *reinterpret_cast<const char4*>(p.f8 + (size_t)jj * kPgN + c0 + 4 * i)
+                                         : make_char4(0, 0, 0, 0);
+                fv[4 * i] = c4.x / 32.0f; fv[4 * i + 1] = c4.y / 32.0f;
+                fv[4 * i + 2] = c4.z / 32.0f; fv[4 * i + 3] = c4.w / 32.0f;
+            }
+            st_row16(s.f, t, c0, kPgN, fv);
+        }
+        tc_sync_operands();
+        const int r = s.r[t];
+        const bool valid = r >= 0;
+        const float* Pr = p.P + (size_t)(valid ? r : 0) * kHidden;
+        // ---- phase 1: scores.  Commits: {Z_0}, {SC_0, Z_1}, {SC_1, Z_0 again}
+        if (tid == 0) { issue_z(0); tc_commit(&s.mbar); }
+        if (!tc_wait(&s.mbar, phase)) s.fail = 1;
+        epi_h(0, Pr, valid);
+        tc_sync_operands();
+        if (tid == 0) { issue_sc(0); issue_z(1); tc_commit(&s.mbar); }
+        if (!tc_wait(&s.mbar, phase)) s.fail = 1;
+        epi_h(1, Pr, valid);
+        tc_sync_operands();
+        if (tid == 0) { issue_sc(1); issue_z(0); tc_commit(&s.mbar); }
+        if (!tc_wait(&s.mbar, phase)) s.fail = 1;
+        // ---- softmax over the stocked warehouses (quarters of a row meet in shared
+        // memory); ds = G (e_a - p), split in BF16 hi + lo
+        {
+            const int n0 = 16 * cq;
+            float sc[16];
+            tc_ld16(tm + lane_base + kColSC + n0, sc);
+            const bool use = s.ok[t] != 0;
+            const int a = s.a[t];
+            const float G = s.G[t];
+            float mx = -INFINITY;
+            unsigned feas = 0;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int n = n0 + i;
+                const float f = __uint_as_float((unsigned)*reinterpret_cast<const uint16_t*>(s.f + lay(t, n, kPgN)) << 16);
+                sc[i] += s.b2[n];
+                if (n < N && f > 0.f) {
+                    feas |= 1u << i;
+                    mx = fmaxf(mx, sc[i]);
+                }
+            }
+            s.red[cq][t] = mx;
+            __syncthreads();
+            mx = fmaxf(fmaxf(s.red[0][t], s.red[1][t]), fmaxf(s.red[2][t], s.red[3][t]));
+            float sum = 0.f, sa = 0.f;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                if (n0 + i == a) sa = sc[i];
+                sc[i] = ((feas >> i) & 1u) ? expf(sc[i] - mx) : 0.f;
+                sum += sc[i];
+            }
+            __syncthreads();  // everyone has read the maxima
+            s.red[cq][t] = sum;
+            __syncthreads();
+            sum = (s.red[0][t] + s.red[1][t]) + (s.red[2][t] + s.red[3][t]);
+            if (use && a >= n0 && a < n0 + 16) Jw += (double)G * (double)(sa - mx - logf(sum));
+            const float inv = use ? 1.0f / sum : 0.f;
+            float dhi[16], dlo[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int n = n0 + i;
+                const float d = use && ((feas >> i) & 1u) ? G * ((n == a ? 1.0f : 0.0f) - sc[i] * inv) : 0.f;
+                dhi[i] = __bfloat162float(__float2bfloat16_rn(d));
+                dlo[i] = d - dhi[i];
+            }
+            st_row16(s.dshi, t, n0, kPgN, dhi);
+            st_row16(s.dslo, t, n0, kPgN, dlo);
+        }
+        tc_sync_operands();
+        if (tid < N) {  // db2: this tile's column sum of ds, rows in order (deterministic)
+            float cs = 0.f;
+            for (int rr = 0; rr < kTcRows; ++rr) {
+                const int o = lay(rr, tid, kPgN);
+                cs += __uint_as_float((unsigned)*reinterpret_cast<const uint16_t*>(s.dshi + o) << 16) +
+                      __uint_as_float((unsigned)*reinterpret_cast<const uint16_t*>(s.dslo + o) << 16);
+            }
+            db2 += (double)cs;
+        }
+        // ---- phase 2: gradients.  Per half: {dW2_h, dH_h}, then {dW1_h (, Z_1)}
+        for (int h = 0; h < 2; ++h) {
+            epi_h(h, Pr, valid);  // Z_h is in the Z columns (issued with the previous group)
+            tc_sync_operands();
+            if (tid == 0) {
+                const unsigned dW2 = tm + kColW2 + 64 * h;
+                const unsigned id = tc_idesc(kPgN, 1, 1);
+                for (int kk = 0; kk < kTcRows / 16; ++kk) {  // K = orders
+                    const unsigned long long ah = sdesc(aH + kk * 4096, 2048, 128);
+                    const unsigned long long al = sdesc(aL + kk * 4096, 2048, 128);
+                    const unsigned long long bh = sdesc(aSh + kk * 2048, 1024, 128);
+                    const unsigned long long bl = sdesc(aSl + kk * 2048, 1024, 128);
+                    tc_mma(dW2, ah, bh, id, (acc_started || kk > 0));
+                    tc_mma(dW2, ah, bl, id, 1);
+                    tc_mma(dW2, al, bh, id, 1);
+                }
+                const unsigned idh = tc_idesc(128, 0, 1);
+                for (int kk = 0; kk < kPgN / 16; ++kk) {  // K = warehouses
+                    const unsigned long long bw = sdesc(aW2 + h * 2048 + kk * 8192, 4096, 128);
+                    tc_mma(tm + kColZ, sdesc(aSh + kk * 256, 128, 1024), bw, idh, kk > 0);
+                    tc_mma(tm + kColZ, sdesc(aSl + kk * 256, 128, 1024), bw, idh, 1);
+                }
+                tc_commit(&s.mbar);
+            }
+            if (!tc_wait(&s.mbar, phase)) s.fail = 1;
+            // dz = dH [h > 0] over the h buffers (hi, lo): this thread's 32 columns
+            for (int c0 = 32 * cq; c0 < 32 * cq + 32; c0 += 16) {
+                float v[16], hi[16], lo[16];
+                tc_ld16(tm + lane_base + kColZ + c0, v);
+#pragma unroll
+                for (int i = 0; i < 16; i += 8) {
+                    const uint4 hq = *reinterpret_cast<const uint4*>(s.hhi + lay(t, c0 + i, 128));
+                    const unsigned hw[4] = {hq.x, hq.y, hq.z, hq.w};
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const float hh = (e & 1) ? hi16(hw[e >> 1]) : lo16(hw[e >> 1]);
+                        const float x = hh > 0.f ? v[i + e] : 0.f;
+                        hi[i + e] = __bfloat162float(__float2bfloat16_rn(x));
+                        lo[i + e] = x - hi[i + e];
+                    }
+                }
+                st_row16(s.hhi, t, c0, 128, hi);
+                st_row16(s.hlo, t, c0, 128, lo);
+            }
+            tc_sync_operands();
+            if (tid == 0) {
+                const unsigned dW1 = tm + kColW1 + 64 * h;
+                const unsigned id = tc_idesc(kPgN, 1, 1);
+                for (int kk = 0; kk < kTcRows / 16; ++kk) {
+                    const unsigned long long bf = sdesc(aF + kk * 2048, 1024, 128);
+                    tc_mma(dW1, sdesc(aH + kk * 4096, 2048, 128), bf, id, (acc_started || kk > 0));
+                    tc_mma(dW1, sdesc(aL + kk * 4096, 2048, 128), bf, id, 1);
+                }
+                if (h == 0) issue_z(1);  // the dz columns were read above
+                tc_commit(&s.mbar);
+            }
+            // region sums of column c = tid % 128 of half h over rows 32 qq .. 32 qq + 31
+            {
+                const int c = tid & 127, qq = tid >> 7;
+                for (int rr = 32 * qq; rr < 32 * qq + 32; ++rr) {
+                    const int rg = s.r[rr];
+                    if (rg < 0) break;
+                    if (rg != cur_r[h]) {
+                        if (cur_r[h] >= 0) atomicAdd(p.dz + (size_t)cur_r[h] * kHidden + 128 * h + c, (double)run[h]);
+                        cur_r[h] = rg;
+                        run[h] = 0.f;
+                    }
+                    const float zh = __uint_as_float((unsigned)*reinterpret_cast<const uint16_t*>(s.hhi + lay(rr, c, 128)) << 16);
+                    const float zl = __uint_as_float((unsigned)*reinterpret_cast<const uint16_t*>(s.hlo + lay(rr, c, 128)) << 16);
+                    run[h] += zh + zl;
+                }
+            }
+            if (!tc_wait(&s.mbar, phase)) s.fail = 1;
+            __syncthreads();
+        }
+        acc_started = true;
+        ok_all = s.fail == 0;
+        __syncthreads();
+    }
+    // ---- flush: objective, region sums, the TMEM accumulators (row t = hidden unit)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) Jw += __shfl_xor_sync(kFull, Jw, o);
+    if ((tid & 31) == 0 && Jw != 0.0) atomicAdd(p.J, Jw);
+    for (int h = 0; h < 2; ++h)
+        if (cur_r[h] >= 0) atomicAdd(p.dz + (size_t)cur_r[h] * kHidden + 128 * h + (tid & 127), (double)run[h]);
+    if (tid < N && db2 != 0.0) atomicAdd(p.accb2 + tid, db2);
+    if (acc_started && ok_all) {
+        for (int h = 0; h < 2; ++h) {
+            const int jj = 128 * h + t;
+            const int c0 = 16 * cq;
+            float v[16], u[16];
+            tc_ld16(tm + lane_base + kColW2 + 64 * h + c0, v);
+            tc_ld16(tm + lane_base + kColW1 + 64 * h + c0, u);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int n = c0 + i;
+                if (n < N) {
+                    atomicAdd(p.accW2 + (size_t)jj * N + n, (double)v[i]);
+                    atomicAdd(p.accW1 + (size_t)(N + n) * kHidden + jj, (double)u[i]);
+                }
+            }
+        }
+    }
+    if (!ok_all && tid == 0) atomicOr(err, 4);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(512));
+}
+
 // ---------------------------------------------------------------- reductions over regions
 // dW1 rows of the cost inputs (n < N), of the embedding (2N + e), and db1, from
 // DZ: acc[row][j] += sum_r coef(row, r) DZ[r][j].  Block: 256 threads = one per
@@ -782,7 +1191,11 @@ extern "C" pic_status pic_policy_grad(pic_instance* h, const pic_policy* pols, c
         a.accW1 = g->acc + oW1; a.accW2 = g->acc + oW2; a.accb2 = g->acc + ob2;
         a.dz = g->dz; a.J = g->J;
         const size_t smem = sizeof(PgSmem);
-        if (want_grad) {
+        if (want_grad && !(opts->flags & PIC_FLAG_NO_TC)) {
+            const size_t tsm = sizeof(TcSmem);
+            PCU(cudaFuncSetAttribute(k_pg_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+            k_pg_tc<<<I.num_sms, kTcThreads, tsm, st>>>(a, g->bad);
+        } else if (want_grad) {
             PCU(cudaFuncSetAttribute(k_pg_grad<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             k_pg_grad<true><<<I.num_sms, kPgThreads, smem, st>>>(a);
         } else {
@@ -811,6 +1224,7 @@ extern "C" pic_status pic_policy_grad(pic_instance* h, const pic_policy* pols, c
     PCU(cudaMemcpyAsync(&J, g->J, sizeof(double), cudaMemcpyDeviceToHost, st));
     PCU(cudaMemcpyAsync(&bad, g->bad, sizeof(int), cudaMemcpyDeviceToHost, st));
     PCU(cudaStreamSynchronize(st));
+    if (bad & 4) return fail(PIC_ERR_TIMEOUT, "gradient kernel: a tensor-core wait timed out");
     if (bad & 2) return fail(PIC_ERR_INVALID_ARG, "actions hold a value outside [-1, N)");
     if (bad & 1) return fail(PIC_ERR_INVALID_ARG, "actions are not a feasible path (an order took a unit "
                                                   "from a warehouse without stock)");

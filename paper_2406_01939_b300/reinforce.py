@@ -55,6 +55,13 @@ class Reinforce:
                                     actions=actions, actions_out=actions_out)
         return J, res
 
+    def step(self, master, grad, actions_out=None):
+        """One policy-gradient step in one call: simulate the paths under
+        BF16(master), then J and dJ/dtheta along them.  Returns (J, result)."""
+        _, J, res = pic_policy_grad(self.batch.handle, self.pols, master, self.e_rows, self.opts,
+                                    actions_out=actions_out, grad=grad)
+        return J, res
+
     def gradient(self, master, actions, grad, scale=1.0):
         _, J, _ = pic_policy_grad(self.batch.handle, self.pols, master, self.e_rows, self.opts,
                                   actions=actions, grad=grad, grad_scale=scale)

@@ -81,8 +81,8 @@ def test_paths_objective_and_gradient_match_oracle(N):
     a = acts.cpu().numpy()
     for b in range(len(insts)):
         np.testing.assert_array_equal(db.split(a)[b], paths[b])
-    # J2 comes from the gradient kernel: FP64 partial sums in another order
-    assert abs(J - Jw) <= 1e-5 * abs(Jw) and abs(J - J2) <= 1e-12 * abs(J)
+    # J2 comes from the gradient kernel (tensor cores, split BF16 products)
+    assert abs(J - Jw) <= 1e-5 * abs(Jw) and abs(J2 - Jw) <= 1e-5 * abs(Jw)
     assert_close_grad(g, gw)
 
 
@@ -179,7 +179,7 @@ def test_autograd_function_and_given_paths():
     (3.0 * J).backward()
     g_direct = torch.empty_like(m)
     Jd = rf.gradient(m.detach(), rf.last_actions, g_direct)
-    assert abs(float(J.detach()) - Jd) <= 1e-12 * abs(Jd)
+    assert abs(float(J.detach()) - Jd) <= 1e-5 * abs(Jd)
     torch.testing.assert_close(m.grad, 3.0 * g_direct, rtol=1e-6, atol=0)
     # masters that are not BF16 values: the gradient is taken at the rounded values
     m2 = (m.detach() * (1 + 1e-4)).contiguous()
@@ -211,6 +211,27 @@ def test_tensor_core_tiles_in_the_simulation():
     a = acts.cpu().numpy()
     for b, (inst, pol) in enumerate(zip(insts, pols)):
         np.testing.assert_array_equal(db.split(a)[b], oracle.seq_sim(inst, pol)["actions"])
+
+
+@pytest.mark.parametrize("N", [16, 64])
+def test_tensor_core_and_cuda_core_gradients_agree(N):
+    """The tcgen05 gradient kernel (default) and the FP32 CUDA-core kernel
+    (PIC_FLAG_NO_TC) give the same gradient along the same paths."""
+    insts, mlp, pols = case(40 + N, [3000, 2000, 4100], N, K=30, R=13)
+    db = DeviceBatch(insts)
+    m = flat_from_mlp(mlp)
+    rf = Reinforce(db, ["gumbel"] * 3, [p.seed for p in pols], [p.traj for p in pols], 13, num_chunks=8)
+    rf_cc = Reinforce(db, ["gumbel"] * 3, [p.seed for p in pols], [p.traj for p in pols], 13, num_chunks=8,
+                      flags=pic.PIC_FLAG_NO_TC)
+    acts = torch.empty(db.T, dtype=torch.int8, device="cuda")
+    rf.objective(m, actions_out=acts)
+    g_tc, g_cc = torch.empty_like(m), torch.empty_like(m)
+    J_tc = rf.gradient(m, acts, g_tc)
+    J_cc = rf_cc.gradient(m, acts, g_cc)
+    assert abs(J_tc - J_cc) <= 1e-5 * abs(J_cc)
+    a = split_flat(g_tc.cpu().double(), N, 13)
+    b = split_flat(g_cc.cpu().double(), N, 13)
+    assert_close_grad(a, {k: v.numpy() for k, v in b.items()})
 
 
 def test_infeasible_paths_rejected():

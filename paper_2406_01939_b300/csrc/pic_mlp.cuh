@@ -10,7 +10,9 @@
 //   h_j = b1_j, then one fmaf per input: cost[r][n]/128 (n = 0..N-1), E[r][e]
 //         (e = 0..15), min(S_n, 32)/32 (n = 0..N-1), weights W1 rows in that
 //         input's position; h_j = max(h_j, 0);
-//   s_n = b2_n, then one fmaf per hidden unit j = 0..255 with W2[j][n].
+//   p_e = 0, then one fmaf per hidden unit j = e, e+8, ... with W2[j][n] (e = 0..7),
+//   s_n = b2_n + (((p_0 + p_1) + (p_2 + p_3)) + ((p_4 + p_5) + (p_6 + p_7))):
+//   eight independent chains keep the latency of one decision short.
 // Parameters are BF16 (exact in FP32).  The part of the h chain before the stock
 // inputs depends only on the region, so it is evaluated once per call into
 // P[r][j] (the same operations in the same order).  Argmax over stocked
@@ -172,20 +174,24 @@ __device__ __forceinline__ int mlp_decide(const MlpPolicy& p, const uint4* W1p, 
     for (int i = 0; i < NPL; ++i) {
         const int n = lane + 32 * i;
         if (n < N && S[i] > 0) {
-            float s = __ldg(p.b2f + n);
+            // eight partial chains p_e over the hidden units 8q + e, then a fixed tree
+            float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f, p4 = 0.f, p5 = 0.f, p6 = 0.f, p7 = 0.f;
 #pragma unroll 4
-            for (int q = 0; q < kHidden / 8; ++q) {  // hidden units 8q .. 8q+7, in order
+            for (int q = 0; q < kHidden / 8; ++q) {
                 const uint4 w = wld4<SMEMW>(W2p + q * N + n);
                 const float4 ha = h4[2 * q], hb = h4[2 * q + 1];
-                s = fmaf(lo16(w.x), ha.x, s);
-                s = fmaf(hi16(w.x), ha.y, s);
-                s = fmaf(lo16(w.y), ha.z, s);
-                s = fmaf(hi16(w.y), ha.w, s);
-                s = fmaf(lo16(w.z), hb.x, s);
-                s = fmaf(hi16(w.z), hb.y, s);
-                s = fmaf(lo16(w.w), hb.z, s);
-                s = fmaf(hi16(w.w), hb.w, s);
+                p0 = fmaf(lo16(w.x), ha.x, p0);
+                p1 = fmaf(hi16(w.x), ha.y, p1);
+                p2 = fmaf(lo16(w.y), ha.z, p2);
+                p3 = fmaf(hi16(w.y), ha.w, p3);
+                p4 = fmaf(lo16(w.z), hb.x, p4);
+                p5 = fmaf(hi16(w.z), hb.y, p5);
+                p6 = fmaf(lo16(w.w), hb.z, p6);
+                p7 = fmaf(hi16(w.w), hb.w, p7);
             }
+            const float v = __fadd_rn(__fadd_rn(__fadd_rn(p0, p1), __fadd_rn(p2, p3)),
+                                      __fadd_rn(__fadd_rn(p4, p5), __fadd_rn(p6, p7)));
+            float s = __fadd_rn(__ldg(p.b2f + n), v);
             if (p.gumbel) s = __fadd_rn(s, gumbel1(p.seed, p.traj, t, n));
             const unsigned kk = ord_key(s);
             if (!any || kk > best_key) { best_key = kk; best_n = n; any = true; }

@@ -41,6 +41,32 @@ METRIC = "orders simulated/sec on 1 B300, Picard vs sequential GPU sim, bit-exac
 UNIT = "orders/s"
 
 
+def over_ranks(x, world, op="max", device=None):
+    """Reduce one float over the ranks of the job (identity at world size 1).
+    "max" gives the job's time from each rank's timed total (every rank starts
+    after the same barrier); "sum" gives the job's units."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_rate(units_this_rank, steps, t_ms_this_rank, world, device=None):
+    """Whole-job throughput: the units all ranks processed in the timed steps
+    over the slowest rank's time.  Returns (rate, job time in ms)."""
+    t_ms = over_ranks(t_ms_this_rank, world, "max", device)
+    units = over_ranks(units_this_rank * steps, world, "sum", device)
+    return units / (t_ms / 1000.0), t_ms
+
+
+def rank_seed(base, rank):
+    """Each rank simulates its own synthetic workload (weak scaling)."""
+    return base + rank
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -334,7 +360,7 @@ def run_batch(args, dev, world, rank):
     from paper_2406_01939_b300 import synth
     from paper_2406_01939_b300.session import DeviceBatch
 
-    insts, pols = synth.batch_uneven(args.seed + rank, **({"B": args.B} if args.B else {}))
+    insts, pols = synth.batch_uneven(rank_seed(args.seed, rank), **({"B": args.B} if args.B else {}))
     db = DeviceBatch(insts, device=dev)
     T = db.T
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -370,12 +396,7 @@ def run_batch(args, dev, world, rank):
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    t_ms = sum(a.elapsed_time(b) for a, b in evs)
-    if world > 1:
-        tt = torch.tensor([t_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    value = world * T * args.steps / (t_ms / 1000.0)
+    value, t_ms = job_rate(T, args.steps, sum(a.elapsed_time(b) for a, b in evs), world, dev)
     last = results[-1]
     sim_ms = statistics.median(r["sim_ms"] for r in results)
 
@@ -415,7 +436,7 @@ def run_batch(args, dev, world, rank):
             if i:
                 e2e_t.append(t1 - t0)
         bit_exact_e2e = bool(np.array_equal(host_act, act.cpu().numpy()))
-    e2e_value = world * T / statistics.median(e2e_t) if e2e_t else None
+    e2e_value = job_rate(T, 1, 1000.0 * statistics.median(e2e_t), world, dev)[0] if e2e_t else None
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -480,7 +501,7 @@ def run_pg(args, dev, world, rank):
     from paper_2406_01939_b300.session import DeviceBatch
 
     B = args.B or 64
-    insts, mlp = synth.pg_large(args.seed + rank, B=B)
+    insts, mlp = synth.pg_large(rank_seed(args.seed, rank), B=B)
     db = DeviceBatch(insts, device=dev)
     T, N = db.T, insts[0].N
     rf = Reinforce(db, ["gumbel"] * B, [1000 + b for b in range(B)], list(range(B)), insts[0].R,
@@ -517,12 +538,7 @@ def run_pg(args, dev, world, rank):
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    t_ms = sum(a.elapsed_time(b) for _, _, (a, b) in recs)
-    if world > 1:
-        tt = torch.tensor([t_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    value = world * T * args.steps / (t_ms / 1000.0)
+    value, t_ms = job_rate(T, args.steps, sum(a.elapsed_time(b) for _, _, (a, b) in recs), world, dev)
     J, res, _ = recs[-1]
     # the gradient kernel alone, timed separately along the last step's paths
     gts = []
@@ -603,7 +619,7 @@ def main():
     import paper_2406_01939_b300 as pic
     from paper_2406_01939_b300.session import DeviceInstance, DevicePolicy
 
-    inst, hpol, _ = make_workload(args, args.seed + rank)
+    inst, hpol, _ = make_workload(args, rank_seed(args.seed, rank))
     di = DeviceInstance(inst, device=dev)
     pol = DevicePolicy(hpol, dev)
     T = inst.T
@@ -638,12 +654,7 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    t_ms = sum(step_ms)
-    if world > 1:
-        tt = torch.tensor([t_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    value = world * T * args.steps / (t_ms / 1000.0)
+    value, t_ms = job_rate(T, args.steps, sum(step_ms), world, dev)
     last = results[-1]
     # one extra (untimed) call with the per-pass trace
     tr = np.zeros((4096, 4), np.int64)
@@ -693,7 +704,7 @@ def main():
         t1 = time.perf_counter()
         if i >= 2:
             e2e_t.append(t1 - t0)
-    e2e_value = world * T / statistics.median(e2e_t) if e2e_t else None
+    e2e_value = job_rate(T, 1, 1000.0 * statistics.median(e2e_t), world, dev)[0] if e2e_t else None
     bit_exact_e2e = bool(np.array_equal(host_act, act.cpu().numpy())) if e2e_t else None
 
     # roofline of the dominant kernel (the persistent Picard kernel)

@@ -55,6 +55,14 @@ def _load():
             lib.orc_picard_literal.restype = C.c_int
             lib.orc_picard_chunked.argtypes = common + [i32, i32, P, P, P, P, P, P]
             lib.orc_picard_chunked.restype = C.c_int
+            capc = [i32, i32, i32, i32, P, P, P, P, P, P, i32]
+            lib.orc_seq_sim_cap.argtypes = capc + [P, P, P, P, P]
+            lib.orc_seq_sim_cap.restype = C.c_int
+            lib.orc_picard_chunked_cap.argtypes = capc + [i32, i32, P, P, P, P, P, P]
+            lib.orc_picard_chunked_cap.restype = C.c_int
+            lib.orc_picard_partition.argtypes = [i32, i32, i32, i32, P, P, P, P, P, P, i32, i32,
+                                                 P, P, P, P, P, u64, i32, P, i32, i32, P, P, P, P]
+            lib.orc_picard_partition.restype = C.c_int
             lib.orc_mlp_scores.argtypes = [C.c_int, C.c_int, P, P, P, P, P, P, i32, P, P]
             lib.orc_mlp_scores.restype = None
             lib.orc_philox4x32_10.argtypes = [P, P, P]
@@ -101,14 +109,43 @@ def _args(inst, pol):
     return args, keep
 
 
+def _cap(inst):
+    cap = getattr(inst, "cap", None)
+    return None if cap is None else _c(cap, np.int32)
+
+
+def _cap_args(inst, pol, cap):
+    kind = KINDS[pol.kind]
+    if kind >= 2:
+        raise ValueError("capacity: integer policies only (greedy, dual)")
+    keep = [_c(inst.prod, np.int32), _c(inst.reg, np.int32), _c(inst.x0, np.int32), cap,
+            _c(inst.cost, np.int32), _c(inst.lam, np.int32) if kind == 1 else None]
+    return [inst.T, inst.N, inst.K, inst.R] + [_p(a) for a in keep] + [kind], keep
+
+
 def seq_sim(inst, pol):
     """Sequential simulation a_t = pi(s_t, w_t), s_{t+1} = f(s_t, a_t, w_t)
-    (Sec. 2 problem statement, Sec. 3 inventory dynamics).
+    (Sec. 2 problem statement, Sec. 3 inventory dynamics; with inst.cap set, the
+    Sec. 3 state (x, c) with node capacity, integer policies only, and the
+    result also holds "c_final").
 
     Pins: brute-force argmin/argmax per step on tiny inputs, conservation
-    (units shipped = x0 - x_final), non-negative stock, a^phi iff no stock,
-    textbook special cases (ample stock => unconstrained argmin)."""
+    (units shipped = x0 - x_final, = cap - c_final per node), non-negative stock
+    and capacity, a^phi iff no feasible node, textbook special cases (ample
+    stock => unconstrained argmin; ample capacity => the inventory-only path)."""
     lib = _load()
+    cap = _cap(inst)
+    if cap is not None:
+        args, keep = _cap_args(inst, pol, cap)
+        act = np.empty(inst.T, np.int8)
+        xf = np.empty((inst.K, inst.N), np.int32)
+        cf = np.empty(inst.N, np.int32)
+        tc, lost = C.c_int64(0), C.c_int64(0)
+        rc = lib.orc_seq_sim_cap(*args, _p(act), _p(xf), _p(cf), C.byref(tc), C.byref(lost))
+        if rc != OK:
+            raise ValueError(f"orc_seq_sim_cap failed rc={rc}")
+        return {"actions": act, "x_final": xf, "c_final": cf, "total_cost": tc.value,
+                "lost": lost.value}
     args, keep = _args(inst, pol)
     act = np.empty(inst.T, np.int8)
     xf = np.empty((inst.K, inst.N), np.int32)
@@ -119,9 +156,10 @@ def seq_sim(inst, pol):
     return {"actions": act, "x_final": xf, "total_cost": tc.value, "lost": lost.value}
 
 
-def _picard(fn, inst, pol, M, max_iters, alpha_init, record, extra):
+def _picard(fn, inst, pol, M, max_iters, alpha_init, record, extra, args=None, keep=None):
     lib = _load()
-    args, keep = _args(inst, pol)
+    if args is None:
+        args, keep = _args(inst, pol)
     if max_iters is None:
         max_iters = M + 1
     act = np.empty(inst.T, np.int8)
@@ -159,9 +197,43 @@ def picard_literal(inst, pol, M, max_iters=None, alpha_init=None, record=False):
 
 def picard_chunked(inst, pol, M, max_iters=None, alpha_init=None, record=False):
     """Algorithm 1 on the same blocks with the cached-prefix replay in closed form
-    max(0, x0 - d).  Pins: identical iterates alpha^k to picard_literal for every
-    k on exhaustive tiny instances and random small ones; fixed point = seq_sim."""
+    max(0, x0 - d) (with inst.cap set: also c = max(0, cap - q), q the cached
+    actions that found inventory).  Pins: identical iterates alpha^k to
+    picard_literal / picard_partition for every k on exhaustive tiny instances
+    and random small ones; fixed point = seq_sim; ample capacity gives the
+    inventory-only iterates."""
+    cap = _cap(inst)
+    if cap is not None:
+        args, keep = _cap_args(inst, pol, cap)
+        return _picard(_load().orc_picard_chunked_cap, inst, pol, M, max_iters, alpha_init,
+                       record, True, args, keep)
     return _picard(_load().orc_picard_chunked, inst, pol, M, max_iters, alpha_init, record, True)
+
+
+def picard_partition(inst, pol, proc, max_iters=None, alpha_init=None, record=False):
+    """Algorithm 1 verbatim for any assignment proc[t] of time-steps to
+    processes (contiguous blocks, product partitions of Sec. 3, uniform random
+    assignment), with node capacity when inst.cap is set.  M = max(proc) + 1;
+    max_iters defaults to T + 1 (Prop. 1).
+
+    Pins: with proc[t] = t // L it equals picard_literal (no capacity) and
+    picard_chunked (capacity) iterate by iterate; its fixed point is seq_sim
+    (Prop. 1); with product partitions and a greedy / bid-price policy the cache
+    is exact after at most |Q_T| + 1 passes, Q_T the nodes whose capacity the
+    sequential path exhausts (Thm. 3.1); without binding capacity product
+    partitions are exact after one pass."""
+    lib = _load()
+    cap = _cap(inst)
+    pr = _c(proc, np.int32)
+    M = int(pr.max()) + 1 if len(pr) else 1
+    if max_iters is None:
+        max_iters = inst.T + 1
+    base, keep = _args(inst, pol)
+    # base: T,N,K,R,prod,reg,x0,cost,lam,kind,H,W1,b1,W2,b2,E,seed,traj
+    args = base[:7] + [_p(cap)] + base[7:] + [_p(pr)]
+    keep = keep + [cap, pr]
+    return _picard(lib.orc_picard_partition, inst, pol, M, max_iters, alpha_init, record, False,
+                   args, keep)
 
 
 def mlp_scores(N, mlp, cost_row, r, stock_row):

@@ -433,3 +433,222 @@ int orc_policy_call(int32_t N, int32_t R, const int32_t* cost, const int32_t* la
     free(P.scratch);
     return a;
 }
+
+/* ========================================================================= */
+/* FO with node capacity (Sec. 3).  The state is (x, c): inventory x[K][N] and
+ * node capacity c[N].  An order of product k may go to node n only if
+ * x[k][n] > 0 and c[n] > 0; f decrements both.  The integer policies (greedy,
+ * bid-price) choose over that feasible set with the same scores as above, so a
+ * policy call sees the row m[n] = (x[k][n] > 0 && c[n] > 0).  The MLP policies
+ * take stock features and are not defined here with capacity. */
+/* ========================================================================= */
+static int check_cap(int32_t N, const int32_t* cap, int32_t kind) {
+    if (kind != ORC_GREEDY && kind != ORC_DUAL) return ORC_ERR_ARG;
+    for (int n = 0; n < N; ++n)
+        if (cap[n] < 0) return ORC_ERR_ARG;
+    return ORC_OK;
+}
+
+/* policy call on the feasible set of (row, c); c == NULL: no capacity */
+static int cap_policy(policy_t* P, const int32_t* row, const int32_t* c, int32_t* mask, int32_t k,
+                      int32_t r, int64_t t) {
+    if (!c) return policy_eval(P, row, k, r, t);
+    for (int n = 0; n < P->N; ++n) mask[n] = (row[n] > 0 && c[n] > 0) ? 1 : 0;
+    return policy_eval(P, mask, k, r, t);
+}
+
+/* Sequential simulation with capacity.  Outputs as orc_seq_sim plus c_final[N]
+ * (may be NULL). */
+int orc_seq_sim_cap(int32_t T, int32_t N, int32_t K, int32_t R, const int32_t* prod,
+                    const int32_t* reg, const int32_t* x0, const int32_t* cap, const int32_t* cost,
+                    const int32_t* lam, int32_t kind, int8_t* act, int32_t* x_final,
+                    int32_t* c_final, int64_t* total_cost, int64_t* lost) {
+    int rc = check_instance(T, N, K, R, prod, reg, x0);
+    if (rc) return rc;
+    if (!cap || check_cap(N, cap, kind)) return ORC_ERR_ARG;
+    policy_t P;
+    rc = policy_init(&P, kind, N, R, cost, lam, 0, NULL, NULL, NULL, NULL, NULL, 0, 0);
+    if (rc) return rc;
+    int32_t* x = (int32_t*)malloc(sizeof(int32_t) * (size_t)K * N);
+    int32_t* c = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
+    int32_t* mask = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
+    memcpy(x, x0, sizeof(int32_t) * (size_t)K * N);
+    memcpy(c, cap, sizeof(int32_t) * (size_t)N);
+    int64_t tc = 0, nl = 0;
+    for (int64_t t = 0; t < T; ++t) {
+        int32_t k = prod[t], r = reg[t];
+        int32_t* row = x + (size_t)k * N;
+        int a = cap_policy(&P, row, c, mask, k, r, t);
+        act[t] = (int8_t)a;
+        if (a >= 0) {
+            row[a] -= 1;
+            c[a] -= 1;
+            tc += cost[(size_t)r * N + a];
+        } else {
+            nl += 1;
+        }
+    }
+    if (x_final) memcpy(x_final, x, sizeof(int32_t) * (size_t)K * N);
+    if (c_final) memcpy(c_final, c, sizeof(int32_t) * (size_t)N);
+    if (total_cost) *total_cost = tc;
+    if (lost) *lost = nl;
+    free(x); free(c); free(mask); free(P.scratch);
+    return ORC_OK;
+}
+
+/* Algorithm 1 verbatim for an arbitrary assignment of time-steps to processes:
+ * proc[t] in [0, M) is the process that owns t (contiguous blocks, product
+ * partitions T_m = union of T_i over i in I_m, or a uniform random assignment).
+ * Process m restarts from s_1 = (x0, cap), walks t = 0 .. its last own step,
+ * evaluates pi on its own steps and applies the cached action elsewhere if it
+ * is feasible in its own state (else a^phi).  cap == NULL: no capacity (then
+ * every policy kind is allowed).  Outputs as orc_picard_literal. */
+int orc_picard_partition(int32_t T, int32_t N, int32_t K, int32_t R, const int32_t* prod,
+                         const int32_t* reg, const int32_t* x0, const int32_t* cap,
+                         const int32_t* cost, const int32_t* lam, int32_t kind, int32_t H,
+                         const uint16_t* W1, const uint16_t* b1, const uint16_t* W2,
+                         const uint16_t* b2, const uint16_t* E, uint64_t seed, int32_t traj,
+                         const int32_t* proc, int32_t M, int32_t max_iters,
+                         const int8_t* alpha_init, int8_t* act_out, int32_t* iters_out,
+                         int8_t* iterates) {
+    int rc = check_instance(T, N, K, R, prod, reg, x0);
+    if (rc) return rc;
+    if (M <= 0 || max_iters <= 0 || !proc) return ORC_ERR_ARG;
+    if (cap && check_cap(N, cap, kind)) return ORC_ERR_ARG;
+    for (int64_t t = 0; t < T; ++t)
+        if (proc[t] < 0 || proc[t] >= M) return ORC_ERR_ARG;
+    policy_t P;
+    rc = policy_init(&P, kind, N, R, cost, lam, H, W1, b1, W2, b2, E, seed, traj);
+    if (rc) return rc;
+    int64_t* last = (int64_t*)malloc(sizeof(int64_t) * (size_t)M);
+    for (int32_t m = 0; m < M; ++m) last[m] = -1;
+    for (int64_t t = 0; t < T; ++t) last[proc[t]] = t;
+    int8_t* prev = (int8_t*)malloc((size_t)T + 1);
+    int8_t* next = (int8_t*)malloc((size_t)T + 1);
+    int32_t* s = (int32_t*)malloc(sizeof(int32_t) * (size_t)K * N);
+    int32_t* c = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
+    int32_t* mask = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
+    for (int64_t t = 0; t < T; ++t) prev[t] = alpha_init ? alpha_init[t] : (int8_t)-1;
+    int converged = 0, k;
+    for (k = 1; k <= max_iters; ++k) {
+        for (int32_t m = 0; m < M; ++m) {
+            if (last[m] < 0) continue;
+            memcpy(s, x0, sizeof(int32_t) * (size_t)K * N); /* s^{k,m}_1 = s_1 */
+            if (cap) memcpy(c, cap, sizeof(int32_t) * (size_t)N);
+            for (int64_t t = 0; t <= last[m]; ++t) {
+                int32_t pk = prod[t], r = reg[t];
+                int32_t* row = s + (size_t)pk * N;
+                int a;
+                if (proc[t] == m) {
+                    a = cap_policy(&P, row, cap ? c : NULL, mask, pk, r, t);
+                    next[t] = (int8_t)a;
+                } else {
+                    a = prev[t];
+                    if (a >= 0 && !(a < N && row[a] > 0 && (!cap || c[a] > 0))) a = -1;
+                }
+                if (a >= 0) {
+                    row[a] -= 1;
+                    if (cap) c[a] -= 1;
+                }
+            }
+        }
+        if (iterates) memcpy(iterates + (size_t)(k - 1) * T, next, (size_t)T);
+        int same = 1;
+        for (int64_t t = 0; t < T; ++t)
+            if (next[t] != prev[t]) { same = 0; break; }
+        int8_t* tmp = prev; prev = next; next = tmp;
+        if (same) { converged = 1; break; }
+    }
+    memcpy(act_out, prev, (size_t)T);
+    *iters_out = converged ? k : max_iters;
+    free(last); free(prev); free(next); free(s); free(c); free(mask); free(P.scratch);
+    return converged ? ORC_OK : ORC_ERR_NOT_CONVERGED;
+}
+
+/* Algorithm 1 with capacity on contiguous blocks [m*L, min((m+1)*L, T)), the
+ * cached-prefix replay written in closed form.  Replaying cached actions before
+ * a block, every decrement is conditional on positivity, and a node whose
+ * capacity reached 0 never becomes feasible again; hence at the block start
+ *   x[k][n] = max(0, x0[k][n] - D[k][n]) for every node with c[n] > 0, and
+ *   c[n]    = max(0, cap[n] - Q[n]),
+ * with D[k][n] = cached actions of product k naming n before the block, and
+ * Q[n] = those cached actions naming n that found inventory, i.e. were taken
+ * while the running D[k][n] was below x0[k][n] (the rows of nodes with c[n] = 0
+ * are never consulted: such nodes are infeasible).  Each block then replays its
+ * own orders from that state with fresh policy calls.  Same outputs, iterates
+ * and iteration count as orc_picard_partition with proc[t] = t / L. */
+int orc_picard_chunked_cap(int32_t T, int32_t N, int32_t K, int32_t R, const int32_t* prod,
+                           const int32_t* reg, const int32_t* x0, const int32_t* cap,
+                           const int32_t* cost, const int32_t* lam, int32_t kind, int32_t M,
+                           int32_t max_iters, const int8_t* alpha_init, int8_t* act_out,
+                           int32_t* iters_out, int8_t* iterates, int64_t* changed_out,
+                           int64_t* first_changed_out) {
+    int rc = check_instance(T, N, K, R, prod, reg, x0);
+    if (rc) return rc;
+    if (M <= 0 || max_iters <= 0 || !cap || check_cap(N, cap, kind)) return ORC_ERR_ARG;
+    policy_t P;
+    rc = policy_init(&P, kind, N, R, cost, lam, 0, NULL, NULL, NULL, NULL, NULL, 0, 0);
+    if (rc) return rc;
+    const int64_t L = ((int64_t)T + M - 1) / M;
+    int8_t* prev = (int8_t*)malloc((size_t)T + 1);
+    int8_t* next = (int8_t*)malloc((size_t)T + 1);
+    int32_t* D = (int32_t*)malloc(sizeof(int32_t) * (size_t)K * N);
+    int32_t* Q = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
+    int32_t* S = (int32_t*)malloc(sizeof(int32_t) * (size_t)K * N);
+    int32_t* c = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
+    int32_t* mask = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
+    int32_t* stamp = (int32_t*)malloc(sizeof(int32_t) * (size_t)K);
+    for (int64_t t = 0; t < T; ++t) prev[t] = alpha_init ? alpha_init[t] : (int8_t)-1;
+    int converged = 0, k;
+    for (k = 1; k <= max_iters; ++k) {
+        memset(D, 0, sizeof(int32_t) * (size_t)K * N);
+        memset(Q, 0, sizeof(int32_t) * (size_t)N);
+        for (int32_t i = 0; i < K; ++i) stamp[i] = -1;
+        for (int32_t m = 0; m < M; ++m) {
+            int64_t lo = (int64_t)m * L, hi = lo + L < T ? lo + L : T;
+            if (lo >= hi) break;
+            for (int n = 0; n < N; ++n) {
+                int32_t v = cap[n] - Q[n];
+                c[n] = v > 0 ? v : 0;
+            }
+            for (int64_t t = lo; t < hi; ++t) {
+                int32_t pk = prod[t], r = reg[t];
+                int32_t* row = S + (size_t)pk * N;
+                if (stamp[pk] != m) { /* first order of product pk in this block */
+                    for (int n = 0; n < N; ++n) {
+                        int32_t v = x0[(size_t)pk * N + n] - D[(size_t)pk * N + n];
+                        row[n] = v > 0 ? v : 0;
+                    }
+                    stamp[pk] = m;
+                }
+                int a = cap_policy(&P, row, c, mask, pk, r, t);
+                next[t] = (int8_t)a;
+                if (a >= 0) {
+                    row[a] -= 1;
+                    c[a] -= 1;
+                }
+            }
+            /* extend the prefix by this block's cached (previous-pass) actions */
+            for (int64_t t = lo; t < hi; ++t) {
+                int a = prev[t];
+                if (a < 0 || a >= N) continue;
+                int32_t* d = D + (size_t)prod[t] * N + a;
+                if (*d < x0[(size_t)prod[t] * N + a]) Q[a] += 1;
+                *d += 1;
+            }
+        }
+        int64_t nchg = 0, first = T;
+        for (int64_t t = 0; t < T; ++t)
+            if (next[t] != prev[t]) { if (first == T) first = t; nchg++; }
+        if (iterates) memcpy(iterates + (size_t)(k - 1) * T, next, (size_t)T);
+        if (changed_out) changed_out[k - 1] = nchg;
+        if (first_changed_out) first_changed_out[k - 1] = first;
+        int8_t* tmp = prev; prev = next; next = tmp;
+        if (nchg == 0) { converged = 1; break; }
+    }
+    memcpy(act_out, prev, (size_t)T);
+    *iters_out = converged ? k : max_iters;
+    free(prev); free(next); free(D); free(Q); free(S); free(c); free(mask); free(stamp);
+    free(P.scratch);
+    return converged ? ORC_OK : ORC_ERR_NOT_CONVERGED;
+}

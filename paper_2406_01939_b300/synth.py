@@ -21,6 +21,8 @@ Named workloads (sizes as the benchmark and tests use them):
   batch_uneven    512 trajectories, T_i ~ U{16,384..262,144}, N=32, K=2,000,
                   R=200; even index greedy, odd index MLP.
   pg_large        64 trajectories of T=2^20, N=64, K=10,000, R=1,000, Gumbel MLP.
+  capacity_large  dual_large plus node capacity c_1 for 80% of the orders, spread
+                  pro rata to log-normal(0, 0.5) node weights (Sec. 3 model).
 Product demand is a finite Zipf(1.1): p_k proportional to (k+1)^-1.1, product 0
 the most popular; regions are uniform.
 """
@@ -48,6 +50,7 @@ class Instance:
     x0: np.ndarray  # int32 [K, N] initial inventory
     cost: np.ndarray  # int32 [R, N] fulfilment cost
     lam: Optional[np.ndarray] = None  # int32 [K, N] dual prices (bid-price policy)
+    cap: Optional[np.ndarray] = None  # int32 [N] node capacity c_1 (None: no capacity)
 
 
 @dataclass
@@ -173,6 +176,23 @@ def batch_uneven(seed=0, B=512, Tlo=16_384, Thi=262_144, N=32, K=2_000, R=200):
                                    stock="poisson", shared_tables=(cost, None)))
         pols.append(Policy("greedy") if b % 2 == 0 else Policy("mlp", mlp=mlp))
     return insts, pols
+
+
+def node_capacity(T, N, seed=0, frac=0.8, sigma=0.5):
+    """Node capacity for about frac x T orders in total, spread over nodes pro
+    rata to seeded log-normal(0, sigma) weights (the stand-in for the paper's
+    population weights, Appendix A.3)."""
+    rng = np.random.Generator(np.random.PCG64(seed + 0xCA9))
+    w = rng.lognormal(0.0, sigma, size=N)
+    return np.floor(frac * T * w / w.sum()).astype(np.int32)
+
+
+def capacity_large(seed=0, T=1 << 20, N=64, K=10_000, R=1_000, frac=0.8):
+    """dual_large's orders, stock, costs and prices plus node capacity for 80%
+    of the orders (the paper's FO model with capacity, Sec. 3)."""
+    inst = dual_large(seed, T=T, N=N, K=K, R=R)
+    inst.cap = node_capacity(T, N, seed=seed, frac=frac)
+    return inst
 
 
 def pg_large(seed=0, B=64, T=1 << 20, N=64, K=10_000, R=1_000):

@@ -99,6 +99,10 @@ typedef struct {
     const int32_t* lam;  /* [K][N] dual prices for PIC_POLICY_DUAL, or NULL */
     int32_t mem;         /* PIC_MEM_HOST or PIC_MEM_DEVICE: where the arrays above live */
     void* stream;        /* cudaStream_t for the copies and preprocessing, or NULL */
+    const int32_t* cap;  /* [N] node capacity c_1 >= 0 (Sec. 3's state (x, c)), or NULL: no
+                            capacity constraint.  With capacity an order may go to node n only
+                            if x[k][n] > 0 and c[n] > 0, and f decrements both; greedy and
+                            bid-price policies only; single instances only (not batches) */
 } pic_instance_desc;
 
 /* Policy.  MLP parameters are BF16 bit patterns in DEVICE memory, borrowed for
@@ -170,8 +174,8 @@ typedef struct {
  * pic_destroy_instance).  Errors: INVALID_ARG, OOM, CUDA. */
 pic_status pic_create_instance(const pic_instance_desc* desc, pic_instance** out);
 
-/* Replace an instance's inputs with new arrays of the same T, N, K, R (and lam
- * present iff it was at create time), reusing its device memory.  Used to stream
+/* Replace an instance's inputs with new arrays of the same T, N, K, R (and lam,
+ * cap present iff they were at create time), reusing its device memory.  Used to stream
  * new trajectories through one instance.  Errors: INVALID_ARG, CUDA. */
 pic_status pic_instance_load(pic_instance* inst, const pic_instance_desc* desc);
 
@@ -184,6 +188,13 @@ void pic_destroy_instance(pic_instance* inst);
  * opts.alpha_init), and stops at the first pass that changes no cached action;
  * the result equals the sequential path (Prop. 1).  PIC_MODE_SEQUENTIAL runs the
  * sequential definition directly.
+ * With node capacity (desc.cap) each chunk replays its orders in time order,
+ * because capacity couples products; its start state is the cached prefix in
+ * closed form, x[k][n] = max(0, x0[k][n] - d[k][n]) and c[n] = max(0, c_1[n] - q[n])
+ * with d the cached actions of product k naming n before the chunk and q those
+ * of them that found inventory.  The chunk length ceil(T/M) must be at most 64
+ * (num_chunks = 0 picks M = ceil(T/64)); seg_window and the MLP / group /
+ * tensor-core flags do not apply.
  *   actions_out  [T] int8 in opts.out_mem memory (required);
  *   final_stock  [K][N] int32 in opts.out_mem memory, or NULL;
  *   res          host struct, or NULL.
@@ -222,7 +233,8 @@ pic_status pic_simulate_sequential_static(const pic_instance_desc* desc, int32_t
  * one combined instance: trajectory b's orders, products and regions occupy
  * their own index ranges in the order given, so trajectories never share state.
  * Limits: sum of T < 2^31, sum of K < 2^31, sum of R < 2^31.  Release with
- * pic_destroy_instance.  Errors: INVALID_ARG (names the trajectory), OOM, CUDA. */
+ * pic_destroy_instance.  Errors: INVALID_ARG (names the trajectory), UNSUPPORTED
+ * (a desc with cap), OOM, CUDA. */
 pic_status pic_create_batch(const pic_instance_desc* descs, int32_t B, pic_instance** out);
 
 /* Simulate every trajectory of a batch instance, each under its own policy,

@@ -43,7 +43,7 @@ class pic_instance_desc(C.Structure):
     _fields_ = [("T", C.c_int32), ("N", C.c_int32), ("K", C.c_int32), ("R", C.c_int32),
                 ("prod", C.c_void_p), ("reg", C.c_void_p), ("x0", C.c_void_p),
                 ("cost", C.c_void_p), ("lam", C.c_void_p), ("mem", C.c_int32),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("cap", C.c_void_p)]
 
 
 class pic_policy(C.Structure):
@@ -143,12 +143,14 @@ def _stream_handle(stream):
     return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
 
 
-def make_desc(T, N, K, R, prod, reg, x0, cost, lam=None, mem=PIC_MEM_DEVICE, stream=None):
+def make_desc(T, N, K, R, prod, reg, x0, cost, lam=None, mem=PIC_MEM_DEVICE, stream=None,
+              cap=None):
     """Build a pic_instance_desc from int32 arrays (torch CUDA tensors for
-    mem=PIC_MEM_DEVICE, C-contiguous numpy arrays for PIC_MEM_HOST).  The caller
-    keeps the arrays alive for the duration of the call."""
+    mem=PIC_MEM_DEVICE, C-contiguous numpy arrays for PIC_MEM_HOST).  cap: [N]
+    node capacity, or None.  The caller keeps the arrays alive for the duration
+    of the call."""
     return pic_instance_desc(int(T), int(N), int(K), int(R), _ptr(prod), _ptr(reg), _ptr(x0),
-                             _ptr(cost), _ptr(lam), int(mem), _stream_handle(stream))
+                             _ptr(cost), _ptr(lam), int(mem), _stream_handle(stream), _ptr(cap))
 
 
 def pic_create_instance(desc: pic_instance_desc) -> int:

@@ -59,6 +59,11 @@ __global__ void k_validate(int T, int N, int K, int R, const int32_t* __restrict
 }
 
 // Exact check of |cost[r][n] - lam[k][n]| < 2^23 via per-warehouse extremes.
+__global__ void k_validate_cap(int N, const int32_t* __restrict__ cap, int* bad) {
+    for (int n = threadIdx.x; n < N; n += blockDim.x)
+        if (cap[n] < 0) atomicOr(bad, 256);
+}
+
 __global__ void k_validate_dual(int N, int K, int R, const int32_t* __restrict__ cost,
                                 const int32_t* __restrict__ lam, int* bad) {
     const int n = blockIdx.x;
@@ -152,6 +157,7 @@ pic_status copy_inputs(Instance& I, const pic_instance_desc* d, cudaStream_t st)
     CU(cudaMemcpyAsync(I.x0, d->x0, sizeof(int32_t) * I.K * I.N, kind, st));
     CU(cudaMemcpyAsync(I.cost, d->cost, sizeof(int32_t) * I.R * I.N, kind, st));
     if (I.has_lam) CU(cudaMemcpyAsync(I.lam, d->lam, sizeof(int32_t) * I.K * I.N, kind, st));
+    if (I.has_cap) CU(cudaMemcpyAsync(I.cap, d->cap, sizeof(int32_t) * I.N, kind, st));
     CU(launch_validate(I, st));
     int* bad = &I.ctrl->pad0;
     int hb = 0;
@@ -162,6 +168,7 @@ pic_status copy_inputs(Instance& I, const pic_instance_desc* d, cudaStream_t st)
     if (hb & 4) return fail(PIC_ERR_INVALID_ARG, "x0 has a negative entry");
     if (hb & (8 | 16 | 32))
         return fail(PIC_ERR_INVALID_ARG, "|cost|, |lam| or |cost - lam| not below 2^23");
+    if (hb & 256) return fail(PIC_ERR_INVALID_ARG, "cap has a negative entry");
     I.cost16 = (hb & 128) ? 0 : 1;
     return PIC_OK;
 }
@@ -186,6 +193,7 @@ cudaError_t launch_validate(Instance& I, cudaStream_t st) {
     k_validate<<<2 * I.num_sms, 256, 0, st>>>(I.T, I.N, I.K, I.R, I.prod, I.reg, I.x0, I.cost,
                                               I.has_lam ? I.lam : nullptr, bad);
     if (I.has_lam) k_validate_dual<<<I.N, 256, 0, st>>>(I.N, I.K, I.R, I.cost, I.lam, bad);
+    if (I.has_cap) k_validate_cap<<<1, 128, 0, st>>>(I.N, I.cap, bad);
     return cudaGetLastError();
 }
 
@@ -195,7 +203,8 @@ void free_instance(Instance& I) {
                     I.pstart, I.run_start, I.run_of, I.seg_run, I.seg_of_run, I.seg_prod, I.seg_cf,
                     I.seg_ce, I.seg_meta, I.seg_lpt, I.len_hist, I.alpha_s, I.agg, I.carry, I.sbagg,
                     I.sbincl, I.fc, I.xfin, I.xwork, I.act_t, I.tmp_a, I.tmp_b, I.tmp_c, I.scan_blk,
-                    I.hist, I.ctrl, I.trace, I.mlp_P, I.mlp_W1p, I.mlp_W2p, I.mlp_b2, I.mlp_Emax, I.mlp_bnd};
+                    I.hist, I.ctrl, I.trace, I.mlp_P, I.mlp_W1p, I.mlp_W2p, I.mlp_b2, I.mlp_Emax, I.mlp_bnd,
+                    I.cap, I.cap_run_t, I.cap_info, I.cap_inv, I.cap_qagg, I.cap_qinc};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < 4; ++i)
@@ -344,6 +353,8 @@ pic_status pic_create_instance(const pic_instance_desc* d, pic_instance** out) {
     Instance& I = h->I;
     memset(&I, 0, sizeof(I));
     cudaError_t e = alloc_instance(I, d->T, d->N, d->K, d->R, d->lam != nullptr);
+    I.has_cap = d->cap != nullptr;
+    if (!e && I.has_cap) e = dmalloc(&I.cap, (size_t)d->N);
     // per-segment histograms: allocated lazily at the first simulate (size depends on W)
     if (e) {
         free_instance(I);
@@ -373,9 +384,11 @@ pic_status pic_instance_load(pic_instance* h, const pic_instance_desc* d) {
     if (!valid_desc(d)) return fail(PIC_ERR_INVALID_ARG, "invalid instance descriptor");
     Instance& I = h->I;
     if (I.batch) return fail(PIC_ERR_INVALID_ARG, "batch instance: inputs are fixed at pic_create_batch");
-    if (d->T != I.T || d->N != I.N || d->K != I.K || d->R != I.R || (d->lam != nullptr) != (I.has_lam != 0))
+    if (d->T != I.T || d->N != I.N || d->K != I.K || d->R != I.R || (d->lam != nullptr) != (I.has_lam != 0) ||
+        (d->cap != nullptr) != (I.has_cap != 0))
         return fail(PIC_ERR_INVALID_ARG, "shape differs from the instance's");
     I.tables_m = 0;  // the order tables describe the old stream
+    I.cap_tables_m = 0;
     return copy_inputs(I, d, (cudaStream_t)d->stream);
 }
 
@@ -405,6 +418,8 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
         return fail(PIC_ERR_UNSUPPORTED, "MLP hidden width must be %d", kHidden);
     if (mlp && (!pol->W1 || !pol->b1 || !pol->W2 || !pol->b2 || !pol->E))
         return fail(PIC_ERR_INVALID_ARG, "MLP policy needs W1, b1, W2, b2 and E (device pointers)");
+    if (mlp && I.has_cap)
+        return fail(PIC_ERR_UNSUPPORTED, "node capacity: greedy and bid-price policies only");
     if (opts->num_chunks < 0 || opts->max_iters < 0 || opts->seg_window < 0)
         return fail(PIC_ERR_INVALID_ARG, "negative num_chunks, max_iters or seg_window");
     cudaStream_t st = (cudaStream_t)opts->stream;
@@ -421,7 +436,9 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
     if (opts->mode == PIC_MODE_SEQUENTIAL) {
         CU(cudaMemcpyAsync(I.xwork, I.x0, sizeof(int32_t) * K * N, cudaMemcpyDeviceToDevice, st));
         if (timing) CU(cudaEventRecord(I.ev[1], st));
-        if (T && mlp) {
+        if (T && I.has_cap) {
+            CU(sequential_cap(&I, pol->kind, st));
+        } else if (T && mlp) {
             CU(sequential_mlp(&I, pol, st));
             CU(reduce_costs(&I, I.act_t, I.reg, st));
         } else if (T) {
@@ -431,6 +448,38 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
         if (T) CU(cudaMemcpyAsync(actions_out, I.act_t, T, okind, st));
         if (final_stock)
             CU(cudaMemcpyAsync(final_stock, I.xwork, sizeof(int32_t) * K * N, okind, st));
+    } else if (I.has_cap) {
+        // time chunks of at most kCapChunk orders, one run per segment
+        M = opts->num_chunks ? opts->num_chunks : (int)((T + kCapChunk - 1) / kCapChunk);
+        if (M < 1) M = 1;
+        if (T && M > (int)T) M = (int)T;
+        if (T && (T + M - 1) / M > (size_t)kCapChunk)
+            return fail(PIC_ERR_INVALID_ARG,
+                        "node capacity: chunk length ceil(T/M) = %zu exceeds %d (raise num_chunks)",
+                        (T + M - 1) / M, kCapChunk);
+        iters_cap = opts->max_iters ? opts->max_iters : M + 1;
+        CU(prepare_picard_state(I, 1, iters_cap, st));
+        const bool reuse = (opts->flags & PIC_FLAG_REUSE_TABLES) && I.tables_m == M && I.tables_w == 1;
+        if (!reuse) {
+            CU(build_tables(&I, M, 1, st));
+            I.tables_m = M;
+            I.tables_w = 1;
+            I.cap_tables_m = 0;
+        }
+        CU(take_tags(I, iters_cap, st));
+        CU(init_cache(I, opts->alpha_init, st));
+        if (T) {
+            if (timing) CU(cudaEventRecord(I.ev[1], st));
+            const bool trace = opts->trace && opts->trace_cap > 0;
+            if (trace) CU(cudaMemsetAsync(I.trace, 0, sizeof(long long) * 4 * kTraceCap, st));
+            CU(picard_cap(&I, pol, M, iters_cap, opts->flags, opts->alpha_init,
+                          opts->timeout_ns ? opts->timeout_ns : 10000000000ull, trace, st));
+            if (timing) CU(cudaEventRecord(I.ev[2], st));
+            CU(reduce_costs(&I, I.act_t, I.reg, st));
+            CU(cudaMemcpyAsync(actions_out, I.act_t, T, okind, st));
+        }
+        if (final_stock)
+            CU(cudaMemcpyAsync(final_stock, I.xfin, sizeof(int32_t) * K * N, okind, st));
     } else {
         M = opts->num_chunks ? opts->num_chunks : (int)((T + 255) / 256);
         if (M < 1) M = 1;

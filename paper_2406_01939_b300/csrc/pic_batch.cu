@@ -555,6 +555,7 @@ pic_status pic_create_batch(const pic_instance_desc* descs, int32_t B, pic_insta
         if (!desc_ok(d))
             return fail(PIC_ERR_INVALID_ARG, "trajectory %d: invalid descriptor (sizes, pointers or mem)", b);
         if (d->N != N) return fail(PIC_ERR_INVALID_ARG, "trajectory %d: N = %d differs from N = %d", b, d->N, N);
+        if (d->cap) return fail(PIC_ERR_UNSUPPORTED, "trajectory %d: node capacity is not supported in a batch", b);
         T += d->T;
         K += d->K;
         R += d->R;

@@ -226,31 +226,9 @@ __global__ void __launch_bounds__(kGrpThreads, 1) k_picard_grp(KArgs a, int NP8)
         // ---- phase S: chain prefixes (warp per super-block, natural segment order)
         for (int k = gtid; k < a.K; k += gthreads) fc_cur[k] = INT_MAX;
         if (gtid == 0) a.ctrl->changed[parity] = 0;
-        if (it > 1 || a.first_dirty) {
-            for (int j0 = 0; gwarp + j0 * nwarps < nseg; j0 += 32) {
-                const int sl = gwarp + (j0 + lane) * nwarps;
-                bool head = false;
-                if (sl < nseg) {
-                    const SegMeta m = load_meta(a.meta + sl);
-                    head = m.ce - m.cf > 1 && (sl - m.cf) % kSuperBlock == 0;
-                    const int f = it > 1 ? fc_prev[m.k] : -1;
-                    if (head && it > 1) head = f != INT_MAX;
-                    if (head) {
-                        s_meta[wib][lane] = m;
-                        s_fcp[wib][lane] = f;
-                    }
-                }
-                unsigned todo = __ballot_sync(kFull, head);
-                while (todo) {  // increasing segment order (lane order)
-                    const int src = __ffs(todo) - 1;
-                    todo &= todo - 1;
-                    const SegMeta mm = smem_meta(&s_meta[wib][src]);
-                    superblock_prefix<NPL>(a, gwarp + (j0 + src) * nwarps, mm, it,
-                                           tag_base + (unsigned)it, s_fcp[wib][src], deadline);
-                }
-                __syncwarp();
-            }
-        }
+        if (it > 1 || a.first_dirty)
+            chain_prefixes<NPL>(a, it, fc_prev, tag_base + (unsigned)it, deadline, s_meta[wib],
+                                s_fcp[wib]);
         if (!grid_sync(a.ctrl, deadline)) { ok = false; break; }
         if (tr && gtid == 0) tr[0] = (long long)(globaltimer_ns() - t_start);
         // ---- phase R: longest-first positions dealt to warps in a snake; each

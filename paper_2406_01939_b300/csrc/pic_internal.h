@@ -19,6 +19,7 @@ constexpr int kTraceCap = 4096;    // passes recorded by the device-side trace
 constexpr int kLenBuckets = 1024;  // segment-length buckets of the longest-first order
 constexpr size_t kGrpSmemMax = 150 * 1024;  // cost table budget of the group-per-segment kernel
 constexpr int kMlpLptWeight = 64;  // work of an MLP order relative to an integer-policy order
+constexpr int kCapChunk = 64;      // longest time chunk of the capacity kernel (orders)
 
 // Device-side control block of one simulate call (zeroed before each launch).
 struct Ctrl {
@@ -36,6 +37,7 @@ struct Ctrl {
     unsigned long long seg_replays;
     unsigned long long mlp_calls;  // MLP / Gumbel policy evaluations (batch kernel)
     unsigned long long tc_rows;    // MLP decisions taken from tensor-core tile scores
+    int cap_fct[2];          // capacity kernel: first changed time of the pass, per parity
     int nruns;               // tables built by the preprocessing kernels
     int nseg;
     int last_m;              // chunk count the tables were built for
@@ -151,6 +153,17 @@ struct Instance {
     int cta_threads, ctas_per_sm;     // its CTA shape
     int launches;                     // kernels launched by the current call
     cudaEvent_t ev[4];                // phase timing events (created with the instance)
+    // node capacity (pic_instance_desc.cap) and the capacity kernel's tables
+    int has_cap;
+    int32_t *cap;                     // [N] c_1
+    int32_t *cap_run_t;               // [T] run of order t
+    int32_t *cap_info;                // [T] slot in its chunk | first << 8 | last of run << 9 |
+                                      //     last of product << 10
+    int32_t *cap_inv;                 // [T] sorted position of order t
+    unsigned long long *cap_qagg;     // [M][NP] tagged per-chunk totals of q
+    unsigned long long *cap_qinc;     // [M][NP] tagged inclusive prefixes of q over chunks
+    int64_t cap_qrows;                // chunks the q words are sized for
+    int cap_tables_m;                 // chunk count the capacity tables describe (0 = none)
     Batch* batch;                     // non-null for a batch instance
     PgState* pg;                      // policy-gradient buffers (allocated at first use)
 };
@@ -181,6 +194,12 @@ cudaError_t picard_run(Instance* I, const pic_policy* pol, int max_iters, int fl
 cudaError_t mlp_alloc(Instance* I);
 cudaError_t mlp_prepare(Instance* I, const pic_policy* pol, cudaStream_t st);
 cudaError_t sequential_mlp(Instance* I, const pic_policy* pol, cudaStream_t st);
+// Node capacity (pic_cap.cu): Algorithm 1 on M contiguous chunks of at most
+// kCapChunk orders with the state (x, c), and the sequential simulator.
+cudaError_t picard_cap(Instance* I, const pic_policy* pol, int M, int max_iters, int flags,
+                       const int8_t* alpha_init, unsigned long long timeout_ns, bool trace,
+                       cudaStream_t st);
+cudaError_t sequential_cap(Instance* I, int kind, cudaStream_t st);
 // Total cost and a^phi count of an action array (any order) with its regions.
 cudaError_t reduce_costs(Instance* I, const int8_t* alpha, const int32_t* reg, cudaStream_t st);
 cudaError_t sequential_int(Instance* I, int kind, cudaStream_t st);

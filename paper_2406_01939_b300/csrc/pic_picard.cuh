@@ -202,6 +202,45 @@ __device__ __forceinline__ void superblock_prefix(const KArgs& a, int s, const S
 }
 
 
+// Phase S of one pass, for every warp of the grid: the super-block heads of
+// chains whose product changed in the previous pass (every chain in pass 1 of
+// a cache started from alpha_init) are assigned to warps gwarp + j * nwarps, 32
+// at a time, and run superblock_prefix.  s_meta / s_fcp: this warp's staging
+// rows (32 entries each).
+template <int NPL>
+__device__ __forceinline__ void chain_prefixes(const KArgs& a, int it, const int* fc_prev,
+                                               unsigned tag, unsigned long long deadline,
+                                               SegMeta* s_meta, int* s_fcp) {
+    const int lane = lane_id();
+    const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int nseg = a.ctrl->nseg;
+    for (int j0 = 0; gwarp + j0 * nwarps < nseg; j0 += 32) {
+        const int sl = gwarp + (j0 + lane) * nwarps;
+        bool head = false;
+        if (sl < nseg) {
+            const SegMeta m = load_meta(a.meta + sl);
+            head = m.ce - m.cf > 1 && (sl - m.cf) % kSuperBlock == 0;
+            const int f = it > 1 ? fc_prev[m.k] : -1;
+            if (head && it > 1) head = f != INT_MAX;
+            if (head) {
+                s_meta[lane] = m;
+                s_fcp[lane] = f;
+            }
+        }
+        unsigned todo = __ballot_sync(kFull, head);
+        while (todo) {  // increasing segment order (lane order)
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const SegMeta mm = smem_meta(&s_meta[src]);
+            superblock_prefix<NPL>(a, gwarp + (j0 + src) * nwarps, mm, it, tag, s_fcp[src],
+                                   deadline);
+        }
+        __syncwarp();
+    }
+}
+
+
 // Algorithm 1's passes inside one persistent cooperative launch; every thread
 // of the grid calls this.  Each pass:
 //   phase S  chain prefixes of the per-segment histograms of cached actions
@@ -247,31 +286,9 @@ __device__ __forceinline__ void picard_passes(const KArgs& a, unsigned long long
         // ---- phase S: this warp's segments gwarp + j * nwarps, 32 at a time
         for (int k = gtid; k < a.K; k += gthreads) fc_cur[k] = INT_MAX;
         if (gtid == 0) a.ctrl->changed[parity] = 0;
-        if (it > 1 || a.first_dirty) {
-            for (int j0 = 0; gwarp + j0 * nwarps < nseg; j0 += 32) {
-                const int sl = gwarp + (j0 + lane) * nwarps;
-                bool head = false;
-                if (sl < nseg) {
-                    const SegMeta m = load_meta(a.meta + sl);
-                    head = m.ce - m.cf > 1 && (sl - m.cf) % kSuperBlock == 0;
-                    const int f = it > 1 ? fc_prev[m.k] : -1;
-                    if (head && it > 1) head = f != INT_MAX;
-                    if (head) {
-                        s_meta[wib][lane] = m;
-                        s_fcp[wib][lane] = f;
-                    }
-                }
-                unsigned todo = __ballot_sync(kFull, head);
-                while (todo) {  // increasing segment order (lane order)
-                    const int src = __ffs(todo) - 1;
-                    todo &= todo - 1;
-                    const SegMeta mm = smem_meta(&s_meta[wib][src]);
-                    superblock_prefix<NPL>(a, gwarp + (j0 + src) * nwarps, mm, it,
-                                           tag_base + (unsigned)it, s_fcp[wib][src], deadline);
-                }
-                __syncwarp();
-            }
-        }
+        if (it > 1 || a.first_dirty)
+            chain_prefixes<NPL>(a, it, fc_prev, tag_base + (unsigned)it, deadline, s_meta[wib],
+                                s_fcp[wib]);
         if (!grid_sync(a.ctrl, deadline)) { ok = false; break; }
         if (tr && gtid == 0) tr[0] = (long long)(globaltimer_ns() - t_start);
         // ---- phase R

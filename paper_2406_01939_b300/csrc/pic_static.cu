@@ -87,6 +87,9 @@ extern "C" pic_status pic_simulate_sequential_static(const pic_instance_desc* d,
     if (kind != PIC_POLICY_GREEDY && kind != PIC_POLICY_DUAL)
         return record_error(PIC_ERR_UNSUPPORTED,
                             "pic_simulate_sequential_static: greedy and bid-price policies only");
+    if (d->cap)
+        return record_error(PIC_ERR_UNSUPPORTED,
+                            "pic_simulate_sequential_static: node capacity needs an instance");
     if (kind == PIC_POLICY_DUAL && !d->lam)
         return record_error(PIC_ERR_INVALID_ARG, "pic_simulate_sequential_static: bid-price needs lam");
     if ((size_t)d->K * (size_t)d->N > kMaxStockEntries) {

@@ -50,12 +50,14 @@ class DeviceInstance:
         d = {k: _dev(getattr(inst, k).astype(np.int32), self.device)
              for k in ("prod", "reg", "x0", "cost")}
         d["lam"] = None if inst.lam is None else _dev(inst.lam.astype(np.int32), self.device)
+        cap = getattr(inst, "cap", None)
+        d["cap"] = None if cap is None else _dev(cap.astype(np.int32), self.device)
         return d
 
     def _desc(self, arrs, stream, mem=PIC_MEM_DEVICE):
         i = self.inst
         return make_desc(i.T, i.N, i.K, i.R, arrs["prod"], arrs["reg"], arrs["x0"], arrs["cost"],
-                         arrs["lam"], mem=mem, stream=stream)
+                         arrs["lam"], mem=mem, stream=stream, cap=arrs.get("cap"))
 
     def load(self, inst):
         """Stream new inputs of the same shape into this instance."""
@@ -124,9 +126,13 @@ class DeviceBatch:
                 a = {k: np.ascontiguousarray(getattr(i, k), dtype=np.int32)
                      for k in ("prod", "reg", "x0", "cost")}
                 a["lam"] = None if i.lam is None else np.ascontiguousarray(i.lam, dtype=np.int32)
+            cap = getattr(i, "cap", None)  # not supported in a batch: the library rejects it
+            if cap is not None:
+                a["cap"] = (_dev(cap.astype(np.int32), device) if mem == PIC_MEM_DEVICE
+                            else np.ascontiguousarray(cap, dtype=np.int32))
             keep.append(a)
             descs.append(make_desc(i.T, i.N, i.K, i.R, a["prod"], a["reg"], a["x0"], a["cost"],
-                                   a["lam"], mem=mem, stream=stream))
+                                   a["lam"], mem=mem, stream=stream, cap=a.get("cap")))
         self.handle = pic_create_batch(descs)
         del keep  # the batch holds its own device copies
 

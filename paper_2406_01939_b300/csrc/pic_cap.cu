@@ -43,6 +43,12 @@ namespace {
 using namespace picard;
 
 constexpr int kCapWarps = 4;  // warps per CTA
+constexpr int kAheadCap = 8;  // orders whose cost and price rows are loaded together
+
+// Phase S loads a whole super-block of histogram rows per round trip when the
+// registers allow (one run per segment makes phase S the larger part of a pass).
+template <int NPL>
+constexpr int kPrefixRows = NPL <= 2 ? kSuperBlock : 8;
 
 // order-info bits (cap_info)
 constexpr int kInfoSlot = 0xff;
@@ -176,12 +182,24 @@ __device__ bool cap_chunk(const KArgs& a, const CapArgs& c, int m, int it, bool 
     __syncwarp();
     const int nslots = __popc(__ballot_sync(kFull, o_info[0] & kInfoFirst)) +
                        __popc(__ballot_sync(kFull, o_info[1] & kInfoFirst));
-    // ---- start rows of the chunk's runs and the chunk's q
+    // ---- start rows of the chunk's runs and the chunk's q.  The runs'
+    // histograms of cached actions are rebuilt in the rows from the chunk's own
+    // orders (no histogram loads), then each row is overwritten by its start state.
     const bool have_cache = it > 1 || a.first_dirty;
     int qsum[NPL];
 #pragma unroll
     for (int i = 0; i < NPL; ++i) qsum[i] = 0;
-#pragma unroll 4
+    if (have_cache) {
+        for (int s = 0; s < nslots; ++s)
+#pragma unroll
+            for (int i = 0; i < NPL; ++i) rows[s * NP + lane + 32 * i] = 0;
+        __syncwarp();
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            if (o_old[h] >= 0) atomicAdd(&rows[(o_info[h] & kInfoSlot) * NP + o_old[h]], 1);
+        __syncwarp();
+    }
+#pragma unroll 8
     for (int s = 0; s < nslots; ++s) {
         const int r = s_run[s], k = s_k[s];
         // segments hold one run each: the run's chain is its product's segment range
@@ -192,8 +210,8 @@ __device__ bool cap_chunk(const KArgs& a, const CapArgs& c, int m, int it, bool 
             const int x0v = n < N ? __ldg(a.x0 + (size_t)k * N + n) : 0;
             const int d = chained ? a.carry[(size_t)r * NP + n] : 0;
             const int xs = max(0, x0v - d);
+            if (have_cache) qsum[i] += min(rows[s * NP + n], xs);
             rows[s * NP + n] = xs;
-            if (have_cache) qsum[i] += min(a.agg[(size_t)r * NP + n], xs);
         }
     }
     // ---- prefix of q: publish the total, look back, publish the inclusive prefix
@@ -217,44 +235,73 @@ __device__ bool cap_chunk(const KArgs& a, const CapArgs& c, int m, int it, bool 
         const int n = lane + 32 * i;
         cv[i] = n < N ? max(0, __ldg(c.cap + n) - pre[i]) : 0;
     }
-    int my_new[2] = {o_old[0], o_old[1]};
-    // cost and price rows of the current order, loaded one order ahead
-    int cc[NPL], lv[NPL];
-    {
-        const int k0 = __shfl_sync(kFull, o_prod[0], 0), r0 = __shfl_sync(kFull, o_reg[0], 0);
+    // Start decision of every order: arg min of its key over the nodes feasible
+    // at the chunk start.  Feasible sets only shrink along the chunk, so while
+    // that node stays feasible it is also the arg min over the current set; the
+    // walk below decides afresh only when it ran out inside the chunk.  Lane q
+    // (q + 32) ends holding the start decision of order q (q + 32).
+    int a0[2] = {-1, -1};
+    for (int qb = 0; qb < cnt; qb += kAheadCap) {
+        int ck[kAheadCap][NPL], sl[kAheadCap];
 #pragma unroll
-        for (int i = 0; i < NPL; ++i) {
-            const int n = lane + 32 * i;
-            cc[i] = n < N ? __ldg(a.cost + (size_t)r0 * N + n) : 0;
-            lv[i] = (DUAL && n < N) ? __ldg(a.lam + (size_t)k0 * N + n) : 0;
-        }
-    }
-    for (int q = 0; q < cnt; ++q) {
-        const bool hi_half = q >= 32;
-        const int src = q & 31;
-        const int inf = __shfl_sync(kFull, hi_half ? o_info[1] : o_info[0], src);
-        const int s = inf & kInfoSlot;
-        int ncc[NPL], nlv[NPL];
-        {
-            const int q1 = q + 1 < cnt ? q + 1 : q;
-            const bool h1 = q1 >= 32;
-            const int k1 = __shfl_sync(kFull, h1 ? o_prod[1] : o_prod[0], q1 & 31);
-            const int r1 = __shfl_sync(kFull, h1 ? o_reg[1] : o_reg[0], q1 & 31);
+        for (int u = 0; u < kAheadCap; ++u) {
+            const int q = min(qb + u, cnt - 1);
+            const bool hh = q >= 32;
+            const int k = __shfl_sync(kFull, hh ? o_prod[1] : o_prod[0], q & 31);
+            const int r = __shfl_sync(kFull, hh ? o_reg[1] : o_reg[0], q & 31);
+            sl[u] = __shfl_sync(kFull, hh ? o_info[1] : o_info[0], q & 31) & kInfoSlot;
 #pragma unroll
             for (int i = 0; i < NPL; ++i) {
                 const int n = lane + 32 * i;
-                ncc[i] = n < N ? __ldg(a.cost + (size_t)r1 * N + n) : 0;
-                nlv[i] = (DUAL && n < N) ? __ldg(a.lam + (size_t)k1 * N + n) : 0;
+                const int cst = n < N ? __ldg(a.cost + (size_t)r * N + n) : 0;
+                const int l = (DUAL && n < N) ? __ldg(a.lam + (size_t)k * N + n) : 0;
+                ck[u][i] = (cst - l) * 128 + n;
             }
         }
-        int key = INT_MAX;
 #pragma unroll
-        for (int i = 0; i < NPL; ++i) {
-            const int n = lane + 32 * i;
-            if (n < N && rows[s * NP + n] > 0 && cv[i] > 0) key = min(key, (cc[i] - lv[i]) * 128 + n);
+        for (int u = 0; u < kAheadCap; ++u) {
+            const int q = qb + u;
+            int key = INT_MAX;
+#pragma unroll
+            for (int i = 0; i < NPL; ++i) {
+                const int n = lane + 32 * i;
+                if (n < N && rows[sl[u] * NP + n] > 0 && cv[i] > 0) key = min(key, ck[u][i]);
+            }
+            key = __reduce_min_sync(kFull, key);
+            const int act = key == INT_MAX ? -1 : (key & 127);
+            if (q < cnt && lane == (q & 31)) {
+                if (q >= 32) a0[1] = act;
+                else a0[0] = act;
+            }
         }
-        key = __reduce_min_sync(kFull, key);
-        const int act = key == INT_MAX ? -1 : (key & 127);
+    }
+    int my_new[2] = {o_old[0], o_old[1]};
+    for (int q = 0; q < cnt; ++q) {
+        const bool hh = q >= 32;
+        const int src = q & 31;
+        const int s = __shfl_sync(kFull, hh ? o_info[1] : o_info[0], src) & kInfoSlot;
+        int act = __shfl_sync(kFull, hh ? a0[1] : a0[0], src);
+        if (act >= 0) {
+            bool still = false;  // only the lane owning node act can set it
+#pragma unroll
+            for (int i = 0; i < NPL; ++i)
+                if (act == lane + 32 * i) still = rows[s * NP + act] > 0 && cv[i] > 0;
+            if (!__any_sync(kFull, still)) {  // ran out inside the chunk: decide afresh
+                const int k = __shfl_sync(kFull, hh ? o_prod[1] : o_prod[0], src);
+                const int r = __shfl_sync(kFull, hh ? o_reg[1] : o_reg[0], src);
+                int key = INT_MAX;
+#pragma unroll
+                for (int i = 0; i < NPL; ++i) {
+                    const int n = lane + 32 * i;
+                    if (n < N && rows[s * NP + n] > 0 && cv[i] > 0) {
+                        const int l = DUAL ? __ldg(a.lam + (size_t)k * N + n) : 0;
+                        key = min(key, (__ldg(a.cost + (size_t)r * N + n) - l) * 128 + n);
+                    }
+                }
+                key = __reduce_min_sync(kFull, key);
+                act = key == INT_MAX ? -1 : (key & 127);
+            }
+        }
 #pragma unroll
         for (int i = 0; i < NPL; ++i)
             if (act == lane + 32 * i) {
@@ -262,13 +309,8 @@ __device__ bool cap_chunk(const KArgs& a, const CapArgs& c, int m, int it, bool 
                 cv[i] -= 1;
             }
         if (lane == src) {
-            if (hi_half) my_new[1] = act;
+            if (hh) my_new[1] = act;
             else my_new[0] = act;
-        }
-#pragma unroll
-        for (int i = 0; i < NPL; ++i) {
-            cc[i] = ncc[i];
-            lv[i] = nlv[i];
         }
     }
     if (lane == 0) calls += (unsigned long long)cnt;
@@ -366,7 +408,8 @@ __global__ void __launch_bounds__(kCapWarps * 32) k_picard_cap(KArgs a, CapArgs 
             a.ctrl->cap_fct[parity] = INT_MAX;
         }
         if (it > 1 || a.first_dirty)
-            chain_prefixes<NPL>(a, it, fc_prev, tag, deadline, s_meta[wib], s_fcp[wib]);
+            chain_prefixes<NPL, kPrefixRows<NPL>>(a, it, fc_prev, tag, deadline, s_meta[wib],
+                                                  s_fcp[wib]);
         if (!grid_sync(a.ctrl, deadline)) { ok = false; break; }
         if (tr && gtid == 0) tr[0] = (long long)(globaltimer_ns() - t_start);
         // ---- phase C

@@ -103,14 +103,16 @@ __device__ __forceinline__ unsigned long long tagged(unsigned tag, int v) {
 // precede the product's first change (clean) keeps last pass's prefixes and only
 // re-publishes them.  Waits are bounded by the deadline; on expiry the error is
 // recorded and the pass is abandoned at the next grid barrier.
-template <int NPL>
+// ROWS: histogram rows loaded per round trip (a whole super-block when
+// registers allow).
+template <int NPL, int ROWS = 8 / NPL>
 __device__ __forceinline__ void superblock_prefix(const KArgs& a, int s, const SegMeta& m, int it,
                                                   unsigned tag, int fcp,
                                                   unsigned long long deadline) {
     const int lane = lane_id();
     const int NP = a.NP;
     const int send = min(s + kSuperBlock, m.ce);
-    constexpr int kRows = 8 / NPL;  // rows per round trip
+    constexpr int kRows = ROWS;
     // the shortcut needs last pass's prefixes: pass 1 computes none unless the
     // cache started from alpha_init
     if (send < m.ce && (it > 2 || (it == 2 && a.first_dirty))) {
@@ -207,7 +209,7 @@ __device__ __forceinline__ void superblock_prefix(const KArgs& a, int s, const S
 // a cache started from alpha_init) are assigned to warps gwarp + j * nwarps, 32
 // at a time, and run superblock_prefix.  s_meta / s_fcp: this warp's staging
 // rows (32 entries each).
-template <int NPL>
+template <int NPL, int ROWS = 8 / NPL>
 __device__ __forceinline__ void chain_prefixes(const KArgs& a, int it, const int* fc_prev,
                                                unsigned tag, unsigned long long deadline,
                                                SegMeta* s_meta, int* s_fcp) {
@@ -233,8 +235,8 @@ __device__ __forceinline__ void chain_prefixes(const KArgs& a, int it, const int
             const int src = __ffs(todo) - 1;
             todo &= todo - 1;
             const SegMeta mm = smem_meta(&s_meta[src]);
-            superblock_prefix<NPL>(a, gwarp + (j0 + src) * nwarps, mm, it, tag, s_fcp[src],
-                                   deadline);
+            superblock_prefix<NPL, ROWS>(a, gwarp + (j0 + src) * nwarps, mm, it, tag, s_fcp[src],
+                                         deadline);
         }
         __syncwarp();
     }

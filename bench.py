@@ -82,14 +82,16 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--T", type=int, default=0, help="orders (0 = the workload's own size)")
     p.add_argument("--workload", default="dual_large",
-                   choices=["dual_large", "mlp_medium", "batch_uneven", "pg_large"])
+                   choices=["dual_large", "mlp_medium", "batch_uneven", "pg_large",
+                            "capacity_large"])
     p.add_argument("--flags", type=int, default=0, help="extra pic_sim_opts flags (tuning)")
     p.add_argument("--B", type=int, default=0,
                    help="trajectories of batch_uneven / pg_large (0 = the workload's 512 / 64)")
     return p.parse_args()
 
 
-DEFAULT_CHUNKS = {"dual_large": 4096, "mlp_medium": 1024, "batch_uneven": 0, "pg_large": 0}
+DEFAULT_CHUNKS = {"dual_large": 4096, "mlp_medium": 1024, "batch_uneven": 0, "pg_large": 0,
+                  "capacity_large": 16384}
 
 # FP32 CUDA-core peak of the MLP scorer's arithmetic: 148 SMs x 128 FP32 lanes x
 # 2 FLOP per FMA x 2.032 GHz (maximum SM clock)
@@ -109,6 +111,9 @@ def make_workload(args, seed):
     if args.workload == "mlp_medium":
         inst, mlp = synth.mlp_medium(seed, **({"T": args.T} if args.T else {}))
         return inst, Policy("mlp", mlp=mlp), "mlp"
+    if args.workload == "capacity_large":
+        inst = synth.capacity_large(seed, **({"T": args.T} if args.T else {}))
+        return inst, Policy("dual"), "dual"
     inst = synth.dual_large(seed, **({"T": args.T} if args.T else {}))
     return inst, Policy("dual"), "dual"
 
@@ -135,11 +140,13 @@ def batch_config(args, insts, res):
 def workload_config(args, inst):
     pol = "MLP Linear(2N+16,256)-ReLU-Linear(256,N), BF16 N(0,0.02)" \
         if args.workload == "mlp_medium" else "bid-price, lambda~U{0..30}"
+    cap = (", node capacity for 80% of the orders (log-normal(0, 0.5) node weights), chunks "
+           "of 64 orders replayed in time order" if getattr(inst, "cap", None) is not None else "")
     return {
         "workload": args.workload,
         "desc": (f"FO, T={inst.T} orders, N={inst.N} warehouses, K={inst.K} products "
                  f"(Zipf 1.1), R={inst.R} regions, x0~Poisson(1.05 T p_k/N), cost~U{{1..100}}, "
-                 f"{pol}"),
+                 f"{pol}{cap}"),
         "T": inst.T, "N": inst.N, "K": inst.K, "R": inst.R,
         "chunks": chunks_of(args), "policy": args.workload == "mlp_medium" and "mlp" or "dual",
         "l2": "flushed between timed steps (256 MiB write)",
@@ -165,20 +172,27 @@ def load_peaks():
     return 6400.0, "fallback"
 
 
-def kernel_source_hash():
+_KERNEL_FILES = {
+    "int": ("pic_int.cu", "pic_replay.cuh", "pic_picard.cuh", "pic_device.cuh", "pic_internal.h"),
+    "capacity": ("pic_cap.cu", "pic_picard.cuh", "pic_device.cuh", "pic_internal.h"),
+}
+_PROFILES = {"int": "picard_int_dual_large.md", "capacity": "picard_cap_capacity_large.md"}
+
+
+def kernel_source_hash(kind="int"):
     h = hashlib.sha256()
-    for f in ("pic_int.cu", "pic_replay.cuh", "pic_picard.cuh", "pic_device.cuh", "pic_internal.h"):
+    for f in _KERNEL_FILES[kind]:
         h.update(open(os.path.join(ROOT, "paper_2406_01939_b300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
+def profiled_traffic(kind="int"):
     """DRAM bytes per launch of the Picard kernel from the committed ncu summary,
     if it was taken on the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "picard_int_dual_large.md")
+    p = os.path.join(ROOT, "profiles", _PROFILES[kind])
     if not os.path.exists(p):
         return None
-    src = kernel_source_hash()
+    src = kernel_source_hash(kind)
     hash_ok, traffic = False, None
     for line in open(p):
         if line.startswith("kernel_source_hash:") and line.split(":", 1)[1].strip() == src:
@@ -235,8 +249,10 @@ def prefix_instance(inst, T):
     """The first T orders of a trajectory (sequential simulation is causal, so its
     actions are the first T actions of the full trajectory)."""
     from paper_2406_01939_b300.synth import Instance
-    return Instance(T, inst.N, inst.K, inst.R, inst.prod[:T].copy(), inst.reg[:T].copy(), inst.x0,
-                    inst.cost, inst.lam)
+    sub = Instance(T, inst.N, inst.K, inst.R, inst.prod[:T].copy(), inst.reg[:T].copy(), inst.x0,
+                   inst.cost, inst.lam)
+    sub.cap = getattr(inst, "cap", None)
+    return sub
 
 
 def cpu_oracle_rate(inst, pol, seconds):
@@ -688,6 +704,7 @@ def main():
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).pin_memory()
     host = {k: pin(getattr(inst, k)) for k in ("prod", "reg", "x0", "cost")}
     host["lam"] = pin(inst.lam) if inst.lam is not None else None
+    host["cap"] = pin(inst.cap) if getattr(inst, "cap", None) is not None else None
     host_np = {k: (v.numpy() if v is not None else None) for k, v in host.items()}
     host_act = torch.empty(T, dtype=torch.int8).pin_memory().numpy()
     opts = pic.make_opts("picard", chunks_of(args), out_mem=pic.PIC_MEM_HOST, seg_window=args.seg_window,
@@ -711,6 +728,17 @@ def main():
     N = inst.N
     if args.workload == "mlp_medium":
         roofline = mlp_roofline(last["mlp_calls"], N, sim_ms, "k_picard_mlp (persistent, all passes)")
+    elif args.workload == "capacity_large":
+        # per replayed order: product, region (4 B each), cached action read and
+        # written (1 B each); per replayed run: its start row read and its
+        # histogram row written (N x 4 B each)
+        alg_bytes = last["policy_calls"] * 10 + last["seg_replays"] * 8 * N
+        achieved = alg_bytes / (sim_ms / 1000.0) / 1e9
+        peak, peak_kind = load_peaks()
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": profiled_traffic("capacity"),
+                    "kernel": "k_picard_cap (persistent, all passes)", "peak_kind": peak_kind,
+                    "algorithmic_bytes": alg_bytes}
     else:
         alg_bytes = last["policy_calls"] * 6 + last["seg_replays"] * 16 * N
         achieved = alg_bytes / (sim_ms / 1000.0) / 1e9

@@ -152,13 +152,15 @@ __device__ __forceinline__ bool lookback_q(const CapArgs& c, const KArgs& a, int
     return true;
 }
 
-// Chunk m of pass `it`: q, its prefix, and (replay) the orders in time order.
+// Chunk m of pass `it`: q, its prefix, and (replay) the orders in time order;
+// a replay adds its orders to calls and its runs to units.
 // rows: this warp's [kCapChunk][NP] shared rows; s_run / s_k: run and product of
 // each slot.  Returns whether a cached action changed.
 template <int NPL, bool DUAL>
 __device__ bool cap_chunk(const KArgs& a, const CapArgs& c, int m, int it, bool replay,
                           unsigned tag, unsigned long long deadline, int* rows, int* s_run,
-                          int* s_k, int* fc_cur, int parity, unsigned long long& calls) {
+                          int* s_k, int* fc_cur, int parity, unsigned long long& calls,
+                          unsigned long long& units) {
     const int lane = lane_id();
     const int N = a.N, NP = a.NP;
     const int lo = m * c.L;
@@ -313,7 +315,10 @@ __device__ bool cap_chunk(const KArgs& a, const CapArgs& c, int m, int it, bool 
             else my_new[0] = act;
         }
     }
-    if (lane == 0) calls += (unsigned long long)cnt;
+    if (lane == 0) {
+        calls += (unsigned long long)cnt;
+        units += (unsigned long long)nslots;  // runs (segments of one run) replayed
+    }
     // ---- cache, first changes (per product in sorted positions, and in time)
     bool chg = false;
 #pragma unroll
@@ -427,8 +432,7 @@ __global__ void __launch_bounds__(kCapWarps * 32) k_picard_cap(KArgs a, CapArgs 
             }
             const bool rep = lo > f_prev;
             chg |= cap_chunk<NPL, DUAL>(a, c, m, it, rep, tag, deadline, rows, s_run[wib], s_k[wib],
-                                        fc_cur, parity, calls);
-            replays += rep ? 1 : 0;
+                                        fc_cur, parity, calls, replays);
         }
         if (tr && lane == 0 && replays != replays0) {
             atomicAdd((unsigned long long*)&tr[2], calls - calls0);

@@ -132,6 +132,29 @@ __device__ __forceinline__ uint4 wld4(const uint4* p) {
 __device__ __forceinline__ float lo16(unsigned w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float hi16(unsigned w) { return __uint_as_float(w & 0xFFFF0000u); }
 
+// One stock input of layer 1 for the lane's 8 hidden units: acc[u] =
+// fma(W1s[n][unit u], f, acc[u]), u in the W1p packing order (low then high half
+// of w.x, w.y, w.z, w.w).  f is the feature's BF16 bit pattern: min(S, 32)/32 is
+// exact in BF16, as are the weights.  The mixed-precision fma.rn.f32.bf16 forms
+// the product of its two BF16 operands exactly and rounds the sum once to FP32,
+// which is fmaf on the widened operands bit for bit, without the 8 unpacking
+// instructions.
+__device__ __forceinline__ void fma8_bf16(float acc[8], uint4 w, unsigned short f) {
+    asm("{\n\t.reg .b16 l0, h0, l1, h1, l2, h2, l3, h3;\n\t"
+        "mov.b32 {l0, h0}, %8;\n\tmov.b32 {l1, h1}, %9;\n\t"
+        "mov.b32 {l2, h2}, %10;\n\tmov.b32 {l3, h3}, %11;\n\t"
+        "fma.rn.f32.bf16 %0, l0, %12, %0;\n\tfma.rn.f32.bf16 %1, h0, %12, %1;\n\t"
+        "fma.rn.f32.bf16 %2, l1, %12, %2;\n\tfma.rn.f32.bf16 %3, h1, %12, %3;\n\t"
+        "fma.rn.f32.bf16 %4, l2, %12, %4;\n\tfma.rn.f32.bf16 %5, h2, %12, %5;\n\t"
+        "fma.rn.f32.bf16 %6, l3, %12, %6;\n\tfma.rn.f32.bf16 %7, h3, %12, %7;\n\t}"
+        : "+f"(acc[0]), "+f"(acc[1]), "+f"(acc[2]), "+f"(acc[3]), "+f"(acc[4]), "+f"(acc[5]),
+          "+f"(acc[6]), "+f"(acc[7])
+        : "r"(w.x), "r"(w.y), "r"(w.z), "r"(w.w), "h"(f));
+}
+__device__ __forceinline__ unsigned short bf16_bits(float x) {
+    return (unsigned short)(__float_as_uint(x) >> 16);  // exact for BF16-representable x
+}
+
 // The warp evaluates the policy for stock row S (lane l holds warehouses l + 32 i)
 // of an order in region r at time t; fs/hs: per-warp shared scratch (N and H
 // floats, hs 16-byte aligned).  Returns the action (warp-uniform).
@@ -151,18 +174,8 @@ __device__ __forceinline__ int mlp_decide(const MlpPolicy& p, const uint4* W1p, 
 #pragma unroll
     for (int u = 0; u < kJ; ++u) acc[u] = __ldg(p.P + (size_t)r * H + lane + 32 * u);
 #pragma unroll 2
-    for (int n = 0; n < N; ++n) {
-        const float f = fs[n];
-        const uint4 w = wld4<SMEMW>(W1p + n * 32 + lane);
-        acc[0] = fmaf(lo16(w.x), f, acc[0]);
-        acc[1] = fmaf(hi16(w.x), f, acc[1]);
-        acc[2] = fmaf(lo16(w.y), f, acc[2]);
-        acc[3] = fmaf(hi16(w.y), f, acc[3]);
-        acc[4] = fmaf(lo16(w.z), f, acc[4]);
-        acc[5] = fmaf(hi16(w.z), f, acc[5]);
-        acc[6] = fmaf(lo16(w.w), f, acc[6]);
-        acc[7] = fmaf(hi16(w.w), f, acc[7]);
-    }
+    for (int n = 0; n < N; ++n)
+        fma8_bf16(acc, wld4<SMEMW>(W1p + n * 32 + lane), bf16_bits(fs[n]));
 #pragma unroll
     for (int u = 0; u < kJ; ++u) hs[lane + 32 * u] = acc[u] > 0.0f ? acc[u] : 0.0f;
     __syncwarp();
@@ -287,18 +300,8 @@ __device__ __noinline__ int spec_tile(const MlpPolicy& p, const uint4* W1p, cons
     __syncwarp();
     {
         float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        for (int n = 0; n < N; ++n) {
-            const float f = fs[n];
-            const uint4 w = wld4<SMEMW>(W1p + n * 32 + lane);
-            acc[0] = fmaf(lo16(w.x), f, acc[0]);
-            acc[1] = fmaf(hi16(w.x), f, acc[1]);
-            acc[2] = fmaf(lo16(w.y), f, acc[2]);
-            acc[3] = fmaf(hi16(w.y), f, acc[3]);
-            acc[4] = fmaf(lo16(w.z), f, acc[4]);
-            acc[5] = fmaf(hi16(w.z), f, acc[5]);
-            acc[6] = fmaf(lo16(w.w), f, acc[6]);
-            acc[7] = fmaf(hi16(w.w), f, acc[7]);
-        }
+        for (int n = 0; n < N; ++n)
+            fma8_bf16(acc, wld4<SMEMW>(W1p + n * 32 + lane), bf16_bits(fs[n]));
 #pragma unroll
         for (int u = 0; u < 8; ++u) hs[lane + 32 * u] = acc[u];
     }

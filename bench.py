@@ -358,6 +358,13 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def fp32_scored(res):
+    """MLP decisions that ran the FP32 scorer: not taken from tensor-core tile
+    scores and not from the saturated-state table (those cost no scorer FLOPs
+    on the CUDA cores)."""
+    return res["mlp_calls"] - res["tc_decisions"] - res["sat_decisions"]
+
+
 def mlp_roofline(mlp_calls, N, ms, kernel):
     flops = mlp_calls * mlp_flops_per_call(N)
     achieved = flops / (ms / 1000.0) / 1e12
@@ -470,8 +477,9 @@ def run_batch(args, dev, world, rank):
         "autotune_s": t_tune,
         "phases_ms": {"per_call_work": sim_ms, "step_device": t_ms / args.steps},
         "policy_calls": last["policy_calls"], "mlp_calls": last["mlp_calls"],
+        "tc_decisions": last["tc_decisions"], "sat_decisions": last["sat_decisions"],
         "segment_replays": last["seg_replays"],
-        "roofline": mlp_roofline(last["mlp_calls"], insts[0].N, sim_ms,
+        "roofline": mlp_roofline(fp32_scored(last), insts[0].N, sim_ms,
                                  "k_picard_batch (persistent, all passes; MLP scorer FP32 FMA)"),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "bit_exact": bit_exact_e2e,
@@ -586,7 +594,7 @@ def run_pg(args, dev, world, rank):
         "phases_ms": {"step": t_ms / args.steps, "simulation": res.sim_ms,
                       "gradient_call_on_given_paths": bwd_ms},
         "policy_calls": res.policy_calls, "tc_decisions": res.tc_decisions,
-        "rescored": res.rescored,
+        "sat_decisions": res.sat_decisions, "rescored": res.rescored,
         "roofline": ({"bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
                       "frac": achieved / bf16_peak, "traffic": None,
                       "kernel": "k_pg_tc (tcgen05, BF16 split products, FP32 accumulation in TMEM)",
@@ -727,7 +735,7 @@ def main():
     # roofline of the dominant kernel (the persistent Picard kernel)
     N = inst.N
     if args.workload == "mlp_medium":
-        roofline = mlp_roofline(last["mlp_calls"], N, sim_ms, "k_picard_mlp (persistent, all passes)")
+        roofline = mlp_roofline(fp32_scored(last), N, sim_ms, "k_picard_mlp (persistent, all passes)")
     elif args.workload == "capacity_large":
         # per replayed order: product, region (4 B each), cached action read and
         # written (1 B each); per replayed run: its start row read and its
@@ -761,6 +769,8 @@ def main():
         "phases_ms": {"tables": prep_ms, "picard_kernel": sim_ms,
                       "step_device": t_ms / args.steps},
         "policy_calls": last["policy_calls"], "segment_replays": last["seg_replays"],
+        "mlp_calls": last["mlp_calls"], "tc_decisions": last["tc_decisions"],
+        "sat_decisions": last["sat_decisions"],
         "pass_trace": pass_trace,
         "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),

@@ -77,7 +77,7 @@ enum {
                                   max_iters, timeout and flags stay the same */
     PIC_FLAG_NO_TC = 32,       /* MLP policies: score every decision with the FP32 scorer
                                   (no tensor-core tiles; see PIC_FLAG_TC) */
-    PIC_FLAG_TC = 64           /* MLP policies (N <= 64), the default unless PIC_FLAG_NO_TC:
+    PIC_FLAG_TC = 64,          /* MLP policies (N <= 64), the default unless PIC_FLAG_NO_TC:
                                   inside long runs of a product whose stocked warehouses all
                                   hold more than 32 units, score up to 16 orders at a time on
                                   the tensor cores (BF16 inputs, FP32 accumulation) and
@@ -85,6 +85,12 @@ enum {
                                   max(1e-3, twice a computed error bound); same results as the
                                   FP32 scorer.  With num_chunks = 0 the batch autotuner
                                   decides unless one of the two flags is given */
+    PIC_FLAG_NO_SAT = 128      /* MLP policies: evaluate the network for every decision.  By
+                                  default a decision whose product holds at least 32 units at
+                                  every warehouse (every stock feature min(x,32)/32 equals 1)
+                                  takes its FP32 scores from a per-region table computed at
+                                  the start of the call by the same scorer in the same
+                                  operation order, so the actions are the same */
 };
 
 typedef struct pic_instance pic_instance;
@@ -157,6 +163,9 @@ typedef struct {
     int64_t tc_decisions; /* MLP decisions taken from tensor-core tile scores (the rest of
                              mlp_calls ran the FP32 scorer; rescored counts tile rows sent
                              back to it because their top-2 margin was too small) */
+    int64_t sat_decisions; /* MLP decisions taken from the saturated-state score table (see
+                              PIC_FLAG_NO_SAT); mlp_calls - tc_decisions - sat_decisions ran
+                              the FP32 scorer */
 } pic_sim_result;
 
 /* Per-trajectory result of pic_simulate_batch. */

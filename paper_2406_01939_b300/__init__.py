@@ -26,7 +26,7 @@ PIC_POLICY_GREEDY, PIC_POLICY_DUAL, PIC_POLICY_MLP, PIC_POLICY_GUMBEL = 0, 1, 2,
 PIC_MODE_PICARD, PIC_MODE_SEQUENTIAL = 0, 1
 PIC_MEM_HOST, PIC_MEM_DEVICE = 0, 1
 PIC_FLAG_NO_RESET, PIC_FLAG_REUSE_TABLES, PIC_FLAG_TIMING, PIC_FLAG_GROUP_KERNEL = 1, 2, 4, 8
-PIC_FLAG_GRAPH, PIC_FLAG_NO_TC, PIC_FLAG_TC = 16, 32, 64
+PIC_FLAG_GRAPH, PIC_FLAG_NO_TC, PIC_FLAG_TC, PIC_FLAG_NO_SAT = 16, 32, 64, 128
 
 POLICY_KINDS = {"greedy": PIC_POLICY_GREEDY, "dual": PIC_POLICY_DUAL, "mlp": PIC_POLICY_MLP,
                 "gumbel": PIC_POLICY_GUMBEL}
@@ -65,7 +65,7 @@ class pic_sim_result(C.Structure):
                 ("seg_replays", C.c_int64), ("launches", C.c_int32), ("prep_ms", C.c_float),
                 ("sim_ms", C.c_float), ("total_ms", C.c_float), ("seg_window", C.c_int32),
                 ("cta_threads", C.c_int32), ("ctas_per_sm", C.c_int32), ("mlp_calls", C.c_int64),
-                ("tc_decisions", C.c_int64)]
+                ("tc_decisions", C.c_int64), ("sat_decisions", C.c_int64)]
 
 
 class pic_traj_result(C.Structure):

@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(32 * kSeqWarps) k_seq_batch(
     int B, int N, const int32_t* __restrict__ toff, const int32_t* __restrict__ prod,
     const int32_t* __restrict__ reg, const int32_t* __restrict__ cost,
     const int32_t* __restrict__ lam, int32_t* xw, int8_t* __restrict__ act_t,
-    const BatchPol* __restrict__ pol, MlpPolicy p, int has_mlp) {
+    const BatchPol* __restrict__ pol, MlpPolicy p, int has_mlp, Ctrl* ctrl) {
     extern __shared__ uint4 s_w[];
     __shared__ float s_fs[kSeqWarps][128];
     __shared__ __align__(16) float s_hs[kSeqWarps][kHidden];
@@ -146,8 +146,10 @@ __global__ void __launch_bounds__(32 * kSeqWarps) k_seq_batch(
         q.gumbel = bp.kind == PIC_POLICY_GUMBEL;
         q.seed = bp.seed;
         q.traj = bp.traj;
+        unsigned long long nsat = 0;
         seq_mlp_body<NPL, SMEMW>(T, N, prod + t0, reg + t0, xw, act_t + t0, q, W1p, W2p, s_fs[w],
-                                 s_hs[w]);
+                                 s_hs[w], nsat);
+        if (lane_id() == 0 && nsat) atomicAdd(&ctrl->sat_rows, nsat);
     }
 }
 
@@ -179,7 +181,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_picard_batch(KArgs a, MlpPoli
     const CostTable<false> ct{a.cost, nullptr, a.N};
     const int wib = threadIdx.x >> 5;
     unsigned long long calls = 0;
-    MlpCounts mc{0, 0, 0};
+    MlpCounts mc{0, 0, 0, 0};
     picard_passes<NPL, WARPS>(a, calls, [&](int seg, const SegMeta& m, int fcp, int* fc_cur, int it) {
         const int tb = __ldg(b.traj_of_prod + m.k);
         const BatchPol bp = b.pol[tb];
@@ -206,6 +208,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_picard_batch(KArgs a, MlpPoli
         atomicAdd(&a.ctrl->mlp_calls, mc.calls);
         atomicAdd(&a.ctrl->rescored, mc.rescored);
         atomicAdd(&a.ctrl->tc_rows, mc.tc);
+        atomicAdd(&a.ctrl->sat_rows, mc.sat);
     }
 }
 
@@ -277,7 +280,8 @@ cudaError_t launch_seq_batch(Instance* I, const MlpPolicy& p, bool has_mlp, cuda
     const int grid = (bt->B + kSeqWarps - 1) / kSeqWarps;
     I->launches += 1;
     kern<<<grid, 32 * kSeqWarps, smem, st>>>(bt->B, I->N, bt->toff, I->prod, I->reg, I->cost, I->lam,
-                                             I->xwork, I->act_t, bt->pol, p, has_mlp ? 1 : 0);
+                                             I->xwork, I->act_t, bt->pol, p, has_mlp ? 1 : 0,
+                                             I->ctrl);
     return cudaGetLastError();
 }
 
@@ -380,7 +384,7 @@ pic_status enqueue_picard(Instance& I, const CallCfg& c, cudaStream_t st) {
     a.trace = c.trace ? I.trace : nullptr;
     pic_policy mp = c.mlp;
     mp.kind = PIC_POLICY_MLP;
-    const MlpPolicy p = make_policy_view(&I, &mp);
+    const MlpPolicy p = make_policy_view(&I, &mp, c.flags);
     BatchArgs ba;
     ba.traj_of_prod = bt->traj_of_prod;
     ba.pol = bt->pol;
@@ -724,7 +728,7 @@ pic_status pic_simulate_batch(pic_instance* h, const pic_policy* pols, const pic
         mp.kind = PIC_POLICY_MLP;
         if (c.has_mlp) BCU(mlp_prepare(&I, &mp, st));
         BCU(cudaEventRecord(I.ev[1], st));
-        const MlpPolicy p = make_policy_view(&I, &mp);
+        const MlpPolicy p = make_policy_view(&I, &mp, opts->flags);
         const int npl = (I.N + 31) / 32;
         if (T) {
             if (npl == 1) BCU(launch_seq_batch<1>(&I, p, c.has_mlp, st));
@@ -807,6 +811,7 @@ pic_status pic_simulate_batch(pic_instance* h, const pic_policy* pols, const pic
         res->launches = I.launches;
         res->mlp_calls = picard ? (int64_t)hc.mlp_calls : 0;
         res->tc_decisions = picard ? (int64_t)hc.tc_rows : 0;
+        res->sat_decisions = (int64_t)hc.sat_rows;
         if (!picard)
             for (int b = 0; b < B; ++b)
                 if (bt->h_pol[b].kind >= PIC_POLICY_MLP) res->mlp_calls += bt->h_toff[b + 1] - bt->h_toff[b];

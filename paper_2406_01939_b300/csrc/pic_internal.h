@@ -37,6 +37,7 @@ struct Ctrl {
     unsigned long long seg_replays;
     unsigned long long mlp_calls;  // MLP / Gumbel policy evaluations (batch kernel)
     unsigned long long tc_rows;    // MLP decisions taken from tensor-core tile scores
+    unsigned long long sat_rows;   // MLP decisions taken from the saturated-state table
     int cap_fct[2];          // capacity kernel: first changed time of the pass, per parity
     int nruns;               // tables built by the preprocessing kernels
     int nseg;
@@ -141,6 +142,7 @@ struct Instance {
     float *mlp_b2;      // [N]
     float *mlp_Emax;    // [R] error-bound constant per region (tensor-core tiles)
     float *mlp_bnd;     // [2] max column sum of |W2|, max |b2|
+    float *mlp_sat;     // [R][N] FP32 scores of the saturated state (every stock feature 1)
     // scratch for the sort and scans
     int32_t *tmp_a, *tmp_b, *tmp_c;   // [T] each
     int32_t *scan_blk;                // block sums
@@ -193,7 +195,7 @@ cudaError_t picard_run(Instance* I, const pic_policy* pol, int max_iters, int fl
 // prefix (E rows through reg_local for a batch) and the FP32 weight copies.
 cudaError_t mlp_alloc(Instance* I);
 cudaError_t mlp_prepare(Instance* I, const pic_policy* pol, cudaStream_t st);
-cudaError_t sequential_mlp(Instance* I, const pic_policy* pol, cudaStream_t st);
+cudaError_t sequential_mlp(Instance* I, const pic_policy* pol, int flags, cudaStream_t st);
 // Node capacity (pic_cap.cu): Algorithm 1 on M contiguous chunks of at most
 // kCapChunk orders with the state (x, c), and the sequential simulator.
 cudaError_t picard_cap(Instance* I, const pic_policy* pol, int M, int max_iters, int flags,

@@ -99,6 +99,31 @@ __global__ void k_mlp_emax(int R, const float* __restrict__ P, const float* __re
     }
 }
 
+// Scores of the saturated state (every warehouse at 32 units or more, so every
+// stock feature is 1) for every region: one warp per region runs mlp_scores.
+constexpr int kSatWarps = 8;
+
+template <int NPL>
+__global__ void __launch_bounds__(32 * kSatWarps) k_mlp_sat(MlpPolicy p, int R, float* __restrict__ sat) {
+    __shared__ float fs[kSatWarps][128];
+    __shared__ __align__(16) float hs[kSatWarps][kHidden];
+    const int w = threadIdx.x >> 5, lane = lane_id();
+    const int r = blockIdx.x * kSatWarps + w;
+    if (r >= R) return;
+    int S[NPL];
+    bool want[NPL];
+#pragma unroll
+    for (int i = 0; i < NPL; ++i) {
+        S[i] = 32;
+        want[i] = lane + 32 * i < p.N;
+    }
+    float s[NPL];
+    mlp_scores<NPL, false>(p, p.W1p, p.W2p, S, r, want, fs[w], hs[w], s);
+#pragma unroll
+    for (int i = 0; i < NPL; ++i)
+        if (want[i]) sat[(size_t)r * p.N + lane + 32 * i] = s[i];
+}
+
 // ---------------------------------------------------------------- sequential simulator
 template <int NPL, bool SMEMW>
 __global__ void __launch_bounds__(32) k_seq_mlp(int T, int N, const int32_t* __restrict__ prod,
@@ -110,11 +135,13 @@ __global__ void __launch_bounds__(32) k_seq_mlp(int T, int N, const int32_t* __r
     if (SMEMW) stage_weights(p, s_w);
     const uint4* W1p = SMEMW ? s_w : p.W1p;
     const uint4* W2p = SMEMW ? s_w + p.N * kHidden / 8 : p.W2p;
-    seq_mlp_body<NPL, SMEMW>(T, N, prod, reg, xw, act_t, p, W1p, W2p, fs, hs);
+    unsigned long long nsat = 0;
+    seq_mlp_body<NPL, SMEMW>(T, N, prod, reg, xw, act_t, p, W1p, W2p, fs, hs, nsat);
     if (lane_id() == 0) {
         ctrl->iters = 1;
         ctrl->converged = 1;
         ctrl->policy_calls = (unsigned long long)T;
+        ctrl->sat_rows = nsat;
     }
 }
 
@@ -131,7 +158,7 @@ __global__ void __launch_bounds__(kMlpThreads, 2) k_picard_mlp(KArgs a, MlpPolic
     const uint4* W2p = SMEMW ? s_w + p.N * kHidden / 8 : p.W2p;
     const int wib = threadIdx.x >> 5;
     unsigned long long calls = 0;
-    MlpCounts mc{0, 0, 0};
+    MlpCounts mc{0, 0, 0, 0};
     picard_passes<NPL, kMlpThreads / 32>(
         a, calls, [&](int seg, const SegMeta& m, int fcp, int* fc_cur, int it) {
             const unsigned long long c0 = mc.calls;
@@ -140,9 +167,10 @@ __global__ void __launch_bounds__(kMlpThreads, 2) k_picard_mlp(KArgs a, MlpPolic
             calls += mc.calls - c0;
             return chg;
         });
-    if (lane_id() == 0 && (mc.rescored || mc.tc)) {
+    if (lane_id() == 0 && (mc.rescored || mc.tc || mc.sat)) {
         atomicAdd(&a.ctrl->rescored, mc.rescored);
         atomicAdd(&a.ctrl->tc_rows, mc.tc);
+        atomicAdd(&a.ctrl->sat_rows, mc.sat);
     }
 }
 
@@ -191,6 +219,7 @@ cudaError_t mlp_alloc(Instance* I) {
     if (!e) e = cudaMalloc((void**)&I->mlp_b2, sizeof(float) * (size_t)I->N);
     if (!e) e = cudaMalloc((void**)&I->mlp_Emax, sizeof(float) * ((size_t)I->R + kHidden));
     if (!e) e = cudaMalloc((void**)&I->mlp_bnd, sizeof(float) * 2);
+    if (!e) e = cudaMalloc((void**)&I->mlp_sat, sizeof(float) * (size_t)I->R * I->N);
     return e;
 }
 
@@ -207,11 +236,22 @@ cudaError_t mlp_prepare(Instance* I, const pic_policy* pol, cudaStream_t st) {
     float* C1 = I->mlp_Emax + I->R;  // scratch after the per-region values
     k_mlp_consts<<<1, kHidden, 0, st>>>(I->N, pol->W1, pol->W2, pol->b2, C1, I->mlp_bnd);
     k_mlp_emax<<<(I->R + 7) / 8, 256, 0, st>>>(I->R, I->mlp_P, C1, I->mlp_Emax);
+    cudaError_t e = cudaGetLastError();
+    if (e) return e;
+    // the saturated-state score table, by the scorer itself (weights from global memory)
+    MlpPolicy p = make_policy_view(I, pol, 0);
+    p.sat = nullptr;
+    const int npl = (I->N + 31) / 32;
+    const int blocks = (I->R + kSatWarps - 1) / kSatWarps;
+    I->launches += 1;
+    if (npl == 1) k_mlp_sat<1><<<blocks, 32 * kSatWarps, 0, st>>>(p, I->R, I->mlp_sat);
+    else if (npl == 2) k_mlp_sat<2><<<blocks, 32 * kSatWarps, 0, st>>>(p, I->R, I->mlp_sat);
+    else k_mlp_sat<4><<<blocks, 32 * kSatWarps, 0, st>>>(p, I->R, I->mlp_sat);
     return cudaGetLastError();
 }
 
-cudaError_t sequential_mlp(Instance* I, const pic_policy* pol, cudaStream_t st) {
-    const MlpPolicy p = make_policy_view(I, pol);
+cudaError_t sequential_mlp(Instance* I, const pic_policy* pol, int flags, cudaStream_t st) {
+    const MlpPolicy p = make_policy_view(I, pol, flags);
     const int npl = (I->N + 31) / 32;
     const bool sw = smem_weights_ok(I->N);
     if (npl == 1) return sw ? launch_seq_mlp<1, true>(I, p, st) : launch_seq_mlp<1, false>(I, p, st);
@@ -220,7 +260,7 @@ cudaError_t sequential_mlp(Instance* I, const pic_policy* pol, cudaStream_t st) 
 }
 
 cudaError_t picard_mlp(Instance* I, const KArgs& a, const pic_policy* pol, cudaStream_t st) {
-    const MlpPolicy p = make_policy_view(I, pol);
+    const MlpPolicy p = make_policy_view(I, pol, a.flags);
     // the packed weights fit in shared memory for every N <= 127; tiles need N <= 64
     const bool tc = (a.flags & PIC_FLAG_NO_TC) == 0 && I->N <= 64;
     const int npl = (I->N + 31) / 32;

@@ -112,15 +112,20 @@ struct MlpPolicy {
     // bnd[1] = max_n |b2[n]|
     const float* __restrict__ Emax;
     const float* __restrict__ bnd;
+    // [R][N] FP32 scores (before the Gumbel term) of the saturated state, where
+    // every warehouse holds at least 32 units (every stock feature is 1), computed
+    // by mlp_scores itself; null: evaluate every decision
+    const float* __restrict__ sat;
     bool gumbel;
     unsigned long long seed;
     int traj;
 };
 
 // Counters of one warp's MLP decisions: evaluations, tile rows re-scored in
-// FP32, tile rows decided by the tensor-core scores.
+// FP32, tile rows decided by the tensor-core scores, decisions taken from the
+// saturated-state table.
 struct MlpCounts {
-    unsigned long long calls, rescored, tc;
+    unsigned long long calls, rescored, tc, sat;
 };
 
 // Packed weights read from shared memory (staged copy) or global memory.
@@ -155,12 +160,14 @@ __device__ __forceinline__ unsigned short bf16_bits(float x) {
     return (unsigned short)(__float_as_uint(x) >> 16);  // exact for BF16-representable x
 }
 
-// The warp evaluates the policy for stock row S (lane l holds warehouses l + 32 i)
-// of an order in region r at time t; fs/hs: per-warp shared scratch (N and H
-// floats, hs 16-byte aligned).  Returns the action (warp-uniform).
+// The FP32 scores (R12 order, before the Gumbel term) of the lane's warehouses
+// n = lane + 32 i with want[i], for stock row S (lane l holds warehouses
+// l + 32 i) in region r; fs/hs: per-warp shared scratch (N and H floats, hs
+// 16-byte aligned).
 template <int NPL, bool SMEMW>
-__device__ __forceinline__ int mlp_decide(const MlpPolicy& p, const uint4* W1p, const uint4* W2p,
-                                          const int S[NPL], int r, int t, float* fs, float* hs) {
+__device__ __forceinline__ void mlp_scores(const MlpPolicy& p, const uint4* W1p, const uint4* W2p,
+                                           const int S[NPL], int r, const bool want[NPL],
+                                           float* fs, float* hs, float s_out[NPL]) {
     const int lane = lane_id();
     const int N = p.N, H = p.H;
 #pragma unroll
@@ -179,14 +186,11 @@ __device__ __forceinline__ int mlp_decide(const MlpPolicy& p, const uint4* W1p, 
 #pragma unroll
     for (int u = 0; u < kJ; ++u) hs[lane + 32 * u] = acc[u] > 0.0f ? acc[u] : 0.0f;
     __syncwarp();
-    unsigned best_key = 0;
-    int best_n = INT_MAX;
-    bool any = false;
     const float4* h4 = reinterpret_cast<const float4*>(hs);
 #pragma unroll
     for (int i = 0; i < NPL; ++i) {
         const int n = lane + 32 * i;
-        if (n < N && S[i] > 0) {
+        if (want[i]) {
             // eight partial chains p_e over the hidden units 8q + e, then a fixed tree
             float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f, p4 = 0.f, p5 = 0.f, p6 = 0.f, p7 = 0.f;
 #pragma unroll 4
@@ -204,17 +208,68 @@ __device__ __forceinline__ int mlp_decide(const MlpPolicy& p, const uint4* W1p, 
             }
             const float v = __fadd_rn(__fadd_rn(__fadd_rn(p0, p1), __fadd_rn(p2, p3)),
                                       __fadd_rn(__fadd_rn(p4, p5), __fadd_rn(p6, p7)));
-            float s = __fadd_rn(__ldg(p.b2f + n), v);
+            s_out[i] = __fadd_rn(__ldg(p.b2f + n), v);
+        }
+    }
+    __syncwarp();  // fs / hs reused by the next call
+}
+
+// The decision from the scores s of the lane's warehouses: arg max over stocked
+// warehouses of s (+ Gumbel noise for time t), ties to the lowest index, a^phi
+// (-1) when nothing is stocked.  Warp-uniform.
+template <int NPL>
+__device__ __forceinline__ int mlp_pick(const MlpPolicy& p, const int S[NPL], const float s_in[NPL],
+                                        int t) {
+    const int lane = lane_id();
+    unsigned best_key = 0;
+    int best_n = INT_MAX;
+    bool any = false;
+#pragma unroll
+    for (int i = 0; i < NPL; ++i) {
+        const int n = lane + 32 * i;
+        if (n < p.N && S[i] > 0) {
+            float s = s_in[i];
             if (p.gumbel) s = __fadd_rn(s, gumbel1(p.seed, p.traj, t, n));
             const unsigned kk = ord_key(s);
             if (!any || kk > best_key) { best_key = kk; best_n = n; any = true; }
         }
     }
-    __syncwarp();  // fs / hs reused by the next call
     const unsigned kmax = __reduce_max_sync(kFull, any ? best_key : 0u);
     const bool stocked = __any_sync(kFull, any);
     const int n = __reduce_min_sync(kFull, (any && best_key == kmax) ? best_n : INT_MAX);
     return stocked ? n : -1;
+}
+
+// The warp evaluates the policy for stock row S (lane l holds warehouses l + 32 i)
+// of an order in region r at time t; fs/hs: per-warp shared scratch (N and H
+// floats, hs 16-byte aligned).  In the saturated state (every warehouse at 32
+// units or more) the scores are row r of p.sat, which mlp_scores wrote for that
+// very state, so the decision is the same.  nsat counts those decisions (lane
+// 0).  Returns the action (warp-uniform).
+template <int NPL, bool SMEMW>
+__device__ __forceinline__ int mlp_decide(const MlpPolicy& p, const uint4* W1p, const uint4* W2p,
+                                          const int S[NPL], int r, int t, float* fs, float* hs,
+                                          unsigned long long& nsat) {
+    const int lane = lane_id();
+    float s[NPL];
+    bool sat = p.sat != nullptr;
+#pragma unroll
+    for (int i = 0; i < NPL; ++i)
+        if (lane + 32 * i < p.N) sat &= S[i] >= 32;
+    if (__all_sync(kFull, sat)) {
+#pragma unroll
+        for (int i = 0; i < NPL; ++i) {
+            const int n = lane + 32 * i;
+            s[i] = n < p.N ? __ldg(p.sat + (size_t)r * p.N + n) : 0.0f;
+        }
+        if (lane == 0) ++nsat;
+    } else {
+        bool want[NPL];
+#pragma unroll
+        for (int i = 0; i < NPL; ++i) want[i] = lane + 32 * i < p.N && S[i] > 0;
+        mlp_scores<NPL, SMEMW>(p, W1p, W2p, S, r, want, fs, hs, s);
+    }
+    return mlp_pick<NPL>(p, S, s, t);
 }
 
 // ---------------------------------------------------------------- speculative tensor-core tiles
@@ -417,7 +472,7 @@ __device__ __forceinline__ void seq_mlp_body(int T, int N, const int32_t* __rest
                                              const int32_t* __restrict__ reg, int32_t* xw,
                                              int8_t* __restrict__ act_t, const MlpPolicy& p,
                                              const uint4* W1p, const uint4* W2p, float* fs,
-                                             float* hs) {
+                                             float* hs, unsigned long long& nsat) {
     const int lane = lane_id();
     int my_act = -1;
     for (int t = 0; t < T; ++t) {
@@ -428,7 +483,7 @@ __device__ __forceinline__ void seq_mlp_body(int T, int N, const int32_t* __rest
             const int n = lane + 32 * i;
             S[i] = n < N ? xw[(size_t)k * N + n] : 0;
         }
-        const int act = mlp_decide<NPL, SMEMW>(p, W1p, W2p, S, r, t, fs, hs);
+        const int act = mlp_decide<NPL, SMEMW>(p, W1p, W2p, S, r, t, fs, hs, nsat);
 #pragma unroll
         for (int i = 0; i < NPL; ++i)
             if (act == lane + 32 * i) xw[(size_t)k * N + act] = S[i] - 1;
@@ -466,7 +521,7 @@ __device__ bool replay_segment_mlp(const KArgs& a, const MlpPolicy& p, const uin
     int r = m.r0;
     int next_run = a.run_start[r + 1];
     bool eval = m.j0 > fcp;
-    unsigned long long evals = 0, resc = 0, tcr = 0;
+    unsigned long long evals = 0, resc = 0, tcr = 0, nsat = 0;
     int first_chg = INT_MAX;
     int spec_act = -2, spec_base = 0, spec_left = 0;  // current tile (rows left)
     for (int base = m.j0; base < m.jend; base += 32) {
@@ -500,10 +555,14 @@ __device__ bool replay_segment_mlp(const KArgs& a, const MlpPolicy& p, const uin
                 // the run, and every stocked warehouse above 32 units, so that no early
                 // decrement can change a feature and waste the tile
                 if (SPEC && NPL <= 2 && spec_left == 0 && next_run - (base + q) >= kSpecMin) {
-                    bool low = false;
+                    bool low = false, empty = false;
 #pragma unroll
-                    for (int i = 0; i < NPL; ++i) low |= S[i] > 0 && S[i] <= 32;
-                    if (!__any_sync(kFull, low)) {
+                    for (int i = 0; i < NPL; ++i) {
+                        low |= S[i] > 0 && S[i] <= 32;
+                        empty |= lane + 32 * i < N && S[i] == 0;
+                    }
+                    // with no empty warehouse the saturated-state table is cheaper
+                    if (!__any_sync(kFull, low) && (!p.sat || __any_sync(kFull, empty))) {
                         const int L = min(kTile, next_run - (base + q));
                         spec_act = spec_tile<NPL, SMEMW>(p, W1p, W2p, S[0], S[NPL > 1 ? 1 : 0], L,
                                                          a.reg_s, perm, base + q, t_off, fs, hs);
@@ -517,7 +576,7 @@ __device__ bool replay_segment_mlp(const KArgs& a, const MlpPolicy& p, const uin
                     --spec_left;
                 }
                 if (sa < -1) {
-                    act = mlp_decide<NPL, SMEMW>(p, W1p, W2p, S, rr, tt, fs, hs);
+                    act = mlp_decide<NPL, SMEMW>(p, W1p, W2p, S, rr, tt, fs, hs, nsat);
                     resc += sa == -2;
                 } else {
                     act = sa;
@@ -562,12 +621,13 @@ __device__ bool replay_segment_mlp(const KArgs& a, const MlpPolicy& p, const uin
         cnt_out.calls += evals;
         cnt_out.rescored += resc;
         cnt_out.tc += tcr;
+        cnt_out.sat += nsat;
     }
     return first_chg != INT_MAX;
 }
 
 
-inline MlpPolicy make_policy_view(const Instance* I, const pic_policy* pol) {
+inline MlpPolicy make_policy_view(const Instance* I, const pic_policy* pol, int flags) {
     MlpPolicy p;
     p.N = I->N;
     p.H = kHidden;
@@ -577,6 +637,7 @@ inline MlpPolicy make_policy_view(const Instance* I, const pic_policy* pol) {
     p.b2f = I->mlp_b2;
     p.Emax = I->mlp_Emax;
     p.bnd = I->mlp_bnd;
+    p.sat = (flags & PIC_FLAG_NO_SAT) ? nullptr : I->mlp_sat;
     p.gumbel = pol->kind == PIC_POLICY_GUMBEL;
     p.seed = pol->seed;
     p.traj = pol->traj;

@@ -122,7 +122,7 @@ def test_batch_tensor_core_tiles_exact():
     for i in insts:
         i.x0 = (i.x0 * 40 + 50).astype(np.int32)  # ample stock: features saturate
     db = DeviceBatch(insts)
-    got = db.simulate(pols, "picard", num_chunks=3, flags=pic.PIC_FLAG_TC)
+    got = db.simulate(pols, "picard", num_chunks=3, flags=pic.PIC_FLAG_TC | pic.PIC_FLAG_NO_SAT)
     check_against_oracle(db, insts, pols, got, 3)
     assert got["tc_decisions"] > 0
 
@@ -196,3 +196,18 @@ def test_batch_uneven_full_size():
             row = oracle.state_before(inst, ab, int(t))
             want = oracle.policy_call(inst, pol, row, inst.prod[t], inst.reg[t], int(t))
             assert want == ab[t], (b, t, want, ab[t])
+
+
+def test_batch_saturated_table_exact():
+    """The saturated-state score table in a batch (one table over the combined
+    regions): Picard and batched sequential runs equal the oracle with and
+    without it."""
+    insts, pols = mixed_batch(41, [3000, 2500, 4000, 1500], 32, K=6, R=9)
+    for i in insts:
+        i.x0 = (i.x0 + 40).astype(np.int32)  # saturated for a while
+    db = DeviceBatch(insts)
+    for flags in (0, pic.PIC_FLAG_NO_SAT):
+        for mode in ("picard", "sequential"):
+            got = db.simulate(pols, mode, num_chunks=9, flags=flags)
+            check_against_oracle(db, insts, pols, got, 9 if mode == "picard" else None)
+            assert (got["sat_decisions"] > 0) == (flags == 0)

@@ -91,7 +91,9 @@ def test_mlp_full_size_sampled_against_oracle():
 def test_tensor_core_tiles_bit_exact(N):
     """PIC_FLAG_TC: long runs with ample stock are scored 16 orders at a time on
     the tensor cores; the actions, pass counts and iterates are the oracle's
-    (rows whose top-2 margin is within the error bound are re-scored in FP32)."""
+    (rows whose top-2 margin is within the error bound are re-scored in FP32).
+    The saturated-state table is turned off (PIC_FLAG_NO_SAT): with every
+    warehouse stocked it would take these decisions instead of the tiles."""
     inst = synth.make_instance(12000, N, 6, 17, seed=N, stock="poisson", fill=1.2)
     mlp = synth.make_mlp(N, 17, seed=N)
     d = DeviceInstance(inst)
@@ -99,7 +101,7 @@ def test_tensor_core_tiles_bit_exact(N):
         seq = oracle.seq_sim(inst, pol)
         for M in (3, 12):
             want = oracle.picard_chunked(inst, pol, M)
-            got = d.simulate(pol, "picard", num_chunks=M, flags=pic.PIC_FLAG_TC)
+            got = d.simulate(pol, "picard", num_chunks=M, flags=pic.PIC_FLAG_TC | pic.PIC_FLAG_NO_SAT)
             np.testing.assert_array_equal(got["actions"].cpu().numpy(), seq["actions"])
             np.testing.assert_array_equal(got["final_stock"].cpu().numpy(), seq["x_final"])
             assert got["iters"] == want["iters"] and got["total_cost"] == seq["total_cost"]
@@ -107,7 +109,7 @@ def test_tensor_core_tiles_bit_exact(N):
             assert got["tc_decisions"] + got["rescored"] <= got["mlp_calls"]
         want = oracle.picard_chunked(inst, pol, 12, record=True)
         for k in (1, 2):
-            g = d.simulate(pol, "picard", num_chunks=12, max_iters=k, flags=pic.PIC_FLAG_TC,
+            g = d.simulate(pol, "picard", num_chunks=12, max_iters=k, flags=pic.PIC_FLAG_TC | pic.PIC_FLAG_NO_SAT,
                            raise_on_error=False)
             np.testing.assert_array_equal(g["actions"].cpu().numpy(), want["iterates"][k - 1])
 
@@ -123,13 +125,42 @@ def test_tensor_core_tiles_with_low_stock_and_ties():
     d = DeviceInstance(inst)
     pol = Policy("mlp", mlp=mlp)
     seq = oracle.seq_sim(inst, pol)
-    got = d.simulate(pol, "picard", num_chunks=4, flags=pic.PIC_FLAG_TC)
+    got = d.simulate(pol, "picard", num_chunks=4, flags=pic.PIC_FLAG_TC | pic.PIC_FLAG_NO_SAT)
     np.testing.assert_array_equal(got["actions"].cpu().numpy(), seq["actions"])
     flat = synth.MLPParams(mlp.W1, mlp.b1, np.zeros_like(mlp.W2), np.zeros_like(mlp.b2), mlp.E)
     inst2 = synth.make_instance(6000, N, 4, 9, seed=6, stock="poisson", fill=2.0)
     d2 = DeviceInstance(inst2)
     pol2 = Policy("mlp", mlp=flat)
     seq2 = oracle.seq_sim(inst2, pol2)
-    got2 = d2.simulate(pol2, "picard", num_chunks=4, flags=pic.PIC_FLAG_TC)
+    got2 = d2.simulate(pol2, "picard", num_chunks=4, flags=pic.PIC_FLAG_TC | pic.PIC_FLAG_NO_SAT)
     np.testing.assert_array_equal(got2["actions"].cpu().numpy(), seq2["actions"])
     assert got2["tc_decisions"] == 0 or got2["rescored"] > 0
+
+
+@pytest.mark.parametrize("N", [8, 33, 64, 100])
+def test_saturated_state_table_exact(N):
+    """Products holding at least 32 units at every warehouse take their scores
+    from the per-region table (built by the scorer itself); other products run
+    the scorer.  Sequential and Picard paths equal the oracle with and without
+    the table (PIC_FLAG_NO_SAT), and the table is used only by default."""
+    inst, mlp = small(3 * N, 3000, N, 12, 9, fill=0.9)
+    x0 = inst.x0.copy()
+    x0[: inst.K // 2] += 60  # the popular half saturated for a while, the rest not
+    inst.x0 = x0
+    d = DeviceInstance(inst)
+    for pol in policies(mlp, N):
+        want = oracle.seq_sim(inst, pol)
+        M = 25
+        iters = oracle.picard_chunked(inst, pol, M)["iters"]
+        for flags in (0, pic.PIC_FLAG_NO_SAT):
+            for mode in ("sequential", "picard"):
+                got = d.simulate(pol, mode, num_chunks=M, flags=flags)
+                np.testing.assert_array_equal(got["actions"].cpu().numpy(), want["actions"])
+                np.testing.assert_array_equal(got["final_stock"].cpu().numpy(), want["x_final"])
+                assert got["total_cost"] == want["total_cost"]
+                if mode == "picard":
+                    assert got["iters"] == iters
+                if flags:
+                    assert got["sat_decisions"] == 0
+                else:
+                    assert 0 < got["sat_decisions"] < got["policy_calls"]

@@ -203,7 +203,7 @@ def test_tensor_core_tiles_in_the_simulation():
     insts, mlp, pols = case(12, [5000, 7000], 32, K=4, R=8, fill=1.5)
     db = DeviceBatch(insts)
     rf = Reinforce(db, ["gumbel"] * 2, [p.seed for p in pols], [p.traj for p in pols], 8,
-                   num_chunks=3, flags=pic.PIC_FLAG_TC)
+                   num_chunks=3, flags=pic.PIC_FLAG_TC | pic.PIC_FLAG_NO_SAT)
     m = flat_from_mlp(mlp)
     acts = torch.empty(db.T, dtype=torch.int8, device="cuda")
     J, res = rf.objective(m, actions_out=acts)

@@ -55,6 +55,8 @@ def _load():
             lib.orc_picard_literal.restype = C.c_int
             lib.orc_picard_chunked.argtypes = common + [i32, i32, P, P, P, P, P, P]
             lib.orc_picard_chunked.restype = C.c_int
+            lib.orc_picard_windowed.argtypes = common + [i32, i64, i32, P, P, P, P, P, P]
+            lib.orc_picard_windowed.restype = C.c_int
             capc = [i32, i32, i32, i32, P, P, P, P, P, P, i32]
             lib.orc_seq_sim_cap.argtypes = capc + [P, P, P, P, P]
             lib.orc_seq_sim_cap.restype = C.c_int
@@ -208,6 +210,39 @@ def picard_chunked(inst, pol, M, max_iters=None, alpha_init=None, record=False):
         return _picard(_load().orc_picard_chunked_cap, inst, pol, M, max_iters, alpha_init,
                        record, True, args, keep)
     return _picard(_load().orc_picard_chunked, inst, pol, M, max_iters, alpha_init, record, True)
+
+
+def picard_windowed(inst, pol, M, max_steps, max_iters=None, alpha_init=None, record=False):
+    """Algorithm 1 on M contiguous blocks with the max_steps window of Appendix
+    A.3 (no capacity): a pass evaluates only the blocks that start before
+    w_start + max_steps; the window starts at the first changed time of the
+    previous pass, or moves past the evaluated blocks after a pass without
+    change; the loop returns after a pass without change that evaluated every
+    block.  max_iters defaults to 2 M + 2.
+
+    Pins: max_steps >= T gives the iterates of picard_chunked; the fixed point is
+    seq_sim for every max_steps (exhaustive tiny family and random instances,
+    every policy kind); with one block per window at most 2 M passes."""
+    if max_iters is None:
+        max_iters = 2 * M + 2
+    lib = _load()
+    args, keep = _args(inst, pol)
+    act = np.empty(inst.T, np.int8)
+    iters = C.c_int32(0)
+    its = np.empty((max_iters, inst.T), np.int8) if record else None
+    chg = np.zeros(max_iters, np.int64)
+    fst = np.zeros(max_iters, np.int64)
+    ai = _c(alpha_init, np.int8)
+    rc = lib.orc_picard_windowed(*args, int(M), int(max_steps), int(max_iters), _p(ai), _p(act),
+                                 C.byref(iters), _p(its), _p(chg), _p(fst))
+    if rc not in (OK, ERR_NOT_CONVERGED):
+        raise ValueError(f"orc_picard_windowed failed rc={rc}")
+    k = iters.value
+    out = {"actions": act, "iters": k, "converged": rc == OK, "changed": chg[:k].copy(),
+           "first_changed": fst[:k].copy()}
+    if record:
+        out["iterates"] = its[:k].copy()
+    return out
 
 
 def picard_partition(inst, pol, proc, max_iters=None, alpha_init=None, record=False):

@@ -652,3 +652,90 @@ int orc_picard_chunked_cap(int32_t T, int32_t N, int32_t K, int32_t R, const int
     free(P.scratch);
     return converged ? ORC_OK : ORC_ERR_NOT_CONVERGED;
 }
+
+/* ========================================================================= */
+/* Algorithm 1 with the max_steps window of Appendix A.3, on the contiguous
+ * blocks [m*L, min((m+1)*L, T)) (no capacity).  A pass evaluates the policy
+ * only on the blocks that start before w_end = w_start + max_steps; later blocks
+ * keep their cached actions.  The window is counted in whole blocks: a block is
+ * evaluated whole once its first order is inside the window, so a pass
+ * evaluates the orders before e = min(T, ceil(w_end / L) L).  The window starts
+ * at 0; after a pass that changed some action it starts at the first changed
+ * time t_reset (earlier actions are final); after a pass that changed nothing it
+ * moves on to e (the evaluated blocks reached their fixed point from an exact
+ * prefix).  The loop returns after a pass that changed nothing with e = T.  Blocks are replayed from
+ * the closed-form prefix, as in orc_picard_chunked.  With max_steps >= T the
+ * passes are those of orc_picard_chunked.  Outputs as orc_picard_chunked. */
+/* ========================================================================= */
+int orc_picard_windowed(int32_t T, int32_t N, int32_t K, int32_t R, const int32_t* prod,
+                        const int32_t* reg, const int32_t* x0, const int32_t* cost,
+                        const int32_t* lam, int32_t kind, int32_t H, const uint16_t* W1,
+                        const uint16_t* b1, const uint16_t* W2, const uint16_t* b2,
+                        const uint16_t* E, uint64_t seed, int32_t traj, int32_t M,
+                        int64_t max_steps, int32_t max_iters, const int8_t* alpha_init,
+                        int8_t* act_out, int32_t* iters_out, int8_t* iterates,
+                        int64_t* changed_out, int64_t* first_changed_out) {
+    int rc = check_instance(T, N, K, R, prod, reg, x0);
+    if (rc) return rc;
+    if (M <= 0 || max_iters <= 0 || max_steps <= 0) return ORC_ERR_ARG;
+    policy_t P;
+    rc = policy_init(&P, kind, N, R, cost, lam, H, W1, b1, W2, b2, E, seed, traj);
+    if (rc) return rc;
+    const int64_t L = ((int64_t)T + M - 1) / M;
+    int8_t* prev = (int8_t*)malloc((size_t)T + 1);
+    int8_t* next = (int8_t*)malloc((size_t)T + 1);
+    int32_t* D = (int32_t*)malloc(sizeof(int32_t) * (size_t)K * N);
+    int32_t* S = (int32_t*)malloc(sizeof(int32_t) * (size_t)K * N);
+    int32_t* stamp = (int32_t*)malloc(sizeof(int32_t) * (size_t)K);
+    for (int64_t t = 0; t < T; ++t) prev[t] = alpha_init ? alpha_init[t] : (int8_t)-1;
+    int converged = 0, k;
+    int64_t w_start = 0;
+    for (k = 1; k <= max_iters; ++k) {
+        const int64_t w_end = w_start + max_steps;
+        memcpy(next, prev, (size_t)T);
+        memset(D, 0, sizeof(int32_t) * (size_t)K * N);
+        for (int32_t i = 0; i < K; ++i) stamp[i] = -1;
+        for (int32_t m = 0; m < M; ++m) {
+            int64_t lo = (int64_t)m * L, hi = lo + L < T ? lo + L : T;
+            if (lo >= hi || lo >= w_end) break; /* blocks from here on keep their cache */
+            for (int64_t t = lo; t < hi; ++t) {
+                int32_t pk = prod[t], r = reg[t];
+                int32_t* row = S + (size_t)pk * N;
+                if (stamp[pk] != m) {
+                    for (int n = 0; n < N; ++n) {
+                        int32_t v = x0[(size_t)pk * N + n] - D[(size_t)pk * N + n];
+                        row[n] = v > 0 ? v : 0;
+                    }
+                    stamp[pk] = m;
+                }
+                int a = policy_eval(&P, row, pk, r, t);
+                next[t] = (int8_t)a;
+                if (a >= 0) row[a] -= 1;
+            }
+            for (int64_t t = lo; t < hi; ++t) {
+                int a = prev[t];
+                if (a >= 0 && a < N) D[(size_t)prod[t] * N + a] += 1;
+            }
+        }
+        int64_t nchg = 0, first = T;
+        for (int64_t t = 0; t < T; ++t)
+            if (next[t] != prev[t]) { if (first == T) first = t; nchg++; }
+        if (iterates) memcpy(iterates + (size_t)(k - 1) * T, next, (size_t)T);
+        if (changed_out) changed_out[k - 1] = nchg;
+        if (first_changed_out) first_changed_out[k - 1] = first;
+        int8_t* tmp = prev; prev = next; next = tmp;
+        /* end of the evaluated blocks: every block that starts before w_end */
+        int64_t e = ((w_end + L - 1) / L) * L;
+        if (e > T) e = T;
+        if (nchg == 0) {
+            if (e >= T) { converged = 1; break; }
+            w_start = e; /* the window converged: move on past its blocks */
+        } else {
+            w_start = first;
+        }
+    }
+    memcpy(act_out, prev, (size_t)T);
+    *iters_out = converged ? k : max_iters;
+    free(prev); free(next); free(D); free(S); free(stamp); free(P.scratch);
+    return converged ? ORC_OK : ORC_ERR_NOT_CONVERGED;
+}

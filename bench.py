@@ -85,10 +85,14 @@ def parse():
                    choices=["dual_large", "mlp_medium", "batch_uneven", "pg_large",
                             "capacity_large"])
     p.add_argument("--flags", type=int, default=0, help="extra pic_sim_opts flags (tuning)")
+    p.add_argument("--max-steps", type=int, default=-1,
+                   help="Picard window of App. A.3 in orders (-1: the workload's default, 0: none)")
     p.add_argument("--B", type=int, default=0,
                    help="trajectories of batch_uneven / pg_large (0 = the workload's 512 / 64)")
     return p.parse_args()
 
+
+DEFAULT_MAX_STEPS = {"mlp_medium": 0}
 
 DEFAULT_CHUNKS = {"dual_large": 4096, "mlp_medium": 1024, "batch_uneven": 0, "pg_large": 0,
                   "capacity_large": 16384}
@@ -149,6 +153,8 @@ def workload_config(args, inst):
                  f"{pol}{cap}"),
         "T": inst.T, "N": inst.N, "K": inst.K, "R": inst.R,
         "chunks": chunks_of(args), "policy": args.workload == "mlp_medium" and "mlp" or "dual",
+        "max_steps": (args.max_steps if args.max_steps >= 0 else
+                      DEFAULT_MAX_STEPS.get(args.workload, 0)) or None,
         "l2": "flushed between timed steps (256 MiB write)",
     }
 
@@ -649,9 +655,12 @@ def main():
     T = inst.T
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
+    max_steps = args.max_steps if args.max_steps >= 0 else DEFAULT_MAX_STEPS.get(args.workload, 0)
+
     def step(out):
         return di.simulate(pol, "picard", num_chunks=chunks_of(args), seg_window=args.seg_window,
-                           flags=pic.PIC_FLAG_TIMING | args.flags, want_stock=False, out=out)
+                           flags=pic.PIC_FLAG_TIMING | args.flags, want_stock=False, out=out,
+                           max_steps=max_steps)
 
     act = torch.empty(T, dtype=torch.int8, device=dev)
     for _ in range(max(3, args.warmup)):
@@ -683,7 +692,7 @@ def main():
     # one extra (untimed) call with the per-pass trace
     tr = np.zeros((4096, 4), np.int64)
     di.simulate(pol, "picard", num_chunks=chunks_of(args), seg_window=args.seg_window,
-                flags=args.flags, want_stock=False, out=act, trace=tr)
+                flags=args.flags, want_stock=False, out=act, trace=tr, max_steps=max_steps)
     ntr = min(last["iters"], 4096)
     ts, tr_end = tr[:ntr, 0], tr[:ntr, 1]
     prev = np.r_[0, tr_end[:-1]]
@@ -716,7 +725,7 @@ def main():
     host_np = {k: (v.numpy() if v is not None else None) for k, v in host.items()}
     host_act = torch.empty(T, dtype=torch.int8).pin_memory().numpy()
     opts = pic.make_opts("picard", chunks_of(args), out_mem=pic.PIC_MEM_HOST, seg_window=args.seg_window,
-                         flags=args.flags)
+                         flags=args.flags, max_steps=max_steps)
     h2d = sum(v.nbytes for v in host_np.values() if v is not None)
     d2h = host_act.nbytes + 64  # actions + the result record
     e2e_t = []

@@ -140,6 +140,15 @@ typedef struct {
                                  phase, ns to the end of its replay phase, policy calls in the
                                  pass, work units replayed in the pass */
     int32_t trace_cap;        /* rows available in trace */
+    int32_t max_steps;        /* PIC_MODE_PICARD on a single instance without capacity: the
+                                 window of Appendix A.3, or 0 for none.  A pass evaluates the
+                                 policy only on the chunks that start before w + max_steps
+                                 (whole chunks); w is 0 at first, then the first time changed
+                                 by the previous pass, or, after a pass that changed nothing,
+                                 the end of the chunks it evaluated.  The call returns after a
+                                 pass that changed nothing and evaluated every chunk.  The
+                                 result is still the sequential path; max_iters defaults to
+                                 2 M + 2.  Batches reject it (UNSUPPORTED) */
 } pic_sim_opts;
 
 typedef struct {

@@ -56,7 +56,7 @@ class pic_sim_opts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("num_chunks", C.c_int32), ("max_iters", C.c_int32),
                 ("flags", C.c_int32), ("alpha_init", C.c_void_p), ("timeout_ns", C.c_uint64),
                 ("out_mem", C.c_int32), ("seg_window", C.c_int32), ("stream", C.c_void_p),
-                ("trace", C.c_void_p), ("trace_cap", C.c_int32)]
+                ("trace", C.c_void_p), ("trace_cap", C.c_int32), ("max_steps", C.c_int32)]
 
 
 class pic_sim_result(C.Structure):
@@ -177,12 +177,14 @@ def make_policy(kind="greedy", W1=None, b1=None, W2=None, b2=None, E=None, hidde
 
 
 def make_opts(mode="picard", num_chunks=0, max_iters=0, flags=0, alpha_init=None, timeout_ns=0,
-              out_mem=PIC_MEM_DEVICE, seg_window=0, stream=None, trace=None) -> pic_sim_opts:
-    """trace: optional host int64 numpy array [cap, 4] receiving the per-pass record."""
+              out_mem=PIC_MEM_DEVICE, seg_window=0, stream=None, trace=None,
+              max_steps=0) -> pic_sim_opts:
+    """trace: optional host int64 numpy array [cap, 4] receiving the per-pass record;
+    max_steps: the Picard window (0: none)."""
     m = MODES[mode] if isinstance(mode, str) else int(mode)
     return pic_sim_opts(m, int(num_chunks), int(max_iters), int(flags), _ptr(alpha_init),
                         int(timeout_ns), int(out_mem), int(seg_window), _stream_handle(stream),
-                        _ptr(trace), 0 if trace is None else int(trace.shape[0]))
+                        _ptr(trace), 0 if trace is None else int(trace.shape[0]), int(max_steps))
 
 
 def pic_simulate(handle: int, policy: pic_policy, opts: pic_sim_opts, actions_out,

@@ -200,7 +200,7 @@ cudaError_t launch_validate(Instance& I, cudaStream_t st) {
 void free_instance(Instance& I) {
     free_pg(I);
     void* ptrs[] = {I.prod, I.reg, I.x0, I.cost, I.lam, I.perm, I.prod_s, I.reg_s, I.pcount,
-                    I.pstart, I.run_start, I.run_of, I.seg_run, I.seg_of_run, I.seg_prod, I.seg_cf,
+                    I.pstart, I.run_start, I.run_of, I.run_chunk, I.seg_run, I.seg_of_run, I.seg_prod, I.seg_cf,
                     I.seg_ce, I.seg_meta, I.seg_lpt, I.len_hist, I.alpha_s, I.agg, I.carry, I.sbagg,
                     I.sbincl, I.fc, I.xfin, I.xwork, I.act_t, I.tmp_a, I.tmp_b, I.tmp_c, I.scan_blk,
                     I.hist, I.ctrl, I.trace, I.mlp_P, I.mlp_W1p, I.mlp_W2p, I.mlp_b2, I.mlp_Emax, I.mlp_bnd, I.mlp_sat,
@@ -253,6 +253,7 @@ cudaError_t alloc_instance(Instance& I, int T_, int N_, int K_, int R_, bool has
     if (!e) e = dmalloc(&I.pstart, K + 1);
     if (!e) e = dmalloc(&I.run_start, T + 2);
     if (!e) e = dmalloc(&I.run_of, T + 1);
+    if (!e) e = dmalloc(&I.run_chunk, T + 1);
     if (!e) e = dmalloc(&I.seg_run, S + 1);
     if (!e) e = dmalloc(&I.seg_of_run, T + 1);
     if (!e) e = dmalloc(&I.seg_prod, S);
@@ -420,8 +421,10 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
         return fail(PIC_ERR_INVALID_ARG, "MLP policy needs W1, b1, W2, b2 and E (device pointers)");
     if (mlp && I.has_cap)
         return fail(PIC_ERR_UNSUPPORTED, "node capacity: greedy and bid-price policies only");
-    if (opts->num_chunks < 0 || opts->max_iters < 0 || opts->seg_window < 0)
-        return fail(PIC_ERR_INVALID_ARG, "negative num_chunks, max_iters or seg_window");
+    if (opts->num_chunks < 0 || opts->max_iters < 0 || opts->seg_window < 0 || opts->max_steps < 0)
+        return fail(PIC_ERR_INVALID_ARG, "negative num_chunks, max_iters, seg_window or max_steps");
+    if (opts->max_steps > 0 && I.has_cap)
+        return fail(PIC_ERR_UNSUPPORTED, "the max_steps window is not supported with node capacity");
     cudaStream_t st = (cudaStream_t)opts->stream;
     const size_t T = I.T, K = I.K, N = I.N;
     const bool host_out = opts->out_mem == PIC_MEM_HOST;
@@ -487,7 +490,8 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
         // default window: long work units amortise the cheap integer policy; the MLP
         // policy's per-order cost makes short units (short critical paths) better
         const int W = opts->seg_window ? opts->seg_window : (mlp ? kSegWindowMlp : kSegWindow);
-        iters_cap = opts->max_iters ? opts->max_iters : M + 1;
+        // the window needs at most two passes per block (one change, one confirmation)
+        iters_cap = opts->max_iters ? opts->max_iters : (opts->max_steps > 0 ? 2 * M + 2 : M + 1);
         CU(prepare_picard_state(I, W, iters_cap, st));
         const bool reuse = (opts->flags & PIC_FLAG_REUSE_TABLES) && I.tables_m == M && I.tables_w == W;
         if (!reuse) {
@@ -497,12 +501,20 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
         }
         CU(take_tags(I, iters_cap, st));
         CU(init_cache(I, opts->alpha_init, st));
+        if (T && opts->max_steps > 0 && !opts->alpha_init) {
+            // segments outside the first windows are not replayed in pass 1: their
+            // histograms and chain prefixes must start as those of the all-a^phi cache
+            const size_t bytes = sizeof(int32_t) * (size_t)I.smax_agg * I.NP;
+            CU(cudaMemsetAsync(I.agg, 0, bytes, st));
+            CU(cudaMemsetAsync(I.carry, 0, bytes, st));
+        }
         if (T) {
             if (timing) CU(cudaEventRecord(I.ev[1], st));
             const bool trace = opts->trace && opts->trace_cap > 0;
             if (trace) CU(cudaMemsetAsync(I.trace, 0, sizeof(long long) * 4 * kTraceCap, st));
             CU(picard_run(&I, pol, iters_cap, opts->flags, opts->alpha_init,
-                          opts->timeout_ns ? opts->timeout_ns : 10000000000ull, trace, st));
+                          opts->timeout_ns ? opts->timeout_ns : 10000000000ull, trace,
+                          opts->max_steps, st));
             if (timing) CU(cudaEventRecord(I.ev[2], st));
             CU(finish_outputs(&I, st));
             CU(cudaMemcpyAsync(actions_out, I.act_t, T, okind, st));

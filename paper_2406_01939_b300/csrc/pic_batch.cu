@@ -382,6 +382,10 @@ pic_status enqueue_picard(Instance& I, const CallCfg& c, cudaStream_t st) {
     a.ctrl = I.ctrl; a.max_iters = c.iters_cap; a.flags = c.flags;
     a.first_dirty = c.alpha_init != nullptr; a.timeout_ns = c.timeout_ns;
     a.trace = c.trace ? I.trace : nullptr;
+    a.run_chunk = nullptr;  // no max_steps window
+    a.perm = nullptr;
+    a.win_steps = 0;
+    a.M = a.L = 0;
     pic_policy mp = c.mlp;
     mp.kind = PIC_POLICY_MLP;
     const MlpPolicy p = make_policy_view(&I, &mp, c.flags);
@@ -680,6 +684,8 @@ pic_status pic_simulate_batch(pic_instance* h, const pic_policy* pols, const pic
         return fail(PIC_ERR_INVALID_ARG, "unknown out_mem %d", opts->out_mem);
     if (opts->num_chunks < 0 || opts->max_iters < 0 || opts->seg_window < 0)
         return fail(PIC_ERR_INVALID_ARG, "negative num_chunks, max_iters or seg_window");
+    if (opts->max_steps != 0)
+        return fail(PIC_ERR_UNSUPPORTED, "the max_steps window is for single instances (pic_simulate)");
     if (opts->flags & PIC_FLAG_GROUP_KERNEL)
         return fail(PIC_ERR_UNSUPPORTED, "PIC_FLAG_GROUP_KERNEL applies to pic_simulate only");
     CallCfg c;

@@ -609,6 +609,10 @@ cudaError_t picard_cap(Instance* I, const pic_policy* pol, int M, int max_iters,
     a.ctrl = I->ctrl; a.max_iters = max_iters; a.flags = flags;
     a.first_dirty = alpha_init != nullptr; a.timeout_ns = timeout_ns;
     a.trace = trace ? I->trace : nullptr;
+    a.run_chunk = nullptr;  // no max_steps window
+    a.perm = nullptr;
+    a.win_steps = 0;
+    a.M = a.L = 0;
     CapArgs c;
     c.M = M;
     c.L = (int)(((long long)T + M - 1) / M);

@@ -142,7 +142,7 @@ bool smem_cost_ok(const Instance* I) {
 
 cudaError_t picard_run(Instance* I, const pic_policy* pol, int max_iters, int flags,
                        const int8_t* alpha_init, unsigned long long timeout_ns, bool trace,
-                       cudaStream_t st) {
+                       int max_steps, cudaStream_t st) {
     const int kind = pol->kind;
     KArgs a;
     a.T = I->T; a.N = I->N; a.K = I->K; a.NP = I->NP; a.R = I->R;
@@ -155,9 +155,15 @@ cudaError_t picard_run(Instance* I, const pic_policy* pol, int max_iters, int fl
     a.ctrl = I->ctrl; a.max_iters = max_iters; a.flags = flags;
     a.first_dirty = alpha_init != nullptr; a.timeout_ns = timeout_ns;
     a.trace = trace ? I->trace : nullptr;
+    a.run_chunk = max_steps > 0 ? I->run_chunk : nullptr;
+    a.perm = I->perm;
+    a.win_steps = max_steps;
+    a.M = I->tables_m;
+    a.L = I->tables_m ? (int)(((long long)I->T + I->tables_m - 1) / I->tables_m) : 1;
     if (kind == PIC_POLICY_MLP || kind == PIC_POLICY_GUMBEL) return picard_mlp(I, a, pol, st);
     const bool dual = kind == PIC_POLICY_DUAL;
-    if ((flags & PIC_FLAG_GROUP_KERNEL) && grp_ok(I)) return picard_grp(I, a, dual, st);
+    // the group kernel has no max_steps window
+    if ((flags & PIC_FLAG_GROUP_KERNEL) && grp_ok(I) && max_steps <= 0) return picard_grp(I, a, dual, st);
     const int npl = (I->N + 31) / 32;
     if (npl == 1) return dual ? picard_dispatch<1, true>(I, a, st) : picard_dispatch<1, false>(I, a, st);
     if (npl == 2) return dual ? picard_dispatch<2, true>(I, a, st) : picard_dispatch<2, false>(I, a, st);

@@ -39,6 +39,10 @@ struct Ctrl {
     unsigned long long tc_rows;    // MLP decisions taken from tensor-core tile scores
     unsigned long long sat_rows;   // MLP decisions taken from the saturated-state table
     int cap_fct[2];          // capacity kernel: first changed time of the pass, per parity
+    int win_fct[2];          // max_steps window: first changed time of the pass, per parity
+    int win_hi, win_hi_prev; // max_steps window of the current pass and of the previous one:
+                             // runs of chunks below win_hi are evaluated; chunks at or above
+                             // win_hi_prev were not evaluated in the previous pass
     int nruns;               // tables built by the preprocessing kernels
     int nseg;
     int last_m;              // chunk count the tables were built for
@@ -113,6 +117,7 @@ struct Instance {
     int32_t *pstart;    // [K+1] first sorted position per product
     int32_t *run_start; // [T+1] first sorted position of each run (chunk x product)
     int32_t *run_of;    // [T]   run of sorted position j
+    int32_t *run_chunk; // [T+1] chunk (time block) of each run (single instances)
     int32_t *seg_run;   // [SMAX+1] first run of each segment
     int32_t *seg_of_run;// [T]
     int32_t *seg_prod;  // [SMAX]
@@ -188,9 +193,10 @@ cudaError_t scatter_actions(Instance* I, cudaStream_t st);
 cudaError_t finish_outputs(Instance* I, cudaStream_t st);
 
 // Picard passes for any policy (pic_int.cu dispatches to the integer or MLP kernels).
+// max_steps > 0: the window of Appendix A.3 (integer and MLP warp kernels).
 cudaError_t picard_run(Instance* I, const pic_policy* pol, int max_iters, int flags,
                        const int8_t* alpha_init, unsigned long long timeout_ns, bool trace,
-                       cudaStream_t st);
+                       int max_steps, cudaStream_t st);
 // MLP policies (pic_mlp.cu).  mlp_prepare evaluates the per-region chain
 // prefix (E rows through reg_local for a batch) and the FP32 weight copies.
 cudaError_t mlp_alloc(Instance* I);

@@ -520,7 +520,10 @@ __device__ bool replay_segment_mlp(const KArgs& a, const MlpPolicy& p, const uin
     }
     int r = m.r0;
     int next_run = a.run_start[r + 1];
-    bool eval = m.j0 > fcp;
+    // the max_steps window of this pass (none: INT_MAX)
+    const int whi = a.run_chunk ? ld_volatile(&a.ctrl->win_hi) : INT_MAX;
+    const int wprev = a.run_chunk ? ld_volatile(&a.ctrl->win_hi_prev) : INT_MAX;
+    bool eval = run_evaluated(a, whi, wprev, r, m.j0 > fcp);
     unsigned long long evals = 0, resc = 0, tcr = 0, nsat = 0;
     int first_chg = INT_MAX;
     int spec_act = -2, spec_base = 0, spec_left = 0;  // current tile (rows left)
@@ -540,7 +543,7 @@ __device__ bool replay_segment_mlp(const KArgs& a, const MlpPolicy& p, const uin
                     S[i] = max(0, x0v[i] - D[i]);
                     S0[i] = S[i];
                 }
-                eval = next_run > fcp;
+                eval = run_evaluated(a, whi, wprev, r + 1, next_run > fcp);
                 ++r;
                 next_run = a.run_start[r + 1];
                 spec_left = 0;  // the state jumps to the next run's start
@@ -610,6 +613,7 @@ __device__ bool replay_segment_mlp(const KArgs& a, const MlpPolicy& p, const uin
     }
     if (lane == 0 && first_chg != INT_MAX && first_chg < ld_volatile(&fc_cur[k]))
         atomicMin(&fc_cur[k], first_chg);
+    if (lane == 0) report_window_change(a, it, first_chg);
     if (s == m.ce - 1) {
 #pragma unroll
         for (int i = 0; i < NPL; ++i) {

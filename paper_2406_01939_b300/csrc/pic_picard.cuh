@@ -35,7 +35,30 @@ struct KArgs {
     int first_dirty;
     unsigned long long timeout_ns;
     long long* trace;  // per-pass record or nullptr
+    // max_steps window (Appendix A.3), or run_chunk == nullptr: no window
+    const int32_t* __restrict__ run_chunk;  // [runs] time block of each run
+    const int32_t* __restrict__ perm;       // [T] sorted position -> time
+    int win_steps;                          // max_steps
+    int M, L;                               // chunks and chunk length
 };
+
+// Whether a run is evaluated in this pass.  Without a window: its start lies
+// after its product's first change of the previous pass (t_reset).  With the
+// window [0, hi) in chunks: the run's chunk is inside it, and either t_reset
+// says so or the chunk was outside the previous pass's window (its cache was
+// not computed from the current prefix).
+__device__ __forceinline__ bool run_evaluated(const KArgs& a, int whi, int wprev, int r,
+                                              bool after_change) {
+    if (!a.run_chunk) return after_change;
+    const int c = __ldg(a.run_chunk + r);
+    return c < whi && (after_change || c >= wprev);
+}
+
+// A replay that changed a cached action reports the time of its first change
+// (lane 0; sorted position j) for the window's t_reset.
+__device__ __forceinline__ void report_window_change(const KArgs& a, int it, int j) {
+    if (a.run_chunk && j != INT_MAX) atomicMin(&a.ctrl->win_fct[it & 1], __ldg(a.perm + j));
+}
 
 template <bool SMEM>
 struct CostTable {
@@ -279,6 +302,12 @@ __device__ __forceinline__ void picard_passes(const KArgs& a, unsigned long long
     const unsigned long long t_start = globaltimer_ns();
     int it = 1;
     bool ok = true, converged = false;
+    // max_steps window (identical in every thread): evaluated chunks [0, whi),
+    // previous pass [0, wprev)
+    const bool win = a.run_chunk != nullptr;
+    long long wstart = 0;
+    int wprev = win ? 0 : INT_MAX;
+    int whi = win ? (int)min((long long)a.M, ((long long)a.win_steps + a.L - 1) / a.L) : INT_MAX;
     for (; it <= a.max_iters; ++it) {
         const int parity = it & 1;
         long long* tr = (a.trace && it <= kTraceCap) ? a.trace + 4 * (it - 1) : nullptr;
@@ -287,7 +316,12 @@ __device__ __forceinline__ void picard_passes(const KArgs& a, unsigned long long
         int* fc_cur = a.fc + (size_t)parity * a.K;
         // ---- phase S: this warp's segments gwarp + j * nwarps, 32 at a time
         for (int k = gtid; k < a.K; k += gthreads) fc_cur[k] = INT_MAX;
-        if (gtid == 0) a.ctrl->changed[parity] = 0;
+        if (gtid == 0) {
+            a.ctrl->changed[parity] = 0;
+            a.ctrl->win_fct[parity] = INT_MAX;
+            a.ctrl->win_hi = whi;
+            a.ctrl->win_hi_prev = wprev;
+        }
         if (it > 1 || a.first_dirty)
             chain_prefixes<NPL>(a, it, fc_prev, tag_base + (unsigned)it, deadline, s_meta[wib],
                                 s_fcp[wib]);
@@ -305,6 +339,10 @@ __device__ __forceinline__ void picard_passes(const KArgs& a, unsigned long long
                 const SegMeta m = load_meta(a.meta + sl);
                 const int fcp = no_reset ? -1 : fc_prev[m.k];
                 act = m.last_start > fcp;  // some run starts after the first change
+                if (win) {  // ... or entered the window; and some run is inside it
+                    const int c0 = __ldg(a.run_chunk + m.r0), c1 = __ldg(a.run_chunk + m.r1 - 1);
+                    act = c0 < whi && (act || c1 >= wprev);
+                }
                 if (act) {
                     s_meta[wib][lane] = m;
                     s_fcp[wib][lane] = fcp;
@@ -333,7 +371,22 @@ __device__ __forceinline__ void picard_passes(const KArgs& a, unsigned long long
         }
         if (!grid_sync(a.ctrl, deadline)) { ok = false; break; }
         if (tr && gtid == 0) tr[1] = (long long)(globaltimer_ns() - t_start);
-        if (ld_volatile(&a.ctrl->changed[parity]) == 0) { converged = true; break; }
+        const bool changed = ld_volatile(&a.ctrl->changed[parity]) != 0;
+        if (!win) {
+            if (!changed) { converged = true; break; }
+            continue;
+        }
+        // the window: evaluated orders end at e; it restarts at the first change,
+        // or moves past e once it changed nothing (Appendix A.3)
+        const long long e = min((long long)a.T, (long long)whi * a.L);
+        if (!changed) {
+            if (e >= a.T) { converged = true; break; }
+            wstart = e;
+        } else {
+            wstart = ld_volatile(&a.ctrl->win_fct[parity]);
+        }
+        wprev = whi;
+        whi = (int)min((long long)a.M, (wstart + a.win_steps + a.L - 1) / a.L);
     }
     if (lane == 0 && replays) {
         atomicAdd(&a.ctrl->policy_calls, calls);

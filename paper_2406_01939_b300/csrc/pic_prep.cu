@@ -218,6 +218,14 @@ __global__ void k_runs(const int32_t* __restrict__ flag, const int32_t* __restri
     }
 }
 
+// Time block of each run (single instances): the chunk of its first order.
+__global__ void k_run_chunk(const int32_t* __restrict__ run_start, const int32_t* __restrict__ perm,
+                            int L, const Ctrl* ctrl, int T, int32_t* __restrict__ run_chunk) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= T || r >= ctrl->nruns) return;
+    run_chunk[r] = perm[run_start[r]] / L;
+}
+
 __global__ void k_seg_flags(const int32_t* __restrict__ run_start, const int32_t* __restrict__ prod_s,
                             const int32_t* __restrict__ pstart, int W, int T, const Ctrl* ctrl,
                             int32_t* __restrict__ flag) {
@@ -413,6 +421,11 @@ cudaError_t build_tables(Instance* I, int M, int W, cudaStream_t st) {
                                                   bt ? bt->chunk_len : nullptr, I->tmp_a);
     if ((e = scan_exclusive(I->tmp_a, I->tmp_b, T, nullptr, I->scan_blk, st))) return e;
     k_runs<<<nblocks(T, 256), 256, 0, st>>>(I->tmp_a, I->tmp_b, T, I->run_of, I->run_start, I->ctrl);
+    if (!bt) {  // time block of each run (the max_steps window)
+        k_run_chunk<<<nblocks(T, 256), 256, 0, st>>>(I->run_start, I->perm, (int)L, I->ctrl, T,
+                                                     I->run_chunk);
+        I->launches += 1;
+    }
     // 4. segments (window W per product) and chains
     k_seg_flags<<<nblocks(T, 256), 256, 0, st>>>(I->run_start, I->prod_s, I->pstart, W, T, I->ctrl,
                                                   I->tmp_a);

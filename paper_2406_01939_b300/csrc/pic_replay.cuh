@@ -44,7 +44,11 @@ __device__ __forceinline__ bool replay_segment(const KArgs& a, const CostTable<S
     int run_end = lane < m.r1 - rwin ? a.run_start[rwin + 1 + lane] : INT_MAX;
     int r = m.r0;
     int next_run = __shfl_sync(kFull, run_end, 0);
-    bool eval = j0 > fcp;  // this run's prefix changed in the previous pass
+    // the max_steps window of this pass (none: INT_MAX)
+    const int whi = a.run_chunk ? ld_volatile(&a.ctrl->win_hi) : INT_MAX;
+    const int wprev = a.run_chunk ? ld_volatile(&a.ctrl->win_hi_prev) : INT_MAX;
+    // this run's prefix changed in the previous pass (or it entered the window)
+    bool eval = run_evaluated(a, whi, wprev, r, j0 > fcp);
     unsigned long long evals = eval ? (unsigned long long)(next_run - j0) : 0ull;
 #pragma unroll
     for (int i = 0; i < NPL; ++i) {
@@ -83,7 +87,7 @@ __device__ __forceinline__ bool replay_segment(const KArgs& a, const CostTable<S
                     run_end = lane < m.r1 - rwin ? a.run_start[rwin + 1 + lane] : INT_MAX;
                 }
                 const int nr = __shfl_sync(kFull, run_end, idx);
-                eval = next_run > fcp;
+                eval = run_evaluated(a, whi, wprev, r, next_run > fcp);
                 if (eval) evals += (unsigned long long)(nr - next_run);
                 next_run = nr;
             }
@@ -127,6 +131,7 @@ __device__ __forceinline__ bool replay_segment(const KArgs& a, const CostTable<S
         // the atomic so that only a new minimum contends for the word
         if (first_chg != INT_MAX && first_chg < ld_volatile(&fc_cur[k]))
             atomicMin(&fc_cur[k], first_chg);
+        report_window_change(a, it, first_chg);
     }
     if (s == m.ce - 1) {  // last segment of the product: its end state is the final stock
 #pragma unroll

@@ -71,7 +71,7 @@ class DeviceInstance:
 
     def simulate(self, policy, mode="picard", num_chunks=0, max_iters=0, flags=0, alpha_init=None,
                  timeout_ns=0, seg_window=0, want_stock=True, raise_on_error=True, out=None,
-                 trace=None):
+                 trace=None, max_steps=0):
         i = self.inst
         dp = policy if isinstance(policy, DevicePolicy) else DevicePolicy(policy, self.device)
         act = out if out is not None else torch.empty(i.T, dtype=torch.int8, device=self.device)
@@ -81,7 +81,7 @@ class DeviceInstance:
             ai = torch.as_tensor(np.ascontiguousarray(alpha_init, dtype=np.int8)).to(self.device) \
                 if not torch.is_tensor(alpha_init) else alpha_init
         opts = make_opts(mode, num_chunks, max_iters, flags, ai, timeout_ns, PIC_MEM_DEVICE,
-                         seg_window, self.stream, trace)
+                         seg_window, self.stream, trace, max_steps)
         st, res = pic_simulate(self.handle, dp.struct, opts, act, stock, raise_on_error)
         return {"status": st, "actions": act, "final_stock": stock, "total_cost": res.total_cost,
                 "lost": res.lost, "iters": res.iters, "policy_calls": res.policy_calls,
@@ -139,7 +139,7 @@ class DeviceBatch:
 
     def simulate(self, policies, mode="picard", num_chunks=0, max_iters=0, flags=0, alpha_init=None,
                  timeout_ns=0, seg_window=0, want_stock=True, raise_on_error=True, out=None,
-                 trace=None, out_mem=PIC_MEM_DEVICE):
+                 trace=None, out_mem=PIC_MEM_DEVICE, max_steps=0):
         """policies: list of synth.Policy or DevicePolicy, one per trajectory (MLP
         kinds must share one parameter set: pass the same DevicePolicy object or
         Policies holding the same MLPParams object)."""
@@ -175,7 +175,7 @@ class DeviceBatch:
             ai = alpha_init if torch.is_tensor(alpha_init) else \
                 torch.as_tensor(np.ascontiguousarray(alpha_init, dtype=np.int8)).to(self.device)
         opts = make_opts(mode, num_chunks, max_iters, flags, ai, timeout_ns, out_mem, seg_window,
-                         self.stream, trace)
+                         self.stream, trace, max_steps)
         st, res, traj = pic_simulate_batch(self.handle, [d.struct for d in dps], opts, act, stock,
                                            raise_on_error)
         return {"status": st, "actions": act, "final_stock": stock, "total_cost": res.total_cost,

@@ -92,9 +92,11 @@ def parse():
     return p.parse_args()
 
 
-DEFAULT_MAX_STEPS = {"mlp_medium": 0}
+# mlp_medium: the window of App. A.3 (16,384 orders = 4 chunks), short segments
+DEFAULT_MAX_STEPS = {"mlp_medium": 16384}
+DEFAULT_SEG_WINDOW = {"mlp_medium": 4}
 
-DEFAULT_CHUNKS = {"dual_large": 4096, "mlp_medium": 1024, "batch_uneven": 0, "pg_large": 0,
+DEFAULT_CHUNKS = {"dual_large": 4096, "mlp_medium": 4096, "batch_uneven": 0, "pg_large": 0,
                   "capacity_large": 16384}
 
 # FP32 CUDA-core peak of the MLP scorer's arithmetic: 148 SMs x 128 FP32 lanes x
@@ -656,6 +658,8 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     max_steps = args.max_steps if args.max_steps >= 0 else DEFAULT_MAX_STEPS.get(args.workload, 0)
+    if not args.seg_window:
+        args.seg_window = DEFAULT_SEG_WINDOW.get(args.workload, 0)
 
     def step(out):
         return di.simulate(pol, "picard", num_chunks=chunks_of(args), seg_window=args.seg_window,
@@ -708,9 +712,11 @@ def main():
     if args.seq_steps > 0:
         seq_act = torch.empty(T, dtype=torch.int8, device=dev)
         seq_ms = []
+        # the MLP's fastest sequential simulator shares each decision between four warps
+        seq_flags = pic.PIC_FLAG_TIMING | (pic.PIC_FLAG_WARP_GROUP if args.workload == "mlp_medium"
+                                           else 0)
         for i in range(args.seq_steps + 1):
-            r = di.simulate(pol, "sequential", flags=pic.PIC_FLAG_TIMING, want_stock=False,
-                            out=seq_act)
+            r = di.simulate(pol, "sequential", flags=seq_flags, want_stock=False, out=seq_act)
             if i:
                 seq_ms.append(r["total_ms"])
             seq_res = r

@@ -85,6 +85,12 @@ enum {
                                   max(1e-3, twice a computed error bound); same results as the
                                   FP32 scorer.  With num_chunks = 0 the batch autotuner
                                   decides unless one of the two flags is given */
+    PIC_FLAG_WARP_GROUP = 256, /* MLP policies with N <= 64, pic_simulate: four warps share
+                                  each decision (two hidden units per thread, the layer-2
+                                  chains split in two halves), which shortens the decisions
+                                  on a pass's critical path; same operations in the same
+                                  order, so the same actions; no tensor-core tiles.  Applies
+                                  to the sequential mode as well */
     PIC_FLAG_NO_SAT = 128      /* MLP policies: evaluate the network for every decision.  By
                                   default a decision whose product holds at least 32 units at
                                   every warehouse (every stock feature min(x,32)/32 equals 1)

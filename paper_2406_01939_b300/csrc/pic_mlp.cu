@@ -125,19 +125,24 @@ __global__ void __launch_bounds__(32 * kSatWarps) k_mlp_sat(MlpPolicy p, int R, 
 }
 
 // ---------------------------------------------------------------- sequential simulator
-template <int NPL, bool SMEMW>
-__global__ void __launch_bounds__(32) k_seq_mlp(int T, int N, const int32_t* __restrict__ prod,
-                                                const int32_t* __restrict__ reg, int32_t* xw,
-                                                int8_t* __restrict__ act_t, MlpPolicy p, Ctrl* ctrl) {
-    __shared__ float fs[128];
+template <int NPL, bool SMEMW, int GROUP = 1>
+__global__ void __launch_bounds__(32 * GROUP) k_seq_mlp(int T, int N, const int32_t* __restrict__ prod,
+                                                        const int32_t* __restrict__ reg, int32_t* xw,
+                                                        int8_t* __restrict__ act_t, MlpPolicy p,
+                                                        Ctrl* ctrl) {
+    __shared__ float fs[GROUP][128];
     __shared__ __align__(16) float hs[kHidden];
+    __shared__ float ht[GROUP > 1 ? 128 : 1];
+    __shared__ uint4 am[2];
     extern __shared__ uint4 s_w[];
     if (SMEMW) stage_weights(p, s_w);
     const uint4* W1p = SMEMW ? s_w : p.W1p;
     const uint4* W2p = SMEMW ? s_w + p.N * kHidden / 8 : p.W2p;
+    const int w = threadIdx.x >> 5;
+    const Group G{w, 1, hs, ht, am};
     unsigned long long nsat = 0;
-    seq_mlp_body<NPL, SMEMW>(T, N, prod, reg, xw, act_t, p, W1p, W2p, fs, hs, nsat);
-    if (lane_id() == 0) {
+    seq_mlp_body<NPL, SMEMW, GROUP>(T, N, prod, reg, xw, act_t, p, W1p, W2p, fs[w], hs, nsat, &G);
+    if (threadIdx.x == 0) {
         ctrl->iters = 1;
         ctrl->converged = 1;
         ctrl->policy_calls = (unsigned long long)T;
@@ -147,26 +152,33 @@ __global__ void __launch_bounds__(32) k_seq_mlp(int T, int N, const int32_t* __r
 
 constexpr int kMlpThreads = 256;
 
-template <int NPL, bool SMEMW, bool SPEC>
+// GROUP = 4: four warps per segment, sharing each decision (N <= 64, no tiles).
+template <int NPL, bool SMEMW, bool SPEC, int GROUP = 1>
 __global__ void __launch_bounds__(kMlpThreads, 2) k_picard_mlp(KArgs a, MlpPolicy p,
                                                               const int32_t* __restrict__ perm) {
+    constexpr int kWarps = kMlpThreads / 32;
+    constexpr int kGroups = kWarps / GROUP;
     extern __shared__ uint4 s_w[];
-    __shared__ float s_fs[kMlpThreads / 32][128];
-    __shared__ __align__(16) float s_hs[kMlpThreads / 32][kHidden];
+    __shared__ float s_fs[kWarps][128];
+    __shared__ __align__(16) float s_hs[GROUP > 1 ? kGroups : kWarps][kHidden];
+    __shared__ float s_ht[kGroups][GROUP > 1 ? 128 : 1];
+    __shared__ uint4 s_am[kGroups][2];
     if (SMEMW) stage_weights(p, s_w);
     const uint4* W1p = SMEMW ? s_w : p.W1p;
     const uint4* W2p = SMEMW ? s_w + p.N * kHidden / 8 : p.W2p;
     const int wib = threadIdx.x >> 5;
+    const int grp = wib / GROUP;
+    const Group G{wib % GROUP, 1 + grp, s_hs[GROUP > 1 ? grp : wib], s_ht[grp], s_am[grp]};
     unsigned long long calls = 0;
     MlpCounts mc{0, 0, 0, 0};
-    picard_passes<NPL, kMlpThreads / 32>(
-        a, calls, [&](int seg, const SegMeta& m, int fcp, int* fc_cur, int it) {
-            const unsigned long long c0 = mc.calls;
-            const bool chg = replay_segment_mlp<NPL, SMEMW, SPEC>(a, p, W1p, W2p, perm, seg, m, fcp, fc_cur,
-                                                            it, 0, mc, s_fs[wib], s_hs[wib]);
-            calls += mc.calls - c0;
-            return chg;
-        });
+    auto replay = [&](int seg, const SegMeta& m, int fcp, int* fc_cur, int it) {
+        const unsigned long long c0 = mc.calls;
+        const bool chg = replay_segment_mlp<NPL, SMEMW, SPEC, GROUP>(
+            a, p, W1p, W2p, perm, seg, m, fcp, fc_cur, it, 0, mc, s_fs[wib], G.hs, &G);
+        calls += mc.calls - c0;
+        return chg;
+    };
+    picard_passes<NPL, kWarps, decltype(replay)&, GROUP>(a, calls, replay);
     if (lane_id() == 0 && (mc.rescored || mc.tc || mc.sat)) {
         atomicAdd(&a.ctrl->rescored, mc.rescored);
         atomicAdd(&a.ctrl->tc_rows, mc.tc);
@@ -174,9 +186,9 @@ __global__ void __launch_bounds__(kMlpThreads, 2) k_picard_mlp(KArgs a, MlpPolic
     }
 }
 
-template <int NPL, bool SMEMW, bool SPEC>
+template <int NPL, bool SMEMW, bool SPEC, int GROUP = 1>
 cudaError_t launch_picard_mlp(Instance* I, const KArgs& a, const MlpPolicy& p, cudaStream_t st) {
-    auto kern = k_picard_mlp<NPL, SMEMW, SPEC>;
+    auto kern = k_picard_mlp<NPL, SMEMW, SPEC, GROUP>;
     const size_t smem = SMEMW ? packed_weight_bytes(I->N) : 0;
     cudaError_t e;
     if (SMEMW && (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
@@ -197,15 +209,15 @@ cudaError_t launch_picard_mlp(Instance* I, const KArgs& a, const MlpPolicy& p, c
     return cudaLaunchCooperativeKernel((const void*)kern, grid, kMlpThreads, params, smem, st);
 }
 
-template <int NPL, bool SMEMW>
+template <int NPL, bool SMEMW, int GROUP = 1>
 cudaError_t launch_seq_mlp(Instance* I, const MlpPolicy& p, cudaStream_t st) {
-    auto kern = k_seq_mlp<NPL, SMEMW>;
+    auto kern = k_seq_mlp<NPL, SMEMW, GROUP>;
     const size_t smem = SMEMW ? packed_weight_bytes(I->N) : 0;
     cudaError_t e;
     if (SMEMW && (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
         return e;
     I->launches += 1;
-    kern<<<1, 32, smem, st>>>(I->T, I->N, I->prod, I->reg, I->xwork, I->act_t, p, I->ctrl);
+    kern<<<1, 32 * GROUP, smem, st>>>(I->T, I->N, I->prod, I->reg, I->xwork, I->act_t, p, I->ctrl);
     return cudaGetLastError();
 }
 
@@ -254,6 +266,8 @@ cudaError_t sequential_mlp(Instance* I, const pic_policy* pol, int flags, cudaSt
     const MlpPolicy p = make_policy_view(I, pol, flags);
     const int npl = (I->N + 31) / 32;
     const bool sw = smem_weights_ok(I->N);
+    if ((flags & PIC_FLAG_WARP_GROUP) && npl <= 2)  // four warps per decision
+        return npl == 1 ? launch_seq_mlp<1, true, 4>(I, p, st) : launch_seq_mlp<2, true, 4>(I, p, st);
     if (npl == 1) return sw ? launch_seq_mlp<1, true>(I, p, st) : launch_seq_mlp<1, false>(I, p, st);
     if (npl == 2) return sw ? launch_seq_mlp<2, true>(I, p, st) : launch_seq_mlp<2, false>(I, p, st);
     return sw ? launch_seq_mlp<4, true>(I, p, st) : launch_seq_mlp<4, false>(I, p, st);
@@ -264,6 +278,9 @@ cudaError_t picard_mlp(Instance* I, const KArgs& a, const pic_policy* pol, cudaS
     // the packed weights fit in shared memory for every N <= 127; tiles need N <= 64
     const bool tc = (a.flags & PIC_FLAG_NO_TC) == 0 && I->N <= 64;
     const int npl = (I->N + 31) / 32;
+    if ((a.flags & PIC_FLAG_WARP_GROUP) && npl <= 2)  // four warps per decision, no tiles
+        return npl == 1 ? launch_picard_mlp<1, true, false, 4>(I, a, p, st)
+                        : launch_picard_mlp<2, true, false, 4>(I, a, p, st);
     if (npl == 1) return tc ? launch_picard_mlp<1, true, true>(I, a, p, st) : launch_picard_mlp<1, true, false>(I, a, p, st);
     if (npl == 2) return tc ? launch_picard_mlp<2, true, true>(I, a, p, st) : launch_picard_mlp<2, true, false>(I, a, p, st);
     return launch_picard_mlp<4, true, false>(I, a, p, st);

@@ -272,6 +272,137 @@ __device__ __forceinline__ int mlp_decide(const MlpPolicy& p, const uint4* W1p, 
     return mlp_pick<NPL>(p, S, s, t);
 }
 
+// ---------------------------------------------------------------- four warps per decision
+// A group of four warps (128 threads) shares each decision, which shortens the
+// latency of one decision (the critical path of a pass whose work is a few long
+// runs).  The operations and their order are mlp_scores' exactly:
+//   layer 1: thread (warp g, lane l) runs the 64-step chains of hidden units
+//            l + 32 g and l + 32 g + 128 (units u = g and u = g + 4 of lane l);
+//   layer 2: thread (g, l) owns output n = l + 32 (g & 1) and the four chains
+//            p_e, e = 4 (g >> 1) .. 4 (g >> 1) + 3, and forms their half of the
+//            fixed tree, (p_0+p_1)+(p_2+p_3) or (p_4+p_5)+(p_6+p_7);
+//   warps 0 and 1 add the halves, add b2 (and the Gumbel term) and take their
+//   arg max; every warp combines the two.
+// N <= 64.  Each warp keeps its own copy of the stock row and its own feature
+// scratch; the group shares hs (256 floats), ht (2 x 64) and am (2 entries),
+// and synchronises with one named barrier (id bar, 128 threads) three times.
+struct Group {
+    int g;        // warp index in the group (0..3)
+    int bar;      // named barrier id
+    float* hs;    // [256] hidden activations
+    float* ht;    // [2][64] halves of the layer-2 tree
+    uint4* am;    // [2] per-warp arg max: key, index, any
+};
+
+__device__ __forceinline__ void group_sync(int bar) {
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(128) : "memory");
+}
+
+// acc = fma(w, f, acc) for one BF16 weight w and BF16 feature f (exact product,
+// one rounding: fmaf on the widened operands)
+__device__ __forceinline__ float fma1_bf16(float acc, unsigned short w, unsigned short f) {
+    asm("fma.rn.f32.bf16 %0, %1, %2, %0;" : "+f"(acc) : "h"(w), "h"(f));
+    return acc;
+}
+
+template <bool SMEMW>
+__device__ __forceinline__ unsigned wld1(const unsigned* p) {
+    if (SMEMW) return *p;
+    return __ldg(p);
+}
+template <bool SMEMW>
+__device__ __forceinline__ uint2 wld2(const uint2* p) {
+    if (SMEMW) return *p;
+    return __ldg(p);
+}
+
+template <int NPL, bool SMEMW>
+__device__ __forceinline__ int mlp_decide_group(const MlpPolicy& p, const uint4* W1p,
+                                                const uint4* W2p, const int S[NPL], int r, int t,
+                                                float* fs, const Group& G,
+                                                unsigned long long& nsat) {
+    static_assert(NPL <= 2, "four-warp decisions need N <= 64");
+    const int lane = lane_id();
+    const int N = p.N, g = G.g;
+    bool sat = p.sat != nullptr;
+#pragma unroll
+    for (int i = 0; i < NPL; ++i)
+        if (lane + 32 * i < N) sat &= S[i] >= 32;
+    if (__all_sync(kFull, sat)) {  // the same branch in every warp of the group
+        float s[NPL];
+#pragma unroll
+        for (int i = 0; i < NPL; ++i) {
+            const int n = lane + 32 * i;
+            s[i] = n < N ? __ldg(p.sat + (size_t)r * N + n) : 0.0f;
+        }
+        if (lane == 0 && g == 0) ++nsat;
+        return mlp_pick<NPL>(p, S, s, t);
+    }
+#pragma unroll
+    for (int i = 0; i < NPL; ++i) {
+        const int n = lane + 32 * i;
+        if (n < N) fs[n] = __fdiv_rn((float)min(S[i], 32), 32.0f);
+    }
+    __syncwarp();
+    // layer 1: units j0 = lane + 32 g (word g >> 1 of W1p, half g & 1) and j1 = j0 + 128
+    // (word 2 + (g >> 1))
+    float a0 = __ldg(p.P + (size_t)r * kHidden + lane + 32 * g);
+    float a1 = __ldg(p.P + (size_t)r * kHidden + lane + 32 * g + 128);
+    const unsigned* W1w = reinterpret_cast<const unsigned*>(W1p) + 4 * lane + (g >> 1);
+    const int sh = (g & 1) * 16;
+#pragma unroll 4
+    for (int n = 0; n < N; ++n) {
+        const unsigned short f = bf16_bits(fs[n]);
+        const unsigned u0 = wld1<SMEMW>(W1w + (size_t)n * 128);
+        const unsigned u1 = wld1<SMEMW>(W1w + (size_t)n * 128 + 2);
+        a0 = fma1_bf16(a0, (unsigned short)(u0 >> sh), f);
+        a1 = fma1_bf16(a1, (unsigned short)(u1 >> sh), f);
+    }
+    G.hs[lane + 32 * g] = a0 > 0.0f ? a0 : 0.0f;
+    G.hs[lane + 32 * g + 128] = a1 > 0.0f ? a1 : 0.0f;
+    group_sync(G.bar);
+    // layer 2: output n, chains 4 hf .. 4 hf + 3 (half hf of each packed uint4)
+    const int n = lane + 32 * (g & 1), hf = g >> 1;
+    if (n < N) {
+        const uint2* W2h = reinterpret_cast<const uint2*>(W2p) + 2 * n + hf;
+        const float4* h4 = reinterpret_cast<const float4*>(G.hs) + hf;
+        float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll 4
+        for (int q = 0; q < kHidden / 8; ++q) {
+            const uint2 w = wld2<SMEMW>(W2h + (size_t)2 * q * N);
+            const float4 h = h4[2 * q];
+            p0 = fmaf(lo16(w.x), h.x, p0);
+            p1 = fmaf(hi16(w.x), h.y, p1);
+            p2 = fmaf(lo16(w.y), h.z, p2);
+            p3 = fmaf(hi16(w.y), h.w, p3);
+        }
+        G.ht[hf * 64 + n] = __fadd_rn(__fadd_rn(p0, p1), __fadd_rn(p2, p3));
+    }
+    group_sync(G.bar);
+    if (hf == 0) {  // warps 0 and 1: outputs 0..31 and 32..63
+        const int Sn = (NPL > 1 && (g & 1)) ? S[NPL - 1] : S[0];
+        unsigned key = 0;
+        bool any = false;
+        if (n < N && Sn > 0) {
+            const float v = __fadd_rn(G.ht[n], G.ht[64 + n]);
+            float s = __fadd_rn(__ldg(p.b2f + n), v);
+            if (p.gumbel) s = __fadd_rn(s, gumbel1(p.seed, p.traj, t, n));
+            key = ord_key(s);
+            any = true;
+        }
+        const unsigned kmax = __reduce_max_sync(kFull, any ? key : 0u);
+        const bool wany = __any_sync(kFull, any);
+        const int nmin = __reduce_min_sync(kFull, (any && key == kmax) ? n : INT_MAX);
+        if (lane == 0) G.am[g] = make_uint4(kmax, (unsigned)nmin, wany ? 1u : 0u, 0u);
+    }
+    group_sync(G.bar);
+    const uint4 m0 = G.am[0], m1 = G.am[1];
+    if (!m0.z && !m1.z) return -1;
+    if (!m0.z) return (int)m1.y;
+    if (!m1.z) return (int)m0.y;
+    return m1.x > m0.x ? (int)m1.y : (int)m0.y;  // ties to the lower index (warp 0's)
+}
+
 // ---------------------------------------------------------------- speculative tensor-core tiles
 // Inside one run the stock features min(x[k][n], 32)/32 stay the same from order
 // to order until a decrement takes some warehouse below 32 units.  For the next
@@ -467,13 +598,18 @@ __device__ __forceinline__ void stage_weights(const MlpPolicy& p, uint4* sw) {
 
 // Sequential simulation on one warp: orders strictly one at a time (time t
 // counts from 0 within prod/reg/act_t).
-template <int NPL, bool SMEMW>
+// GROUP = 4: the four warps of a group run the loop together and share each
+// decision (mlp_decide_group); every warp keeps the stock rows current (the
+// same value written by each), warp 0 of the group writes the actions.
+template <int NPL, bool SMEMW, int GROUP = 1>
 __device__ __forceinline__ void seq_mlp_body(int T, int N, const int32_t* __restrict__ prod,
                                              const int32_t* __restrict__ reg, int32_t* xw,
                                              int8_t* __restrict__ act_t, const MlpPolicy& p,
                                              const uint4* W1p, const uint4* W2p, float* fs,
-                                             float* hs, unsigned long long& nsat) {
+                                             float* hs, unsigned long long& nsat,
+                                             const Group* G = nullptr) {
     const int lane = lane_id();
+    const bool lead = GROUP == 1 || G->g == 0;
     int my_act = -1;
     for (int t = 0; t < T; ++t) {
         const int k = __ldg(prod + t), r = __ldg(reg + t);
@@ -483,12 +619,20 @@ __device__ __forceinline__ void seq_mlp_body(int T, int N, const int32_t* __rest
             const int n = lane + 32 * i;
             S[i] = n < N ? xw[(size_t)k * N + n] : 0;
         }
-        const int act = mlp_decide<NPL, SMEMW>(p, W1p, W2p, S, r, t, fs, hs, nsat);
+        int act;
+        if constexpr (GROUP > 1) {
+            act = mlp_decide_group<NPL, SMEMW>(p, W1p, W2p, S, r, t, fs, *G, nsat);
+            // every warp has read this order's stock row before it is decremented (a
+            // table decision has no other barrier)
+            group_sync(G->bar);
+        } else {
+            act = mlp_decide<NPL, SMEMW>(p, W1p, W2p, S, r, t, fs, hs, nsat);
+        }
 #pragma unroll
         for (int i = 0; i < NPL; ++i)
             if (act == lane + 32 * i) xw[(size_t)k * N + act] = S[i] - 1;
         if (lane == (t & 31)) my_act = act;
-        if ((t & 31) == 31 || t == T - 1) {
+        if (lead && ((t & 31) == 31 || t == T - 1)) {
             const int tw = (t & ~31) + lane;
             if (tw < T) act_t[tw] = (int8_t)my_act;
         }
@@ -497,11 +641,17 @@ __device__ __forceinline__ void seq_mlp_body(int T, int N, const int32_t* __rest
 }
 
 // ---------------------------------------------------------------- Picard, one warp per segment
-template <int NPL, bool SMEMW, bool SPEC>
+// GROUP = 4: the four warps of a group replay the segment together, sharing
+// each decision (mlp_decide_group; no tensor-core tiles); warp 0 of the group
+// writes the cache, the histogram, the final stock and the counters.
+template <int NPL, bool SMEMW, bool SPEC, int GROUP = 1>
 __device__ bool replay_segment_mlp(const KArgs& a, const MlpPolicy& p, const uint4* W1p,
                                    const uint4* W2p, const int32_t* __restrict__ perm, int s,
                                    const SegMeta& m, int fcp, int* fc_cur, int it, int t_off,
-                                   MlpCounts& cnt_out, float* fs, float* hs) {
+                                   MlpCounts& cnt_out, float* fs, float* hs,
+                                   const Group* G = nullptr) {
+    static_assert(GROUP == 1 || !SPEC, "tiles are per warp");
+    const bool lead = GROUP == 1 || G->g == 0;
     const int lane = lane_id();
     const int N = a.N, NP = a.NP;
     const int k = m.k;
@@ -579,7 +729,10 @@ __device__ bool replay_segment_mlp(const KArgs& a, const MlpPolicy& p, const uin
                     --spec_left;
                 }
                 if (sa < -1) {
-                    act = mlp_decide<NPL, SMEMW>(p, W1p, W2p, S, rr, tt, fs, hs, nsat);
+                    if constexpr (GROUP > 1)
+                        act = mlp_decide_group<NPL, SMEMW>(p, W1p, W2p, S, rr, tt, fs, *G, nsat);
+                    else
+                        act = mlp_decide<NPL, SMEMW>(p, W1p, W2p, S, rr, tt, fs, hs, nsat);
                     resc += sa == -2;
                 } else {
                     act = sa;
@@ -602,26 +755,29 @@ __device__ bool replay_segment_mlp(const KArgs& a, const MlpPolicy& p, const uin
             }
             if (lane == q) my_new = act;
         }
-        if (lane < cnt) a.alpha_s[base + lane] = (int8_t)my_new;
+        // every warp of a group has read this batch's cached actions before they
+        // are overwritten (a batch without decisions has no other barrier)
+        if constexpr (GROUP > 1) group_sync(G->bar);
+        if (lead && lane < cnt) a.alpha_s[base + lane] = (int8_t)my_new;
         const unsigned chg = __ballot_sync(kFull, lane < cnt && my_new != my_old);
         if (chg && first_chg == INT_MAX) first_chg = base + __ffs(chg) - 1;
     }
 #pragma unroll
     for (int i = 0; i < NPL; ++i) {
         hist[i] += S0[i] - S[i];
-        a.agg[(size_t)s * NP + lane + 32 * i] = hist[i];
+        if (lead) a.agg[(size_t)s * NP + lane + 32 * i] = hist[i];
     }
-    if (lane == 0 && first_chg != INT_MAX && first_chg < ld_volatile(&fc_cur[k]))
+    if (lead && lane == 0 && first_chg != INT_MAX && first_chg < ld_volatile(&fc_cur[k]))
         atomicMin(&fc_cur[k], first_chg);
-    if (lane == 0) report_window_change(a, it, first_chg);
-    if (s == m.ce - 1) {
+    if (lead && lane == 0) report_window_change(a, it, first_chg);
+    if (lead && s == m.ce - 1) {
 #pragma unroll
         for (int i = 0; i < NPL; ++i) {
             const int n = lane + 32 * i;
             if (n < N) a.xfin[(size_t)k * N + n] = S[i];
         }
     }
-    if (lane == 0) {
+    if (lead && lane == 0) {
         cnt_out.calls += evals;
         cnt_out.rescored += resc;
         cnt_out.tc += tcr;

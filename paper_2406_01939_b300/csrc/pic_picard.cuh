@@ -279,7 +279,10 @@ __device__ __forceinline__ void chain_prefixes(const KArgs& a, int it, const int
 //            policy calls to `calls` on lane 0);
 // separated by grid barriers.  The loop ends at the first pass that changes no
 // cached action (line 13 of Algorithm 1), or after max_iters passes.
-template <int NPL, int WARPS, class Replay>
+// GROUP > 1: work units go to groups of GROUP consecutive warps of a CTA (each
+// warp of a group walks the same candidates and calls replay for the same
+// segment; the replay shares its decisions); the group's first warp counts.
+template <int NPL, int WARPS, class Replay, int GROUP = 1>
 __device__ __forceinline__ void picard_passes(const KArgs& a, unsigned long long& calls,
                                               Replay&& replay) {
     __shared__ int s_changed;
@@ -329,9 +332,10 @@ __device__ __forceinline__ void picard_passes(const KArgs& a, unsigned long long
         if (tr && gtid == 0) tr[0] = (long long)(globaltimer_ns() - t_start);
         // ---- phase R
         bool chg = false;
-        for (int j0 = 0; j0 * nwarps < nseg; j0 += 32) {
+        const int unit = gwarp / GROUP, nunits = nwarps / GROUP;
+        for (int j0 = 0; j0 * nunits < nseg; j0 += 32) {
             const int j = j0 + lane;
-            const int pos = j * nwarps + ((j & 1) ? nwarps - 1 - gwarp : gwarp);
+            const int pos = j * nunits + ((j & 1) ? nunits - 1 - unit : unit);
             int sl = nseg;
             bool act = false;
             if (pos < nseg) {
@@ -355,7 +359,7 @@ __device__ __forceinline__ void picard_passes(const KArgs& a, unsigned long long
                 const SegMeta mm = smem_meta(&s_meta[wib][src]);
                 const int seg = __shfl_sync(kFull, sl, src);
                 chg |= replay(seg, mm, s_fcp[wib][src], fc_cur, it);
-                replays += 1;
+                if (wib % GROUP == 0) replays += 1;
             }
             __syncwarp();
         }

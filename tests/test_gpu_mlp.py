@@ -164,3 +164,34 @@ def test_saturated_state_table_exact(N):
                     assert got["sat_decisions"] == 0
                 else:
                     assert 0 < got["sat_decisions"] < got["policy_calls"]
+
+
+@pytest.mark.parametrize("N", [8, 33, 64, 100])
+def test_four_warp_decisions_bit_exact(N):
+    """PIC_FLAG_WARP_GROUP: four warps share each decision (same operations in
+    the same order).  Sequential and Picard paths, with and without the window
+    and the saturated-state table, equal the oracle; N > 64 falls back to one
+    warp per decision."""
+    inst, mlp = small(5 * N, 3000, N, 14, 9, fill=0.9)
+    x0 = inst.x0.copy()
+    x0[:3] += 40  # a few products saturated for a while (table decisions)
+    inst.x0 = x0
+    d = DeviceInstance(inst)
+    G = pic.PIC_FLAG_WARP_GROUP
+    for pol in policies(mlp, N):
+        want = oracle.seq_sim(inst, pol)
+        got = d.simulate(pol, "sequential", flags=G)
+        np.testing.assert_array_equal(got["actions"].cpu().numpy(), want["actions"])
+        np.testing.assert_array_equal(got["final_stock"].cpu().numpy(), want["x_final"])
+        for M, ms in ((30, 0), (100, 0), (100, 300)):
+            for flags in (G, G | pic.PIC_FLAG_NO_SAT):
+                ref = (oracle.picard_windowed(inst, pol, M, ms) if ms else
+                       oracle.picard_chunked(inst, pol, M))
+                got = d.simulate(pol, "picard", num_chunks=M, max_steps=ms, flags=flags)
+                np.testing.assert_array_equal(got["actions"].cpu().numpy(), want["actions"])
+                np.testing.assert_array_equal(got["final_stock"].cpu().numpy(), want["x_final"])
+                assert got["iters"] == ref["iters"] and got["total_cost"] == want["total_cost"]
+        rec = oracle.picard_chunked(inst, pol, 30, record=True)
+        for k in (1, 3):
+            g = d.simulate(pol, "picard", num_chunks=30, max_iters=k, flags=G, raise_on_error=False)
+            np.testing.assert_array_equal(g["actions"].cpu().numpy(), rec["iterates"][k - 1])

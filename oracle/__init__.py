@@ -32,12 +32,15 @@ OK, ERR_ARG, ERR_NOT_CONVERGED = 0, 1, 4
 
 
 def build(force: bool = False) -> str:
-    """Compile fo_oracle.c with gcc (IEEE FP32, no contraction)."""
+    """Compile fo_oracle.c (and the OWMR oracle, owmr_oracle.c) with gcc (IEEE
+    FP32, no contraction)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c99",
                                "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
+    from . import owmr
+    owmr.build(force)
     return _LIB
 
 

@@ -25,6 +25,14 @@ Named workloads (sizes as the benchmark and tests use them):
                   pro rata to log-normal(0, 0.5) node weights (Sec. 3 model).
 Product demand is a finite Zipf(1.1): p_k proportional to (k+1)^-1.1, product 0
 the most popular; regions are uniform.
+
+OWMR inventory control (Appendix B): one central warehouse, N retailers.
+  owmr_base       one year of one product selling about 10,000 units a day over
+                  4,000 stores (Appendix B.3): T = 3,650,000 unit demands, store
+                  n drawn with weight (1 - a)^n (a = 0: uniform), stores reorder
+                  at 10 units up to 20 (capacity 24), central (s, S) =
+                  (1,000, 71,000), about one central replenishment a week;
+                  two-hidden-layer network of width 512, BF16 N(0, 0.02).
 """
 from __future__ import annotations
 
@@ -203,3 +211,84 @@ def pg_large(seed=0, B=64, T=1 << 20, N=64, K=10_000, R=1_000):
     insts = [make_instance(T, N, K, R, seed=seed * 1_000_003 + b + 1, stock="poisson",
                            shared_tables=(cost, None)) for b in range(B)]
     return insts, mlp
+
+
+# --------------------------------------------------------------------------- OWMR
+@dataclass
+class OwmrInstance:
+    """One OWMR trajectory's inputs (host numpy arrays, C-contiguous)."""
+
+    T: int
+    N: int
+    ret: np.ndarray  # int32 [T] retailer n(w_t) of step t
+    dem: np.ndarray  # int32 [T] demand d(w_t) >= 0
+    cap: np.ndarray  # int32 [N] retailer capacity c_n
+    x0r: np.ndarray  # int32 [N] initial retailer inventory
+    sl: np.ndarray  # int32 [N] retailer reorder point s_n
+    Sl: np.ndarray  # int32 [N] retailer order-up-to level S_n <= c_n
+    X0: int  # initial central inventory
+    s: int  # central reorder point
+    S: int  # central order-up-to level
+
+
+@dataclass
+class OwmrNet:
+    """Two-hidden-layer network (2 -> H -> H -> 1), BF16 bit patterns (uint16);
+    weight matrices input-major: W1 [2, H], W2 [H, H] (row = input unit)."""
+
+    H: int
+    W1: np.ndarray
+    b1: np.ndarray
+    W2: np.ndarray
+    b2: np.ndarray
+    w3: np.ndarray
+    b3: np.ndarray
+
+
+def owmr_store_weights(N, a=0.0):
+    """Store-selection probabilities p_n proportional to (1 - a)^n (Appendix B.3
+    ablation; a = 0 is uniform)."""
+    w = (1.0 - a) ** np.arange(N, dtype=np.float64)
+    return w / w.sum()
+
+
+def make_owmr(T, N, seed=0, a=0.0, demand="unit", s_loc=10, S_loc=20, cap=24, s=None, S=None,
+              X0=None, x0r=None):
+    """Seeded OWMR instance: T steps, store of step t drawn with
+    owmr_store_weights(N, a); demand 1 per step ("unit") or U{0..3} ("small");
+    per-store (s_n, S_n, c_n) scalars or arrays; central (s, S) default
+    (1,000, 1,000 + T / 52) so that the central warehouse replenishes about 52
+    times over the horizon."""
+    rng = np.random.Generator(np.random.PCG64(seed + 0x0A3B))
+    p = owmr_store_weights(N, a)
+    ret = rng.choice(N, size=T, p=p).astype(np.int32)
+    if demand == "unit":
+        dem = np.ones(T, np.int32)
+    elif demand == "small":
+        dem = rng.integers(0, 4, size=T).astype(np.int32)
+    else:
+        raise ValueError(demand)
+    full = lambda v: np.ascontiguousarray(np.broadcast_to(np.asarray(v, np.int32), (N,)))
+    capa, sla, Sla = full(cap), full(s_loc), full(S_loc)
+    s = 1_000 if s is None else int(s)
+    S = s + max(1, T // 52) if S is None else int(S)
+    X0 = S if X0 is None else int(X0)
+    x0r = Sla.copy() if x0r is None else full(x0r)
+    return OwmrInstance(T, N, ret, dem, capa, x0r, sla, Sla, X0, s, S)
+
+
+def make_owmr_net(H=512, seed=0, std=0.02) -> OwmrNet:
+    """BF16 N(0, std) parameters drawn in the order W1, b1, W2, b2, w3, b3."""
+    rng = np.random.Generator(np.random.PCG64(seed + 0x0E7))
+    g = lambda *shape: f32_to_bf16(rng.normal(0.0, std, size=shape).astype(np.float32))
+    W1, b1, W2, b2, w3, b3 = g(2, H), g(H), g(H, H), g(H), g(H), g(1)
+    return OwmrNet(H, W1, b1, W2, b2, w3, b3)
+
+
+def owmr_base(seed=0, T=3_650_000, N=4_000, a=0.0, H=512):
+    """Appendix B.3's base case: 10,000 unit demands a day for a year over
+    4,000 stores, stores (s_n, S_n) = (10, 20) with capacity 24, central
+    (s, S) = (1,000, 71,000) (about one replenishment a week), width-512
+    network."""
+    inst = make_owmr(T, N, seed=seed, a=a, s=1_000, S=71_000)
+    return inst, make_owmr_net(H, seed=seed)

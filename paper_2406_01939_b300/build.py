@@ -20,7 +20,7 @@ def sources():
 
 def _deps():
     return sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
-        [os.path.join(INCLUDE, "pic.h")]
+        glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
 def needs_build() -> bool:

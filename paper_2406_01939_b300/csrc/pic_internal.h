@@ -184,6 +184,13 @@ cudaError_t build_tables(Instance* I, int M, int W, cudaStream_t st);
 // instance's histogram scratch); tmp_k / tmp_v are n-element scratch arrays.
 cudaError_t sort_pairs(Instance* I, const int32_t* keys, int n, int max_key, int32_t* keys_out,
                        int32_t* vals_out, int32_t* tmp_k, int32_t* tmp_v, cudaStream_t st);
+// The same LSD radix sort with explicit scratch: hist [sort_hist_len(n)] and
+// scan_blk [scan_blk_len(sort_hist_len(n))] (5 launches per key byte).
+cudaError_t sort_pairs_raw(const int32_t* keys, int n, int max_key, int32_t* keys_out,
+                           int32_t* vals_out, int32_t* tmp_k, int32_t* tmp_v, int32_t* hist,
+                           int32_t* scan_blk, cudaStream_t st);
+int sort_hist_len(int n);
+int scan_blk_len(int n);
 // Longest-first order of the segments by estimated work: length, times
 // mlp_weight for segments of trajectories whose policy (pol, batch only) is an
 // MLP kind.

@@ -1,0 +1,992 @@
+// OWMR inventory control (Appendix B): Picard iteration with the retailer
+// partition, and the sequential baseline, behind include/pic_owmr.h.
+//
+// A pass of Algorithm 1 runs as three phases of one persistent cooperative
+// kernel, separated by grid barriers:
+//   A  tile summaries of the cache alpha^{k-1} (time order),
+//   B  per step t the prefix quantities of the cache before t --
+//        Qc = sum of q,  LR = last step with r = 1,  D = sum of q after LR --
+//      written with the cached action itself as pre[t] = {Qc, D, LR, alpha_t},
+//   C  the walks: processor p (one lane of warp 0) visits only its own steps in
+//      time order.  Between two own steps every step is cached, and the central
+//      inventory only moves by "reset to S" and "subtract q, floor at 0", so
+//        x0(t_b) = max(0, S - D[t_b])                          if LR[t_b] > t_a,
+//                  max(0, x0(t_a + 1) - (Qc[t_b] - Qc[t_a + 1])) otherwise.
+//      Retailer stock lives in shared memory (a retailer belongs to one lane).
+//      With a network, a lane whose step needs a call (memo miss) parks it;
+//      the CTA then evaluates all parked calls as one batched FP32 round.
+// The loop ends after the first pass that changed no cached action.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "pic_device.cuh"
+#include "pic_owmr.h"
+
+using namespace pic;
+
+namespace {
+
+constexpr int kOwThreads = 256;             // 8 warps
+constexpr int kLanes = 32;                  // processors per group (lanes of warp 0)
+constexpr int kCh = 32;                     // steps per lane staged per chunk
+constexpr int kItems = 16;                  // scan items per thread
+constexpr int kTile = kOwThreads * kItems;  // steps per scan tile
+constexpr int kMaxSlots = 4096;             // retailers per group (shared-memory stock)
+constexpr int kMaxH = 512;
+
+// Format the message pic_last_error() returns and pass the status through.
+pic_status fail(pic_status s, const char* fmt, ...) {
+    char msg[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(msg, sizeof(msg), fmt, ap);
+    va_end(ap);
+    return record_error(s, msg);
+}
+
+#define CU(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(e_ == cudaErrorMemoryAllocation ? PIC_ERR_OOM : PIC_ERR_CUDA,   \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                      \
+    } while (0)
+
+// Device control block: pic::Ctrl's barrier and error fields, then per-pass
+// statistics in three rotating slots (slot k % 3 is written in pass k, read
+// after its last barrier, and cleared in pass k + 2 after a barrier).
+struct OwCtrl {
+    Ctrl c;
+    int changed[3];
+    int pad;
+    long long lost[3], shipped[3], R[3];
+    unsigned long long evals, rounds;
+};
+
+struct OwArgs {
+    int T, N, P, B, ngroups, H, X0, s, S, ntiles, max_iters, rp;  // rp = ceil(N / P)
+    long long timeout_ns;
+    const int32_t *cap, *sl, *Sl, *x0r;
+    const int2* rec;        // interleaved [rows][32]: {t, d << 16 | n}, t = -1 pads
+    const int32_t* gbase;   // [ngroups + 1] first row of each group
+    int32_t* act;           // [T] cache, time order
+    int4* pre;              // [T + 1]
+    int4* tsum;             // [ntiles]
+    int2* memo;             // interleaved like rec: {y, q} of the last evaluation
+    int32_t* xfin;          // [N] retailer stock after the last pass's walks
+    OwCtrl* oc;
+    const uint16_t *W1, *b1, *W2, *b2, *w3, *b3;
+};
+
+// ------------------------------------------------------------------ prefix monoid
+// (sq, lr, da): sum of q, last replenishment index (-1 none), sum of q after it
+// (the whole sum when lr = -1).  Combine left then right.
+struct Mono {
+    int sq, lr, da;
+};
+
+__device__ __forceinline__ Mono mono_id() { return {0, -1, 0}; }
+
+__device__ __forceinline__ Mono mono_cat(const Mono& a, const Mono& b) {
+    Mono r;
+    r.sq = a.sq + b.sq;
+    r.lr = b.lr >= 0 ? b.lr : a.lr;
+    r.da = b.lr >= 0 ? b.da : a.da + b.sq;
+    return r;
+}
+
+__device__ __forceinline__ Mono mono_step(const Mono& a, int t, int act) {
+    const int q = act >> 1;
+    Mono r;
+    r.sq = a.sq + q;
+    if (act & 1) {
+        r.lr = t;
+        r.da = 0;
+    } else {
+        r.lr = a.lr;
+        r.da = a.da + q;
+    }
+    return r;
+}
+
+__device__ __forceinline__ Mono shfl_up_mono(const Mono& m, int o) {
+    return {__shfl_up_sync(kFull, m.sq, o), __shfl_up_sync(kFull, m.lr, o),
+            __shfl_up_sync(kFull, m.da, o)};
+}
+
+// Exclusive scan of one Mono per thread over the CTA, in thread order; *total
+// receives the CTA's combination.  Uses the 9-entry shared array `ws`.
+__device__ Mono block_exscan_mono(Mono v, Mono* total, Mono* ws) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    Mono x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        Mono y = shfl_up_mono(x, o);
+        if (lane >= o) x = mono_cat(y, x);
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Mono run = mono_id();
+        for (int i = 0; i < kOwThreads / 32; ++i) {
+            Mono nx = mono_cat(run, ws[i]);
+            ws[i] = run;  // exclusive prefix of warp i
+            run = nx;
+        }
+        ws[kOwThreads / 32] = run;
+    }
+    __syncthreads();
+    Mono before = ws[w];
+    const Mono incl_prev = shfl_up_mono(x, 1);  // every lane takes part in the shuffle
+    Mono ex = lane ? mono_cat(before, incl_prev) : before;
+    *total = ws[kOwThreads / 32];
+    __syncthreads();
+    return ex;
+}
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ float bf_lo(unsigned u) { return __uint_as_float(u << 16); }
+__device__ __forceinline__ float bf_hi(unsigned u) { return __uint_as_float(u & 0xffff0000u); }
+__device__ __forceinline__ float bf1(uint16_t b) { return __uint_as_float((unsigned)b << 16); }
+
+__device__ __forceinline__ int retailer_base(int y, int sl, int Sl) { return y <= sl ? Sl - y : 0; }
+
+// q from the network output (the clamp of the retailer rule)
+__device__ __forceinline__ int q_of(int base, int room, float z) {
+    float v = floorf(__fadd_rn((float)base, z));
+    v = v > 0.f ? v : 0.f;
+    if (v > (float)room) v = (float)room;
+    return (int)v;
+}
+
+// Shared memory of the Picard kernel (dynamic; the network part only with H > 0).
+struct __align__(16) OwSmem {
+    int2 rec[kCh][kLanes];
+    int4 pre[kCh][kLanes];
+    int2 memo[kCh][kLanes];
+    int xs[kMaxSlots];
+    Mono ws[kOwThreads / 32 + 1];
+    int feat_y[kLanes], feat_d[kLanes], feat_base[kLanes], feat_room[kLanes];
+    int qout[kLanes];
+    int pend_any, pend_rows;
+};
+
+// One batched round of the network for the rows flagged in `rows` (bit b =
+// lane b).  Every output is computed in the order documented in pic_owmr.h.
+// h1s [H][32] (k-major), zpart [32][H/8], W1s/b1s/b2s/w3s [H] staged floats.
+__device__ void mlp_round(const OwArgs& a, OwSmem& sm, float* h1s, float* zpart,
+                          const float* W1s, const float* b1s, const float* b2s, const float* w3s,
+                          unsigned rows) {
+    const int H = a.H, ncg = H >> 3;
+    for (int idx = threadIdx.x; idx < H * kLanes; idx += kOwThreads) {
+        const int k = idx >> 5, b = idx & 31;
+        float v = 0.f;
+        if ((rows >> b) & 1u) {
+            float acc = fmaf(W1s[k], (float)sm.feat_y[b], b1s[k]);
+            acc = fmaf(W1s[H + k], (float)sm.feat_d[b], acc);
+            v = acc > 0.f ? acc : 0.f;
+        }
+        h1s[idx] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4 * ncg) {
+        const int rg = threadIdx.x / ncg, cg = threadIdx.x - rg * ncg;
+        if ((rows >> (8 * rg)) & 0xffu) {
+            float acc[8][8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float bb = b2s[8 * cg + c];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) acc[r][c] = bb;
+            }
+            const uint4* wp = reinterpret_cast<const uint4*>(a.W2) + cg;  // row k: H/8 uint4
+            const float4* hp = reinterpret_cast<const float4*>(h1s) + 2 * rg;
+#pragma unroll 4
+            for (int k = 0; k < H; ++k) {
+                const uint4 w = __ldg(wp + (size_t)k * ncg);
+                const float4 h0 = hp[k * 8], h1 = hp[k * 8 + 1];
+                const float wf[8] = {bf_lo(w.x), bf_hi(w.x), bf_lo(w.y), bf_hi(w.y),
+                                     bf_lo(w.z), bf_hi(w.z), bf_lo(w.w), bf_hi(w.w)};
+                const float hf[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+#pragma unroll
+                for (int r = 0; r < 8; ++r)
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(wf[c], hf[r], acc[r][c]);
+            }
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                float p = 0.f;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const float h = acc[r][c] > 0.f ? acc[r][c] : 0.f;
+                    p = fmaf(w3s[8 * cg + c], h, p);
+                }
+                zpart[(8 * rg + r) * ncg + cg] = p;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < kLanes && ((rows >> threadIdx.x) & 1u)) {
+        const int b = threadIdx.x;
+        float z = bf1(a.b3[0]);
+        for (int g = 0; g < ncg; ++g) z = __fadd_rn(z, zpart[b * ncg + g]);
+        sm.qout[b] = q_of(sm.feat_base[b], sm.feat_room[b], z);
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------ Picard kernel
+template <bool NET>
+__global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    OwSmem& sm = *reinterpret_cast<OwSmem*>(smem_raw);
+    float* h1s = reinterpret_cast<float*>(smem_raw + sizeof(OwSmem));  // [H][32]
+    float* zpart = h1s + (NET ? a.H * kLanes : 0);                     // [32][H/8]
+    float* W1s = zpart + (NET ? kLanes * (a.H >> 3) : 0);              // [2][H]
+    float* b1s = W1s + (NET ? 2 * a.H : 0);
+    float* b2s = b1s + (NET ? a.H : 0);
+    float* w3s = b2s + (NET ? a.H : 0);
+    OwCtrl* oc = a.oc;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned long long deadline = globaltimer_ns() + (unsigned long long)a.timeout_ns;
+
+    if (NET) {
+        for (int i = tid; i < a.H; i += kOwThreads) {
+            W1s[i] = bf1(a.W1[i]);
+            W1s[a.H + i] = bf1(a.W1[a.H + i]);
+            b1s[i] = bf1(a.b1[i]);
+            b2s[i] = bf1(a.b2[i]);
+            w3s[i] = bf1(a.w3[i]);
+        }
+    }
+    // contiguous tile range of this CTA (phases A and B)
+    const int tpc = (a.ntiles + gridDim.x - 1) / gridDim.x;
+    const int tile0 = min(a.ntiles, (int)blockIdx.x * tpc), tile1 = min(a.ntiles, tile0 + tpc);
+
+    for (int pass = 1;; ++pass) {
+        const int slot = pass % 3;
+        // ---------------- phase A: tile summaries
+        for (int tile = tile0; tile < tile1; ++tile) {
+            const long long base = (long long)tile * kTile + tid * kItems;
+            Mono m = mono_id();
+#pragma unroll 4
+            for (int i = 0; i < kItems; ++i) {
+                const long long t = base + i;
+                if (t < a.T) m = mono_step(m, (int)t, a.act[t]);
+            }
+            Mono tot;
+            block_exscan_mono(m, &tot, sm.ws);
+            if (tid == 0) a.tsum[tile] = make_int4(tot.sq, tot.lr, tot.da, 0);
+        }
+        if (!grid_sync(&oc->c, deadline)) break;
+        // ---------------- phase B: prefix quantities before every step
+        if (blockIdx.x == 0 && tid == 0) {
+            const int nx = (pass + 1) % 3;
+            oc->changed[nx] = 0;
+            oc->lost[nx] = oc->shipped[nx] = oc->R[nx] = 0;
+        }
+        if (tile0 < tile1 || (blockIdx.x == 0 && a.T == 0)) {
+            // prefix of the tiles before tile0
+            Mono m = mono_id();
+            const int per = (tile0 + kOwThreads - 1) / kOwThreads;
+            for (int i = 0; i < per; ++i) {
+                const int tl = tid * per + i;
+                if (tl < tile0) {
+                    const int4 s4 = a.tsum[tl];
+                    m = mono_cat(m, Mono{s4.x, s4.y, s4.z});
+                }
+            }
+            Mono run;
+            block_exscan_mono(m, &run, sm.ws);
+            for (int tile = tile0; tile < tile1; ++tile) {
+                const long long base = (long long)tile * kTile + tid * kItems;
+                Mono loc = mono_id();
+                for (int i = 0; i < kItems; ++i) {
+                    const long long t = base + i;
+                    if (t < a.T) loc = mono_step(loc, (int)t, a.act[t]);
+                }
+                Mono tot;
+                Mono ex = block_exscan_mono(loc, &tot, sm.ws);
+                Mono cur = mono_cat(run, ex);
+                for (int i = 0; i < kItems; ++i) {
+                    const long long t = base + i;
+                    if (t < a.T) {
+                        const int v = a.act[t];
+                        a.pre[t] = make_int4(cur.sq, cur.da, cur.lr, v);
+                        cur = mono_step(cur, (int)t, v);
+                        if (t == a.T - 1) a.pre[a.T] = make_int4(cur.sq, cur.da, cur.lr, 0);
+                    }
+                }
+                run = mono_cat(run, tot);
+            }
+            if (a.T == 0 && blockIdx.x == 0 && tid == 0) a.pre[0] = make_int4(0, 0, -1, 0);
+        }
+        if (!grid_sync(&oc->c, deadline)) break;
+        // ---------------- phase C: walks
+        int my_changed = 0;
+        long long my_lost = 0, my_ship = 0, my_R = 0;
+        unsigned long long my_evals = 0, my_rounds = 0;
+        for (int g = blockIdx.x; g < a.ngroups; g += gridDim.x) {
+            const int p0 = g * a.B, nb = min(a.B, a.P - p0);
+            // stock of the group's retailers: slot j * 32 + lane for n = p0 + lane + j P
+            for (int i = tid; i < a.rp * kLanes; i += kOwThreads) {
+                const int l = i & 31, j = i >> 5;
+                const long long n = (long long)p0 + l + (long long)j * a.P;
+                if (l < nb && n < a.N) sm.xs[i] = a.x0r[n];
+            }
+            // per-lane walk state (warp 0)
+            int x0a = a.X0, ta = -1, qc_after = 0;
+            int pend = 0, pt = 0, px0 = 0, py = 0, pold = 0, pqc = 0, pslot = 0;
+            const long long row0 = a.gbase[g], row1 = a.gbase[g + 1];
+            for (long long r0 = row0; r0 < row1; r0 += kCh) {
+                __syncthreads();
+                for (int i = tid; i < kCh * kLanes; i += kOwThreads)
+                    (&sm.rec[0][0])[i] = a.rec[r0 * kLanes + i];
+                if (NET)
+                    for (int i = tid; i < kCh * kLanes; i += kOwThreads)
+                        (&sm.memo[0][0])[i] = a.memo[r0 * kLanes + i];
+                __syncthreads();
+                for (int i = tid; i < kCh * kLanes; i += kOwThreads) {
+                    const int t = (&sm.rec[0][0])[i].x;
+                    if (t >= 0) (&sm.pre[0][0])[i] = a.pre[t];
+                }
+                __syncthreads();
+                int pos = 0;
+                for (;;) {
+                    if (warp == 0) {
+                        bool parked = false;
+                        if (lane < nb) {
+                            if (NET && pend) {
+                                // finish the parked step with the round's q
+                                const int q = sm.qout[lane];
+                                const long long mi = (r0 + pos) * kLanes + lane;
+                                a.memo[mi] = make_int2(py, q);
+                                const int r = px0 - q <= a.s;
+                                const int recv = q < px0 ? q : px0;
+                                sm.xs[pslot] = py + recv;
+                                my_ship += recv;
+                                my_R += r;
+                                x0a = r ? a.S : (px0 > q ? px0 - q : 0);
+                                qc_after = pqc + (pold >> 1);
+                                ta = pt;
+                                const int nv = 2 * q + r;
+                                if (nv != pold) {
+                                    a.act[pt] = nv;
+                                    ++my_changed;
+                                }
+                                pend = 0;
+                                ++pos;
+                            }
+                            while (pos < kCh) {
+                                const int2 rc = sm.rec[pos][lane];
+                                if (rc.x < 0) {
+                                    pos = kCh;
+                                    break;
+                                }
+                                const int t = rc.x, n = rc.y & 0xffff, d = rc.y >> 16;
+                                const int4 pr = sm.pre[pos][lane];  // {Qc, D, LR, old}
+                                int x0 = pr.z > ta ? a.S - pr.y : x0a - (pr.x - qc_after);
+                                x0 = x0 > 0 ? x0 : 0;
+                                const int slotn = (n / a.P) * kLanes + lane;
+                                const int xn = sm.xs[slotn];
+                                const int y = xn > d ? xn - d : 0;
+                                my_lost += d > xn ? d - xn : 0;
+                                const int base = retailer_base(y, __ldg(a.sl + n), __ldg(a.Sl + n));
+                                const int room = __ldg(a.cap + n) - y;
+                                int q;
+                                if (NET) {
+                                    const int2 mm = sm.memo[pos][lane];
+                                    if (mm.x != y) {
+                                        pend = 1;
+                                        pt = t; px0 = x0; py = y; pold = pr.w;
+                                        pqc = pr.x; pslot = slotn;
+                                        sm.feat_y[lane] = y;
+                                        sm.feat_d[lane] = d;
+                                        sm.feat_base[lane] = base;
+                                        sm.feat_room[lane] = room;
+                                        parked = true;
+                                        break;
+                                    }
+                                    q = mm.y;
+                                } else {
+                                    q = base < room ? base : room;
+                                }
+                                const int r = x0 - q <= a.s;
+                                const int recv = q < x0 ? q : x0;
+                                sm.xs[slotn] = y + recv;
+                                my_ship += recv;
+                                my_R += r;
+                                x0a = r ? a.S : (x0 > q ? x0 - q : 0);
+                                qc_after = pr.x + (pr.w >> 1);
+                                ta = t;
+                                const int nv = 2 * q + r;
+                                if (nv != pr.w) {
+                                    a.act[t] = nv;
+                                    ++my_changed;
+                                }
+                                ++pos;
+                            }
+                        }
+                        const unsigned rows = __ballot_sync(kFull, parked);
+                        if (lane == 0) {
+                            sm.pend_rows = (int)rows;
+                            sm.pend_any = rows != 0u;
+                        }
+                    }
+                    __syncthreads();
+                    if (!NET || !sm.pend_any) break;
+                    const unsigned rows = (unsigned)sm.pend_rows;
+                    mlp_round(a, sm, h1s, zpart, W1s, b1s, b2s, w3s, rows);
+                    if (tid == 0) {
+                        my_evals += __popc(rows);
+                        ++my_rounds;
+                    }
+                }
+            }
+            __syncthreads();
+            for (int i = tid; i < a.rp * kLanes; i += kOwThreads) {
+                const int l = i & 31, j = i >> 5;
+                const long long n = (long long)p0 + l + (long long)j * a.P;
+                if (l < nb && n < a.N) a.xfin[n] = sm.xs[i];
+            }
+        }
+        // CTA totals
+        if (warp == 0) {
+            const int ch = __reduce_add_sync(kFull, my_changed);
+            const long long lo = warp_sum_i64(my_lost), sh = warp_sum_i64(my_ship),
+                            rr = warp_sum_i64(my_R);
+            if (lane == 0) {
+                if (ch) atomicAdd(&oc->changed[slot], ch);
+                if (lo) atomicAdd((unsigned long long*)&oc->lost[slot], (unsigned long long)lo);
+                if (sh) atomicAdd((unsigned long long*)&oc->shipped[slot], (unsigned long long)sh);
+                if (rr) atomicAdd((unsigned long long*)&oc->R[slot], (unsigned long long)rr);
+            }
+        }
+        if (tid == 0 && my_evals) {
+            atomicAdd(&oc->evals, my_evals);
+            atomicAdd(&oc->rounds, my_rounds);
+        }
+        if (!grid_sync(&oc->c, deadline)) break;
+        const int changed = ld_volatile(&oc->changed[slot]);
+        if (changed == 0 || pass >= a.max_iters) {
+            if (blockIdx.x == 0 && tid == 0) {
+                oc->c.iters = pass;
+                oc->c.converged = changed == 0;
+                oc->c.pad0 = slot;
+            }
+            break;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ sequential baseline
+// One CTA walks the horizon one step at a time.  Network: thread k computes h1_k,
+// thread j the layer-2 unit j (its k chain), thread g the partial p_g, thread 0
+// the sum and the state update.  Without a network one warp runs the steps.
+template <bool NET>
+__global__ void __launch_bounds__(kMaxH) k_owmr_seq(OwArgs a, int32_t* xs_g, int use_smem) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int* xs = use_smem ? reinterpret_cast<int*>(smem_raw) : xs_g;
+    float* h1s = reinterpret_cast<float*>(smem_raw + (use_smem ? ((a.N + 3) & ~3) * 4 : 0));
+    float* h2s = h1s + kMaxH;
+    float* zp = h2s + kMaxH;
+    __shared__ int s_y, s_d, s_base, s_room;
+    const int tid = threadIdx.x;
+    for (int n = tid; n < a.N; n += blockDim.x) xs[n] = a.x0r[n];
+    __syncthreads();
+    int x0 = a.X0;
+    long long lost = 0, ship = 0, R = 0;
+    unsigned long long evals = 0;
+    if (!NET) {
+        if (tid >= 32) return;
+        for (long long t0 = 0; t0 < a.T; t0 += 32) {
+            const long long tt = t0 + tid;
+            int2 rc = tt < a.T ? a.rec[tt] : make_int2(-1, 0);
+            for (int j = 0; j < 32 && t0 + j < a.T; ++j) {
+                const int packed = __shfl_sync(kFull, rc.y, j);
+                if (tid == 0) {
+                    const int n = packed & 0xffff, d = packed >> 16;
+                    const int xn = xs[n];
+                    const int y = xn > d ? xn - d : 0;
+                    lost += d > xn ? d - xn : 0;
+                    const int base = retailer_base(y, a.sl[n], a.Sl[n]);
+                    const int room = a.cap[n] - y;
+                    const int q = base < room ? base : room;
+                    const int r = x0 - q <= a.s;
+                    const int recv = q < x0 ? q : x0;
+                    xs[n] = y + recv;
+                    ship += recv;
+                    R += r;
+                    x0 = r ? a.S : (x0 > q ? x0 - q : 0);
+                    a.act[t0 + j] = 2 * q + r;
+                }
+            }
+        }
+    } else {
+        const int H = a.H;
+        for (long long t = 0; t < a.T; ++t) {
+            if (tid == 0) {
+                const int packed = a.rec[t].y;
+                const int n = packed & 0xffff, d = packed >> 16;
+                const int xn = xs[n];
+                const int y = xn > d ? xn - d : 0;
+                lost += d > xn ? d - xn : 0;
+                s_y = y;
+                s_d = d;
+                s_base = retailer_base(y, a.sl[n], a.Sl[n]);
+                s_room = a.cap[n] - y;
+            }
+            __syncthreads();
+            if (tid < H) {
+                float acc = fmaf(bf1(a.W1[tid]), (float)s_y, bf1(a.b1[tid]));
+                acc = fmaf(bf1(a.W1[H + tid]), (float)s_d, acc);
+                h1s[tid] = acc > 0.f ? acc : 0.f;
+            }
+            __syncthreads();
+            if (tid < H) {
+                float acc = bf1(a.b2[tid]);
+                const uint16_t* col = a.W2 + tid;
+#pragma unroll 8
+                for (int k = 0; k < H; ++k) acc = fmaf(bf1(__ldg(col + (size_t)k * H)), h1s[k], acc);
+                h2s[tid] = acc > 0.f ? acc : 0.f;
+            }
+            __syncthreads();
+            if (tid < (H >> 3)) {
+                float p = 0.f;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) p = fmaf(bf1(a.w3[8 * tid + c]), h2s[8 * tid + c], p);
+                zp[tid] = p;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                float z = bf1(a.b3[0]);
+                for (int g = 0; g < (H >> 3); ++g) z = __fadd_rn(z, zp[g]);
+                const int q = q_of(s_base, s_room, z);
+                const int packed = a.rec[t].y;
+                const int n = packed & 0xffff;
+                const int r = x0 - q <= a.s;
+                const int recv = q < x0 ? q : x0;
+                xs[n] = s_y + recv;
+                ship += recv;
+                R += r;
+                x0 = r ? a.S : (x0 > q ? x0 - q : 0);
+                a.act[t] = 2 * q + r;
+                ++evals;
+            }
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    for (int n = tid; n < a.N; n += blockDim.x) a.xfin[n] = xs[n];
+    if (tid == 0) {
+        OwCtrl* oc = a.oc;
+        oc->lost[0] = lost;
+        oc->shipped[0] = ship;
+        oc->R[0] = R;
+        oc->evals = evals;
+        oc->c.pad0 = 0;
+        oc->c.iters = 0;
+        oc->c.converged = 1;
+        a.pre[0] = make_int4(x0, 0, 0, 0);  // final central stock for the host
+    }
+}
+
+// ------------------------------------------------------------------ tables
+__global__ void k_ow_validate(int T, int N, const int32_t* __restrict__ ret,
+                              const int32_t* __restrict__ dem, const int32_t* __restrict__ cap,
+                              const int32_t* __restrict__ x0r, const int32_t* __restrict__ sl,
+                              const int32_t* __restrict__ Sl, int* bad, int* maxcap) {
+    int b = 0, mc = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < T;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (ret[i] < 0 || ret[i] >= N) b |= 1;
+        if (dem[i] < 0 || dem[i] >= 32768) b |= 2;
+    }
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int c = cap[i];
+        if (c < 0 || c >= (1 << 20)) b |= 4;
+        if (x0r[i] < 0 || x0r[i] > c) b |= 8;
+        if (sl[i] < 0 || Sl[i] < sl[i] || Sl[i] > c) b |= 16;
+        mc = max(mc, c);
+    }
+    if (b) atomicOr(bad, b);
+    if (mc) atomicMax(maxcap, mc);
+}
+
+__global__ void k_ow_keys(int T, int P, const int32_t* __restrict__ ret, int32_t* __restrict__ key,
+                          int32_t* __restrict__ cnt) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < T;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int p = ret[i] % P;
+        key[i] = p;
+        atomicAdd(cnt + p, 1);
+    }
+}
+
+__global__ void k_ow_group_rows(int P, int B, int ngroups, const int32_t* __restrict__ cnt,
+                                int32_t* __restrict__ rows) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ngroups) return;
+    int m = 0;
+    for (int l = 0; l < B && g * B + l < P; ++l) m = max(m, cnt[g * B + l]);
+    rows[g] = (m + kCh - 1) / kCh * kCh;
+}
+
+__global__ void k_ow_rec(int T, int B, const int32_t* __restrict__ key_s,
+                         const int32_t* __restrict__ perm, const int32_t* __restrict__ off,
+                         const int32_t* __restrict__ gbase, const int32_t* __restrict__ ret,
+                         const int32_t* __restrict__ dem, int2* __restrict__ rec) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < T;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int p = key_s[i], j = (int)(i - off[p]), g = p / B, l = p - g * B;
+        const int t = perm[i];
+        rec[((long long)gbase[g] + j) * kLanes + l] = make_int2(t, (dem[t] << 16) | ret[t]);
+    }
+}
+
+__global__ void k_ow_time_rec(int T, const int32_t* __restrict__ ret,
+                              const int32_t* __restrict__ dem, int2* __restrict__ rec) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < T;
+         i += (long long)gridDim.x * blockDim.x)
+        rec[i] = make_int2((int)i, (dem[i] << 16) | ret[i]);
+}
+
+__global__ void k_ow_check_init(int T, const int32_t* __restrict__ init, int maxcap, int* bad) {
+    int b = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < T;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int v = init[i];
+        if (v < 0 || (v >> 1) > maxcap) b = 1;
+    }
+    if (b) atomicOr(bad, 32);
+}
+
+inline int nblk(long long n, int per) { return (int)((n + per - 1) / per); }
+
+}  // namespace
+
+// ------------------------------------------------------------------ handle
+struct pic_owmr {
+    int T = 0, N = 0, X0 = 0, s = 0, S = 0, maxcap = 0, num_sms = 0;
+    int32_t *ret = nullptr, *dem = nullptr, *cap = nullptr, *x0r = nullptr, *sl = nullptr,
+            *Sl = nullptr;
+    int32_t* act = nullptr;
+    int4* pre = nullptr;
+    int32_t* xfin = nullptr;
+    int* bad = nullptr;
+    OwCtrl* oc = nullptr;
+    // tables of the current processor count
+    int P = 0, B = 0, ngroups = 0;
+    long long rows = 0;
+    int2* rec = nullptr;   // interleaved (Picard) or time order (sequential, tseq)
+    int2* trec = nullptr;  // time-order records for the sequential kernel
+    int2* memo = nullptr;
+    int32_t* gbase = nullptr;
+    int4* tsum = nullptr;
+    int ntiles = 0;
+};
+
+namespace {
+
+void free_tables(pic_owmr* h) {
+    cudaFree(h->rec);
+    cudaFree(h->memo);
+    cudaFree(h->gbase);
+    h->rec = nullptr;
+    h->memo = nullptr;
+    h->gbase = nullptr;
+    h->P = 0;
+}
+
+pic_status build_tables(pic_owmr* h, int P, cudaStream_t st, int* launches) {
+    if (h->P == P) return PIC_OK;
+    free_tables(h);
+    const int T = h->T;
+    int B = (P + h->num_sms - 1) / h->num_sms;
+    B = B < 1 ? 1 : (B > kLanes ? kLanes : B);
+    const int ngroups = (P + B - 1) / B;
+    int32_t *key = nullptr, *key_s = nullptr, *perm = nullptr, *tk = nullptr, *tv = nullptr,
+            *cnt = nullptr, *off = nullptr, *grows = nullptr, *hist = nullptr, *blk = nullptr;
+    const int Tn = T > 0 ? T : 1;
+    const int hl = sort_hist_len(Tn);
+    const int bl = scan_blk_len(hl > P + 1 ? hl : P + 1) + scan_blk_len(ngroups + 1) + 2;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](int32_t** p, size_t n) {
+        if (!e) e = cudaMalloc(p, n * sizeof(int32_t));
+    };
+    A(&key, Tn); A(&key_s, Tn); A(&perm, Tn); A(&tk, Tn); A(&tv, Tn); A(&cnt, (size_t)P + 1);
+    A(&off, (size_t)P + 1); A(&grows, (size_t)ngroups + 1); A(&hist, hl); A(&blk, bl);
+    A(&h->gbase, (size_t)ngroups + 1);
+    pic_status ps = PIC_OK;
+    if (!e) e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (P + 1), st);
+    if (!e && T > 0) {
+        k_ow_keys<<<nblk(T, 256) < 4096 ? nblk(T, 256) : 4096, 256, 0, st>>>(T, P, h->ret, key, cnt);
+        e = sort_pairs_raw(key, T, P - 1, key_s, perm, tk, tv, hist, blk, st);
+        int passes = 1;
+        while (passes < 4 && ((unsigned)(P - 1) >> (8 * passes)) != 0) ++passes;
+        *launches += 1 + 5 * passes;
+    }
+    if (!e) e = scan_exclusive(cnt, off, P + 1, nullptr, blk, st);
+    if (!e) {
+        k_ow_group_rows<<<nblk(ngroups, 256), 256, 0, st>>>(P, B, ngroups, cnt, grows);
+        e = cudaMemsetAsync(grows + ngroups, 0, sizeof(int32_t), st);
+    }
+    if (!e) e = scan_exclusive(grows, h->gbase, ngroups + 1, nullptr, blk, st);
+    *launches += 7;
+    int rows_total = 0;
+    if (!e) e = cudaMemcpyAsync(&rows_total, h->gbase + ngroups, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    if (!e) {
+        const size_t nrec = (size_t)(rows_total > 0 ? rows_total : 1) * kLanes;
+        e = cudaMalloc(&h->rec, nrec * sizeof(int2));
+        if (!e) e = cudaMalloc(&h->memo, nrec * sizeof(int2));
+        if (!e) e = cudaMemsetAsync(h->rec, 0xff, nrec * sizeof(int2), st);
+        if (!e && T > 0) {
+            k_ow_rec<<<nblk(T, 256) < 4096 ? nblk(T, 256) : 4096, 256, 0, st>>>(
+                T, B, key_s, perm, off, h->gbase, h->ret, h->dem, h->rec);
+            *launches += 1;
+        }
+    }
+    if (!e) e = cudaStreamSynchronize(st);
+    cudaFree(key); cudaFree(key_s); cudaFree(perm); cudaFree(tk); cudaFree(tv); cudaFree(cnt);
+    cudaFree(off); cudaFree(grows); cudaFree(hist); cudaFree(blk);
+    if (e) {
+        free_tables(h);
+        return fail(e == cudaErrorMemoryAllocation ? PIC_ERR_OOM : PIC_ERR_CUDA,
+                    "OWMR tables: %s", cudaGetErrorString(e));
+    }
+    h->P = P;
+    h->B = B;
+    h->ngroups = ngroups;
+    h->rows = rows_total;
+    return ps;
+}
+
+size_t picard_smem(int H) {
+    size_t s = sizeof(OwSmem);
+    if (H) s += sizeof(float) * ((size_t)H * kLanes + (size_t)kLanes * (H / 8) + 5 * (size_t)H);
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+pic_status pic_owmr_create(const pic_owmr_desc* d, pic_owmr** out) {
+    if (!d || !out) return fail(PIC_ERR_INVALID_ARG, "desc and out are required");
+    *out = nullptr;
+    if (d->T < 0 || d->N < 1 || d->N > 65536)
+        return fail(PIC_ERR_INVALID_ARG, "need 0 <= T and 1 <= N <= 65536");
+    if ((d->T > 0 && (!d->ret || !d->dem)) || !d->cap || !d->x0r || !d->sl || !d->Sl)
+        return fail(PIC_ERR_INVALID_ARG, "missing input array");
+    if (d->mem != PIC_MEM_HOST && d->mem != PIC_MEM_DEVICE)
+        return fail(PIC_ERR_INVALID_ARG, "unknown mem %d", d->mem);
+    if (d->s < 0 || d->S <= d->s || d->S >= (1 << 30) || d->X0 < 0 || d->X0 >= (1 << 30))
+        return fail(PIC_ERR_INVALID_ARG, "need 0 <= s < S < 2^30 and 0 <= X0 < 2^30");
+    pic_owmr* h = new (std::nothrow) pic_owmr();
+    if (!h) return fail(PIC_ERR_OOM, "host allocation failed");
+    cudaStream_t st = (cudaStream_t)d->stream;
+    h->T = d->T; h->N = d->N; h->X0 = d->X0; h->s = d->s; h->S = d->S;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (!e) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t Tn = d->T > 0 ? (size_t)d->T : 1;
+    auto A = [&](void** p, size_t bytes) {
+        if (!e) e = cudaMalloc(p, bytes);
+    };
+    A((void**)&h->ret, Tn * 4); A((void**)&h->dem, Tn * 4); A((void**)&h->cap, (size_t)d->N * 4);
+    A((void**)&h->x0r, (size_t)d->N * 4); A((void**)&h->sl, (size_t)d->N * 4);
+    A((void**)&h->Sl, (size_t)d->N * 4); A((void**)&h->act, Tn * 4);
+    A((void**)&h->pre, (Tn + 1) * sizeof(int4)); A((void**)&h->xfin, (size_t)d->N * 4);
+    A((void**)&h->bad, 2 * sizeof(int)); A((void**)&h->oc, sizeof(OwCtrl));
+    A((void**)&h->trec, Tn * sizeof(int2));
+    h->ntiles = nblk(d->T, kTile);
+    A((void**)&h->tsum, (size_t)(h->ntiles > 0 ? h->ntiles : 1) * sizeof(int4));
+    const cudaMemcpyKind k = d->mem == PIC_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (!e && d->T > 0) e = cudaMemcpyAsync(h->ret, d->ret, (size_t)d->T * 4, k, st);
+    if (!e && d->T > 0) e = cudaMemcpyAsync(h->dem, d->dem, (size_t)d->T * 4, k, st);
+    if (!e) e = cudaMemcpyAsync(h->cap, d->cap, (size_t)d->N * 4, k, st);
+    if (!e) e = cudaMemcpyAsync(h->x0r, d->x0r, (size_t)d->N * 4, k, st);
+    if (!e) e = cudaMemcpyAsync(h->sl, d->sl, (size_t)d->N * 4, k, st);
+    if (!e) e = cudaMemcpyAsync(h->Sl, d->Sl, (size_t)d->N * 4, k, st);
+    if (!e) e = cudaMemsetAsync(h->bad, 0, 2 * sizeof(int), st);
+    if (!e) e = cudaMemsetAsync(h->oc, 0, sizeof(OwCtrl), st);
+    int hb[2] = {0, 0};
+    if (!e) {
+        const long long n = d->T > d->N ? d->T : d->N;
+        k_ow_validate<<<nblk(n, 256) < 1024 ? nblk(n, 256) : 1024, 256, 0, st>>>(
+            d->T, d->N, h->ret, h->dem, h->cap, h->x0r, h->sl, h->Sl, h->bad, h->bad + 1);
+        e = cudaGetLastError();
+    }
+    if (!e) e = cudaMemcpyAsync(hb, h->bad, sizeof(hb), cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    pic_status ps = PIC_OK;
+    if (e) ps = fail(e == cudaErrorMemoryAllocation ? PIC_ERR_OOM : PIC_ERR_CUDA, "OWMR create: %s",
+                     cudaGetErrorString(e));
+    else if (hb[0] & 1) ps = fail(PIC_ERR_INVALID_ARG, "ret[t] outside [0, N)");
+    else if (hb[0] & 2) ps = fail(PIC_ERR_INVALID_ARG, "dem[t] outside [0, 32768)");
+    else if (hb[0] & 4) ps = fail(PIC_ERR_INVALID_ARG, "cap outside [0, 2^20)");
+    else if (hb[0] & 8) ps = fail(PIC_ERR_INVALID_ARG, "x0r outside [0, cap]");
+    else if (hb[0] & 16) ps = fail(PIC_ERR_INVALID_ARG, "need 0 <= sl <= Sl <= cap");
+    else if ((long long)d->T * hb[1] >= (1ll << 31))
+        ps = fail(PIC_ERR_INVALID_ARG, "T * max(cap) must be below 2^31");
+    if (!ps && d->T > 0) {
+        k_ow_time_rec<<<nblk(d->T, 256) < 4096 ? nblk(d->T, 256) : 4096, 256, 0, st>>>(
+            d->T, h->ret, h->dem, h->trec);
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+            ps = fail(PIC_ERR_CUDA, "OWMR create: record table");
+    }
+    h->maxcap = hb[1];
+    if (ps) {
+        pic_owmr_destroy(h);
+        return ps;
+    }
+    *out = h;
+    return PIC_OK;
+}
+
+void pic_owmr_destroy(pic_owmr* h) {
+    if (!h) return;
+    free_tables(h);
+    cudaFree(h->ret); cudaFree(h->dem); cudaFree(h->cap); cudaFree(h->x0r); cudaFree(h->sl);
+    cudaFree(h->Sl); cudaFree(h->act); cudaFree(h->pre); cudaFree(h->xfin); cudaFree(h->bad);
+    cudaFree(h->oc); cudaFree(h->trec); cudaFree(h->tsum);
+    delete h;
+}
+
+pic_status pic_owmr_simulate(pic_owmr* h, const pic_owmr_policy* pol, const pic_owmr_opts* o,
+                             int32_t* actions_out, int32_t* state_out, int32_t out_mem,
+                             pic_owmr_result* res, void* stream) {
+    if (!h || !pol || !o || (!actions_out && h->T > 0))
+        return fail(PIC_ERR_INVALID_ARG, "handle, policy, opts and actions_out are required");
+    if (o->mode != PIC_MODE_PICARD && o->mode != PIC_MODE_SEQUENTIAL)
+        return fail(PIC_ERR_INVALID_ARG, "unknown mode %d", o->mode);
+    if (out_mem != PIC_MEM_HOST && out_mem != PIC_MEM_DEVICE)
+        return fail(PIC_ERR_INVALID_ARG, "unknown out_mem %d", out_mem);
+    const int H = pol->hidden;
+    if (H != 0 && (H < 64 || H > kMaxH || H % 64))
+        return fail(PIC_ERR_INVALID_ARG, "hidden must be 0 or a multiple of 64 in [64, 512]");
+    if (H && (!pol->W1 || !pol->b1 || !pol->W2 || !pol->b2 || !pol->w3 || !pol->b3))
+        return fail(PIC_ERR_INVALID_ARG, "network needs W1, b1, W2, b2, w3, b3 (device)");
+    if (H && ((uintptr_t)pol->W2 & 15u))
+        return fail(PIC_ERR_INVALID_ARG, "W2 must be 16-byte aligned");
+    if (o->num_procs < 0 || o->num_procs > h->N || o->max_iters < 0 || o->timeout_ns < 0)
+        return fail(PIC_ERR_INVALID_ARG, "need 0 <= num_procs <= N, max_iters >= 0, timeout >= 0");
+    const int P = o->num_procs ? o->num_procs : h->N;
+    const int rp = (h->N + P - 1) / P;
+    if (o->mode == PIC_MODE_PICARD && rp > kMaxSlots / kLanes)
+        return fail(PIC_ERR_UNSUPPORTED, "more than %d retailers per processor", kMaxSlots / kLanes);
+    cudaStream_t st = (cudaStream_t)stream;
+    int launches = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    const bool timing = (o->flags & PIC_FLAG_TIMING) != 0;
+    if (timing) {
+        CU(cudaEventCreate(&ev0));
+        CU(cudaEventCreate(&ev1));
+        CU(cudaEventRecord(ev0, st));
+    }
+    CU(cudaMemsetAsync(h->oc, 0, sizeof(OwCtrl), st));
+    CU(cudaMemsetAsync(h->bad, 0, sizeof(int), st));
+    if (o->alpha_init && h->T > 0) {
+        CU(cudaMemcpyAsync(h->act, o->alpha_init, (size_t)h->T * 4, cudaMemcpyDeviceToDevice, st));
+        k_ow_check_init<<<nblk(h->T, 256) < 1024 ? nblk(h->T, 256) : 1024, 256, 0, st>>>(
+            h->T, h->act, h->maxcap, h->bad);
+        ++launches;
+        int hb0 = 0;
+        CU(cudaMemcpyAsync(&hb0, h->bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        if (hb0 & 32) return fail(PIC_ERR_INVALID_ARG, "alpha_init holds a negative value or q > max cap");
+    } else if (h->T > 0) {
+        CU(cudaMemsetAsync(h->act, 0, (size_t)h->T * 4, st));
+    }
+    OwArgs a{};
+    a.T = h->T; a.N = h->N; a.P = P; a.H = H; a.X0 = h->X0; a.s = h->s; a.S = h->S;
+    a.ntiles = h->ntiles; a.rp = rp;
+    a.max_iters = o->max_iters ? o->max_iters : (h->T < INT_MAX ? h->T + 1 : INT_MAX);
+    a.timeout_ns = o->timeout_ns ? o->timeout_ns : 60000000000ll;
+    a.cap = h->cap; a.sl = h->sl; a.Sl = h->Sl; a.x0r = h->x0r;
+    a.act = h->act; a.pre = h->pre; a.tsum = h->tsum; a.xfin = h->xfin; a.oc = h->oc;
+    a.W1 = pol->W1; a.b1 = pol->b1; a.W2 = pol->W2; a.b2 = pol->b2; a.w3 = pol->w3; a.b3 = pol->b3;
+    if (o->mode == PIC_MODE_PICARD) {
+        pic_status ps = build_tables(h, P, st, &launches);
+        if (ps) return ps;
+        a.B = h->B; a.ngroups = h->ngroups; a.rec = h->rec; a.gbase = h->gbase; a.memo = h->memo;
+        if (H) CU(cudaMemsetAsync(h->memo, 0xff, (size_t)(h->rows > 0 ? h->rows : 1) * kLanes * sizeof(int2), st));
+        const size_t smem = picard_smem(H);
+        void (*kern)(OwArgs) = H ? k_owmr_picard<true> : k_owmr_picard<false>;
+        CU(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int occ = 0;
+        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kOwThreads, smem));
+        if (occ < 1) return fail(PIC_ERR_CUDA, "OWMR kernel does not fit an SM");
+        const int grid = h->num_sms * occ;
+        void* params[] = {&a};
+        CU(cudaLaunchCooperativeKernel((const void*)kern, grid, kOwThreads, params, smem, st));
+        ++launches;
+    } else {
+        a.rec = h->trec;
+        const int use_smem = h->N <= 16384;
+        const size_t smem = (use_smem ? (size_t)((h->N + 3) & ~3) * 4 : 0) +
+                            (H ? sizeof(float) * (2 * kMaxH + kMaxH / 8) : 0);
+        int32_t* xs_g = nullptr;
+        if (!use_smem) CU(cudaMallocAsync(&xs_g, (size_t)h->N * 4, st));
+        void (*kern)(OwArgs, int32_t*, int) = H ? k_owmr_seq<true> : k_owmr_seq<false>;
+        CU(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<1, H ? kMaxH : 32, smem, st>>>(a, xs_g, use_smem);
+        CU(cudaGetLastError());
+        ++launches;
+        if (xs_g) CU(cudaFreeAsync(xs_g, st));
+    }
+    OwCtrl hc;
+    int hbad = 0;
+    int4 pT = make_int4(0, 0, -1, 0);
+    CU(cudaMemcpyAsync(&hc, h->oc, sizeof(OwCtrl), cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(&hbad, h->bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(&pT, h->pre + (o->mode == PIC_MODE_PICARD ? h->T : 0), sizeof(int4),
+                       cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (hbad & 32) return fail(PIC_ERR_INVALID_ARG, "alpha_init holds a negative value or q > max cap");
+    if (hc.c.err) return fail((pic_status)hc.c.err, "device wait exceeded timeout (%lld ns)", a.timeout_ns);
+    const cudaMemcpyKind k = out_mem == PIC_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (h->T > 0) CU(cudaMemcpyAsync(actions_out, h->act, (size_t)h->T * 4, k, st));
+    if (state_out) {
+        int x0f;
+        if (o->mode == PIC_MODE_PICARD)
+            x0f = pT.z >= 0 ? (h->S - pT.y > 0 ? h->S - pT.y : 0) : (h->X0 - pT.x > 0 ? h->X0 - pT.x : 0);
+        else
+            x0f = pT.x;
+        if (out_mem == PIC_MEM_HOST) {
+            state_out[0] = x0f;
+        } else {
+            CU(cudaMemcpyAsync(state_out, &x0f, sizeof(int), cudaMemcpyHostToDevice, st));
+        }
+        CU(cudaMemcpyAsync(state_out + 1, h->xfin, (size_t)h->N * 4, k, st));
+    }
+    if (timing) CU(cudaEventRecord(ev1, st));
+    CU(cudaStreamSynchronize(st));
+    const int sl = hc.c.pad0;
+    if (res) {
+        res->iters = hc.c.iters;
+        res->procs = o->mode == PIC_MODE_PICARD ? P : 1;
+        res->replenishments = hc.R[sl];
+        res->lost = hc.lost[sl];
+        res->shipped = hc.shipped[sl];
+        res->policy_calls = (long long)hc.evals;
+        res->eval_rounds = (long long)hc.rounds;
+        res->launches = launches;
+        res->ms_total = 0.f;
+        if (timing) cudaEventElapsedTime(&res->ms_total, ev0, ev1);
+    }
+    if (timing) {
+        cudaEventDestroy(ev0);
+        cudaEventDestroy(ev1);
+    }
+    if (o->mode == PIC_MODE_PICARD && !hc.c.converged)
+        return fail(PIC_ERR_NOT_CONVERGED, "no fixed point within %d passes", a.max_iters);
+    return PIC_OK;
+}
+
+}  // extern "C"

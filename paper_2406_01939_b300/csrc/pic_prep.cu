@@ -374,15 +374,27 @@ cudaError_t scan_exclusive(const int32_t* in, int32_t* out, int n, int32_t* tota
     return cudaGetLastError();
 }
 
+int sort_hist_len(int n) { return 256 * nblocks(n, kRadixTile); }
+int scan_blk_len(int n) { return nblocks(n, kScanTile); }
+
 cudaError_t sort_pairs(Instance* I, const int32_t* keys, int n, int max_key, int32_t* keys_out,
                        int32_t* vals_out, int32_t* tmp_k, int32_t* tmp_v, cudaStream_t st) {
+    int passes = 1;
+    while (passes < 4 && ((unsigned)max_key >> (8 * passes)) != 0) ++passes;
+    I->launches += n > 0 ? passes * 5 : 0;
+    return sort_pairs_raw(keys, n, max_key, keys_out, vals_out, tmp_k, tmp_v, I->hist,
+                          I->scan_blk, st);
+}
+
+cudaError_t sort_pairs_raw(const int32_t* keys, int n, int max_key, int32_t* keys_out,
+                           int32_t* vals_out, int32_t* tmp_k, int32_t* tmp_v, int32_t* hist,
+                           int32_t* scan_blk, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     // LSD radix, 8-bit digits, as many passes as max_key has bytes; the passes
     // alternate between (tmp_k, tmp_v) and (keys_out, vals_out) so that the last
     // one lands in (keys_out, vals_out)
     int passes = 1;
     while (passes < 4 && ((unsigned)max_key >> (8 * passes)) != 0) ++passes;
-    I->launches += passes * 5;  // per pass: histogram, 3-kernel scan, scatter
     const int nblk = nblocks(n, kRadixTile);
     const int32_t* kin = keys;
     const int32_t* vin = nullptr;
@@ -392,9 +404,9 @@ cudaError_t sort_pairs(Instance* I, const int32_t* keys, int n, int max_key, int
         int32_t* kout = last_side ? keys_out : tmp_k;
         int32_t* vout = last_side ? vals_out : tmp_v;
         const int shift = 8 * p;
-        k_radix_hist<<<nblk, kRadixThreads, 0, st>>>(kin, n, shift, I->hist, nblk);
-        if ((e = scan_exclusive(I->hist, I->hist, 256 * nblk, nullptr, I->scan_blk, st))) return e;
-        k_radix_scatter<<<nblk, kRadixThreads, 0, st>>>(kin, vin, n, shift, I->hist, nblk, kout, vout);
+        k_radix_hist<<<nblk, kRadixThreads, 0, st>>>(kin, n, shift, hist, nblk);
+        if ((e = scan_exclusive(hist, hist, 256 * nblk, nullptr, scan_blk, st))) return e;
+        k_radix_scatter<<<nblk, kRadixThreads, 0, st>>>(kin, vin, n, shift, hist, nblk, kout, vout);
         kin = kout;
         vin = vout;
     }

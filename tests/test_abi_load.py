@@ -25,7 +25,7 @@ def test_header_declares_the_entry_points():
     names = declared_functions()
     for want in ("pic_create_instance", "pic_instance_load", "pic_destroy_instance",
                  "pic_simulate", "pic_create_batch", "pic_simulate_batch", "pic_policy_grad",
-                 "pic_last_error"):
+                 "pic_last_error", "pic_owmr_create", "pic_owmr_simulate", "pic_owmr_destroy"):
         assert want in names
 
 
@@ -54,3 +54,15 @@ def test_null_arguments_rejected_without_gpu():
     assert L.pic_simulate_batch(None, None, None, None, None, None, None) == pic.PIC_ERR_INVALID_ARG
     assert "batch" in pic.pic_last_error()
     assert L.pic_policy_grad(None, None, None, None, None, None) == pic.PIC_ERR_INVALID_ARG
+
+
+def test_owmr_null_and_shape_arguments_rejected_without_gpu():
+    """pic_owmr_create checks its descriptor before any device work."""
+    import paper_2406_01939_b300 as pic
+    from paper_2406_01939_b300 import owmr
+    L = owmr._lib()
+    h = ctypes.c_void_p()
+    assert L.pic_owmr_create(None, ctypes.byref(h)) == pic.PIC_ERR_INVALID_ARG
+    d = owmr.pic_owmr_desc(10, 0)  # N = 0
+    assert L.pic_owmr_create(ctypes.byref(d), ctypes.byref(h)) == pic.PIC_ERR_INVALID_ARG
+    assert "N" in pic.pic_last_error()

@@ -6,14 +6,16 @@
  * Model (Appendix B.1), integer units.  State s_t = (x0, x_1..x_N): the central
  * warehouse and N retailers.  Step t brings demand d_t at retailer n_t.  The
  * action is a_t = (q_t, r_t): q_t units retailer n_t asks from the central
- * warehouse and r_t = 1 when the central warehouse replenishes up to S.  Any
+ * warehouse and r_t = 1 when the central warehouse replenishes up to S.  The
+ * disturbance also carries e_t, the steps since the store's previous demand (the
+ * demand history the retailer policy may use).  Any
  * action (fresh or cached) moves the state by
  *     y = max(0, x_n - d),  x_n <- y + min(q, x0),  x0 <- r ? S : max(0, x0 - q);
  * the demand lost at t is max(0, d - x_n).
  *
  * Policy (Appendix B.2).  The retailer's q depends only on its own inventory and
  * on the disturbance: base = (y <= s_n) ? S_n - y : 0 and, with a network,
- * q = clamp(floor(base + z), 0, c_n - y), z = MLP(y, d) in FP32 (the order is
+ * q = clamp(floor(base + z), 0, c_n - y), z = MLP(y, d, e / 4096) in FP32 (the order is
  * given with pic_owmr_policy); without one, q = base.  The central warehouse
  * follows (s, S): r = [x0 - q <= s].
  *
@@ -32,7 +34,7 @@
  * row-major arrays, caller-owned buffers, work ordered on the given stream
  * (calls return after it completed).  Actions are encoded as 2 q + r (int32).
  * Limits (else PIC_ERR_INVALID_ARG): 1 <= N <= 65,536; 0 <= T <= 2^31 - 1;
- * 0 <= d_t < 32,768; 0 <= x0_n <= c_n < 2^20; 0 <= s_n <= S_n <= c_n;
+ * 0 <= d_t < 32,768; 0 <= e_t < 32,768; 0 <= x0_n <= c_n < 2^20; 0 <= s_n <= S_n <= c_n;
  * 0 <= s < S < 2^30; 0 <= X0 < 2^30; T * max(c_n) < 2^31 (prefix sums of q
  * fit int32).
  */
@@ -54,6 +56,7 @@ typedef struct {
     int32_t T, N;
     const int32_t* ret; /* [T] retailer n_t of step t, 0 <= n_t < N */
     const int32_t* dem; /* [T] demand d_t */
+    const int32_t* ex;  /* [T] exogenous feature e_t (steps since the store's previous demand) */
     const int32_t* cap; /* [N] retailer capacity c_n */
     const int32_t* x0r; /* [N] initial retailer inventory */
     const int32_t* sl;  /* [N] retailer reorder point s_n */
@@ -64,11 +67,11 @@ typedef struct {
     void* stream;       /* cudaStream_t for the copies and validation, or NULL */
 } pic_owmr_desc;
 
-/* Retailer network: 2 -> H -> H -> 1 with ReLU, BF16 bit patterns in DEVICE
- * memory, borrowed for the call.  W1 [2][H] and W2 [H][H] are input-major
+/* Retailer network: 3 -> H -> H -> 1 with ReLU, BF16 bit patterns in DEVICE
+ * memory, borrowed for the call.  W1 [3][H] and W2 [H][H] are input-major
  * (W2[k][j] connects hidden unit k of layer 1 to unit j of layer 2); b1, b2,
- * w3 [H]; b3 [1].  FP32 order, features y and d as floats:
- *   h1_k = relu(fma(W1[1][k], d, fma(W1[0][k], y, b1_k)))
+ * w3 [H]; b3 [1].  FP32 order, features y, d and g = e * 2^-12 as floats:
+ *   h1_k = relu(fma(W1[2][k], g, fma(W1[1][k], d, fma(W1[0][k], y, b1_k))))
  *   h2_j = relu(acc), acc = b2_j, then acc = fma(W2[k][j], h1_k, acc) for k = 0..H-1
  *   p_g  = fma chain over j = 8g..8g+7 of w3_j h2_j, from 0
  *   z    = b3 + p_0 + p_1 + ... (left to right);  relu(v) = v > 0 ? v : 0.

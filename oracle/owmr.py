@@ -3,8 +3,8 @@ INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 benchmark's CPU legs may import it.  The arithmetic lives in ``owmr_oracle.c``
 (plain C, ``-ffp-contract=off``); this module only marshals arguments.
 
-Inputs are duck-typed: an instance needs T, N, ret, dem, cap, x0r, sl, Sl
-(int arrays), X0, s, S (ints); a network needs H and W1 [2][H], b1 [H],
+Inputs are duck-typed: an instance needs T, N, ret, dem, ex, cap, x0r, sl, Sl
+(int arrays), X0, s, S (ints); a network needs H and W1 [3][H], b1 [H],
 W2 [H][H] (input-major), b2 [H], w3 [H], b3 [1] as BF16 bit patterns (uint16),
 or is None.
 
@@ -44,14 +44,14 @@ def _load():
         if _lib is None:
             lib = C.CDLL(build())
             P, i32 = C.c_void_p, C.c_int32
-            model = [i32, i32, P, P, P, P, P, P, i32, i32, i32, i32, P, P, P, P, P, P]
+            model = [i32, i32, P, P, P, P, P, P, P, i32, i32, i32, i32, P, P, P, P, P, P]
             lib.orc_owmr_seq.argtypes = model + [P, P, P]
             lib.orc_owmr_seq.restype = C.c_int
             lib.orc_owmr_picard_literal.argtypes = model + [i32, P, i32, P, P, P, P, P]
             lib.orc_owmr_picard_literal.restype = C.c_int
             lib.orc_owmr_picard_walk.argtypes = model + [i32, P, i32, P, P, P, P, P, P, P]
             lib.orc_owmr_picard_walk.restype = C.c_int
-            lib.owmr_mlp.argtypes = [P, i32, i32, P, P]
+            lib.owmr_mlp.argtypes = [P, i32, i32, i32, P, P]
             lib.owmr_mlp.restype = C.c_float
             _lib = lib
     return _lib
@@ -70,8 +70,8 @@ def _u16(a):
 
 
 def _model(inst, net):
-    keep = [_i32(inst.ret), _i32(inst.dem), _i32(inst.cap), _i32(inst.x0r), _i32(inst.sl),
-            _i32(inst.Sl)]
+    keep = [_i32(inst.ret), _i32(inst.dem), _i32(inst.ex), _i32(inst.cap), _i32(inst.x0r),
+            _i32(inst.sl), _i32(inst.Sl)]
     if net is None:
         nk, H = [None] * 6, 0
     else:
@@ -79,7 +79,7 @@ def _model(inst, net):
               _u16(net.b3)]
         H = int(net.H)
     keep += nk
-    args = [int(inst.T), int(inst.N)] + [_p(a) for a in keep[:6]] + \
+    args = [int(inst.T), int(inst.N)] + [_p(a) for a in keep[:7]] + \
         [int(inst.X0), int(inst.s), int(inst.S), H] + [_p(a) for a in nk]
     return args, keep
 
@@ -142,8 +142,9 @@ def picard_literal(inst, net, proc, max_iters=None, alpha_init=None, record=Fals
     """Algorithm 1 with the retailer partition (processor of retailer n =
     proc[n]), every processor replaying the whole horizon each pass.
 
-    Pins: Prop. 1 (fixed point = sequential path, at most one pass per
-    processor plus one); one processor = one pass plus a confirming pass;
+    Pins: Prop. 1 (fixed point = sequential path; the first step that differs
+    from it moves strictly forward every pass); one processor = one pass plus a
+    confirming pass;
     Theorem B.1: with s >= every retailer capacity and x0 > s, alpha^k equals
     the sequential path for every k >= 2R + 1 (R replenishments of the
     sequential path), and for k >= 1 when R = 0."""
@@ -169,12 +170,13 @@ class _Net(C.Structure):
                 ("b2", C.c_void_p), ("w3", C.c_void_p), ("b3", C.c_void_p)]
 
 
-def mlp(net, y, d):
-    """The network's FP32 output z for features (y, d) in the fixed order of
-    owmr_mlp().  Pin: within the FP32 rounding bound of an FP64 evaluation."""
+def mlp(net, y, d, e=0):
+    """The network's FP32 output z for features (y, d, e / 4096) in the fixed
+    order of owmr_mlp().  Pin: within the FP32 rounding bound of an FP64
+    evaluation."""
     lib = _load()
     keep = [_u16(net.W1), _u16(net.b1), _u16(net.W2), _u16(net.b2), _u16(net.w3), _u16(net.b3)]
     s = _Net(int(net.H), *[_p(a) for a in keep])
     h1 = np.zeros(int(net.H), np.float32)
     h2 = np.zeros(int(net.H), np.float32)
-    return float(lib.owmr_mlp(C.byref(s), int(y), int(d), _p(h1), _p(h2)))
+    return float(lib.owmr_mlp(C.byref(s), int(y), int(d), int(e), _p(h1), _p(h2)))

@@ -4,7 +4,9 @@
  * and the benchmark's CPU legs use it; it shares no code with the CUDA path.
  *
  * Model (Appendix B.1), integer units.  State s_t = (x0, x_1..x_N): central
- * warehouse and N retailers.  Disturbance w_t = (retailer n_t, demand d_t).
+ * warehouse and N retailers.  Disturbance w_t = (retailer n_t, demand d_t,
+ * e_t = steps since the store's previous demand: the demand history the policy
+ * may use).
  * Action a_t = (q_t, r_t): q_t >= 0 units retailer n_t asks from the central
  * warehouse, r_t = 1 when the central warehouse replenishes (order up to S).
  * Transition for any action (cached or fresh):
@@ -15,8 +17,8 @@
  * the disturbance only; the central warehouse follows (s, S): r = [x0 - q <= s].
  * Retailer rule (a reading; the appendix fixes the network's size, not its
  * inputs or output map): base = (y <= s_n) ? S_n - y : 0; with a network,
- * q = clamp(floor(base + z), 0, c_n - y) where z = MLP(y, d) in FP32 in the fixed
- * operation order of owmr_mlp() below; without one, q = min(base, c_n - y).
+ * q = clamp(floor(base + z), 0, c_n - y) where z = MLP(y, d, e / 4096) in FP32 in
+ * the fixed operation order of owmr_mlp() below; without one, q = min(base, c_n - y).
  *
  * Picard iteration (Algorithm 1 with the retailer partition of Appendix B.2:
  * processor m owns the time steps of its retailers).  Pass k: every processor
@@ -49,7 +51,7 @@ static float bf16f(uint16_t b) {
 
 typedef struct {
     int H;                   /* 0: no network */
-    const uint16_t *W1;      /* [2][H]  input-major: W1[i*H + k] */
+    const uint16_t *W1;      /* [3][H]  input-major: W1[i*H + k] */
     const uint16_t *b1;      /* [H] */
     const uint16_t *W2;      /* [H][H]  input-major: W2[k*H + j] */
     const uint16_t *b2;      /* [H] */
@@ -57,17 +59,18 @@ typedef struct {
     const uint16_t *b3;      /* [1] */
 } Net;
 
-/* The network's FP32 output z for features (y, d), in this order:
- *   h1_k = relu(fma(W1[1][k], d, fma(W1[0][k], y, b1_k)))
+/* The network's FP32 output z for features (y, d, g = e * 2^-12), in this order:
+ *   h1_k = relu(fma(W1[2][k], g, fma(W1[1][k], d, fma(W1[0][k], y, b1_k))))
  *   h2_j = relu(b2_j + sum_k W2[k][j] h1_k), one fma per k in increasing k
  *   p_g  = sum_{j = 8g..8g+7} w3_j h2_j, one fma per j from 0
  *   z    = b3 + p_0 + p_1 + ... (left to right), relu(v) = v > 0 ? v : 0. */
-float owmr_mlp(const Net* net, int y, int d, float* h1, float* h2) {
+float owmr_mlp(const Net* net, int y, int d, int e, float* h1, float* h2) {
     const int H = net->H;
-    const float fy = (float)y, fd = (float)d;
+    const float fy = (float)y, fd = (float)d, fg = (float)e * 0.000244140625f; /* exact */
     for (int k = 0; k < H; ++k) {
         float a = fmaf(bf16f(net->W1[k]), fy, bf16f(net->b1[k]));
         a = fmaf(bf16f(net->W1[H + k]), fd, a);
+        a = fmaf(bf16f(net->W1[2 * H + k]), fg, a);
         h1[k] = a > 0.f ? a : 0.f;
     }
     for (int j = 0; j < H; ++j) {
@@ -86,19 +89,19 @@ float owmr_mlp(const Net* net, int y, int d, float* h1, float* h2) {
 
 typedef struct {
     int T, N;
-    const int32_t *ret, *dem, *cap, *x0r, *sl, *Sl;
+    const int32_t *ret, *dem, *ex, *cap, *x0r, *sl, *Sl;
     int X0, s, S;
     Net net;
     float *h1, *h2; /* scratch [H] */
 } Model;
 
 /* Retailer order quantity for post-demand inventory y (Appendix B.2's pi_n). */
-static int retailer_q(Model* M, int n, int y, int d, long long* evals) {
+static int retailer_q(Model* M, int n, int y, int d, int e, long long* evals) {
     const int base = y <= M->sl[n] ? M->Sl[n] - y : 0;
     const int room = M->cap[n] - y;
     if (M->net.H == 0) return base < room ? base : room;
     ++*evals;
-    const float z = owmr_mlp(&M->net, y, d, M->h1, M->h2);
+    const float z = owmr_mlp(&M->net, y, d, e, M->h1, M->h2);
     float v = floorf((float)base + z);
     v = v > 0.f ? v : 0.f;               /* NaN-free: z is finite for finite weights */
     if (v > (float)room) v = (float)room;
@@ -112,15 +115,16 @@ static int check(const Model* M) {
         if (M->cap[n] < 0 || M->x0r[n] < 0 || M->x0r[n] > M->cap[n] || M->sl[n] < 0 ||
             M->Sl[n] < M->sl[n] || M->Sl[n] > M->cap[n]) return ERR_ARG;
     for (int t = 0; t < M->T; ++t)
-        if (M->ret[t] < 0 || M->ret[t] >= M->N || M->dem[t] < 0) return ERR_ARG;
+        if (M->ret[t] < 0 || M->ret[t] >= M->N || M->dem[t] < 0 || M->ex[t] < 0 ||
+            M->ex[t] >= 32768) return ERR_ARG;
     return OK;
 }
 
 static int setup(Model* M, int T, int N, const int32_t* ret, const int32_t* dem,
-                 const int32_t* cap, const int32_t* x0r, const int32_t* sl, const int32_t* Sl,
+                 const int32_t* ex, const int32_t* cap, const int32_t* x0r, const int32_t* sl, const int32_t* Sl,
                  int X0, int s, int S, int H, const uint16_t* W1, const uint16_t* b1,
                  const uint16_t* W2, const uint16_t* b2, const uint16_t* w3, const uint16_t* b3) {
-    M->T = T; M->N = N; M->ret = ret; M->dem = dem; M->cap = cap; M->x0r = x0r;
+    M->T = T; M->N = N; M->ret = ret; M->dem = dem; M->ex = ex; M->cap = cap; M->x0r = x0r;
     M->sl = sl; M->Sl = Sl; M->X0 = X0; M->s = s; M->S = S;
     M->net.H = H; M->net.W1 = W1; M->net.b1 = b1; M->net.W2 = W2; M->net.b2 = b2;
     M->net.w3 = w3; M->net.b3 = b3;
@@ -142,13 +146,14 @@ static void teardown(Model* M) {
 /* Sequential simulation (the baseline of Appendix B.3): act[t] = 2 q_t + r_t,
  * xfin = (x0, x_1..x_N) after step T, stats = (R = sum r, lost units, shipped
  * units sum min(q, x0), policy evaluations). */
-int orc_owmr_seq(int T, int N, const int32_t* ret, const int32_t* dem, const int32_t* cap,
+int orc_owmr_seq(int T, int N, const int32_t* ret, const int32_t* dem, const int32_t* ex,
+                 const int32_t* cap,
                  const int32_t* x0r, const int32_t* sl, const int32_t* Sl, int X0, int s, int S,
                  int H, const uint16_t* W1, const uint16_t* b1, const uint16_t* W2,
                  const uint16_t* b2, const uint16_t* w3, const uint16_t* b3, int32_t* act,
                  int32_t* xfin, int64_t* stats) {
     Model M;
-    int e = setup(&M, T, N, ret, dem, cap, x0r, sl, Sl, X0, s, S, H, W1, b1, W2, b2, w3, b3);
+    int e = setup(&M, T, N, ret, dem, ex, cap, x0r, sl, Sl, X0, s, S, H, W1, b1, W2, b2, w3, b3);
     if (e) return e;
     int32_t* x = (int32_t*)malloc(sizeof(int32_t) * (N ? N : 1));
     memcpy(x, x0r, sizeof(int32_t) * N);
@@ -157,7 +162,7 @@ int orc_owmr_seq(int T, int N, const int32_t* ret, const int32_t* dem, const int
         const int n = ret[t], d = dem[t];
         const int y = x[n] > d ? x[n] - d : 0;
         lost += d > x[n] ? d - x[n] : 0;
-        const int q = retailer_q(&M, n, y, d, &evals);
+        const int q = retailer_q(&M, n, y, d, ex[t], &evals);
         const int r = x0 - q <= s;
         const long long recv = q < x0 ? q : x0;
         shipped += recv;
@@ -187,7 +192,7 @@ static int check_procs(int N, int P, const int32_t* proc) {
  * from s_1 and calls the policy at each of its own steps.  init = alpha^0 (NULL:
  * q = 0, r = 0 everywhere).  record (optional, [max_iters][T]) receives alpha^k.
  * Returns ERR_NOT_CONVERGED if max_iters passes change something every time. */
-int orc_owmr_picard_literal(int T, int N, const int32_t* ret, const int32_t* dem,
+int orc_owmr_picard_literal(int T, int N, const int32_t* ret, const int32_t* dem, const int32_t* ex,
                             const int32_t* cap, const int32_t* x0r, const int32_t* sl,
                             const int32_t* Sl, int X0, int s, int S, int H, const uint16_t* W1,
                             const uint16_t* b1, const uint16_t* W2, const uint16_t* b2,
@@ -195,7 +200,7 @@ int orc_owmr_picard_literal(int T, int N, const int32_t* ret, const int32_t* dem
                             int max_iters, const int32_t* init, int32_t* act, int32_t* iters,
                             int32_t* record, int64_t* evals_out) {
     Model M;
-    int e = setup(&M, T, N, ret, dem, cap, x0r, sl, Sl, X0, s, S, H, W1, b1, W2, b2, w3, b3);
+    int e = setup(&M, T, N, ret, dem, ex, cap, x0r, sl, Sl, X0, s, S, H, W1, b1, W2, b2, w3, b3);
     if (e) return e;
     if ((e = check_procs(N, P, proc))) { teardown(&M); return e; }
     int32_t* alpha = (int32_t*)calloc(T ? T : 1, sizeof(int32_t));
@@ -214,7 +219,7 @@ int orc_owmr_picard_literal(int T, int N, const int32_t* ret, const int32_t* dem
                 const int y = x[n] > d ? x[n] - d : 0;
                 int q, r;
                 if (proc[n] == m) {
-                    q = retailer_q(&M, n, y, d, &evals);
+                    q = retailer_q(&M, n, y, d, ex[t], &evals);
                     r = x0 - q <= s;
                     next[t] = 2 * q + r;
                 } else {
@@ -251,7 +256,7 @@ int orc_owmr_picard_literal(int T, int N, const int32_t* ret, const int32_t* dem
  * only its own steps in time order.  A policy call whose input y (and step) is
  * the same as at the previous evaluation of that step reuses its result (the
  * policy is deterministic); evals_out counts the calls actually made. */
-int orc_owmr_picard_walk(int T, int N, const int32_t* ret, const int32_t* dem,
+int orc_owmr_picard_walk(int T, int N, const int32_t* ret, const int32_t* dem, const int32_t* ex,
                          const int32_t* cap, const int32_t* x0r, const int32_t* sl,
                          const int32_t* Sl, int X0, int s, int S, int H, const uint16_t* W1,
                          const uint16_t* b1, const uint16_t* W2, const uint16_t* b2,
@@ -259,7 +264,7 @@ int orc_owmr_picard_walk(int T, int N, const int32_t* ret, const int32_t* dem,
                          int max_iters, const int32_t* init, int32_t* act, int32_t* iters,
                          int32_t* record, int64_t* evals_out, int32_t* xfin, int64_t* stats) {
     Model M;
-    int e = setup(&M, T, N, ret, dem, cap, x0r, sl, Sl, X0, s, S, H, W1, b1, W2, b2, w3, b3);
+    int e = setup(&M, T, N, ret, dem, ex, cap, x0r, sl, Sl, X0, s, S, H, W1, b1, W2, b2, w3, b3);
     if (e) return e;
     if ((e = check_procs(N, P, proc))) { teardown(&M); return e; }
     const size_t Tn = T ? (size_t)T : 1;
@@ -313,7 +318,7 @@ int orc_owmr_picard_walk(int T, int N, const int32_t* ret, const int32_t* dem,
                 int q;
                 if (memo_y[t] == y) q = memo_q[t];
                 else {
-                    q = retailer_q(&M, n, y, d, &evals);
+                    q = retailer_q(&M, n, y, d, ex[t], &evals);
                     memo_y[t] = y;
                     memo_q[t] = q;
                 }

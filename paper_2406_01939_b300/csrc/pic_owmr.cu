@@ -70,7 +70,7 @@ struct OwArgs {
     int T, N, P, B, ngroups, H, X0, s, S, ntiles, max_iters, rp;  // rp = ceil(N / P)
     long long timeout_ns;
     const int32_t *cap, *sl, *Sl, *x0r;
-    const int2* rec;        // interleaved [rows][32]: {t, d << 16 | n}, t = -1 pads
+    const int4* rec;        // interleaved [rows][32]: {t, n, d, e}, t = -1 pads
     const int32_t* gbase;   // [ngroups + 1] first row of each group
     int32_t* act;           // [T] cache, time order
     int4* pre;              // [T + 1]
@@ -164,19 +164,19 @@ __device__ __forceinline__ int q_of(int base, int room, float z) {
 
 // Shared memory of the Picard kernel (dynamic; the network part only with H > 0).
 struct __align__(16) OwSmem {
-    int2 rec[kCh][kLanes];
+    int4 rec[kCh][kLanes];
     int4 pre[kCh][kLanes];
     int2 memo[kCh][kLanes];
     int xs[kMaxSlots];
     Mono ws[kOwThreads / 32 + 1];
-    int feat_y[kLanes], feat_d[kLanes], feat_base[kLanes], feat_room[kLanes];
+    int feat_y[kLanes], feat_d[kLanes], feat_e[kLanes], feat_base[kLanes], feat_room[kLanes];
     int qout[kLanes];
     int pend_any, pend_rows;
 };
 
 // One batched round of the network for the rows flagged in `rows` (bit b =
 // lane b).  Every output is computed in the order documented in pic_owmr.h.
-// h1s [H][32] (k-major), zpart [32][H/8], W1s/b1s/b2s/w3s [H] staged floats.
+// h1s [H][32] (k-major), zpart [32][H/8], W1s [3][H], b1s/b2s/w3s [H] staged floats.
 __device__ void mlp_round(const OwArgs& a, OwSmem& sm, float* h1s, float* zpart,
                           const float* W1s, const float* b1s, const float* b2s, const float* w3s,
                           unsigned rows) {
@@ -187,6 +187,7 @@ __device__ void mlp_round(const OwArgs& a, OwSmem& sm, float* h1s, float* zpart,
         if ((rows >> b) & 1u) {
             float acc = fmaf(W1s[k], (float)sm.feat_y[b], b1s[k]);
             acc = fmaf(W1s[H + k], (float)sm.feat_d[b], acc);
+            acc = fmaf(W1s[2 * H + k], (float)sm.feat_e[b] * 0.000244140625f, acc);
             v = acc > 0.f ? acc : 0.f;
         }
         h1s[idx] = v;
@@ -245,8 +246,8 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
     OwSmem& sm = *reinterpret_cast<OwSmem*>(smem_raw);
     float* h1s = reinterpret_cast<float*>(smem_raw + sizeof(OwSmem));  // [H][32]
     float* zpart = h1s + (NET ? a.H * kLanes : 0);                     // [32][H/8]
-    float* W1s = zpart + (NET ? kLanes * (a.H >> 3) : 0);              // [2][H]
-    float* b1s = W1s + (NET ? 2 * a.H : 0);
+    float* W1s = zpart + (NET ? kLanes * (a.H >> 3) : 0);              // [3][H]
+    float* b1s = W1s + (NET ? 3 * a.H : 0);
     float* b2s = b1s + (NET ? a.H : 0);
     float* w3s = b2s + (NET ? a.H : 0);
     OwCtrl* oc = a.oc;
@@ -257,6 +258,7 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
         for (int i = tid; i < a.H; i += kOwThreads) {
             W1s[i] = bf1(a.W1[i]);
             W1s[a.H + i] = bf1(a.W1[a.H + i]);
+            W1s[2 * a.H + i] = bf1(a.W1[2 * a.H + i]);
             b1s[i] = bf1(a.b1[i]);
             b2s[i] = bf1(a.b2[i]);
             w3s[i] = bf1(a.w3[i]);
@@ -381,12 +383,12 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
                                 ++pos;
                             }
                             while (pos < kCh) {
-                                const int2 rc = sm.rec[pos][lane];
+                                const int4 rc = sm.rec[pos][lane];
                                 if (rc.x < 0) {
                                     pos = kCh;
                                     break;
                                 }
-                                const int t = rc.x, n = rc.y & 0xffff, d = rc.y >> 16;
+                                const int t = rc.x, n = rc.y, d = rc.z;
                                 const int4 pr = sm.pre[pos][lane];  // {Qc, D, LR, old}
                                 int x0 = pr.z > ta ? a.S - pr.y : x0a - (pr.x - qc_after);
                                 x0 = x0 > 0 ? x0 : 0;
@@ -405,6 +407,7 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
                                         pqc = pr.x; pslot = slotn;
                                         sm.feat_y[lane] = y;
                                         sm.feat_d[lane] = d;
+                                        sm.feat_e[lane] = rc.w;
                                         sm.feat_base[lane] = base;
                                         sm.feat_room[lane] = room;
                                         parked = true;
@@ -493,7 +496,7 @@ __global__ void __launch_bounds__(kMaxH) k_owmr_seq(OwArgs a, int32_t* xs_g, int
     float* h1s = reinterpret_cast<float*>(smem_raw + (use_smem ? ((a.N + 3) & ~3) * 4 : 0));
     float* h2s = h1s + kMaxH;
     float* zp = h2s + kMaxH;
-    __shared__ int s_y, s_d, s_base, s_room;
+    __shared__ int s_y, s_d, s_e, s_base, s_room;
     const int tid = threadIdx.x;
     for (int n = tid; n < a.N; n += blockDim.x) xs[n] = a.x0r[n];
     __syncthreads();
@@ -504,11 +507,10 @@ __global__ void __launch_bounds__(kMaxH) k_owmr_seq(OwArgs a, int32_t* xs_g, int
         if (tid >= 32) return;
         for (long long t0 = 0; t0 < a.T; t0 += 32) {
             const long long tt = t0 + tid;
-            int2 rc = tt < a.T ? a.rec[tt] : make_int2(-1, 0);
+            const int4 rc = tt < a.T ? a.rec[tt] : make_int4(-1, 0, 0, 0);
             for (int j = 0; j < 32 && t0 + j < a.T; ++j) {
-                const int packed = __shfl_sync(kFull, rc.y, j);
+                const int n = __shfl_sync(kFull, rc.y, j), d = __shfl_sync(kFull, rc.z, j);
                 if (tid == 0) {
-                    const int n = packed & 0xffff, d = packed >> 16;
                     const int xn = xs[n];
                     const int y = xn > d ? xn - d : 0;
                     lost += d > xn ? d - xn : 0;
@@ -529,13 +531,14 @@ __global__ void __launch_bounds__(kMaxH) k_owmr_seq(OwArgs a, int32_t* xs_g, int
         const int H = a.H;
         for (long long t = 0; t < a.T; ++t) {
             if (tid == 0) {
-                const int packed = a.rec[t].y;
-                const int n = packed & 0xffff, d = packed >> 16;
+                const int4 rc = a.rec[t];
+                const int n = rc.y, d = rc.z;
                 const int xn = xs[n];
                 const int y = xn > d ? xn - d : 0;
                 lost += d > xn ? d - xn : 0;
                 s_y = y;
                 s_d = d;
+                s_e = rc.w;
                 s_base = retailer_base(y, a.sl[n], a.Sl[n]);
                 s_room = a.cap[n] - y;
             }
@@ -543,6 +546,7 @@ __global__ void __launch_bounds__(kMaxH) k_owmr_seq(OwArgs a, int32_t* xs_g, int
             if (tid < H) {
                 float acc = fmaf(bf1(a.W1[tid]), (float)s_y, bf1(a.b1[tid]));
                 acc = fmaf(bf1(a.W1[H + tid]), (float)s_d, acc);
+                acc = fmaf(bf1(a.W1[2 * H + tid]), (float)s_e * 0.000244140625f, acc);
                 h1s[tid] = acc > 0.f ? acc : 0.f;
             }
             __syncthreads();
@@ -565,8 +569,7 @@ __global__ void __launch_bounds__(kMaxH) k_owmr_seq(OwArgs a, int32_t* xs_g, int
                 float z = bf1(a.b3[0]);
                 for (int g = 0; g < (H >> 3); ++g) z = __fadd_rn(z, zp[g]);
                 const int q = q_of(s_base, s_room, z);
-                const int packed = a.rec[t].y;
-                const int n = packed & 0xffff;
+                const int n = a.rec[t].y;
                 const int r = x0 - q <= a.s;
                 const int recv = q < x0 ? q : x0;
                 xs[n] = s_y + recv;
@@ -596,7 +599,8 @@ __global__ void __launch_bounds__(kMaxH) k_owmr_seq(OwArgs a, int32_t* xs_g, int
 
 // ------------------------------------------------------------------ tables
 __global__ void k_ow_validate(int T, int N, const int32_t* __restrict__ ret,
-                              const int32_t* __restrict__ dem, const int32_t* __restrict__ cap,
+                              const int32_t* __restrict__ dem, const int32_t* __restrict__ ex,
+                              const int32_t* __restrict__ cap,
                               const int32_t* __restrict__ x0r, const int32_t* __restrict__ sl,
                               const int32_t* __restrict__ Sl, int* bad, int* maxcap) {
     int b = 0, mc = 0;
@@ -604,6 +608,7 @@ __global__ void k_ow_validate(int T, int N, const int32_t* __restrict__ ret,
          i += (long long)gridDim.x * blockDim.x) {
         if (ret[i] < 0 || ret[i] >= N) b |= 1;
         if (dem[i] < 0 || dem[i] >= 32768) b |= 2;
+        if (ex[i] < 0 || ex[i] >= 32768) b |= 32;
     }
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x) {
@@ -639,20 +644,22 @@ __global__ void k_ow_group_rows(int P, int B, int ngroups, const int32_t* __rest
 __global__ void k_ow_rec(int T, int B, const int32_t* __restrict__ key_s,
                          const int32_t* __restrict__ perm, const int32_t* __restrict__ off,
                          const int32_t* __restrict__ gbase, const int32_t* __restrict__ ret,
-                         const int32_t* __restrict__ dem, int2* __restrict__ rec) {
+                         const int32_t* __restrict__ dem, const int32_t* __restrict__ ex,
+                         int4* __restrict__ rec) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < T;
          i += (long long)gridDim.x * blockDim.x) {
         const int p = key_s[i], j = (int)(i - off[p]), g = p / B, l = p - g * B;
         const int t = perm[i];
-        rec[((long long)gbase[g] + j) * kLanes + l] = make_int2(t, (dem[t] << 16) | ret[t]);
+        rec[((long long)gbase[g] + j) * kLanes + l] = make_int4(t, ret[t], dem[t], ex[t]);
     }
 }
 
 __global__ void k_ow_time_rec(int T, const int32_t* __restrict__ ret,
-                              const int32_t* __restrict__ dem, int2* __restrict__ rec) {
+                              const int32_t* __restrict__ dem, const int32_t* __restrict__ ex,
+                              int4* __restrict__ rec) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < T;
          i += (long long)gridDim.x * blockDim.x)
-        rec[i] = make_int2((int)i, (dem[i] << 16) | ret[i]);
+        rec[i] = make_int4((int)i, ret[i], dem[i], ex[i]);
 }
 
 __global__ void k_ow_check_init(int T, const int32_t* __restrict__ init, int maxcap, int* bad) {
@@ -672,7 +679,7 @@ inline int nblk(long long n, int per) { return (int)((n + per - 1) / per); }
 // ------------------------------------------------------------------ handle
 struct pic_owmr {
     int T = 0, N = 0, X0 = 0, s = 0, S = 0, maxcap = 0, num_sms = 0;
-    int32_t *ret = nullptr, *dem = nullptr, *cap = nullptr, *x0r = nullptr, *sl = nullptr,
+    int32_t *ret = nullptr, *dem = nullptr, *ex = nullptr, *cap = nullptr, *x0r = nullptr, *sl = nullptr,
             *Sl = nullptr;
     int32_t* act = nullptr;
     int4* pre = nullptr;
@@ -682,8 +689,8 @@ struct pic_owmr {
     // tables of the current processor count
     int P = 0, B = 0, ngroups = 0;
     long long rows = 0;
-    int2* rec = nullptr;   // interleaved (Picard) or time order (sequential, tseq)
-    int2* trec = nullptr;  // time-order records for the sequential kernel
+    int4* rec = nullptr;   // interleaved step records of the Picard walks
+    int4* trec = nullptr;  // time-order records for the sequential kernel
     int2* memo = nullptr;
     int32_t* gbase = nullptr;
     int4* tsum = nullptr;
@@ -742,12 +749,12 @@ pic_status build_tables(pic_owmr* h, int P, cudaStream_t st, int* launches) {
     if (!e) e = cudaStreamSynchronize(st);
     if (!e) {
         const size_t nrec = (size_t)(rows_total > 0 ? rows_total : 1) * kLanes;
-        e = cudaMalloc(&h->rec, nrec * sizeof(int2));
+        e = cudaMalloc(&h->rec, nrec * sizeof(int4));
         if (!e) e = cudaMalloc(&h->memo, nrec * sizeof(int2));
-        if (!e) e = cudaMemsetAsync(h->rec, 0xff, nrec * sizeof(int2), st);
+        if (!e) e = cudaMemsetAsync(h->rec, 0xff, nrec * sizeof(int4), st);
         if (!e && T > 0) {
             k_ow_rec<<<nblk(T, 256) < 4096 ? nblk(T, 256) : 4096, 256, 0, st>>>(
-                T, B, key_s, perm, off, h->gbase, h->ret, h->dem, h->rec);
+                T, B, key_s, perm, off, h->gbase, h->ret, h->dem, h->ex, h->rec);
             *launches += 1;
         }
     }
@@ -768,7 +775,7 @@ pic_status build_tables(pic_owmr* h, int P, cudaStream_t st, int* launches) {
 
 size_t picard_smem(int H) {
     size_t s = sizeof(OwSmem);
-    if (H) s += sizeof(float) * ((size_t)H * kLanes + (size_t)kLanes * (H / 8) + 5 * (size_t)H);
+    if (H) s += sizeof(float) * ((size_t)H * kLanes + (size_t)kLanes * (H / 8) + 6 * (size_t)H);
     return s;
 }
 
@@ -781,7 +788,7 @@ pic_status pic_owmr_create(const pic_owmr_desc* d, pic_owmr** out) {
     *out = nullptr;
     if (d->T < 0 || d->N < 1 || d->N > 65536)
         return fail(PIC_ERR_INVALID_ARG, "need 0 <= T and 1 <= N <= 65536");
-    if ((d->T > 0 && (!d->ret || !d->dem)) || !d->cap || !d->x0r || !d->sl || !d->Sl)
+    if ((d->T > 0 && (!d->ret || !d->dem || !d->ex)) || !d->cap || !d->x0r || !d->sl || !d->Sl)
         return fail(PIC_ERR_INVALID_ARG, "missing input array");
     if (d->mem != PIC_MEM_HOST && d->mem != PIC_MEM_DEVICE)
         return fail(PIC_ERR_INVALID_ARG, "unknown mem %d", d->mem);
@@ -798,17 +805,18 @@ pic_status pic_owmr_create(const pic_owmr_desc* d, pic_owmr** out) {
     auto A = [&](void** p, size_t bytes) {
         if (!e) e = cudaMalloc(p, bytes);
     };
-    A((void**)&h->ret, Tn * 4); A((void**)&h->dem, Tn * 4); A((void**)&h->cap, (size_t)d->N * 4);
+    A((void**)&h->ret, Tn * 4); A((void**)&h->dem, Tn * 4); A((void**)&h->ex, Tn * 4); A((void**)&h->cap, (size_t)d->N * 4);
     A((void**)&h->x0r, (size_t)d->N * 4); A((void**)&h->sl, (size_t)d->N * 4);
     A((void**)&h->Sl, (size_t)d->N * 4); A((void**)&h->act, Tn * 4);
     A((void**)&h->pre, (Tn + 1) * sizeof(int4)); A((void**)&h->xfin, (size_t)d->N * 4);
     A((void**)&h->bad, 2 * sizeof(int)); A((void**)&h->oc, sizeof(OwCtrl));
-    A((void**)&h->trec, Tn * sizeof(int2));
+    A((void**)&h->trec, Tn * sizeof(int4));
     h->ntiles = nblk(d->T, kTile);
     A((void**)&h->tsum, (size_t)(h->ntiles > 0 ? h->ntiles : 1) * sizeof(int4));
     const cudaMemcpyKind k = d->mem == PIC_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     if (!e && d->T > 0) e = cudaMemcpyAsync(h->ret, d->ret, (size_t)d->T * 4, k, st);
     if (!e && d->T > 0) e = cudaMemcpyAsync(h->dem, d->dem, (size_t)d->T * 4, k, st);
+    if (!e && d->T > 0) e = cudaMemcpyAsync(h->ex, d->ex, (size_t)d->T * 4, k, st);
     if (!e) e = cudaMemcpyAsync(h->cap, d->cap, (size_t)d->N * 4, k, st);
     if (!e) e = cudaMemcpyAsync(h->x0r, d->x0r, (size_t)d->N * 4, k, st);
     if (!e) e = cudaMemcpyAsync(h->sl, d->sl, (size_t)d->N * 4, k, st);
@@ -819,7 +827,7 @@ pic_status pic_owmr_create(const pic_owmr_desc* d, pic_owmr** out) {
     if (!e) {
         const long long n = d->T > d->N ? d->T : d->N;
         k_ow_validate<<<nblk(n, 256) < 1024 ? nblk(n, 256) : 1024, 256, 0, st>>>(
-            d->T, d->N, h->ret, h->dem, h->cap, h->x0r, h->sl, h->Sl, h->bad, h->bad + 1);
+            d->T, d->N, h->ret, h->dem, h->ex, h->cap, h->x0r, h->sl, h->Sl, h->bad, h->bad + 1);
         e = cudaGetLastError();
     }
     if (!e) e = cudaMemcpyAsync(hb, h->bad, sizeof(hb), cudaMemcpyDeviceToHost, st);
@@ -829,6 +837,7 @@ pic_status pic_owmr_create(const pic_owmr_desc* d, pic_owmr** out) {
                      cudaGetErrorString(e));
     else if (hb[0] & 1) ps = fail(PIC_ERR_INVALID_ARG, "ret[t] outside [0, N)");
     else if (hb[0] & 2) ps = fail(PIC_ERR_INVALID_ARG, "dem[t] outside [0, 32768)");
+    else if (hb[0] & 32) ps = fail(PIC_ERR_INVALID_ARG, "ex[t] outside [0, 32768)");
     else if (hb[0] & 4) ps = fail(PIC_ERR_INVALID_ARG, "cap outside [0, 2^20)");
     else if (hb[0] & 8) ps = fail(PIC_ERR_INVALID_ARG, "x0r outside [0, cap]");
     else if (hb[0] & 16) ps = fail(PIC_ERR_INVALID_ARG, "need 0 <= sl <= Sl <= cap");
@@ -836,7 +845,7 @@ pic_status pic_owmr_create(const pic_owmr_desc* d, pic_owmr** out) {
         ps = fail(PIC_ERR_INVALID_ARG, "T * max(cap) must be below 2^31");
     if (!ps && d->T > 0) {
         k_ow_time_rec<<<nblk(d->T, 256) < 4096 ? nblk(d->T, 256) : 4096, 256, 0, st>>>(
-            d->T, h->ret, h->dem, h->trec);
+            d->T, h->ret, h->dem, h->ex, h->trec);
         if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
             ps = fail(PIC_ERR_CUDA, "OWMR create: record table");
     }
@@ -852,7 +861,7 @@ pic_status pic_owmr_create(const pic_owmr_desc* d, pic_owmr** out) {
 void pic_owmr_destroy(pic_owmr* h) {
     if (!h) return;
     free_tables(h);
-    cudaFree(h->ret); cudaFree(h->dem); cudaFree(h->cap); cudaFree(h->x0r); cudaFree(h->sl);
+    cudaFree(h->ret); cudaFree(h->dem); cudaFree(h->ex); cudaFree(h->cap); cudaFree(h->x0r); cudaFree(h->sl);
     cudaFree(h->Sl); cudaFree(h->act); cudaFree(h->pre); cudaFree(h->xfin); cudaFree(h->bad);
     cudaFree(h->oc); cudaFree(h->trec); cudaFree(h->tsum);
     delete h;

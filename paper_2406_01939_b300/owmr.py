@@ -16,7 +16,7 @@ P_ = C.c_void_p
 
 
 class pic_owmr_desc(C.Structure):
-    _fields_ = [("T", C.c_int32), ("N", C.c_int32), ("ret", P_), ("dem", P_), ("cap", P_),
+    _fields_ = [("T", C.c_int32), ("N", C.c_int32), ("ret", P_), ("dem", P_), ("ex", P_), ("cap", P_),
                 ("x0r", P_), ("sl", P_), ("Sl", P_), ("X0", C.c_int32), ("s", C.c_int32),
                 ("S", C.c_int32), ("mem", C.c_int32), ("stream", P_)]
 
@@ -106,7 +106,7 @@ class DeviceOwmr:
         self.inst = inst
         self.device = torch.device(device)
         self.T, self.N = int(inst.T), int(inst.N)
-        arrs = [inst.ret, inst.dem, inst.cap, inst.x0r, inst.sl, inst.Sl]
+        arrs = [inst.ret, inst.dem, inst.ex, inst.cap, inst.x0r, inst.sl, inst.Sl]
         self._keep = [_dev_i32(a, self.device) for a in arrs]
         d = pic_owmr_desc(self.T, self.N, *[_ptr(x) for x in self._keep], int(inst.X0),
                           int(inst.s), int(inst.S), PIC_MEM_DEVICE, _stream_handle(stream))

@@ -32,7 +32,9 @@ OWMR inventory control (Appendix B): one central warehouse, N retailers.
                   n drawn with weight (1 - a)^n (a = 0: uniform), stores reorder
                   at 10 units up to 20 (capacity 24), central (s, S) =
                   (1,000, 71,000), about one central replenishment a week;
-                  two-hidden-layer network of width 512, BF16 N(0, 0.02).
+                  two-hidden-layer network of width 512, BF16 N(0, 0.02), fed
+                  (post-demand stock, demand, steps since the store's
+                  previous demand / 4096).
 """
 from __future__ import annotations
 
@@ -222,6 +224,8 @@ class OwmrInstance:
     N: int
     ret: np.ndarray  # int32 [T] retailer n(w_t) of step t
     dem: np.ndarray  # int32 [T] demand d(w_t) >= 0
+    ex: np.ndarray  # int32 [T] steps since the store's previous demand (t + 1 at its first),
+    #                 capped at 32,767: the demand history the retailer network sees
     cap: np.ndarray  # int32 [N] retailer capacity c_n
     x0r: np.ndarray  # int32 [N] initial retailer inventory
     sl: np.ndarray  # int32 [N] retailer reorder point s_n
@@ -233,8 +237,8 @@ class OwmrInstance:
 
 @dataclass
 class OwmrNet:
-    """Two-hidden-layer network (2 -> H -> H -> 1), BF16 bit patterns (uint16);
-    weight matrices input-major: W1 [2, H], W2 [H, H] (row = input unit)."""
+    """Two-hidden-layer network (3 -> H -> H -> 1), BF16 bit patterns (uint16);
+    weight matrices input-major: W1 [3, H], W2 [H, H] (row = input unit)."""
 
     H: int
     W1: np.ndarray
@@ -274,14 +278,30 @@ def make_owmr(T, N, seed=0, a=0.0, demand="unit", s_loc=10, S_loc=20, cap=24, s=
     S = s + max(1, T // 52) if S is None else int(S)
     X0 = S if X0 is None else int(X0)
     x0r = Sla.copy() if x0r is None else full(x0r)
-    return OwmrInstance(T, N, ret, dem, capa, x0r, sla, Sla, X0, s, S)
+    return OwmrInstance(T, N, ret, dem, demand_gaps(ret), capa, x0r, sla, Sla, X0, s, S)
+
+
+def demand_gaps(ret):
+    """Per step, the steps since the same store's previous demand (t + 1 for its
+    first), capped at 32,767."""
+    T = len(ret)
+    t = np.arange(T, dtype=np.int64)
+    order = np.lexsort((t, ret))
+    rs, ts = ret[order], t[order]
+    prev = np.full(T, -1, np.int64)
+    if T > 1:
+        same = rs[1:] == rs[:-1]
+        prev[1:][same] = ts[:-1][same]
+    gap = np.empty(T, np.int64)
+    gap[order] = ts - prev
+    return np.minimum(gap, 32_767).astype(np.int32)
 
 
 def make_owmr_net(H=512, seed=0, std=0.02) -> OwmrNet:
     """BF16 N(0, std) parameters drawn in the order W1, b1, W2, b2, w3, b3."""
     rng = np.random.Generator(np.random.PCG64(seed + 0x0E7))
     g = lambda *shape: f32_to_bf16(rng.normal(0.0, std, size=shape).astype(np.float32))
-    W1, b1, W2, b2, w3, b3 = g(2, H), g(H), g(H, H), g(H), g(H), g(1)
+    W1, b1, W2, b2, w3, b3 = g(3, H), g(H), g(H, H), g(H), g(H), g(1)
     return OwmrNet(H, W1, b1, W2, b2, w3, b3)
 
 

@@ -159,6 +159,6 @@ def test_base_case_full_size():
     assert torch.equal(pg["actions"], sg["actions"]) and torch.equal(pg["state"], sg["state"])
     assert pg["R"] == sg["R"] and pg["lost"] == sg["lost"]
     Tp = 20_000
-    pre = synth.OwmrInstance(Tp, inst.N, inst.ret[:Tp], inst.dem[:Tp], inst.cap, inst.x0r,
-                             inst.sl, inst.Sl, inst.X0, inst.s, inst.S)
+    pre = synth.OwmrInstance(Tp, inst.N, inst.ret[:Tp], inst.dem[:Tp], inst.ex[:Tp], inst.cap,
+                             inst.x0r, inst.sl, inst.Sl, inst.X0, inst.s, inst.S)
     np.testing.assert_array_equal(pg["actions"][:Tp].cpu().numpy(), ow.seq_sim(pre, net)["actions"])

@@ -13,7 +13,8 @@ from paper_2406_01939_b300.synth import OwmrInstance, OwmrNet
 
 def inst_of(ret, dem, cap, x0r, sl, Sl, X0, s, S):
     a = lambda v: np.asarray(v, np.int32)
-    return OwmrInstance(len(ret), len(cap), a(ret), a(dem), a(cap), a(x0r), a(sl), a(Sl), X0, s, S)
+    return OwmrInstance(len(ret), len(cap), a(ret), a(dem), synth.demand_gaps(a(ret)), a(cap),
+                        a(x0r), a(sl), a(Sl), X0, s, S)
 
 
 def test_hand_trace_theorem_setting():
@@ -112,7 +113,7 @@ def bf(x):
 
 def const_net(H, b3):
     z = bf(np.zeros(1))
-    return OwmrNet(H, np.repeat(bf(np.zeros(2 * H)), 1), bf(np.zeros(H)), bf(np.zeros(H * H)),
+    return OwmrNet(H, bf(np.zeros(3 * H)), bf(np.zeros(H)), bf(np.zeros(H * H)),
                    bf(np.zeros(H)), bf(np.zeros(H)), bf([b3]))
 
 
@@ -123,7 +124,7 @@ def test_network_constant_output_special_cases():
     rng = np.random.default_rng(11)
     inst = random_inst(rng, 300, 5)
     plain = ow.seq_sim(inst)
-    assert ow.mlp(const_net(64, 0.5), 7, 2) == 0.5
+    assert ow.mlp(const_net(64, 0.5), 7, 2, 1000) == 0.5
     assert ow.mlp(const_net(64, -0.75), 0, 0) == -0.75
     same = ow.seq_sim(inst, const_net(64, 0.5))
     assert (same["actions"] == plain["actions"]).all()
@@ -146,26 +147,26 @@ def test_network_within_fp32_bound_of_fp64():
     H = 128
     net = synth.make_owmr_net(H, seed=2, std=0.2)
     f = lambda a: synth.bf16_to_f32(np.asarray(a)).astype(np.float64)
-    W1, b1, W2, b2, w3, b3 = f(net.W1).reshape(2, H), f(net.b1), f(net.W2).reshape(H, H), \
+    W1, b1, W2, b2, w3, b3 = f(net.W1).reshape(3, H), f(net.b1), f(net.W2).reshape(H, H), \
         f(net.b2), f(net.w3), f(net.b3)[0]
     u = 2.0 ** -24
     g = lambda n: n * u / (1 - n * u)
     worst = 0.0
-    for y in range(0, 40, 3):
-        for d in range(4):
-            a1 = b1 + W1[0] * y + W1[1] * d
-            h1 = np.maximum(a1, 0)
-            e1 = g(3) * (np.abs(b1) + np.abs(W1[0] * y) + np.abs(W1[1] * d))
-            a2 = b2 + h1 @ W2
-            h2 = np.maximum(a2, 0)
-            e2 = g(H + 1) * (np.abs(b2) + (np.abs(h1) + e1) @ np.abs(W2)) + e1 @ np.abs(W2)
-            z64 = b3 + h2 @ w3
-            ez = g(H + 1) * (abs(b3) + (np.abs(h2) + e2) @ np.abs(w3)) + e2 @ np.abs(w3)
-            z32 = ow.mlp(net, y, d)
-            assert abs(z32 - z64) <= ez * 1.0001 + 1e-30, (y, d, z32, z64, ez)
-            worst = max(worst, abs(z32 - z64) / max(ez, 1e-30))
-            # a dropped bias or a skipped relu is far outside the bound
-            assert abs((z64 - b3) - z32) > ez or abs(b3) <= ez
+    for y, d, e in [(y, d, e) for y in range(0, 40, 3) for d in range(4) for e in (1, 777, 32767)]:
+        gf = e / 4096.0
+        a1 = b1 + W1[0] * y + W1[1] * d + W1[2] * gf
+        h1 = np.maximum(a1, 0)
+        e1 = g(4) * (np.abs(b1) + np.abs(W1[0] * y) + np.abs(W1[1] * d) + np.abs(W1[2] * gf))
+        a2 = b2 + h1 @ W2
+        h2 = np.maximum(a2, 0)
+        e2 = g(H + 1) * (np.abs(b2) + (np.abs(h1) + e1) @ np.abs(W2)) + e1 @ np.abs(W2)
+        z64 = b3 + h2 @ w3
+        ez = g(H + 1) * (abs(b3) + (np.abs(h2) + e2) @ np.abs(w3)) + e2 @ np.abs(w3)
+        z32 = ow.mlp(net, y, d, e)
+        assert abs(z32 - z64) <= ez * 1.0001 + 1e-30, (y, d, e, z32, z64, ez)
+        worst = max(worst, abs(z32 - z64) / max(ez, 1e-30))
+        # a dropped bias or a skipped relu is far outside the bound
+        assert abs((z64 - b3) - z32) > ez or abs(b3) <= ez
     assert worst < 1.0
 
 

@@ -89,6 +89,14 @@ typedef struct {
     int32_t flags;             /* PIC_FLAG_TIMING */
     const int32_t* alpha_init; /* [T] DEVICE, initial cache (2 q + r, q >= 0), or NULL: all 0 */
     int64_t timeout_ns;        /* bound on each device-side wait; 0 = 60 s */
+    int32_t max_steps;         /* max_steps window of Appendix A.3, in steps: a pass calls
+                                  the policy only at steps t < w + max_steps and keeps the
+                                  cached actions of later steps; w starts at 0, becomes the
+                                  first changed step after a pass that changed the cache, and
+                                  the end of the evaluated range after one that did not; the
+                                  call ends after a pass that changed nothing with the range
+                                  covering the horizon (same result).  0 = no window; the
+                                  default max_iters is then T + 1 + T / max_steps + 1 */
 } pic_owmr_opts;
 
 typedef struct {

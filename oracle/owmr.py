@@ -47,9 +47,9 @@ def _load():
             model = [i32, i32, P, P, P, P, P, P, P, i32, i32, i32, i32, P, P, P, P, P, P]
             lib.orc_owmr_seq.argtypes = model + [P, P, P]
             lib.orc_owmr_seq.restype = C.c_int
-            lib.orc_owmr_picard_literal.argtypes = model + [i32, P, i32, P, P, P, P, P]
+            lib.orc_owmr_picard_literal.argtypes = model + [i32, P, i32, i32, P, P, P, P, P]
             lib.orc_owmr_picard_literal.restype = C.c_int
-            lib.orc_owmr_picard_walk.argtypes = model + [i32, P, i32, P, P, P, P, P, P, P]
+            lib.orc_owmr_picard_walk.argtypes = model + [i32, P, i32, i32, P, P, P, P, P, P, P]
             lib.orc_owmr_picard_walk.restype = C.c_int
             lib.owmr_mlp.argtypes = [P, i32, i32, i32, P, P]
             lib.owmr_mlp.restype = C.c_float
@@ -116,19 +116,20 @@ def _procs(inst, proc):
     return proc, P
 
 
-def _run_picard(fn, inst, net, proc, max_iters, alpha_init, record, extra):
+def _run_picard(fn, inst, net, proc, max_iters, alpha_init, record, extra, window=0):
     lib = _load()
     args, keep = _model(inst, net)
     proc, P = _procs(inst, proc)
     T = int(inst.T)
     if max_iters is None:
-        max_iters = 2 * T + 2
+        max_iters = 2 * T + 2 + (2 * (T // window + 1) if window else 0)
     init = None if alpha_init is None else _i32(alpha_init)
     act = np.zeros(max(T, 1), np.int32)
     iters = np.zeros(1, np.int32)
     ev = np.zeros(1, np.int64)
     rec = np.zeros((max_iters, max(T, 1)), np.int32) if record else None
-    rc = getattr(lib, fn)(*args, P, _p(proc), int(max_iters), _p(init), _p(act), _p(iters),
+    rc = getattr(lib, fn)(*args, P, _p(proc), int(max_iters), int(window), _p(init), _p(act),
+                          _p(iters),
                           _p(rec), _p(ev), *[_p(a) for a in extra])
     _err(rc, fn)
     k = int(iters[0])
@@ -138,7 +139,7 @@ def _run_picard(fn, inst, net, proc, max_iters, alpha_init, record, extra):
     return out
 
 
-def picard_literal(inst, net, proc, max_iters=None, alpha_init=None, record=False):
+def picard_literal(inst, net, proc, max_iters=None, alpha_init=None, record=False, window=0):
     """Algorithm 1 with the retailer partition (processor of retailer n =
     proc[n]), every processor replaying the whole horizon each pass.
 
@@ -147,12 +148,17 @@ def picard_literal(inst, net, proc, max_iters=None, alpha_init=None, record=Fals
     confirming pass;
     Theorem B.1: with s >= every retailer capacity and x0 > s, alpha^k equals
     the sequential path for every k >= 2R + 1 (R replenishments of the
-    sequential path), and for k >= 1 when R = 0."""
+    sequential path), and for k >= 1 when R = 0.
+
+    window > 0: the max_steps window of Appendix A.3 in steps (see
+    owmr_oracle.c).  Pins: fixed point = sequential path for every window; a
+    window >= T gives the unwindowed iterates; one processor on a path whose
+    every action is nonzero takes exactly 2 ceil(T / window) passes."""
     return _run_picard("orc_owmr_picard_literal", inst, net, proc, max_iters, alpha_init,
-                       record, [])
+                       record, [], window)
 
 
-def picard_walk(inst, net, proc, max_iters=None, alpha_init=None, record=False):
+def picard_walk(inst, net, proc, max_iters=None, alpha_init=None, record=False, window=0):
     """The same iteration through prefix quantities of the cache and a walk of
     each processor's own steps (the organisation the GPU path uses), with
     memoised policy calls.  Pins: every iterate equal to picard_literal's."""
@@ -160,7 +166,7 @@ def picard_walk(inst, net, proc, max_iters=None, alpha_init=None, record=False):
     xf = np.zeros(N + 1, np.int32)
     st = np.zeros(4, np.int64)
     out = _run_picard("orc_owmr_picard_walk", inst, net, proc, max_iters, alpha_init, record,
-                      [xf, st])
+                      [xf, st], window)
     out.update(x_final=xf, R=int(st[0]), lost=int(st[1]), shipped=int(st[2]))
     return out
 

@@ -188,6 +188,23 @@ static int check_procs(int N, int P, const int32_t* proc) {
     return OK;
 }
 
+/* The max_steps window (Appendix A.3).  A pass evaluates the policy only at
+ * steps t < w + window; later steps keep their cached actions.  w starts at 0;
+ * after a pass that changed the cache, w is the first changed step; after a
+ * pass that changed nothing, w moves to the end of the evaluated range, and the
+ * iteration ends once that range covered the horizon.  window = 0: no window. */
+static int window_end(int T, int w, int window) {
+    if (window <= 0) return T;
+    const long long e = (long long)w + window;
+    return e < T ? (int)e : T;
+}
+
+static int first_change(const int32_t* a, const int32_t* b, int T) {
+    for (int t = 0; t < T; ++t)
+        if (a[t] != b[t]) return t;
+    return -1;
+}
+
 /* Algorithm 1, literally: every pass, every processor replays the whole horizon
  * from s_1 and calls the policy at each of its own steps.  init = alpha^0 (NULL:
  * q = 0, r = 0 everywhere).  record (optional, [max_iters][T]) receives alpha^k.
@@ -197,8 +214,8 @@ int orc_owmr_picard_literal(int T, int N, const int32_t* ret, const int32_t* dem
                             const int32_t* Sl, int X0, int s, int S, int H, const uint16_t* W1,
                             const uint16_t* b1, const uint16_t* W2, const uint16_t* b2,
                             const uint16_t* w3, const uint16_t* b3, int P, const int32_t* proc,
-                            int max_iters, const int32_t* init, int32_t* act, int32_t* iters,
-                            int32_t* record, int64_t* evals_out) {
+                            int max_iters, int window, const int32_t* init, int32_t* act,
+                            int32_t* iters, int32_t* record, int64_t* evals_out) {
     Model M;
     int e = setup(&M, T, N, ret, dem, ex, cap, x0r, sl, Sl, X0, s, S, H, W1, b1, W2, b2, w3, b3);
     if (e) return e;
@@ -208,9 +225,11 @@ int orc_owmr_picard_literal(int T, int N, const int32_t* ret, const int32_t* dem
     int32_t* x = (int32_t*)malloc(sizeof(int32_t) * N);
     if (init) memcpy(alpha, init, sizeof(int32_t) * T);
     long long evals = 0;
-    int k = 0, status = ERR_NOT_CONVERGED;
+    int k = 0, status = ERR_NOT_CONVERGED, w = 0;
     while (k < max_iters) {
         ++k;
+        const int whi = window_end(T, w, window);
+        memcpy(next, alpha, sizeof(int32_t) * T);
         for (int m = 0; m < P; ++m) {
             memcpy(x, x0r, sizeof(int32_t) * N);
             long long x0 = X0;
@@ -218,7 +237,7 @@ int orc_owmr_picard_literal(int T, int N, const int32_t* ret, const int32_t* dem
                 const int n = ret[t], d = dem[t];
                 const int y = x[n] > d ? x[n] - d : 0;
                 int q, r;
-                if (proc[n] == m) {
+                if (proc[n] == m && t < whi) {
                     q = retailer_q(&M, n, y, d, ex[t], &evals);
                     r = x0 - q <= s;
                     next[t] = 2 * q + r;
@@ -232,9 +251,10 @@ int orc_owmr_picard_literal(int T, int N, const int32_t* ret, const int32_t* dem
             }
         }
         if (record) memcpy(record + (size_t)(k - 1) * T, next, sizeof(int32_t) * T);
-        const int same = memcmp(alpha, next, sizeof(int32_t) * T) == 0;
+        const int fc = first_change(alpha, next, T);
         memcpy(alpha, next, sizeof(int32_t) * T);
-        if (same) { status = OK; break; }
+        if (fc < 0 && whi >= T) { status = OK; break; }
+        w = fc >= 0 ? fc : whi;
     }
     memcpy(act, alpha, sizeof(int32_t) * T);
     *iters = k;
@@ -255,14 +275,16 @@ int orc_owmr_picard_literal(int T, int N, const int32_t* ret, const int32_t* dem
  * with ta = -1, x0(0) = X0 before the first own step.  Each processor then walks
  * only its own steps in time order.  A policy call whose input y (and step) is
  * the same as at the previous evaluation of that step reuses its result (the
- * policy is deterministic); evals_out counts the calls actually made. */
+ * policy is deterministic); evals_out counts the calls actually made.  With a
+ * window, a processor stops its walk at the window's end. */
 int orc_owmr_picard_walk(int T, int N, const int32_t* ret, const int32_t* dem, const int32_t* ex,
                          const int32_t* cap, const int32_t* x0r, const int32_t* sl,
                          const int32_t* Sl, int X0, int s, int S, int H, const uint16_t* W1,
                          const uint16_t* b1, const uint16_t* W2, const uint16_t* b2,
                          const uint16_t* w3, const uint16_t* b3, int P, const int32_t* proc,
-                         int max_iters, const int32_t* init, int32_t* act, int32_t* iters,
-                         int32_t* record, int64_t* evals_out, int32_t* xfin, int64_t* stats) {
+                         int max_iters, int window, const int32_t* init, int32_t* act,
+                         int32_t* iters, int32_t* record, int64_t* evals_out, int32_t* xfin,
+                         int64_t* stats) {
     Model M;
     int e = setup(&M, T, N, ret, dem, ex, cap, x0r, sl, Sl, X0, s, S, H, W1, b1, W2, b2, w3, b3);
     if (e) return e;
@@ -290,9 +312,10 @@ int orc_owmr_picard_walk(int T, int N, const int32_t* ret, const int32_t* dem, c
     for (int t = 0; t < T; ++t) memo_y[t] = -1;
     if (init) memcpy(alpha, init, sizeof(int32_t) * T);
     long long evals = 0, lost = 0, shipped = 0;
-    int k = 0, status = ERR_NOT_CONVERGED;
+    int k = 0, status = ERR_NOT_CONVERGED, w = 0;
     while (k < max_iters) {
         ++k;
+        const int whi = window_end(T, w, window);
         /* prefix quantities of the cache */
         Qc[0] = 0; D[0] = 0; LR[0] = -1;
         for (int t = 0; t < T; ++t) {
@@ -307,7 +330,7 @@ int orc_owmr_picard_walk(int T, int N, const int32_t* ret, const int32_t* dem, c
         for (int m = 0; m < P; ++m) {
             long long x0a = X0;   /* x0 just after the previous own step */
             int ta = -1;
-            for (int i = off[m]; i < off[m + 1]; ++i) {
+            for (int i = off[m]; i < off[m + 1] && own[i] < whi; ++i) {
                 const int t = own[i], n = ret[t], d = dem[t];
                 long long x0;
                 if (LR[t] > ta) x0 = (long long)S - D[t];
@@ -332,9 +355,10 @@ int orc_owmr_picard_walk(int T, int N, const int32_t* ret, const int32_t* dem, c
             }
         }
         if (record) memcpy(record + (size_t)(k - 1) * T, next, sizeof(int32_t) * T);
-        const int same = memcmp(alpha, next, sizeof(int32_t) * T) == 0;
+        const int fc = first_change(alpha, next, T);
         memcpy(alpha, next, sizeof(int32_t) * T);
-        if (same) { status = OK; break; }
+        if (fc < 0 && whi >= T) { status = OK; break; }
+        w = fc >= 0 ? fc : whi;
     }
     memcpy(act, alpha, sizeof(int32_t) * T);
     *iters = k;

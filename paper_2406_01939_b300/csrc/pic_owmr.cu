@@ -61,13 +61,14 @@ pic_status fail(pic_status s, const char* fmt, ...) {
 struct OwCtrl {
     Ctrl c;
     int changed[3];
-    int pad;
+    int fct[3];  // first changed step of the pass (INT_MAX: none)
     long long lost[3], shipped[3], R[3];
     unsigned long long evals, rounds;
 };
 
 struct OwArgs {
     int T, N, P, B, ngroups, H, X0, s, S, ntiles, max_iters, rp;  // rp = ceil(N / P)
+    int window;                                                   // max_steps, 0 = none
     long long timeout_ns;
     const int32_t *cap, *sl, *Sl, *x0r;
     const int4* rec;        // interleaved [rows][32]: {t, n, d, e}, t = -1 pads
@@ -171,72 +172,234 @@ struct __align__(16) OwSmem {
     Mono ws[kOwThreads / 32 + 1];
     int feat_y[kLanes], feat_d[kLanes], feat_e[kLanes], feat_base[kLanes], feat_room[kLanes];
     int qout[kLanes];
-    int pend_any, pend_rows;
+    int rowidx[kLanes];
+    int pend_any, pend_rows, all_done, abort;
+    unsigned long long mbar[2];
 };
 
-// One batched round of the network for the rows flagged in `rows` (bit b =
-// lane b).  Every output is computed in the order documented in pic_owmr.h.
-// h1s [H][32] (k-major), zpart [32][H/8], W1s [3][H], b1s/b2s/w3s [H] staged floats.
-__device__ void mlp_round(const OwArgs& a, OwSmem& sm, float* h1s, float* zpart,
-                          const float* W1s, const float* b1s, const float* b2s, const float* w3s,
-                          unsigned rows) {
-    const int H = a.H, ncg = H >> 3;
-    for (int idx = threadIdx.x; idx < H * kLanes; idx += kOwThreads) {
-        const int k = idx >> 5, b = idx & 31;
+// ------------------------------------------------------------------ W2 staging
+// W2 streams through shared memory in chunks of kKc rows (kKc * H BF16) moved
+// by bulk asynchronous copies, kNbuf buffers deep.  Chunk number `seq` (counted
+// over the CTA's life, identically in every thread) uses buffer seq % kNbuf and
+// completes phase (seq / kNbuf) & 1 of that buffer's mbarrier.
+constexpr int kKc = 32;
+constexpr int kNbuf = 2;
+
+struct NetCtx {
+    float *h1s, *zpart, *W1s, *b1s, *b2s, *w3s;
+    uint16_t* w2buf;  // [kNbuf][kKc][H]
+    unsigned long long* mbar;
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void w2_issue(const NetCtx& nc, const uint16_t* W2, int H, int chunk,
+                                         unsigned seq) {
+    const int buf = seq % kNbuf;
+    const unsigned bytes = (unsigned)(kKc * H * 2);
+    unsigned long long* b = nc.mbar + buf;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(nc.w2buf + (size_t)buf * kKc * H)),
+        "l"(W2 + (size_t)chunk * kKc * H), "r"(bytes), "r"(smem_u32(b))
+        : "memory");
+}
+
+// Wait for chunk `seq`; a wait past the kernel's deadline records a timeout
+// and returns (the grid barrier then ends the kernel).
+__device__ __forceinline__ void w2_wait(const NetCtx& nc, unsigned seq, OwCtrl* oc,
+                                        unsigned long long deadline) {
+    unsigned long long* b = nc.mbar + (seq % kNbuf);
+    const unsigned par = (seq / kNbuf) & 1u;
+    for (unsigned it = 1;; ++it) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(smem_u32(b)), "r"(par)
+            : "memory");
+        if (ok) return;
+        if ((it & 1023u) == 0 && globaltimer_ns() > deadline) {
+            atomicCAS(&oc->c.err, 0, (int)PIC_ERR_TIMEOUT);
+            return;
+        }
+    }
+}
+
+// Layer 2 for row groups of RPT compacted rows, CPT columns per thread
+// (H / CPT threads per row group): acc = b2_j, then one fma per k in
+// increasing k (the reference order); relu(acc) is written to the h2 table
+// [row][H], which takes the place of h1s once every thread passed the last
+// chunk.
+template <int RPT, int CPT>
+__device__ void net_layer2(const NetCtx& nc, const uint16_t* W2, int H, int nrowg,
+                           unsigned& wuse, OwCtrl* oc, unsigned long long deadline) {
+    const int tpr = H / CPT, nch = H / kKc;
+    const bool active = (int)threadIdx.x < nrowg * tpr;
+    const int rg = active ? (int)threadIdx.x / tpr : 0;
+    const int col0 = ((int)threadIdx.x - rg * tpr) * CPT;
+    float acc[RPT][CPT];
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+        const float bb = active ? nc.b2s[col0 + c] : 0.f;
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) acc[r][c] = bb;
+    }
+    for (int ch = 0; ch < nch; ++ch) {
+        const unsigned seq = wuse + ch;
+        w2_wait(nc, seq, oc, deadline);
+        if (active) {
+            const uint16_t* wb = nc.w2buf + (size_t)(seq % kNbuf) * kKc * H + col0;
+            const float* hb = nc.h1s + (size_t)ch * kKc * kLanes + rg * RPT;
+#pragma unroll 4
+            for (int kk = 0; kk < kKc; ++kk) {
+                float wf[CPT], hf[RPT];
+                if constexpr (CPT == 8) {
+                    const uint4 w = *reinterpret_cast<const uint4*>(wb + (size_t)kk * H);
+                    wf[0] = bf_lo(w.x); wf[1] = bf_hi(w.x); wf[2] = bf_lo(w.y); wf[3] = bf_hi(w.y);
+                    wf[4] = bf_lo(w.z); wf[5] = bf_hi(w.z); wf[6] = bf_lo(w.w); wf[7] = bf_hi(w.w);
+                } else if constexpr (CPT == 4) {
+                    const uint2 w = *reinterpret_cast<const uint2*>(wb + (size_t)kk * H);
+                    wf[0] = bf_lo(w.x); wf[1] = bf_hi(w.x); wf[2] = bf_lo(w.y); wf[3] = bf_hi(w.y);
+                } else {
+                    const unsigned w = *reinterpret_cast<const unsigned*>(wb + (size_t)kk * H);
+                    wf[0] = bf_lo(w); wf[1] = bf_hi(w);
+                }
+                if constexpr (RPT == 8) {
+                    const float4 h0 = *reinterpret_cast<const float4*>(hb + kk * kLanes);
+                    const float4 h1 = *reinterpret_cast<const float4*>(hb + kk * kLanes + 4);
+                    hf[0] = h0.x; hf[1] = h0.y; hf[2] = h0.z; hf[3] = h0.w;
+                    hf[4] = h1.x; hf[5] = h1.y; hf[6] = h1.z; hf[7] = h1.w;
+                } else {
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r) hf[r] = hb[kk * kLanes + r];
+                }
+#pragma unroll
+                for (int r = 0; r < RPT; ++r)
+#pragma unroll
+                    for (int c = 0; c < CPT; ++c) acc[r][c] = fmaf(wf[c], hf[r], acc[r][c]);
+            }
+        }
+        __syncthreads();  // buffer seq % kNbuf is free again
+        if (threadIdx.x == 0 && ch + kNbuf < nch) w2_issue(nc, W2, H, ch + kNbuf, seq + kNbuf);
+    }
+    wuse += nch;
+    if (active) {
+#pragma unroll
+        for (int r = 0; r < RPT; ++r)
+#pragma unroll
+            for (int c = 0; c < CPT; ++c)
+                nc.h1s[(size_t)(rg * RPT + r) * H + col0 + c] = acc[r][c] > 0.f ? acc[r][c] : 0.f;
+    }
+    __syncthreads();
+}
+
+// One batched round of the network for the lanes flagged in `rows` (bit b =
+// lane b, features in sm.feat_*).  The pending lanes are compacted; layer 1
+// gives h1s [k][row]; layer 2 runs with 8 rows x 2G columns per thread for
+// G = 1, 2 or 4 groups of 8 rows (RPT = 1: one row, 2 columns per thread);
+// then p_g per (row, g) and z = b3 + p_0 + p_1 + ... per row.  Every output
+// follows the order documented in pic_owmr.h.
+template <int RPT>
+__device__ void net_round(const OwArgs& a, OwSmem& sm, const NetCtx& nc, unsigned rows,
+                          unsigned& wuse, unsigned long long deadline) {
+    const int H = a.H, ncg = H >> 3, nch = H / kKc;
+    const int m = __popc(rows);
+    if (threadIdx.x == 0)
+        for (int c = 0; c < kNbuf && c < nch; ++c) w2_issue(nc, a.W2, H, c, wuse + c);
+    if (threadIdx.x < kLanes && ((rows >> threadIdx.x) & 1u))
+        sm.rowidx[__popc(rows & ((1u << threadIdx.x) - 1u))] = threadIdx.x;
+    __syncthreads();
+    const int G = RPT == 1 ? 1 : (m <= 8 ? 1 : (m <= 16 ? 2 : 4));
+    const int nr = RPT * G;  // rows computed
+    for (int idx = threadIdx.x; idx < H * nr; idx += blockDim.x) {
+        const int k = idx / nr, i = idx - k * nr;
         float v = 0.f;
-        if ((rows >> b) & 1u) {
-            float acc = fmaf(W1s[k], (float)sm.feat_y[b], b1s[k]);
-            acc = fmaf(W1s[H + k], (float)sm.feat_d[b], acc);
-            acc = fmaf(W1s[2 * H + k], (float)sm.feat_e[b] * 0.000244140625f, acc);
+        if (i < m) {
+            const int b = sm.rowidx[i];
+            float acc = fmaf(nc.W1s[k], (float)sm.feat_y[b], nc.b1s[k]);
+            acc = fmaf(nc.W1s[H + k], (float)sm.feat_d[b], acc);
+            acc = fmaf(nc.W1s[2 * H + k], (float)sm.feat_e[b] * 0.000244140625f, acc);
             v = acc > 0.f ? acc : 0.f;
         }
-        h1s[idx] = v;
+        nc.h1s[k * kLanes + i] = v;
     }
     __syncthreads();
-    if (threadIdx.x < 4 * ncg) {
-        const int rg = threadIdx.x / ncg, cg = threadIdx.x - rg * ncg;
-        if ((rows >> (8 * rg)) & 0xffu) {
-            float acc[8][8];
+    if (RPT == 1) {
+        net_layer2<1, 2>(nc, a.W2, H, 1, wuse, a.oc, deadline);
+    } else if (G == 1) {
+        net_layer2<RPT, 2>(nc, a.W2, H, 1, wuse, a.oc, deadline);
+    } else if (G == 2) {
+        net_layer2<RPT, 4>(nc, a.W2, H, 2, wuse, a.oc, deadline);
+    } else {
+        net_layer2<RPT, 8>(nc, a.W2, H, 4, wuse, a.oc, deadline);
+    }
+    for (int idx = threadIdx.x; idx < m * ncg; idx += blockDim.x) {
+        const int i = idx / ncg, g = idx - i * ncg;
+        const float* h2 = nc.h1s + (size_t)i * H + 8 * g;
+        float p = 0.f;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const float bb = b2s[8 * cg + c];
-#pragma unroll
-                for (int r = 0; r < 8; ++r) acc[r][c] = bb;
-            }
-            const uint4* wp = reinterpret_cast<const uint4*>(a.W2) + cg;  // row k: H/8 uint4
-            const float4* hp = reinterpret_cast<const float4*>(h1s) + 2 * rg;
-#pragma unroll 4
-            for (int k = 0; k < H; ++k) {
-                const uint4 w = __ldg(wp + (size_t)k * ncg);
-                const float4 h0 = hp[k * 8], h1 = hp[k * 8 + 1];
-                const float wf[8] = {bf_lo(w.x), bf_hi(w.x), bf_lo(w.y), bf_hi(w.y),
-                                     bf_lo(w.z), bf_hi(w.z), bf_lo(w.w), bf_hi(w.w)};
-                const float hf[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
-#pragma unroll
-                for (int r = 0; r < 8; ++r)
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(wf[c], hf[r], acc[r][c]);
-            }
-#pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                float p = 0.f;
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const float h = acc[r][c] > 0.f ? acc[r][c] : 0.f;
-                    p = fmaf(w3s[8 * cg + c], h, p);
-                }
-                zpart[(8 * rg + r) * ncg + cg] = p;
-            }
-        }
+        for (int c = 0; c < 8; ++c) p = fmaf(nc.w3s[8 * g + c], h2[c], p);
+        nc.zpart[i * ncg + g] = p;
     }
     __syncthreads();
-    if (threadIdx.x < kLanes && ((rows >> threadIdx.x) & 1u)) {
-        const int b = threadIdx.x;
+    if ((int)threadIdx.x < m) {
+        const int b = sm.rowidx[threadIdx.x];
         float z = bf1(a.b3[0]);
-        for (int g = 0; g < ncg; ++g) z = __fadd_rn(z, zpart[b * ncg + g]);
+        for (int g = 0; g < ncg; ++g) z = __fadd_rn(z, nc.zpart[threadIdx.x * ncg + g]);
         sm.qout[b] = q_of(sm.feat_base[b], sm.feat_room[b], z);
     }
     __syncthreads();
+}
+
+// Carve the network's shared memory after OwSmem: h1s [H][32] (h2 [32][H]
+// later), zpart [32][H/8], W1s [3][H], b1s, b2s, w3s [H], W2 buffers; stage
+// the small weights and initialise the mbarriers.
+__device__ NetCtx net_setup(const OwArgs& a, unsigned char* smem_raw, OwSmem& sm) {
+    NetCtx nc;
+    const int H = a.H;
+    nc.h1s = reinterpret_cast<float*>(smem_raw + sizeof(OwSmem));
+    nc.zpart = nc.h1s + H * kLanes;
+    nc.W1s = nc.zpart + kLanes * (H >> 3);
+    nc.b1s = nc.W1s + 3 * H;
+    nc.b2s = nc.b1s + H;
+    nc.w3s = nc.b2s + H;
+    nc.w2buf = reinterpret_cast<uint16_t*>(nc.w3s + H);
+    nc.mbar = sm.mbar;
+    for (int i = threadIdx.x; i < H; i += blockDim.x) {
+        nc.W1s[i] = bf1(a.W1[i]);
+        nc.W1s[H + i] = bf1(a.W1[H + i]);
+        nc.W1s[2 * H + i] = bf1(a.W1[2 * H + i]);
+        nc.b1s[i] = bf1(a.b1[i]);
+        nc.b2s[i] = bf1(a.b2[i]);
+        nc.w3s[i] = bf1(a.w3[i]);
+    }
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kNbuf; ++i) mbar_init(nc.mbar + i, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    return nc;
+}
+
+size_t net_smem(int H) {
+    return sizeof(float) * ((size_t)H * kLanes + (size_t)kLanes * (H / 8) + 6 * (size_t)H) +
+           (size_t)kNbuf * kKc * H * 2;
 }
 
 // ------------------------------------------------------------------ Picard kernel
@@ -244,32 +407,22 @@ template <bool NET>
 __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     OwSmem& sm = *reinterpret_cast<OwSmem*>(smem_raw);
-    float* h1s = reinterpret_cast<float*>(smem_raw + sizeof(OwSmem));  // [H][32]
-    float* zpart = h1s + (NET ? a.H * kLanes : 0);                     // [32][H/8]
-    float* W1s = zpart + (NET ? kLanes * (a.H >> 3) : 0);              // [3][H]
-    float* b1s = W1s + (NET ? 3 * a.H : 0);
-    float* b2s = b1s + (NET ? a.H : 0);
-    float* w3s = b2s + (NET ? a.H : 0);
     OwCtrl* oc = a.oc;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned long long deadline = globaltimer_ns() + (unsigned long long)a.timeout_ns;
-
-    if (NET) {
-        for (int i = tid; i < a.H; i += kOwThreads) {
-            W1s[i] = bf1(a.W1[i]);
-            W1s[a.H + i] = bf1(a.W1[a.H + i]);
-            W1s[2 * a.H + i] = bf1(a.W1[2 * a.H + i]);
-            b1s[i] = bf1(a.b1[i]);
-            b2s[i] = bf1(a.b2[i]);
-            w3s[i] = bf1(a.w3[i]);
-        }
-    }
+    NetCtx nc{};
+    unsigned wuse = 0;  // W2 chunks consumed by this CTA
+    if (NET) nc = net_setup(a, smem_raw, sm);
     // contiguous tile range of this CTA (phases A and B)
     const int tpc = (a.ntiles + gridDim.x - 1) / gridDim.x;
     const int tile0 = min(a.ntiles, (int)blockIdx.x * tpc), tile1 = min(a.ntiles, tile0 + tpc);
+    if (blockIdx.x == 0 && tid == 0)
+        for (int i = 0; i < 3; ++i) oc->fct[i] = INT_MAX;
+    int w = 0;  // window start (identical in every CTA)
 
     for (int pass = 1;; ++pass) {
         const int slot = pass % 3;
+        const int whi = a.window > 0 ? (int)min((long long)a.T, (long long)w + a.window) : a.T;
         // ---------------- phase A: tile summaries
         for (int tile = tile0; tile < tile1; ++tile) {
             const long long base = (long long)tile * kTile + tid * kItems;
@@ -288,6 +441,7 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
         if (blockIdx.x == 0 && tid == 0) {
             const int nx = (pass + 1) % 3;
             oc->changed[nx] = 0;
+            oc->fct[nx] = INT_MAX;
             oc->lost[nx] = oc->shipped[nx] = oc->R[nx] = 0;
         }
         if (tile0 < tile1 || (blockIdx.x == 0 && a.T == 0)) {
@@ -328,7 +482,7 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
         }
         if (!grid_sync(&oc->c, deadline)) break;
         // ---------------- phase C: walks
-        int my_changed = 0;
+        int my_changed = 0, my_first = INT_MAX;
         long long my_lost = 0, my_ship = 0, my_R = 0;
         unsigned long long my_evals = 0, my_rounds = 0;
         for (int g = blockIdx.x; g < a.ngroups; g += gridDim.x) {
@@ -340,7 +494,7 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
                 if (l < nb && n < a.N) sm.xs[i] = a.x0r[n];
             }
             // per-lane walk state (warp 0)
-            int x0a = a.X0, ta = -1, qc_after = 0;
+            int x0a = a.X0, ta = -1, qc_after = 0, done = 0;
             int pend = 0, pt = 0, px0 = 0, py = 0, pold = 0, pqc = 0, pslot = 0;
             const long long row0 = a.gbase[g], row1 = a.gbase[g + 1];
             for (long long r0 = row0; r0 < row1; r0 += kCh) {
@@ -377,6 +531,7 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
                                 const int nv = 2 * q + r;
                                 if (nv != pold) {
                                     a.act[pt] = nv;
+                                    if (!my_changed) my_first = pt;
                                     ++my_changed;
                                 }
                                 pend = 0;
@@ -384,8 +539,9 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
                             }
                             while (pos < kCh) {
                                 const int4 rc = sm.rec[pos][lane];
-                                if (rc.x < 0) {
+                                if (rc.x < 0 || rc.x >= whi) {  // list end or window end
                                     pos = kCh;
+                                    done = 1;
                                     break;
                                 }
                                 const int t = rc.x, n = rc.y, d = rc.z;
@@ -428,26 +584,31 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
                                 const int nv = 2 * q + r;
                                 if (nv != pr.w) {
                                     a.act[t] = nv;
+                                    if (!my_changed) my_first = t;
                                     ++my_changed;
                                 }
                                 ++pos;
                             }
                         }
                         const unsigned rows = __ballot_sync(kFull, parked);
+                        const bool all = __all_sync(kFull, done || lane >= nb);
                         if (lane == 0) {
                             sm.pend_rows = (int)rows;
                             sm.pend_any = rows != 0u;
+                            sm.all_done = all;
+                            sm.abort = ld_volatile(&oc->c.err) != 0;  // one CTA-wide decision
                         }
                     }
                     __syncthreads();
-                    if (!NET || !sm.pend_any) break;
+                    if (!NET || !sm.pend_any || sm.abort) break;
                     const unsigned rows = (unsigned)sm.pend_rows;
-                    mlp_round(a, sm, h1s, zpart, W1s, b1s, b2s, w3s, rows);
+                    net_round<8>(a, sm, nc, rows, wuse, deadline);
                     if (tid == 0) {
                         my_evals += __popc(rows);
                         ++my_rounds;
                     }
                 }
+                if (sm.all_done || sm.abort) break;  // lists or window done, or a wait timed out
             }
             __syncthreads();
             for (int i = tid; i < a.rp * kLanes; i += kOwThreads) {
@@ -459,10 +620,14 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
         // CTA totals
         if (warp == 0) {
             const int ch = __reduce_add_sync(kFull, my_changed);
+            const int fmin = __reduce_min_sync(kFull, my_first);
             const long long lo = warp_sum_i64(my_lost), sh = warp_sum_i64(my_ship),
                             rr = warp_sum_i64(my_R);
             if (lane == 0) {
-                if (ch) atomicAdd(&oc->changed[slot], ch);
+                if (ch) {
+                    atomicAdd(&oc->changed[slot], ch);
+                    atomicMin(&oc->fct[slot], fmin);
+                }
                 if (lo) atomicAdd((unsigned long long*)&oc->lost[slot], (unsigned long long)lo);
                 if (sh) atomicAdd((unsigned long long*)&oc->shipped[slot], (unsigned long long)sh);
                 if (rr) atomicAdd((unsigned long long*)&oc->R[slot], (unsigned long long)rr);
@@ -474,112 +639,94 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
         }
         if (!grid_sync(&oc->c, deadline)) break;
         const int changed = ld_volatile(&oc->changed[slot]);
-        if (changed == 0 || pass >= a.max_iters) {
+        const bool fixed = changed == 0 && whi >= a.T;
+        if (fixed || pass >= a.max_iters) {
             if (blockIdx.x == 0 && tid == 0) {
                 oc->c.iters = pass;
-                oc->c.converged = changed == 0;
+                oc->c.converged = fixed;
                 oc->c.pad0 = slot;
             }
             break;
         }
+        w = changed ? ld_volatile(&oc->fct[slot]) : whi;
     }
 }
 
 // ------------------------------------------------------------------ sequential baseline
-// One CTA walks the horizon one step at a time.  Network: thread k computes h1_k,
-// thread j the layer-2 unit j (its k chain), thread g the partial p_g, thread 0
-// the sum and the state update.  Without a network one warp runs the steps.
+// One CTA walks the horizon one step at a time.  With a network, thread 0
+// prepares each step and the CTA evaluates it as a one-row round (W2 streamed
+// through shared memory, 2 layer-2 units per thread); without one, one warp
+// runs the steps.  Retailer stock sits in shared memory when N <= 4096.
 template <bool NET>
-__global__ void __launch_bounds__(kMaxH) k_owmr_seq(OwArgs a, int32_t* xs_g, int use_smem) {
+__global__ void __launch_bounds__(kOwThreads, 1) k_owmr_seq(OwArgs a, int32_t* xs_g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    int* xs = use_smem ? reinterpret_cast<int*>(smem_raw) : xs_g;
-    float* h1s = reinterpret_cast<float*>(smem_raw + (use_smem ? ((a.N + 3) & ~3) * 4 : 0));
-    float* h2s = h1s + kMaxH;
-    float* zp = h2s + kMaxH;
-    __shared__ int s_y, s_d, s_e, s_base, s_room;
+    OwSmem& sm = *reinterpret_cast<OwSmem*>(smem_raw);
+    int* xs = a.N <= kMaxSlots ? sm.xs : xs_g;
     const int tid = threadIdx.x;
+    const unsigned long long deadline = globaltimer_ns() + (unsigned long long)a.timeout_ns;
+    NetCtx nc{};
+    unsigned wuse = 0;
+    if (NET) nc = net_setup(a, smem_raw, sm);
     for (int n = tid; n < a.N; n += blockDim.x) xs[n] = a.x0r[n];
     __syncthreads();
     int x0 = a.X0;
     long long lost = 0, ship = 0, R = 0;
     unsigned long long evals = 0;
     if (!NET) {
-        if (tid >= 32) return;
-        for (long long t0 = 0; t0 < a.T; t0 += 32) {
-            const long long tt = t0 + tid;
-            const int4 rc = tt < a.T ? a.rec[tt] : make_int4(-1, 0, 0, 0);
-            for (int j = 0; j < 32 && t0 + j < a.T; ++j) {
-                const int n = __shfl_sync(kFull, rc.y, j), d = __shfl_sync(kFull, rc.z, j);
-                if (tid == 0) {
-                    const int xn = xs[n];
-                    const int y = xn > d ? xn - d : 0;
-                    lost += d > xn ? d - xn : 0;
-                    const int base = retailer_base(y, a.sl[n], a.Sl[n]);
-                    const int room = a.cap[n] - y;
-                    const int q = base < room ? base : room;
-                    const int r = x0 - q <= a.s;
-                    const int recv = q < x0 ? q : x0;
-                    xs[n] = y + recv;
-                    ship += recv;
-                    R += r;
-                    x0 = r ? a.S : (x0 > q ? x0 - q : 0);
-                    a.act[t0 + j] = 2 * q + r;
+        if (tid < 32) {
+            for (long long t0 = 0; t0 < a.T; t0 += 32) {
+                const long long tt = t0 + tid;
+                const int4 rc = tt < a.T ? a.rec[tt] : make_int4(-1, 0, 0, 0);
+                for (int j = 0; j < 32 && t0 + j < a.T; ++j) {
+                    const int n = __shfl_sync(kFull, rc.y, j), d = __shfl_sync(kFull, rc.z, j);
+                    if (tid == 0) {
+                        const int xn = xs[n];
+                        const int y = xn > d ? xn - d : 0;
+                        lost += d > xn ? d - xn : 0;
+                        const int base = retailer_base(y, a.sl[n], a.Sl[n]);
+                        const int room = a.cap[n] - y;
+                        const int q = base < room ? base : room;
+                        const int r = x0 - q <= a.s;
+                        const int recv = q < x0 ? q : x0;
+                        xs[n] = y + recv;
+                        ship += recv;
+                        R += r;
+                        x0 = r ? a.S : (x0 > q ? x0 - q : 0);
+                        a.act[t0 + j] = 2 * q + r;
+                    }
                 }
             }
         }
     } else {
-        const int H = a.H;
         for (long long t = 0; t < a.T; ++t) {
+            int n = 0, y = 0;
             if (tid == 0) {
                 const int4 rc = a.rec[t];
-                const int n = rc.y, d = rc.z;
+                n = rc.y;
+                const int d = rc.z;
                 const int xn = xs[n];
-                const int y = xn > d ? xn - d : 0;
+                y = xn > d ? xn - d : 0;
                 lost += d > xn ? d - xn : 0;
-                s_y = y;
-                s_d = d;
-                s_e = rc.w;
-                s_base = retailer_base(y, a.sl[n], a.Sl[n]);
-                s_room = a.cap[n] - y;
+                sm.feat_y[0] = y;
+                sm.feat_d[0] = d;
+                sm.feat_e[0] = rc.w;
+                sm.feat_base[0] = retailer_base(y, a.sl[n], a.Sl[n]);
+                sm.feat_room[0] = a.cap[n] - y;
             }
             __syncthreads();
-            if (tid < H) {
-                float acc = fmaf(bf1(a.W1[tid]), (float)s_y, bf1(a.b1[tid]));
-                acc = fmaf(bf1(a.W1[H + tid]), (float)s_d, acc);
-                acc = fmaf(bf1(a.W1[2 * H + tid]), (float)s_e * 0.000244140625f, acc);
-                h1s[tid] = acc > 0.f ? acc : 0.f;
-            }
-            __syncthreads();
-            if (tid < H) {
-                float acc = bf1(a.b2[tid]);
-                const uint16_t* col = a.W2 + tid;
-#pragma unroll 8
-                for (int k = 0; k < H; ++k) acc = fmaf(bf1(__ldg(col + (size_t)k * H)), h1s[k], acc);
-                h2s[tid] = acc > 0.f ? acc : 0.f;
-            }
-            __syncthreads();
-            if (tid < (H >> 3)) {
-                float p = 0.f;
-#pragma unroll
-                for (int c = 0; c < 8; ++c) p = fmaf(bf1(a.w3[8 * tid + c]), h2s[8 * tid + c], p);
-                zp[tid] = p;
-            }
-            __syncthreads();
+            net_round<1>(a, sm, nc, 1u, wuse, deadline);
             if (tid == 0) {
-                float z = bf1(a.b3[0]);
-                for (int g = 0; g < (H >> 3); ++g) z = __fadd_rn(z, zp[g]);
-                const int q = q_of(s_base, s_room, z);
-                const int n = a.rec[t].y;
+                const int q = sm.qout[0];
                 const int r = x0 - q <= a.s;
                 const int recv = q < x0 ? q : x0;
-                xs[n] = s_y + recv;
+                xs[n] = y + recv;
                 ship += recv;
                 R += r;
                 x0 = r ? a.S : (x0 > q ? x0 - q : 0);
                 a.act[t] = 2 * q + r;
                 ++evals;
             }
-            __syncthreads();
+            if (ld_volatile(&a.oc->c.err)) break;
         }
     }
     __syncthreads();
@@ -773,11 +920,7 @@ pic_status build_tables(pic_owmr* h, int P, cudaStream_t st, int* launches) {
     return ps;
 }
 
-size_t picard_smem(int H) {
-    size_t s = sizeof(OwSmem);
-    if (H) s += sizeof(float) * ((size_t)H * kLanes + (size_t)kLanes * (H / 8) + 6 * (size_t)H);
-    return s;
-}
+size_t picard_smem(int H) { return sizeof(OwSmem) + (H ? net_smem(H) : 0); }
 
 }  // namespace
 
@@ -883,8 +1026,10 @@ pic_status pic_owmr_simulate(pic_owmr* h, const pic_owmr_policy* pol, const pic_
         return fail(PIC_ERR_INVALID_ARG, "network needs W1, b1, W2, b2, w3, b3 (device)");
     if (H && ((uintptr_t)pol->W2 & 15u))
         return fail(PIC_ERR_INVALID_ARG, "W2 must be 16-byte aligned");
-    if (o->num_procs < 0 || o->num_procs > h->N || o->max_iters < 0 || o->timeout_ns < 0)
-        return fail(PIC_ERR_INVALID_ARG, "need 0 <= num_procs <= N, max_iters >= 0, timeout >= 0");
+    if (o->num_procs < 0 || o->num_procs > h->N || o->max_iters < 0 || o->timeout_ns < 0 ||
+        o->max_steps < 0)
+        return fail(PIC_ERR_INVALID_ARG,
+                    "need 0 <= num_procs <= N, max_iters >= 0, timeout >= 0, max_steps >= 0");
     const int P = o->num_procs ? o->num_procs : h->N;
     const int rp = (h->N + P - 1) / P;
     if (o->mode == PIC_MODE_PICARD && rp > kMaxSlots / kLanes)
@@ -915,7 +1060,12 @@ pic_status pic_owmr_simulate(pic_owmr* h, const pic_owmr_policy* pol, const pic_
     OwArgs a{};
     a.T = h->T; a.N = h->N; a.P = P; a.H = H; a.X0 = h->X0; a.s = h->s; a.S = h->S;
     a.ntiles = h->ntiles; a.rp = rp;
-    a.max_iters = o->max_iters ? o->max_iters : (h->T < INT_MAX ? h->T + 1 : INT_MAX);
+    a.window = o->max_steps;
+    {
+        long long cap = (long long)h->T + 1;
+        if (a.window > 0) cap += (long long)h->T / a.window + 1;
+        a.max_iters = o->max_iters ? o->max_iters : (int)(cap < INT_MAX ? cap : INT_MAX);
+    }
     a.timeout_ns = o->timeout_ns ? o->timeout_ns : 60000000000ll;
     a.cap = h->cap; a.sl = h->sl; a.Sl = h->Sl; a.x0r = h->x0r;
     a.act = h->act; a.pre = h->pre; a.tsum = h->tsum; a.xfin = h->xfin; a.oc = h->oc;
@@ -937,14 +1087,13 @@ pic_status pic_owmr_simulate(pic_owmr* h, const pic_owmr_policy* pol, const pic_
         ++launches;
     } else {
         a.rec = h->trec;
-        const int use_smem = h->N <= 16384;
-        const size_t smem = (use_smem ? (size_t)((h->N + 3) & ~3) * 4 : 0) +
-                            (H ? sizeof(float) * (2 * kMaxH + kMaxH / 8) : 0);
+        const bool use_smem = h->N <= kMaxSlots;
+        const size_t smem = picard_smem(H);
         int32_t* xs_g = nullptr;
         if (!use_smem) CU(cudaMallocAsync(&xs_g, (size_t)h->N * 4, st));
-        void (*kern)(OwArgs, int32_t*, int) = H ? k_owmr_seq<true> : k_owmr_seq<false>;
+        void (*kern)(OwArgs, int32_t*) = H ? k_owmr_seq<true> : k_owmr_seq<false>;
         CU(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<1, H ? kMaxH : 32, smem, st>>>(a, xs_g, use_smem);
+        kern<<<1, kOwThreads, smem, st>>>(a, xs_g);
         CU(cudaGetLastError());
         ++launches;
         if (xs_g) CU(cudaFreeAsync(xs_g, st));

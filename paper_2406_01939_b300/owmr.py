@@ -28,7 +28,8 @@ class pic_owmr_policy(C.Structure):
 
 class pic_owmr_opts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("num_procs", C.c_int32), ("max_iters", C.c_int32),
-                ("flags", C.c_int32), ("alpha_init", P_), ("timeout_ns", C.c_int64)]
+                ("flags", C.c_int32), ("alpha_init", P_), ("timeout_ns", C.c_int64),
+                ("max_steps", C.c_int32)]
 
 
 class pic_owmr_result(C.Structure):
@@ -124,7 +125,7 @@ class DeviceOwmr:
             pass
 
     def simulate(self, net=None, mode="picard", num_procs=0, max_iters=0, alpha_init=None,
-                 timing=False, timeout_ns=0, raise_on_error=True, stream=None):
+                 timing=False, timeout_ns=0, raise_on_error=True, stream=None, max_steps=0):
         """Run the Picard iteration (or the sequential baseline) under the
         retailer rule, with the network `net` (a DeviceOwmrNet, an OwmrNet, or
         None).  Returns device tensors and the call's statistics."""
@@ -136,7 +137,7 @@ class DeviceOwmr:
             init = alpha_init if torch.is_tensor(alpha_init) else _dev_i32(alpha_init, self.device)
         opts = pic_owmr_opts(PIC_MODE_PICARD if mode == "picard" else PIC_MODE_SEQUENTIAL,
                              int(num_procs), int(max_iters), PIC_FLAG_TIMING if timing else 0,
-                             _ptr(init), int(timeout_ns))
+                             _ptr(init), int(timeout_ns), int(max_steps))
         act = torch.empty(max(self.T, 1), dtype=torch.int32, device=self.device)
         state = torch.empty(self.N + 1, dtype=torch.int32, device=self.device)
         st, res = pic_owmr_simulate(self.handle, pol, opts, act, state, PIC_MEM_DEVICE, stream)

@@ -105,6 +105,45 @@ def test_warm_start():
     assert got["iters"] == want["iters"] and got["policy_calls"] == want["evals"]
 
 
+def test_window_bit_exact_and_passes():
+    """The max_steps window: same iterates, passes and network calls as the
+    oracle's windowed walk, for windows from one step to the horizon."""
+    net = synth.make_owmr_net(64, seed=12)
+    for seed, T, N in ((21, 3000, 24), (22, 5000, 70), (23, 777, 5)):
+        inst = rand_inst(seed, T, N, theorem=seed != 22)
+        d = DeviceOwmr(inst)
+        dn = DeviceOwmrNet(net)
+        for W in (1, 37, 500, T):
+            for nn, dd in ((None, None), (net, dn)):
+                seq = ow.seq_sim(inst, nn)
+                want = ow.picard_walk(inst, nn, procs_of(N, N), window=W)
+                got = d.simulate(dd, max_steps=W)
+                np.testing.assert_array_equal(got["actions"].cpu().numpy(), seq["actions"])
+                np.testing.assert_array_equal(got["state"].cpu().numpy(), seq["x_final"])
+                assert got["iters"] == want["iters"], (W, got["iters"], want["iters"])
+                if nn is not None:
+                    assert got["policy_calls"] == want["evals"]
+    inst = rand_inst(24, 1500, 9, theorem=False)
+    d = DeviceOwmr(inst)
+    want = ow.picard_literal(inst, net, procs_of(9, 9), record=True, window=100)
+    for k in range(1, want["iters"] + 1, 3):
+        got = d.simulate(net, max_iters=k, max_steps=100, raise_on_error=False)
+        np.testing.assert_array_equal(got["actions"].cpu().numpy(), want["iterates"][k - 1])
+
+
+def test_window_scaled_base_case():
+    """The base case at a tenth of its size (365,000 steps, 400 stores) with a
+    window of 16,000 steps: the oracle's passes and network calls (each step's
+    network evaluated about once)."""
+    inst, _ = synth.owmr_base(0, T=365_000, N=400, H=64)
+    inst.S = inst.s + 7_000
+    net = synth.make_owmr_net(64, seed=0)
+    want = ow.picard_walk(inst, net, procs_of(400, 400), window=16_000)
+    got = DeviceOwmr(inst).simulate(net, max_steps=16_000)
+    np.testing.assert_array_equal(got["actions"].cpu().numpy(), want["actions"])
+    assert got["iters"] == want["iters"] and got["policy_calls"] == want["evals"]
+
+
 def test_many_groups_per_cta():
     """More processors than 32 per SM: each CTA walks several groups."""
     inst = rand_inst(11, 30000, 6000)

@@ -285,3 +285,46 @@ def test_invalid_inputs():
         ow.seq_sim(bad)
     with pytest.raises(ValueError):
         ow.picard_walk(inst, None, np.array([0, -1], np.int32))
+
+
+def test_window_fixed_point_and_walk_equals_literal():
+    """max_steps window (Appendix A.3): every window reaches the sequential
+    path; the walk gives the literal iteration's iterates pass by pass; a
+    window covering the horizon gives the unwindowed iterates."""
+    rng = np.random.default_rng(41)
+    net = synth.make_owmr_net(64, seed=6)
+    for trial in range(30):
+        N = int(rng.integers(1, 7))
+        inst = random_inst(rng, int(rng.integers(1, 80)), N, theorem=bool(trial % 2))
+        P = int(rng.integers(1, N + 1))
+        proc = rng.permutation(np.arange(N) % P)
+        nn = net if trial % 3 == 0 else None
+        seq = ow.seq_sim(inst, nn)["actions"]
+        for W in (1, 2, 7, int(rng.integers(1, inst.T + 2))):
+            lit = ow.picard_literal(inst, nn, proc, record=True, window=W)
+            wk = ow.picard_walk(inst, nn, proc, record=True, window=W)
+            assert lit["converged"] and (lit["actions"] == seq).all()
+            assert lit["iters"] == wk["iters"] and (lit["iterates"] == wk["iterates"]).all()
+        full = ow.picard_literal(inst, nn, proc, record=True)
+        big = ow.picard_literal(inst, nn, proc, record=True, window=inst.T)
+        assert full["iters"] == big["iters"] and (full["iterates"] == big["iterates"]).all()
+
+
+@pytest.mark.parametrize("T,W", [(1, 1), (10, 3), (64, 8), (100, 7), (99, 100)])
+def test_window_pass_count_closed_form(T, W):
+    """One processor on a path whose every action is nonzero (unit demand,
+    stores reorder up to S_n whenever below it): pass 1 writes the first
+    window, pass 2 confirms it and moves on, so the iteration takes exactly
+    2 ceil(T / W) passes, and alpha^(2j-1) holds the sequential path on
+    [0, min(jW, T)) and zeros after it."""
+    cap = np.array([9, 6, 8])
+    inst = synth.make_owmr(T, 3, seed=T + W, demand="unit", s_loc=cap - 1, S_loc=cap, cap=cap,
+                           s=20, S=200)
+    seq = ow.seq_sim(inst)["actions"]
+    assert (seq > 0).all()
+    out = ow.picard_walk(inst, None, np.zeros(3, np.int32), record=True, window=W)
+    assert out["iters"] == 2 * -(-T // W)
+    for j in range(1, -(-T // W) + 1):
+        it = out["iterates"][2 * j - 2]
+        e = min(j * W, T)
+        assert (it[:e] == seq[:e]).all() and (it[e:] == 0).all()

@@ -14,7 +14,10 @@ orders, N = 32, K = 2,000, R = 200, even index greedy, odd index MLP, one
 persistent launch per step (autotuned chunking, CUDA graph).  --workload
 pg_large: a policy-gradient step over 64 trajectories of T = 2^20 orders (N = 64,
 K = 10,000, R = 1,000, Gumbel-max MLP): the batch simulated by Picard, then the
-REINFORCE gradient (hand-written backward kernel).
+REINFORCE gradient (hand-written backward kernel).  --workload owmr_base: the
+OWMR inventory-control base case of Appendix B.3 (T = 3,650,000 unit demands
+over 4,000 stores, central (s, S) = (1,000, 71,000), width-512 retailer
+network), one processor per store, max_steps window of 80,000 steps.
 
 Prints one JSON line (rank 0).  Under torchrun every rank simulates its own
 trajectory (weak scaling, no collective on the data path).  --impl reference
@@ -83,7 +86,7 @@ def parse():
     p.add_argument("--T", type=int, default=0, help="orders (0 = the workload's own size)")
     p.add_argument("--workload", default="dual_large",
                    choices=["dual_large", "mlp_medium", "batch_uneven", "pg_large",
-                            "capacity_large"])
+                            "capacity_large", "owmr_base"])
     p.add_argument("--flags", type=int, default=0, help="extra pic_sim_opts flags (tuning)")
     p.add_argument("--max-steps", type=int, default=-1,
                    help="Picard window of App. A.3 in orders (-1: the workload's default, 0: none)")
@@ -93,7 +96,7 @@ def parse():
 
 
 # mlp_medium: the window of App. A.3 (16,384 orders = 4 chunks), short segments
-DEFAULT_MAX_STEPS = {"mlp_medium": 16384}
+DEFAULT_MAX_STEPS = {"mlp_medium": 16384, "owmr_base": 80_000}
 DEFAULT_SEG_WINDOW = {"mlp_medium": 4}
 
 DEFAULT_CHUNKS = {"dual_large": 4096, "mlp_medium": 4096, "batch_uneven": 0, "pg_large": 0,
@@ -313,6 +316,37 @@ def run_reference(args):
     per = max(1, int(args.steps))
     # each step a bounded sample, so that warm-up + timed steps take about a minute
     budget = max(0.05, min(10.0, 60.0 / (per + max(0, args.warmup))))
+    if args.workload == "owmr_base":
+        from oracle import owmr as ow
+        from paper_2406_01939_b300 import synth
+        inst, net = synth.owmr_base(args.seed, **({"T": args.T} if args.T else {}))
+        cut = lambda n: synth.OwmrInstance(n, inst.N, inst.ret[:n], inst.dem[:n], inst.ex[:n],
+                                           inst.cap, inst.x0r, inst.sl, inst.Sl, inst.X0, inst.s,
+                                           inst.S)
+        t0 = time.perf_counter()
+        ow.seq_sim(cut(200), net)
+        per_step = max((time.perf_counter() - t0) / 200, 1e-9)
+        sub = cut(max(200, min(inst.T, int(budget / per_step))))
+        for _ in range(max(0, args.warmup)):
+            ow.seq_sim(sub, net)
+        t0 = time.perf_counter()
+        for _ in range(per):
+            ow.seq_sim(sub, net)
+        el = time.perf_counter() - t0
+        value = per * sub.T / el
+        line = {
+            "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": per, "warmup": args.warmup,
+            "ms_per_step": 1000 * inst.T / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32+f32", "data": "synthetic",
+            "config": owmr_config(args, inst, net, DEFAULT_MAX_STEPS["owmr_base"], inst.N),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"first {sub.T} of {inst.T} steps per step, sequential C "
+                                       "oracle with the network, 1 thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line), flush=True)
+        return
     if args.workload == "batch_uneven":
         from paper_2406_01939_b300 import synth
         insts, pols = synth.batch_uneven(args.seed)
@@ -624,6 +658,155 @@ def run_pg(args, dev, world, rank):
     db.close()
 
 
+def owmr_flops_per_call(H):
+    """FLOPs of one retailer-network call: 3H + H^2 + H FMA, 2 FLOP each."""
+    return 2 * (3 * H + H * H + H)
+
+
+def owmr_config(args, inst, net, W, P):
+    return {"workload": "owmr_base",
+            "desc": (f"OWMR inventory control (App. B.3 base case): T={inst.T} unit demands over "
+                     f"N={inst.N} stores (uniform), stores (s_n,S_n)=(10,20) capacity 24, central "
+                     f"(s,S)=({inst.s},{inst.S}), retailer network 3-{net.H}-{net.H}-1 BF16 "
+                     "N(0,0.02) fed (stock, demand, steps since the store's previous demand/4096)"),
+            "T": inst.T, "N": inst.N, "hidden": net.H, "procs": P, "max_steps": W,
+            "l2": "working set (about 0.3 GB) exceeds L2; flushed between timed steps (256 MiB write)"}
+
+
+def run_owmr(args, dev, world, rank):
+    """OWMR (Appendix B): one Picard simulation per step, from the demand stream
+    resident in HBM (per-processor step tables, every pass to the fixed point,
+    actions and final state)."""
+    import torch
+    import paper_2406_01939_b300 as pic
+    from paper_2406_01939_b300 import synth
+    from paper_2406_01939_b300.owmr import (DeviceOwmr, DeviceOwmrNet, pic_owmr_create,
+                                            pic_owmr_desc, pic_owmr_destroy, pic_owmr_opts,
+                                            pic_owmr_policy, pic_owmr_simulate)
+    inst, net = synth.owmr_base(rank_seed(args.seed, rank), **({"T": args.T} if args.T else {}))
+    W = args.max_steps if args.max_steps >= 0 else DEFAULT_MAX_STEPS["owmr_base"]
+    P = inst.N
+    d = DeviceOwmr(inst, device=dev)
+    dn = DeviceOwmrNet(net, device=dev)
+    T = inst.T
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    step = lambda: d.simulate(dn, num_procs=P, max_steps=W, timing=True, flags=args.flags)
+    for _ in range(max(3, args.warmup)):
+        r = step()
+    clocks = Clocks(int(str(dev).split(":")[-1]) if ":" in str(dev) else 0)
+    torch.cuda.synchronize(dev)
+    evs, results = [], []
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        results.append(step())
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    value, t_ms = job_rate(T, args.steps, sum(a.elapsed_time(b) for a, b in evs), world, dev)
+    last = results[-1]
+    act = last["actions"].clone()
+    state = last["state"].clone()
+
+    # the sequential GPU simulator on a prefix (a prefix of the path depends only
+    # on the prefix of the demand stream); its rate is the speedup denominator
+    seq = None
+    if args.seq_steps > 0:
+        Tp = min(T, 200_000)
+        pre = synth.OwmrInstance(Tp, inst.N, inst.ret[:Tp], inst.dem[:Tp], inst.ex[:Tp], inst.cap,
+                                 inst.x0r, inst.sl, inst.Sl, inst.X0, inst.s, inst.S)
+        dp = DeviceOwmr(pre, device=dev)
+        sr = dp.simulate(dn, mode="sequential", timing=True)
+        rate = Tp / (sr["ms"] / 1000.0)
+        seq = {"value": rate, "unit": UNIT, "ms_prefix": sr["ms"], "prefix_steps": Tp,
+               "ms_full_horizon_est": 1000.0 * T / rate,
+               "bit_exact_on_prefix": bool(torch.equal(sr["actions"], act[:Tp]))}
+        dp.close()
+
+    # end to end through host buffers: create from pinned host arrays, simulate
+    # with host outputs, release
+    pin = lambda a: torch.from_numpy(np.array(a, dtype=np.int32, copy=True)).pin_memory()
+    host = [pin(getattr(inst, k)) for k in ("ret", "dem", "ex", "cap", "x0r", "sl", "Sl")]
+    host_act = torch.empty(T, dtype=torch.int32).pin_memory()
+    host_state = torch.empty(inst.N + 1, dtype=torch.int32).pin_memory()
+    h2d = sum(x.numel() * 4 for x in host)
+    d2h = (T + inst.N + 1) * 4
+    e2e_t = []
+    for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
+        flush.fill_(1)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        desc = pic_owmr_desc(T, inst.N, *[x.data_ptr() for x in host], inst.X0, inst.s, inst.S,
+                             pic.PIC_MEM_HOST, None)
+        h = pic_owmr_create(desc)
+        opts = pic_owmr_opts(pic.PIC_MODE_PICARD, P, 0, 0, None, 0, W)
+        st, res = pic_owmr_simulate(h, dn.policy(), opts, host_act, host_state, pic.PIC_MEM_HOST)
+        pic_owmr_destroy(h)
+        t1 = time.perf_counter()
+        if st != pic.PIC_OK:
+            raise RuntimeError(f"e2e simulate failed: {st}")
+        if i >= 1:
+            e2e_t.append(t1 - t0)
+    e2e_value = T / statistics.median(e2e_t) if e2e_t else None
+    bit_exact_e2e = bool(torch.equal(host_act, act.cpu())) if e2e_t else None
+
+    sim_ms = statistics.median(r["ms"] for r in results)
+    flops = last["policy_calls"] * owmr_flops_per_call(net.H)
+    achieved = flops / (sim_ms / 1000.0) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32+f32", "data": "synthetic",
+        "config": owmr_config(args, inst, net, W, P),
+        "iters": last["iters"], "replenishments": last["R"],
+        "passes_bound_2R_plus_2": 2 * last["R"] + 2,
+        "policy_calls": last["policy_calls"], "eval_rounds": last["eval_rounds"],
+        "seq_gpu": seq,
+        "speedup_vs_seq_gpu": (seq["ms_full_horizon_est"] / (t_ms / args.steps)) if seq else None,
+        "phases_ms": {"call": sim_ms, "step_device": t_ms / args.steps},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "k_owmr_picard (persistent, all passes; FP32 network rounds)",
+                     "peak_kind": "derived: 148 SMs x 128 FP32 lanes x 2 FLOP x 2.032 GHz",
+                     "algorithmic_flops": flops},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "bit_exact": bit_exact_e2e,
+                "what": "pic_owmr_create from pinned host arrays + pic_owmr_simulate with host "
+                        "outputs + pic_owmr_destroy, per step"},
+        "gpu_launches": int(last["launches"]) * args.steps,
+        "clocks": clk,
+        "wall_s_timed_loop": wall,
+    }
+    if rank == 0 and world == 1 and args.cpu_seconds > 0:
+        from oracle import owmr as ow
+        Tc, el, out = 1000, 0.0, None
+        while True:
+            pre = synth.OwmrInstance(Tc, inst.N, inst.ret[:Tc], inst.dem[:Tc], inst.ex[:Tc],
+                                     inst.cap, inst.x0r, inst.sl, inst.Sl, inst.X0, inst.s, inst.S)
+            t0 = time.perf_counter()
+            out = ow.seq_sim(pre, net)
+            el = time.perf_counter() - t0
+            if el * 4 > args.cpu_seconds or Tc >= T:
+                break
+            Tc = min(T, Tc * 4)
+        line["cpu_baseline"] = {"value": Tc / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"first {Tc} of {T} steps, sequential C oracle with the "
+                                          f"width-{net.H} network, 1 thread ({el:.1f} s)"}
+        line["bit_exact_vs_oracle"] = bool(np.array_equal(out["actions"], act.cpu().numpy()[:Tc]))
+        line["oracle_steps_checked"] = Tc
+    elif rank == 0:
+        line["cpu_baseline"] = None
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    d.close()
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -641,8 +824,9 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
 
-    if args.workload in ("batch_uneven", "pg_large"):
-        (run_batch if args.workload == "batch_uneven" else run_pg)(args, dev, world, rank)
+    if args.workload in ("batch_uneven", "pg_large", "owmr_base"):
+        {"batch_uneven": run_batch, "pg_large": run_pg, "owmr_base": run_owmr}[args.workload](
+            args, dev, world, rank)
         if world > 1:
             dist.barrier()
             dist.destroy_process_group()

@@ -86,7 +86,9 @@ typedef struct {
                                   on the GPU, the baseline of Appendix B.3) */
     int32_t num_procs;         /* P processors (Picard), 1 <= P <= N; 0 = N (one per retailer) */
     int32_t max_iters;         /* pass limit; 0 = T + 1 (Prop. 1) */
-    int32_t flags;             /* PIC_FLAG_TIMING */
+    int32_t flags;             /* PIC_FLAG_TIMING; PIC_FLAG_REUSE_TABLES: keep the previous
+                                  call's per-processor step tables when P is the same
+                                  (otherwise every call rebuilds them) */
     const int32_t* alpha_init; /* [T] DEVICE, initial cache (2 q + r, q >= 0), or NULL: all 0 */
     int64_t timeout_ns;        /* bound on each device-side wait; 0 = 60 s */
     int32_t max_steps;         /* max_steps window of Appendix A.3, in steps: a pass calls

@@ -1071,6 +1071,7 @@ pic_status pic_owmr_simulate(pic_owmr* h, const pic_owmr_policy* pol, const pic_
     a.act = h->act; a.pre = h->pre; a.tsum = h->tsum; a.xfin = h->xfin; a.oc = h->oc;
     a.W1 = pol->W1; a.b1 = pol->b1; a.W2 = pol->W2; a.b2 = pol->b2; a.w3 = pol->w3; a.b3 = pol->b3;
     if (o->mode == PIC_MODE_PICARD) {
+        if (!(o->flags & PIC_FLAG_REUSE_TABLES)) free_tables(h);  // rebuilt by this call
         pic_status ps = build_tables(h, P, st, &launches);
         if (ps) return ps;
         a.B = h->B; a.ngroups = h->ngroups; a.rec = h->rec; a.gbase = h->gbase; a.memo = h->memo;

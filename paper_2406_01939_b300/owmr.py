@@ -12,6 +12,10 @@ import torch
 from . import PIC_MEM_DEVICE, PIC_MEM_HOST, PIC_MODE_PICARD, PIC_MODE_SEQUENTIAL, PIC_OK, \
     PIC_FLAG_TIMING, PicError, _ptr, _stream_handle, lib, pic_last_error
 
+__all__ = ["DeviceOwmr", "DeviceOwmrNet", "pic_owmr_create", "pic_owmr_simulate",
+           "pic_owmr_destroy", "pic_owmr_desc", "pic_owmr_policy", "pic_owmr_opts",
+           "pic_owmr_result", "PIC_MEM_HOST"]
+
 P_ = C.c_void_p
 
 
@@ -125,7 +129,8 @@ class DeviceOwmr:
             pass
 
     def simulate(self, net=None, mode="picard", num_procs=0, max_iters=0, alpha_init=None,
-                 timing=False, timeout_ns=0, raise_on_error=True, stream=None, max_steps=0):
+                 timing=False, timeout_ns=0, raise_on_error=True, stream=None, max_steps=0,
+                 flags=0):
         """Run the Picard iteration (or the sequential baseline) under the
         retailer rule, with the network `net` (a DeviceOwmrNet, an OwmrNet, or
         None).  Returns device tensors and the call's statistics."""
@@ -136,7 +141,8 @@ class DeviceOwmr:
         if alpha_init is not None:
             init = alpha_init if torch.is_tensor(alpha_init) else _dev_i32(alpha_init, self.device)
         opts = pic_owmr_opts(PIC_MODE_PICARD if mode == "picard" else PIC_MODE_SEQUENTIAL,
-                             int(num_procs), int(max_iters), PIC_FLAG_TIMING if timing else 0,
+                             int(num_procs), int(max_iters),
+                             (PIC_FLAG_TIMING if timing else 0) | int(flags),
                              _ptr(init), int(timeout_ns), int(max_steps))
         act = torch.empty(max(self.T, 1), dtype=torch.int32, device=self.device)
         state = torch.empty(self.N + 1, dtype=torch.int32, device=self.device)

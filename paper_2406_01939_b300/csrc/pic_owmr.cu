@@ -69,6 +69,7 @@ struct OwCtrl {
 struct OwArgs {
     int T, N, P, B, ngroups, H, X0, s, S, ntiles, max_iters, rp;  // rp = ceil(N / P)
     int window;                                                   // max_steps, 0 = none
+    int xs_len, nbuf;  // retailer-stock ints in shared memory; W2 buffers
     long long timeout_ns;
     const int32_t *cap, *sl, *Sl, *x0r;
     const int4* rec;        // interleaved [rows][32]: {t, n, d, e}, t = -1 pads
@@ -168,27 +169,41 @@ struct __align__(16) OwSmem {
     int4 rec[kCh][kLanes];
     int4 pre[kCh][kLanes];
     int2 memo[kCh][kLanes];
-    int xs[kMaxSlots];
     Mono ws[kOwThreads / 32 + 1];
     int feat_y[kLanes], feat_d[kLanes], feat_e[kLanes], feat_base[kLanes], feat_room[kLanes];
     int qout[kLanes];
     int rowidx[kLanes];
     int pend_any, pend_rows, all_done, abort;
-    unsigned long long mbar[2];
+    unsigned long long full[8], empty[8];  // W2 buffers: data landed / every warp done (<= 8)
 };
+
+// Bytes of retailer stock in shared memory (16-byte multiple).
+__host__ __device__ constexpr size_t xs_bytes(int n) { return ((size_t)n * 4 + 15) & ~(size_t)15; }
 
 // ------------------------------------------------------------------ W2 staging
 // W2 streams through shared memory in chunks of kKc rows (kKc * H BF16) moved
-// by bulk asynchronous copies, kNbuf buffers deep.  Chunk number `seq` (counted
-// over the CTA's life, identically in every thread) uses buffer seq % kNbuf and
-// completes phase (seq / kNbuf) & 1 of that buffer's mbarrier.
-constexpr int kKc = 32;
-constexpr int kNbuf = 2;
+// by bulk asynchronous copies, nbuf buffers deep (as many as shared memory
+// holds, at most 8).  Chunk number `seq` (counted over the CTA's life,
+// identically in every thread) uses buffer seq % nbuf; use u = seq / nbuf of
+// that buffer completes phase u & 1 of its `full` mbarrier (the copy landed)
+// and of its `empty` mbarrier (all 8 warps arrived after reading it).
+#ifndef OWMR_KC
+#define OWMR_KC 32
+#endif
+#ifndef OWMR_MAXBUF
+#define OWMR_MAXBUF 2
+#endif
+#ifndef OWMR_EMPTY_MBAR
+#define OWMR_EMPTY_MBAR 0
+#endif
+constexpr int kKc = OWMR_KC;
+constexpr int kMaxBuf = OWMR_MAXBUF;
 
 struct NetCtx {
     float *h1s, *zpart, *W1s, *b1s, *b2s, *w3s;
-    uint16_t* w2buf;  // [kNbuf][kKc][H]
-    unsigned long long* mbar;
+    uint16_t* w2buf;  // [nbuf][kKc][H]
+    unsigned long long *full, *empty;
+    int nbuf;
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -206,9 +221,9 @@ __device__ __forceinline__ void fence_mbar_init() {
 
 __device__ __forceinline__ void w2_issue(const NetCtx& nc, const uint16_t* W2, int H, int chunk,
                                          unsigned seq) {
-    const int buf = seq % kNbuf;
+    const int buf = seq % nc.nbuf;
     const unsigned bytes = (unsigned)(kKc * H * 2);
-    unsigned long long* b = nc.mbar + buf;
+    unsigned long long* b = nc.full + buf;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
                  "r"(bytes)
                  : "memory");
@@ -219,12 +234,10 @@ __device__ __forceinline__ void w2_issue(const NetCtx& nc, const uint16_t* W2, i
         : "memory");
 }
 
-// Wait for chunk `seq`; a wait past the kernel's deadline records a timeout
-// and returns (the grid barrier then ends the kernel).
-__device__ __forceinline__ void w2_wait(const NetCtx& nc, unsigned seq, OwCtrl* oc,
-                                        unsigned long long deadline) {
-    unsigned long long* b = nc.mbar + (seq % kNbuf);
-    const unsigned par = (seq / kNbuf) & 1u;
+// Wait for phase `par` of mbarrier b; a wait past the kernel's deadline
+// records a timeout and returns (the grid barrier then ends the kernel).
+__device__ __forceinline__ void mbar_wait(unsigned long long* b, unsigned par, OwCtrl* oc,
+                                          unsigned long long deadline) {
     for (unsigned it = 1;; ++it) {
         unsigned ok;
         asm volatile(
@@ -239,6 +252,16 @@ __device__ __forceinline__ void w2_wait(const NetCtx& nc, unsigned seq, OwCtrl* 
             return;
         }
     }
+}
+
+// fma(a0, b0, c0) and fma(a1, b1, c1), each rounded once (fma.rn.f32x2: two
+// fmaf results bit for bit).
+__device__ __forceinline__ void fma2(float& c0, float& c1, float a0, float a1, float b0, float b1) {
+    asm("{\n\t.reg .b64 ra, rb, rc;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%0, %1};\n\t"
+        "fma.rn.f32x2 rc, ra, rb, rc;\n\tmov.b64 {%0, %1}, rc;\n\t}"
+        : "+f"(c0), "+f"(c1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
 }
 
 // Layer 2 for row groups of RPT compacted rows, CPT columns per thread
@@ -260,11 +283,12 @@ __device__ void net_layer2(const NetCtx& nc, const uint16_t* W2, int H, int nrow
 #pragma unroll
         for (int r = 0; r < RPT; ++r) acc[r][c] = bb;
     }
+    const unsigned nb = (unsigned)nc.nbuf;
     for (int ch = 0; ch < nch; ++ch) {
         const unsigned seq = wuse + ch;
-        w2_wait(nc, seq, oc, deadline);
+        mbar_wait(nc.full + seq % nb, (seq / nb) & 1u, oc, deadline);
         if (active) {
-            const uint16_t* wb = nc.w2buf + (size_t)(seq % kNbuf) * kKc * H + col0;
+            const uint16_t* wb = nc.w2buf + (size_t)(seq % nb) * kKc * H + col0;
             const float* hb = nc.h1s + (size_t)ch * kKc * kLanes + rg * RPT;
 #pragma unroll 4
             for (int kk = 0; kk < kKc; ++kk) {
@@ -285,20 +309,46 @@ __device__ void net_layer2(const NetCtx& nc, const uint16_t* W2, int H, int nrow
                     const float4 h1 = *reinterpret_cast<const float4*>(hb + kk * kLanes + 4);
                     hf[0] = h0.x; hf[1] = h0.y; hf[2] = h0.z; hf[3] = h0.w;
                     hf[4] = h1.x; hf[5] = h1.y; hf[6] = h1.z; hf[7] = h1.w;
+                } else if constexpr (RPT == 4) {
+                    const float4 h0 = *reinterpret_cast<const float4*>(hb + kk * kLanes);
+                    hf[0] = h0.x; hf[1] = h0.y; hf[2] = h0.z; hf[3] = h0.w;
+                } else if constexpr (RPT == 2) {
+                    const float2 h0 = *reinterpret_cast<const float2*>(hb + kk * kLanes);
+                    hf[0] = h0.x; hf[1] = h0.y;
+                } else {
+                    hf[0] = hb[kk * kLanes];
+                }
+                if constexpr (RPT % 2 == 0) {
+                    // rows in pairs: two independent fmaf chains per instruction
+#pragma unroll
+                    for (int r = 0; r < RPT; r += 2)
+#pragma unroll
+                        for (int c = 0; c < CPT; ++c)
+                            fma2(acc[r][c], acc[r + 1][c], wf[c], wf[c], hf[r], hf[r + 1]);
                 } else {
 #pragma unroll
-                    for (int r = 0; r < RPT; ++r) hf[r] = hb[kk * kLanes + r];
+                    for (int c = 0; c < CPT; ++c) acc[0][c] = fmaf(wf[c], hf[0], acc[0][c]);
                 }
-#pragma unroll
-                for (int r = 0; r < RPT; ++r)
-#pragma unroll
-                    for (int c = 0; c < CPT; ++c) acc[r][c] = fmaf(wf[c], hf[r], acc[r][c]);
             }
         }
-        __syncthreads();  // buffer seq % kNbuf is free again
-        if (threadIdx.x == 0 && ch + kNbuf < nch) w2_issue(nc, W2, H, ch + kNbuf, seq + kNbuf);
+#if OWMR_EMPTY_MBAR
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(nc.empty + seq % nb))
+                         : "memory");
+        // refill the buffer of the previous chunk once every warp has left it
+        if (threadIdx.x == 0 && ch >= 1 && ch - 1 + (int)nb < nch) {
+            const unsigned prev = seq - 1;
+            mbar_wait(nc.empty + prev % nb, (prev / nb) & 1u, oc, deadline);
+            w2_issue(nc, W2, H, ch - 1 + nb, prev + nb);
+        }
+#else
+        __syncthreads();  // every thread is done with buffer seq % nb: refill it
+        if (threadIdx.x == 0 && ch + (int)nb < nch) w2_issue(nc, W2, H, ch + nb, seq + nb);
+#endif
     }
     wuse += nch;
+    __syncthreads();  // every warp is done with h1s and with this round's buffers
     if (active) {
 #pragma unroll
         for (int r = 0; r < RPT; ++r)
@@ -311,22 +361,22 @@ __device__ void net_layer2(const NetCtx& nc, const uint16_t* W2, int H, int nrow
 
 // One batched round of the network for the lanes flagged in `rows` (bit b =
 // lane b, features in sm.feat_*).  The pending lanes are compacted; layer 1
-// gives h1s [k][row]; layer 2 runs with 8 rows x 2G columns per thread for
-// G = 1, 2 or 4 groups of 8 rows (RPT = 1: one row, 2 columns per thread);
-// then p_g per (row, g) and z = b3 + p_0 + p_1 + ... per row.  Every output
-// follows the order documented in pic_owmr.h.
-template <int RPT>
+// gives h1s [k][row] for nr rows, the smallest of 2, 4, 8, 16, 32 that holds
+// them (ONE: a single row); layer 2 runs nr <= 8 rows x 2 columns per thread,
+// or 8 rows x 4 / 8 columns for 16 / 32 rows; then p_g per (row, g) and
+// z = b3 + p_0 + p_1 + ... per row.  Every output follows the order
+// documented in pic_owmr.h.
+template <bool ONE>
 __device__ void net_round(const OwArgs& a, OwSmem& sm, const NetCtx& nc, unsigned rows,
                           unsigned& wuse, unsigned long long deadline) {
     const int H = a.H, ncg = H >> 3, nch = H / kKc;
     const int m = __popc(rows);
     if (threadIdx.x == 0)
-        for (int c = 0; c < kNbuf && c < nch; ++c) w2_issue(nc, a.W2, H, c, wuse + c);
+        for (int c = 0; c < nc.nbuf && c < nch; ++c) w2_issue(nc, a.W2, H, c, wuse + c);
     if (threadIdx.x < kLanes && ((rows >> threadIdx.x) & 1u))
         sm.rowidx[__popc(rows & ((1u << threadIdx.x) - 1u))] = threadIdx.x;
     __syncthreads();
-    const int G = RPT == 1 ? 1 : (m <= 8 ? 1 : (m <= 16 ? 2 : 4));
-    const int nr = RPT * G;  // rows computed
+    const int nr = ONE ? 1 : (m <= 2 ? 2 : (m <= 4 ? 4 : (m <= 8 ? 8 : (m <= 16 ? 16 : 32))));
     for (int idx = threadIdx.x; idx < H * nr; idx += blockDim.x) {
         const int k = idx / nr, i = idx - k * nr;
         float v = 0.f;
@@ -340,14 +390,18 @@ __device__ void net_round(const OwArgs& a, OwSmem& sm, const NetCtx& nc, unsigne
         nc.h1s[k * kLanes + i] = v;
     }
     __syncthreads();
-    if (RPT == 1) {
+    if (ONE) {
         net_layer2<1, 2>(nc, a.W2, H, 1, wuse, a.oc, deadline);
-    } else if (G == 1) {
-        net_layer2<RPT, 2>(nc, a.W2, H, 1, wuse, a.oc, deadline);
-    } else if (G == 2) {
-        net_layer2<RPT, 4>(nc, a.W2, H, 2, wuse, a.oc, deadline);
+    } else if (nr == 2) {
+        net_layer2<2, 2>(nc, a.W2, H, 1, wuse, a.oc, deadline);
+    } else if (nr == 4) {
+        net_layer2<4, 2>(nc, a.W2, H, 1, wuse, a.oc, deadline);
+    } else if (nr == 8) {
+        net_layer2<8, 2>(nc, a.W2, H, 1, wuse, a.oc, deadline);
+    } else if (nr == 16) {
+        net_layer2<8, 4>(nc, a.W2, H, 2, wuse, a.oc, deadline);
     } else {
-        net_layer2<RPT, 8>(nc, a.W2, H, 4, wuse, a.oc, deadline);
+        net_layer2<8, 8>(nc, a.W2, H, 4, wuse, a.oc, deadline);
     }
     for (int idx = threadIdx.x; idx < m * ncg; idx += blockDim.x) {
         const int i = idx / ncg, g = idx - i * ncg;
@@ -373,14 +427,16 @@ __device__ void net_round(const OwArgs& a, OwSmem& sm, const NetCtx& nc, unsigne
 __device__ NetCtx net_setup(const OwArgs& a, unsigned char* smem_raw, OwSmem& sm) {
     NetCtx nc;
     const int H = a.H;
-    nc.h1s = reinterpret_cast<float*>(smem_raw + sizeof(OwSmem));
+    nc.h1s = reinterpret_cast<float*>(smem_raw + sizeof(OwSmem) + xs_bytes(a.xs_len));
     nc.zpart = nc.h1s + H * kLanes;
     nc.W1s = nc.zpart + kLanes * (H >> 3);
     nc.b1s = nc.W1s + 3 * H;
     nc.b2s = nc.b1s + H;
     nc.w3s = nc.b2s + H;
     nc.w2buf = reinterpret_cast<uint16_t*>(nc.w3s + H);
-    nc.mbar = sm.mbar;
+    nc.full = sm.full;
+    nc.empty = sm.empty;
+    nc.nbuf = a.nbuf;
     for (int i = threadIdx.x; i < H; i += blockDim.x) {
         nc.W1s[i] = bf1(a.W1[i]);
         nc.W1s[H + i] = bf1(a.W1[H + i]);
@@ -390,16 +446,18 @@ __device__ NetCtx net_setup(const OwArgs& a, unsigned char* smem_raw, OwSmem& sm
         nc.w3s[i] = bf1(a.w3[i]);
     }
     if (threadIdx.x == 0) {
-        for (int i = 0; i < kNbuf; ++i) mbar_init(nc.mbar + i, 1);
+        for (int i = 0; i < nc.nbuf; ++i) {
+            mbar_init(nc.full + i, 1);
+            mbar_init(nc.empty + i, kOwThreads / 32);
+        }
         fence_mbar_init();
     }
     __syncthreads();
     return nc;
 }
 
-size_t net_smem(int H) {
-    return sizeof(float) * ((size_t)H * kLanes + (size_t)kLanes * (H / 8) + 6 * (size_t)H) +
-           (size_t)kNbuf * kKc * H * 2;
+size_t net_fixed_smem(int H) {
+    return sizeof(float) * ((size_t)H * kLanes + (size_t)kLanes * (H / 8) + 6 * (size_t)H);
 }
 
 // ------------------------------------------------------------------ Picard kernel
@@ -407,6 +465,7 @@ template <bool NET>
 __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     OwSmem& sm = *reinterpret_cast<OwSmem*>(smem_raw);
+    int* xs = reinterpret_cast<int*>(smem_raw + sizeof(OwSmem));  // [rp * 32] retailer stock
     OwCtrl* oc = a.oc;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned long long deadline = globaltimer_ns() + (unsigned long long)a.timeout_ns;
@@ -491,7 +550,7 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
             for (int i = tid; i < a.rp * kLanes; i += kOwThreads) {
                 const int l = i & 31, j = i >> 5;
                 const long long n = (long long)p0 + l + (long long)j * a.P;
-                if (l < nb && n < a.N) sm.xs[i] = a.x0r[n];
+                if (l < nb && n < a.N) xs[i] = a.x0r[n];
             }
             // per-lane walk state (warp 0)
             int x0a = a.X0, ta = -1, qc_after = 0, done = 0;
@@ -522,7 +581,7 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
                                 a.memo[mi] = make_int2(py, q);
                                 const int r = px0 - q <= a.s;
                                 const int recv = q < px0 ? q : px0;
-                                sm.xs[pslot] = py + recv;
+                                xs[pslot] = py + recv;
                                 my_ship += recv;
                                 my_R += r;
                                 x0a = r ? a.S : (px0 > q ? px0 - q : 0);
@@ -549,7 +608,7 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
                                 int x0 = pr.z > ta ? a.S - pr.y : x0a - (pr.x - qc_after);
                                 x0 = x0 > 0 ? x0 : 0;
                                 const int slotn = (n / a.P) * kLanes + lane;
-                                const int xn = sm.xs[slotn];
+                                const int xn = xs[slotn];
                                 const int y = xn > d ? xn - d : 0;
                                 my_lost += d > xn ? d - xn : 0;
                                 const int base = retailer_base(y, __ldg(a.sl + n), __ldg(a.Sl + n));
@@ -575,7 +634,7 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
                                 }
                                 const int r = x0 - q <= a.s;
                                 const int recv = q < x0 ? q : x0;
-                                sm.xs[slotn] = y + recv;
+                                xs[slotn] = y + recv;
                                 my_ship += recv;
                                 my_R += r;
                                 x0a = r ? a.S : (x0 > q ? x0 - q : 0);
@@ -602,7 +661,7 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
                     __syncthreads();
                     if (!NET || !sm.pend_any || sm.abort) break;
                     const unsigned rows = (unsigned)sm.pend_rows;
-                    net_round<8>(a, sm, nc, rows, wuse, deadline);
+                    net_round<false>(a, sm, nc, rows, wuse, deadline);
                     if (tid == 0) {
                         my_evals += __popc(rows);
                         ++my_rounds;
@@ -614,7 +673,7 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
             for (int i = tid; i < a.rp * kLanes; i += kOwThreads) {
                 const int l = i & 31, j = i >> 5;
                 const long long n = (long long)p0 + l + (long long)j * a.P;
-                if (l < nb && n < a.N) a.xfin[n] = sm.xs[i];
+                if (l < nb && n < a.N) a.xfin[n] = xs[i];
             }
         }
         // CTA totals
@@ -661,7 +720,7 @@ template <bool NET>
 __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_seq(OwArgs a, int32_t* xs_g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     OwSmem& sm = *reinterpret_cast<OwSmem*>(smem_raw);
-    int* xs = a.N <= kMaxSlots ? sm.xs : xs_g;
+    int* xs = a.xs_len ? reinterpret_cast<int*>(smem_raw + sizeof(OwSmem)) : xs_g;
     const int tid = threadIdx.x;
     const unsigned long long deadline = globaltimer_ns() + (unsigned long long)a.timeout_ns;
     NetCtx nc{};
@@ -714,7 +773,7 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_seq(OwArgs a, int32_t* x
                 sm.feat_room[0] = a.cap[n] - y;
             }
             __syncthreads();
-            net_round<1>(a, sm, nc, 1u, wuse, deadline);
+            net_round<true>(a, sm, nc, 1u, wuse, deadline);
             if (tid == 0) {
                 const int q = sm.qout[0];
                 const int r = x0 - q <= a.s;
@@ -825,7 +884,7 @@ inline int nblk(long long n, int per) { return (int)((n + per - 1) / per); }
 
 // ------------------------------------------------------------------ handle
 struct pic_owmr {
-    int T = 0, N = 0, X0 = 0, s = 0, S = 0, maxcap = 0, num_sms = 0;
+    int T = 0, N = 0, X0 = 0, s = 0, S = 0, maxcap = 0, num_sms = 0, max_smem = 0;
     int32_t *ret = nullptr, *dem = nullptr, *ex = nullptr, *cap = nullptr, *x0r = nullptr, *sl = nullptr,
             *Sl = nullptr;
     int32_t* act = nullptr;
@@ -920,7 +979,22 @@ pic_status build_tables(pic_owmr* h, int P, cudaStream_t st, int* launches) {
     return ps;
 }
 
-size_t picard_smem(int H) { return sizeof(OwSmem) + (H ? net_smem(H) : 0); }
+// Dynamic shared memory: OwSmem, retailer stock, and with a network its fixed
+// part plus nbuf W2 buffers (as many as the opt-in limit allows, 2..8).
+size_t owmr_smem(int H, int xs_len, int max_smem, int* nbuf) {
+    size_t s = sizeof(OwSmem) + xs_bytes(xs_len);
+    *nbuf = 0;
+    if (H) {
+        s += net_fixed_smem(H);
+        const size_t chunk = (size_t)kKc * H * 2;
+        long long room = (long long)max_smem - 1024 - (long long)s;  // 1 KB for static smem
+        int nb = room > 0 ? (int)(room / (long long)chunk) : 0;
+        nb = nb > kMaxBuf ? kMaxBuf : nb;
+        *nbuf = nb;
+        s += (size_t)(nb > 0 ? nb : 0) * chunk;
+    }
+    return s;
+}
 
 }  // namespace
 
@@ -944,6 +1018,7 @@ pic_status pic_owmr_create(const pic_owmr_desc* d, pic_owmr** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (!e) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (!e) e = cudaDeviceGetAttribute(&h->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const size_t Tn = d->T > 0 ? (size_t)d->T : 1;
     auto A = [&](void** p, size_t bytes) {
         if (!e) e = cudaMalloc(p, bytes);
@@ -1076,7 +1151,9 @@ pic_status pic_owmr_simulate(pic_owmr* h, const pic_owmr_policy* pol, const pic_
         if (ps) return ps;
         a.B = h->B; a.ngroups = h->ngroups; a.rec = h->rec; a.gbase = h->gbase; a.memo = h->memo;
         if (H) CU(cudaMemsetAsync(h->memo, 0xff, (size_t)(h->rows > 0 ? h->rows : 1) * kLanes * sizeof(int2), st));
-        const size_t smem = picard_smem(H);
+        a.xs_len = rp * kLanes;
+        const size_t smem = owmr_smem(H, a.xs_len, h->max_smem, &a.nbuf);
+        if (H && a.nbuf < 2) return fail(PIC_ERR_UNSUPPORTED, "shared memory too small for the network");
         void (*kern)(OwArgs) = H ? k_owmr_picard<true> : k_owmr_picard<false>;
         CU(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int occ = 0;
@@ -1089,7 +1166,9 @@ pic_status pic_owmr_simulate(pic_owmr* h, const pic_owmr_policy* pol, const pic_
     } else {
         a.rec = h->trec;
         const bool use_smem = h->N <= kMaxSlots;
-        const size_t smem = picard_smem(H);
+        a.xs_len = use_smem ? h->N : 0;
+        const size_t smem = owmr_smem(H, a.xs_len, h->max_smem, &a.nbuf);
+        if (H && a.nbuf < 2) return fail(PIC_ERR_UNSUPPORTED, "shared memory too small for the network");
         int32_t* xs_g = nullptr;
         if (!use_smem) CU(cudaMallocAsync(&xs_g, (size_t)h->N * 4, st));
         void (*kern)(OwArgs, int32_t*) = H ? k_owmr_seq<true> : k_owmr_seq<false>;

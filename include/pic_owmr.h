@@ -51,6 +51,13 @@ extern "C" {
 
 typedef struct pic_owmr pic_owmr;
 
+/* pic_owmr_opts.flags bit (besides PIC_FLAG_TIMING and PIC_FLAG_REUSE_TABLES): with a network,
+ * keep W2 resident across clusters of 4 CTAs (each holds a column quarter in shared memory and
+ * the cluster pools its pending calls into shared rounds) instead of streaming W2 through each
+ * CTA in every round.  Same operations in the same order, so the same results; slower on B300
+ * (the rounds are bound by their FMA chains, and cluster-wide rounds are more numerous). */
+enum { PIC_OWMR_FLAG_CLUSTER_W2 = 1 << 16 };
+
 /* One OWMR trajectory's inputs. */
 typedef struct {
     int32_t T, N;

@@ -21,6 +21,8 @@
 #include <cstring>
 #include <new>
 
+#include <cooperative_groups.h>
+
 #include "pic_device.cuh"
 #include "pic_owmr.h"
 
@@ -164,6 +166,8 @@ __device__ __forceinline__ int q_of(int base, int room, float z) {
     return (int)v;
 }
 
+constexpr int kMaxBufSlots = 2;  // mbarriers reserved for the W2 ring (kMaxBuf)
+
 // Shared memory of the Picard kernel (dynamic; the network part only with H > 0).
 struct __align__(16) OwSmem {
     int4 rec[kCh][kLanes];
@@ -174,7 +178,7 @@ struct __align__(16) OwSmem {
     int qout[kLanes];
     int rowidx[kLanes];
     int pend_any, pend_rows, all_done, abort;
-    unsigned long long full[8], empty[8];  // W2 buffers: data landed / every warp done (<= 8)
+    unsigned long long full[kMaxBufSlots];  // W2 buffers: the copy landed
 };
 
 // Bytes of retailer stock in shared memory (16-byte multiple).
@@ -183,26 +187,20 @@ __host__ __device__ constexpr size_t xs_bytes(int n) { return ((size_t)n * 4 + 1
 // ------------------------------------------------------------------ W2 staging
 // W2 streams through shared memory in chunks of kKc rows (kKc * H BF16) moved
 // by bulk asynchronous copies, nbuf buffers deep (as many as shared memory
-// holds, at most 8).  Chunk number `seq` (counted over the CTA's life,
+// holds, at most kMaxBuf).  Chunk number `seq` (counted over the CTA's life,
 // identically in every thread) uses buffer seq % nbuf; use u = seq / nbuf of
-// that buffer completes phase u & 1 of its `full` mbarrier (the copy landed)
-// and of its `empty` mbarrier (all 8 warps arrived after reading it).
-#ifndef OWMR_KC
-#define OWMR_KC 32
-#endif
-#ifndef OWMR_MAXBUF
-#define OWMR_MAXBUF 2
-#endif
-#ifndef OWMR_EMPTY_MBAR
-#define OWMR_EMPTY_MBAR 0
-#endif
-constexpr int kKc = OWMR_KC;
-constexpr int kMaxBuf = OWMR_MAXBUF;
+// that buffer completes phase u & 1 of its `full` mbarrier (the copy landed).
+// 32 rows x 2 buffers measured fastest: a third buffer gains nothing, 16-row
+// chunks pay one more barrier per chunk, and releasing buffers through
+// per-warp mbarrier arrivals instead of __syncthreads was slower.
+constexpr int kKc = 32;
+constexpr int kMaxBuf = 2;
+static_assert(kMaxBuf <= kMaxBufSlots, "one mbarrier per W2 buffer");
 
 struct NetCtx {
     float *h1s, *zpart, *W1s, *b1s, *b2s, *w3s;
     uint16_t* w2buf;  // [nbuf][kKc][H]
-    unsigned long long *full, *empty;
+    unsigned long long* full;
     int nbuf;
 };
 
@@ -327,25 +325,14 @@ __device__ void net_layer2(const NetCtx& nc, const uint16_t* W2, int H, int nrow
                             fma2(acc[r][c], acc[r + 1][c], wf[c], wf[c], hf[r], hf[r + 1]);
                 } else {
 #pragma unroll
-                    for (int c = 0; c < CPT; ++c) acc[0][c] = fmaf(wf[c], hf[0], acc[0][c]);
+                    for (int r = 0; r < RPT; ++r)
+#pragma unroll
+                        for (int c = 0; c < CPT; ++c) acc[r][c] = fmaf(wf[c], hf[r], acc[r][c]);
                 }
             }
         }
-#if OWMR_EMPTY_MBAR
-        __syncwarp();
-        if ((threadIdx.x & 31) == 0)
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(nc.empty + seq % nb))
-                         : "memory");
-        // refill the buffer of the previous chunk once every warp has left it
-        if (threadIdx.x == 0 && ch >= 1 && ch - 1 + (int)nb < nch) {
-            const unsigned prev = seq - 1;
-            mbar_wait(nc.empty + prev % nb, (prev / nb) & 1u, oc, deadline);
-            w2_issue(nc, W2, H, ch - 1 + nb, prev + nb);
-        }
-#else
         __syncthreads();  // every thread is done with buffer seq % nb: refill it
         if (threadIdx.x == 0 && ch + (int)nb < nch) w2_issue(nc, W2, H, ch + nb, seq + nb);
-#endif
     }
     wuse += nch;
     __syncthreads();  // every warp is done with h1s and with this round's buffers
@@ -435,7 +422,6 @@ __device__ NetCtx net_setup(const OwArgs& a, unsigned char* smem_raw, OwSmem& sm
     nc.w3s = nc.b2s + H;
     nc.w2buf = reinterpret_cast<uint16_t*>(nc.w3s + H);
     nc.full = sm.full;
-    nc.empty = sm.empty;
     nc.nbuf = a.nbuf;
     for (int i = threadIdx.x; i < H; i += blockDim.x) {
         nc.W1s[i] = bf1(a.W1[i]);
@@ -446,10 +432,7 @@ __device__ NetCtx net_setup(const OwArgs& a, unsigned char* smem_raw, OwSmem& sm
         nc.w3s[i] = bf1(a.w3[i]);
     }
     if (threadIdx.x == 0) {
-        for (int i = 0; i < nc.nbuf; ++i) {
-            mbar_init(nc.full + i, 1);
-            mbar_init(nc.empty + i, kOwThreads / 32);
-        }
+        for (int i = 0; i < nc.nbuf; ++i) mbar_init(nc.full + i, 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -458,6 +441,70 @@ __device__ NetCtx net_setup(const OwArgs& a, unsigned char* smem_raw, OwSmem& sm
 
 size_t net_fixed_smem(int H) {
     return sizeof(float) * ((size_t)H * kLanes + (size_t)kLanes * (H / 8) + 6 * (size_t)H);
+}
+
+// Phases A and B of pass `pass`: tile summaries of the cache, a grid barrier,
+// then pre[t] = {Qc, D, LR, alpha_t} for the CTA's contiguous tiles (and
+// pre[T]), and a second grid barrier.  Returns false when a barrier failed.
+__device__ bool prefix_phases(const OwArgs& a, OwCtrl* oc, Mono* ws, int tile0, int tile1,
+                              int pass, unsigned long long deadline) {
+    const int tid = threadIdx.x;
+    for (int tile = tile0; tile < tile1; ++tile) {
+        const long long base = (long long)tile * kTile + tid * kItems;
+        Mono m = mono_id();
+#pragma unroll 4
+        for (int i = 0; i < kItems; ++i) {
+            const long long t = base + i;
+            if (t < a.T) m = mono_step(m, (int)t, a.act[t]);
+        }
+        Mono tot;
+        block_exscan_mono(m, &tot, ws);
+        if (tid == 0) a.tsum[tile] = make_int4(tot.sq, tot.lr, tot.da, 0);
+    }
+    if (!grid_sync(&oc->c, deadline)) return false;
+    if (blockIdx.x == 0 && tid == 0) {
+        const int nx = (pass + 1) % 3;
+        oc->changed[nx] = 0;
+        oc->fct[nx] = INT_MAX;
+        oc->lost[nx] = oc->shipped[nx] = oc->R[nx] = 0;
+    }
+    if (tile0 < tile1 || (blockIdx.x == 0 && a.T == 0)) {
+        // prefix of the tiles before tile0
+        Mono m = mono_id();
+        const int per = (tile0 + kOwThreads - 1) / kOwThreads;
+        for (int i = 0; i < per; ++i) {
+            const int tl = tid * per + i;
+            if (tl < tile0) {
+                const int4 s4 = a.tsum[tl];
+                m = mono_cat(m, Mono{s4.x, s4.y, s4.z});
+            }
+        }
+        Mono run;
+        block_exscan_mono(m, &run, ws);
+        for (int tile = tile0; tile < tile1; ++tile) {
+            const long long base = (long long)tile * kTile + tid * kItems;
+            Mono loc = mono_id();
+            for (int i = 0; i < kItems; ++i) {
+                const long long t = base + i;
+                if (t < a.T) loc = mono_step(loc, (int)t, a.act[t]);
+            }
+            Mono tot;
+            Mono ex = block_exscan_mono(loc, &tot, ws);
+            Mono cur = mono_cat(run, ex);
+            for (int i = 0; i < kItems; ++i) {
+                const long long t = base + i;
+                if (t < a.T) {
+                    const int v = a.act[t];
+                    a.pre[t] = make_int4(cur.sq, cur.da, cur.lr, v);
+                    cur = mono_step(cur, (int)t, v);
+                    if (t == a.T - 1) a.pre[a.T] = make_int4(cur.sq, cur.da, cur.lr, 0);
+                }
+            }
+            run = mono_cat(run, tot);
+        }
+        if (a.T == 0 && blockIdx.x == 0 && tid == 0) a.pre[0] = make_int4(0, 0, -1, 0);
+    }
+    return grid_sync(&oc->c, deadline);
 }
 
 // ------------------------------------------------------------------ Picard kernel
@@ -482,64 +529,7 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
     for (int pass = 1;; ++pass) {
         const int slot = pass % 3;
         const int whi = a.window > 0 ? (int)min((long long)a.T, (long long)w + a.window) : a.T;
-        // ---------------- phase A: tile summaries
-        for (int tile = tile0; tile < tile1; ++tile) {
-            const long long base = (long long)tile * kTile + tid * kItems;
-            Mono m = mono_id();
-#pragma unroll 4
-            for (int i = 0; i < kItems; ++i) {
-                const long long t = base + i;
-                if (t < a.T) m = mono_step(m, (int)t, a.act[t]);
-            }
-            Mono tot;
-            block_exscan_mono(m, &tot, sm.ws);
-            if (tid == 0) a.tsum[tile] = make_int4(tot.sq, tot.lr, tot.da, 0);
-        }
-        if (!grid_sync(&oc->c, deadline)) break;
-        // ---------------- phase B: prefix quantities before every step
-        if (blockIdx.x == 0 && tid == 0) {
-            const int nx = (pass + 1) % 3;
-            oc->changed[nx] = 0;
-            oc->fct[nx] = INT_MAX;
-            oc->lost[nx] = oc->shipped[nx] = oc->R[nx] = 0;
-        }
-        if (tile0 < tile1 || (blockIdx.x == 0 && a.T == 0)) {
-            // prefix of the tiles before tile0
-            Mono m = mono_id();
-            const int per = (tile0 + kOwThreads - 1) / kOwThreads;
-            for (int i = 0; i < per; ++i) {
-                const int tl = tid * per + i;
-                if (tl < tile0) {
-                    const int4 s4 = a.tsum[tl];
-                    m = mono_cat(m, Mono{s4.x, s4.y, s4.z});
-                }
-            }
-            Mono run;
-            block_exscan_mono(m, &run, sm.ws);
-            for (int tile = tile0; tile < tile1; ++tile) {
-                const long long base = (long long)tile * kTile + tid * kItems;
-                Mono loc = mono_id();
-                for (int i = 0; i < kItems; ++i) {
-                    const long long t = base + i;
-                    if (t < a.T) loc = mono_step(loc, (int)t, a.act[t]);
-                }
-                Mono tot;
-                Mono ex = block_exscan_mono(loc, &tot, sm.ws);
-                Mono cur = mono_cat(run, ex);
-                for (int i = 0; i < kItems; ++i) {
-                    const long long t = base + i;
-                    if (t < a.T) {
-                        const int v = a.act[t];
-                        a.pre[t] = make_int4(cur.sq, cur.da, cur.lr, v);
-                        cur = mono_step(cur, (int)t, v);
-                        if (t == a.T - 1) a.pre[a.T] = make_int4(cur.sq, cur.da, cur.lr, 0);
-                    }
-                }
-                run = mono_cat(run, tot);
-            }
-            if (a.T == 0 && blockIdx.x == 0 && tid == 0) a.pre[0] = make_int4(0, 0, -1, 0);
-        }
-        if (!grid_sync(&oc->c, deadline)) break;
+        if (!prefix_phases(a, oc, sm.ws, tile0, tile1, pass, deadline)) break;
         // ---------------- phase C: walks
         int my_changed = 0, my_first = INT_MAX;
         long long my_lost = 0, my_ship = 0, my_R = 0;
@@ -709,6 +699,388 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
         }
         w = changed ? ld_volatile(&oc->fct[slot]) : whi;
     }
+}
+
+// ------------------------------------------------------------------ cluster kernel
+// The same pass loop with the network's W2 resident in distributed shared
+// memory: a cluster of kClSize CTAs keeps W2 split by columns (CTA rank r holds
+// columns [r H/4, (r+1) H/4), H^2/4 BF16), so no round streams W2.  Rounds are
+// cluster-wide: each CTA contributes up to kClRows pending calls, writes their
+// h1 rows into every CTA's pooled h1 [H][32] (slot 8 r + i), every CTA computes
+// its column slice for all pooled rows and sends the layer-3 partials of its
+// 8-column groups to the rows' owners, which add p_0 + p_1 + ... in order.
+// Between rounds a CTA walks (chunk staging and walks are CTA-local); a CTA
+// with nothing to evaluate still joins the rounds until every CTA of its
+// cluster has finished the pass.  Decisions that end loops are taken from
+// data every CTA of the cluster reads after the same cluster barrier.
+namespace cg = cooperative_groups;
+constexpr int kClSize = 4;
+constexpr int kClRows = 8;
+constexpr int kClCh = 16;
+
+struct __align__(16) OwSmemCl {
+    int4 rec[kClCh][kLanes];
+    int4 pre[kClCh][kLanes];
+    int2 memo[kClCh][kLanes];
+    Mono ws[kOwThreads / 32 + 1];
+    int feat_y[kLanes], feat_d[kLanes], feat_e[kLanes], feat_base[kLanes], feat_room[kLanes];
+    int qout[kLanes];
+    int rowidx[kClRows];
+    int pend_any, pend_rows, all_done, served, m;
+    int cnt[kClSize], fin[kClSize], okf[kClSize];  // written by the cluster's CTAs
+    float zpool[kClRows][kMaxH / 8];               // p_g of this CTA's served rows
+    float b2s[kMaxH / kClSize], w3s[kMaxH / kClSize];
+    float W1s[3 * kMaxH], b1s[kMaxH];
+};
+
+size_t cl_smem(int H, int xs_len) {
+    return sizeof(OwSmemCl) + xs_bytes(xs_len) + sizeof(float) * (size_t)H * kLanes +
+           (size_t)H * (H / kClSize) * 2;
+}
+
+// One cluster round.  `rows`: this CTA's parked lanes; `fin`: this CTA has no
+// more steps in this pass.  Serves up to kClRows of them (sm.served), leaves
+// q in sm.qout.  Returns true when every CTA of the cluster is finished and
+// none had a call to make (then nothing was computed).
+__device__ bool cl_round(const OwArgs& a, OwSmemCl& sm, float* h1pool, const uint16_t* w2s,
+                         unsigned rank, unsigned rows, bool fin) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int H = a.H, tid = threadIdx.x, cols = H / kClSize;
+    if (tid == 0) {
+        unsigned r = rows, served = 0;
+        int m = 0;
+        while (r && m < kClRows) {
+            const int b = __ffs(r) - 1;
+            sm.rowidx[m++] = b;
+            served |= 1u << b;
+            r &= r - 1;
+        }
+        sm.served = (int)served;
+        sm.m = m;
+    }
+    __syncthreads();
+    const int m = sm.m;
+    // layer 1 of the served rows, into every CTA's pool at slots 8 rank + i
+    for (int idx = tid; idx < H * kClRows; idx += kOwThreads) {
+        const int k = idx >> 3, i = idx & 7;
+        float v = 0.f;
+        if (i < m) {
+            const int b = sm.rowidx[i];
+            float acc = fmaf(sm.W1s[k], (float)sm.feat_y[b], sm.b1s[k]);
+            acc = fmaf(sm.W1s[H + k], (float)sm.feat_d[b], acc);
+            acc = fmaf(sm.W1s[2 * H + k], (float)sm.feat_e[b] * 0.000244140625f, acc);
+            v = acc > 0.f ? acc : 0.f;
+        }
+#pragma unroll
+        for (int d = 0; d < kClSize; ++d) cl.map_shared_rank(h1pool, d)[k * kLanes + 8 * rank + i] = v;
+    }
+    if (tid < kClSize) {
+        cl.map_shared_rank(sm.cnt, tid)[rank] = m;
+        cl.map_shared_rank(sm.fin, tid)[rank] = (fin && m == 0) ? 1 : 0;
+    }
+    cl.sync();  // pooled rows and flags are in place
+    int cnt[kClSize], any = 0, all_fin = 1;
+#pragma unroll
+    for (int j = 0; j < kClSize; ++j) {
+        cnt[j] = sm.cnt[j];
+        any |= cnt[j];
+        all_fin &= sm.fin[j];
+    }
+    if (!any && all_fin) return true;
+    // layer 2 for this CTA's column slice: source CTA rg's 8 rows x 2 columns per thread
+    const int tpr = cols / 2, rg = tid / 64, cp = tid & 63;
+    const bool active = cp < tpr && cnt[rg] > 0;
+    float acc[8][2];
+    if (active) {
+        const float bb0 = sm.b2s[2 * cp], bb1 = sm.b2s[2 * cp + 1];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            acc[r][0] = bb0;
+            acc[r][1] = bb1;
+        }
+        const float* hb = h1pool + 8 * rg;
+#pragma unroll 4
+        for (int k = 0; k < H; ++k) {
+            const unsigned w = *reinterpret_cast<const unsigned*>(w2s + (size_t)k * cols + 2 * cp);
+            const float w0 = bf_lo(w), w1 = bf_hi(w);
+            const float4 h0 = *reinterpret_cast<const float4*>(hb + k * kLanes);
+            const float4 h1 = *reinterpret_cast<const float4*>(hb + k * kLanes + 4);
+            fma2(acc[0][0], acc[1][0], w0, w0, h0.x, h0.y);
+            fma2(acc[2][0], acc[3][0], w0, w0, h0.z, h0.w);
+            fma2(acc[4][0], acc[5][0], w0, w0, h1.x, h1.y);
+            fma2(acc[6][0], acc[7][0], w0, w0, h1.z, h1.w);
+            fma2(acc[0][1], acc[1][1], w1, w1, h0.x, h0.y);
+            fma2(acc[2][1], acc[3][1], w1, w1, h0.z, h0.w);
+            fma2(acc[4][1], acc[5][1], w1, w1, h1.x, h1.y);
+            fma2(acc[6][1], acc[7][1], w1, w1, h1.z, h1.w);
+        }
+    }
+    __syncthreads();  // the pool is read; it now holds h2 [32][cols]
+    if (active) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            h1pool[(8 * rg + r) * cols + 2 * cp] = acc[r][0] > 0.f ? acc[r][0] : 0.f;
+            h1pool[(8 * rg + r) * cols + 2 * cp + 1] = acc[r][1] > 0.f ? acc[r][1] : 0.f;
+        }
+    }
+    __syncthreads();
+    // layer-3 partials of this slice's 8-column groups, sent to the rows' owners
+    const int ng = cols / 8;
+    for (int idx = tid; idx < kLanes * ng; idx += kOwThreads) {
+        const int slot = idx / ng, gl = idx - slot * ng, owner = slot >> 3, i = slot & 7;
+        if (i < cnt[owner]) {
+            const float* h2 = h1pool + slot * cols + 8 * gl;
+            float p = 0.f;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) p = fmaf(sm.w3s[8 * gl + c], h2[c], p);
+            cl.map_shared_rank(&sm.zpool[0][0], owner)[i * (kMaxH / 8) + ng * rank + gl] = p;
+        }
+    }
+    cl.sync();  // partials delivered; the pools may be refilled from here on
+    if (tid < m) {
+        const int b = sm.rowidx[tid];
+        float z = bf1(a.b3[0]);
+        for (int g = 0; g < H / 8; ++g) z = __fadd_rn(z, sm.zpool[tid][g]);
+        sm.qout[b] = q_of(sm.feat_base[b], sm.feat_room[b], z);
+    }
+    __syncthreads();
+    return false;
+}
+
+// AND of `ok` over the cluster (every CTA gets the same answer).
+__device__ bool cl_agree(OwSmemCl& sm, unsigned rank, bool ok) {
+    cg::cluster_group cl = cg::this_cluster();
+    if (threadIdx.x < kClSize) cl.map_shared_rank(sm.okf, threadIdx.x)[rank] = ok ? 1 : 0;
+    cl.sync();
+    int all = 1;
+#pragma unroll
+    for (int j = 0; j < kClSize; ++j) all &= sm.okf[j];
+    cl.sync();  // okf may be rewritten after this
+    return all != 0;
+}
+
+__global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard_cl(OwArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    OwSmemCl& sm = *reinterpret_cast<OwSmemCl*>(smem_raw);
+    int* xs = reinterpret_cast<int*>(smem_raw + sizeof(OwSmemCl));
+    float* h1pool = reinterpret_cast<float*>(smem_raw + sizeof(OwSmemCl) + xs_bytes(a.xs_len));
+    uint16_t* w2s = reinterpret_cast<uint16_t*>(h1pool + a.H * kLanes);  // [H][H/4]
+    cg::cluster_group cl = cg::this_cluster();
+    const unsigned rank = cl.block_rank();
+    OwCtrl* oc = a.oc;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, H = a.H, cols = H / kClSize;
+    const unsigned long long deadline = globaltimer_ns() + (unsigned long long)a.timeout_ns;
+    // resident weights: the W2 column slice, the slice of b2 and w3, layer 1
+    for (int i = tid; i < H * cols / 8; i += kOwThreads) {
+        const int k = i / (cols / 8), c8 = i - k * (cols / 8);
+        reinterpret_cast<uint4*>(w2s)[i] =
+            reinterpret_cast<const uint4*>(a.W2 + (size_t)k * H + rank * cols)[c8];
+    }
+    for (int i = tid; i < H; i += kOwThreads) {
+        sm.W1s[i] = bf1(a.W1[i]);
+        sm.W1s[H + i] = bf1(a.W1[H + i]);
+        sm.W1s[2 * H + i] = bf1(a.W1[2 * H + i]);
+        sm.b1s[i] = bf1(a.b1[i]);
+        if (i < cols) {
+            sm.b2s[i] = bf1(a.b2[rank * cols + i]);
+            sm.w3s[i] = bf1(a.w3[rank * cols + i]);
+        }
+    }
+    const int tpc = (a.ntiles + gridDim.x - 1) / gridDim.x;
+    const int tile0 = min(a.ntiles, (int)blockIdx.x * tpc), tile1 = min(a.ntiles, tile0 + tpc);
+    if (blockIdx.x == 0 && tid == 0)
+        for (int i = 0; i < 3; ++i) oc->fct[i] = INT_MAX;
+    int w = 0;
+    cl.sync();  // slices and flags of every CTA are initialised before any remote write
+
+    for (int pass = 1;; ++pass) {
+        const int slot = pass % 3;
+        const int whi = a.window > 0 ? (int)min((long long)a.T, (long long)w + a.window) : a.T;
+        if (!cl_agree(sm, rank, prefix_phases(a, oc, sm.ws, tile0, tile1, pass, deadline))) break;
+        // ---------------- phase C: walks with cluster rounds
+        int my_changed = 0, my_first = INT_MAX;
+        long long my_lost = 0, my_ship = 0, my_R = 0;
+        unsigned long long my_evals = 0, my_rounds = 0;
+        int g = blockIdx.x;
+        bool fin = g >= a.ngroups, loaded = false, group_init = false;
+        long long r0 = 0, row1 = 0;
+        int p0 = 0, nb = 0;
+        // lane state (warp 0)
+        int x0a = 0, ta = -1, qc_after = 0, done = 0, pos = 0;
+        int pend = 0, pt = 0, px0 = 0, py = 0, pold = 0, pqc = 0, pslot = 0;
+        for (;;) {
+            // advance the CTA's walk until some lane waits for a call or the CTA is done
+            while (!fin) {
+                if (!group_init) {
+                    p0 = g * a.B;
+                    nb = min(a.B, a.P - p0);
+                    for (int i = tid; i < a.rp * kLanes; i += kOwThreads) {
+                        const int l = i & 31, j = i >> 5;
+                        const long long n = (long long)p0 + l + (long long)j * a.P;
+                        if (l < nb && n < a.N) xs[i] = a.x0r[n];
+                    }
+                    x0a = a.X0; ta = -1; qc_after = 0; done = 0; pend = 0;
+                    r0 = a.gbase[g];
+                    row1 = a.gbase[g + 1];
+                    group_init = true;
+                    loaded = false;
+                }
+                if (!loaded) {
+                    if (r0 >= row1) {  // the group is finished
+                        __syncthreads();
+                        for (int i = tid; i < a.rp * kLanes; i += kOwThreads) {
+                            const int l = i & 31, j = i >> 5;
+                            const long long n = (long long)p0 + l + (long long)j * a.P;
+                            if (l < nb && n < a.N) a.xfin[n] = xs[i];
+                        }
+                        g += gridDim.x;
+                        group_init = false;
+                        if (g >= a.ngroups) fin = true;
+                        continue;
+                    }
+                    __syncthreads();
+                    for (int i = tid; i < kClCh * kLanes; i += kOwThreads)
+                        (&sm.rec[0][0])[i] = a.rec[r0 * kLanes + i];
+                    for (int i = tid; i < kClCh * kLanes; i += kOwThreads)
+                        (&sm.memo[0][0])[i] = a.memo[r0 * kLanes + i];
+                    __syncthreads();
+                    for (int i = tid; i < kClCh * kLanes; i += kOwThreads) {
+                        const int t = (&sm.rec[0][0])[i].x;
+                        if (t >= 0) (&sm.pre[0][0])[i] = a.pre[t];
+                    }
+                    __syncthreads();
+                    loaded = true;
+                    pos = 0;
+                }
+                if (warp == 0) {
+                    bool parked = false;
+                    if (lane < nb) {
+                        if (pend && ((sm.served >> lane) & 1)) {
+                            const int q = sm.qout[lane];
+                            a.memo[(r0 + pos) * kLanes + lane] = make_int2(py, q);
+                            const int r = px0 - q <= a.s;
+                            const int recv = q < px0 ? q : px0;
+                            xs[pslot] = py + recv;
+                            my_ship += recv;
+                            my_R += r;
+                            x0a = r ? a.S : (px0 > q ? px0 - q : 0);
+                            qc_after = pqc + (pold >> 1);
+                            ta = pt;
+                            const int nv = 2 * q + r;
+                            if (nv != pold) {
+                                a.act[pt] = nv;
+                                if (!my_changed) my_first = pt;
+                                ++my_changed;
+                            }
+                            pend = 0;
+                            ++pos;
+                        }
+                        if (pend) {
+                            parked = true;  // still waiting (not served in the last round)
+                        } else {
+                            while (pos < kClCh) {
+                                const int4 rc = sm.rec[pos][lane];
+                                if (rc.x < 0 || rc.x >= whi) {
+                                    pos = kClCh;
+                                    done = 1;
+                                    break;
+                                }
+                                const int t = rc.x, n = rc.y, d = rc.z;
+                                const int4 pr = sm.pre[pos][lane];
+                                int x0 = pr.z > ta ? a.S - pr.y : x0a - (pr.x - qc_after);
+                                x0 = x0 > 0 ? x0 : 0;
+                                const int slotn = (n / a.P) * kLanes + lane;
+                                const int xn = xs[slotn];
+                                const int y = xn > d ? xn - d : 0;
+                                my_lost += d > xn ? d - xn : 0;
+                                const int base = retailer_base(y, __ldg(a.sl + n), __ldg(a.Sl + n));
+                                const int room = __ldg(a.cap + n) - y;
+                                const int2 mm = sm.memo[pos][lane];
+                                if (mm.x != y) {
+                                    pend = 1;
+                                    pt = t; px0 = x0; py = y; pold = pr.w; pqc = pr.x; pslot = slotn;
+                                    sm.feat_y[lane] = y;
+                                    sm.feat_d[lane] = d;
+                                    sm.feat_e[lane] = rc.w;
+                                    sm.feat_base[lane] = base;
+                                    sm.feat_room[lane] = room;
+                                    parked = true;
+                                    break;
+                                }
+                                const int q = mm.y;
+                                const int r = x0 - q <= a.s;
+                                const int recv = q < x0 ? q : x0;
+                                xs[slotn] = y + recv;
+                                my_ship += recv;
+                                my_R += r;
+                                x0a = r ? a.S : (x0 > q ? x0 - q : 0);
+                                qc_after = pr.x + (pr.w >> 1);
+                                ta = t;
+                                const int nv = 2 * q + r;
+                                if (nv != pr.w) {
+                                    a.act[t] = nv;
+                                    if (!my_changed) my_first = t;
+                                    ++my_changed;
+                                }
+                                ++pos;
+                            }
+                        }
+                    }
+                    const unsigned rows = __ballot_sync(kFull, parked);
+                    const bool all = __all_sync(kFull, done || lane >= nb);
+                    if (lane == 0) {
+                        sm.pend_rows = (int)rows;
+                        sm.pend_any = rows != 0u;
+                        sm.all_done = all;
+                    }
+                }
+                __syncthreads();
+                if (sm.pend_any) break;  // calls to make: join a round
+                // every lane reached the chunk's end (or its list / window end)
+                loaded = false;
+                r0 += kClCh;
+                if (sm.all_done) r0 = row1;
+            }
+            const unsigned rows = fin ? 0u : (unsigned)sm.pend_rows;
+            if (cl_round(a, sm, h1pool, w2s, rank, rows, fin)) break;
+            if (tid == 0 && sm.m) {
+                my_evals += sm.m;
+                ++my_rounds;
+            }
+        }
+        if (warp == 0) {
+            const int ch = __reduce_add_sync(kFull, my_changed);
+            const int fmin = __reduce_min_sync(kFull, my_first);
+            const long long lo = warp_sum_i64(my_lost), sh = warp_sum_i64(my_ship),
+                            rr = warp_sum_i64(my_R);
+            if (lane == 0) {
+                if (ch) {
+                    atomicAdd(&oc->changed[slot], ch);
+                    atomicMin(&oc->fct[slot], fmin);
+                }
+                if (lo) atomicAdd((unsigned long long*)&oc->lost[slot], (unsigned long long)lo);
+                if (sh) atomicAdd((unsigned long long*)&oc->shipped[slot], (unsigned long long)sh);
+                if (rr) atomicAdd((unsigned long long*)&oc->R[slot], (unsigned long long)rr);
+            }
+        }
+        if (tid == 0 && my_evals) {
+            atomicAdd(&oc->evals, my_evals);
+            atomicAdd(&oc->rounds, my_rounds);
+        }
+        if (!cl_agree(sm, rank, grid_sync(&oc->c, deadline))) break;
+        const int changed = ld_volatile(&oc->changed[slot]);
+        const bool fixed = changed == 0 && whi >= a.T;
+        if (fixed || pass >= a.max_iters) {
+            if (blockIdx.x == 0 && tid == 0) {
+                oc->c.iters = pass;
+                oc->c.converged = fixed;
+                oc->c.pad0 = slot;
+            }
+            break;
+        }
+        w = changed ? ld_volatile(&oc->fct[slot]) : whi;
+    }
+    cl.sync();  // no CTA leaves while a peer may still address its shared memory
 }
 
 // ------------------------------------------------------------------ sequential baseline
@@ -893,7 +1265,7 @@ struct pic_owmr {
     int* bad = nullptr;
     OwCtrl* oc = nullptr;
     // tables of the current processor count
-    int P = 0, B = 0, ngroups = 0;
+    int P = 0, B = 0, ngroups = 0, ctas = 0;
     long long rows = 0;
     int4* rec = nullptr;   // interleaved step records of the Picard walks
     int4* trec = nullptr;  // time-order records for the sequential kernel
@@ -915,11 +1287,11 @@ void free_tables(pic_owmr* h) {
     h->P = 0;
 }
 
-pic_status build_tables(pic_owmr* h, int P, cudaStream_t st, int* launches) {
-    if (h->P == P) return PIC_OK;
+pic_status build_tables(pic_owmr* h, int P, int ctas, cudaStream_t st, int* launches) {
+    if (h->P == P && h->ctas == ctas) return PIC_OK;
     free_tables(h);
     const int T = h->T;
-    int B = (P + h->num_sms - 1) / h->num_sms;
+    int B = (P + ctas - 1) / ctas;
     B = B < 1 ? 1 : (B > kLanes ? kLanes : B);
     const int ngroups = (P + B - 1) / B;
     int32_t *key = nullptr, *key_s = nullptr, *perm = nullptr, *tk = nullptr, *tv = nullptr,
@@ -973,6 +1345,7 @@ pic_status build_tables(pic_owmr* h, int P, cudaStream_t st, int* launches) {
                     "OWMR tables: %s", cudaGetErrorString(e));
     }
     h->P = P;
+    h->ctas = ctas;
     h->B = B;
     h->ngroups = ngroups;
     h->rows = rows_total;
@@ -1146,23 +1519,62 @@ pic_status pic_owmr_simulate(pic_owmr* h, const pic_owmr_policy* pol, const pic_
     a.act = h->act; a.pre = h->pre; a.tsum = h->tsum; a.xfin = h->xfin; a.oc = h->oc;
     a.W1 = pol->W1; a.b1 = pol->b1; a.W2 = pol->W2; a.b2 = pol->b2; a.w3 = pol->w3; a.b3 = pol->b3;
     if (o->mode == PIC_MODE_PICARD) {
-        if (!(o->flags & PIC_FLAG_REUSE_TABLES)) free_tables(h);  // rebuilt by this call
-        pic_status ps = build_tables(h, P, st, &launches);
-        if (ps) return ps;
-        a.B = h->B; a.ngroups = h->ngroups; a.rec = h->rec; a.gbase = h->gbase; a.memo = h->memo;
-        if (H) CU(cudaMemsetAsync(h->memo, 0xff, (size_t)(h->rows > 0 ? h->rows : 1) * kLanes * sizeof(int2), st));
+        if (!(o->flags & PIC_FLAG_REUSE_TABLES)) free_tables(h);
         a.xs_len = rp * kLanes;
-        const size_t smem = owmr_smem(H, a.xs_len, h->max_smem, &a.nbuf);
-        if (H && a.nbuf < 2) return fail(PIC_ERR_UNSUPPORTED, "shared memory too small for the network");
-        void (*kern)(OwArgs) = H ? k_owmr_picard<true> : k_owmr_picard<false>;
-        CU(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int occ = 0;
-        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kOwThreads, smem));
-        if (occ < 1) return fail(PIC_ERR_CUDA, "OWMR kernel does not fit an SM");
-        const int grid = h->num_sms * occ;
-        void* params[] = {&a};
-        CU(cudaLaunchCooperativeKernel((const void*)kern, grid, kOwThreads, params, smem, st));
-        ++launches;
+        // with a network and PIC_OWMR_FLAG_CLUSTER_W2, W2 resident in clusters of 4 CTAs
+        // (when such clusters fit); otherwise W2 streamed through each CTA per round
+        const bool cluster = H > 0 && (o->flags & PIC_OWMR_FLAG_CLUSTER_W2) &&
+                             cl_smem(H, a.xs_len) + 1024 <= (size_t)h->max_smem;
+        const size_t smem_cl = cl_smem(H, a.xs_len);
+        int ncl = 0;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[2];
+        if (cluster) {
+            CU(cudaFuncSetAttribute((const void*)k_owmr_picard_cl,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cl));
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = kClSize;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            attr[1].id = cudaLaunchAttributeCooperative;
+            attr[1].val.cooperative = 1;
+            cfg.blockDim = dim3(kOwThreads);
+            cfg.dynamicSmemBytes = smem_cl;
+            cfg.stream = st;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            cfg.gridDim = dim3(kClSize * h->num_sms);
+            if (cudaOccupancyMaxActiveClusters(&ncl, (const void*)k_owmr_picard_cl, &cfg) != cudaSuccess)
+                ncl = 0;
+            cudaGetLastError();
+        }
+        if (ncl > 0) {
+            const int grid = ncl * kClSize;
+            pic_status ps = build_tables(h, P, grid, st, &launches);
+            if (ps) return ps;
+            a.B = h->B; a.ngroups = h->ngroups; a.rec = h->rec; a.gbase = h->gbase; a.memo = h->memo;
+            CU(cudaMemsetAsync(h->memo, 0xff, (size_t)(h->rows > 0 ? h->rows : 1) * kLanes * sizeof(int2), st));
+            cfg.gridDim = dim3(grid);
+            cfg.numAttrs = 2;
+            CU(cudaLaunchKernelEx(&cfg, k_owmr_picard_cl, a));
+            ++launches;
+        } else {
+            const size_t smem = owmr_smem(H, a.xs_len, h->max_smem, &a.nbuf);
+            if (H && a.nbuf < 2) return fail(PIC_ERR_UNSUPPORTED, "shared memory too small for the network");
+            void (*kern)(OwArgs) = H ? k_owmr_picard<true> : k_owmr_picard<false>;
+            CU(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            int occ = 0;
+            CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kOwThreads, smem));
+            if (occ < 1) return fail(PIC_ERR_CUDA, "OWMR kernel does not fit an SM");
+            const int grid = h->num_sms * occ;
+            pic_status ps = build_tables(h, P, grid, st, &launches);
+            if (ps) return ps;
+            a.B = h->B; a.ngroups = h->ngroups; a.rec = h->rec; a.gbase = h->gbase; a.memo = h->memo;
+            if (H) CU(cudaMemsetAsync(h->memo, 0xff, (size_t)(h->rows > 0 ? h->rows : 1) * kLanes * sizeof(int2), st));
+            void* params[] = {&a};
+            CU(cudaLaunchCooperativeKernel((const void*)kern, grid, kOwThreads, params, smem, st));
+            ++launches;
+        }
     } else {
         a.rec = h->trec;
         const bool use_smem = h->N <= kMaxSlots;

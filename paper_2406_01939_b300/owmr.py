@@ -12,11 +12,14 @@ import torch
 from . import PIC_MEM_DEVICE, PIC_MEM_HOST, PIC_MODE_PICARD, PIC_MODE_SEQUENTIAL, PIC_OK, \
     PIC_FLAG_TIMING, PicError, _ptr, _stream_handle, lib, pic_last_error
 
-__all__ = ["DeviceOwmr", "DeviceOwmrNet", "pic_owmr_create", "pic_owmr_simulate",
+__all__ = ["DeviceOwmr", "DeviceOwmrNet", "PIC_OWMR_FLAG_CLUSTER_W2", "pic_owmr_create", "pic_owmr_simulate",
            "pic_owmr_destroy", "pic_owmr_desc", "pic_owmr_policy", "pic_owmr_opts",
            "pic_owmr_result", "PIC_MEM_HOST"]
 
 P_ = C.c_void_p
+
+# pic_owmr_opts.flags: keep W2 resident across 4-CTA clusters (pooled rounds) instead of streaming it
+PIC_OWMR_FLAG_CLUSTER_W2 = 1 << 16
 
 
 class pic_owmr_desc(C.Structure):

@@ -9,7 +9,10 @@ import torch
 import paper_2406_01939_b300 as pic
 from oracle import owmr as ow
 from paper_2406_01939_b300 import synth
-from paper_2406_01939_b300.owmr import DeviceOwmr, DeviceOwmrNet
+from paper_2406_01939_b300.owmr import PIC_OWMR_FLAG_CLUSTER_W2, DeviceOwmr, DeviceOwmrNet
+
+# the network's two kernels: W2 streamed per round (default), W2 resident across 4-CTA clusters
+KERNELS = [0, PIC_OWMR_FLAG_CLUSTER_W2]
 
 pytestmark = pytest.mark.gpu
 
@@ -56,26 +59,31 @@ def test_no_network_random_bit_exact(N):
             check(inst, None, P, dev=d)
 
 
-def test_network_bit_exact_and_calls():
+@pytest.mark.parametrize("flags", KERNELS)
+def test_network_bit_exact_and_calls(flags):
     """H = 64 and 512, ragged groups (N = 45 processors over several lanes),
-    skewed store weights; the same calls as the oracle's memo."""
-    for H, T, N, a in ((64, 3000, 45, 0.0), (512, 1500, 37, 0.02), (128, 2500, 70, 0.0)):
+    skewed store weights; the same calls as the oracle's memo; both kernels."""
+    # N = 2,000: 16 processors per CTA, so a round has more pending calls than
+    # one CTA may contribute (8) and the rest wait for the next round
+    for H, T, N, a in ((64, 3000, 45, 0.0), (512, 1500, 37, 0.02), (128, 2500, 70, 0.0),
+                       (256, 4000, 300, 0.0), (64, 30000, 2000, 0.0)):
         inst = rand_inst(H + N, T, N, theorem=H != 128, a=a)
         net = synth.make_owmr_net(H, seed=H)
         d = DeviceOwmr(inst)
         dn = DeviceOwmrNet(net)
         for P in (N, max(1, N // 3)):
-            check(inst, net, P, dev=d, dnet=dn)
+            check(inst, net, P, dev=d, dnet=dn, flags=flags)
 
 
-def test_every_iterate_matches_algorithm_1():
+@pytest.mark.parametrize("flags", KERNELS)
+def test_every_iterate_matches_algorithm_1(flags):
     inst = rand_inst(7, 1200, 9, theorem=False)
     net = synth.make_owmr_net(64, seed=2)
     d = DeviceOwmr(inst)
     for nn in (None, net):
         want = ow.picard_literal(inst, nn, procs_of(9, 9), record=True)
         for k in range(1, want["iters"] + 1):
-            got = d.simulate(nn, num_procs=9, max_iters=k, raise_on_error=False)
+            got = d.simulate(nn, num_procs=9, max_iters=k, raise_on_error=False, flags=flags)
             assert got["status"] == (pic.PIC_OK if k == want["iters"] else pic.PIC_ERR_NOT_CONVERGED)
             np.testing.assert_array_equal(got["actions"].cpu().numpy(), want["iterates"][k - 1])
 
@@ -105,7 +113,8 @@ def test_warm_start():
     assert got["iters"] == want["iters"] and got["policy_calls"] == want["evals"]
 
 
-def test_window_bit_exact_and_passes():
+@pytest.mark.parametrize("flags", KERNELS)
+def test_window_bit_exact_and_passes(flags):
     """The max_steps window: same iterates, passes and network calls as the
     oracle's windowed walk, for windows from one step to the horizon."""
     net = synth.make_owmr_net(64, seed=12)
@@ -117,7 +126,7 @@ def test_window_bit_exact_and_passes():
             for nn, dd in ((None, None), (net, dn)):
                 seq = ow.seq_sim(inst, nn)
                 want = ow.picard_walk(inst, nn, procs_of(N, N), window=W)
-                got = d.simulate(dd, max_steps=W)
+                got = d.simulate(dd, max_steps=W, flags=flags)
                 np.testing.assert_array_equal(got["actions"].cpu().numpy(), seq["actions"])
                 np.testing.assert_array_equal(got["state"].cpu().numpy(), seq["x_final"])
                 assert got["iters"] == want["iters"], (W, got["iters"], want["iters"])
@@ -127,21 +136,23 @@ def test_window_bit_exact_and_passes():
     d = DeviceOwmr(inst)
     want = ow.picard_literal(inst, net, procs_of(9, 9), record=True, window=100)
     for k in range(1, want["iters"] + 1, 3):
-        got = d.simulate(net, max_iters=k, max_steps=100, raise_on_error=False)
+        got = d.simulate(net, max_iters=k, max_steps=100, raise_on_error=False, flags=flags)
         np.testing.assert_array_equal(got["actions"].cpu().numpy(), want["iterates"][k - 1])
 
 
 def test_window_scaled_base_case():
     """The base case at a tenth of its size (365,000 steps, 400 stores) with a
     window of 16,000 steps: the oracle's passes and network calls (each step's
-    network evaluated about once)."""
+    network evaluated about once), through both kernels."""
     inst, _ = synth.owmr_base(0, T=365_000, N=400, H=64)
     inst.S = inst.s + 7_000
     net = synth.make_owmr_net(64, seed=0)
     want = ow.picard_walk(inst, net, procs_of(400, 400), window=16_000)
-    got = DeviceOwmr(inst).simulate(net, max_steps=16_000)
-    np.testing.assert_array_equal(got["actions"].cpu().numpy(), want["actions"])
-    assert got["iters"] == want["iters"] and got["policy_calls"] == want["evals"]
+    d = DeviceOwmr(inst)
+    for flags in KERNELS:
+        got = d.simulate(net, max_steps=16_000, flags=flags)
+        np.testing.assert_array_equal(got["actions"].cpu().numpy(), want["actions"])
+        assert got["iters"] == want["iters"] and got["policy_calls"] == want["evals"]
 
 
 def test_many_groups_per_cta():
@@ -193,9 +204,12 @@ def test_base_case_full_size():
     np.testing.assert_array_equal(got["state"].cpu().numpy(), seq["x_final"])
     assert got["iters"] <= 2 * seq["R"] + 2
     dn = DeviceOwmrNet(net)
-    pg = d.simulate(dn)
+    pg = d.simulate(dn, max_steps=80_000)
     sg = d.simulate(dn, mode="sequential")
     assert torch.equal(pg["actions"], sg["actions"]) and torch.equal(pg["state"], sg["state"])
+    ps = d.simulate(dn, max_steps=80_000, flags=PIC_OWMR_FLAG_CLUSTER_W2)
+    assert torch.equal(ps["actions"], pg["actions"]) and ps["iters"] == pg["iters"]
+    assert ps["policy_calls"] == pg["policy_calls"]
     assert pg["R"] == sg["R"] and pg["lost"] == sg["lost"]
     Tp = 20_000
     pre = synth.OwmrInstance(Tp, inst.N, inst.ret[:Tp], inst.dem[:Tp], inst.ex[:Tp], inst.cap,

@@ -90,6 +90,8 @@ def parse():
     p.add_argument("--flags", type=int, default=0, help="extra pic_sim_opts flags (tuning)")
     p.add_argument("--max-steps", type=int, default=-1,
                    help="Picard window of App. A.3 in orders (-1: the workload's default, 0: none)")
+    p.add_argument("--skew", type=float, default=0.0,
+                   help="owmr_base: store weights (1 - skew)^n (App. B.3 ablation; 0 = uniform)")
     p.add_argument("--B", type=int, default=0,
                    help="trajectories of batch_uneven / pg_large (0 = the workload's 512 / 64)")
     return p.parse_args()
@@ -319,7 +321,7 @@ def run_reference(args):
     if args.workload == "owmr_base":
         from oracle import owmr as ow
         from paper_2406_01939_b300 import synth
-        inst, net = synth.owmr_base(args.seed, **({"T": args.T} if args.T else {}))
+        inst, net = synth.owmr_base(args.seed, a=args.skew, **({"T": args.T} if args.T else {}))
         cut = lambda n: synth.OwmrInstance(n, inst.N, inst.ret[:n], inst.dem[:n], inst.ex[:n],
                                            inst.cap, inst.x0r, inst.sl, inst.Sl, inst.X0, inst.s,
                                            inst.S)
@@ -666,10 +668,11 @@ def owmr_flops_per_call(H):
 def owmr_config(args, inst, net, W, P):
     return {"workload": "owmr_base",
             "desc": (f"OWMR inventory control (App. B.3 base case): T={inst.T} unit demands over "
-                     f"N={inst.N} stores (uniform), stores (s_n,S_n)=(10,20) capacity 24, central "
+                     f"N={inst.N} stores ({'uniform' if not args.skew else f'weights (1-{args.skew})^n'}), "
+                     "stores (s_n,S_n)=(10,20) capacity 24, central "
                      f"(s,S)=({inst.s},{inst.S}), retailer network 3-{net.H}-{net.H}-1 BF16 "
                      "N(0,0.02) fed (stock, demand, steps since the store's previous demand/4096)"),
-            "T": inst.T, "N": inst.N, "hidden": net.H, "procs": P, "max_steps": W,
+            "T": inst.T, "N": inst.N, "hidden": net.H, "procs": P, "max_steps": W, "skew": args.skew,
             "l2": "working set (about 0.3 GB) exceeds L2; flushed between timed steps (256 MiB write)"}
 
 
@@ -683,7 +686,8 @@ def run_owmr(args, dev, world, rank):
     from paper_2406_01939_b300.owmr import (DeviceOwmr, DeviceOwmrNet, pic_owmr_create,
                                             pic_owmr_desc, pic_owmr_destroy, pic_owmr_opts,
                                             pic_owmr_policy, pic_owmr_simulate)
-    inst, net = synth.owmr_base(rank_seed(args.seed, rank), **({"T": args.T} if args.T else {}))
+    inst, net = synth.owmr_base(rank_seed(args.seed, rank), a=args.skew,
+                                **({"T": args.T} if args.T else {}))
     W = args.max_steps if args.max_steps >= 0 else DEFAULT_MAX_STEPS["owmr_base"]
     P = inst.N
     d = DeviceOwmr(inst, device=dev)

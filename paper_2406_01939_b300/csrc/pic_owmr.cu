@@ -168,6 +168,11 @@ __device__ __forceinline__ int q_of(int base, int room, float z) {
 
 constexpr int kMaxBufSlots = 2;  // mbarriers reserved for the W2 ring (kMaxBuf)
 
+// Processors are interleaved over the groups (processor p: group p mod ngroups,
+// lane p / ngroups) so that the busiest stores, which skewed demand puts at the
+// low indices, fall into different CTAs.  Lanes of group g:
+__device__ __forceinline__ int group_lanes(const OwArgs& a, int g) { return (a.P - 1 - g) / a.ngroups + 1; }
+
 // Shared memory of the Picard kernel (dynamic; the network part only with H > 0).
 struct __align__(16) OwSmem {
     int4 rec[kCh][kLanes];
@@ -535,11 +540,11 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
         long long my_lost = 0, my_ship = 0, my_R = 0;
         unsigned long long my_evals = 0, my_rounds = 0;
         for (int g = blockIdx.x; g < a.ngroups; g += gridDim.x) {
-            const int p0 = g * a.B, nb = min(a.B, a.P - p0);
-            // stock of the group's retailers: slot j * 32 + lane for n = p0 + lane + j P
+            const int nb = group_lanes(a, g);
+            // stock of the group's retailers: slot j * 32 + lane for n = lane_proc + j P
             for (int i = tid; i < a.rp * kLanes; i += kOwThreads) {
                 const int l = i & 31, j = i >> 5;
-                const long long n = (long long)p0 + l + (long long)j * a.P;
+                const long long n = (long long)l * a.ngroups + g + (long long)j * a.P;
                 if (l < nb && n < a.N) xs[i] = a.x0r[n];
             }
             // per-lane walk state (warp 0)
@@ -662,7 +667,7 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
             __syncthreads();
             for (int i = tid; i < a.rp * kLanes; i += kOwThreads) {
                 const int l = i & 31, j = i >> 5;
-                const long long n = (long long)p0 + l + (long long)j * a.P;
+                const long long n = (long long)l * a.ngroups + g + (long long)j * a.P;
                 if (l < nb && n < a.N) a.xfin[n] = xs[i];
             }
         }
@@ -904,7 +909,7 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard_cl(OwArgs a) {
         int g = blockIdx.x;
         bool fin = g >= a.ngroups, loaded = false, group_init = false;
         long long r0 = 0, row1 = 0;
-        int p0 = 0, nb = 0;
+        int nb = 0;
         // lane state (warp 0)
         int x0a = 0, ta = -1, qc_after = 0, done = 0, pos = 0;
         int pend = 0, pt = 0, px0 = 0, py = 0, pold = 0, pqc = 0, pslot = 0;
@@ -912,11 +917,10 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard_cl(OwArgs a) {
             // advance the CTA's walk until some lane waits for a call or the CTA is done
             while (!fin) {
                 if (!group_init) {
-                    p0 = g * a.B;
-                    nb = min(a.B, a.P - p0);
+                    nb = group_lanes(a, g);
                     for (int i = tid; i < a.rp * kLanes; i += kOwThreads) {
                         const int l = i & 31, j = i >> 5;
-                        const long long n = (long long)p0 + l + (long long)j * a.P;
+                        const long long n = (long long)l * a.ngroups + g + (long long)j * a.P;
                         if (l < nb && n < a.N) xs[i] = a.x0r[n];
                     }
                     x0a = a.X0; ta = -1; qc_after = 0; done = 0; pend = 0;
@@ -930,7 +934,7 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard_cl(OwArgs a) {
                         __syncthreads();
                         for (int i = tid; i < a.rp * kLanes; i += kOwThreads) {
                             const int l = i & 31, j = i >> 5;
-                            const long long n = (long long)p0 + l + (long long)j * a.P;
+                            const long long n = (long long)l * a.ngroups + g + (long long)j * a.P;
                             if (l < nb && n < a.N) a.xfin[n] = xs[i];
                         }
                         g += gridDim.x;
@@ -1215,18 +1219,18 @@ __global__ void k_ow_group_rows(int P, int B, int ngroups, const int32_t* __rest
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ngroups) return;
     int m = 0;
-    for (int l = 0; l < B && g * B + l < P; ++l) m = max(m, cnt[g * B + l]);
+    for (long long p = g; p < P; p += ngroups) m = max(m, cnt[p]);  // lanes of group g
     rows[g] = (m + kCh - 1) / kCh * kCh;
 }
 
-__global__ void k_ow_rec(int T, int B, const int32_t* __restrict__ key_s,
+__global__ void k_ow_rec(int T, int ngroups, const int32_t* __restrict__ key_s,
                          const int32_t* __restrict__ perm, const int32_t* __restrict__ off,
                          const int32_t* __restrict__ gbase, const int32_t* __restrict__ ret,
                          const int32_t* __restrict__ dem, const int32_t* __restrict__ ex,
                          int4* __restrict__ rec) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < T;
          i += (long long)gridDim.x * blockDim.x) {
-        const int p = key_s[i], j = (int)(i - off[p]), g = p / B, l = p - g * B;
+        const int p = key_s[i], j = (int)(i - off[p]), g = p % ngroups, l = p / ngroups;
         const int t = perm[i];
         rec[((long long)gbase[g] + j) * kLanes + l] = make_int4(t, ret[t], dem[t], ex[t]);
     }
@@ -1332,7 +1336,7 @@ pic_status build_tables(pic_owmr* h, int P, int ctas, cudaStream_t st, int* laun
         if (!e) e = cudaMemsetAsync(h->rec, 0xff, nrec * sizeof(int4), st);
         if (!e && T > 0) {
             k_ow_rec<<<nblk(T, 256) < 4096 ? nblk(T, 256) : 4096, 256, 0, st>>>(
-                T, B, key_s, perm, off, h->gbase, h->ret, h->dem, h->ex, h->rec);
+                T, ngroups, key_s, perm, off, h->gbase, h->ret, h->dem, h->ex, h->rec);
             *launches += 1;
         }
     }

@@ -80,6 +80,9 @@ struct OwArgs {
     int4* pre;              // [T + 1]
     int4* tsum;             // [ntiles]
     int2* memo;             // interleaved like rec: {y, q} of the last evaluation
+    const int32_t* cmax;    // [rows / 32] per chunk: latest first-step time over its lanes
+    int4* ckpt;             // [rows / 32][2][32] walk state of each lane before each chunk
+    int resume;             // walks resume at the last chunk that starts before w
     int32_t* xfin;          // [N] retailer stock after the last pass's walks
     OwCtrl* oc;
     const uint16_t *W1, *b1, *W2, *b2, *w3, *b3;
@@ -182,7 +185,7 @@ struct __align__(16) OwSmem {
     int feat_y[kLanes], feat_d[kLanes], feat_e[kLanes], feat_base[kLanes], feat_room[kLanes];
     int qout[kLanes];
     int rowidx[kLanes];
-    int pend_any, pend_rows, all_done, abort;
+    int pend_any, pend_rows, all_done, abort, resume_q;
     unsigned long long full[kMaxBufSlots];  // W2 buffers: the copy landed
 };
 
@@ -450,11 +453,14 @@ size_t net_fixed_smem(int H) {
 
 // Phases A and B of pass `pass`: tile summaries of the cache, a grid barrier,
 // then pre[t] = {Qc, D, LR, alpha_t} for the CTA's contiguous tiles (and
-// pre[T]), and a second grid barrier.  Returns false when a barrier failed.
+// pre[T]), and a second grid barrier.  Tiles that end at or before `wstart`
+// (the previous pass's first change) keep last pass's summaries and records:
+// the cache before wstart did not change.  Returns false when a barrier failed.
 __device__ bool prefix_phases(const OwArgs& a, OwCtrl* oc, Mono* ws, int tile0, int tile1,
-                              int pass, unsigned long long deadline) {
+                              int pass, unsigned long long deadline, int wstart) {
     const int tid = threadIdx.x;
-    for (int tile = tile0; tile < tile1; ++tile) {
+    const int tb = max(tile0, wstart / kTile);  // first tile this pass recomputes
+    for (int tile = tb; tile < tile1; ++tile) {
         const long long base = (long long)tile * kTile + tid * kItems;
         Mono m = mono_id();
 #pragma unroll 4
@@ -473,20 +479,20 @@ __device__ bool prefix_phases(const OwArgs& a, OwCtrl* oc, Mono* ws, int tile0, 
         oc->fct[nx] = INT_MAX;
         oc->lost[nx] = oc->shipped[nx] = oc->R[nx] = 0;
     }
-    if (tile0 < tile1 || (blockIdx.x == 0 && a.T == 0)) {
-        // prefix of the tiles before tile0
+    if (tb < tile1 || (blockIdx.x == 0 && a.T == 0)) {
+        // prefix of the tiles before tb
         Mono m = mono_id();
-        const int per = (tile0 + kOwThreads - 1) / kOwThreads;
+        const int per = (tb + kOwThreads - 1) / kOwThreads;
         for (int i = 0; i < per; ++i) {
             const int tl = tid * per + i;
-            if (tl < tile0) {
+            if (tl < tb) {
                 const int4 s4 = a.tsum[tl];
                 m = mono_cat(m, Mono{s4.x, s4.y, s4.z});
             }
         }
         Mono run;
         block_exscan_mono(m, &run, ws);
-        for (int tile = tile0; tile < tile1; ++tile) {
+        for (int tile = tb; tile < tile1; ++tile) {
             const long long base = (long long)tile * kTile + tid * kItems;
             Mono loc = mono_id();
             for (int i = 0; i < kItems; ++i) {
@@ -534,7 +540,7 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
     for (int pass = 1;; ++pass) {
         const int slot = pass % 3;
         const int whi = a.window > 0 ? (int)min((long long)a.T, (long long)w + a.window) : a.T;
-        if (!prefix_phases(a, oc, sm.ws, tile0, tile1, pass, deadline)) break;
+        if (!prefix_phases(a, oc, sm.ws, tile0, tile1, pass, deadline, w)) break;
         // ---------------- phase C: walks
         int my_changed = 0, my_first = INT_MAX;
         long long my_lost = 0, my_ship = 0, my_R = 0;
@@ -547,11 +553,49 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
                 const long long n = (long long)l * a.ngroups + g + (long long)j * a.P;
                 if (l < nb && n < a.N) xs[i] = a.x0r[n];
             }
-            // per-lane walk state (warp 0)
-            int x0a = a.X0, ta = -1, qc_after = 0, done = 0;
+            // per-lane walk state (warp 0); gl_*: the lane's statistics over its steps
+            int x0a = a.X0, ta = -1, qc_after = 0, done = 0, wdone = 0;
             int pend = 0, pt = 0, px0 = 0, py = 0, pold = 0, pqc = 0, pslot = 0;
+            long long gl_lost = 0;
+            int gl_ship = 0, gl_R = 0;
             const long long row0 = a.gbase[g], row1 = a.gbase[g + 1];
-            for (long long r0 = row0; r0 < row1; r0 += kCh) {
+            long long rstart = row0;
+            if (a.resume && w > 0) {
+                // the last chunk whose lanes' states precede w (keys increase along the group)
+                if (warp == 0) {
+                    const int q0 = (int)(row0 / kCh), q1 = (int)(row1 / kCh);
+                    int best = q0;
+                    for (int qb = q0; qb < q1; qb += 32) {
+                        const int q = qb + lane;
+                        const unsigned m = __ballot_sync(kFull, q < q1 && a.cmax[q] < w);
+                        if (m) best = qb + 31 - __clz(m);
+                        if (m != kFull) break;
+                    }
+                    if (lane == 0) sm.resume_q = best;
+                }
+                __syncthreads();
+                rstart = (long long)sm.resume_q * kCh;
+                if (rstart > row0 && warp == 0 && lane < nb) {
+                    const size_t q = (size_t)sm.resume_q * 2 * kLanes;
+                    const int4 c0 = a.ckpt[q + lane], c1 = a.ckpt[q + kLanes + lane];
+                    x0a = c0.x;
+                    ta = c0.y;
+                    qc_after = c0.z;
+                    xs[lane] = c0.w;
+                    gl_lost = (long long)(((unsigned long long)(unsigned)c1.y << 32) | (unsigned)c1.x);
+                    gl_ship = c1.z;
+                    gl_R = c1.w;
+                }
+            }
+            for (long long r0 = rstart; r0 < row1; r0 += kCh) {
+                if (a.resume && warp == 0 && lane < nb && !wdone) {
+                    // state before this chunk (lanes that stopped at the window end excepted)
+                    const size_t q = (size_t)(r0 / kCh) * 2 * kLanes;
+                    a.ckpt[q + lane] = make_int4(x0a, ta, qc_after, xs[lane]);
+                    a.ckpt[q + kLanes + lane] =
+                        make_int4((int)(unsigned)(unsigned long long)gl_lost,
+                                  (int)(unsigned)((unsigned long long)gl_lost >> 32), gl_ship, gl_R);
+                }
                 __syncthreads();
                 for (int i = tid; i < kCh * kLanes; i += kOwThreads)
                     (&sm.rec[0][0])[i] = a.rec[r0 * kLanes + i];
@@ -577,8 +621,8 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
                                 const int r = px0 - q <= a.s;
                                 const int recv = q < px0 ? q : px0;
                                 xs[pslot] = py + recv;
-                                my_ship += recv;
-                                my_R += r;
+                                gl_ship += recv;
+                                gl_R += r;
                                 x0a = r ? a.S : (px0 > q ? px0 - q : 0);
                                 qc_after = pqc + (pold >> 1);
                                 ta = pt;
@@ -596,6 +640,7 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
                                 if (rc.x < 0 || rc.x >= whi) {  // list end or window end
                                     pos = kCh;
                                     done = 1;
+                                    wdone = rc.x >= 0;
                                     break;
                                 }
                                 const int t = rc.x, n = rc.y, d = rc.z;
@@ -605,7 +650,7 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
                                 const int slotn = (n / a.P) * kLanes + lane;
                                 const int xn = xs[slotn];
                                 const int y = xn > d ? xn - d : 0;
-                                my_lost += d > xn ? d - xn : 0;
+                                gl_lost += d > xn ? d - xn : 0;
                                 const int base = retailer_base(y, __ldg(a.sl + n), __ldg(a.Sl + n));
                                 const int room = __ldg(a.cap + n) - y;
                                 int q;
@@ -630,8 +675,8 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
                                 const int r = x0 - q <= a.s;
                                 const int recv = q < x0 ? q : x0;
                                 xs[slotn] = y + recv;
-                                my_ship += recv;
-                                my_R += r;
+                                gl_ship += recv;
+                                gl_R += r;
                                 x0a = r ? a.S : (x0 > q ? x0 - q : 0);
                                 qc_after = pr.x + (pr.w >> 1);
                                 ta = t;
@@ -670,6 +715,9 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
                 const long long n = (long long)l * a.ngroups + g + (long long)j * a.P;
                 if (l < nb && n < a.N) a.xfin[n] = xs[i];
             }
+            my_lost += gl_lost;
+            my_ship += gl_ship;
+            my_R += gl_R;
         }
         // CTA totals
         if (warp == 0) {
@@ -901,7 +949,7 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard_cl(OwArgs a) {
     for (int pass = 1;; ++pass) {
         const int slot = pass % 3;
         const int whi = a.window > 0 ? (int)min((long long)a.T, (long long)w + a.window) : a.T;
-        if (!cl_agree(sm, rank, prefix_phases(a, oc, sm.ws, tile0, tile1, pass, deadline))) break;
+        if (!cl_agree(sm, rank, prefix_phases(a, oc, sm.ws, tile0, tile1, pass, deadline, w))) break;
         // ---------------- phase C: walks with cluster rounds
         int my_changed = 0, my_first = INT_MAX;
         long long my_lost = 0, my_ship = 0, my_R = 0;
@@ -1227,12 +1275,29 @@ __global__ void k_ow_rec(int T, int ngroups, const int32_t* __restrict__ key_s,
                          const int32_t* __restrict__ perm, const int32_t* __restrict__ off,
                          const int32_t* __restrict__ gbase, const int32_t* __restrict__ ret,
                          const int32_t* __restrict__ dem, const int32_t* __restrict__ ex,
-                         int4* __restrict__ rec) {
+                         int4* __restrict__ rec, int32_t* __restrict__ lastt) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < T;
          i += (long long)gridDim.x * blockDim.x) {
         const int p = key_s[i], j = (int)(i - off[p]), g = p % ngroups, l = p / ngroups;
         const int t = perm[i];
         rec[((long long)gbase[g] + j) * kLanes + l] = make_int4(t, ret[t], dem[t], ex[t]);
+        if (j == off[p + 1] - off[p] - 1) lastt[g * kLanes + l] = t;  // the lane's last step
+    }
+}
+
+// Per chunk (kCh rows of one group), the latest over its lanes of the time that
+// the lane's state before the chunk depends on: its first step in the chunk, or
+// its last step when its list ended earlier (-1: no steps).  A lane's state
+// before the chunk is unchanged by a pass whose first change is after that time.
+__global__ void k_ow_cmax(const int32_t* __restrict__ gbase, const int4* __restrict__ rec,
+                          const int32_t* __restrict__ lastt, int32_t* __restrict__ cmax) {
+    const int g = blockIdx.x, lane = threadIdx.x;
+    const int lt = lastt[g * kLanes + lane];
+    for (long long r = gbase[g]; r < gbase[g + 1]; r += kCh) {
+        int v = rec[r * kLanes + lane].x;
+        if (v < 0) v = lt;
+        v = __reduce_max_sync(kFull, v);
+        if (lane == 0) cmax[r / kCh] = v;
     }
 }
 
@@ -1274,6 +1339,9 @@ struct pic_owmr {
     int4* rec = nullptr;   // interleaved step records of the Picard walks
     int4* trec = nullptr;  // time-order records for the sequential kernel
     int2* memo = nullptr;
+    int32_t* cmax = nullptr;
+    int32_t* lastt = nullptr;
+    int4* ckpt = nullptr;
     int32_t* gbase = nullptr;
     int4* tsum = nullptr;
     int ntiles = 0;
@@ -1284,6 +1352,11 @@ namespace {
 void free_tables(pic_owmr* h) {
     cudaFree(h->rec);
     cudaFree(h->memo);
+    cudaFree(h->cmax);
+    cudaFree(h->lastt);
+    cudaFree(h->ckpt);
+    h->cmax = h->lastt = nullptr;
+    h->ckpt = nullptr;
     cudaFree(h->gbase);
     h->rec = nullptr;
     h->memo = nullptr;
@@ -1331,12 +1404,21 @@ pic_status build_tables(pic_owmr* h, int P, int ctas, cudaStream_t st, int* laun
     if (!e) e = cudaStreamSynchronize(st);
     if (!e) {
         const size_t nrec = (size_t)(rows_total > 0 ? rows_total : 1) * kLanes;
+        const size_t nchunk = nrec / ((size_t)kCh * kLanes) + 1;
         e = cudaMalloc(&h->rec, nrec * sizeof(int4));
         if (!e) e = cudaMalloc(&h->memo, nrec * sizeof(int2));
+        if (!e) e = cudaMalloc(&h->cmax, nchunk * sizeof(int32_t));
+        if (!e) e = cudaMalloc(&h->lastt, (size_t)ngroups * kLanes * sizeof(int32_t));
+        if (!e) e = cudaMalloc(&h->ckpt, nchunk * 2 * kLanes * sizeof(int4));
         if (!e) e = cudaMemsetAsync(h->rec, 0xff, nrec * sizeof(int4), st);
+        if (!e) e = cudaMemsetAsync(h->lastt, 0xff, (size_t)ngroups * kLanes * sizeof(int32_t), st);
         if (!e && T > 0) {
             k_ow_rec<<<nblk(T, 256) < 4096 ? nblk(T, 256) : 4096, 256, 0, st>>>(
-                T, ngroups, key_s, perm, off, h->gbase, h->ret, h->dem, h->ex, h->rec);
+                T, ngroups, key_s, perm, off, h->gbase, h->ret, h->dem, h->ex, h->rec, h->lastt);
+            *launches += 1;
+        }
+        if (!e) {
+            k_ow_cmax<<<ngroups, kLanes, 0, st>>>(h->gbase, h->rec, h->lastt, h->cmax);
             *launches += 1;
         }
     }
@@ -1574,6 +1656,8 @@ pic_status pic_owmr_simulate(pic_owmr* h, const pic_owmr_policy* pol, const pic_
             pic_status ps = build_tables(h, P, grid, st, &launches);
             if (ps) return ps;
             a.B = h->B; a.ngroups = h->ngroups; a.rec = h->rec; a.gbase = h->gbase; a.memo = h->memo;
+            a.cmax = h->cmax; a.ckpt = h->ckpt;
+            a.resume = rp == 1;  // checkpoints hold one store's stock per lane
             if (H) CU(cudaMemsetAsync(h->memo, 0xff, (size_t)(h->rows > 0 ? h->rows : 1) * kLanes * sizeof(int2), st));
             void* params[] = {&a};
             CU(cudaLaunchCooperativeKernel((const void*)kern, grid, kOwThreads, params, smem, st));

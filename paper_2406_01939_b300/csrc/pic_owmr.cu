@@ -15,7 +15,13 @@
 //      Retailer stock lives in shared memory (a retailer belongs to one lane).
 //      With a network, a lane whose step needs a call (memo miss) parks it;
 //      the CTA then evaluates all parked calls as one batched FP32 round.
-// The loop ends after the first pass that changed no cached action.
+// Nothing before the previous pass's first changed step w moved, so phase B
+// keeps the tiles that end before w, and each walk resumes from a checkpoint
+// at its last chunk whose lanes' states precede w.  With the max_steps window
+// a pass evaluates only steps before w + max_steps.  The loop ends after the
+// first pass that changed no cached action with the window covering the
+// horizon.  Processors are interleaved over the CTAs' groups of 32 lanes.
+// k_owmr_picard_cl is the same loop with W2 resident across 4-CTA clusters.
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>

@@ -56,7 +56,13 @@ enum {
 /* Simulation modes (pic_sim_opts.mode). */
 enum {
     PIC_MODE_PICARD = 0,    /* Algorithm 1 on contiguous time chunks */
-    PIC_MODE_SEQUENTIAL = 1 /* one order at a time on the GPU (the baseline of Sec. 4) */
+    PIC_MODE_SEQUENTIAL = 1, /* one order at a time on the GPU (the baseline of Sec. 4) */
+    PIC_MODE_PICARD_PRODUCTS = 2 /* Algorithm 1 with the product partition of Sec. 3: processor
+                                    m owns the orders of the products k with k mod P = m,
+                                    P = num_chunks (0: K); greedy and bid-price policies, with
+                                    or without node capacity; single instances; no max_steps.
+                                    Same fixed point; Thm. 3.1 bounds the passes by |Q_T| + 2
+                                    (Q_T: nodes whose capacity runs out) */
 };
 
 /* Where a pointer lives. */

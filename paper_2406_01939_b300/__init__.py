@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(HERE, "libpic.so")
 PIC_OK, PIC_ERR_INVALID_ARG, PIC_ERR_CUDA, PIC_ERR_OOM = 0, 1, 2, 3
 PIC_ERR_NOT_CONVERGED, PIC_ERR_TIMEOUT, PIC_ERR_UNSUPPORTED = 4, 5, 6
 PIC_POLICY_GREEDY, PIC_POLICY_DUAL, PIC_POLICY_MLP, PIC_POLICY_GUMBEL = 0, 1, 2, 3
-PIC_MODE_PICARD, PIC_MODE_SEQUENTIAL = 0, 1
+PIC_MODE_PICARD, PIC_MODE_SEQUENTIAL, PIC_MODE_PICARD_PRODUCTS = 0, 1, 2
 PIC_MEM_HOST, PIC_MEM_DEVICE = 0, 1
 PIC_FLAG_NO_RESET, PIC_FLAG_REUSE_TABLES, PIC_FLAG_TIMING, PIC_FLAG_GROUP_KERNEL = 1, 2, 4, 8
 PIC_FLAG_GRAPH, PIC_FLAG_NO_TC, PIC_FLAG_TC, PIC_FLAG_NO_SAT = 16, 32, 64, 128
@@ -31,7 +31,8 @@ PIC_FLAG_WARP_GROUP = 256
 
 POLICY_KINDS = {"greedy": PIC_POLICY_GREEDY, "dual": PIC_POLICY_DUAL, "mlp": PIC_POLICY_MLP,
                 "gumbel": PIC_POLICY_GUMBEL}
-MODES = {"picard": PIC_MODE_PICARD, "sequential": PIC_MODE_SEQUENTIAL}
+MODES = {"picard": PIC_MODE_PICARD, "sequential": PIC_MODE_SEQUENTIAL,
+         "products": PIC_MODE_PICARD_PRODUCTS}
 
 
 class PicError(RuntimeError):

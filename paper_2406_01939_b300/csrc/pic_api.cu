@@ -406,7 +406,8 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
         return fail(PIC_ERR_INVALID_ARG, "instance, policy, opts and actions_out are required");
     Instance& I = h->I;
     if (I.batch) return fail(PIC_ERR_INVALID_ARG, "batch instance: use pic_simulate_batch");
-    if (opts->mode != PIC_MODE_PICARD && opts->mode != PIC_MODE_SEQUENTIAL)
+    if (opts->mode != PIC_MODE_PICARD && opts->mode != PIC_MODE_SEQUENTIAL &&
+        opts->mode != PIC_MODE_PICARD_PRODUCTS)
         return fail(PIC_ERR_INVALID_ARG, "unknown mode %d", opts->mode);
     if (opts->out_mem != PIC_MEM_HOST && opts->out_mem != PIC_MEM_DEVICE)
         return fail(PIC_ERR_INVALID_ARG, "unknown out_mem %d", opts->out_mem);
@@ -425,6 +426,8 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
         return fail(PIC_ERR_INVALID_ARG, "negative num_chunks, max_iters, seg_window or max_steps");
     if (opts->max_steps > 0 && I.has_cap)
         return fail(PIC_ERR_UNSUPPORTED, "the max_steps window is not supported with node capacity");
+    if (opts->mode == PIC_MODE_PICARD_PRODUCTS && (mlp || opts->max_steps > 0))
+        return fail(PIC_ERR_UNSUPPORTED, "product partition: greedy and bid-price policies, no window");
     cudaStream_t st = (cudaStream_t)opts->stream;
     const size_t T = I.T, K = I.K, N = I.N;
     const bool host_out = opts->out_mem == PIC_MEM_HOST;
@@ -451,6 +454,27 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
         if (T) CU(cudaMemcpyAsync(actions_out, I.act_t, T, okind, st));
         if (final_stock)
             CU(cudaMemcpyAsync(final_stock, I.xwork, sizeof(int32_t) * K * N, okind, st));
+    } else if (opts->mode == PIC_MODE_PICARD_PRODUCTS) {
+        // processor of product k: k mod M; M > K gives the same assignment as M = K
+        M = opts->num_chunks && opts->num_chunks < (int)K ? opts->num_chunks : (int)K;
+        iters_cap = opts->max_iters ? opts->max_iters : (T < (size_t)INT_MAX ? (int)T + 1 : INT_MAX);
+        if (T) {
+            if (opts->alpha_init) {
+                CU(cudaMemcpyAsync(I.act_t, opts->alpha_init, T, cudaMemcpyDeviceToDevice, st));
+                CU(check_alpha_init(&I, I.act_t, st));
+            } else {
+                CU(cudaMemsetAsync(I.act_t, 0xFF, T, st));  // a^phi everywhere (Alg. 1)
+            }
+        }
+        if (timing) CU(cudaEventRecord(I.ev[1], st));
+        CU(picard_products(&I, pol, M, iters_cap, st));
+        if (timing) CU(cudaEventRecord(I.ev[2], st));
+        if (T) {
+            CU(reduce_costs(&I, I.act_t, I.reg, st));
+            CU(cudaMemcpyAsync(actions_out, I.act_t, T, okind, st));
+        }
+        if (final_stock)
+            CU(cudaMemcpyAsync(final_stock, I.xfin, sizeof(int32_t) * K * N, okind, st));
     } else if (I.has_cap) {
         // time chunks of at most kCapChunk orders, one run per segment
         M = opts->num_chunks ? opts->num_chunks : (int)((T + kCapChunk - 1) / kCapChunk);
@@ -545,7 +569,7 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
         res->total_cost = hc.total_cost;
         res->lost = hc.lost;
         res->policy_calls = (int64_t)hc.policy_calls;
-        res->iters = T ? hc.iters : 1;
+        res->iters = T ? hc.iters : 1;  // (set for every Picard mode)
         res->num_chunks = M;
         res->mlp_calls = mlp ? res->policy_calls : 0;
         res->seg_window = opts->mode == PIC_MODE_PICARD ? I.tables_w : 0;
@@ -563,7 +587,7 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
             CU(cudaEventElapsedTime(&res->total_ms, I.ev[0], I.ev[3]));
         }
     }
-    if (T && opts->mode == PIC_MODE_PICARD && !hc.converged)
+    if (T && opts->mode != PIC_MODE_SEQUENTIAL && !hc.converged)
         return fail(PIC_ERR_NOT_CONVERGED, "no fixed point within %d passes", iters_cap);
     return PIC_OK;
 }

@@ -1,0 +1,274 @@
+// Algorithm 1 with the product partition (Sec. 3: all orders of a product go
+// to one process), for the greedy and bid-price policies, with or without node
+// capacity.  Processor m owns the products k with k mod P = m and, every pass,
+// replays the whole horizon taking its own orders' actions from the policy and
+// every other order's action from the cache.
+//
+// Only the processor's own products' stock matters to its decisions (foreign
+// actions never touch it), and node capacity follows from counts: the capacity
+// of node j before order t, in processor m's view, is
+//   max(0, c_j - q_j),  q_j = successes of cached actions to j before t
+//                            - those of m's own cached actions + m's fresh ones,
+// where a cached action "succeeds" when its product still has stock at j under
+// that product's cached actions alone (once a node's capacity is spent, whether
+// later actions to it find stock no longer matters).  So with S_j(n) the time of
+// the n-th cached success at node j (time order), node j has capacity at t iff
+//   S_j(c_j + own_cached_j - fresh_j) >= t   (or fewer successes than that).
+// A pass therefore needs, from the cache: every cached action's success (its
+// rank among the cached actions of its product and node, against x0), the
+// successes listed per node in time order, then one warp per processor walking
+// its own orders with a threshold S_j(.) per node, refreshed only when its own
+// cached or fresh successes move it.
+#include <climits>
+
+#include "pic_device.cuh"
+
+namespace pic {
+
+namespace {
+
+constexpr int kPartWarps = 8;  // warps (processors) per CTA of the walk
+
+// key of each cached action: product * N + node, or K N for a^phi
+__global__ void k_part_keys(int T, int N, int KN, const int32_t* __restrict__ prod,
+                            const int8_t* __restrict__ act, int32_t* __restrict__ key) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < T;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int a = act[t];
+        key[t] = a >= 0 ? prod[t] * N + a : KN;
+    }
+}
+
+__device__ __forceinline__ int lower_bound_i32(const int32_t* __restrict__ v, int n, int x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (v[mid] < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Success of each cached action (stable sort by key keeps time order inside a
+// key): rank within (product, node) below x0[product][node].  succ[t] = node, or
+// N when the action is a^phi or finds no stock.
+__global__ void k_part_succ(int T, int N, int KN, const int32_t* __restrict__ key_s,
+                            const int32_t* __restrict__ t_s, const int32_t* __restrict__ x0,
+                            int32_t* __restrict__ succ) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < T;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int k = key_s[i];
+        int node = N;
+        if (k < KN) {
+            const int rank = (int)i - lower_bound_i32(key_s, T, k);
+            if (rank < x0[k]) node = k % N;  // x0 is [K][N]: x0[k] = x0[product][node]
+        }
+        succ[t_s[i]] = node;
+    }
+}
+
+// first position of each value 0..nv in a sorted array (offsets, nv + 1 entries)
+__global__ void k_part_offsets(const int32_t* __restrict__ sorted, int n, int nv,
+                               int32_t* __restrict__ off) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v <= nv) off[v] = lower_bound_i32(sorted, n, v);
+}
+
+// processor key of each order
+__global__ void k_part_pkey(int T, int P, const int32_t* __restrict__ prod, int32_t* __restrict__ pk) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < T;
+         t += (long long)gridDim.x * blockDim.x)
+        pk[t] = prod[t] % P;
+}
+
+__global__ void k_part_check_init(int T, int N, const int8_t* __restrict__ a, Ctrl* ctrl) {
+    int b = 0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < T;
+         t += (long long)gridDim.x * blockDim.x)
+        if (a[t] < -1 || a[t] >= N) b = 1;
+    if (b) atomicOr(&ctrl->pad0, 64);
+}
+
+// Capacity threshold of node j with own correction d: the time of the
+// (c_j + d)-th cached success at j; -1 when c_j + d <= 0 (no capacity left),
+// INT_MAX when there are fewer successes (capacity left for the whole horizon).
+__device__ __forceinline__ int part_theta(const int32_t* __restrict__ cap,
+                                          const int32_t* __restrict__ S,
+                                          const int32_t* __restrict__ soff, int j, int d) {
+    const int n = cap[j] + d;
+    if (n <= 0) return -1;
+    const int c = soff[j + 1] - soff[j];
+    return n > c ? INT_MAX : S[soff[j] + n - 1];
+}
+
+// One warp per processor m (grid-stride): its orders in time order.  Lane l
+// holds warehouses l + 32 i.  Stock of m's products in xv (each product belongs
+// to one processor); the decision is the arg min of cost (- lam) over warehouses
+// with stock and capacity, ties to the lowest index, a^phi if none.
+template <int NPL, bool DUAL, bool CAP>
+__global__ void __launch_bounds__(kPartWarps * 32) k_part_walk(
+    int P, int N, const int32_t* __restrict__ own_t, const int32_t* __restrict__ own_off,
+    const int32_t* __restrict__ prod, const int32_t* __restrict__ reg,
+    const int32_t* __restrict__ cost, const int32_t* __restrict__ lam,
+    const int32_t* __restrict__ cap, const int32_t* __restrict__ succ,
+    const int32_t* __restrict__ S, const int32_t* __restrict__ soff, int8_t* __restrict__ act,
+    int32_t* __restrict__ xv, Ctrl* ctrl, int32_t* __restrict__ changed) {
+    const int lane = threadIdx.x & 31;
+    const int nwarps = gridDim.x * kPartWarps;
+    int my_changed = 0;
+    unsigned long long calls = 0;
+    for (int m = blockIdx.x * kPartWarps + (threadIdx.x >> 5); m < P; m += nwarps) {
+        int delta[NPL], theta[NPL];
+#pragma unroll
+        for (int i = 0; i < NPL; ++i) {
+            const int j = lane + 32 * i;
+            delta[i] = 0;
+            theta[i] = (CAP && j < N) ? part_theta(cap, S, soff, j, 0) : INT_MAX;
+        }
+        const int e1 = own_off[m + 1];
+        for (int e = own_off[m]; e < e1; ++e) {
+            const int t = own_t[e], k = prod[t], r = reg[t];
+            int best = INT_MAX;
+#pragma unroll
+            for (int i = 0; i < NPL; ++i) {
+                const int j = lane + 32 * i;
+                if (j < N && xv[(size_t)k * N + j] > 0 && theta[i] >= t) {
+                    int sc = cost[(size_t)r * N + j];
+                    if (DUAL) sc -= lam[(size_t)k * N + j];
+                    best = min(best, sc * 128 + j);
+                }
+            }
+            best = __reduce_min_sync(kFull, best);
+            const int a = best == INT_MAX ? -1 : (best & 127);
+            const int old = act[t];
+            const int sn = CAP ? succ[t] : N;  // this order's cached action, if it succeeded
+#pragma unroll
+            for (int i = 0; i < NPL; ++i) {
+                const int j = lane + 32 * i;
+                if (j == a) {  // the fresh action: one unit of stock, and one of capacity
+                    xv[(size_t)k * N + j] -= 1;
+                    if (CAP) {
+                        delta[i] -= 1;
+                        theta[i] = part_theta(cap, S, soff, j, delta[i]);
+                    }
+                }
+                if (CAP && j == sn && j < N) {  // the replaced cached success no longer counts
+                    delta[i] += 1;
+                    theta[i] = part_theta(cap, S, soff, j, delta[i]);
+                }
+            }
+            if (lane == 0) {
+                act[t] = (int8_t)a;
+                my_changed |= a != old;
+            }
+            ++calls;
+        }
+    }
+    if (lane == 0) {
+        if (my_changed) atomicExch(changed, 1);
+        if (calls) atomicAdd(&ctrl->policy_calls, calls);
+    }
+}
+
+__global__ void k_part_result(Ctrl* ctrl, int iters, int converged) {
+    ctrl->iters = iters;
+    ctrl->converged = converged;
+}
+
+}  // namespace
+
+// Algorithm 1 with the product partition (processor of product k: k mod P) on
+// the instance's orders.  The cache (time order, I->act_t) must hold alpha^0;
+// returns with the last iterate there, the own products' final stock in
+// I->xfin, and iters / converged in I->ctrl.
+cudaError_t picard_products(Instance* I, const pic_policy* pol, int P, int iters_cap,
+                            cudaStream_t st) {
+    const int T = I->T, N = I->N, K = I->K, KN = K * N;
+    const bool dual = pol->kind == PIC_POLICY_DUAL, cap = I->has_cap != 0;
+    const int NPL = N <= 32 ? 1 : (N <= 64 ? 2 : 4);
+    int32_t *key = nullptr, *key_s = nullptr, *t_s = nullptr, *succ = nullptr, *skey = nullptr,
+            *S = nullptr, *pk = nullptr, *pks = nullptr, *own_t = nullptr, *soff = nullptr,
+            *own_off = nullptr, *flag = nullptr;
+    cudaError_t e = cudaSuccess;
+    const size_t Tn = T > 0 ? (size_t)T : 1;
+    auto A = [&](int32_t** p, size_t n) {
+        if (!e) e = cudaMallocAsync(p, n * sizeof(int32_t), st);
+    };
+    A(&key, Tn); A(&key_s, Tn); A(&t_s, Tn); A(&succ, Tn); A(&skey, Tn); A(&S, Tn); A(&pk, Tn);
+    A(&pks, Tn); A(&own_t, Tn); A(&soff, (size_t)N + 2); A(&own_off, (size_t)P + 1); A(&flag, 1);
+    const int gb = (int)((Tn + 255) / 256) < 4 * I->num_sms ? (int)((Tn + 255) / 256) : 4 * I->num_sms;
+    int iters = 0, converged = 0;
+    if (!e && T > 0) {
+        // each processor's orders in time order (stable sort by processor)
+        k_part_pkey<<<gb, 256, 0, st>>>(T, P, I->prod, pk);
+        e = sort_pairs(I, pk, T, P - 1, pks, own_t, I->tmp_a, I->tmp_b, st);
+        if (!e) k_part_offsets<<<(P + 256) / 256, 256, 0, st>>>(pks, T, P, own_off);
+        I->launches += 2;
+    }
+    const int blocks = (P + kPartWarps - 1) / kPartWarps;
+    for (int pass = 1; !e && T > 0 && pass <= iters_cap; ++pass) {
+        if (cap) {
+            // which cached actions find stock, listed per node in time order
+            k_part_keys<<<gb, 256, 0, st>>>(T, N, KN, I->prod, I->act_t, key);
+            e = sort_pairs(I, key, T, KN, key_s, t_s, I->tmp_a, I->tmp_b, st);
+            if (e) break;
+            k_part_succ<<<gb, 256, 0, st>>>(T, N, KN, key_s, t_s, I->x0, succ);
+            e = sort_pairs(I, succ, T, N, skey, S, I->tmp_a, I->tmp_b, st);
+            if (e) break;
+            k_part_offsets<<<1, 128, 0, st>>>(skey, T, N, soff);
+            I->launches += 3;
+        }
+        if ((e = cudaMemcpyAsync(I->xfin, I->x0, sizeof(int32_t) * (size_t)K * N,
+                                 cudaMemcpyDeviceToDevice, st)))
+            break;
+        if ((e = cudaMemsetAsync(flag, 0, sizeof(int32_t), st))) break;
+#define PART_WALK(NP_, D_, C_)                                                              \
+    k_part_walk<NP_, D_, C_><<<blocks, kPartWarps * 32, 0, st>>>(                          \
+        P, N, own_t, own_off, I->prod, I->reg, I->cost, I->lam, I->cap, succ, S, soff, I->act_t, \
+        I->xfin, I->ctrl, flag)
+        if (NPL == 1) {
+            if (dual) { if (cap) PART_WALK(1, true, true); else PART_WALK(1, true, false); }
+            else { if (cap) PART_WALK(1, false, true); else PART_WALK(1, false, false); }
+        } else if (NPL == 2) {
+            if (dual) { if (cap) PART_WALK(2, true, true); else PART_WALK(2, true, false); }
+            else { if (cap) PART_WALK(2, false, true); else PART_WALK(2, false, false); }
+        } else {
+            if (dual) { if (cap) PART_WALK(4, true, true); else PART_WALK(4, true, false); }
+            else { if (cap) PART_WALK(4, false, true); else PART_WALK(4, false, false); }
+        }
+#undef PART_WALK
+        I->launches += 1;
+        int hf = 0;
+        if ((e = cudaGetLastError())) break;
+        if ((e = cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, st))) break;
+        if ((e = cudaStreamSynchronize(st))) break;
+        iters = pass;
+        if (!hf) {
+            converged = 1;
+            break;
+        }
+    }
+    if (T == 0) {
+        iters = 1;
+        converged = 1;
+        if (!e) e = cudaMemcpyAsync(I->xfin, I->x0, sizeof(int32_t) * (size_t)K * N,
+                                    cudaMemcpyDeviceToDevice, st);
+    }
+    if (!e) {
+        k_part_result<<<1, 1, 0, st>>>(I->ctrl, iters, converged);
+        e = cudaGetLastError();
+    }
+    int32_t* bufs[] = {key, key_s, t_s, succ, skey, S, pk, pks, own_t, soff, own_off, flag};
+    for (int32_t* b : bufs)
+        if (b) cudaFreeAsync(b, st);
+    return e;
+}
+
+cudaError_t check_alpha_init(Instance* I, const int8_t* alpha, cudaStream_t st) {
+    if (I->T == 0) return cudaSuccess;
+    k_part_check_init<<<4 * I->num_sms, 256, 0, st>>>(I->T, I->N, alpha, I->ctrl);
+    I->launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace pic

@@ -90,6 +90,9 @@ def parse():
     p.add_argument("--flags", type=int, default=0, help="extra pic_sim_opts flags (tuning)")
     p.add_argument("--max-steps", type=int, default=-1,
                    help="Picard window of App. A.3 in orders (-1: the workload's default, 0: none)")
+    p.add_argument("--partition", default="chunks", choices=["chunks", "products"],
+                   help="FO workloads: Algorithm 1 on contiguous time chunks (default) or the "
+                        "product partition of Sec. 3 (one processor per product)")
     p.add_argument("--skew", type=float, default=0.0,
                    help="owmr_base: store weights (1 - skew)^n (App. B.3 ablation; 0 = uniform)")
     p.add_argument("--B", type=int, default=0,
@@ -159,7 +162,10 @@ def workload_config(args, inst):
                  f"(Zipf 1.1), R={inst.R} regions, x0~Poisson(1.05 T p_k/N), cost~U{{1..100}}, "
                  f"{pol}{cap}"),
         "T": inst.T, "N": inst.N, "K": inst.K, "R": inst.R,
-        "chunks": chunks_of(args), "policy": args.workload == "mlp_medium" and "mlp" or "dual",
+        "chunks": chunks_of(args) if args.partition == "chunks" else None,
+        "partition": "contiguous time chunks" if args.partition == "chunks" else
+                     f"products (processor of product k: k mod {inst.K})",
+        "policy": args.workload == "mlp_medium" and "mlp" or "dual",
         "max_steps": (args.max_steps if args.max_steps >= 0 else
                       DEFAULT_MAX_STEPS.get(args.workload, 0)) or None,
         "l2": "flushed between timed steps (256 MiB write)",
@@ -849,8 +855,14 @@ def main():
     if not args.seg_window:
         args.seg_window = DEFAULT_SEG_WINDOW.get(args.workload, 0)
 
+    products = args.partition == "products"
+    if products and (args.workload == "mlp_medium" or max_steps):
+        raise SystemExit("--partition products: greedy / bid-price workloads, no max_steps window")
+    fo_mode = "products" if products else "picard"
+    fo_chunks = 0 if products else chunks_of(args)
+
     def step(out):
-        return di.simulate(pol, "picard", num_chunks=chunks_of(args), seg_window=args.seg_window,
+        return di.simulate(pol, fo_mode, num_chunks=fo_chunks, seg_window=args.seg_window,
                            flags=pic.PIC_FLAG_TIMING | args.flags, want_stock=False, out=out,
                            max_steps=max_steps)
 
@@ -881,16 +893,18 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in evs]
     value, t_ms = job_rate(T, args.steps, sum(step_ms), world, dev)
     last = results[-1]
-    # one extra (untimed) call with the per-pass trace
-    tr = np.zeros((4096, 4), np.int64)
-    di.simulate(pol, "picard", num_chunks=chunks_of(args), seg_window=args.seg_window,
-                flags=args.flags, want_stock=False, out=act, trace=tr, max_steps=max_steps)
-    ntr = min(last["iters"], 4096)
-    ts, tr_end = tr[:ntr, 0], tr[:ntr, 1]
-    prev = np.r_[0, tr_end[:-1]]
-    pass_trace = {"prefix_us": ((ts - prev) / 1e3).round(1).tolist(),
-                  "replay_us": ((tr_end - ts) / 1e3).round(1).tolist(),
-                  "policy_calls": tr[:ntr, 2].tolist(), "units": tr[:ntr, 3].tolist()}
+    # one extra (untimed) call with the per-pass trace (contiguous chunks)
+    pass_trace = None
+    if not products:
+        tr = np.zeros((4096, 4), np.int64)
+        di.simulate(pol, "picard", num_chunks=chunks_of(args), seg_window=args.seg_window,
+                    flags=args.flags, want_stock=False, out=act, trace=tr, max_steps=max_steps)
+        ntr = min(last["iters"], 4096)
+        ts, tr_end = tr[:ntr, 0], tr[:ntr, 1]
+        prev = np.r_[0, tr_end[:-1]]
+        pass_trace = {"prefix_us": ((ts - prev) / 1e3).round(1).tolist(),
+                      "replay_us": ((tr_end - ts) / 1e3).round(1).tolist(),
+                      "policy_calls": tr[:ntr, 2].tolist(), "units": tr[:ntr, 3].tolist()}
     sim_ms = statistics.median(r["sim_ms"] for r in results)
     prep_ms = statistics.median(r["prep_ms"] for r in results)
     iters = last["iters"]
@@ -918,7 +932,7 @@ def main():
     host["cap"] = pin(inst.cap) if getattr(inst, "cap", None) is not None else None
     host_np = {k: (v.numpy() if v is not None else None) for k, v in host.items()}
     host_act = torch.empty(T, dtype=torch.int8).pin_memory().numpy()
-    opts = pic.make_opts("picard", chunks_of(args), out_mem=pic.PIC_MEM_HOST, seg_window=args.seg_window,
+    opts = pic.make_opts(fo_mode, fo_chunks, out_mem=pic.PIC_MEM_HOST, seg_window=args.seg_window,
                          flags=args.flags, max_steps=max_steps)
     h2d = sum(v.nbytes for v in host_np.values() if v is not None)
     d2h = host_act.nbytes + 64  # actions + the result record
@@ -937,7 +951,21 @@ def main():
 
     # roofline of the dominant kernel (the persistent Picard kernel)
     N = inst.N
-    if args.workload == "mlp_medium":
+    if products:
+        # per pass and order: its time, product, region, cached action (read and
+        # written) and, with capacity, its cached success (4 + 4 + 4 + 2 (+ 4) B), and
+        # its cost row (N x 4 B).  The pass is bound by the longest product's chain
+        # of orders, walked one at a time by one warp: the fraction is low by design.
+        per = 14 + 4 * N + (4 if getattr(inst, "cap", None) is not None else 0)
+        alg_bytes = last["policy_calls"] * per
+        achieved = alg_bytes / (sim_ms / 1000.0) / 1e9
+        peak, peak_kind = load_peaks()
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "kernel": "k_part_walk plus the per-pass sorts (all passes)",
+                    "peak_kind": peak_kind, "algorithmic_bytes": alg_bytes,
+                    "critical_path_orders_per_pass": int(np.bincount(inst.prod).max())}
+    elif args.workload == "mlp_medium":
         roofline = mlp_roofline(fp32_scored(last), N, sim_ms, "k_picard_mlp (persistent, all passes)")
     elif args.workload == "capacity_large":
         # per replayed order: product, region (4 B each), cached action read and

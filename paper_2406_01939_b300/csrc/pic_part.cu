@@ -27,7 +27,8 @@ namespace pic {
 
 namespace {
 
-constexpr int kPartWarps = 8;  // warps (processors) per CTA of the walk
+constexpr int kPartWarps = 4;   // warps (processors) per CTA of the walk
+constexpr int kPartBatch = 32;  // own orders staged per warp at a time
 
 // key of each cached action: product * N + node, or K N for a^phi
 __global__ void k_part_keys(int T, int N, int KN, const int32_t* __restrict__ prod,
@@ -89,22 +90,30 @@ __global__ void k_part_check_init(int T, int N, const int8_t* __restrict__ a, Ct
     if (b) atomicOr(&ctrl->pad0, 64);
 }
 
-// Capacity threshold of node j with own correction d: the time of the
-// (c_j + d)-th cached success at j; -1 when c_j + d <= 0 (no capacity left),
-// INT_MAX when there are fewer successes (capacity left for the whole horizon).
-__device__ __forceinline__ int part_theta(const int32_t* __restrict__ cap,
-                                          const int32_t* __restrict__ S,
-                                          const int32_t* __restrict__ soff, int j, int d) {
-    const int n = cap[j] + d;
-    if (n <= 0) return -1;
-    const int c = soff[j + 1] - soff[j];
-    return n > c ? INT_MAX : S[soff[j] + n - 1];
+// 4-byte asynchronous global -> shared copy (completed by cp.async.wait_group)
+__device__ __forceinline__ void part_copy4(int32_t* dst, const int32_t* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+// S_j(n), the time of the n-th cached success at node j (list at S + base, cnt
+// entries): -1 when n <= 0 (no capacity left), INT_MAX past the list (capacity
+// left for the whole horizon).
+__device__ __forceinline__ int part_sval(const int32_t* __restrict__ S, int base, int cnt, int n) {
+    return n <= 0 ? -1 : (n > cnt ? INT_MAX : __ldg(S + base + n - 1));
 }
 
 // One warp per processor m (grid-stride): its orders in time order.  Lane l
-// holds warehouses l + 32 i.  Stock of m's products in xv (each product belongs
-// to one processor); the decision is the arg min of cost (- lam) over warehouses
-// with stock and capacity, ties to the lowest index, a^phi if none.
+// holds warehouses j = l + 32 q.  The decision is the arg min of cost (- lam)
+// over warehouses with stock and capacity, ties to the lowest index, a^phi if
+// none.  Per lane and warehouse: the stock of the current product (each
+// product belongs to one processor, so the row is this warp's alone), and for
+// capacity n = c_j + own cached successes - fresh actions so far with
+// th = S_j(n) (capacity at t iff th >= t) and its neighbours S_j(n -/+ 1),
+// prefetched so that a one-step change of n needs no load.  Orders are taken
+// kPartBatch at a time: their indices are loaded one batch ahead and their
+// cost rows staged in shared memory, so the per-order chain is shuffles,
+// shared loads and one warp reduction.
 template <int NPL, bool DUAL, bool CAP>
 __global__ void __launch_bounds__(kPartWarps * 32) k_part_walk(
     int P, int N, const int32_t* __restrict__ own_t, const int32_t* __restrict__ own_off,
@@ -113,57 +122,148 @@ __global__ void __launch_bounds__(kPartWarps * 32) k_part_walk(
     const int32_t* __restrict__ cap, const int32_t* __restrict__ succ,
     const int32_t* __restrict__ S, const int32_t* __restrict__ soff, int8_t* __restrict__ act,
     int32_t* __restrict__ xv, Ctrl* ctrl, int32_t* __restrict__ changed) {
+    extern __shared__ int32_t part_smem[];
+    constexpr int kRow = NPL * 32;
     const int lane = threadIdx.x & 31;
+    int32_t* cst = part_smem + (threadIdx.x >> 5) * kPartBatch * kRow;  // [kPartBatch][kRow]
     const int nwarps = gridDim.x * kPartWarps;
     int my_changed = 0;
     unsigned long long calls = 0;
-    for (int m = blockIdx.x * kPartWarps + (threadIdx.x >> 5); m < P; m += nwarps) {
-        int delta[NPL], theta[NPL];
+    int sb[NPL], sc[NPL], cj[NPL];
 #pragma unroll
-        for (int i = 0; i < NPL; ++i) {
-            const int j = lane + 32 * i;
-            delta[i] = 0;
-            theta[i] = (CAP && j < N) ? part_theta(cap, S, soff, j, 0) : INT_MAX;
-        }
-        const int e1 = own_off[m + 1];
-        for (int e = own_off[m]; e < e1; ++e) {
-            const int t = own_t[e], k = prod[t], r = reg[t];
-            int best = INT_MAX;
-#pragma unroll
-            for (int i = 0; i < NPL; ++i) {
-                const int j = lane + 32 * i;
-                if (j < N && xv[(size_t)k * N + j] > 0 && theta[i] >= t) {
-                    int sc = cost[(size_t)r * N + j];
-                    if (DUAL) sc -= lam[(size_t)k * N + j];
-                    best = min(best, sc * 128 + j);
-                }
-            }
-            best = __reduce_min_sync(kFull, best);
-            const int a = best == INT_MAX ? -1 : (best & 127);
-            const int old = act[t];
-            const int sn = CAP ? succ[t] : N;  // this order's cached action, if it succeeded
-#pragma unroll
-            for (int i = 0; i < NPL; ++i) {
-                const int j = lane + 32 * i;
-                if (j == a) {  // the fresh action: one unit of stock, and one of capacity
-                    xv[(size_t)k * N + j] -= 1;
-                    if (CAP) {
-                        delta[i] -= 1;
-                        theta[i] = part_theta(cap, S, soff, j, delta[i]);
-                    }
-                }
-                if (CAP && j == sn && j < N) {  // the replaced cached success no longer counts
-                    delta[i] += 1;
-                    theta[i] = part_theta(cap, S, soff, j, delta[i]);
-                }
-            }
-            if (lane == 0) {
-                act[t] = (int8_t)a;
-                my_changed |= a != old;
-            }
-            ++calls;
+    for (int q = 0; q < NPL; ++q) {
+        const int j = lane + 32 * q;
+        sb[q] = 0, sc[q] = 0, cj[q] = 0;
+        if (CAP && j < N) {
+            sb[q] = soff[j];
+            sc[q] = soff[j + 1] - sb[q];
+            cj[q] = cap[j];
         }
     }
+    for (int m = blockIdx.x * kPartWarps + (threadIdx.x >> 5); m < P; m += nwarps) {
+        const int e0 = own_off[m], e1 = own_off[m + 1];
+        if (e0 >= e1) continue;
+        int n[NPL], th[NPL], tm[NPL], tp[NPL], xr[NPL], lr[NPL];
+#pragma unroll
+        for (int q = 0; q < NPL; ++q) {
+            n[q] = cj[q];
+            th[q] = CAP ? part_sval(S, sb[q], sc[q], n[q]) : INT_MAX;
+            tm[q] = CAP ? part_sval(S, sb[q], sc[q], n[q] - 1) : INT_MAX;
+            tp[q] = CAP ? part_sval(S, sb[q], sc[q], n[q] + 1) : INT_MAX;
+            xr[q] = 0, lr[q] = 0;
+        }
+        int kc = -1;
+        // batch b's indices (bt .. bo) and batch b + 1's order times (nt)
+        int bt = 0, bk = 0, br = 0, bs = N, bo = 0, nt = 0;
+        if (lane < e1 - e0) {
+            bt = own_t[e0 + lane];
+            bk = prod[bt], br = reg[bt], bo = act[bt];
+            if (CAP) bs = succ[bt];
+        }
+        if (e0 + kPartBatch + lane < e1) nt = own_t[e0 + kPartBatch + lane];
+        for (int eb = e0; eb < e1; eb += kPartBatch) {
+            const int nb = min(kPartBatch, e1 - eb);
+            // next batch's indices (consumed after this batch's orders)
+            int nk = 0, nr = 0, ns = N, no = 0, nnt = 0;
+            if (eb + kPartBatch + lane < e1) {
+                nk = prod[nt], nr = reg[nt], no = act[nt];
+                if (CAP) ns = succ[nt];
+            }
+            if (eb + 2 * kPartBatch + lane < e1) nnt = own_t[eb + 2 * kPartBatch + lane];
+            __syncwarp();  // the previous batch's reads of cst are done
+            // all of the batch's cost rows in flight at once (asynchronous copies), one wait
+#pragma unroll 8
+            for (int i = 0; i < kPartBatch; ++i) {
+                const int r = __shfl_sync(kFull, br, i);
+                if (i < nb) {
+#pragma unroll
+                    for (int q = 0; q < NPL; ++q) {
+                        const int j = lane + 32 * q;
+                        if (j < N) part_copy4(cst + i * kRow + j, cost + (size_t)r * N + j);
+                    }
+                }
+            }
+            asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;\n" ::: "memory");
+            __syncwarp();
+            int bnew = -1;
+            // order i's indices and cost row are read during order i - 1 (off the
+            // loop-carried chain: stock and capacity -> decision -> update)
+            int t_n = __shfl_sync(kFull, bt, 0), k_n = __shfl_sync(kFull, bk, 0);
+            int sn_n = CAP ? __shfl_sync(kFull, bs, 0) : N;
+            int cv_n[NPL];
+#pragma unroll
+            for (int q = 0; q < NPL; ++q) cv_n[q] = cst[lane + 32 * q];
+            for (int i = 0; i < nb; ++i) {
+                const int t = t_n, k = k_n, sn = sn_n;
+                int cv[NPL];
+#pragma unroll
+                for (int q = 0; q < NPL; ++q) cv[q] = cv_n[q];
+                const int i1 = i + 1 < kPartBatch ? i + 1 : i;  // row i1 >= nb: stale, unused
+                t_n = __shfl_sync(kFull, bt, i1), k_n = __shfl_sync(kFull, bk, i1);
+                if (CAP) sn_n = __shfl_sync(kFull, bs, i1);
+#pragma unroll
+                for (int q = 0; q < NPL; ++q) cv_n[q] = cst[i1 * kRow + lane + 32 * q];
+                if (k != kc) {  // warp-uniform: switch the register row to product k
+#pragma unroll
+                    for (int q = 0; q < NPL; ++q) {
+                        const int j = lane + 32 * q;
+                        if (j < N) {
+                            if (kc >= 0) xv[(size_t)kc * N + j] = xr[q];
+                            xr[q] = xv[(size_t)k * N + j];
+                            if (DUAL) lr[q] = __ldg(lam + (size_t)k * N + j);
+                        }
+                    }
+                    kc = k;
+                }
+                int best = INT_MAX;
+#pragma unroll
+                for (int q = 0; q < NPL; ++q) {
+                    const int j = lane + 32 * q;
+                    if (j < N && xr[q] > 0 && th[q] >= t) {
+                        int v = cv[q];
+                        if (DUAL) v -= lr[q];
+                        best = min(best, v * 128 + j);
+                    }
+                }
+                best = __reduce_min_sync(kFull, best);
+                const int a = best == INT_MAX ? -1 : (best & 127);
+#pragma unroll
+                for (int q = 0; q < NPL; ++q) {
+                    const int j = lane + 32 * q;
+                    if (j == a) xr[q] -= 1;  // the fresh action takes one unit of stock
+                    if (CAP && j < N) {
+                        // fresh action: one unit of capacity; this order's cached
+                        // success (if any) no longer counts
+                        const int dd = (j == sn ? 1 : 0) - (j == a ? 1 : 0);
+                        if (dd > 0) {
+                            n[q] += 1;
+                            tm[q] = th[q], th[q] = tp[q];
+                            tp[q] = part_sval(S, sb[q], sc[q], n[q] + 1);
+                        } else if (dd < 0) {
+                            n[q] -= 1;
+                            tp[q] = th[q], th[q] = tm[q];
+                            tm[q] = part_sval(S, sb[q], sc[q], n[q] - 1);
+                        }
+                    }
+                }
+                if (lane == i) bnew = a;
+            }
+            if (lane < nb) {
+                act[bt] = (int8_t)bnew;
+                my_changed |= bnew != bo;
+            }
+            calls += nb;
+            bt = nt, bk = nk, br = nr, bs = ns, bo = no, nt = nnt;
+        }
+        if (kc >= 0) {
+#pragma unroll
+            for (int q = 0; q < NPL; ++q) {
+                const int j = lane + 32 * q;
+                if (j < N) xv[(size_t)kc * N + j] = xr[q];
+            }
+        }
+    }
+    my_changed = __any_sync(kFull, my_changed);
     if (lane == 0) {
         if (my_changed) atomicExch(changed, 1);
         if (calls) atomicAdd(&ctrl->policy_calls, calls);
@@ -206,6 +306,7 @@ cudaError_t picard_products(Instance* I, const pic_policy* pol, int P, int iters
         I->launches += 2;
     }
     const int blocks = (P + kPartWarps - 1) / kPartWarps;
+    const int smem = kPartWarps * kPartBatch * NPL * 32 * (int)sizeof(int32_t);
     for (int pass = 1; !e && T > 0 && pass <= iters_cap; ++pass) {
         if (cap) {
             // which cached actions find stock, listed per node in time order
@@ -223,9 +324,14 @@ cudaError_t picard_products(Instance* I, const pic_policy* pol, int P, int iters
             break;
         if ((e = cudaMemsetAsync(flag, 0, sizeof(int32_t), st))) break;
 #define PART_WALK(NP_, D_, C_)                                                              \
-    k_part_walk<NP_, D_, C_><<<blocks, kPartWarps * 32, 0, st>>>(                          \
-        P, N, own_t, own_off, I->prod, I->reg, I->cost, I->lam, I->cap, succ, S, soff, I->act_t, \
-        I->xfin, I->ctrl, flag)
+    do {                                                                                    \
+        e = cudaFuncSetAttribute(k_part_walk<NP_, D_, C_>,                                 \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);       \
+        if (!e)                                                                             \
+            k_part_walk<NP_, D_, C_><<<blocks, kPartWarps * 32, smem, st>>>(               \
+                P, N, own_t, own_off, I->prod, I->reg, I->cost, I->lam, I->cap, succ, S,   \
+                soff, I->act_t, I->xfin, I->ctrl, flag);                                   \
+    } while (0)
         if (NPL == 1) {
             if (dual) { if (cap) PART_WALK(1, true, true); else PART_WALK(1, true, false); }
             else { if (cap) PART_WALK(1, false, true); else PART_WALK(1, false, false); }
@@ -237,6 +343,7 @@ cudaError_t picard_products(Instance* I, const pic_policy* pol, int P, int iters
             else { if (cap) PART_WALK(4, false, true); else PART_WALK(4, false, false); }
         }
 #undef PART_WALK
+        if (e) break;
         I->launches += 1;
         int hf = 0;
         if ((e = cudaGetLastError())) break;

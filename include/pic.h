@@ -137,8 +137,11 @@ typedef struct {
 
 typedef struct {
     int32_t mode;             /* PIC_MODE_* */
-    int32_t num_chunks;       /* M >= 1 time chunks (Picard); 0 = pick automatically */
-    int32_t max_iters;        /* cap on passes; 0 = M + 1 (Prop. 1 bound plus the confirming pass) */
+    int32_t num_chunks;       /* M >= 1 time chunks (Picard); 0 = pick automatically.
+                                 PIC_MODE_PICARD_PRODUCTS: P processors (product k -> k mod P;
+                                 0 or P > K: K) */
+    int32_t max_iters;        /* cap on passes; 0 = M + 1 (Prop. 1 bound plus the confirming pass);
+                                 PIC_MODE_PICARD_PRODUCTS: 0 = T + 1 */
     int32_t flags;            /* PIC_FLAG_* */
     const int8_t* alpha_init; /* DEVICE [T] initial action cache, or NULL = all a^phi (Alg. 1) */
     uint64_t timeout_ns;      /* bound on the device-side waits of the simulation kernel,
@@ -170,7 +173,7 @@ typedef struct {
     int32_t iters;        /* passes of Algorithm 1's loop, including the confirming one
                              (1 for PIC_MODE_SEQUENTIAL); also the rows written to opts.trace
                              (at most trace_cap) */
-    int32_t num_chunks;   /* M used */
+    int32_t num_chunks;   /* M used (P with PIC_MODE_PICARD_PRODUCTS) */
     int64_t rescored;     /* MLP tile rows re-scored in FP32 (top-2 margin below the bound) */
     int64_t seg_replays;  /* warp work units (segments) replayed, over all passes */
     int32_t launches;     /* kernels this call launched */
@@ -225,6 +228,14 @@ void pic_destroy_instance(pic_instance* inst);
  * of them that found inventory.  The chunk length ceil(T/M) must be at most 64
  * (num_chunks = 0 picks M = ceil(T/64)); seg_window and the MLP / group /
  * tensor-core flags do not apply.
+ * PIC_MODE_PICARD_PRODUCTS runs Algorithm 1 with process m owning the orders of
+ * the products k with k mod P = m (the product partition of Sec. 3): each pass a
+ * process walks its own orders in time order, with its products' stock from its
+ * own decisions and, with capacity, node n available before order t iff fewer
+ * than c_1[n] cached actions found inventory at n before t once its own cached
+ * ones are replaced by its fresh ones.  Greedy and bid-price policies only, no
+ * max_steps (else UNSUPPORTED); device memory for the per-pass sorts is taken
+ * with cudaMallocAsync on the call's stream.
  *   actions_out  [T] int8 in opts.out_mem memory (required);
  *   final_stock  [K][N] int32 in opts.out_mem memory, or NULL;
  *   res          host struct, or NULL.

@@ -69,7 +69,25 @@ __device__ __forceinline__ bool replay_segment(const KArgs& a, const CostTable<S
             nold = a.alpha_s[base + 32 + lane];
         }
         int my_new = my_old;
+        // order q's region, cached action and cost row are read during order q - 1,
+        // off the loop-carried chain (stock -> decision -> stock)
+        int rr_n = __shfl_sync(kFull, my_reg, 0), ao_n = __shfl_sync(kFull, my_old, 0);
+        int c_n[NPL];
+#pragma unroll
+        for (int i = 0; i < NPL; ++i)
+            c_n[i] = (FULL || lane + 32 * i < N) ? ct.at(rr_n, lane + 32 * i) : 0;
         for (int q = 0; q < cnt; ++q) {
+            const int ao = ao_n;
+            int c[NPL];
+#pragma unroll
+            for (int i = 0; i < NPL; ++i) c[i] = c_n[i];
+            // lanes at or past cnt hold an earlier batch's (valid) region: read, unused
+            const int q1 = q + 1 < 32 ? q + 1 : q;
+            rr_n = __shfl_sync(kFull, my_reg, q1);
+            ao_n = __shfl_sync(kFull, my_old, q1);
+#pragma unroll
+            for (int i = 0; i < NPL; ++i)
+                c_n[i] = (FULL || lane + 32 * i < N) ? ct.at(rr_n, lane + 32 * i) : 0;
             if (base + q == next_run) {  // close run r, open run r+1
 #pragma unroll
                 for (int i = 0; i < NPL; ++i) {
@@ -91,12 +109,6 @@ __device__ __forceinline__ bool replay_segment(const KArgs& a, const CostTable<S
                 if (eval) evals += (unsigned long long)(nr - next_run);
                 next_run = nr;
             }
-            const int rr = __shfl_sync(kFull, my_reg, q);
-            const int ao = __shfl_sync(kFull, my_old, q);
-            int c[NPL];
-#pragma unroll
-            for (int i = 0; i < NPL; ++i)
-                c[i] = (FULL || lane + 32 * i < N) ? ct.at(rr, lane + 32 * i) : 0;
             int act = ao;  // unchanged prefix: the cached action is the policy's
             if (eval) {
                 int key = INT_MAX;

@@ -39,17 +39,56 @@ __device__ __forceinline__ bool replay_segment(const KArgs& a, const CostTable<S
         D[i] = chained ? a.carry[(size_t)s * NP + n] : 0;
     }
     const int j0 = m.j0, jend = m.jend;
+    // Runs starting at or before fcp keep their cached actions (t_reset), so
+    // walking them only advances D by the counts of those actions: without the
+    // max_steps window they are skipped, and the counts taken in parallel (each
+    // lane tallies its own warehouses over 32 cached actions at a time).
+    int jst = j0, rst = m.r0;  // first position and run walked
+    if (!a.run_chunk && j0 <= fcp) {
+        int rs = m.r1;  // first run starting after fcp
+        for (int w = m.r0 + 1; w < m.r1; w += 32) {
+            const int st = w + lane < m.r1 ? a.run_start[w + lane] : INT_MAX;
+            const unsigned b = __ballot_sync(kFull, st > fcp);
+            if (b) {
+                rs = w + __ffs(b) - 1;
+                break;
+            }
+        }
+        if (rs < m.r1) {
+            rst = rs;
+            jst = a.run_start[rs];
+            int cnt[NPL];
+#pragma unroll
+            for (int i = 0; i < NPL; ++i) cnt[i] = 0;
+            int v = j0 + lane < jst ? a.alpha_s[j0 + lane] : -1;
+            for (int p = j0; p < jst; p += 32) {
+                const int u = v;
+                v = p + 32 + lane < jst ? a.alpha_s[p + 32 + lane] : -1;
+#pragma unroll 8
+                for (int q = 0; q < 32; ++q) {
+                    const int aq = __shfl_sync(kFull, u, q);
+#pragma unroll
+                    for (int i = 0; i < NPL; ++i) cnt[i] += aq == lane + 32 * i;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < NPL; ++i) {
+                D[i] += cnt[i];
+                hist[i] += cnt[i];
+            }
+        }
+    }
     // lane i holds the end (= next start) of run rwin + i
-    int rwin = m.r0;
+    int rwin = rst;
     int run_end = lane < m.r1 - rwin ? a.run_start[rwin + 1 + lane] : INT_MAX;
-    int r = m.r0;
+    int r = rst;
     int next_run = __shfl_sync(kFull, run_end, 0);
     // the max_steps window of this pass (none: INT_MAX)
     const int whi = a.run_chunk ? ld_volatile(&a.ctrl->win_hi) : INT_MAX;
     const int wprev = a.run_chunk ? ld_volatile(&a.ctrl->win_hi_prev) : INT_MAX;
     // this run's prefix changed in the previous pass (or it entered the window)
-    bool eval = run_evaluated(a, whi, wprev, r, j0 > fcp);
-    unsigned long long evals = eval ? (unsigned long long)(next_run - j0) : 0ull;
+    bool eval = run_evaluated(a, whi, wprev, r, jst > fcp);
+    unsigned long long evals = eval ? (unsigned long long)(next_run - jst) : 0ull;
 #pragma unroll
     for (int i = 0; i < NPL; ++i) {
         S[i] = max(0, x0v[i] - D[i]);
@@ -57,11 +96,11 @@ __device__ __forceinline__ bool replay_segment(const KArgs& a, const CostTable<S
     }
     int first_chg = INT_MAX;
     int nreg = 0, nold = -1;
-    if (lane < jend - j0) {
-        nreg = a.reg_s[j0 + lane];
-        nold = a.alpha_s[j0 + lane];
+    if (lane < jend - jst) {
+        nreg = a.reg_s[jst + lane];
+        nold = a.alpha_s[jst + lane];
     }
-    for (int base = j0; base < jend; base += 32) {
+    for (int base = jst; base < jend; base += 32) {
         const int cnt = min(32, jend - base);
         const int my_reg = nreg, my_old = nold;
         if (base + 32 + lane < jend) {  // prefetch the next batch of orders

@@ -62,7 +62,12 @@ enum {
                                     P = num_chunks (0: K); greedy and bid-price policies, with
                                     or without node capacity; single instances; no max_steps.
                                     Same fixed point; Thm. 3.1 bounds the passes by |Q_T| + 2
-                                    (Q_T: nodes whose capacity runs out) */
+                                    (Q_T: nodes whose capacity runs out) */,
+    PIC_MODE_PICARD_ASSIGNED = 3 /* Algorithm 1 for a caller's assignment of orders to
+                                    processes (opts.proc, P = num_chunks >= 1), e.g. the
+                                    uniform random assignment of Sec. 4.1 (Table 1); greedy and
+                                    bid-price policies, no capacity, single instances, no
+                                    max_steps.  Same fixed point (Prop. 1) */
 };
 
 /* Where a pointer lives. */
@@ -164,6 +169,9 @@ typedef struct {
                                  pass that changed nothing and evaluated every chunk.  The
                                  result is still the sequential path; max_iters defaults to
                                  2 M + 2.  Batches reject it (UNSUPPORTED) */
+    const int32_t* proc;      /* PIC_MODE_PICARD_ASSIGNED: DEVICE [T] process of each order,
+                                 0 <= proc[t] < num_chunks (else INVALID_ARG), with
+                                 num_chunks * K < 2^31; ignored by the other modes */
 } pic_sim_opts;
 
 typedef struct {
@@ -236,6 +244,12 @@ void pic_destroy_instance(pic_instance* inst);
  * ones are replaced by its fresh ones.  Greedy and bid-price policies only, no
  * max_steps (else UNSUPPORTED); device memory for the per-pass sorts is taken
  * with cudaMallocAsync on the call's stream.
+ * PIC_MODE_PICARD_ASSIGNED runs Algorithm 1 with process proc[t] owning order t
+ * (no capacity): in a process's view the stock of (k, n) before its order t is
+ * max(0, x0[k][n] - attempts), the attempts being the cached actions naming
+ * (k, n) at other processes' orders and its own fresh ones, so each (product,
+ * process) pair is walked as an independent chain.  Same restrictions and
+ * allocation as PIC_MODE_PICARD_PRODUCTS, plus node capacity UNSUPPORTED.
  *   actions_out  [T] int8 in opts.out_mem memory (required);
  *   final_stock  [K][N] int32 in opts.out_mem memory, or NULL;
  *   res          host struct, or NULL.

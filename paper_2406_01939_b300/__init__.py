@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(HERE, "libpic.so")
 PIC_OK, PIC_ERR_INVALID_ARG, PIC_ERR_CUDA, PIC_ERR_OOM = 0, 1, 2, 3
 PIC_ERR_NOT_CONVERGED, PIC_ERR_TIMEOUT, PIC_ERR_UNSUPPORTED = 4, 5, 6
 PIC_POLICY_GREEDY, PIC_POLICY_DUAL, PIC_POLICY_MLP, PIC_POLICY_GUMBEL = 0, 1, 2, 3
-PIC_MODE_PICARD, PIC_MODE_SEQUENTIAL, PIC_MODE_PICARD_PRODUCTS = 0, 1, 2
+PIC_MODE_PICARD, PIC_MODE_SEQUENTIAL, PIC_MODE_PICARD_PRODUCTS, PIC_MODE_PICARD_ASSIGNED = 0, 1, 2, 3
 PIC_MEM_HOST, PIC_MEM_DEVICE = 0, 1
 PIC_FLAG_NO_RESET, PIC_FLAG_REUSE_TABLES, PIC_FLAG_TIMING, PIC_FLAG_GROUP_KERNEL = 1, 2, 4, 8
 PIC_FLAG_GRAPH, PIC_FLAG_NO_TC, PIC_FLAG_TC, PIC_FLAG_NO_SAT = 16, 32, 64, 128
@@ -32,7 +32,7 @@ PIC_FLAG_WARP_GROUP = 256
 POLICY_KINDS = {"greedy": PIC_POLICY_GREEDY, "dual": PIC_POLICY_DUAL, "mlp": PIC_POLICY_MLP,
                 "gumbel": PIC_POLICY_GUMBEL}
 MODES = {"picard": PIC_MODE_PICARD, "sequential": PIC_MODE_SEQUENTIAL,
-         "products": PIC_MODE_PICARD_PRODUCTS}
+         "products": PIC_MODE_PICARD_PRODUCTS, "assigned": PIC_MODE_PICARD_ASSIGNED}
 
 
 class PicError(RuntimeError):
@@ -58,7 +58,8 @@ class pic_sim_opts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("num_chunks", C.c_int32), ("max_iters", C.c_int32),
                 ("flags", C.c_int32), ("alpha_init", C.c_void_p), ("timeout_ns", C.c_uint64),
                 ("out_mem", C.c_int32), ("seg_window", C.c_int32), ("stream", C.c_void_p),
-                ("trace", C.c_void_p), ("trace_cap", C.c_int32), ("max_steps", C.c_int32)]
+                ("trace", C.c_void_p), ("trace_cap", C.c_int32), ("max_steps", C.c_int32),
+                ("proc", C.c_void_p)]
 
 
 class pic_sim_result(C.Structure):
@@ -180,13 +181,15 @@ def make_policy(kind="greedy", W1=None, b1=None, W2=None, b2=None, E=None, hidde
 
 def make_opts(mode="picard", num_chunks=0, max_iters=0, flags=0, alpha_init=None, timeout_ns=0,
               out_mem=PIC_MEM_DEVICE, seg_window=0, stream=None, trace=None,
-              max_steps=0) -> pic_sim_opts:
+              max_steps=0, proc=None) -> pic_sim_opts:
     """trace: optional host int64 numpy array [cap, 4] receiving the per-pass record;
-    max_steps: the Picard window (0: none)."""
+    max_steps: the Picard window (0: none); proc: device int32 [T] process of each
+    order (mode "assigned")."""
     m = MODES[mode] if isinstance(mode, str) else int(mode)
     return pic_sim_opts(m, int(num_chunks), int(max_iters), int(flags), _ptr(alpha_init),
                         int(timeout_ns), int(out_mem), int(seg_window), _stream_handle(stream),
-                        _ptr(trace), 0 if trace is None else int(trace.shape[0]), int(max_steps))
+                        _ptr(trace), 0 if trace is None else int(trace.shape[0]), int(max_steps),
+                        _ptr(proc))
 
 
 def pic_simulate(handle: int, policy: pic_policy, opts: pic_sim_opts, actions_out,

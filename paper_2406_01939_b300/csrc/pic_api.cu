@@ -407,7 +407,7 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
     Instance& I = h->I;
     if (I.batch) return fail(PIC_ERR_INVALID_ARG, "batch instance: use pic_simulate_batch");
     if (opts->mode != PIC_MODE_PICARD && opts->mode != PIC_MODE_SEQUENTIAL &&
-        opts->mode != PIC_MODE_PICARD_PRODUCTS)
+        opts->mode != PIC_MODE_PICARD_PRODUCTS && opts->mode != PIC_MODE_PICARD_ASSIGNED)
         return fail(PIC_ERR_INVALID_ARG, "unknown mode %d", opts->mode);
     if (opts->out_mem != PIC_MEM_HOST && opts->out_mem != PIC_MEM_DEVICE)
         return fail(PIC_ERR_INVALID_ARG, "unknown out_mem %d", opts->out_mem);
@@ -428,6 +428,14 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
         return fail(PIC_ERR_UNSUPPORTED, "the max_steps window is not supported with node capacity");
     if (opts->mode == PIC_MODE_PICARD_PRODUCTS && (mlp || opts->max_steps > 0))
         return fail(PIC_ERR_UNSUPPORTED, "product partition: greedy and bid-price policies, no window");
+    if (opts->mode == PIC_MODE_PICARD_ASSIGNED) {
+        if (mlp || opts->max_steps > 0 || I.has_cap)
+            return fail(PIC_ERR_UNSUPPORTED,
+                        "assigned partition: greedy and bid-price policies, no window, no capacity");
+        if (opts->num_chunks < 1 || (long long)opts->num_chunks * I.K >= (1LL << 31))
+            return fail(PIC_ERR_INVALID_ARG, "assigned partition: need 1 <= num_chunks and num_chunks * K < 2^31");
+        if (I.T && !opts->proc) return fail(PIC_ERR_INVALID_ARG, "assigned partition: proc is NULL");
+    }
     cudaStream_t st = (cudaStream_t)opts->stream;
     const size_t T = I.T, K = I.K, N = I.N;
     const bool host_out = opts->out_mem == PIC_MEM_HOST;
@@ -454,9 +462,13 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
         if (T) CU(cudaMemcpyAsync(actions_out, I.act_t, T, okind, st));
         if (final_stock)
             CU(cudaMemcpyAsync(final_stock, I.xwork, sizeof(int32_t) * K * N, okind, st));
-    } else if (opts->mode == PIC_MODE_PICARD_PRODUCTS) {
-        // processor of product k: k mod M; M > K gives the same assignment as M = K
-        M = opts->num_chunks && opts->num_chunks < (int)K ? opts->num_chunks : (int)K;
+    } else if (opts->mode == PIC_MODE_PICARD_PRODUCTS || opts->mode == PIC_MODE_PICARD_ASSIGNED) {
+        // products: processor of product k is k mod M, and M > K gives the same
+        // assignment as M = K; assigned: M processes named by opts->proc
+        if (opts->mode == PIC_MODE_PICARD_ASSIGNED)
+            M = opts->num_chunks;
+        else
+            M = opts->num_chunks && opts->num_chunks < (int)K ? opts->num_chunks : (int)K;
         iters_cap = opts->max_iters ? opts->max_iters : (T < (size_t)INT_MAX ? (int)T + 1 : INT_MAX);
         if (T) {
             if (opts->alpha_init) {
@@ -467,7 +479,10 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
             }
         }
         if (timing) CU(cudaEventRecord(I.ev[1], st));
-        CU(picard_products(&I, pol, M, iters_cap, st));
+        if (opts->mode == PIC_MODE_PICARD_PRODUCTS)
+            CU(picard_products(&I, pol, M, iters_cap, st));
+        else
+            CU(picard_assigned(&I, pol, opts->proc, M, iters_cap, st));
         if (timing) CU(cudaEventRecord(I.ev[2], st));
         if (T) {
             CU(reduce_costs(&I, I.act_t, I.reg, st));
@@ -557,6 +572,7 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
     CU(cudaMemcpyAsync(&hc, I.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
     if (hc.pad0 & 64) return fail(PIC_ERR_INVALID_ARG, "alpha_init holds a value outside [-1, N)");
+    if (hc.pad0 & 128) return fail(PIC_ERR_INVALID_ARG, "proc holds a process outside [0, num_chunks)");
     if (hc.err) return fail((pic_status)hc.err, "device wait exceeded timeout (%llu ns)",
                             (unsigned long long)opts->timeout_ns);
     if (T && opts->mode == PIC_MODE_PICARD && opts->trace && opts->trace_cap > 0) {

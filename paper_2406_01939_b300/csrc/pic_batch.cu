@@ -678,6 +678,8 @@ pic_status pic_simulate_batch(pic_instance* h, const pic_policy* pols, const pic
     const int B = bt->B;
     if (!pols || !opts || (!actions_out && I.T > 0))
         return fail(PIC_ERR_INVALID_ARG, "pols, opts and actions_out are required");
+    if (opts->mode == PIC_MODE_PICARD_PRODUCTS || opts->mode == PIC_MODE_PICARD_ASSIGNED)
+        return fail(PIC_ERR_UNSUPPORTED, "batches: PIC_MODE_PICARD or PIC_MODE_SEQUENTIAL only");
     if (opts->mode != PIC_MODE_PICARD && opts->mode != PIC_MODE_SEQUENTIAL)
         return fail(PIC_ERR_INVALID_ARG, "unknown mode %d", opts->mode);
     if (opts->out_mem != PIC_MEM_HOST && opts->out_mem != PIC_MEM_DEVICE)

@@ -216,6 +216,11 @@ cudaError_t sequential_mlp(Instance* I, const pic_policy* pol, int flags, cudaSt
 // last iterate on return; final stock in I->xfin; iters and converged in I->ctrl.
 cudaError_t picard_products(Instance* I, const pic_policy* pol, int P, int iters_cap,
                             cudaStream_t st);
+// Algorithm 1 for the assignment proc[t] in [0, P) (DEVICE), no capacity
+// (pic_part.cu); contract as picard_products; a process outside [0, P) raises
+// Ctrl::pad0 bit 128.
+cudaError_t picard_assigned(Instance* I, const pic_policy* pol, const int32_t* proc, int P,
+                            int iters_cap, cudaStream_t st);
 // Flag (Ctrl::pad0 bit 64) an initial cache holding a value outside [-1, N).
 cudaError_t check_alpha_init(Instance* I, const int8_t* alpha, cudaStream_t st);
 cudaError_t picard_cap(Instance* I, const pic_policy* pol, int M, int max_iters, int flags,

@@ -270,6 +270,181 @@ __global__ void __launch_bounds__(kPartWarps * 32) k_part_walk(
     }
 }
 
+// ---------------------------------------------------------------- any assignment
+// Algorithm 1 for an arbitrary assignment proc[t] of orders to processes, no
+// capacity.  In process m's view the stock of (k, j) moves only by attempts on
+// it: the cached actions of other processes' orders (applied while stock
+// remains) and m's fresh actions (always feasible), so before order t it is
+//   max(0, x0[k][j] - (C(t) - O(t) + F(t))),
+// C the cached actions naming (k, j) before t (all orders), O those at m's own
+// orders, F m's fresh actions naming j for product k before t.  m's orders of
+// product k therefore form an independent chain (unit (k, m)), and stock > 0 at
+// t iff the X-th cached action naming (k, j) comes at or after t, X = x0 - F + O.
+
+// unit key m * K + k of each order; a process outside [0, P) sets Ctrl::pad0 bit 128
+__global__ void k_assign_ukey(int T, int K, int P, const int32_t* __restrict__ proc,
+                              const int32_t* __restrict__ prod, int32_t* __restrict__ ukey,
+                              Ctrl* ctrl) {
+    int bad = 0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < T;
+         t += (long long)gridDim.x * blockDim.x) {
+        int m = proc[t];
+        if (m < 0 || m >= P) {
+            bad = 1;
+            m = 0;
+        }
+        ukey[t] = m * K + prod[t];
+    }
+    if (bad) atomicOr(&ctrl->pad0, 128);
+}
+
+__global__ void k_assign_uflags(int n, const int32_t* __restrict__ uks, int32_t* __restrict__ flag) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        flag[i] = i == 0 || uks[i] != uks[i - 1];
+}
+
+// ustart[u] = first sorted position of unit u; ustart[U] = n
+__global__ void k_assign_ustart(int n, const int32_t* __restrict__ flag,
+                                const int32_t* __restrict__ upos, int32_t* __restrict__ ustart) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (flag[i]) ustart[upos[i]] = (int)i;
+        if (i == n - 1) ustart[upos[i] + flag[i]] = n;
+    }
+}
+
+// final stock of a cache without capacity: max(0, x0 - its actions naming (k, j))
+__global__ void k_assign_final(int KN, const int32_t* __restrict__ x0,
+                               const int32_t* __restrict__ off, int32_t* __restrict__ xfin) {
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < KN;
+         v += (long long)gridDim.x * blockDim.x)
+        xfin[v] = max(0, x0[v] - (off[v + 1] - off[v]));
+}
+
+// One warp per unit (k, m): its orders in time order, 32 at a time (indices one
+// batch ahead, cost rows staged by asynchronous copies, the next order read
+// during the current one).  Lane l holds nodes j = l + 32 q with
+// X = x0 - F + O and th = L_kj(X), the time of the X-th cached action naming
+// (k, j), and its neighbours L_kj(X -/+ 1), moved when a fresh action (X - 1)
+// or the order's own cached action (X + 1) touches j.
+template <int NPL, bool DUAL>
+__global__ void __launch_bounds__(kPartWarps * 32) k_assign_walk(
+    int U, int N, const int32_t* __restrict__ ustart, const int32_t* __restrict__ uord,
+    const int32_t* __restrict__ prod, const int32_t* __restrict__ reg,
+    const int32_t* __restrict__ cost, const int32_t* __restrict__ lam,
+    const int32_t* __restrict__ x0, const int32_t* __restrict__ L,
+    const int32_t* __restrict__ off, int8_t* __restrict__ act, Ctrl* ctrl,
+    int32_t* __restrict__ changed) {
+    extern __shared__ int32_t part_smem[];
+    constexpr int kRow = NPL * 32;
+    const int lane = threadIdx.x & 31;
+    int32_t* cst = part_smem + (threadIdx.x >> 5) * kPartBatch * kRow;  // [kPartBatch][kRow]
+    const int nwarps = gridDim.x * kPartWarps;
+    int my_changed = 0;
+    unsigned long long calls = 0;
+    for (int u = blockIdx.x * kPartWarps + (threadIdx.x >> 5); u < U; u += nwarps) {
+        const int e0 = ustart[u], e1 = ustart[u + 1];
+        int bt = 0, br = 0, bo = -1, nt = 0;
+        if (lane < e1 - e0) {
+            bt = uord[e0 + lane];
+            br = reg[bt], bo = act[bt];
+        }
+        if (e0 + kPartBatch + lane < e1) nt = uord[e0 + kPartBatch + lane];
+        const int k = prod[__shfl_sync(kFull, bt, 0)];
+        int sb[NPL], sc[NPL], X[NPL], th[NPL], tm[NPL], tp[NPL], lr[NPL];
+#pragma unroll
+        for (int q = 0; q < NPL; ++q) {
+            const int j = lane + 32 * q;
+            sb[q] = 0, sc[q] = 0, X[q] = 0, lr[q] = 0;
+            if (j < N) {
+                const size_t v = (size_t)k * N + j;
+                sb[q] = off[v];
+                sc[q] = off[v + 1] - sb[q];
+                X[q] = x0[v];
+                if (DUAL) lr[q] = __ldg(lam + v);
+            }
+            th[q] = part_sval(L, sb[q], sc[q], X[q]);
+            tm[q] = part_sval(L, sb[q], sc[q], X[q] - 1);
+            tp[q] = part_sval(L, sb[q], sc[q], X[q] + 1);
+        }
+        for (int eb = e0; eb < e1; eb += kPartBatch) {
+            const int nb = min(kPartBatch, e1 - eb);
+            int nr = 0, no = -1, nnt = 0;
+            if (eb + kPartBatch + lane < e1) nr = reg[nt], no = act[nt];
+            if (eb + 2 * kPartBatch + lane < e1) nnt = uord[eb + 2 * kPartBatch + lane];
+            __syncwarp();  // the previous batch's reads of cst are done
+#pragma unroll 8
+            for (int i = 0; i < kPartBatch; ++i) {
+                const int r = __shfl_sync(kFull, br, i);
+                if (i < nb) {
+#pragma unroll
+                    for (int q = 0; q < NPL; ++q) {
+                        const int j = lane + 32 * q;
+                        if (j < N) part_copy4(cst + i * kRow + j, cost + (size_t)r * N + j);
+                    }
+                }
+            }
+            asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;\n" ::: "memory");
+            __syncwarp();
+            int bnew = -1;
+            int t_n = __shfl_sync(kFull, bt, 0), c_n = __shfl_sync(kFull, bo, 0);
+            int cv_n[NPL];
+#pragma unroll
+            for (int q = 0; q < NPL; ++q) cv_n[q] = cst[lane + 32 * q];
+            for (int i = 0; i < nb; ++i) {
+                const int t = t_n, c = c_n;
+                int cv[NPL];
+#pragma unroll
+                for (int q = 0; q < NPL; ++q) cv[q] = cv_n[q];
+                const int i1 = i + 1 < kPartBatch ? i + 1 : i;  // row i1 >= nb: stale, unused
+                t_n = __shfl_sync(kFull, bt, i1), c_n = __shfl_sync(kFull, bo, i1);
+#pragma unroll
+                for (int q = 0; q < NPL; ++q) cv_n[q] = cst[i1 * kRow + lane + 32 * q];
+                int best = INT_MAX;
+#pragma unroll
+                for (int q = 0; q < NPL; ++q) {
+                    const int j = lane + 32 * q;
+                    if (j < N && th[q] >= t) {
+                        int v = cv[q];
+                        if (DUAL) v -= lr[q];
+                        best = min(best, v * 128 + j);
+                    }
+                }
+                best = __reduce_min_sync(kFull, best);
+                const int a = best == INT_MAX ? -1 : (best & 127);
+#pragma unroll
+                for (int q = 0; q < NPL; ++q) {
+                    const int j = lane + 32 * q;
+                    // fresh action: F + 1; the order's own cached action: O + 1
+                    const int dd = (j < N && j == c ? 1 : 0) - (j == a ? 1 : 0);
+                    if (dd > 0) {
+                        X[q] += 1;
+                        tm[q] = th[q], th[q] = tp[q];
+                        tp[q] = part_sval(L, sb[q], sc[q], X[q] + 1);
+                    } else if (dd < 0) {
+                        X[q] -= 1;
+                        tp[q] = th[q], th[q] = tm[q];
+                        tm[q] = part_sval(L, sb[q], sc[q], X[q] - 1);
+                    }
+                }
+                if (lane == i) bnew = a;
+            }
+            if (lane < nb) {
+                act[bt] = (int8_t)bnew;
+                my_changed |= bnew != bo;
+            }
+            calls += nb;
+            bt = nt, br = nr, bo = no, nt = nnt;
+        }
+    }
+    my_changed = __any_sync(kFull, my_changed);
+    if (lane == 0) {
+        if (my_changed) atomicExch(changed, 1);
+        if (calls) atomicAdd(&ctrl->policy_calls, calls);
+    }
+}
+
 __global__ void k_part_result(Ctrl* ctrl, int iters, int converged) {
     ctrl->iters = iters;
     ctrl->converged = converged;
@@ -366,6 +541,109 @@ cudaError_t picard_products(Instance* I, const pic_policy* pol, int P, int iters
         e = cudaGetLastError();
     }
     int32_t* bufs[] = {key, key_s, t_s, succ, skey, S, pk, pks, own_t, soff, own_off, flag};
+    for (int32_t* b : bufs)
+        if (b) cudaFreeAsync(b, st);
+    return e;
+}
+
+// Algorithm 1 for the assignment proc[t] in [0, P) (DEVICE), no capacity, on the
+// instance's orders.  Same contract as picard_products; a process outside
+// [0, P) raises Ctrl::pad0 bit 128.
+cudaError_t picard_assigned(Instance* I, const pic_policy* pol, const int32_t* proc, int P,
+                            int iters_cap, cudaStream_t st) {
+    const int T = I->T, N = I->N, K = I->K, KN = K * N;
+    const bool dual = pol->kind == PIC_POLICY_DUAL;
+    const int NPL = N <= 32 ? 1 : (N <= 64 ? 2 : 4);
+    int32_t *ukey = nullptr, *uks = nullptr, *uord = nullptr, *flag = nullptr, *upos = nullptr,
+            *ustart = nullptr, *key = nullptr, *key_s = nullptr, *t_s = nullptr, *off = nullptr,
+            *cflag = nullptr, *total = nullptr;
+    cudaError_t e = cudaSuccess;
+    const size_t Tn = T > 0 ? (size_t)T : 1;
+    auto A = [&](int32_t** p, size_t n) {
+        if (!e) e = cudaMallocAsync(p, n * sizeof(int32_t), st);
+    };
+    A(&ukey, Tn); A(&uks, Tn); A(&uord, Tn); A(&flag, Tn); A(&upos, Tn); A(&ustart, Tn + 1);
+    A(&key, Tn); A(&key_s, Tn); A(&t_s, Tn); A(&off, (size_t)KN + 1); A(&cflag, 1); A(&total, 1);
+    const int gb = (int)((Tn + 255) / 256) < 4 * I->num_sms ? (int)((Tn + 255) / 256) : 4 * I->num_sms;
+    int U = 0;
+    if (!e && T > 0) {
+        // units (k, m): orders sorted stably by m * K + k, so time order within a unit
+        k_assign_ukey<<<gb, 256, 0, st>>>(T, K, P, proc, I->prod, ukey, I->ctrl);
+        e = sort_pairs(I, ukey, T, P * K - 1, uks, uord, I->tmp_a, I->tmp_b, st);
+        if (!e) {
+            k_assign_uflags<<<gb, 256, 0, st>>>(T, uks, flag);
+            e = scan_exclusive(flag, upos, T, total, I->scan_blk, st);
+        }
+        if (!e) {
+            k_assign_ustart<<<gb, 256, 0, st>>>(T, flag, upos, ustart);
+            e = cudaMemcpyAsync(&U, total, sizeof(int), cudaMemcpyDeviceToHost, st);
+        }
+        if (!e) e = cudaStreamSynchronize(st);
+        I->launches += 6;
+    }
+    // the cached actions naming (k, j), listed per (k, j) in time order
+    auto tables = [&]() {
+        k_part_keys<<<gb, 256, 0, st>>>(T, N, KN, I->prod, I->act_t, key);
+        cudaError_t r = sort_pairs(I, key, T, KN, key_s, t_s, I->tmp_a, I->tmp_b, st);
+        if (!r) k_part_offsets<<<(KN + 256) / 256, 256, 0, st>>>(key_s, T, KN, off);
+        I->launches += 2;
+        return r ? r : cudaGetLastError();
+    };
+    const int smem = kPartWarps * kPartBatch * NPL * 32 * (int)sizeof(int32_t);
+    const int blocks = (U + kPartWarps - 1) / kPartWarps;
+    int iters = 0, converged = 0;
+    for (int pass = 1; !e && T > 0 && pass <= iters_cap; ++pass) {
+        if ((e = tables())) break;
+        if ((e = cudaMemsetAsync(cflag, 0, sizeof(int32_t), st))) break;
+#define ASSIGN_WALK(NP_, D_)                                                                \
+    do {                                                                                    \
+        e = cudaFuncSetAttribute(k_assign_walk<NP_, D_>,                                   \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);       \
+        if (!e)                                                                             \
+            k_assign_walk<NP_, D_><<<blocks, kPartWarps * 32, smem, st>>>(                 \
+                U, N, ustart, uord, I->prod, I->reg, I->cost, I->lam, I->x0, t_s, off,     \
+                I->act_t, I->ctrl, cflag);                                                 \
+    } while (0)
+        if (NPL == 1) {
+            if (dual) ASSIGN_WALK(1, true); else ASSIGN_WALK(1, false);
+        } else if (NPL == 2) {
+            if (dual) ASSIGN_WALK(2, true); else ASSIGN_WALK(2, false);
+        } else {
+            if (dual) ASSIGN_WALK(4, true); else ASSIGN_WALK(4, false);
+        }
+#undef ASSIGN_WALK
+        if (e) break;
+        I->launches += 1;
+        int hf = 0;
+        if ((e = cudaGetLastError())) break;
+        if ((e = cudaMemcpyAsync(&hf, cflag, sizeof(int), cudaMemcpyDeviceToHost, st))) break;
+        if ((e = cudaStreamSynchronize(st))) break;
+        iters = pass;
+        if (!hf) {
+            converged = 1;
+            break;
+        }
+    }
+    if (T == 0) {
+        iters = 1;
+        converged = 1;
+    }
+    // final stock of the returned cache (the last pass's tables describe it when it
+    // changed nothing)
+    if (!e && T > 0 && !converged) e = tables();
+    if (!e && T > 0) {
+        k_assign_final<<<gb, 256, 0, st>>>(KN, I->x0, off, I->xfin);
+        I->launches += 1;
+        e = cudaGetLastError();
+    } else if (!e) {
+        e = cudaMemcpyAsync(I->xfin, I->x0, sizeof(int32_t) * (size_t)KN, cudaMemcpyDeviceToDevice,
+                            st);
+    }
+    if (!e) {
+        k_part_result<<<1, 1, 0, st>>>(I->ctrl, iters, converged);
+        e = cudaGetLastError();
+    }
+    int32_t* bufs[] = {ukey, uks, uord, flag, upos, ustart, key, key_s, t_s, off, cflag, total};
     for (int32_t* b : bufs)
         if (b) cudaFreeAsync(b, st);
     return e;

@@ -71,7 +71,7 @@ class DeviceInstance:
 
     def simulate(self, policy, mode="picard", num_chunks=0, max_iters=0, flags=0, alpha_init=None,
                  timeout_ns=0, seg_window=0, want_stock=True, raise_on_error=True, out=None,
-                 trace=None, max_steps=0):
+                 trace=None, max_steps=0, proc=None):
         i = self.inst
         dp = policy if isinstance(policy, DevicePolicy) else DevicePolicy(policy, self.device)
         act = out if out is not None else torch.empty(i.T, dtype=torch.int8, device=self.device)
@@ -80,8 +80,12 @@ class DeviceInstance:
         if alpha_init is not None:
             ai = torch.as_tensor(np.ascontiguousarray(alpha_init, dtype=np.int8)).to(self.device) \
                 if not torch.is_tensor(alpha_init) else alpha_init
+        pr = None
+        if proc is not None:
+            pr = proc if torch.is_tensor(proc) else \
+                torch.as_tensor(np.ascontiguousarray(proc, dtype=np.int32)).to(self.device)
         opts = make_opts(mode, num_chunks, max_iters, flags, ai, timeout_ns, PIC_MEM_DEVICE,
-                         seg_window, self.stream, trace, max_steps)
+                         seg_window, self.stream, trace, max_steps, pr)
         st, res = pic_simulate(self.handle, dp.struct, opts, act, stock, raise_on_error)
         return {"status": st, "actions": act, "final_stock": stock, "total_cost": res.total_cost,
                 "lost": res.lost, "iters": res.iters, "policy_calls": res.policy_calls,

@@ -197,6 +197,13 @@ def node_capacity(T, N, seed=0, frac=0.8, sigma=0.5):
     return np.floor(frac * T * w / w.sum()).astype(np.int32)
 
 
+def uniform_assignment(T, P, seed=0):
+    """Each order's process drawn uniformly from 0..P-1, seeded (the uniform
+    partition of Sec. 4.1, Table 1)."""
+    rng = np.random.Generator(np.random.PCG64(seed + 0xA55))
+    return rng.integers(0, P, size=T).astype(np.int32)
+
+
 def capacity_large(seed=0, T=1 << 20, N=64, K=10_000, R=1_000, frac=0.8):
     """dual_large's orders, stock, costs and prices plus node capacity for 80%
     of the orders (the paper's FO model with capacity, Sec. 3)."""

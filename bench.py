@@ -90,9 +90,10 @@ def parse():
     p.add_argument("--flags", type=int, default=0, help="extra pic_sim_opts flags (tuning)")
     p.add_argument("--max-steps", type=int, default=-1,
                    help="Picard window of App. A.3 in orders (-1: the workload's default, 0: none)")
-    p.add_argument("--partition", default="chunks", choices=["chunks", "products"],
-                   help="FO workloads: Algorithm 1 on contiguous time chunks (default) or the "
-                        "product partition of Sec. 3 (one processor per product)")
+    p.add_argument("--partition", default="chunks", choices=["chunks", "products", "random"],
+                   help="FO workloads: Algorithm 1 on contiguous time chunks (default), the "
+                        "product partition of Sec. 3 (one processor per product), or the uniform "
+                        "random assignment of Sec. 4.1 over --chunks processes (no capacity)")
     p.add_argument("--skew", type=float, default=0.0,
                    help="owmr_base: store weights (1 - skew)^n (App. B.3 ablation; 0 = uniform)")
     p.add_argument("--B", type=int, default=0,
@@ -162,9 +163,11 @@ def workload_config(args, inst):
                  f"(Zipf 1.1), R={inst.R} regions, x0~Poisson(1.05 T p_k/N), cost~U{{1..100}}, "
                  f"{pol}{cap}"),
         "T": inst.T, "N": inst.N, "K": inst.K, "R": inst.R,
-        "chunks": chunks_of(args) if args.partition == "chunks" else None,
-        "partition": "contiguous time chunks" if args.partition == "chunks" else
-                     f"products (processor of product k: k mod {inst.K})",
+        "chunks": chunks_of(args) if args.partition != "products" else None,
+        "partition": {"chunks": "contiguous time chunks",
+                      "products": f"products (processor of product k: k mod {inst.K})",
+                      "random": f"uniform random over {chunks_of(args)} processes (seeded)"}[
+                          args.partition],
         "policy": args.workload == "mlp_medium" and "mlp" or "dual",
         "max_steps": (args.max_steps if args.max_steps >= 0 else
                       DEFAULT_MAX_STEPS.get(args.workload, 0)) or None,
@@ -843,6 +846,7 @@ def main():
         return
 
     import paper_2406_01939_b300 as pic
+    from paper_2406_01939_b300 import synth as synth_mod
     from paper_2406_01939_b300.session import DeviceInstance, DevicePolicy
 
     inst, hpol, _ = make_workload(args, rank_seed(args.seed, rank))
@@ -856,13 +860,19 @@ def main():
         args.seg_window = DEFAULT_SEG_WINDOW.get(args.workload, 0)
 
     products = args.partition == "products"
-    if products and (args.workload == "mlp_medium" or max_steps):
-        raise SystemExit("--partition products: greedy / bid-price workloads, no max_steps window")
-    fo_mode = "products" if products else "picard"
+    rand = args.partition == "random"
+    if (products or rand) and (args.workload == "mlp_medium" or max_steps):
+        raise SystemExit("--partition products/random: greedy / bid-price workloads, no max_steps")
+    if rand and getattr(inst, "cap", None) is not None:
+        raise SystemExit("--partition random: no node capacity")
+    fo_mode = {"chunks": "picard", "products": "products", "random": "assigned"}[args.partition]
     fo_chunks = 0 if products else chunks_of(args)
+    proc_host = synth_mod.uniform_assignment(T, fo_chunks, seed=args.seed) if rand else None
+    proc_dev = torch.as_tensor(proc_host).to(dev) if rand else None
 
     def step(out):
         return di.simulate(pol, fo_mode, num_chunks=fo_chunks, seg_window=args.seg_window,
+                           proc=proc_dev,
                            flags=pic.PIC_FLAG_TIMING | args.flags, want_stock=False, out=out,
                            max_steps=max_steps)
 
@@ -895,7 +905,7 @@ def main():
     last = results[-1]
     # one extra (untimed) call with the per-pass trace (contiguous chunks)
     pass_trace = None
-    if not products:
+    if args.partition == "chunks":
         tr = np.zeros((4096, 4), np.int64)
         di.simulate(pol, "picard", num_chunks=chunks_of(args), seg_window=args.seg_window,
                     flags=args.flags, want_stock=False, out=act, trace=tr, max_steps=max_steps)
@@ -930,11 +940,14 @@ def main():
     host = {k: pin(getattr(inst, k)) for k in ("prod", "reg", "x0", "cost")}
     host["lam"] = pin(inst.lam) if inst.lam is not None else None
     host["cap"] = pin(inst.cap) if getattr(inst, "cap", None) is not None else None
+    proc_pin = pin(proc_host) if rand else None
+    proc_e2e = torch.empty(T, dtype=torch.int32, device=dev) if rand else None
     host_np = {k: (v.numpy() if v is not None else None) for k, v in host.items()}
     host_act = torch.empty(T, dtype=torch.int8).pin_memory().numpy()
     opts = pic.make_opts(fo_mode, fo_chunks, out_mem=pic.PIC_MEM_HOST, seg_window=args.seg_window,
+                         proc=proc_e2e,
                          flags=args.flags, max_steps=max_steps)
-    h2d = sum(v.nbytes for v in host_np.values() if v is not None)
+    h2d = sum(v.nbytes for v in host_np.values() if v is not None) + (proc_host.nbytes if rand else 0)
     d2h = host_act.nbytes + 64  # actions + the result record
     e2e_t = []
     for i in range(args.e2e_steps + 2 if args.e2e_steps > 0 else 0):
@@ -942,6 +955,8 @@ def main():
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         di.load_host(host_np)
+        if rand:
+            proc_e2e.copy_(proc_pin, non_blocking=True)  # the assignment is an input too
         st, res = pic.pic_simulate(di.handle, pol.struct, opts, host_act)
         t1 = time.perf_counter()
         if i >= 2:
@@ -951,20 +966,25 @@ def main():
 
     # roofline of the dominant kernel (the persistent Picard kernel)
     N = inst.N
-    if products:
+    if products or rand:
         # per pass and order: its time, product, region, cached action (read and
         # written) and, with capacity, its cached success (4 + 4 + 4 + 2 (+ 4) B), and
-        # its cost row (N x 4 B).  The pass is bound by the longest product's chain
-        # of orders, walked one at a time by one warp: the fraction is low by design.
+        # its cost row (N x 4 B).  Products: the pass is bound by the longest
+        # product's chain of orders, walked one at a time by one warp; random: by the
+        # start latency of the ~10^5-10^6 (product, process) chains.  The fraction is
+        # low by design.
         per = 14 + 4 * N + (4 if getattr(inst, "cap", None) is not None else 0)
         alg_bytes = last["policy_calls"] * per
         achieved = alg_bytes / (sim_ms / 1000.0) / 1e9
         peak, peak_kind = load_peaks()
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "traffic": None,
-                    "kernel": "k_part_walk plus the per-pass sorts (all passes)",
+                    "kernel": ("k_part_walk" if products else "k_assign_walk") +
+                              " plus the per-pass sorts (all passes)",
                     "peak_kind": peak_kind, "algorithmic_bytes": alg_bytes,
-                    "critical_path_orders_per_pass": int(np.bincount(inst.prod).max())}
+                    "critical_path_orders_per_pass": int(np.bincount(inst.prod).max()) if products
+                    else int(np.unique(proc_host.astype(np.int64) * inst.K + inst.prod,
+                                       return_counts=True)[1].max())}
     elif args.workload == "mlp_medium":
         roofline = mlp_roofline(fp32_scored(last), N, sim_ms, "k_picard_mlp (persistent, all passes)")
     elif args.workload == "capacity_large":

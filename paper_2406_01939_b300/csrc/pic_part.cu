@@ -314,6 +314,20 @@ __global__ void k_assign_ustart(int n, const int32_t* __restrict__ flag,
     }
 }
 
+// Per (k, j) pair v: its list of cached actions (base, count) and the thresholds
+// at X = x0 and x0 -/+ 1, so that a unit's start needs one coalesced row per
+// field instead of offsets followed by list reads.
+__global__ void k_assign_pairs(int KN, const int32_t* __restrict__ x0,
+                               const int32_t* __restrict__ off, const int32_t* __restrict__ L,
+                               int4* __restrict__ pr, int32_t* __restrict__ ptp) {
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < KN;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int b = off[v], c = off[v + 1] - b, X = x0[v];
+        pr[v] = make_int4(b, c, part_sval(L, b, c, X), part_sval(L, b, c, X - 1));
+        ptp[v] = part_sval(L, b, c, X + 1);
+    }
+}
+
 // final stock of a cache without capacity: max(0, x0 - its actions naming (k, j))
 __global__ void k_assign_final(int KN, const int32_t* __restrict__ x0,
                                const int32_t* __restrict__ off, int32_t* __restrict__ xfin) {
@@ -334,8 +348,8 @@ __global__ void __launch_bounds__(kPartWarps * 32) k_assign_walk(
     const int32_t* __restrict__ prod, const int32_t* __restrict__ reg,
     const int32_t* __restrict__ cost, const int32_t* __restrict__ lam,
     const int32_t* __restrict__ x0, const int32_t* __restrict__ L,
-    const int32_t* __restrict__ off, int8_t* __restrict__ act, Ctrl* ctrl,
-    int32_t* __restrict__ changed) {
+    const int4* __restrict__ pr, const int32_t* __restrict__ ptp, int8_t* __restrict__ act,
+    Ctrl* ctrl, int32_t* __restrict__ changed) {
     extern __shared__ int32_t part_smem[];
     constexpr int kRow = NPL * 32;
     const int lane = threadIdx.x & 31;
@@ -343,8 +357,12 @@ __global__ void __launch_bounds__(kPartWarps * 32) k_assign_walk(
     const int nwarps = gridDim.x * kPartWarps;
     int my_changed = 0;
     unsigned long long calls = 0;
-    for (int u = blockIdx.x * kPartWarps + (threadIdx.x >> 5); u < U; u += nwarps) {
-        const int e0 = ustart[u], e1 = ustart[u + 1];
+    int u = blockIdx.x * kPartWarps + (threadIdx.x >> 5);
+    int e0n = 0, e1n = 0;  // the next unit's range, read one unit ahead
+    if (u < U) e0n = ustart[u], e1n = ustart[u + 1];
+    for (; u < U; u += nwarps) {
+        const int e0 = e0n, e1 = e1n;
+        if (u + nwarps < U) e0n = ustart[u + nwarps], e1n = ustart[u + nwarps + 1];
         int bt = 0, br = 0, bo = -1, nt = 0;
         if (lane < e1 - e0) {
             bt = uord[e0 + lane];
@@ -357,16 +375,15 @@ __global__ void __launch_bounds__(kPartWarps * 32) k_assign_walk(
         for (int q = 0; q < NPL; ++q) {
             const int j = lane + 32 * q;
             sb[q] = 0, sc[q] = 0, X[q] = 0, lr[q] = 0;
+            th[q] = -1, tm[q] = -1, tp[q] = -1;
             if (j < N) {
                 const size_t v = (size_t)k * N + j;
-                sb[q] = off[v];
-                sc[q] = off[v + 1] - sb[q];
+                const int4 w = pr[v];
+                sb[q] = w.x, sc[q] = w.y, th[q] = w.z, tm[q] = w.w;
+                tp[q] = ptp[v];
                 X[q] = x0[v];
                 if (DUAL) lr[q] = __ldg(lam + v);
             }
-            th[q] = part_sval(L, sb[q], sc[q], X[q]);
-            tm[q] = part_sval(L, sb[q], sc[q], X[q] - 1);
-            tp[q] = part_sval(L, sb[q], sc[q], X[q] + 1);
         }
         for (int eb = e0; eb < e1; eb += kPartBatch) {
             const int nb = min(kPartBatch, e1 - eb);
@@ -564,6 +581,10 @@ cudaError_t picard_assigned(Instance* I, const pic_policy* pol, const int32_t* p
     };
     A(&ukey, Tn); A(&uks, Tn); A(&uord, Tn); A(&flag, Tn); A(&upos, Tn); A(&ustart, Tn + 1);
     A(&key, Tn); A(&key_s, Tn); A(&t_s, Tn); A(&off, (size_t)KN + 1); A(&cflag, 1); A(&total, 1);
+    int4* pr = nullptr;
+    int32_t* ptp = nullptr;
+    A(&ptp, (size_t)KN);
+    if (!e) e = cudaMallocAsync(&pr, sizeof(int4) * (size_t)KN, st);
     const int gb = (int)((Tn + 255) / 256) < 4 * I->num_sms ? (int)((Tn + 255) / 256) : 4 * I->num_sms;
     int U = 0;
     if (!e && T > 0) {
@@ -589,11 +610,14 @@ cudaError_t picard_assigned(Instance* I, const pic_policy* pol, const int32_t* p
         I->launches += 2;
         return r ? r : cudaGetLastError();
     };
+    const int gkn = (KN + 255) / 256 < 8 * I->num_sms ? (KN + 255) / 256 : 8 * I->num_sms;
     const int smem = kPartWarps * kPartBatch * NPL * 32 * (int)sizeof(int32_t);
     const int blocks = (U + kPartWarps - 1) / kPartWarps;
     int iters = 0, converged = 0;
     for (int pass = 1; !e && T > 0 && pass <= iters_cap; ++pass) {
         if ((e = tables())) break;
+        k_assign_pairs<<<gkn, 256, 0, st>>>(KN, I->x0, off, t_s, pr, ptp);
+        I->launches += 1;
         if ((e = cudaMemsetAsync(cflag, 0, sizeof(int32_t), st))) break;
 #define ASSIGN_WALK(NP_, D_)                                                                \
     do {                                                                                    \
@@ -601,7 +625,7 @@ cudaError_t picard_assigned(Instance* I, const pic_policy* pol, const int32_t* p
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem);       \
         if (!e)                                                                             \
             k_assign_walk<NP_, D_><<<blocks, kPartWarps * 32, smem, st>>>(                 \
-                U, N, ustart, uord, I->prod, I->reg, I->cost, I->lam, I->x0, t_s, off,     \
+                U, N, ustart, uord, I->prod, I->reg, I->cost, I->lam, I->x0, t_s, pr, ptp, \
                 I->act_t, I->ctrl, cflag);                                                 \
     } while (0)
         if (NPL == 1) {
@@ -643,9 +667,10 @@ cudaError_t picard_assigned(Instance* I, const pic_policy* pol, const int32_t* p
         k_part_result<<<1, 1, 0, st>>>(I->ctrl, iters, converged);
         e = cudaGetLastError();
     }
-    int32_t* bufs[] = {ukey, uks, uord, flag, upos, ustart, key, key_s, t_s, off, cflag, total};
+    int32_t* bufs[] = {ukey, uks, uord, flag, upos, ustart, key, key_s, t_s, off, cflag, total, ptp};
     for (int32_t* b : bufs)
         if (b) cudaFreeAsync(b, st);
+    if (pr) cudaFreeAsync(pr, st);
     return e;
 }
 

@@ -319,12 +319,108 @@ __global__ void k_assign_ustart(int n, const int32_t* __restrict__ flag,
 // field instead of offsets followed by list reads.
 __global__ void k_assign_pairs(int KN, const int32_t* __restrict__ x0,
                                const int32_t* __restrict__ off, const int32_t* __restrict__ L,
-                               int4* __restrict__ pr, int32_t* __restrict__ ptp) {
+                               int4* __restrict__ pr, int32_t* __restrict__ ptp,
+                               int32_t* __restrict__ pth) {
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < KN;
          v += (long long)gridDim.x * blockDim.x) {
         const int b = off[v], c = off[v + 1] - b, X = x0[v];
-        pr[v] = make_int4(b, c, part_sval(L, b, c, X), part_sval(L, b, c, X - 1));
+        const int th = part_sval(L, b, c, X);
+        pr[v] = make_int4(b, c, th, part_sval(L, b, c, X - 1));
         ptp[v] = part_sval(L, b, c, X + 1);
+        pth[v] = th;
+    }
+}
+
+// Per unit u (once per call): its first order, product and region, and whether
+// it has more orders; the units with more are listed with their range after the
+// first order, their product and first order.
+__global__ void k_assign_units(int U, const int32_t* __restrict__ ustart,
+                               const int32_t* __restrict__ uord, const int32_t* __restrict__ prod,
+                               const int32_t* __restrict__ reg, int32_t* __restrict__ ft,
+                               int32_t* __restrict__ fk, int32_t* __restrict__ fr,
+                               int32_t* __restrict__ mflag) {
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < U;
+         u += (long long)gridDim.x * blockDim.x) {
+        const int e0 = ustart[u], t = uord[e0];
+        ft[u] = t, fk[u] = prod[t], fr[u] = reg[t];
+        mflag[u] = ustart[u + 1] - e0 > 1;
+    }
+}
+
+__global__ void k_assign_mlist(int U, const int32_t* __restrict__ ustart,
+                               const int32_t* __restrict__ ft, const int32_t* __restrict__ fk,
+                               const int32_t* __restrict__ mflag, const int32_t* __restrict__ mpos,
+                               int4* __restrict__ mu) {
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < U;
+         u += (long long)gridDim.x * blockDim.x)
+        if (mflag[u]) mu[mpos[u]] = make_int4(ustart[u] + 1, ustart[u + 1], fk[u], (int)u);
+}
+
+// The first order of every unit: its process has taken no own action of the
+// product yet, so X = x0 and stock > 0 iff pth >= t.  One warp per 32 units:
+// their first orders' indices lane-parallel, then each decision with lanes over
+// the nodes (coalesced rows), the rows of four units loaded before their four
+// decisions.  The order's cached action is kept in fold[u] for the walk of the
+// unit's later orders.
+template <int NPL, bool DUAL>
+__global__ void __launch_bounds__(256) k_assign_first(
+    int U, int N, const int32_t* __restrict__ ft, const int32_t* __restrict__ fk,
+    const int32_t* __restrict__ fr, const int32_t* __restrict__ cost,
+    const int32_t* __restrict__ lam, const int32_t* __restrict__ pth, int8_t* __restrict__ act,
+    int8_t* __restrict__ fold, Ctrl* ctrl, int32_t* __restrict__ changed) {
+    constexpr int G = 4;
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    int my_changed = 0;
+    unsigned calls = 0;
+    for (long long ub = (long long)gw * 32; ub < U; ub += (long long)nw * 32) {
+        const int u = (int)ub + lane;
+        int t = 0, k = 0, r = 0, c = -1;  // lanes past U: row 0 read, decision unused
+        if (u < U) {
+            t = ft[u], k = fk[u], r = fr[u];
+            c = act[t];
+        }
+        const int nu = min(32, U - (int)ub);
+        int anew = -1;
+        for (int i0 = 0; i0 < nu; i0 += G) {
+            int th[G][NPL], cv[G][NPL];
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const int kk = __shfl_sync(kFull, k, i0 + g), rr = __shfl_sync(kFull, r, i0 + g);
+#pragma unroll
+                for (int q = 0; q < NPL; ++q) {
+                    const int j = lane + 32 * q;
+                    th[g][q] = -1, cv[g][q] = 0;
+                    if (j < N) {
+                        th[g][q] = __ldg(pth + (size_t)kk * N + j);
+                        cv[g][q] = __ldg(cost + (size_t)rr * N + j);
+                        if (DUAL) cv[g][q] -= __ldg(lam + (size_t)kk * N + j);
+                    }
+                }
+            }
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const int tt = __shfl_sync(kFull, t, i0 + g);
+                int key = INT_MAX;
+#pragma unroll
+                for (int q = 0; q < NPL; ++q)
+                    if (th[g][q] >= tt) key = min(key, cv[g][q] * 128 + lane + 32 * q);
+                key = __reduce_min_sync(kFull, key);
+                if (lane == i0 + g) anew = key == INT_MAX ? -1 : (key & 127);
+            }
+        }
+        if (u < U) {
+            act[t] = (int8_t)anew;
+            fold[u] = (int8_t)c;
+            my_changed |= anew != c;
+        }
+        calls += nu;
+    }
+    my_changed = __any_sync(kFull, my_changed);
+    if (lane == 0) {
+        if (my_changed) atomicExch(changed, 1);
+        if (calls) atomicAdd(&ctrl->policy_calls, (unsigned long long)calls);
     }
 }
 
@@ -336,16 +432,18 @@ __global__ void k_assign_final(int KN, const int32_t* __restrict__ x0,
         xfin[v] = max(0, x0[v] - (off[v + 1] - off[v]));
 }
 
-// One warp per unit (k, m): its orders in time order, 32 at a time (indices one
-// batch ahead, cost rows staged by asynchronous copies, the next order read
-// during the current one).  Lane l holds nodes j = l + 32 q with
+// One warp per unit (k, m) with more than one order, from its second order on
+// (the first was decided by k_assign_first): its orders in time order, 32 at a
+// time (indices one batch ahead, cost rows staged by asynchronous copies, the
+// next order read during the current one).  Lane l holds nodes j = l + 32 q with
 // X = x0 - F + O and th = L_kj(X), the time of the X-th cached action naming
 // (k, j), and its neighbours L_kj(X -/+ 1), moved when a fresh action (X - 1)
 // or the order's own cached action (X + 1) touches j.
 template <int NPL, bool DUAL>
 __global__ void __launch_bounds__(kPartWarps * 32) k_assign_walk(
-    int U, int N, const int32_t* __restrict__ ustart, const int32_t* __restrict__ uord,
-    const int32_t* __restrict__ prod, const int32_t* __restrict__ reg,
+    int MU, int N, const int4* __restrict__ mu, const int32_t* __restrict__ ft,
+    const int8_t* __restrict__ fold, const int32_t* __restrict__ uord,
+    const int32_t* __restrict__ reg,
     const int32_t* __restrict__ cost, const int32_t* __restrict__ lam,
     const int32_t* __restrict__ x0, const int32_t* __restrict__ L,
     const int4* __restrict__ pr, const int32_t* __restrict__ ptp, int8_t* __restrict__ act,
@@ -357,19 +455,21 @@ __global__ void __launch_bounds__(kPartWarps * 32) k_assign_walk(
     const int nwarps = gridDim.x * kPartWarps;
     int my_changed = 0;
     unsigned long long calls = 0;
-    int u = blockIdx.x * kPartWarps + (threadIdx.x >> 5);
-    int e0n = 0, e1n = 0;  // the next unit's range, read one unit ahead
-    if (u < U) e0n = ustart[u], e1n = ustart[u + 1];
-    for (; u < U; u += nwarps) {
-        const int e0 = e0n, e1 = e1n;
-        if (u + nwarps < U) e0n = ustart[u + nwarps], e1n = ustart[u + nwarps + 1];
+    int i = blockIdx.x * kPartWarps + (threadIdx.x >> 5);
+    int4 mn = make_int4(0, 0, 0, 0);  // the next unit {e0, e1, k, u}, read one unit ahead
+    if (i < MU) mn = mu[i];
+    for (; i < MU; i += nwarps) {
+        const int e0 = mn.x, e1 = mn.y, k = mn.z, u = mn.w;
+        if (i + nwarps < MU) mn = mu[i + nwarps];
+        // the unit's first order: its fresh action (already in the cache) and the
+        // cached action it replaced
+        const int a1 = act[ft[u]], c1 = fold[u];
         int bt = 0, br = 0, bo = -1, nt = 0;
         if (lane < e1 - e0) {
             bt = uord[e0 + lane];
             br = reg[bt], bo = act[bt];
         }
         if (e0 + kPartBatch + lane < e1) nt = uord[e0 + kPartBatch + lane];
-        const int k = prod[__shfl_sync(kFull, bt, 0)];
         int sb[NPL], sc[NPL], X[NPL], th[NPL], tm[NPL], tp[NPL], lr[NPL];
 #pragma unroll
         for (int q = 0; q < NPL; ++q) {
@@ -383,6 +483,17 @@ __global__ void __launch_bounds__(kPartWarps * 32) k_assign_walk(
                 tp[q] = ptp[v];
                 X[q] = x0[v];
                 if (DUAL) lr[q] = __ldg(lam + v);
+                // after the first order: O + [j == c1], F + [j == a1]
+                const int dd = (j == c1 ? 1 : 0) - (j == a1 ? 1 : 0);
+                if (dd > 0) {
+                    X[q] += 1;
+                    tm[q] = th[q], th[q] = tp[q];
+                    tp[q] = part_sval(L, sb[q], sc[q], X[q] + 1);
+                } else if (dd < 0) {
+                    X[q] -= 1;
+                    tp[q] = th[q], th[q] = tm[q];
+                    tm[q] = part_sval(L, sb[q], sc[q], X[q] - 1);
+                }
             }
         }
         for (int eb = e0; eb < e1; eb += kPartBatch) {
@@ -581,10 +692,15 @@ cudaError_t picard_assigned(Instance* I, const pic_policy* pol, const int32_t* p
     };
     A(&ukey, Tn); A(&uks, Tn); A(&uord, Tn); A(&flag, Tn); A(&upos, Tn); A(&ustart, Tn + 1);
     A(&key, Tn); A(&key_s, Tn); A(&t_s, Tn); A(&off, (size_t)KN + 1); A(&cflag, 1); A(&total, 1);
-    int4* pr = nullptr;
-    int32_t* ptp = nullptr;
-    A(&ptp, (size_t)KN);
+    int4 *pr = nullptr, *mu = nullptr;
+    int32_t *ptp = nullptr, *pth = nullptr, *ft = nullptr, *fk = nullptr, *fr = nullptr,
+            *mflag = nullptr, *mpos = nullptr;
+    int8_t* fold = nullptr;
+    A(&ptp, (size_t)KN); A(&pth, (size_t)KN);
+    A(&ft, Tn); A(&fk, Tn); A(&fr, Tn); A(&mflag, Tn); A(&mpos, Tn);
     if (!e) e = cudaMallocAsync(&pr, sizeof(int4) * (size_t)KN, st);
+    if (!e) e = cudaMallocAsync(&mu, sizeof(int4) * Tn, st);
+    if (!e) e = cudaMallocAsync(&fold, Tn, st);
     const int gb = (int)((Tn + 255) / 256) < 4 * I->num_sms ? (int)((Tn + 255) / 256) : 4 * I->num_sms;
     int U = 0;
     if (!e && T > 0) {
@@ -602,6 +718,19 @@ cudaError_t picard_assigned(Instance* I, const pic_policy* pol, const int32_t* p
         if (!e) e = cudaStreamSynchronize(st);
         I->launches += 6;
     }
+    // per unit: first order, product, region; the units with more than one order
+    int MU = 0;
+    if (!e && T > 0) {
+        const int gu = (U + 255) / 256 < 4 * I->num_sms ? (U + 255) / 256 : 4 * I->num_sms;
+        k_assign_units<<<gu, 256, 0, st>>>(U, ustart, uord, I->prod, I->reg, ft, fk, fr, mflag);
+        e = scan_exclusive(mflag, mpos, U, total, I->scan_blk, st);
+        if (!e) {
+            k_assign_mlist<<<gu, 256, 0, st>>>(U, ustart, ft, fk, mflag, mpos, mu);
+            e = cudaMemcpyAsync(&MU, total, sizeof(int), cudaMemcpyDeviceToHost, st);
+        }
+        if (!e) e = cudaStreamSynchronize(st);
+        I->launches += 5;
+    }
     // the cached actions naming (k, j), listed per (k, j) in time order
     auto tables = [&]() {
         k_part_keys<<<gb, 256, 0, st>>>(T, N, KN, I->prod, I->act_t, key);
@@ -612,32 +741,49 @@ cudaError_t picard_assigned(Instance* I, const pic_policy* pol, const int32_t* p
     };
     const int gkn = (KN + 255) / 256 < 8 * I->num_sms ? (KN + 255) / 256 : 8 * I->num_sms;
     const int smem = kPartWarps * kPartBatch * NPL * 32 * (int)sizeof(int32_t);
-    const int blocks = (U + kPartWarps - 1) / kPartWarps;
+    const int blocks = (MU + kPartWarps - 1) / kPartWarps;
+    // one warp per 32 units: U / 32 warps, 8 per CTA
+    const int gfirst = (U + 255) / 256 < 8 * I->num_sms ? (U + 255) / 256 : 8 * I->num_sms;
     int iters = 0, converged = 0;
     for (int pass = 1; !e && T > 0 && pass <= iters_cap; ++pass) {
         if ((e = tables())) break;
-        k_assign_pairs<<<gkn, 256, 0, st>>>(KN, I->x0, off, t_s, pr, ptp);
+        k_assign_pairs<<<gkn, 256, 0, st>>>(KN, I->x0, off, t_s, pr, ptp, pth);
         I->launches += 1;
         if ((e = cudaMemsetAsync(cflag, 0, sizeof(int32_t), st))) break;
+#define ASSIGN_FIRST(NP_, D_)                                                               \
+    k_assign_first<NP_, D_><<<gfirst, 256, 0, st>>>(U, N, ft, fk, fr, I->cost, I->lam, pth,   \
+                                                    I->act_t, fold, I->ctrl, cflag)
+        if (NPL == 1) {
+            if (dual) ASSIGN_FIRST(1, true); else ASSIGN_FIRST(1, false);
+        } else if (NPL == 2) {
+            if (dual) ASSIGN_FIRST(2, true); else ASSIGN_FIRST(2, false);
+        } else {
+            if (dual) ASSIGN_FIRST(4, true); else ASSIGN_FIRST(4, false);
+        }
+#undef ASSIGN_FIRST
+        I->launches += 1;
+        if ((e = cudaGetLastError())) break;
 #define ASSIGN_WALK(NP_, D_)                                                                \
     do {                                                                                    \
         e = cudaFuncSetAttribute(k_assign_walk<NP_, D_>,                                   \
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem);       \
         if (!e)                                                                             \
             k_assign_walk<NP_, D_><<<blocks, kPartWarps * 32, smem, st>>>(                 \
-                U, N, ustart, uord, I->prod, I->reg, I->cost, I->lam, I->x0, t_s, pr, ptp, \
+                MU, N, mu, ft, fold, uord, I->reg, I->cost, I->lam, I->x0, t_s, pr, ptp,   \
                 I->act_t, I->ctrl, cflag);                                                 \
     } while (0)
-        if (NPL == 1) {
-            if (dual) ASSIGN_WALK(1, true); else ASSIGN_WALK(1, false);
-        } else if (NPL == 2) {
-            if (dual) ASSIGN_WALK(2, true); else ASSIGN_WALK(2, false);
-        } else {
-            if (dual) ASSIGN_WALK(4, true); else ASSIGN_WALK(4, false);
+        if (MU > 0) {
+            if (NPL == 1) {
+                if (dual) ASSIGN_WALK(1, true); else ASSIGN_WALK(1, false);
+            } else if (NPL == 2) {
+                if (dual) ASSIGN_WALK(2, true); else ASSIGN_WALK(2, false);
+            } else {
+                if (dual) ASSIGN_WALK(4, true); else ASSIGN_WALK(4, false);
+            }
+            I->launches += 1;
         }
 #undef ASSIGN_WALK
         if (e) break;
-        I->launches += 1;
         int hf = 0;
         if ((e = cudaGetLastError())) break;
         if ((e = cudaMemcpyAsync(&hf, cflag, sizeof(int), cudaMemcpyDeviceToHost, st))) break;
@@ -667,10 +813,13 @@ cudaError_t picard_assigned(Instance* I, const pic_policy* pol, const int32_t* p
         k_part_result<<<1, 1, 0, st>>>(I->ctrl, iters, converged);
         e = cudaGetLastError();
     }
-    int32_t* bufs[] = {ukey, uks, uord, flag, upos, ustart, key, key_s, t_s, off, cflag, total, ptp};
+    int32_t* bufs[] = {ukey, uks, uord, flag, upos, ustart, key, key_s, t_s, off, cflag, total,
+                       ptp, pth, ft, fk, fr, mflag, mpos};
     for (int32_t* b : bufs)
         if (b) cudaFreeAsync(b, st);
     if (pr) cudaFreeAsync(pr, st);
+    if (mu) cudaFreeAsync(mu, st);
+    if (fold) cudaFreeAsync(fold, st);
     return e;
 }
 

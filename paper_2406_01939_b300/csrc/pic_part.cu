@@ -1,9 +1,15 @@
-// Algorithm 1 with the product partition (Sec. 3: all orders of a product go
-// to one process), for the greedy and bid-price policies, with or without node
-// capacity.  Processor m owns the products k with k mod P = m and, every pass,
-// replays the whole horizon taking its own orders' actions from the policy and
-// every other order's action from the cache.
+// Algorithm 1 for partitions of the orders other than contiguous time chunks,
+// greedy and bid-price policies:
+//   picard_products  the product partition (Sec. 3: all orders of a product go
+//                    to one process), with or without node capacity;
+//   picard_assigned  any caller-given assignment proc[t] (e.g. the uniform
+//                    random partition of Sec. 4.1), without capacity.
+// Each pass, Algorithm 1 has every process replay the horizon, taking its own
+// orders' actions from the policy and every other order's action from the
+// cache.  Here a process visits only its own orders: what the foreign cached
+// actions do to its state is read from per-pass lists of the cache.
 //
+// Product partition.  Processor m owns the products k with k mod P = m.
 // Only the processor's own products' stock matters to its decisions (foreign
 // actions never touch it), and node capacity follows from counts: the capacity
 // of node j before order t, in processor m's view, is

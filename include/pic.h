@@ -155,7 +155,8 @@ typedef struct {
     int32_t seg_window;       /* tuning: orders of one product per warp work unit; 0 = 64
                                  (greedy, bid-price) or 8 (MLP policies) */
     void* stream;             /* cudaStream_t or NULL */
-    int64_t* trace;           /* HOST [trace_cap][4] per-pass record, or NULL: ns from the
+    int64_t* trace;           /* PIC_MODE_PICARD: HOST [trace_cap][4] per-pass record, or NULL (the
+                                 other modes leave it untouched): ns from the
                                  simulation kernel's start to the end of the pass's prefix
                                  phase, ns to the end of its replay phase, policy calls in the
                                  pass, work units replayed in the pass */

@@ -209,8 +209,6 @@ cudaError_t picard_run(Instance* I, const pic_policy* pol, int max_iters, int fl
 cudaError_t mlp_alloc(Instance* I);
 cudaError_t mlp_prepare(Instance* I, const pic_policy* pol, cudaStream_t st);
 cudaError_t sequential_mlp(Instance* I, const pic_policy* pol, int flags, cudaStream_t st);
-// Node capacity (pic_cap.cu): Algorithm 1 on M contiguous chunks of at most
-// kCapChunk orders with the state (x, c), and the sequential simulator.
 // Algorithm 1 with the product partition (pic_part.cu): processor of product k
 // is k mod P; the cache I->act_t (time order) holds alpha^0 on entry and the
 // last iterate on return; final stock in I->xfin; iters and converged in I->ctrl.
@@ -223,6 +221,8 @@ cudaError_t picard_assigned(Instance* I, const pic_policy* pol, const int32_t* p
                             int iters_cap, cudaStream_t st);
 // Flag (Ctrl::pad0 bit 64) an initial cache holding a value outside [-1, N).
 cudaError_t check_alpha_init(Instance* I, const int8_t* alpha, cudaStream_t st);
+// Node capacity (pic_cap.cu): Algorithm 1 on M contiguous chunks of at most
+// kCapChunk orders with the state (x, c), and the sequential simulator.
 cudaError_t picard_cap(Instance* I, const pic_policy* pol, int M, int max_iters, int flags,
                        const int8_t* alpha_init, unsigned long long timeout_ns, bool trace,
                        cudaStream_t st);

@@ -36,13 +36,15 @@ namespace {
 constexpr int kPartWarps = 4;   // warps (processors) per CTA of the walk
 constexpr int kPartBatch = 32;  // own orders staged per warp at a time
 
-// key of each cached action: product * N + node, or K N for a^phi
+// key of each cached action: product * N + node, or K N for a^phi (and for a
+// value outside [0, N), which the call reports as an invalid initial cache), so
+// that every key lies in [0, K N]
 __global__ void k_part_keys(int T, int N, int KN, const int32_t* __restrict__ prod,
                             const int8_t* __restrict__ act, int32_t* __restrict__ key) {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < T;
          t += (long long)gridDim.x * blockDim.x) {
         const int a = act[t];
-        key[t] = a >= 0 ? prod[t] * N + a : KN;
+        key[t] = a >= 0 && a < N ? prod[t] * N + a : KN;
     }
 }
 

@@ -119,15 +119,16 @@ float orc_gumbel(uint64_t seed, int32_t traj, int64_t t, int32_t n) {
 }
 
 /* ------------------------------------------------------------------------- */
-/* MLP scorer.  Parameters are BF16 bit patterns (upcast to FP32 exactly).
- * Layout: W1[IN][H] with IN = 2N+16 rows ordered [cost (N) | stock (N) | emb (16)],
- * b1[H], W2[H][N], b2[N], E[R][16].  Features: cost[r][n]/128,
- * min(S_n,32)/32, E[r][e].  Fixed FP32 order: h_j = b1_j, then one fmaf per
- * input over cost rows, embedding rows, stock rows (in that order); ReLU; then
- * eight partial sums p_e (e = 0..7), each an fmaf chain from 0 over the hidden
- * units j = e, e+8, e+16, ... in increasing j, and
- * s_n = b2_n + (((p_0 + p_1) + (p_2 + p_3)) + ((p_4 + p_5) + (p_6 + p_7))).
- * H must be a multiple of 8. */
+/* MLP scorer (the policy network of Sec. 4.1: two dense layers with a ReLU,
+ * one score per node).  Parameters are BF16 bit patterns (upcast to FP32
+ * exactly).  Layout: W1[IN][H] with IN = 2N+16 rows ordered
+ * [cost (N) | stock (N) | emb (16)], b1[H], W2[H][N], b2[N], E[R][16].
+ * Features: cost[r][n]/128, min(S_n,32)/32, E[r][e].  The paper fixes no FP32
+ * evaluation order (it runs 16-bit JAX); this is the plain one, a single
+ * sequential fmaf chain per output:
+ *   h_j = b1_j, then one fmaf per input over the cost rows, the embedding rows
+ *         and the stock rows (in that order); h_j = max(h_j, 0);
+ *   s_n = b2_n, then one fmaf per hidden unit j = 0, 1, ..., H-1 (W2[j][n] h_j). */
 /* ------------------------------------------------------------------------- */
 static inline float bf16f(uint16_t b) {
     uint32_t u = (uint32_t)b << 16;
@@ -158,10 +159,9 @@ void orc_mlp_scores(int N, int H, const uint16_t* W1, const uint16_t* b1, const 
         h[j] = a > 0.0f ? a : 0.0f;
     }
     for (int n = 0; n < N; ++n) {
-        float p[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-        for (int j = 0; j < H; ++j) p[j & 7] = fmaf(bf16f(W2[(size_t)j * N + n]), h[j], p[j & 7]);
-        const float v = ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
-        s_out[n] = bf16f(b2[n]) + v;
+        float a = bf16f(b2[n]);
+        for (int j = 0; j < H; ++j) a = fmaf(bf16f(W2[(size_t)j * N + n]), h[j], a);
+        s_out[n] = a;
     }
     free(h);
 }

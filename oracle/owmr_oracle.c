@@ -62,8 +62,9 @@ typedef struct {
 /* The network's FP32 output z for features (y, d, g = e * 2^-12), in this order:
  *   h1_k = relu(fma(W1[2][k], g, fma(W1[1][k], d, fma(W1[0][k], y, b1_k))))
  *   h2_j = relu(b2_j + sum_k W2[k][j] h1_k), one fma per k in increasing k
- *   p_g  = sum_{j = 8g..8g+7} w3_j h2_j, one fma per j from 0
- *   z    = b3 + p_0 + p_1 + ... (left to right), relu(v) = v > 0 ? v : 0. */
+ *   z    = b3, then one fma per j in increasing j (w3_j h2_j),
+ * relu(v) = v > 0 ? v : 0.  Every output is one sequential fma chain: the
+ * appendix fixes no FP32 order, and this is the plain one. */
 float owmr_mlp(const Net* net, int y, int d, int e, float* h1, float* h2) {
     const int H = net->H;
     const float fy = (float)y, fd = (float)d, fg = (float)e * 0.000244140625f; /* exact */
@@ -79,11 +80,7 @@ float owmr_mlp(const Net* net, int y, int d, int e, float* h1, float* h2) {
         h2[j] = a > 0.f ? a : 0.f;
     }
     float z = bf16f(net->b3[0]);
-    for (int g = 0; g < H / 8; ++g) {
-        float p = 0.f;
-        for (int j = 8 * g; j < 8 * g + 8; ++j) p = fmaf(bf16f(net->w3[j]), h2[j], p);
-        z = z + p;
-    }
+    for (int j = 0; j < H; ++j) z = fmaf(bf16f(net->w3[j]), h2[j], z);
     return z;
 }
 

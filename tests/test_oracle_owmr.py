@@ -170,6 +170,26 @@ def test_network_within_fp32_bound_of_fp64():
     assert worst < 1.0
 
 
+def test_network_output_is_one_chain_from_the_bias():
+    """The FP32 order of the network's output layer, pinned by a case whose
+    rounding has a closed form: with h2_j = 1 for every unit (W2 = 0, b2 = 1)
+    and w3 = 1, b3 = 2^24, a single fma chain starting from b3 rounds every
+    step back to 2^24 (ties to even), so z = 2^24 exactly; summing the H ones
+    in groups first, or adding b3 last, gives 2^24 + H."""
+    H = 64
+    bf = lambda v: synth.f32_to_bf16(np.asarray(v, np.float32))
+    net = synth.OwmrNet(H, bf(np.zeros((3, H))), bf(np.zeros(H)), bf(np.zeros((H, H))),
+                        bf(np.ones(H)), bf(np.ones(H)), bf([2.0 ** 24]))
+    assert ow.mlp(net, 5, 1, 3) == 2.0 ** 24
+    # increasing j: w3_0 = 2^24 first, then the ones vanish; decreasing j would
+    # give (H - 1) + 2^24, which rounds to 2^24 + H
+    w3 = np.ones(H)
+    w3[0] = 2.0 ** 24
+    net = synth.OwmrNet(H, bf(np.zeros((3, H))), bf(np.zeros(H)), bf(np.zeros((H, H))),
+                        bf(np.ones(H)), bf(w3), bf([0.0]))
+    assert ow.mlp(net, 5, 1, 3) == 2.0 ** 24
+
+
 def test_literal_fixed_point_prop1_random():
     """Prop. 1 for a partition by retailers: the first step where alpha^k
     differs from the sequential path moves strictly forward with k (its owner

@@ -310,6 +310,55 @@ def test_mlp_scores_match_fp64_matmul():
             assert (np.abs(got - s) <= 2 * bound + 1e-12).all()
 
 
+def _bf(v):
+    return synth.f32_to_bf16(np.asarray(v, np.float32))
+
+
+def test_mlp_score_order_is_one_chain_from_the_bias():
+    """The FP32 order of the scorer, pinned by cases whose rounding has a closed
+    form.  With h_j = 1 for every hidden unit (W1 = 0, b1 = 1):
+      - b2 = 2^24 and W2[:, 0] = 1: starting from b2, every fmaf adds 1 to 2^24
+        and rounds back to 2^24 (a tie, to the even neighbour), so s_0 = 2^24
+        exactly; summing the 256 ones first (any grouped or tree order, or b2
+        added last) gives 2^24 + 256;
+      - b2 = 0, W2[0, 1] = 2^24, W2[j>0, 1] = 1: increasing j gives 2^24;
+        decreasing j gives 255 + 2^24, which rounds to 2^24 + 256.
+    Layer 1 (N = 3, W1 = 0 except: cost row 0 = 2^24 with cost 128, so the
+    feature is 1; embedding row 0 = -1 with E[r][0] = 2^24; stock rows = 1 with
+    stock >= 32, feature 1): cost, then embedding, then stock gives
+    2^24 - 2^24 + 3 = 3; stock before the embedding gives 0 (the ones vanish
+    into 2^24); stock first gives 4 (2^24 + 3 rounds to 2^24 + 4)."""
+    N, H, R = 3, 256, 2
+    IN = 2 * N + 16
+    W1 = np.zeros((IN, H), np.float32)
+    b1 = np.ones(H, np.float32)
+    W2 = np.zeros((H, N), np.float32)
+    b2 = np.zeros(N, np.float32)
+    W2[:, 0] = 1.0
+    b2[0] = 2.0 ** 24
+    W2[0, 1] = 2.0 ** 24
+    W2[1:, 1] = 1.0
+    E = np.zeros((R, 16), np.float32)
+    mlp = synth.MLPParams(_bf(W1), _bf(b1), _bf(W2), _bf(b2), _bf(E), H)
+    s = oracle.mlp_scores(N, mlp, np.array([1, 1, 1], np.int32), 0, np.array([40, 40, 40], np.int32))
+    assert s[0] == np.float32(2.0 ** 24)
+    assert s[1] == np.float32(2.0 ** 24)
+    assert s[2] == np.float32(0.0)
+    # layer 1: read h_0 back through W2[0, 2] = 1 (b2 = 0, every other W2 = 0)
+    W1 = np.zeros((IN, H), np.float32)
+    W1[0, 0] = 2.0 ** 24           # cost feature of node 0 (cost 128 -> 1.0)
+    W1[2 * N, 0] = -1.0            # embedding input 0
+    W1[N:2 * N, 0] = 1.0           # stock features (>= 32 units -> 1.0)
+    E = np.zeros((R, 16), np.float32)
+    E[1, 0] = 2.0 ** 24
+    W2 = np.zeros((H, N), np.float32)
+    W2[0, 2] = 1.0
+    mlp = synth.MLPParams(_bf(W1), _bf(np.zeros(H)), _bf(W2), _bf(np.zeros(N)), _bf(E), H)
+    s = oracle.mlp_scores(N, mlp, np.array([128, 0, 0], np.int32), 1,
+                          np.array([32, 33, 90], np.int32))
+    assert s[2] == np.float32(3.0)
+
+
 # ----------------------------------------------------------------------------- Philox / log / Gumbel
 def _kat():
     import os

@@ -199,6 +199,9 @@ typedef struct {
     int64_t sat_decisions; /* MLP decisions taken from the saturated-state score table (see
                               PIC_FLAG_NO_SAT); mlp_calls - tc_decisions - sat_decisions ran
                               the FP32 scorer */
+    int64_t near_ties;     /* FP32-scorer decisions whose fast layer-2 scores left a near tie
+                              within their error bound, re-scored in the reference order
+                              (one sequential fmaf chain per output, from the bias) */
 } pic_sim_result;
 
 /* Per-trajectory result of pic_simulate_batch. */

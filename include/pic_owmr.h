@@ -51,13 +51,6 @@ extern "C" {
 
 typedef struct pic_owmr pic_owmr;
 
-/* pic_owmr_opts.flags bit (besides PIC_FLAG_TIMING and PIC_FLAG_REUSE_TABLES): with a network,
- * keep W2 resident across clusters of 4 CTAs (each holds a column quarter in shared memory and
- * the cluster pools its pending calls into shared rounds) instead of streaming W2 through each
- * CTA in every round.  Same operations in the same order, so the same results; slower on B300
- * (the rounds are bound by their FMA chains, and cluster-wide rounds are more numerous). */
-enum { PIC_OWMR_FLAG_CLUSTER_W2 = 1 << 16 };
-
 /* One OWMR trajectory's inputs. */
 typedef struct {
     int32_t T, N;
@@ -80,8 +73,11 @@ typedef struct {
  * w3 [H]; b3 [1].  FP32 order, features y, d and g = e * 2^-12 as floats:
  *   h1_k = relu(fma(W1[2][k], g, fma(W1[1][k], d, fma(W1[0][k], y, b1_k))))
  *   h2_j = relu(acc), acc = b2_j, then acc = fma(W2[k][j], h1_k, acc) for k = 0..H-1
- *   p_g  = fma chain over j = 8g..8g+7 of w3_j h2_j, from 0
- *   z    = b3 + p_0 + p_1 + ... (left to right);  relu(v) = v > 0 ? v : 0.
+ *   z    = b3, then z = fma(w3_j, h2_j, z) for j = 0..H-1;  relu(v) = v > 0 ? v : 0.
+ * Every output is one sequential chain from its bias.  The kernels add the
+ * output layer in groups of 8 first (a shorter chain) and keep a bound on the
+ * difference; a q whose floor that bound leaves undecided is taken from z in
+ * the order above (counted in pic_owmr_result.near_ties).
  * hidden = 0: no network (q = base).  Otherwise 64 <= H <= 512, H % 64 == 0. */
 typedef struct {
     int32_t hidden;
@@ -118,6 +114,8 @@ typedef struct {
     int64_t eval_rounds;    /* batched network rounds (Picard) */
     int32_t launches;       /* kernels this call launched */
     float ms_total;         /* device time of the call (PIC_FLAG_TIMING) */
+    int64_t near_ties;      /* network calls whose q the fast output layer left undecided
+                               within its error bound, re-evaluated in the reference order */
 } pic_owmr_result;
 
 /* Copy and validate an instance.  *out is owned by the caller and freed with

@@ -68,7 +68,8 @@ class pic_sim_result(C.Structure):
                 ("seg_replays", C.c_int64), ("launches", C.c_int32), ("prep_ms", C.c_float),
                 ("sim_ms", C.c_float), ("total_ms", C.c_float), ("seg_window", C.c_int32),
                 ("cta_threads", C.c_int32), ("ctas_per_sm", C.c_int32), ("mlp_calls", C.c_int64),
-                ("tc_decisions", C.c_int64), ("sat_decisions", C.c_int64)]
+                ("tc_decisions", C.c_int64), ("sat_decisions", C.c_int64),
+                ("near_ties", C.c_int64)]
 
 
 class pic_traj_result(C.Structure):

@@ -203,7 +203,7 @@ void free_instance(Instance& I) {
                     I.pstart, I.run_start, I.run_of, I.run_chunk, I.seg_run, I.seg_of_run, I.seg_prod, I.seg_cf,
                     I.seg_ce, I.seg_meta, I.seg_lpt, I.len_hist, I.alpha_s, I.agg, I.carry, I.sbagg,
                     I.sbincl, I.fc, I.xfin, I.xwork, I.act_t, I.tmp_a, I.tmp_b, I.tmp_c, I.scan_blk,
-                    I.hist, I.ctrl, I.trace, I.mlp_P, I.mlp_W1p, I.mlp_W2p, I.mlp_b2, I.mlp_Emax, I.mlp_bnd, I.mlp_sat,
+                    I.hist, I.ctrl, I.trace, I.mlp_P, I.mlp_W1p, I.mlp_W2p, I.mlp_b2, I.mlp_Emax, I.mlp_bnd, I.mlp_c2, I.mlp_sat,
                     I.cap, I.cap_run_t, I.cap_info, I.cap_inv, I.cap_qagg, I.cap_qinc};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -594,6 +594,7 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
         res->rescored = (int64_t)hc.rescored;
         res->tc_decisions = (int64_t)hc.tc_rows;
         res->sat_decisions = (int64_t)hc.sat_rows;
+        res->near_ties = (int64_t)hc.near_ties;
         res->seg_replays = (int64_t)hc.seg_replays;
         res->launches = I.launches;
         res->prep_ms = res->sim_ms = res->total_ms = 0.0f;

@@ -146,10 +146,11 @@ __global__ void __launch_bounds__(32 * kSeqWarps) k_seq_batch(
         q.gumbel = bp.kind == PIC_POLICY_GUMBEL;
         q.seed = bp.seed;
         q.traj = bp.traj;
-        unsigned long long nsat = 0;
+        MlpCounts mc{0, 0, 0, 0, 0};
         seq_mlp_body<NPL, SMEMW>(T, N, prod + t0, reg + t0, xw, act_t + t0, q, W1p, W2p, s_fs[w],
-                                 s_hs[w], nsat);
-        if (lane_id() == 0 && nsat) atomicAdd(&ctrl->sat_rows, nsat);
+                                 s_hs[w], mc);
+        if (lane_id() == 0 && mc.sat) atomicAdd(&ctrl->sat_rows, mc.sat);
+        if (lane_id() == 0 && mc.near) atomicAdd(&ctrl->near_ties, mc.near);
     }
 }
 
@@ -181,7 +182,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_picard_batch(KArgs a, MlpPoli
     const CostTable<false> ct{a.cost, nullptr, a.N};
     const int wib = threadIdx.x >> 5;
     unsigned long long calls = 0;
-    MlpCounts mc{0, 0, 0, 0};
+    MlpCounts mc{0, 0, 0, 0, 0};
     picard_passes<NPL, WARPS>(a, calls, [&](int seg, const SegMeta& m, int fcp, int* fc_cur, int it) {
         const int tb = __ldg(b.traj_of_prod + m.k);
         const BatchPol bp = b.pol[tb];
@@ -209,6 +210,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_picard_batch(KArgs a, MlpPoli
         atomicAdd(&a.ctrl->rescored, mc.rescored);
         atomicAdd(&a.ctrl->tc_rows, mc.tc);
         atomicAdd(&a.ctrl->sat_rows, mc.sat);
+        atomicAdd(&a.ctrl->near_ties, mc.near);
     }
 }
 
@@ -820,6 +822,7 @@ pic_status pic_simulate_batch(pic_instance* h, const pic_policy* pols, const pic
         res->mlp_calls = picard ? (int64_t)hc.mlp_calls : 0;
         res->tc_decisions = picard ? (int64_t)hc.tc_rows : 0;
         res->sat_decisions = (int64_t)hc.sat_rows;
+        res->near_ties = (int64_t)hc.near_ties;
         if (!picard)
             for (int b = 0; b < B; ++b)
                 if (bt->h_pol[b].kind >= PIC_POLICY_MLP) res->mlp_calls += bt->h_toff[b + 1] - bt->h_toff[b];

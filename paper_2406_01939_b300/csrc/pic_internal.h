@@ -38,6 +38,7 @@ struct Ctrl {
     unsigned long long mlp_calls;  // MLP / Gumbel policy evaluations (batch kernel)
     unsigned long long tc_rows;    // MLP decisions taken from tensor-core tile scores
     unsigned long long sat_rows;   // MLP decisions taken from the saturated-state table
+    unsigned long long near_ties;  // MLP decisions re-scored in the reference order (near ties)
     int cap_fct[2];          // capacity kernel: first changed time of the pass, per parity
     int win_fct[2];          // max_steps window: first changed time of the pass, per parity
     int win_hi, win_hi_prev; // max_steps window of the current pass and of the previous one:
@@ -147,7 +148,9 @@ struct Instance {
     float *mlp_b2;      // [N]
     float *mlp_Emax;    // [R] error-bound constant per region (tensor-core tiles)
     float *mlp_bnd;     // [2] max column sum of |W2|, max |b2|
-    float *mlp_sat;     // [R][N] FP32 scores of the saturated state (every stock feature 1)
+    float *mlp_c2;      // [N] column sums of |W2| (rounded up)
+    float *mlp_sat;     // [R][N] reference-order scores of the saturated state (every stock
+                        // feature 1)
     // scratch for the sort and scans
     int32_t *tmp_a, *tmp_b, *tmp_c;   // [T] each
     int32_t *scan_blk;                // block sums

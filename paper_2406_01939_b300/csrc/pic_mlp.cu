@@ -52,13 +52,14 @@ __global__ void k_mlp_prefix(MlpArgs m) {
     if (idx < N) m.b2f[idx] = bf16f(m.b2[idx]);
 }
 
-// Error-bound constants of the tensor-core tiles.  C1[j] = sum_n |W1s[n][j]| and
-// the scalars bnd = {max_n sum_j |W2[j][n]|, max_n |b2[n]|} (one block), then
-// Emax[r] = max_j (|P[r][j]| + C1[j]) (one warp per region).  Sums are rounded
-// up by a relative 2^-16 so that they bound the exact values.
+// Error-bound constants.  c2[n] = sum_j |W2[j][n]| (the fast layer-2 order's
+// bound), C1[j] = sum_n |W1s[n][j]| and the scalars bnd = {max_n c2[n],
+// max_n |b2[n]|} (one block), then Emax[r] = max_j (|P[r][j]| + C1[j]) (one
+// warp per region; the tensor-core tiles' bound).  Sums are rounded up by a
+// relative 2^-16 so that they bound the exact values.
 __global__ void k_mlp_consts(int N, const uint16_t* __restrict__ W1, const uint16_t* __restrict__ W2,
                              const uint16_t* __restrict__ b2, float* __restrict__ C1,
-                             float* __restrict__ bnd) {
+                             float* __restrict__ bnd, float* __restrict__ c2out) {
     __shared__ float red[2][kHidden];
     const int j = threadIdx.x;  // blockDim = kHidden
     float c1 = 0.f;
@@ -68,6 +69,7 @@ __global__ void k_mlp_consts(int N, const uint16_t* __restrict__ W1, const uint1
     if (j < N) {
         for (int jj = 0; jj < kHidden; ++jj) c2 += fabsf(bf16f(W2[(size_t)jj * N + j]));
         bb = fabsf(bf16f(b2[j]));
+        c2out[j] = c2 * (1.0f + 1.0f / 65536.0f);
     }
     red[0][j] = c2;
     red[1][j] = bb;
@@ -100,7 +102,8 @@ __global__ void k_mlp_emax(int R, const float* __restrict__ P, const float* __re
 }
 
 // Scores of the saturated state (every warehouse at 32 units or more, so every
-// stock feature is 1) for every region: one warp per region runs mlp_scores.
+// stock feature is 1) for every region, in the reference order: one warp per
+// region runs layer 1 as the scorer does, then each output's single chain.
 constexpr int kSatWarps = 8;
 
 template <int NPL>
@@ -111,17 +114,14 @@ __global__ void __launch_bounds__(32 * kSatWarps) k_mlp_sat(MlpPolicy p, int R, 
     const int r = blockIdx.x * kSatWarps + w;
     if (r >= R) return;
     int S[NPL];
-    bool want[NPL];
+#pragma unroll
+    for (int i = 0; i < NPL; ++i) S[i] = 32;
+    mlp_hidden<NPL, false>(p, p.W1p, S, r, fs[w], hs[w]);
 #pragma unroll
     for (int i = 0; i < NPL; ++i) {
-        S[i] = 32;
-        want[i] = lane + 32 * i < p.N;
+        const int n = lane + 32 * i;
+        if (n < p.N) sat[(size_t)r * p.N + n] = ref_score<false>(p, p.W2p, hs[w], n);
     }
-    float s[NPL];
-    mlp_scores<NPL, false>(p, p.W1p, p.W2p, S, r, want, fs[w], hs[w], s);
-#pragma unroll
-    for (int i = 0; i < NPL; ++i)
-        if (want[i]) sat[(size_t)r * p.N + lane + 32 * i] = s[i];
 }
 
 // ---------------------------------------------------------------- sequential simulator
@@ -133,20 +133,21 @@ __global__ void __launch_bounds__(32 * GROUP) k_seq_mlp(int T, int N, const int3
     __shared__ float fs[GROUP][128];
     __shared__ __align__(16) float hs[kHidden];
     __shared__ float ht[GROUP > 1 ? 128 : 1];
-    __shared__ uint4 am[2];
+    __shared__ uint4 am[4];
     extern __shared__ uint4 s_w[];
     if (SMEMW) stage_weights(p, s_w);
     const uint4* W1p = SMEMW ? s_w : p.W1p;
     const uint4* W2p = SMEMW ? s_w + p.N * kHidden / 8 : p.W2p;
     const int w = threadIdx.x >> 5;
     const Group G{w, 1, hs, ht, am};
-    unsigned long long nsat = 0;
-    seq_mlp_body<NPL, SMEMW, GROUP>(T, N, prod, reg, xw, act_t, p, W1p, W2p, fs[w], hs, nsat, &G);
+    MlpCounts mc{0, 0, 0, 0, 0};
+    seq_mlp_body<NPL, SMEMW, GROUP>(T, N, prod, reg, xw, act_t, p, W1p, W2p, fs[w], hs, mc, &G);
     if (threadIdx.x == 0) {
         ctrl->iters = 1;
         ctrl->converged = 1;
         ctrl->policy_calls = (unsigned long long)T;
-        ctrl->sat_rows = nsat;
+        ctrl->sat_rows = mc.sat;
+        ctrl->near_ties = mc.near;
     }
 }
 
@@ -162,7 +163,7 @@ __global__ void __launch_bounds__(kMlpThreads, 2) k_picard_mlp(KArgs a, MlpPolic
     __shared__ float s_fs[kWarps][128];
     __shared__ __align__(16) float s_hs[GROUP > 1 ? kGroups : kWarps][kHidden];
     __shared__ float s_ht[kGroups][GROUP > 1 ? 128 : 1];
-    __shared__ uint4 s_am[kGroups][2];
+    __shared__ uint4 s_am[kGroups][4];
     if (SMEMW) stage_weights(p, s_w);
     const uint4* W1p = SMEMW ? s_w : p.W1p;
     const uint4* W2p = SMEMW ? s_w + p.N * kHidden / 8 : p.W2p;
@@ -170,7 +171,7 @@ __global__ void __launch_bounds__(kMlpThreads, 2) k_picard_mlp(KArgs a, MlpPolic
     const int grp = wib / GROUP;
     const Group G{wib % GROUP, 1 + grp, s_hs[GROUP > 1 ? grp : wib], s_ht[grp], s_am[grp]};
     unsigned long long calls = 0;
-    MlpCounts mc{0, 0, 0, 0};
+    MlpCounts mc{0, 0, 0, 0, 0};
     auto replay = [&](int seg, const SegMeta& m, int fcp, int* fc_cur, int it) {
         const unsigned long long c0 = mc.calls;
         const bool chg = replay_segment_mlp<NPL, SMEMW, SPEC, GROUP>(
@@ -179,10 +180,11 @@ __global__ void __launch_bounds__(kMlpThreads, 2) k_picard_mlp(KArgs a, MlpPolic
         return chg;
     };
     picard_passes<NPL, kWarps, decltype(replay)&, GROUP>(a, calls, replay);
-    if (lane_id() == 0 && (mc.rescored || mc.tc || mc.sat)) {
+    if (lane_id() == 0 && (mc.rescored || mc.tc || mc.sat || mc.near)) {
         atomicAdd(&a.ctrl->rescored, mc.rescored);
         atomicAdd(&a.ctrl->tc_rows, mc.tc);
         atomicAdd(&a.ctrl->sat_rows, mc.sat);
+        atomicAdd(&a.ctrl->near_ties, mc.near);
     }
 }
 
@@ -231,6 +233,7 @@ cudaError_t mlp_alloc(Instance* I) {
     if (!e) e = cudaMalloc((void**)&I->mlp_b2, sizeof(float) * (size_t)I->N);
     if (!e) e = cudaMalloc((void**)&I->mlp_Emax, sizeof(float) * ((size_t)I->R + kHidden));
     if (!e) e = cudaMalloc((void**)&I->mlp_bnd, sizeof(float) * 2);
+    if (!e) e = cudaMalloc((void**)&I->mlp_c2, sizeof(float) * (size_t)I->N);
     if (!e) e = cudaMalloc((void**)&I->mlp_sat, sizeof(float) * (size_t)I->R * I->N);
     return e;
 }
@@ -246,7 +249,7 @@ cudaError_t mlp_prepare(Instance* I, const pic_policy* pol, cudaStream_t st) {
     I->launches += 3;
     k_mlp_prefix<<<(n + 255) / 256, 256, 0, st>>>(m);
     float* C1 = I->mlp_Emax + I->R;  // scratch after the per-region values
-    k_mlp_consts<<<1, kHidden, 0, st>>>(I->N, pol->W1, pol->W2, pol->b2, C1, I->mlp_bnd);
+    k_mlp_consts<<<1, kHidden, 0, st>>>(I->N, pol->W1, pol->W2, pol->b2, C1, I->mlp_bnd, I->mlp_c2);
     k_mlp_emax<<<(I->R + 7) / 8, 256, 0, st>>>(I->R, I->mlp_P, C1, I->mlp_Emax);
     cudaError_t e = cudaGetLastError();
     if (e) return e;

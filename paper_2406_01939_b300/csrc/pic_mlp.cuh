@@ -10,13 +10,25 @@
 //   h_j = b1_j, then one fmaf per input: cost[r][n]/128 (n = 0..N-1), E[r][e]
 //         (e = 0..15), min(S_n, 32)/32 (n = 0..N-1), weights W1 rows in that
 //         input's position; h_j = max(h_j, 0);
-//   p_e = 0, then one fmaf per hidden unit j = e, e+8, ... with W2[j][n] (e = 0..7),
-//   s_n = b2_n + (((p_0 + p_1) + (p_2 + p_3)) + ((p_4 + p_5) + (p_6 + p_7))):
-//   eight independent chains keep the latency of one decision short.
+//   s_n = b2_n, then one fmaf per hidden unit j = 0, 1, ..., 255 with W2[j][n]
+//         (the reference order: one sequential chain per output).
 // Parameters are BF16 (exact in FP32).  The part of the h chain before the stock
 // inputs depends only on the region, so it is evaluated once per call into
 // P[r][j] (the same operations in the same order).  Argmax over stocked
 // warehouses, ties to the lowest index; a^phi when nothing is stocked.
+//
+// Layer 1 runs in the reference order.  Layer 2 is scored fast first: eight
+// partial chains over j = e mod 8 joined by a fixed tree (36 roundings per term
+// at most, against 256 in the reference chain), so that one decision's latency
+// stays short.  Both are FP32 evaluations of the same exact sum, hence
+//   |s_fast - s_ref| <= (gamma_36 + gamma_256) (|b2_n| + sum_j |W2[j][n]| h_j)
+//                    <= kScoreC (|b2_n| + hmax c2_n),
+// gamma_m = m u / (1 - m u), u = 2^-24, hmax = max_j h_j, c2_n = sum_j |W2[j][n]|
+// (rounded up).  The fast arg max stands when no other stocked warehouse can
+// overtake it within these bounds; otherwise (a near tie) the winner and every
+// warehouse within reach are re-scored in the reference order and the arg max
+// is taken over those exact scores.  Either way the decision is the
+// reference's.
 //
 // Gumbel: s_n + g_n with g_n = -log(-log u), u = ((w >> 9) + 1/2) 2^-23 from
 // Philox4x32-10 (Salmon et al., SC'11) with key = seed and counter = (t,
@@ -112,9 +124,11 @@ struct MlpPolicy {
     // bnd[1] = max_n |b2[n]|
     const float* __restrict__ Emax;
     const float* __restrict__ bnd;
+    // c2[n] = sum_j |W2[j][n]| rounded up (bound of the fast layer-2 order)
+    const float* __restrict__ c2;
     // [R][N] FP32 scores (before the Gumbel term) of the saturated state, where
-    // every warehouse holds at least 32 units (every stock feature is 1), computed
-    // by mlp_scores itself; null: evaluate every decision
+    // every warehouse holds at least 32 units (every stock feature is 1), in the
+    // reference order; null: evaluate every decision
     const float* __restrict__ sat;
     bool gumbel;
     unsigned long long seed;
@@ -123,10 +137,14 @@ struct MlpPolicy {
 
 // Counters of one warp's MLP decisions: evaluations, tile rows re-scored in
 // FP32, tile rows decided by the tensor-core scores, decisions taken from the
-// saturated-state table.
+// saturated-state table, near ties re-scored in the reference order.
 struct MlpCounts {
-    unsigned long long calls, rescored, tc, sat;
+    unsigned long long calls, rescored, tc, sat, near;
 };
+
+// gamma_36 + gamma_256 = 1.7405e-5, rounded up with room for the FP32
+// evaluation of the bound itself (a few roundings of relative 2^-24).
+constexpr float kScoreC = 1.75e-5f;
 
 // Packed weights read from shared memory (staged copy) or global memory.
 template <bool SMEMW>
@@ -171,14 +189,13 @@ __device__ __forceinline__ unsigned short bf16_bits(float x) {
     return (unsigned short)(__float_as_uint(x) >> 16);  // exact for BF16-representable x
 }
 
-// The FP32 scores (R12 order, before the Gumbel term) of the lane's warehouses
-// n = lane + 32 i with want[i], for stock row S (lane l holds warehouses
-// l + 32 i) in region r; fs/hs: per-warp shared scratch (N and H floats, hs
-// 16-byte aligned).
+// Layer 1 in the reference order for stock row S (lane l holds warehouses
+// l + 32 i) in region r: hs[j] = max(P[r][j] + stock chain, 0), every lane
+// holding units l + 32 u.  fs/hs: per-warp shared scratch (N and H floats, hs
+// 16-byte aligned).  Returns max_j hs[j] (warp-uniform).
 template <int NPL, bool SMEMW>
-__device__ __forceinline__ void mlp_scores(const MlpPolicy& p, const uint4* W1p, const uint4* W2p,
-                                           const int S[NPL], int r, const bool want[NPL],
-                                           float* fs, float* hs, float s_out[NPL]) {
+__device__ __forceinline__ float mlp_hidden(const MlpPolicy& p, const uint4* W1p, const int S[NPL],
+                                            int r, float* fs, float* hs) {
     const int lane = lane_id();
     const int N = p.N, H = p.H;
 #pragma unroll
@@ -194,9 +211,48 @@ __device__ __forceinline__ void mlp_scores(const MlpPolicy& p, const uint4* W1p,
 #pragma unroll 2
     for (int n = 0; n < N; ++n)
         fma8_bf16(acc, wld4<SMEMW>(W1p + n * 32 + lane), bf16_bits(fs[n]));
+    float hm = 0.f;
 #pragma unroll
-    for (int u = 0; u < kJ; ++u) hs[lane + 32 * u] = acc[u] > 0.0f ? acc[u] : 0.0f;
+    for (int u = 0; u < kJ; ++u) {
+        const float h = acc[u] > 0.0f ? acc[u] : 0.0f;
+        hs[lane + 32 * u] = h;
+        hm = fmaxf(hm, h);
+    }
     __syncwarp();
+    // h >= 0: the bit patterns order like the values
+    return __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(hm)));
+}
+
+// The reference-order score of warehouse n from the hidden layer hs: b2_n,
+// then one fmaf per hidden unit in increasing j.
+template <bool SMEMW>
+__device__ __forceinline__ float ref_score(const MlpPolicy& p, const uint4* W2p, const float* hs,
+                                           int n) {
+    const float4* h4 = reinterpret_cast<const float4*>(hs);
+    float s = __ldg(p.b2f + n);
+#pragma unroll 4
+    for (int q = 0; q < kHidden / 8; ++q) {
+        const uint4 w = wld4<SMEMW>(W2p + q * p.N + n);
+        const float4 ha = h4[2 * q], hb = h4[2 * q + 1];
+        s = fmaf(lo16(w.x), ha.x, s);
+        s = fmaf(hi16(w.x), ha.y, s);
+        s = fmaf(lo16(w.y), ha.z, s);
+        s = fmaf(hi16(w.y), ha.w, s);
+        s = fmaf(lo16(w.z), hb.x, s);
+        s = fmaf(hi16(w.z), hb.y, s);
+        s = fmaf(lo16(w.w), hb.z, s);
+        s = fmaf(hi16(w.w), hb.w, s);
+    }
+    return s;
+}
+
+// The fast layer-2 scores (eight chains and a fixed tree, before the Gumbel
+// term) of the lane's warehouses n = lane + 32 i with want[i], from hs.
+template <int NPL, bool SMEMW>
+__device__ __forceinline__ void fast_scores(const MlpPolicy& p, const uint4* W2p, const float* hs,
+                                            const bool want[NPL], float s_out[NPL]) {
+    const int lane = lane_id();
+    const int N = p.N;
     const float4* h4 = reinterpret_cast<const float4*>(hs);
 #pragma unroll
     for (int i = 0; i < NPL; ++i) {
@@ -218,45 +274,99 @@ __device__ __forceinline__ void mlp_scores(const MlpPolicy& p, const uint4* W1p,
             s_out[i] = __fadd_rn(__ldg(p.b2f + n), v);
         }
     }
-    __syncwarp();  // fs / hs reused by the next call
+}
+
+// Bound on |key_fast - key_ref| of warehouse n: the score bound, plus, with
+// Gumbel noise, the two roundings of s + g (relative 2^-24 each).
+__device__ __forceinline__ float key_bound(const MlpPolicy& p, int n, float hmax, float key) {
+    const float bs = kScoreC * fmaf(hmax, __ldg(p.c2 + n), fabsf(__ldg(p.b2f + n)));
+    return p.gumbel ? fmaf(bs, 1.0001f, ldexpf(fabsf(key), -22)) : bs;
 }
 
 // The decision from the scores s of the lane's warehouses: arg max over stocked
 // warehouses of s (+ Gumbel noise for time t), ties to the lowest index, a^phi
-// (-1) when nothing is stocked.  Warp-uniform.
-template <int NPL>
-__device__ __forceinline__ int mlp_pick(const MlpPolicy& p, const int S[NPL], const float s_in[NPL],
-                                        int t) {
+// (-1) when nothing is stocked.  exact: s are reference-order scores (the
+// saturated table).  Otherwise s are fast scores of the hidden layer in hs
+// (hmax its largest unit), and near ties are re-scored in the reference order
+// (counted in `near`, lane 0).  Warp-uniform.
+template <int NPL, bool SMEMW>
+__device__ __forceinline__ int mlp_pick(const MlpPolicy& p, const uint4* W2p, const int S[NPL],
+                                        const float s_in[NPL], int t, bool exact, float hmax,
+                                        const float* hs, unsigned long long& near) {
     const int lane = lane_id();
+    float key[NPL], g[NPL];
+    bool feas[NPL];
     unsigned best_key = 0;
     int best_n = INT_MAX;
     bool any = false;
 #pragma unroll
     for (int i = 0; i < NPL; ++i) {
         const int n = lane + 32 * i;
-        if (n < p.N && S[i] > 0) {
+        feas[i] = n < p.N && S[i] > 0;
+        g[i] = 0.f;
+        key[i] = 0.f;
+        if (feas[i]) {
             float s = s_in[i];
-            if (p.gumbel) s = __fadd_rn(s, gumbel1(p.seed, p.traj, t, n));
+            if (p.gumbel) {
+                g[i] = gumbel1(p.seed, p.traj, t, n);
+                s = __fadd_rn(s, g[i]);
+            }
+            key[i] = s;
             const unsigned kk = ord_key(s);
             if (!any || kk > best_key) { best_key = kk; best_n = n; any = true; }
         }
     }
     const unsigned kmax = __reduce_max_sync(kFull, any ? best_key : 0u);
     const bool stocked = __any_sync(kFull, any);
-    const int n = __reduce_min_sync(kFull, (any && best_key == kmax) ? best_n : INT_MAX);
-    return stocked ? n : -1;
+    const int nw = __reduce_min_sync(kFull, (any && best_key == kmax) ? best_n : INT_MAX);
+    if (!stocked) return -1;
+    if (exact) return nw;
+    // the winner's key and bound, then every stocked warehouse that could reach it
+    float kw_l = 0.f, bw_l = 0.f;
+#pragma unroll
+    for (int i = 0; i < NPL; ++i)
+        if (lane + 32 * i == nw) { kw_l = key[i]; bw_l = key_bound(p, nw, hmax, key[i]); }
+    const float kw = __shfl_sync(kFull, kw_l, nw & 31), bw = __shfl_sync(kFull, bw_l, nw & 31);
+    bool cand[NPL];
+    bool anyc = false;
+#pragma unroll
+    for (int i = 0; i < NPL; ++i) {
+        const int n = lane + 32 * i;
+        // key_n + B_n >= key_w - B_w, tested with directed roundings that never exclude
+        cand[i] = feas[i] && n != nw &&
+                  __fsub_rd(kw, __fadd_ru(key[i], key_bound(p, n, hmax, key[i]))) <= bw;
+        anyc |= cand[i];
+    }
+    if (!__any_sync(kFull, anyc)) return nw;
+    if (lane == 0) ++near;
+    best_key = 0;
+    best_n = INT_MAX;
+    any = false;
+#pragma unroll
+    for (int i = 0; i < NPL; ++i) {
+        const int n = lane + 32 * i;
+        if (cand[i] || n == nw) {
+            float s = ref_score<SMEMW>(p, W2p, hs, n);
+            if (p.gumbel) s = __fadd_rn(s, g[i]);
+            const unsigned kk = ord_key(s);
+            if (!any || kk > best_key) { best_key = kk; best_n = n; any = true; }
+        }
+    }
+    const unsigned km2 = __reduce_max_sync(kFull, any ? best_key : 0u);
+    return __reduce_min_sync(kFull, (any && best_key == km2) ? best_n : INT_MAX);
 }
 
 // The warp evaluates the policy for stock row S (lane l holds warehouses l + 32 i)
 // of an order in region r at time t; fs/hs: per-warp shared scratch (N and H
 // floats, hs 16-byte aligned).  In the saturated state (every warehouse at 32
-// units or more) the scores are row r of p.sat, which mlp_scores wrote for that
-// very state, so the decision is the same.  nsat counts those decisions (lane
-// 0).  Returns the action (warp-uniform).
+// units or more) the scores are row r of p.sat, which holds that state's
+// reference-order scores, so the decision is the same.  Counts table decisions
+// (cnt.sat) and near ties (cnt.near) on lane 0.  Returns the action
+// (warp-uniform).
 template <int NPL, bool SMEMW>
 __device__ __forceinline__ int mlp_decide(const MlpPolicy& p, const uint4* W1p, const uint4* W2p,
                                           const int S[NPL], int r, int t, float* fs, float* hs,
-                                          unsigned long long& nsat) {
+                                          MlpCounts& cnt) {
     const int lane = lane_id();
     float s[NPL];
     bool sat = p.sat != nullptr;
@@ -269,37 +379,49 @@ __device__ __forceinline__ int mlp_decide(const MlpPolicy& p, const uint4* W1p, 
             const int n = lane + 32 * i;
             s[i] = n < p.N ? __ldg(p.sat + (size_t)r * p.N + n) : 0.0f;
         }
-        if (lane == 0) ++nsat;
-    } else {
-        bool want[NPL];
-#pragma unroll
-        for (int i = 0; i < NPL; ++i) want[i] = lane + 32 * i < p.N && S[i] > 0;
-        mlp_scores<NPL, SMEMW>(p, W1p, W2p, S, r, want, fs, hs, s);
+        if (lane == 0) ++cnt.sat;
+        return mlp_pick<NPL, SMEMW>(p, W2p, S, s, t, true, 0.f, hs, cnt.near);
     }
-    return mlp_pick<NPL>(p, S, s, t);
+    bool want[NPL];
+#pragma unroll
+    for (int i = 0; i < NPL; ++i) want[i] = lane + 32 * i < p.N && S[i] > 0;
+    const float hmax = mlp_hidden<NPL, SMEMW>(p, W1p, S, r, fs, hs);
+    fast_scores<NPL, SMEMW>(p, W2p, hs, want, s);
+    const int act = mlp_pick<NPL, SMEMW>(p, W2p, S, s, t, false, hmax, hs, cnt.near);
+    __syncwarp();  // fs / hs reused by the next call
+    return act;
 }
 
 // ---------------------------------------------------------------- four warps per decision
 // A group of four warps (128 threads) shares each decision, which shortens the
 // latency of one decision (the critical path of a pass whose work is a few long
-// runs).  The operations and their order are mlp_scores' exactly:
+// runs).  The operations and their order are mlp_decide's exactly:
 //   layer 1: thread (warp g, lane l) runs the 64-step chains of hidden units
 //            l + 32 g and l + 32 g + 128 (units u = g and u = g + 4 of lane l);
-//   layer 2: thread (g, l) owns output n = l + 32 (g & 1) and the four chains
-//            p_e, e = 4 (g >> 1) .. 4 (g >> 1) + 3, and forms their half of the
-//            fixed tree, (p_0+p_1)+(p_2+p_3) or (p_4+p_5)+(p_6+p_7);
-//   warps 0 and 1 add the halves, add b2 (and the Gumbel term) and take their
-//   arg max; every warp combines the two.
+//   layer 2 (fast order): thread (g, l) owns output n = l + 32 (g & 1) and the
+//            four chains p_e, e = 4 (g >> 1) .. 4 (g >> 1) + 3, and forms their
+//            half of the fixed tree, (p_0+p_1)+(p_2+p_3) or (p_4+p_5)+(p_6+p_7);
+//   warps 0 and 1 add the halves, add b2 (and the Gumbel term), take their arg
+//   max and publish it with its bound and the largest reach (key + bound) of
+//   their other warehouses; every warp combines the two.  On a near tie every
+//   warp re-scores the same candidates in the reference order (ref_score).
 // N <= 64.  Each warp keeps its own copy of the stock row and its own feature
-// scratch; the group shares hs (256 floats), ht (2 x 64) and am (2 entries),
-// and synchronises with one named barrier (id bar, 128 threads) three times.
+// scratch; the group shares hs (256 floats), ht (2 x 64) and am (4 entries),
+// and synchronises with one named barrier (id bar, 128 threads) three times
+// (four after a near tie).
 struct Group {
     int g;        // warp index in the group (0..3)
     int bar;      // named barrier id
     float* hs;    // [256] hidden activations
     float* ht;    // [2][64] halves of the layer-2 tree
-    uint4* am;    // [2] per-warp arg max: key, index, any
+    uint4* am;    // [4]: per warp w = 0, 1: am[w] = {key order, index, any, hmax},
+                  //      am[2 + w] = {key, bound, reach of the others, reach of all} (FP32 bits)
 };
+
+// Inverse of ord_key.
+__device__ __forceinline__ float ord_inv(unsigned k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
 
 __device__ __forceinline__ void group_sync(int bar) {
     asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(128) : "memory");
@@ -326,8 +448,7 @@ __device__ __forceinline__ uint2 wld2(const uint2* p) {
 template <int NPL, bool SMEMW>
 __device__ __forceinline__ int mlp_decide_group(const MlpPolicy& p, const uint4* W1p,
                                                 const uint4* W2p, const int S[NPL], int r, int t,
-                                                float* fs, const Group& G,
-                                                unsigned long long& nsat) {
+                                                float* fs, const Group& G, MlpCounts& cnt) {
     static_assert(NPL <= 2, "four-warp decisions need N <= 64");
     const int lane = lane_id();
     const int N = p.N, g = G.g;
@@ -342,8 +463,8 @@ __device__ __forceinline__ int mlp_decide_group(const MlpPolicy& p, const uint4*
             const int n = lane + 32 * i;
             s[i] = n < N ? __ldg(p.sat + (size_t)r * N + n) : 0.0f;
         }
-        if (lane == 0 && g == 0) ++nsat;
-        return mlp_pick<NPL>(p, S, s, t);
+        if (lane == 0 && g == 0) ++cnt.sat;
+        return mlp_pick<NPL, SMEMW>(p, W2p, S, s, t, true, 0.f, G.hs, cnt.near);
     }
 #pragma unroll
     for (int i = 0; i < NPL; ++i) {
@@ -385,27 +506,77 @@ __device__ __forceinline__ int mlp_decide_group(const MlpPolicy& p, const uint4*
     }
     group_sync(G.bar);
     if (hf == 0) {  // warps 0 and 1: outputs 0..31 and 32..63
+        float hm = 0.f;
+#pragma unroll
+        for (int u = 0; u < kHidden / 32; ++u) hm = fmaxf(hm, G.hs[lane + 32 * u]);
+        const float hmax = __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(hm)));
         const int Sn = (NPL > 1 && (g & 1)) ? S[NPL - 1] : S[0];
         unsigned key = 0;
+        float kf = 0.f, kb = 0.f;
         bool any = false;
         if (n < N && Sn > 0) {
             const float v = __fadd_rn(G.ht[n], G.ht[64 + n]);
             float s = __fadd_rn(__ldg(p.b2f + n), v);
             if (p.gumbel) s = __fadd_rn(s, gumbel1(p.seed, p.traj, t, n));
+            kf = s;
+            kb = key_bound(p, n, hmax, s);
             key = ord_key(s);
             any = true;
         }
         const unsigned kmax = __reduce_max_sync(kFull, any ? key : 0u);
         const bool wany = __any_sync(kFull, any);
         const int nmin = __reduce_min_sync(kFull, (any && key == kmax) ? n : INT_MAX);
-        if (lane == 0) G.am[g] = make_uint4(kmax, (unsigned)nmin, wany ? 1u : 0u, 0u);
+        const int wl = nmin & 31;
+        const float kw = __shfl_sync(kFull, kf, wl), bw = __shfl_sync(kFull, kb, wl);
+        // reach = key + bound (rounded up) of this warp's other stocked warehouses, and of all
+        const float reach = any ? __fadd_ru(kf, kb) : -INFINITY;
+        const float rex = ord_inv(__reduce_max_sync(kFull, ord_key(lane != wl ? reach : -INFINITY)));
+        const float rall = ord_inv(__reduce_max_sync(kFull, ord_key(reach)));
+        if (lane == 0) {
+            G.am[g] = make_uint4(kmax, (unsigned)nmin, wany ? 1u : 0u, __float_as_uint(hmax));
+            G.am[2 + g] = make_uint4(__float_as_uint(kw), __float_as_uint(bw), __float_as_uint(rex),
+                                     __float_as_uint(rall));
+        }
     }
     group_sync(G.bar);
     const uint4 m0 = G.am[0], m1 = G.am[1];
     if (!m0.z && !m1.z) return -1;
-    if (!m0.z) return (int)m1.y;
-    if (!m1.z) return (int)m0.y;
-    return m1.x > m0.x ? (int)m1.y : (int)m0.y;  // ties to the lower index (warp 0's)
+    // the winner: the larger key, ties to the lower index (warp 0's)
+    const int wi = !m0.z ? 1 : (!m1.z ? 0 : (m1.x > m0.x ? 1 : 0));
+    const int nw = (int)(wi ? m1.y : m0.y);
+    const uint4 fw = G.am[2 + wi], fo = G.am[3 - wi];
+    const bool oany = (wi ? m0.z : m1.z) != 0;
+    const float kw = __uint_as_float(fw.x), bw = __uint_as_float(fw.y);
+    float reach = __uint_as_float(fw.z);
+    if (oany) reach = fmaxf(reach, __uint_as_float(fo.w));
+    if (!(__fsub_rd(kw, reach) <= bw)) return nw;  // nothing else can reach the winner
+    // near tie: every warp scores the same candidates in the reference order
+    const float hmax = __uint_as_float(m0.w);
+    unsigned best_key = 0;
+    int best_n = INT_MAX;
+    bool any = false;
+#pragma unroll
+    for (int i = 0; i < NPL; ++i) {
+        const int nn = lane + 32 * i;
+        if (nn < N && S[i] > 0) {
+            const float gn = p.gumbel ? gumbel1(p.seed, p.traj, t, nn) : 0.f;
+            float kf = __fadd_rn(__ldg(p.b2f + nn), __fadd_rn(G.ht[nn], G.ht[64 + nn]));
+            if (p.gumbel) kf = __fadd_rn(kf, gn);
+            const bool cand =
+                nn == nw || __fsub_rd(kw, __fadd_ru(kf, key_bound(p, nn, hmax, kf))) <= bw;
+            if (cand) {
+                float sr = ref_score<SMEMW>(p, W2p, G.hs, nn);
+                if (p.gumbel) sr = __fadd_rn(sr, gn);
+                const unsigned kk = ord_key(sr);
+                if (!any || kk > best_key) { best_key = kk; best_n = nn; any = true; }
+            }
+        }
+    }
+    const unsigned km = __reduce_max_sync(kFull, any ? best_key : 0u);
+    const int res = __reduce_min_sync(kFull, (any && best_key == km) ? best_n : INT_MAX);
+    if (lane == 0 && g == 0) ++cnt.near;
+    group_sync(G.bar);  // hs / ht are read: the next decision may overwrite them
+    return res;
 }
 
 // ---------------------------------------------------------------- speculative tensor-core tiles
@@ -415,13 +586,18 @@ __device__ __forceinline__ int mlp_decide_group(const MlpPolicy& p, const uint4*
 // the current state: c = W1s^T f (FP32, shared by the rows), h_t = max(P[r_t] +
 // c, 0) rounded to BF16, and s_t = h_t W2 (+ b2) and u_t = h_t |W2| with
 // mma.sync m16n8k16 (BF16 inputs, FP32 accumulation).  A row's decision is the
-// FP32 scorer's exactly when its top-2 margin among stocked warehouses exceeds
-// max(1e-3, 2 B) with B a bound on |s_tc - s_fp32| for that row:
-//   |z_tc - z_fp32| <= e1 = 2^-22 (N + 2) Emax[r]      (two FP32 chains of N terms),
+// reference order's exactly when its top-2 margin among stocked warehouses
+// exceeds max(1e-3, 2 B) with B a bound on |s_tc - s_ref| for that row:
+//   |z_tc - z_ref| <= e1 = 2^-22 (N + 2) Emax[r]       (two FP32 chains of N terms),
 //   B = 2.1e-3 max_n u_n + 1.01 e1 max_n sum_j |W2_jn| + 1.6e-5 max|b2| + 2^-21 |key|
-// (BF16 rounding of h, relative 2^-9; the two 256-term FP32 sums; the key's own
-// roundings).  Other rows are re-scored by mlp_decide.  Returns, on lane l < L,
-// the action of row l (-2: re-score), and the lanes' state is unchanged.
+// The terms cover, in order: the BF16 rounding of h (relative 2^-9) together
+// with the two 256-term FP32 sums, the tensor-core accumulation and the
+// reference chain from b2, each charged gamma_256 = 1.53e-5 relative (the
+// first coefficient exceeds 2^-9 + 2 gamma_256 with the relative growth from
+// h to its BF16 value); e1 propagated through layer 2; b2's own roundings in
+// the reference chain; the roundings of the key.  Other rows are re-scored by
+// mlp_decide.  Returns, on lane l < L, the action of row l (-2: re-score), and
+// the lanes' state is unchanged.
 constexpr int kTile = 16;
 constexpr int kSpecMin = 8;          // shortest run remainder scored by a tile
 constexpr float kTieMargin = 1e-3f;  // re-score rows whose top-2 margin is below this
@@ -611,7 +787,7 @@ __device__ __forceinline__ void seq_mlp_body(int T, int N, const int32_t* __rest
                                              const int32_t* __restrict__ reg, int32_t* xw,
                                              int8_t* __restrict__ act_t, const MlpPolicy& p,
                                              const uint4* W1p, const uint4* W2p, float* fs,
-                                             float* hs, unsigned long long& nsat,
+                                             float* hs, MlpCounts& cnt,
                                              const Group* G = nullptr) {
     const int lane = lane_id();
     const bool lead = GROUP == 1 || G->g == 0;
@@ -626,12 +802,12 @@ __device__ __forceinline__ void seq_mlp_body(int T, int N, const int32_t* __rest
         }
         int act;
         if constexpr (GROUP > 1) {
-            act = mlp_decide_group<NPL, SMEMW>(p, W1p, W2p, S, r, t, fs, *G, nsat);
+            act = mlp_decide_group<NPL, SMEMW>(p, W1p, W2p, S, r, t, fs, *G, cnt);
             // every warp has read this order's stock row before it is decremented (a
             // table decision has no other barrier)
             group_sync(G->bar);
         } else {
-            act = mlp_decide<NPL, SMEMW>(p, W1p, W2p, S, r, t, fs, hs, nsat);
+            act = mlp_decide<NPL, SMEMW>(p, W1p, W2p, S, r, t, fs, hs, cnt);
         }
 #pragma unroll
         for (int i = 0; i < NPL; ++i)
@@ -679,7 +855,8 @@ __device__ bool replay_segment_mlp(const KArgs& a, const MlpPolicy& p, const uin
     const int whi = a.run_chunk ? ld_volatile(&a.ctrl->win_hi) : INT_MAX;
     const int wprev = a.run_chunk ? ld_volatile(&a.ctrl->win_hi_prev) : INT_MAX;
     bool eval = run_evaluated(a, whi, wprev, r, m.j0 > fcp);
-    unsigned long long evals = 0, resc = 0, tcr = 0, nsat = 0;
+    unsigned long long evals = 0, resc = 0, tcr = 0;
+    MlpCounts dc{0, 0, 0, 0, 0};  // table decisions and near ties of mlp_decide
     int first_chg = INT_MAX;
     int spec_act = -2, spec_base = 0, spec_left = 0;  // current tile (rows left)
     for (int base = m.j0; base < m.jend; base += 32) {
@@ -735,9 +912,9 @@ __device__ bool replay_segment_mlp(const KArgs& a, const MlpPolicy& p, const uin
                 }
                 if (sa < -1) {
                     if constexpr (GROUP > 1)
-                        act = mlp_decide_group<NPL, SMEMW>(p, W1p, W2p, S, rr, tt, fs, *G, nsat);
+                        act = mlp_decide_group<NPL, SMEMW>(p, W1p, W2p, S, rr, tt, fs, *G, dc);
                     else
-                        act = mlp_decide<NPL, SMEMW>(p, W1p, W2p, S, rr, tt, fs, hs, nsat);
+                        act = mlp_decide<NPL, SMEMW>(p, W1p, W2p, S, rr, tt, fs, hs, dc);
                     resc += sa == -2;
                 } else {
                     act = sa;
@@ -786,7 +963,8 @@ __device__ bool replay_segment_mlp(const KArgs& a, const MlpPolicy& p, const uin
         cnt_out.calls += evals;
         cnt_out.rescored += resc;
         cnt_out.tc += tcr;
-        cnt_out.sat += nsat;
+        cnt_out.sat += dc.sat;
+        cnt_out.near += dc.near;
     }
     return first_chg != INT_MAX;
 }
@@ -802,6 +980,7 @@ inline MlpPolicy make_policy_view(const Instance* I, const pic_policy* pol, int 
     p.b2f = I->mlp_b2;
     p.Emax = I->mlp_Emax;
     p.bnd = I->mlp_bnd;
+    p.c2 = I->mlp_c2;
     p.sat = (flags & PIC_FLAG_NO_SAT) ? nullptr : I->mlp_sat;
     p.gumbel = pol->kind == PIC_POLICY_GUMBEL;
     p.seed = pol->seed;

@@ -21,13 +21,10 @@
 // a pass evaluates only steps before w + max_steps.  The loop ends after the
 // first pass that changed no cached action with the window covering the
 // horizon.  Processors are interleaved over the CTAs' groups of 32 lanes.
-// k_owmr_picard_cl is the same loop with W2 resident across 4-CTA clusters.
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <new>
-
-#include <cooperative_groups.h>
 
 #include "pic_device.cuh"
 #include "pic_owmr.h"
@@ -71,7 +68,7 @@ struct OwCtrl {
     int changed[3];
     int fct[3];  // first changed step of the pass (INT_MAX: none)
     long long lost[3], shipped[3], R[3];
-    unsigned long long evals, rounds;
+    unsigned long long evals, rounds, near;
 };
 
 struct OwArgs {
@@ -212,7 +209,8 @@ constexpr int kMaxBuf = 2;
 static_assert(kMaxBuf <= kMaxBufSlots, "one mbarrier per W2 buffer");
 
 struct NetCtx {
-    float *h1s, *zpart, *W1s, *b1s, *b2s, *w3s;
+    float *h1s, *W1s, *b1s, *b2s, *w3s;
+    float2* zpart;  // [32][H/8] per row and 8-unit group: {sum w3 h2, sum |w3| h2}
     uint16_t* w2buf;  // [nbuf][kKc][H]
     unsigned long long* full;
     int nbuf;
@@ -360,13 +358,42 @@ __device__ void net_layer2(const NetCtx& nc, const uint16_t* W2, int H, int nrow
     __syncthreads();
 }
 
+// Layer 3 and the retailer rule for one row (h2: its H hidden values; zp: its
+// H/8 group partials).  The fast output adds the partials in order,
+// z = b3 + p_0 + p_1 + ... (each term rounded at most 8 + H/8 times, against H
+// times in the reference chain z = b3, then one fma per unit), so
+//   |z_fast - z_ref| <= (gamma_{8+H/8} + gamma_H) (|b3| + sum_j |w3_j| h2_j).
+// q = clamp(floor(base + z), 0, room) is taken from z_fast when every z in
+// that interval gives the same q (bounds rounded outwards); otherwise z is
+// evaluated in the reference order.  Returns q; near: set on a re-score.
+__device__ __forceinline__ int layer3_q(const NetCtx& nc, float b3, int H, const float* h2,
+                                        const float2* zp, int base, int room, bool& near) {
+    float z = b3, za = fabsf(b3);
+    for (int g = 0; g < H / 8; ++g) {
+        z = __fadd_rn(z, zp[g].x);
+        za = __fadd_ru(za, zp[g].y);
+    }
+    // gamma_{8 + H/8} + gamma_H, with room for the partials' own roundings
+    const float c = (float)(8 + H / 8 + H) * 5.9605e-8f * 1.002f;
+    const float B = __fmul_ru(c, za);
+    const float lo = floorf(__fadd_rd((float)base, __fsub_rd(z, B)));
+    const float hi = floorf(__fadd_ru((float)base, __fadd_ru(z, B)));
+    const float cl_lo = fminf(fmaxf(lo, 0.f), (float)room), cl_hi = fminf(fmaxf(hi, 0.f), (float)room);
+    near = cl_lo != cl_hi;
+    if (near) {
+        z = b3;
+        for (int j = 0; j < H; ++j) z = fmaf(nc.w3s[j], h2[j], z);
+    }
+    return q_of(base, room, z);
+}
+
 // One batched round of the network for the lanes flagged in `rows` (bit b =
 // lane b, features in sm.feat_*).  The pending lanes are compacted; layer 1
 // gives h1s [k][row] for nr rows, the smallest of 2, 4, 8, 16, 32 that holds
 // them (ONE: a single row); layer 2 runs nr <= 8 rows x 2 columns per thread,
-// or 8 rows x 4 / 8 columns for 16 / 32 rows; then p_g per (row, g) and
-// z = b3 + p_0 + p_1 + ... per row.  Every output follows the order
-// documented in pic_owmr.h.
+// or 8 rows x 4 / 8 columns for 16 / 32 rows; then the partials p_g (and their
+// absolute counterparts) per (row, g) and layer3_q per row.  Every output
+// follows the order documented in pic_owmr.h.
 template <bool ONE>
 __device__ void net_round(const OwArgs& a, OwSmem& sm, const NetCtx& nc, unsigned rows,
                           unsigned& wuse, unsigned long long deadline) {
@@ -407,30 +434,34 @@ __device__ void net_round(const OwArgs& a, OwSmem& sm, const NetCtx& nc, unsigne
     for (int idx = threadIdx.x; idx < m * ncg; idx += blockDim.x) {
         const int i = idx / ncg, g = idx - i * ncg;
         const float* h2 = nc.h1s + (size_t)i * H + 8 * g;
-        float p = 0.f;
+        float p = 0.f, pa = 0.f;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) p = fmaf(nc.w3s[8 * g + c], h2[c], p);
-        nc.zpart[i * ncg + g] = p;
+        for (int c = 0; c < 8; ++c) {
+            p = fmaf(nc.w3s[8 * g + c], h2[c], p);
+            pa = fmaf(fabsf(nc.w3s[8 * g + c]), h2[c], pa);
+        }
+        nc.zpart[i * ncg + g] = make_float2(p, pa);
     }
     __syncthreads();
     if ((int)threadIdx.x < m) {
         const int b = sm.rowidx[threadIdx.x];
-        float z = bf1(a.b3[0]);
-        for (int g = 0; g < ncg; ++g) z = __fadd_rn(z, nc.zpart[threadIdx.x * ncg + g]);
-        sm.qout[b] = q_of(sm.feat_base[b], sm.feat_room[b], z);
+        bool near = false;
+        sm.qout[b] = layer3_q(nc, bf1(a.b3[0]), H, nc.h1s + (size_t)threadIdx.x * H,
+                              nc.zpart + threadIdx.x * ncg, sm.feat_base[b], sm.feat_room[b], near);
+        if (near) atomicAdd(&a.oc->near, 1ull);
     }
     __syncthreads();
 }
 
 // Carve the network's shared memory after OwSmem: h1s [H][32] (h2 [32][H]
-// later), zpart [32][H/8], W1s [3][H], b1s, b2s, w3s [H], W2 buffers; stage
-// the small weights and initialise the mbarriers.
+// later), zpart [32][H/8] (float2), W1s [3][H], b1s, b2s, w3s [H], W2 buffers;
+// stage the small weights and initialise the mbarriers.
 __device__ NetCtx net_setup(const OwArgs& a, unsigned char* smem_raw, OwSmem& sm) {
     NetCtx nc;
     const int H = a.H;
     nc.h1s = reinterpret_cast<float*>(smem_raw + sizeof(OwSmem) + xs_bytes(a.xs_len));
-    nc.zpart = nc.h1s + H * kLanes;
-    nc.W1s = nc.zpart + kLanes * (H >> 3);
+    nc.zpart = reinterpret_cast<float2*>(nc.h1s + H * kLanes);
+    nc.W1s = reinterpret_cast<float*>(nc.zpart + kLanes * (H >> 3));
     nc.b1s = nc.W1s + 3 * H;
     nc.b2s = nc.b1s + H;
     nc.w3s = nc.b2s + H;
@@ -454,7 +485,7 @@ __device__ NetCtx net_setup(const OwArgs& a, unsigned char* smem_raw, OwSmem& sm
 }
 
 size_t net_fixed_smem(int H) {
-    return sizeof(float) * ((size_t)H * kLanes + (size_t)kLanes * (H / 8) + 6 * (size_t)H);
+    return sizeof(float) * ((size_t)H * kLanes + 2 * (size_t)kLanes * (H / 8) + 6 * (size_t)H);
 }
 
 // Phases A and B of pass `pass`: tile summaries of the cache, a grid barrier,
@@ -758,387 +789,6 @@ __global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard(OwArgs a) {
         }
         w = changed ? ld_volatile(&oc->fct[slot]) : whi;
     }
-}
-
-// ------------------------------------------------------------------ cluster kernel
-// The same pass loop with the network's W2 resident in distributed shared
-// memory: a cluster of kClSize CTAs keeps W2 split by columns (CTA rank r holds
-// columns [r H/4, (r+1) H/4), H^2/4 BF16), so no round streams W2.  Rounds are
-// cluster-wide: each CTA contributes up to kClRows pending calls, writes their
-// h1 rows into every CTA's pooled h1 [H][32] (slot 8 r + i), every CTA computes
-// its column slice for all pooled rows and sends the layer-3 partials of its
-// 8-column groups to the rows' owners, which add p_0 + p_1 + ... in order.
-// Between rounds a CTA walks (chunk staging and walks are CTA-local); a CTA
-// with nothing to evaluate still joins the rounds until every CTA of its
-// cluster has finished the pass.  Decisions that end loops are taken from
-// data every CTA of the cluster reads after the same cluster barrier.
-namespace cg = cooperative_groups;
-constexpr int kClSize = 4;
-constexpr int kClRows = 8;
-constexpr int kClCh = 16;
-
-struct __align__(16) OwSmemCl {
-    int4 rec[kClCh][kLanes];
-    int4 pre[kClCh][kLanes];
-    int2 memo[kClCh][kLanes];
-    Mono ws[kOwThreads / 32 + 1];
-    int feat_y[kLanes], feat_d[kLanes], feat_e[kLanes], feat_base[kLanes], feat_room[kLanes];
-    int qout[kLanes];
-    int rowidx[kClRows];
-    int pend_any, pend_rows, all_done, served, m;
-    int cnt[kClSize], fin[kClSize], okf[kClSize];  // written by the cluster's CTAs
-    float zpool[kClRows][kMaxH / 8];               // p_g of this CTA's served rows
-    float b2s[kMaxH / kClSize], w3s[kMaxH / kClSize];
-    float W1s[3 * kMaxH], b1s[kMaxH];
-};
-
-size_t cl_smem(int H, int xs_len) {
-    return sizeof(OwSmemCl) + xs_bytes(xs_len) + sizeof(float) * (size_t)H * kLanes +
-           (size_t)H * (H / kClSize) * 2;
-}
-
-// One cluster round.  `rows`: this CTA's parked lanes; `fin`: this CTA has no
-// more steps in this pass.  Serves up to kClRows of them (sm.served), leaves
-// q in sm.qout.  Returns true when every CTA of the cluster is finished and
-// none had a call to make (then nothing was computed).
-__device__ bool cl_round(const OwArgs& a, OwSmemCl& sm, float* h1pool, const uint16_t* w2s,
-                         unsigned rank, unsigned rows, bool fin) {
-    cg::cluster_group cl = cg::this_cluster();
-    const int H = a.H, tid = threadIdx.x, cols = H / kClSize;
-    if (tid == 0) {
-        unsigned r = rows, served = 0;
-        int m = 0;
-        while (r && m < kClRows) {
-            const int b = __ffs(r) - 1;
-            sm.rowidx[m++] = b;
-            served |= 1u << b;
-            r &= r - 1;
-        }
-        sm.served = (int)served;
-        sm.m = m;
-    }
-    __syncthreads();
-    const int m = sm.m;
-    // layer 1 of the served rows, into every CTA's pool at slots 8 rank + i
-    for (int idx = tid; idx < H * kClRows; idx += kOwThreads) {
-        const int k = idx >> 3, i = idx & 7;
-        float v = 0.f;
-        if (i < m) {
-            const int b = sm.rowidx[i];
-            float acc = fmaf(sm.W1s[k], (float)sm.feat_y[b], sm.b1s[k]);
-            acc = fmaf(sm.W1s[H + k], (float)sm.feat_d[b], acc);
-            acc = fmaf(sm.W1s[2 * H + k], (float)sm.feat_e[b] * 0.000244140625f, acc);
-            v = acc > 0.f ? acc : 0.f;
-        }
-#pragma unroll
-        for (int d = 0; d < kClSize; ++d) cl.map_shared_rank(h1pool, d)[k * kLanes + 8 * rank + i] = v;
-    }
-    if (tid < kClSize) {
-        cl.map_shared_rank(sm.cnt, tid)[rank] = m;
-        cl.map_shared_rank(sm.fin, tid)[rank] = (fin && m == 0) ? 1 : 0;
-    }
-    cl.sync();  // pooled rows and flags are in place
-    int cnt[kClSize], any = 0, all_fin = 1;
-#pragma unroll
-    for (int j = 0; j < kClSize; ++j) {
-        cnt[j] = sm.cnt[j];
-        any |= cnt[j];
-        all_fin &= sm.fin[j];
-    }
-    if (!any && all_fin) return true;
-    // layer 2 for this CTA's column slice: source CTA rg's 8 rows x 2 columns per thread
-    const int tpr = cols / 2, rg = tid / 64, cp = tid & 63;
-    const bool active = cp < tpr && cnt[rg] > 0;
-    float acc[8][2];
-    if (active) {
-        const float bb0 = sm.b2s[2 * cp], bb1 = sm.b2s[2 * cp + 1];
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            acc[r][0] = bb0;
-            acc[r][1] = bb1;
-        }
-        const float* hb = h1pool + 8 * rg;
-#pragma unroll 4
-        for (int k = 0; k < H; ++k) {
-            const unsigned w = *reinterpret_cast<const unsigned*>(w2s + (size_t)k * cols + 2 * cp);
-            const float w0 = bf_lo(w), w1 = bf_hi(w);
-            const float4 h0 = *reinterpret_cast<const float4*>(hb + k * kLanes);
-            const float4 h1 = *reinterpret_cast<const float4*>(hb + k * kLanes + 4);
-            fma2(acc[0][0], acc[1][0], w0, w0, h0.x, h0.y);
-            fma2(acc[2][0], acc[3][0], w0, w0, h0.z, h0.w);
-            fma2(acc[4][0], acc[5][0], w0, w0, h1.x, h1.y);
-            fma2(acc[6][0], acc[7][0], w0, w0, h1.z, h1.w);
-            fma2(acc[0][1], acc[1][1], w1, w1, h0.x, h0.y);
-            fma2(acc[2][1], acc[3][1], w1, w1, h0.z, h0.w);
-            fma2(acc[4][1], acc[5][1], w1, w1, h1.x, h1.y);
-            fma2(acc[6][1], acc[7][1], w1, w1, h1.z, h1.w);
-        }
-    }
-    __syncthreads();  // the pool is read; it now holds h2 [32][cols]
-    if (active) {
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            h1pool[(8 * rg + r) * cols + 2 * cp] = acc[r][0] > 0.f ? acc[r][0] : 0.f;
-            h1pool[(8 * rg + r) * cols + 2 * cp + 1] = acc[r][1] > 0.f ? acc[r][1] : 0.f;
-        }
-    }
-    __syncthreads();
-    // layer-3 partials of this slice's 8-column groups, sent to the rows' owners
-    const int ng = cols / 8;
-    for (int idx = tid; idx < kLanes * ng; idx += kOwThreads) {
-        const int slot = idx / ng, gl = idx - slot * ng, owner = slot >> 3, i = slot & 7;
-        if (i < cnt[owner]) {
-            const float* h2 = h1pool + slot * cols + 8 * gl;
-            float p = 0.f;
-#pragma unroll
-            for (int c = 0; c < 8; ++c) p = fmaf(sm.w3s[8 * gl + c], h2[c], p);
-            cl.map_shared_rank(&sm.zpool[0][0], owner)[i * (kMaxH / 8) + ng * rank + gl] = p;
-        }
-    }
-    cl.sync();  // partials delivered; the pools may be refilled from here on
-    if (tid < m) {
-        const int b = sm.rowidx[tid];
-        float z = bf1(a.b3[0]);
-        for (int g = 0; g < H / 8; ++g) z = __fadd_rn(z, sm.zpool[tid][g]);
-        sm.qout[b] = q_of(sm.feat_base[b], sm.feat_room[b], z);
-    }
-    __syncthreads();
-    return false;
-}
-
-// AND of `ok` over the cluster (every CTA gets the same answer).
-__device__ bool cl_agree(OwSmemCl& sm, unsigned rank, bool ok) {
-    cg::cluster_group cl = cg::this_cluster();
-    if (threadIdx.x < kClSize) cl.map_shared_rank(sm.okf, threadIdx.x)[rank] = ok ? 1 : 0;
-    cl.sync();
-    int all = 1;
-#pragma unroll
-    for (int j = 0; j < kClSize; ++j) all &= sm.okf[j];
-    cl.sync();  // okf may be rewritten after this
-    return all != 0;
-}
-
-__global__ void __launch_bounds__(kOwThreads, 1) k_owmr_picard_cl(OwArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    OwSmemCl& sm = *reinterpret_cast<OwSmemCl*>(smem_raw);
-    int* xs = reinterpret_cast<int*>(smem_raw + sizeof(OwSmemCl));
-    float* h1pool = reinterpret_cast<float*>(smem_raw + sizeof(OwSmemCl) + xs_bytes(a.xs_len));
-    uint16_t* w2s = reinterpret_cast<uint16_t*>(h1pool + a.H * kLanes);  // [H][H/4]
-    cg::cluster_group cl = cg::this_cluster();
-    const unsigned rank = cl.block_rank();
-    OwCtrl* oc = a.oc;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, H = a.H, cols = H / kClSize;
-    const unsigned long long deadline = globaltimer_ns() + (unsigned long long)a.timeout_ns;
-    // resident weights: the W2 column slice, the slice of b2 and w3, layer 1
-    for (int i = tid; i < H * cols / 8; i += kOwThreads) {
-        const int k = i / (cols / 8), c8 = i - k * (cols / 8);
-        reinterpret_cast<uint4*>(w2s)[i] =
-            reinterpret_cast<const uint4*>(a.W2 + (size_t)k * H + rank * cols)[c8];
-    }
-    for (int i = tid; i < H; i += kOwThreads) {
-        sm.W1s[i] = bf1(a.W1[i]);
-        sm.W1s[H + i] = bf1(a.W1[H + i]);
-        sm.W1s[2 * H + i] = bf1(a.W1[2 * H + i]);
-        sm.b1s[i] = bf1(a.b1[i]);
-        if (i < cols) {
-            sm.b2s[i] = bf1(a.b2[rank * cols + i]);
-            sm.w3s[i] = bf1(a.w3[rank * cols + i]);
-        }
-    }
-    const int tpc = (a.ntiles + gridDim.x - 1) / gridDim.x;
-    const int tile0 = min(a.ntiles, (int)blockIdx.x * tpc), tile1 = min(a.ntiles, tile0 + tpc);
-    if (blockIdx.x == 0 && tid == 0)
-        for (int i = 0; i < 3; ++i) oc->fct[i] = INT_MAX;
-    int w = 0;
-    cl.sync();  // slices and flags of every CTA are initialised before any remote write
-
-    for (int pass = 1;; ++pass) {
-        const int slot = pass % 3;
-        const int whi = a.window > 0 ? (int)min((long long)a.T, (long long)w + a.window) : a.T;
-        if (!cl_agree(sm, rank, prefix_phases(a, oc, sm.ws, tile0, tile1, pass, deadline, w))) break;
-        // ---------------- phase C: walks with cluster rounds
-        int my_changed = 0, my_first = INT_MAX;
-        long long my_lost = 0, my_ship = 0, my_R = 0;
-        unsigned long long my_evals = 0, my_rounds = 0;
-        int g = blockIdx.x;
-        bool fin = g >= a.ngroups, loaded = false, group_init = false;
-        long long r0 = 0, row1 = 0;
-        int nb = 0;
-        // lane state (warp 0)
-        int x0a = 0, ta = -1, qc_after = 0, done = 0, pos = 0;
-        int pend = 0, pt = 0, px0 = 0, py = 0, pold = 0, pqc = 0, pslot = 0;
-        for (;;) {
-            // advance the CTA's walk until some lane waits for a call or the CTA is done
-            while (!fin) {
-                if (!group_init) {
-                    nb = group_lanes(a, g);
-                    for (int i = tid; i < a.rp * kLanes; i += kOwThreads) {
-                        const int l = i & 31, j = i >> 5;
-                        const long long n = (long long)l * a.ngroups + g + (long long)j * a.P;
-                        if (l < nb && n < a.N) xs[i] = a.x0r[n];
-                    }
-                    x0a = a.X0; ta = -1; qc_after = 0; done = 0; pend = 0;
-                    r0 = a.gbase[g];
-                    row1 = a.gbase[g + 1];
-                    group_init = true;
-                    loaded = false;
-                }
-                if (!loaded) {
-                    if (r0 >= row1) {  // the group is finished
-                        __syncthreads();
-                        for (int i = tid; i < a.rp * kLanes; i += kOwThreads) {
-                            const int l = i & 31, j = i >> 5;
-                            const long long n = (long long)l * a.ngroups + g + (long long)j * a.P;
-                            if (l < nb && n < a.N) a.xfin[n] = xs[i];
-                        }
-                        g += gridDim.x;
-                        group_init = false;
-                        if (g >= a.ngroups) fin = true;
-                        continue;
-                    }
-                    __syncthreads();
-                    for (int i = tid; i < kClCh * kLanes; i += kOwThreads)
-                        (&sm.rec[0][0])[i] = a.rec[r0 * kLanes + i];
-                    for (int i = tid; i < kClCh * kLanes; i += kOwThreads)
-                        (&sm.memo[0][0])[i] = a.memo[r0 * kLanes + i];
-                    __syncthreads();
-                    for (int i = tid; i < kClCh * kLanes; i += kOwThreads) {
-                        const int t = (&sm.rec[0][0])[i].x;
-                        if (t >= 0) (&sm.pre[0][0])[i] = a.pre[t];
-                    }
-                    __syncthreads();
-                    loaded = true;
-                    pos = 0;
-                }
-                if (warp == 0) {
-                    bool parked = false;
-                    if (lane < nb) {
-                        if (pend && ((sm.served >> lane) & 1)) {
-                            const int q = sm.qout[lane];
-                            a.memo[(r0 + pos) * kLanes + lane] = make_int2(py, q);
-                            const int r = px0 - q <= a.s;
-                            const int recv = q < px0 ? q : px0;
-                            xs[pslot] = py + recv;
-                            my_ship += recv;
-                            my_R += r;
-                            x0a = r ? a.S : (px0 > q ? px0 - q : 0);
-                            qc_after = pqc + (pold >> 1);
-                            ta = pt;
-                            const int nv = 2 * q + r;
-                            if (nv != pold) {
-                                a.act[pt] = nv;
-                                if (!my_changed) my_first = pt;
-                                ++my_changed;
-                            }
-                            pend = 0;
-                            ++pos;
-                        }
-                        if (pend) {
-                            parked = true;  // still waiting (not served in the last round)
-                        } else {
-                            while (pos < kClCh) {
-                                const int4 rc = sm.rec[pos][lane];
-                                if (rc.x < 0 || rc.x >= whi) {
-                                    pos = kClCh;
-                                    done = 1;
-                                    break;
-                                }
-                                const int t = rc.x, n = rc.y, d = rc.z;
-                                const int4 pr = sm.pre[pos][lane];
-                                int x0 = pr.z > ta ? a.S - pr.y : x0a - (pr.x - qc_after);
-                                x0 = x0 > 0 ? x0 : 0;
-                                const int slotn = (n / a.P) * kLanes + lane;
-                                const int xn = xs[slotn];
-                                const int y = xn > d ? xn - d : 0;
-                                my_lost += d > xn ? d - xn : 0;
-                                const int base = retailer_base(y, __ldg(a.sl + n), __ldg(a.Sl + n));
-                                const int room = __ldg(a.cap + n) - y;
-                                const int2 mm = sm.memo[pos][lane];
-                                if (mm.x != y) {
-                                    pend = 1;
-                                    pt = t; px0 = x0; py = y; pold = pr.w; pqc = pr.x; pslot = slotn;
-                                    sm.feat_y[lane] = y;
-                                    sm.feat_d[lane] = d;
-                                    sm.feat_e[lane] = rc.w;
-                                    sm.feat_base[lane] = base;
-                                    sm.feat_room[lane] = room;
-                                    parked = true;
-                                    break;
-                                }
-                                const int q = mm.y;
-                                const int r = x0 - q <= a.s;
-                                const int recv = q < x0 ? q : x0;
-                                xs[slotn] = y + recv;
-                                my_ship += recv;
-                                my_R += r;
-                                x0a = r ? a.S : (x0 > q ? x0 - q : 0);
-                                qc_after = pr.x + (pr.w >> 1);
-                                ta = t;
-                                const int nv = 2 * q + r;
-                                if (nv != pr.w) {
-                                    a.act[t] = nv;
-                                    if (!my_changed) my_first = t;
-                                    ++my_changed;
-                                }
-                                ++pos;
-                            }
-                        }
-                    }
-                    const unsigned rows = __ballot_sync(kFull, parked);
-                    const bool all = __all_sync(kFull, done || lane >= nb);
-                    if (lane == 0) {
-                        sm.pend_rows = (int)rows;
-                        sm.pend_any = rows != 0u;
-                        sm.all_done = all;
-                    }
-                }
-                __syncthreads();
-                if (sm.pend_any) break;  // calls to make: join a round
-                // every lane reached the chunk's end (or its list / window end)
-                loaded = false;
-                r0 += kClCh;
-                if (sm.all_done) r0 = row1;
-            }
-            const unsigned rows = fin ? 0u : (unsigned)sm.pend_rows;
-            if (cl_round(a, sm, h1pool, w2s, rank, rows, fin)) break;
-            if (tid == 0 && sm.m) {
-                my_evals += sm.m;
-                ++my_rounds;
-            }
-        }
-        if (warp == 0) {
-            const int ch = __reduce_add_sync(kFull, my_changed);
-            const int fmin = __reduce_min_sync(kFull, my_first);
-            const long long lo = warp_sum_i64(my_lost), sh = warp_sum_i64(my_ship),
-                            rr = warp_sum_i64(my_R);
-            if (lane == 0) {
-                if (ch) {
-                    atomicAdd(&oc->changed[slot], ch);
-                    atomicMin(&oc->fct[slot], fmin);
-                }
-                if (lo) atomicAdd((unsigned long long*)&oc->lost[slot], (unsigned long long)lo);
-                if (sh) atomicAdd((unsigned long long*)&oc->shipped[slot], (unsigned long long)sh);
-                if (rr) atomicAdd((unsigned long long*)&oc->R[slot], (unsigned long long)rr);
-            }
-        }
-        if (tid == 0 && my_evals) {
-            atomicAdd(&oc->evals, my_evals);
-            atomicAdd(&oc->rounds, my_rounds);
-        }
-        if (!cl_agree(sm, rank, grid_sync(&oc->c, deadline))) break;
-        const int changed = ld_volatile(&oc->changed[slot]);
-        const bool fixed = changed == 0 && whi >= a.T;
-        if (fixed || pass >= a.max_iters) {
-            if (blockIdx.x == 0 && tid == 0) {
-                oc->c.iters = pass;
-                oc->c.converged = fixed;
-                oc->c.pad0 = slot;
-            }
-            break;
-        }
-        w = changed ? ld_volatile(&oc->fct[slot]) : whi;
-    }
-    cl.sync();  // no CTA leaves while a peer may still address its shared memory
 }
 
 // ------------------------------------------------------------------ sequential baseline
@@ -1613,62 +1263,23 @@ pic_status pic_owmr_simulate(pic_owmr* h, const pic_owmr_policy* pol, const pic_
     if (o->mode == PIC_MODE_PICARD) {
         if (!(o->flags & PIC_FLAG_REUSE_TABLES)) free_tables(h);
         a.xs_len = rp * kLanes;
-        // with a network and PIC_OWMR_FLAG_CLUSTER_W2, W2 resident in clusters of 4 CTAs
-        // (when such clusters fit); otherwise W2 streamed through each CTA per round
-        const bool cluster = H > 0 && (o->flags & PIC_OWMR_FLAG_CLUSTER_W2) &&
-                             cl_smem(H, a.xs_len) + 1024 <= (size_t)h->max_smem;
-        const size_t smem_cl = cl_smem(H, a.xs_len);
-        int ncl = 0;
-        cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute attr[2];
-        if (cluster) {
-            CU(cudaFuncSetAttribute((const void*)k_owmr_picard_cl,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cl));
-            attr[0].id = cudaLaunchAttributeClusterDimension;
-            attr[0].val.clusterDim.x = kClSize;
-            attr[0].val.clusterDim.y = 1;
-            attr[0].val.clusterDim.z = 1;
-            attr[1].id = cudaLaunchAttributeCooperative;
-            attr[1].val.cooperative = 1;
-            cfg.blockDim = dim3(kOwThreads);
-            cfg.dynamicSmemBytes = smem_cl;
-            cfg.stream = st;
-            cfg.attrs = attr;
-            cfg.numAttrs = 1;
-            cfg.gridDim = dim3(kClSize * h->num_sms);
-            if (cudaOccupancyMaxActiveClusters(&ncl, (const void*)k_owmr_picard_cl, &cfg) != cudaSuccess)
-                ncl = 0;
-            cudaGetLastError();
-        }
-        if (ncl > 0) {
-            const int grid = ncl * kClSize;
-            pic_status ps = build_tables(h, P, grid, st, &launches);
-            if (ps) return ps;
-            a.B = h->B; a.ngroups = h->ngroups; a.rec = h->rec; a.gbase = h->gbase; a.memo = h->memo;
-            CU(cudaMemsetAsync(h->memo, 0xff, (size_t)(h->rows > 0 ? h->rows : 1) * kLanes * sizeof(int2), st));
-            cfg.gridDim = dim3(grid);
-            cfg.numAttrs = 2;
-            CU(cudaLaunchKernelEx(&cfg, k_owmr_picard_cl, a));
-            ++launches;
-        } else {
-            const size_t smem = owmr_smem(H, a.xs_len, h->max_smem, &a.nbuf);
-            if (H && a.nbuf < 2) return fail(PIC_ERR_UNSUPPORTED, "shared memory too small for the network");
-            void (*kern)(OwArgs) = H ? k_owmr_picard<true> : k_owmr_picard<false>;
-            CU(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            int occ = 0;
-            CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kOwThreads, smem));
-            if (occ < 1) return fail(PIC_ERR_CUDA, "OWMR kernel does not fit an SM");
-            const int grid = h->num_sms * occ;
-            pic_status ps = build_tables(h, P, grid, st, &launches);
-            if (ps) return ps;
-            a.B = h->B; a.ngroups = h->ngroups; a.rec = h->rec; a.gbase = h->gbase; a.memo = h->memo;
-            a.cmax = h->cmax; a.ckpt = h->ckpt;
-            a.resume = rp == 1;  // checkpoints hold one store's stock per lane
-            if (H) CU(cudaMemsetAsync(h->memo, 0xff, (size_t)(h->rows > 0 ? h->rows : 1) * kLanes * sizeof(int2), st));
-            void* params[] = {&a};
-            CU(cudaLaunchCooperativeKernel((const void*)kern, grid, kOwThreads, params, smem, st));
-            ++launches;
-        }
+        const size_t smem = owmr_smem(H, a.xs_len, h->max_smem, &a.nbuf);
+        if (H && a.nbuf < 2) return fail(PIC_ERR_UNSUPPORTED, "shared memory too small for the network");
+        void (*kern)(OwArgs) = H ? k_owmr_picard<true> : k_owmr_picard<false>;
+        CU(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int occ = 0;
+        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kOwThreads, smem));
+        if (occ < 1) return fail(PIC_ERR_CUDA, "OWMR kernel does not fit an SM");
+        const int grid = h->num_sms * occ;
+        pic_status ps = build_tables(h, P, grid, st, &launches);
+        if (ps) return ps;
+        a.B = h->B; a.ngroups = h->ngroups; a.rec = h->rec; a.gbase = h->gbase; a.memo = h->memo;
+        a.cmax = h->cmax; a.ckpt = h->ckpt;
+        a.resume = rp == 1;  // checkpoints hold one store's stock per lane
+        if (H) CU(cudaMemsetAsync(h->memo, 0xff, (size_t)(h->rows > 0 ? h->rows : 1) * kLanes * sizeof(int2), st));
+        void* params[] = {&a};
+        CU(cudaLaunchCooperativeKernel((const void*)kern, grid, kOwThreads, params, smem, st));
+        ++launches;
     } else {
         a.rec = h->trec;
         const bool use_smem = h->N <= kMaxSlots;
@@ -1720,6 +1331,7 @@ pic_status pic_owmr_simulate(pic_owmr* h, const pic_owmr_policy* pol, const pic_
         res->shipped = hc.shipped[sl];
         res->policy_calls = (long long)hc.evals;
         res->eval_rounds = (long long)hc.rounds;
+        res->near_ties = (long long)hc.near;
         res->launches = launches;
         res->ms_total = 0.f;
         if (timing) cudaEventElapsedTime(&res->ms_total, ev0, ev1);

@@ -12,15 +12,11 @@ import torch
 from . import PIC_MEM_DEVICE, PIC_MEM_HOST, PIC_MODE_PICARD, PIC_MODE_SEQUENTIAL, PIC_OK, \
     PIC_FLAG_TIMING, PicError, _ptr, _stream_handle, lib, pic_last_error
 
-__all__ = ["DeviceOwmr", "DeviceOwmrNet", "PIC_OWMR_FLAG_CLUSTER_W2", "pic_owmr_create", "pic_owmr_simulate",
+__all__ = ["DeviceOwmr", "DeviceOwmrNet", "pic_owmr_create", "pic_owmr_simulate",
            "pic_owmr_destroy", "pic_owmr_desc", "pic_owmr_policy", "pic_owmr_opts",
            "pic_owmr_result", "PIC_MEM_HOST"]
 
 P_ = C.c_void_p
-
-# pic_owmr_opts.flags: keep W2 resident across 4-CTA clusters (pooled rounds) instead of streaming it
-PIC_OWMR_FLAG_CLUSTER_W2 = 1 << 16
-
 
 class pic_owmr_desc(C.Structure):
     _fields_ = [("T", C.c_int32), ("N", C.c_int32), ("ret", P_), ("dem", P_), ("ex", P_), ("cap", P_),
@@ -42,7 +38,8 @@ class pic_owmr_opts(C.Structure):
 class pic_owmr_result(C.Structure):
     _fields_ = [("iters", C.c_int32), ("procs", C.c_int32), ("replenishments", C.c_int64),
                 ("lost", C.c_int64), ("shipped", C.c_int64), ("policy_calls", C.c_int64),
-                ("eval_rounds", C.c_int64), ("launches", C.c_int32), ("ms_total", C.c_float)]
+                ("eval_rounds", C.c_int64), ("launches", C.c_int32), ("ms_total", C.c_float),
+                ("near_ties", C.c_int64)]
 
 
 _bound = False
@@ -156,5 +153,5 @@ class DeviceOwmr:
         return {"status": st, "actions": act, "q": act >> 1, "r": act & 1, "state": state,
                 "iters": res.iters, "procs": res.procs, "R": res.replenishments,
                 "lost": res.lost, "shipped": res.shipped, "policy_calls": res.policy_calls,
-                "eval_rounds": res.eval_rounds, "launches": res.launches, "ms": res.ms_total,
+                "eval_rounds": res.eval_rounds, "near_ties": res.near_ties, "launches": res.launches, "ms": res.ms_total,
                 "_keep": (net, init)}

@@ -1,6 +1,8 @@
 """GPU parity of the MLP policies (argmax and Gumbel-max) against the CPU oracle
-through the C ABI.  Scores use a fixed FP32 operation order on both sides, so
-actions, pass counts, final stock and total cost must be identical."""
+through the C ABI.  The oracle scores in the reference FP32 order (one fmaf
+chain per output from its bias); the kernels score faster and re-score near
+ties in that order, so actions, pass counts, final stock and total cost must be
+identical."""
 import numpy as np
 import pytest
 import torch
@@ -195,3 +197,59 @@ def test_four_warp_decisions_bit_exact(N):
         for k in (1, 3):
             g = d.simulate(pol, "picard", num_chunks=30, max_iters=k, flags=G, raise_on_error=False)
             np.testing.assert_array_equal(g["actions"].cpu().numpy(), rec["iterates"][k - 1])
+
+
+def _bf(v):
+    return synth.f32_to_bf16(np.asarray(v, np.float32))
+
+
+def adversarial_mlp(N, R):
+    """Weights on which the fast layer-2 order and the reference order rank two
+    warehouses differently.  h_j = 1 for every hidden unit (W1 = 0, b1 = 1).
+    Warehouse 0: b2 = 2^24 and W2[:, 0] = 1; the reference chain from b2 rounds
+    every step back to 2^24 (ties to even), while any order that sums the 256
+    ones first gives 2^24 + 256.  Warehouse 1: W2[0, 1] = 2^24, W2[1, 1] = 128,
+    2^24 + 128 in every order.  The other warehouses score 0.  So the reference
+    sends an order to warehouse 1 while it has stock, and the fast scores alone
+    would send it to warehouse 0."""
+    H = 256
+    W1 = np.zeros((2 * N + 16, H))
+    W2 = np.zeros((H, N))
+    b2 = np.zeros(N)
+    W2[:, 0] = 1.0
+    b2[0] = 2.0 ** 24
+    W2[0, 1] = 2.0 ** 24
+    W2[1, 1] = 128.0
+    return synth.MLPParams(_bf(W1), _bf(np.ones(H)), _bf(W2), _bf(b2), _bf(np.zeros((R, 16))), H)
+
+
+@pytest.mark.parametrize("N", [8, 64, 100])
+def test_near_ties_take_the_reference_order(N):
+    """On adversarial_mlp the fast order disagrees with the reference on every
+    decision where warehouses 0 and 1 both hold stock: the bound flags each one
+    as a near tie and the re-score gives the oracle's action.  Every decision
+    path: sequential, Picard, four warps per decision, tensor-core tiles, with
+    and without the saturated-state table (whose scores are exact), argmax and
+    Gumbel-max."""
+    inst = synth.make_instance(3000, N, 4, 3, seed=N, stock="poisson", fill=0.6)
+    mlp = adversarial_mlp(N, 3)
+    d = DeviceInstance(inst)
+    G, TC, NS = pic.PIC_FLAG_WARP_GROUP, pic.PIC_FLAG_TC, pic.PIC_FLAG_NO_SAT
+    for pol in policies(mlp, N):
+        want = oracle.seq_sim(inst, pol)
+        a = want["actions"]
+        # the reference picks warehouse 1 while it is stocked, then warehouse 0
+        assert (a == 1).sum() > 10 and (a == 0).sum() > 0
+        iters = oracle.picard_chunked(inst, pol, 30)["iters"]
+        runs = [("sequential", 0), ("sequential", NS), ("picard", 0), ("picard", NS)]
+        if N <= 64:
+            runs += [("sequential", G | NS), ("picard", G | NS), ("picard", TC | NS)]
+        for mode, flags in runs:
+            got = d.simulate(pol, mode, num_chunks=30, flags=flags)
+            np.testing.assert_array_equal(got["actions"].cpu().numpy(), a, err_msg=f"{mode} {flags}")
+            np.testing.assert_array_equal(got["final_stock"].cpu().numpy(), want["x_final"])
+            assert got["total_cost"] == want["total_cost"]
+            if mode == "picard":
+                assert got["iters"] == iters
+            if flags & NS:
+                assert got["near_ties"] > 0, (mode, flags)

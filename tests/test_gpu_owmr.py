@@ -9,10 +9,7 @@ import torch
 import paper_2406_01939_b300 as pic
 from oracle import owmr as ow
 from paper_2406_01939_b300 import synth
-from paper_2406_01939_b300.owmr import PIC_OWMR_FLAG_CLUSTER_W2, DeviceOwmr, DeviceOwmrNet
-
-# the network's two kernels: W2 streamed per round (default), W2 resident across 4-CTA clusters
-KERNELS = [0, PIC_OWMR_FLAG_CLUSTER_W2]
+from paper_2406_01939_b300.owmr import DeviceOwmr, DeviceOwmrNet
 
 pytestmark = pytest.mark.gpu
 
@@ -59,12 +56,9 @@ def test_no_network_random_bit_exact(N):
             check(inst, None, P, dev=d)
 
 
-@pytest.mark.parametrize("flags", KERNELS)
-def test_network_bit_exact_and_calls(flags):
+def test_network_bit_exact_and_calls():
     """H = 64 and 512, ragged groups (N = 45 processors over several lanes),
-    skewed store weights; the same calls as the oracle's memo; both kernels."""
-    # N = 2,000: 16 processors per CTA, so a round has more pending calls than
-    # one CTA may contribute (8) and the rest wait for the next round
+    skewed store weights; the same calls as the oracle's memo."""
     for H, T, N, a in ((64, 3000, 45, 0.0), (512, 1500, 37, 0.02), (128, 2500, 70, 0.0),
                        (256, 4000, 300, 0.0), (64, 30000, 2000, 0.0)):
         inst = rand_inst(H + N, T, N, theorem=H != 128, a=a)
@@ -72,18 +66,17 @@ def test_network_bit_exact_and_calls(flags):
         d = DeviceOwmr(inst)
         dn = DeviceOwmrNet(net)
         for P in (N, max(1, N // 3)):
-            check(inst, net, P, dev=d, dnet=dn, flags=flags)
+            check(inst, net, P, dev=d, dnet=dn)
 
 
-@pytest.mark.parametrize("flags", KERNELS)
-def test_every_iterate_matches_algorithm_1(flags):
+def test_every_iterate_matches_algorithm_1():
     inst = rand_inst(7, 1200, 9, theorem=False)
     net = synth.make_owmr_net(64, seed=2)
     d = DeviceOwmr(inst)
     for nn in (None, net):
         want = ow.picard_literal(inst, nn, procs_of(9, 9), record=True)
         for k in range(1, want["iters"] + 1):
-            got = d.simulate(nn, num_procs=9, max_iters=k, raise_on_error=False, flags=flags)
+            got = d.simulate(nn, num_procs=9, max_iters=k, raise_on_error=False)
             assert got["status"] == (pic.PIC_OK if k == want["iters"] else pic.PIC_ERR_NOT_CONVERGED)
             np.testing.assert_array_equal(got["actions"].cpu().numpy(), want["iterates"][k - 1])
 
@@ -113,8 +106,7 @@ def test_warm_start():
     assert got["iters"] == want["iters"] and got["policy_calls"] == want["evals"]
 
 
-@pytest.mark.parametrize("flags", KERNELS)
-def test_window_bit_exact_and_passes(flags):
+def test_window_bit_exact_and_passes():
     """The max_steps window: same iterates, passes and network calls as the
     oracle's windowed walk, for windows from one step to the horizon."""
     net = synth.make_owmr_net(64, seed=12)
@@ -126,7 +118,7 @@ def test_window_bit_exact_and_passes(flags):
             for nn, dd in ((None, None), (net, dn)):
                 seq = ow.seq_sim(inst, nn)
                 want = ow.picard_walk(inst, nn, procs_of(N, N), window=W)
-                got = d.simulate(dd, max_steps=W, flags=flags)
+                got = d.simulate(dd, max_steps=W)
                 np.testing.assert_array_equal(got["actions"].cpu().numpy(), seq["actions"])
                 np.testing.assert_array_equal(got["state"].cpu().numpy(), seq["x_final"])
                 assert got["iters"] == want["iters"], (W, got["iters"], want["iters"])
@@ -136,23 +128,22 @@ def test_window_bit_exact_and_passes(flags):
     d = DeviceOwmr(inst)
     want = ow.picard_literal(inst, net, procs_of(9, 9), record=True, window=100)
     for k in range(1, want["iters"] + 1, 3):
-        got = d.simulate(net, max_iters=k, max_steps=100, raise_on_error=False, flags=flags)
+        got = d.simulate(net, max_iters=k, max_steps=100, raise_on_error=False)
         np.testing.assert_array_equal(got["actions"].cpu().numpy(), want["iterates"][k - 1])
 
 
 def test_window_scaled_base_case():
     """The base case at a tenth of its size (365,000 steps, 400 stores) with a
     window of 16,000 steps: the oracle's passes and network calls (each step's
-    network evaluated about once), through both kernels."""
+    network evaluated about once)."""
     inst, _ = synth.owmr_base(0, T=365_000, N=400, H=64)
     inst.S = inst.s + 7_000
     net = synth.make_owmr_net(64, seed=0)
     want = ow.picard_walk(inst, net, procs_of(400, 400), window=16_000)
     d = DeviceOwmr(inst)
-    for flags in KERNELS:
-        got = d.simulate(net, max_steps=16_000, flags=flags)
-        np.testing.assert_array_equal(got["actions"].cpu().numpy(), want["actions"])
-        assert got["iters"] == want["iters"] and got["policy_calls"] == want["evals"]
+    got = d.simulate(net, max_steps=16_000)
+    np.testing.assert_array_equal(got["actions"].cpu().numpy(), want["actions"])
+    assert got["iters"] == want["iters"] and got["policy_calls"] == want["evals"]
 
 
 def test_many_groups_per_cta():
@@ -207,11 +198,36 @@ def test_base_case_full_size():
     pg = d.simulate(dn, max_steps=80_000)
     sg = d.simulate(dn, mode="sequential")
     assert torch.equal(pg["actions"], sg["actions"]) and torch.equal(pg["state"], sg["state"])
-    ps = d.simulate(dn, max_steps=80_000, flags=PIC_OWMR_FLAG_CLUSTER_W2)
-    assert torch.equal(ps["actions"], pg["actions"]) and ps["iters"] == pg["iters"]
-    assert ps["policy_calls"] == pg["policy_calls"]
     assert pg["R"] == sg["R"] and pg["lost"] == sg["lost"]
     Tp = 20_000
     pre = synth.OwmrInstance(Tp, inst.N, inst.ret[:Tp], inst.dem[:Tp], inst.ex[:Tp], inst.cap,
                              inst.x0r, inst.sl, inst.Sl, inst.X0, inst.s, inst.S)
     np.testing.assert_array_equal(pg["actions"][:Tp].cpu().numpy(), ow.seq_sim(pre, net)["actions"])
+
+
+def test_output_layer_near_ties_take_the_reference_order():
+    """A network whose fast output layer and reference chain disagree: h2_j = 1
+    (W1 = 0, b1 = 0, W2 = 0, b2 = 1), w3_0 = -2^24, w3_1..3 = 1, other w3 = 0,
+    b3 = 2^24.  The reference chain gives 2^24 - 2^24 + 1 + 1 + 1 = 3; the
+    group of eight first gives -2^24 (each +1 rounds back), then z = 0.  Every
+    q with room for it differs, so the kernels must detect the undecided floor
+    and re-evaluate z in the reference order: actions equal the oracle's, in
+    Picard and sequential mode."""
+    H = 64
+    bf = lambda v: synth.f32_to_bf16(np.asarray(v, np.float32))
+    w3 = np.zeros(H)
+    w3[0] = -(2.0 ** 24)
+    w3[1:4] = 1.0
+    net = synth.OwmrNet(H, bf(np.zeros((3, H))), bf(np.zeros(H)), bf(np.zeros((H, H))),
+                        bf(np.ones(H)), bf(w3), bf([2.0 ** 24]))
+    assert ow.mlp(net, 1, 1, 1) == 3.0
+    inst = rand_inst(77, 3000, 12, theorem=False)
+    seq = ow.seq_sim(inst, net)
+    base_only = ow.seq_sim(inst, None)
+    assert (seq["actions"] != base_only["actions"]).any()  # the network moves q
+    d = DeviceOwmr(inst)
+    for mode in ("picard", "sequential"):
+        got = d.simulate(net, mode=mode)
+        np.testing.assert_array_equal(got["actions"].cpu().numpy(), seq["actions"])
+        np.testing.assert_array_equal(got["state"].cpu().numpy(), seq["x_final"])
+        assert got["near_ties"] > 0

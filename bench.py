@@ -85,8 +85,11 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--T", type=int, default=0, help="orders (0 = the workload's own size)")
     p.add_argument("--workload", default="dual_large",
-                   choices=["dual_large", "mlp_medium", "batch_uneven", "pg_large",
-                            "capacity_large", "owmr_base"])
+                   choices=["dual_large", "greedy_small", "mlp_medium", "batch_uneven",
+                            "pg_large", "capacity_large", "owmr_base"])
+    p.add_argument("--chunk-sweep", default="",
+                   help="comma-separated chunk counts: one JSON line per count (single-trajectory "
+                        "workloads), e.g. 256,1024,4096,16384,65536")
     p.add_argument("--flags", type=int, default=0, help="extra pic_sim_opts flags (tuning)")
     p.add_argument("--max-steps", type=int, default=-1,
                    help="Picard window of App. A.3 in orders (-1: the workload's default, 0: none)")
@@ -105,8 +108,8 @@ def parse():
 DEFAULT_MAX_STEPS = {"mlp_medium": 16384, "owmr_base": 80_000}
 DEFAULT_SEG_WINDOW = {"mlp_medium": 4}
 
-DEFAULT_CHUNKS = {"dual_large": 4096, "mlp_medium": 4096, "batch_uneven": 0, "pg_large": 0,
-                  "capacity_large": 16384}
+DEFAULT_CHUNKS = {"dual_large": 4096, "greedy_small": 64, "mlp_medium": 4096, "batch_uneven": 0,
+                  "pg_large": 0, "capacity_large": 16384}
 
 # FP32 CUDA-core peak of the MLP scorer's arithmetic: 148 SMs x 128 FP32 lanes x
 # 2 FLOP per FMA x 2.032 GHz (maximum SM clock)
@@ -129,6 +132,9 @@ def make_workload(args, seed):
     if args.workload == "capacity_large":
         inst = synth.capacity_large(seed, **({"T": args.T} if args.T else {}))
         return inst, Policy("dual"), "dual"
+    if args.workload == "greedy_small":
+        inst = synth.greedy_small(seed, **({"T": args.T} if args.T else {}))
+        return inst, Policy("greedy"), "greedy"
     inst = synth.dual_large(seed, **({"T": args.T} if args.T else {}))
     return inst, Policy("dual"), "dual"
 
@@ -153,14 +159,16 @@ def batch_config(args, insts, res):
 
 
 def workload_config(args, inst):
-    pol = "MLP Linear(2N+16,256)-ReLU-Linear(256,N), BF16 N(0,0.02)" \
-        if args.workload == "mlp_medium" else "bid-price, lambda~U{0..30}"
+    pol = {"mlp_medium": "MLP Linear(2N+16,256)-ReLU-Linear(256,N), BF16 N(0,0.02)",
+           "greedy_small": "greedy (argmin cost over stocked warehouses)"}.get(
+               args.workload, "bid-price, lambda~U{0..30}")
+    stock = "x0~U{0..20}" if args.workload == "greedy_small" else "x0~Poisson(1.05 T p_k/N)"
     cap = (", node capacity for 80% of the orders (log-normal(0, 0.5) node weights), chunks "
            "of 64 orders replayed in time order" if getattr(inst, "cap", None) is not None else "")
     return {
         "workload": args.workload,
         "desc": (f"FO, T={inst.T} orders, N={inst.N} warehouses, K={inst.K} products "
-                 f"(Zipf 1.1), R={inst.R} regions, x0~Poisson(1.05 T p_k/N), cost~U{{1..100}}, "
+                 f"(Zipf 1.1), R={inst.R} regions, {stock}, cost~U{{1..100}}, "
                  f"{pol}{cap}"),
         "T": inst.T, "N": inst.N, "K": inst.K, "R": inst.R,
         "chunks": chunks_of(args) if args.partition != "products" else None,
@@ -168,7 +176,7 @@ def workload_config(args, inst):
                       "products": f"products (processor of product k: k mod {inst.K})",
                       "random": f"uniform random over {chunks_of(args)} processes (seeded)"}[
                           args.partition],
-        "policy": args.workload == "mlp_medium" and "mlp" or "dual",
+        "policy": {"mlp_medium": "mlp", "greedy_small": "greedy"}.get(args.workload, "dual"),
         "max_steps": (args.max_steps if args.max_steps >= 0 else
                       DEFAULT_MAX_STEPS.get(args.workload, 0)) or None,
         "l2": "flushed between timed steps (256 MiB write)",
@@ -411,6 +419,39 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def pass_trace_of(tr, iters):
+    """Per-pass record (pic_sim_opts.trace rows) as lists: prefix and replay
+    phase times, policy calls, work units, and the largest unit's calls and
+    orders."""
+    n = min(iters, tr.shape[0])
+    ts, tr_end = tr[:n, 0], tr[:n, 1]
+    prev = np.r_[0, tr_end[:-1]]
+    return {"prefix_us": ((ts - prev) / 1e3).round(1).tolist(),
+            "replay_us": ((tr_end - ts) / 1e3).round(1).tolist(),
+            "policy_calls": tr[:n, 2].tolist(), "units": tr[:n, 3].tolist(),
+            "longest_unit_calls": tr[:n, 4].tolist(), "longest_unit_orders": tr[:n, 5].tolist()}
+
+
+def critical_path(trace, t_dec_us, kernel_ms, what):
+    """A lower bound model of the persistent kernel's time from its pass trace:
+    every pass waits for its largest work unit, whose policy calls run one after
+    another (t_dec_us each, the measured latency of one decision by one warp),
+    and costs at least the cheapest pass of the call (t_floor: the barriers and
+    the prefix phase with almost no work).  frac = bound / kernel time."""
+    if not trace or not trace["policy_calls"]:
+        return None
+    pass_us = [a + b for a, b in zip(trace["prefix_us"], trace["replay_us"])]
+    floor_us = min(pass_us)
+    chain = sum(trace["longest_unit_calls"])
+    bound_us = chain * t_dec_us + floor_us * len(pass_us)
+    return {"bound_us": bound_us, "kernel_us": kernel_ms * 1000.0,
+            "frac": bound_us / (kernel_ms * 1000.0), "passes": len(pass_us),
+            "sequential_decisions": int(chain), "t_decision_us": t_dec_us,
+            "t_pass_floor_us": floor_us,
+            "model": "sum over passes of (largest unit's policy calls x t_decision) + passes x "
+                     "t_pass_floor; " + what}
+
+
 def fp32_scored(res):
     """MLP decisions that ran the FP32 scorer: not taken from tensor-core tile
     scores and not from the saturated-state table (those cost no scorer FLOPs
@@ -475,6 +516,25 @@ def run_batch(args, dev, world, rank):
     value, t_ms = job_rate(T, args.steps, sum(a.elapsed_time(b) for a, b in evs), world, dev)
     last = results[-1]
     sim_ms = statistics.median(r["sim_ms"] for r in results)
+    # one extra (untimed) call with the per-pass trace, and the latency of one MLP
+    # decision by one warp (the longest work units are MLP runs): the one-warp
+    # sequential simulator on the first orders of the first MLP trajectory
+    tr = np.zeros((4096, 6), np.int64)
+    db.simulate(pols, "picard", num_chunks=last["num_chunks"], seg_window=last["seg_window"],
+                flags=args.flags, want_stock=False, out=act, trace=tr)
+    pass_trace = pass_trace_of(tr, last["iters"])
+    from paper_2406_01939_b300.session import DeviceInstance
+    bm = next(b for b, p in enumerate(pols) if p.kind != "greedy")
+    Tp = min(insts[bm].T, 16384)
+    dp = DeviceInstance(prefix_instance(insts[bm], Tp), device=dev)
+    pact = torch.empty(Tp, dtype=torch.int8, device=dev)
+    tds = [dp.simulate(pols[bm], "sequential", flags=pic.PIC_FLAG_TIMING, want_stock=False,
+                       out=pact)["total_ms"] for _ in range(3)]
+    dp.close()
+    t_dec_us = 1000.0 * statistics.median(tds[1:]) / Tp
+    cp = critical_path(pass_trace, t_dec_us, sim_ms,
+                       f"every unit's calls charged as MLP decisions; t_decision: one-warp "
+                       f"sequential simulator on the first {Tp} orders of trajectory {bm} (MLP)")
 
     seq_ms, bit_exact_gpu = None, None
     if args.seq_steps > 0:
@@ -531,9 +591,12 @@ def run_batch(args, dev, world, rank):
         "phases_ms": {"per_call_work": sim_ms, "step_device": t_ms / args.steps},
         "policy_calls": last["policy_calls"], "mlp_calls": last["mlp_calls"],
         "tc_decisions": last["tc_decisions"], "sat_decisions": last["sat_decisions"],
+        "near_ties": last["near_ties"],
         "segment_replays": last["seg_replays"],
         "roofline": mlp_roofline(fp32_scored(last), insts[0].N, sim_ms,
                                  "k_picard_batch (persistent, all passes; MLP scorer FP32 FMA)"),
+        "critical_path": cp,
+        "pass_trace": pass_trace,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "bit_exact": bit_exact_e2e,
                 "what": "pic_create_batch from pinned host arrays + pic_simulate_batch with host "
@@ -628,6 +691,47 @@ def run_pg(args, dev, world, rank):
         torch.cuda.synchronize(dev)
         gts.append(g0.elapsed_time(g1))
     bwd_ms = statistics.median(gts)
+    # the sequential GPU simulator on the same batch (one warp per trajectory,
+    # every trajectory in one launch, the same BF16 parameters and noise)
+    from paper_2406_01939_b300.synth import Policy
+    spols = [Policy("gumbel", mlp=mlp, seed=1000 + b, traj=b) for b in range(B)]
+    seq_ms, bit_exact_gpu = None, None
+    if args.seq_steps > 0:
+        seq_act = torch.empty(T, dtype=torch.int8, device=dev)
+        sms = [db.simulate(spols, "sequential", flags=pic.PIC_FLAG_TIMING, want_stock=False,
+                           out=seq_act)["total_ms"] for _ in range(min(2, args.seq_steps) + 1)]
+        seq_ms = statistics.median(sms[1:])
+        bit_exact_gpu = bool(torch.equal(seq_act, acts))
+    # end to end: the batch created from pinned host arrays, the master parameters
+    # copied from pinned host memory, one gradient step, J read back (a double)
+    e2e = None
+    if args.e2e_steps > 0:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).pin_memory().numpy()
+        host = [synth.Instance(i.T, i.N, i.K, i.R, pin(i.prod), pin(i.reg), pin(i.x0), pin(i.cost),
+                               None) for i in insts]
+        master_h = master.cpu().pin_memory()
+        h2d = sum(i.prod.nbytes + i.reg.nbytes + i.x0.nbytes + i.cost.nbytes for i in host) + \
+            master_h.numel() * 4
+        ts = []
+        for i in range(min(3, args.e2e_steps) + 1):
+            flush.fill_(1)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            hb = DeviceBatch(host, device=dev, mem=pic.PIC_MEM_HOST)
+            m_dev = master_h.to(dev, non_blocking=True)
+            hrf = Reinforce(hb, ["gumbel"] * B, [1000 + b for b in range(B)], list(range(B)),
+                            insts[0].R, num_chunks=res.num_chunks, seg_window=res.seg_window,
+                            flags=args.flags)
+            Jh, _ = hrf.step(m_dev, grad)
+            hb.close()
+            t1 = time.perf_counter()
+            if i:
+                ts.append(t1 - t0)
+        e2e = {"value": job_rate(T, 1, 1000.0 * statistics.median(ts), world, dev)[0], "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8,
+               "objective_rel_diff": abs(Jh - J) / max(abs(J), 1e-300),
+               "what": "pic_create_batch from pinned host arrays + master parameters H2D + "
+                       "pic_policy_grad (simulate + J + gradient) with J returned to the host"}
     flops = T * grad_flops_per_order(N)
     achieved = flops / (bwd_ms / 1000.0) / 1e12
     tc = not (args.flags & pic.PIC_FLAG_NO_TC)
@@ -646,8 +750,15 @@ def run_pg(args, dev, world, rank):
         "iters": res.iters, "objective": J,
         "phases_ms": {"step": t_ms / args.steps, "simulation": res.sim_ms,
                       "gradient_call_on_given_paths": bwd_ms},
+        "seq_gpu": {"value": T / (seq_ms / 1000.0), "unit": UNIT, "ms": seq_ms,
+                    "what": "one warp per trajectory, all trajectories in one launch"}
+        if seq_ms else None,
+        "speedup_vs_seq_gpu": seq_ms / res.sim_ms if seq_ms else None,
+        "speedup_basis": "sequential simulation / Picard simulation inside the step",
+        "bit_exact_vs_seq_gpu": bit_exact_gpu,
         "policy_calls": res.policy_calls, "tc_decisions": res.tc_decisions,
         "sat_decisions": res.sat_decisions, "rescored": res.rescored,
+        "near_ties": res.near_ties,
         "roofline": ({"bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
                       "frac": achieved / bf16_peak, "traffic": None,
                       "kernel": "k_pg_tc (tcgen05, BF16 split products, FP32 accumulation in TMEM)",
@@ -658,12 +769,19 @@ def run_pg(args, dev, world, rank):
                       "kernel": "k_pg_grad (FP32 CUDA cores)",
                       "peak_kind": "derived: 148 SMs x 128 FP32 lanes x 2 FLOP x 2.032 GHz",
                       "algorithmic_flops": flops}),
-        "e2e": None,
-        "gpu_launches": None,
+        "e2e": e2e,
+        "gpu_launches": int(res.launches) * args.steps,
         "clocks": clk,
         "wall_s_timed_loop": wall,
         "cpu_baseline": None,
     }
+    if rank == 0 and world == 1 and args.cpu_seconds > 0:
+        rate, sample, out, covered = cpu_oracle_rate(insts[0], spols[0], args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "trajectory 0: " + sample}
+        line["bit_exact_vs_oracle"] = bool(np.array_equal(out["actions"],
+                                                          acts[:covered].cpu().numpy()))
+        line["oracle_orders_checked"] = covered
     if rank == 0:
         print(json.dumps(line), flush=True)
     db.close()
@@ -845,6 +963,21 @@ def main():
             dist.destroy_process_group()
         return
 
+    if args.chunk_sweep:
+        for M in [int(x) for x in args.chunk_sweep.split(",") if x.strip()]:
+            args.chunks = M
+            run_single(args, dev, world, rank)
+    else:
+        run_single(args, dev, world, rank)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_single(args, dev, world, rank):
+    """Single-trajectory FO workloads: one whole simulation per step."""
+    import torch
+    import torch.distributed as dist
     import paper_2406_01939_b300 as pic
     from paper_2406_01939_b300 import synth as synth_mod
     from paper_2406_01939_b300.session import DeviceInstance, DevicePolicy
@@ -880,7 +1013,7 @@ def main():
     for _ in range(max(3, args.warmup)):
         r = step(act)
     stream = torch.cuda.current_stream(dev)
-    clocks = Clocks(local)
+    clocks = Clocks(dev.index or 0)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -906,15 +1039,10 @@ def main():
     # one extra (untimed) call with the per-pass trace (contiguous chunks)
     pass_trace = None
     if args.partition == "chunks":
-        tr = np.zeros((4096, 4), np.int64)
+        tr = np.zeros((4096, 6), np.int64)
         di.simulate(pol, "picard", num_chunks=chunks_of(args), seg_window=args.seg_window,
                     flags=args.flags, want_stock=False, out=act, trace=tr, max_steps=max_steps)
-        ntr = min(last["iters"], 4096)
-        ts, tr_end = tr[:ntr, 0], tr[:ntr, 1]
-        prev = np.r_[0, tr_end[:-1]]
-        pass_trace = {"prefix_us": ((ts - prev) / 1e3).round(1).tolist(),
-                      "replay_us": ((tr_end - ts) / 1e3).round(1).tolist(),
-                      "policy_calls": tr[:ntr, 2].tolist(), "units": tr[:ntr, 3].tolist()}
+        pass_trace = pass_trace_of(tr, last["iters"])
     sim_ms = statistics.median(r["sim_ms"] for r in results)
     prep_ms = statistics.median(r["prep_ms"] for r in results)
     iters = last["iters"]
@@ -934,6 +1062,17 @@ def main():
             seq_res = r
         seq_ms = statistics.median(seq_ms)
         bit_exact_gpu = bool(torch.equal(seq_act, act)) and seq_res["total_cost"] == last["total_cost"]
+    # latency of one decision by one warp (the Picard kernel's unit of sequential
+    # work): the one-warp sequential simulator on the first orders of the trajectory
+    t_dec_us = None
+    if args.partition == "chunks":
+        Tp = min(T, 16384)
+        dp = DeviceInstance(prefix_instance(inst, Tp), device=dev)
+        pact = torch.empty(Tp, dtype=torch.int8, device=dev)
+        tds = [dp.simulate(pol, "sequential", flags=pic.PIC_FLAG_TIMING, want_stock=False,
+                           out=pact)["total_ms"] for _ in range(3)]
+        t_dec_us = 1000.0 * statistics.median(tds[1:]) / Tp
+        dp.close()
 
     # end to end through host buffers: H2D of the inputs, simulate, D2H of the actions
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).pin_memory()
@@ -988,9 +1127,11 @@ def main():
     elif args.workload == "mlp_medium":
         roofline = mlp_roofline(fp32_scored(last), N, sim_ms, "k_picard_mlp (persistent, all passes)")
     elif args.workload == "capacity_large":
-        # per replayed order: product, region (4 B each), cached action read and
-        # written (1 B each); per replayed run: its start row read and its
-        # histogram row written (N x 4 B each)
+        # the method's bytes: per replayed order its record (product and region,
+        # 2 B each), its sorted position (4 B) and its cached action read and
+        # written (1 B each); per replayed run the x0 row and the lambda row of its
+        # product (N x 4 B each).  The kernel's own histogram and prefix rows are
+        # intermediates, not counted (they show in the measured traffic).
         alg_bytes = last["policy_calls"] * 10 + last["seg_replays"] * 8 * N
         achieved = alg_bytes / (sim_ms / 1000.0) / 1e9
         peak, peak_kind = load_peaks()
@@ -999,7 +1140,9 @@ def main():
                     "kernel": "k_picard_cap (persistent, all passes)", "peak_kind": peak_kind,
                     "algorithmic_bytes": alg_bytes}
     else:
-        alg_bytes = last["policy_calls"] * 6 + last["seg_replays"] * 16 * N
+        # the method's bytes (as above): 10 B per replayed order, and the x0 and
+        # lambda rows (N x 4 B each) per replayed work unit of one product
+        alg_bytes = last["policy_calls"] * 10 + last["seg_replays"] * 8 * N
         achieved = alg_bytes / (sim_ms / 1000.0) / 1e9
         peak, peak_kind = load_peaks()
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -1007,6 +1150,9 @@ def main():
                     "kernel": "k_picard_int (persistent, all passes)", "peak_kind": peak_kind,
                     "algorithmic_bytes": alg_bytes}
 
+    cp = critical_path(pass_trace, t_dec_us, sim_ms,
+                       "t_decision: one-warp sequential simulator on the first "
+                       f"{min(T, 16384)} orders") if t_dec_us else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
@@ -1021,9 +1167,10 @@ def main():
                       "step_device": t_ms / args.steps},
         "policy_calls": last["policy_calls"], "segment_replays": last["seg_replays"],
         "mlp_calls": last["mlp_calls"], "tc_decisions": last["tc_decisions"],
-        "sat_decisions": last["sat_decisions"],
+        "sat_decisions": last["sat_decisions"], "near_ties": last["near_ties"],
         "pass_trace": pass_trace,
         "roofline": roofline,
+        "critical_path": cp,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "bit_exact": bit_exact_e2e},
         "gpu_launches": int(last["launches"]) * args.steps,
@@ -1044,9 +1191,6 @@ def main():
     if rank == 0:
         print(json.dumps(line), flush=True)
     di.close()
-    if world > 1:
-        dist.barrier()
-        dist.destroy_process_group()
 
 
 if __name__ == "__main__":

@@ -155,11 +155,14 @@ typedef struct {
     int32_t seg_window;       /* tuning: orders of one product per warp work unit; 0 = 64
                                  (greedy, bid-price) or 8 (MLP policies) */
     void* stream;             /* cudaStream_t or NULL */
-    int64_t* trace;           /* PIC_MODE_PICARD: HOST [trace_cap][4] per-pass record, or NULL (the
+    int64_t* trace;           /* PIC_MODE_PICARD: HOST [trace_cap][6] per-pass record, or NULL (the
                                  other modes leave it untouched): ns from the
                                  simulation kernel's start to the end of the pass's prefix
                                  phase, ns to the end of its replay phase, policy calls in the
-                                 pass, work units replayed in the pass */
+                                 pass, work units replayed in the pass, policy calls of the
+                                 pass's largest work unit, orders walked by its longest work
+                                 unit (the last two: the pass's critical path of sequential
+                                 decisions) */
     int32_t trace_cap;        /* rows available in trace */
     int32_t max_steps;        /* PIC_MODE_PICARD on a single instance without capacity: the
                                  window of Appendix A.3, or 0 for none.  A pass evaluates the

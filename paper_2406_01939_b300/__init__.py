@@ -17,6 +17,8 @@ import ctypes as C
 import os
 import threading
 
+import numpy as np
+
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpic.so")
 
@@ -183,9 +185,12 @@ def make_policy(kind="greedy", W1=None, b1=None, W2=None, b2=None, E=None, hidde
 def make_opts(mode="picard", num_chunks=0, max_iters=0, flags=0, alpha_init=None, timeout_ns=0,
               out_mem=PIC_MEM_DEVICE, seg_window=0, stream=None, trace=None,
               max_steps=0, proc=None) -> pic_sim_opts:
-    """trace: optional host int64 numpy array [cap, 4] receiving the per-pass record;
+    """trace: optional host int64 numpy array [cap, 6] receiving the per-pass record;
     max_steps: the Picard window (0: none); proc: device int32 [T] process of each
     order (mode "assigned")."""
+    if trace is not None and (trace.dtype != np.int64 or trace.ndim != 2 or trace.shape[1] != 6
+                              or not trace.flags.c_contiguous):
+        raise ValueError("trace must be a C-contiguous int64 array of shape [cap, 6]")
     m = MODES[mode] if isinstance(mode, str) else int(mode)
     return pic_sim_opts(m, int(num_chunks), int(max_iters), int(flags), _ptr(alpha_init),
                         int(timeout_ns), int(out_mem), int(seg_window), _stream_handle(stream),
@@ -250,7 +255,17 @@ def pic_policy_grad(handle: int, policies, master, e_rows, opts: pic_sim_opts, a
 def pic_simulate_sequential_static(desc: pic_instance_desc, kind, actions_out, final_stock=None,
                                    raise_on_error=True):
     """Sequential simulation with library-owned scratch (no device allocation).
-    desc must describe DEVICE arrays.  Returns (status, total_cost, lost)."""
+    desc must describe DEVICE arrays; actions_out: CUDA int8 tensor of at least T
+    entries; final_stock: None or a CUDA int32 tensor of at least K*N entries.
+    Returns (status, total_cost, lost)."""
+    import torch
+    for name, t, dt, n in (("actions_out", actions_out, torch.int8, desc.T),
+                           ("final_stock", final_stock, torch.int32, desc.K * desc.N)):
+        if t is None and name == "final_stock":
+            continue
+        if not (torch.is_tensor(t) and t.is_cuda and t.dtype == dt and t.is_contiguous()
+                and t.numel() >= n):
+            raise ValueError(f"{name} must be a contiguous CUDA {dt} tensor of at least {n} entries")
     k = POLICY_KINDS[kind] if isinstance(kind, str) else int(kind)
     tc, lost = C.c_int64(0), C.c_int64(0)
     st = lib().pic_simulate_sequential_static(C.byref(desc), k, _ptr(actions_out),

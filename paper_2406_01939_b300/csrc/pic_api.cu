@@ -272,7 +272,7 @@ cudaError_t alloc_instance(Instance& I, int T_, int N_, int K_, int R_, bool has
     if (!e) e = dmalloc(&I.scan_blk, nscan / 2048 + 2);
     if (!e) e = dmalloc(&I.hist, (size_t)I.hist_cap);
     if (!e) e = cudaMalloc((void**)&I.ctrl, sizeof(Ctrl));
-    if (!e) e = cudaMalloc((void**)&I.trace, sizeof(long long) * 4 * kTraceCap);
+    if (!e) e = cudaMalloc((void**)&I.trace, sizeof(long long) * kTraceCols * kTraceCap);
     for (int i = 0; i < 4 && !e; ++i) e = cudaEventCreate(&I.ev[i]);
     return e;
 }
@@ -474,6 +474,11 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
             if (opts->alpha_init) {
                 CU(cudaMemcpyAsync(I.act_t, opts->alpha_init, T, cudaMemcpyDeviceToDevice, st));
                 CU(check_alpha_init(&I, I.act_t, st));
+                // an invalid cache is rejected before any pass runs on it
+                int bad = 0;
+                CU(cudaMemcpyAsync(&bad, &I.ctrl->pad0, sizeof(int), cudaMemcpyDeviceToHost, st));
+                CU(cudaStreamSynchronize(st));
+                if (bad & 64) return fail(PIC_ERR_INVALID_ARG, "alpha_init holds a value outside [-1, N)");
             } else {
                 CU(cudaMemsetAsync(I.act_t, 0xFF, T, st));  // a^phi everywhere (Alg. 1)
             }
@@ -513,7 +518,7 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
         if (T) {
             if (timing) CU(cudaEventRecord(I.ev[1], st));
             const bool trace = opts->trace && opts->trace_cap > 0;
-            if (trace) CU(cudaMemsetAsync(I.trace, 0, sizeof(long long) * 4 * kTraceCap, st));
+            if (trace) CU(cudaMemsetAsync(I.trace, 0, sizeof(long long) * kTraceCols * kTraceCap, st));
             CU(picard_cap(&I, pol, M, iters_cap, opts->flags, opts->alpha_init,
                           opts->timeout_ns ? opts->timeout_ns : 10000000000ull, trace, st));
             if (timing) CU(cudaEventRecord(I.ev[2], st));
@@ -550,7 +555,7 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
         if (T) {
             if (timing) CU(cudaEventRecord(I.ev[1], st));
             const bool trace = opts->trace && opts->trace_cap > 0;
-            if (trace) CU(cudaMemsetAsync(I.trace, 0, sizeof(long long) * 4 * kTraceCap, st));
+            if (trace) CU(cudaMemsetAsync(I.trace, 0, sizeof(long long) * kTraceCols * kTraceCap, st));
             CU(picard_run(&I, pol, iters_cap, opts->flags, opts->alpha_init,
                           opts->timeout_ns ? opts->timeout_ns : 10000000000ull, trace,
                           opts->max_steps, st));
@@ -579,7 +584,7 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
         int rows = hc.iters < opts->trace_cap ? hc.iters : opts->trace_cap;
         if (rows > kTraceCap) rows = kTraceCap;
         if (rows > 0)
-            CU(cudaMemcpy(opts->trace, I.trace, sizeof(long long) * 4 * rows, cudaMemcpyDeviceToHost));
+            CU(cudaMemcpy(opts->trace, I.trace, sizeof(long long) * kTraceCols * rows, cudaMemcpyDeviceToHost));
     }
     if (res) {
         res->total_cost = hc.total_cost;

@@ -372,7 +372,7 @@ pic_status enqueue_picard(Instance& I, const CallCfg& c, cudaStream_t st) {
     BCU(build_lpt(&I, bt->pol, kMlpLptWeight, st));
     BCU(init_cache(I, c.alpha_init, st));
     if (c.has_mlp) BCU(mlp_prepare(&I, &c.mlp, st));
-    if (c.trace) BCU(cudaMemsetAsync(I.trace, 0, sizeof(long long) * 4 * kTraceCap, st));
+    if (c.trace) BCU(cudaMemsetAsync(I.trace, 0, sizeof(long long) * kTraceCols * kTraceCap, st));
     KArgs a;
     a.T = I.T; a.N = I.N; a.K = I.K; a.NP = I.NP; a.R = I.R;
     a.reg_s = I.reg_s; a.run_start = I.run_start; a.seg_run = I.seg_run;
@@ -792,7 +792,7 @@ pic_status pic_simulate_batch(pic_instance* h, const pic_policy* pols, const pic
         int rows = passes < opts->trace_cap ? passes : opts->trace_cap;
         if (rows > kTraceCap) rows = kTraceCap;
         if (rows > 0)
-            BCU(cudaMemcpy(opts->trace, I.trace, sizeof(long long) * 4 * rows, cudaMemcpyDeviceToHost));
+            BCU(cudaMemcpy(opts->trace, I.trace, sizeof(long long) * kTraceCols * rows, cudaMemcpyDeviceToHost));
     }
     if (traj) {
         for (int b = 0; b < B; ++b) {

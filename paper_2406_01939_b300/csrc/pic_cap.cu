@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(kCapWarps * 32) k_picard_cap(KArgs a, CapArgs 
     bool ok = true, converged = false;
     for (; it <= a.max_iters; ++it) {
         const int parity = it & 1;
-        long long* tr = (a.trace && it <= kTraceCap) ? a.trace + 4 * (it - 1) : nullptr;
+        long long* tr = (a.trace && it <= kTraceCap) ? a.trace + kTraceCols * (it - 1) : nullptr;
         const unsigned long long calls0 = calls, replays0 = replays;
         const int* fc_prev = a.fc + (size_t)(parity ^ 1) * a.K;
         int* fc_cur = a.fc + (size_t)parity * a.K;
@@ -419,6 +419,7 @@ __global__ void __launch_bounds__(kCapWarps * 32) k_picard_cap(KArgs a, CapArgs 
         if (tr && gtid == 0) tr[0] = (long long)(globaltimer_ns() - t_start);
         // ---- phase C
         bool chg = false;
+        unsigned long long ucalls = 0;  // largest chunk of this warp (policy calls, lane 0)
         for (int m = gwarp; m < c.M; m += nwarps) {
             const int lo = m * c.L;
             const int hi = min(a.T, lo + c.L);
@@ -431,12 +432,16 @@ __global__ void __launch_bounds__(kCapWarps * 32) k_picard_cap(KArgs a, CapArgs 
                 continue;
             }
             const bool rep = lo > f_prev;
+            const unsigned long long cu0 = calls;
             chg |= cap_chunk<NPL, DUAL>(a, c, m, it, rep, tag, deadline, rows, s_run[wib], s_k[wib],
                                         fc_cur, parity, calls, replays);
+            if (calls - cu0 > ucalls) ucalls = calls - cu0;
         }
         if (tr && lane == 0 && replays != replays0) {
             atomicAdd((unsigned long long*)&tr[2], calls - calls0);
             atomicAdd((unsigned long long*)&tr[3], replays - replays0);
+            atomicMax((unsigned long long*)&tr[4], ucalls);
+            atomicMax((unsigned long long*)&tr[5], (unsigned long long)c.L);
         }
         if (chg && lane == 0) s_changed = 1;
         __syncthreads();

@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(kGrpThreads, 1) k_picard_grp(KArgs a, int NP8)
     bool ok = true, converged = false;
     for (; it <= a.max_iters; ++it) {
         const int parity = it & 1;
-        long long* tr = (a.trace && it <= kTraceCap) ? a.trace + 4 * (it - 1) : nullptr;
+        long long* tr = (a.trace && it <= kTraceCap) ? a.trace + kTraceCols * (it - 1) : nullptr;
         const unsigned long long calls0 = calls, replays0 = replays;
         const int* fc_prev = a.fc + (size_t)(parity ^ 1) * a.K;
         int* fc_cur = a.fc + (size_t)parity * a.K;

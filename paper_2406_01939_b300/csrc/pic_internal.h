@@ -16,6 +16,7 @@ constexpr int kSuperBlock = 32;    // segments per carry super-block
 constexpr int kThreads = 256;      // threads per CTA of the persistent kernels
 constexpr size_t kSmemCostMax = 200 * 1024;  // largest int16 cost table staged in shared memory
 constexpr int kTraceCap = 4096;    // passes recorded by the device-side trace
+constexpr int kTraceCols = 6;      // int64 fields per recorded pass (see pic_sim_opts.trace)
 constexpr int kLenBuckets = 1024;  // segment-length buckets of the longest-first order
 constexpr size_t kGrpSmemMax = 150 * 1024;  // cost table budget of the group-per-segment kernel
 constexpr int kMlpLptWeight = 64;  // work of an MLP order relative to an integer-policy order

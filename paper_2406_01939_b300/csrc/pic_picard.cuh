@@ -276,7 +276,8 @@ __device__ __forceinline__ void chain_prefixes(const KArgs& a, int it, const int
 //            2W+w, ...), examined 32 at a time per warp, and
 //            replay(seg, meta, fcp, fc_cur, it) replays one of them and returns
 //            whether it changed a cached action (warp-uniform; it adds its
-//            policy calls to `calls` on lane 0);
+//            policy calls to `calls` on lane 0); the trace records the pass's
+//            largest unit (policy calls, orders walked), its critical path;
 // separated by grid barriers.  The loop ends at the first pass that changes no
 // cached action (line 13 of Algorithm 1), or after max_iters passes.
 // GROUP > 1: work units go to groups of GROUP consecutive warps of a CTA (each
@@ -313,7 +314,7 @@ __device__ __forceinline__ void picard_passes(const KArgs& a, unsigned long long
     int whi = win ? (int)min((long long)a.M, ((long long)a.win_steps + a.L - 1) / a.L) : INT_MAX;
     for (; it <= a.max_iters; ++it) {
         const int parity = it & 1;
-        long long* tr = (a.trace && it <= kTraceCap) ? a.trace + 4 * (it - 1) : nullptr;
+        long long* tr = (a.trace && it <= kTraceCap) ? a.trace + kTraceCols * (it - 1) : nullptr;
         const unsigned long long calls0 = calls, replays0 = replays;
         const int* fc_prev = a.fc + (size_t)(parity ^ 1) * a.K;
         int* fc_cur = a.fc + (size_t)parity * a.K;
@@ -332,6 +333,7 @@ __device__ __forceinline__ void picard_passes(const KArgs& a, unsigned long long
         if (tr && gtid == 0) tr[0] = (long long)(globaltimer_ns() - t_start);
         // ---- phase R
         bool chg = false;
+        unsigned long long ucalls = 0, uorders = 0;  // largest unit of this warp (lane 0)
         const int unit = gwarp / GROUP, nunits = nwarps / GROUP;
         for (int j0 = 0; j0 * nunits < nseg; j0 += 32) {
             const int j = j0 + lane;
@@ -358,14 +360,19 @@ __device__ __forceinline__ void picard_passes(const KArgs& a, unsigned long long
                 todo &= todo - 1;
                 const SegMeta mm = smem_meta(&s_meta[wib][src]);
                 const int seg = __shfl_sync(kFull, sl, src);
+                const unsigned long long cu0 = calls;
                 chg |= replay(seg, mm, s_fcp[wib][src], fc_cur, it);
                 if (wib % GROUP == 0) replays += 1;
+                if (calls - cu0 > ucalls) ucalls = calls - cu0;
+                if ((unsigned long long)(mm.jend - mm.j0) > uorders) uorders = mm.jend - mm.j0;
             }
             __syncwarp();
         }
         if (tr && lane == 0 && replays != replays0) {
             atomicAdd((unsigned long long*)&tr[2], calls - calls0);
             atomicAdd((unsigned long long*)&tr[3], replays - replays0);
+            atomicMax((unsigned long long*)&tr[4], ucalls);
+            atomicMax((unsigned long long*)&tr[5], uorders);
         }
         if (chg && lane == 0) s_changed = 1;  // one global write per CTA, below
         __syncthreads();

@@ -15,10 +15,18 @@
 // device address: on the first call on each device (with that device current)
 // cudaGetSymbolAddress translates it once, and the translated pointer is what
 // the kernels receive.  That first call should therefore come before any stream
-// capture on the device.  Every call shares the one array and leaves the last
-// call's contents in it; the parts that must start at zero are cleared at the
-// start of each call.  Two calls whose work overlaps on the same GPU (different
-// streams or threads) race on the array.
+// capture on the device.  Every call synchronizes its stream before it returns.
+// Every call shares the one array and leaves the last call's contents in it;
+// the parts that must start at zero are cleared at the start of each call.  Two
+// calls whose work overlaps on the same GPU (different streams or threads) race
+// on the array.
+//
+// The kernels read and write the caller's arrays directly, so every pointer is
+// checked on the host before the first launch: it must be device memory of the
+// current device (or managed memory), and the bytes the call touches must lie
+// inside the allocation that holds it (cuMemGetAddressRange, reached through
+// the runtime's driver entry point).  A host pointer, another device's pointer
+// or a short array is INVALID_ARG, never a fault.
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -72,6 +80,51 @@ pic_status cuda_fail(cudaError_t e, const char* what) {
     return record_error(PIC_ERR_CUDA, msg);
 }
 
+// cuMemGetAddressRange (driver API): base and size of the allocation holding a
+// device address.  Resolved once; null when the driver does not provide it.
+typedef int (*AddressRangeFn)(unsigned long long* base, size_t* size, unsigned long long ptr);
+
+AddressRangeFn address_range_fn() {
+    static std::once_flag once;
+    static AddressRangeFn fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<AddressRangeFn>(p);
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// Whether `bytes` bytes at p are device (or managed) memory that device `dev`
+// may access: the pointer's memory type and device, then the extent of its
+// allocation.  bytes == 0 accepts any pointer (nothing is touched).
+bool device_range_ok(const void* p, size_t bytes, int dev) {
+    if (bytes == 0) return true;
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (at.type == cudaMemoryTypeDevice) {
+        if (at.device != dev) return false;
+    } else if (at.type != cudaMemoryTypeManaged) {
+        return false;
+    }
+    if (AddressRangeFn fn = address_range_fn()) {
+        unsigned long long base = 0;
+        size_t size = 0;
+        const unsigned long long a = (unsigned long long)(uintptr_t)p;
+        if (fn(&base, &size, a) != 0) return false;
+        if (a < base || bytes > size || a - base > size - bytes) return false;
+    }
+    return true;
+}
+
 }  // namespace
 
 extern "C" pic_status pic_simulate_sequential_static(const pic_instance_desc* d, int32_t kind,
@@ -105,6 +158,23 @@ extern "C" pic_status pic_simulate_sequential_static(const pic_instance_desc* d,
     if (e) return cuda_fail(e, "cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices)
         return record_error(PIC_ERR_UNSUPPORTED, "pic_simulate_sequential_static: device index too large");
+    {
+        const size_t T = (size_t)d->T, KN4 = (size_t)d->K * d->N * 4;
+        struct { const void* p; size_t bytes; const char* name; } arrays[] = {
+            {d->prod, 4 * T, "prod"}, {d->reg, 4 * T, "reg"}, {d->x0, KN4, "x0"},
+            {d->cost, (size_t)d->R * d->N * 4, "cost"},
+            {d->lam, kind == PIC_POLICY_DUAL ? KN4 : 0, "lam"},
+            {actions_out, T, "actions_out"}, {final_stock, final_stock ? KN4 : 0, "final_stock"}};
+        for (const auto& x : arrays)
+            if (!device_range_ok(x.p, x.bytes, dev)) {
+                char msg[200];
+                snprintf(msg, sizeof(msg),
+                         "pic_simulate_sequential_static: %s is not %zu bytes of device memory of "
+                         "the current device",
+                         x.name, x.bytes);
+                return record_error(PIC_ERR_INVALID_ARG, msg);
+            }
+    }
     void* base = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_addr_mu);

@@ -192,10 +192,11 @@ def test_dual_large_full_size(M):
 
 def test_pass_trace_records_every_pass():
     """The per-pass trace has one row per pass: increasing timestamps, and its
-    policy-call column sums to the call's total."""
+    policy-call column sums to the call's total; the largest unit of a pass made
+    at most the pass's calls and walked at least its own calls' orders."""
     inst = synth.greedy_small(5)
     d = DeviceInstance(inst)
-    tr = np.zeros((100, 4), np.int64)
+    tr = np.zeros((100, 6), np.int64)
     got = d.simulate(Policy("greedy"), num_chunks=64, trace=tr)
     n = got["iters"]
     assert (tr[n:] == 0).all()
@@ -204,3 +205,5 @@ def test_pass_trace_records_every_pass():
     assert tr[:n, 2].sum() == got["policy_calls"]
     assert tr[:n, 3].sum() == got["seg_replays"]
     assert tr[0, 2] == inst.T  # every order is evaluated in the first pass
+    assert (tr[:n, 4] <= tr[:n, 2]).all() and (tr[:n, 4] <= tr[:n, 5]).all()
+    assert ((tr[:n, 4] > 0) == (tr[:n, 2] > 0)).all()

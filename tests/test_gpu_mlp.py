@@ -70,23 +70,24 @@ def test_picard_mlp_windows_and_chunk_counts():
             assert got["iters"] == want["iters"]
 
 
-def test_mlp_full_size_sampled_against_oracle():
-    """T=2^18, N=64, K=2,000, R=500 MLP workload: the Picard fixed point equals the
-    GPU sequential simulation, and at sampled orders the oracle's decision from
-    the state implied by the GPU path's earlier actions is the GPU's action."""
+def test_mlp_full_size_whole_trajectory_against_oracle():
+    """T=2^18, N=64, K=2,000, R=500 MLP workload, the whole trajectory against
+    the oracle's sequential simulation (every action, final stock, cost, lost
+    count): Picard in the benchmark's configuration (4,096 chunks, max_steps
+    window of 16,384 orders, segment window 4) and with 1,024 chunks, and the GPU
+    sequential simulator with one warp and with four warps per decision."""
     inst, mlp = synth.mlp_medium(0)
     d = DeviceInstance(inst)
     pol = Policy("mlp", mlp=mlp)
-    got = d.simulate(pol, "picard", num_chunks=1024)
-    seq = d.simulate(pol, "sequential")
-    a = got["actions"].cpu().numpy()
-    assert torch.equal(got["actions"], seq["actions"])
-    assert got["total_cost"] == seq["total_cost"]
-    rng = np.random.default_rng(0)
-    for t in np.concatenate([rng.integers(0, inst.T, 24), [0, inst.T - 1]]):
-        row = oracle.state_before(inst, a, int(t))
-        want = oracle.policy_call(inst, pol, row, inst.prod[t], inst.reg[t], int(t))
-        assert want == a[t], (t, want, a[t])
+    want = oracle.seq_sim(inst, pol)
+    runs = [d.simulate(pol, "picard", num_chunks=4096, max_steps=16384, seg_window=4),
+            d.simulate(pol, "picard", num_chunks=1024),
+            d.simulate(pol, "sequential"),
+            d.simulate(pol, "sequential", flags=pic.PIC_FLAG_WARP_GROUP)]
+    for got in runs:
+        np.testing.assert_array_equal(got["actions"].cpu().numpy(), want["actions"])
+        np.testing.assert_array_equal(got["final_stock"].cpu().numpy(), want["x_final"])
+        assert got["total_cost"] == want["total_cost"] and got["lost"] == want["lost"]
 
 
 @pytest.mark.parametrize("N", [24, 32, 64])

@@ -251,17 +251,21 @@ def test_infeasible_paths_rejected():
 
 def test_full_size_trajectory_gradient():
     """One trajectory of the policy-gradient shape (T=2^20, N=64, K=10,000,
-    R=1,000, Gumbel MLP): paths equal the oracle's decisions at sampled orders
+    R=1,000, Gumbel MLP): the path's first 2^18 orders equal the oracle's
+    sequential simulation of those orders (a prefix of the path depends only on
+    the orders before it), the whole path equals the GPU sequential simulator's,
     and the gradient matches the FP64 oracle gradient along the GPU paths."""
     insts, mlp = synth.pg_large(0, B=1)
     inst = insts[0]
     pol = Policy("gumbel", mlp=mlp, seed=77, traj=0)
     db, rf, m, acts, J, J2, g = run_gpu([inst], [pol], mlp, num_chunks=0)
     a = acts.cpu().numpy()
-    rng = np.random.default_rng(0)
-    for t in np.concatenate([rng.integers(0, inst.T, 12), [inst.T - 1]]):
-        row = oracle.state_before(inst, a, int(t))
-        assert oracle.policy_call(inst, pol, row, inst.prod[t], inst.reg[t], int(t)) == a[t]
+    Tp = 1 << 18
+    pre = synth.Instance(Tp, inst.N, inst.K, inst.R, inst.prod[:Tp].copy(), inst.reg[:Tp].copy(),
+                         inst.x0, inst.cost, inst.lam)
+    np.testing.assert_array_equal(a[:Tp], oracle.seq_sim(pre, pol)["actions"])
+    seq = db.simulate([pol], "sequential")
+    np.testing.assert_array_equal(seq["actions"].cpu().numpy(), a)
     Jw, gw = pg.surrogate(inst, pg.bf16_params_f64(mlp), a)
     assert abs(J - Jw) <= 1e-5 * abs(Jw)
     # 2.7e8 hidden pre-activations: a few lie within FP32 rounding of 0, where the

@@ -102,12 +102,30 @@ enum {
                                   on a pass's critical path; same operations in the same
                                   order, so the same actions; no tensor-core tiles.  Applies
                                   to the sequential mode as well */
-    PIC_FLAG_NO_SAT = 128      /* MLP policies: evaluate the network for every decision.  By
+    PIC_FLAG_NO_SAT = 128,     /* MLP policies: evaluate the network for every decision.  By
                                   default a decision whose product holds at least 32 units at
                                   every warehouse (every stock feature min(x,32)/32 equals 1)
                                   takes its FP32 scores from a per-region table computed at
                                   the start of the call by the same scorer in the same
                                   operation order, so the actions are the same */
+    PIC_FLAG_WAVE = 512,       /* MLP policies with N <= 64 (pic_simulate,
+                                  pic_simulate_batch, pic_policy_grad):
+                                  replay the work units in CTA-wide waves, one unit per thread
+                                  of 128, every pending decision of a wave scored at once on
+                                  the tensor cores (tcgen05, BF16 operands with FP32
+                                  accumulation) and kept when its top-2 margin exceeds twice
+                                  a bound on the difference from the reference FP32 order,
+                                  else re-scored by the FP32 scorer; the actions are the same.
+                                  A wave with at most 16 network decisions runs them on the
+                                  FP32 scorer instead (one warp each); with PIC_FLAG_TC every
+                                  wave uses the tensor cores, with PIC_FLAG_NO_TC none does.
+                                  Greedy and bid-price trajectories of a batch, and
+                                  saturated-state decisions, are decided in the same waves.
+                                  The work units are single runs (segment window 1).
+                                  Ignored where it does not apply.  pic_simulate_batch and
+                                  pic_policy_grad with num_chunks = 0 time this kernel as
+                                  one of the autotuner's choices */
+    PIC_FLAG_NO_WAVE = 1024    /* exclude the wave kernel from the autotuner's choices */
 };
 
 typedef struct pic_instance pic_instance;

@@ -29,7 +29,7 @@ PIC_MODE_PICARD, PIC_MODE_SEQUENTIAL, PIC_MODE_PICARD_PRODUCTS, PIC_MODE_PICARD_
 PIC_MEM_HOST, PIC_MEM_DEVICE = 0, 1
 PIC_FLAG_NO_RESET, PIC_FLAG_REUSE_TABLES, PIC_FLAG_TIMING, PIC_FLAG_GROUP_KERNEL = 1, 2, 4, 8
 PIC_FLAG_GRAPH, PIC_FLAG_NO_TC, PIC_FLAG_TC, PIC_FLAG_NO_SAT = 16, 32, 64, 128
-PIC_FLAG_WARP_GROUP = 256
+PIC_FLAG_WARP_GROUP, PIC_FLAG_WAVE, PIC_FLAG_NO_WAVE = 256, 512, 1024
 
 POLICY_KINDS = {"greedy": PIC_POLICY_GREEDY, "dual": PIC_POLICY_DUAL, "mlp": PIC_POLICY_MLP,
                 "gumbel": PIC_POLICY_GUMBEL}

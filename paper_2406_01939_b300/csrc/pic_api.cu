@@ -533,7 +533,9 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
         if (T && M > (int)T) M = (int)T;
         // default window: long work units amortise the cheap integer policy; the MLP
         // policy's per-order cost makes short units (short critical paths) better
-        const int W = opts->seg_window ? opts->seg_window : (mlp ? kSegWindowMlp : kSegWindow);
+        // the wave kernel takes one run per work unit
+        const bool wave = mlp && (opts->flags & PIC_FLAG_WAVE) && wave_applies(&I);
+        const int W = wave ? 1 : opts->seg_window ? opts->seg_window : (mlp ? kSegWindowMlp : kSegWindow);
         // the window needs at most two passes per block (one change, one confirmation)
         iters_cap = opts->max_iters ? opts->max_iters : (opts->max_steps > 0 ? 2 * M + 2 : M + 1);
         CU(prepare_picard_state(I, W, iters_cap, st));

@@ -34,6 +34,19 @@ namespace {
 using namespace pic::picard;
 using namespace pic::mlp;
 
+}  // namespace
+
+namespace pic {
+cudaError_t picard_wave_batch(Instance* I, const KArgs& a, const MlpPolicy& p,
+                              const int32_t* traj_of_prod, const BatchPol* pol, const int32_t* toff,
+                              int32_t* last_chg, cudaStream_t st);
+}  // namespace pic
+
+namespace {
+
+using namespace pic::picard;
+using namespace pic::mlp;
+
 // ---------------------------------------------------------------------------- creation kernels
 // Owner of global index i in an offset table off[0..B] (off[0] = 0, non-
 // decreasing, off[B] > i): the largest b < B with off[b] <= i, which skips
@@ -398,7 +411,10 @@ pic_status enqueue_picard(Instance& I, const CallCfg& c, cudaStream_t st) {
     ba.perm = I.perm;
     ba.last_chg = bt->last_chg;
     ba.has_mlp = c.has_mlp ? 1 : 0;
-    BCU(batch_dispatch(&I, c.shape, c.tc && I.N <= 64, a, p, ba, st));
+    if (c.has_mlp && (c.flags & PIC_FLAG_WAVE) && wave_applies(&I) && c.W == 1)  // one run per unit
+        BCU(picard_wave_batch(&I, a, p, ba.traj_of_prod, ba.pol, ba.toff, ba.last_chg, st));
+    else
+        BCU(batch_dispatch(&I, c.shape, c.tc && I.N <= 64, a, p, ba, st));
     BCU(scatter_actions(&I, st));
     I.launches += 1;
     k_traj_reduce<<<B, kReduceThreads, 0, st>>>(I.act_t, I.reg, I.cost, I.N, bt->toff, bt->tres, I.ctrl);
@@ -475,15 +491,17 @@ pic_status autotune(Instance& I, CallCfg& c, cudaStream_t st) {
         c.W = bt->tune_w;
         c.shape = bt->tune_shape;
         c.tc = bt->tune_tc != 0;
+        if (bt->tune_wave) c.flags |= PIC_FLAG_WAVE;
         return PIC_OK;
     }
     const int max_t = bt->max_t > 0 ? bt->max_t : 1;
-    auto trial = [&](int M, int W, int shape, bool tc, float* ms) -> pic_status {
+    auto trial = [&](int M, int W, int shape, bool tc, bool wv, float* ms) -> pic_status {
         CallCfg t = c;
         t.M = M;
         t.W = W;
         t.shape = shape;
         t.tc = tc;
+        if (wv) t.flags |= PIC_FLAG_WAVE;
         t.iters_cap = (M < max_t ? M : max_t) + 1;
         t.trace = false;
         pic_status s = run_picard(I, t, false, st);
@@ -495,46 +513,62 @@ pic_status autotune(Instance& I, CallCfg& c, cudaStream_t st) {
         BCU(cudaEventElapsedTime(ms, I.ev[1], I.ev[2]));
         return PIC_OK;
     };
+    // the wave kernel (one run per unit, one CTA shape, no tiles): forced by
+    // PIC_FLAG_WAVE, excluded by PIC_FLAG_NO_WAVE, otherwise a tuning choice
+    const bool wave_ok = c.has_mlp && wave_applies(&I) && !(c.flags & PIC_FLAG_NO_WAVE);
+    const bool wave_forced = wave_ok && (c.flags & PIC_FLAG_WAVE);
     const int w_def = c.has_mlp ? kSegWindowMlp : kSegWindow;
     // tensor-core tiles are a tuning choice unless a flag fixes them
-    const bool tc_free = c.has_mlp && I.N <= 64 && !(c.flags & (PIC_FLAG_TC | PIC_FLAG_NO_TC));
-    bool bestT = c.tc;
+    const bool tc_free = !wave_forced && c.has_mlp && I.N <= 64 &&
+                         !(c.flags & (PIC_FLAG_TC | PIC_FLAG_NO_TC));
+    bool bestT = c.tc, bestWave = false;
     int bestM = 0, bestW = w_def, bestS = kDefaultShape;
     float best = 3.4e38f;
-    for (int M = 4; M <= 1024; M *= 2) {
+    for (int M = 4; M <= 1024 && !wave_forced; M *= 2) {
         if (M > 4 && M / 2 >= max_t) break;  // larger M only repeats min(M, T_b) = T_b
         for (int tcv = 0; tcv < (tc_free ? 2 : 1); ++tcv) {
             const bool tc = tc_free ? tcv == 1 : c.tc;
             float ms;
-            pic_status s = trial(M, w_def, kDefaultShape, tc, &ms);
+            pic_status s = trial(M, w_def, kDefaultShape, tc, false, &ms);
             if (s != PIC_OK) return s;
             if (ms < best) { best = ms; bestM = M; bestT = tc; }
         }
     }
-    for (int sh = 0; sh < kNumShapes; ++sh) {
+    for (int sh = 0; sh < kNumShapes && !wave_forced; ++sh) {
         if (sh == kDefaultShape) continue;
         float ms;
-        pic_status s = trial(bestM, w_def, sh, bestT, &ms);
+        pic_status s = trial(bestM, w_def, sh, bestT, false, &ms);
         if (s != PIC_OK) return s;
         if (ms < best) { best = ms; bestS = sh; }
     }
     const int wins_mlp[] = {4, 16, 32}, wins_int[] = {16, 32, 128};
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 3 && !wave_forced; ++i) {
         const int W = c.has_mlp ? wins_mlp[i] : wins_int[i];
         float ms;
-        pic_status s = trial(bestM, W, bestS, bestT, &ms);
+        pic_status s = trial(bestM, W, bestS, bestT, false, &ms);
         if (s != PIC_OK) return s;
         if (ms < best) { best = ms; bestW = W; }
+    }
+    if (wave_ok) {
+        for (int M = 4; M <= 4096; M *= 4) {
+            if (M > 4 && M / 4 >= max_t) break;
+            float ms;
+            pic_status s = trial(M, 1, kDefaultShape, bestT, true, &ms);
+            if (s != PIC_OK) return s;
+            if (ms < best) { best = ms; bestM = M; bestW = 1; bestWave = true; }
+        }
     }
     bt->tune_sig = sig;
     bt->tune_m = bestM;
     bt->tune_w = bestW;
     bt->tune_shape = bestS;
     bt->tune_tc = bestT ? 1 : 0;
+    bt->tune_wave = bestWave ? 1 : 0;
     c.M = bestM;
     c.W = bestW;
     c.shape = bestS;
     c.tc = bestT;
+    if (bestWave) c.flags |= PIC_FLAG_WAVE;
     return PIC_OK;
 }
 
@@ -763,12 +797,13 @@ pic_status pic_simulate_batch(pic_instance* h, const pic_policy* pols, const pic
         c.timeout_ns = opts->timeout_ns ? opts->timeout_ns : 60000000000ull;
         c.shape = kDefaultShape;
         c.W = opts->seg_window ? opts->seg_window : (c.has_mlp ? kSegWindowMlp : kSegWindow);
+        if (c.has_mlp && (c.flags & PIC_FLAG_WAVE) && wave_applies(&I)) c.W = 1;  // one run per unit
         if (opts->num_chunks) {
             c.M = opts->num_chunks;
         } else {
             pic_status s = autotune(I, c, st);
             if (s != PIC_OK) return s;
-            if (opts->seg_window) c.W = opts->seg_window;
+            if (opts->seg_window && !(c.flags & PIC_FLAG_WAVE)) c.W = opts->seg_window;
         }
         const int maxM = c.M < bt->max_t ? c.M : (bt->max_t > 0 ? bt->max_t : 1);
         c.iters_cap = opts->max_iters ? opts->max_iters : maxM + 1;

@@ -97,7 +97,7 @@ struct Batch {
     cudaStream_t cap_stream;
     // autotuner result and the policy signature it was tuned for
     unsigned long long tune_sig;
-    int tune_m, tune_w, tune_shape, tune_tc;
+    int tune_m, tune_w, tune_shape, tune_tc, tune_wave;
 };
 
 struct PgState;  // buffers of the policy gradient (pic_pg.cu)
@@ -208,6 +208,10 @@ cudaError_t finish_outputs(Instance* I, cudaStream_t st);
 cudaError_t picard_run(Instance* I, const pic_policy* pol, int max_iters, int flags,
                        const int8_t* alpha_init, unsigned long long timeout_ns, bool trace,
                        int max_steps, cudaStream_t st);
+// Wave kernel (pic_wave.cu): MLP decisions in CTA-wide tensor-core waves
+// (N <= 64); its work units are single runs (segment window 1).
+bool wave_applies(const Instance* I);
+
 // MLP policies (pic_mlp.cu).  mlp_prepare evaluates the per-region chain
 // prefix (E rows through reg_local for a batch) and the FP32 weight copies.
 cudaError_t mlp_alloc(Instance* I);

@@ -276,8 +276,12 @@ cudaError_t sequential_mlp(Instance* I, const pic_policy* pol, int flags, cudaSt
     return sw ? launch_seq_mlp<4, true>(I, p, st) : launch_seq_mlp<4, false>(I, p, st);
 }
 
+cudaError_t picard_wave(Instance* I, const KArgs& a, const MlpPolicy& p, cudaStream_t st);
+
 cudaError_t picard_mlp(Instance* I, const KArgs& a, const pic_policy* pol, cudaStream_t st) {
     const MlpPolicy p = make_policy_view(I, pol, a.flags);
+    if ((a.flags & PIC_FLAG_WAVE) && wave_applies(I) && I->tables_w == 1)  // one run per unit
+        return picard_wave(I, a, p, st);
     // the packed weights fit in shared memory for every N <= 127; tiles need N <= 64
     const bool tc = (a.flags & PIC_FLAG_NO_TC) == 0 && I->N <= 64;
     const int npl = (I->N + 31) / 32;

@@ -126,6 +126,9 @@ struct MlpPolicy {
     const float* __restrict__ bnd;
     // c2[n] = sum_j |W2[j][n]| rounded up (bound of the fast layer-2 order)
     const float* __restrict__ c2;
+    // the caller's BF16 weights W1 [2N+16][H] and W2 [H][N] (tensor-core operands)
+    const uint16_t* __restrict__ W1raw;
+    const uint16_t* __restrict__ W2raw;
     // [R][N] FP32 scores (before the Gumbel term) of the saturated state, where
     // every warehouse holds at least 32 units (every stock feature is 1), in the
     // reference order; null: evaluate every decision
@@ -981,6 +984,8 @@ inline MlpPolicy make_policy_view(const Instance* I, const pic_policy* pol, int 
     p.Emax = I->mlp_Emax;
     p.bnd = I->mlp_bnd;
     p.c2 = I->mlp_c2;
+    p.W1raw = static_cast<const uint16_t*>(pol->W1);
+    p.W2raw = static_cast<const uint16_t*>(pol->W2);
     p.sat = (flags & PIC_FLAG_NO_SAT) ? nullptr : I->mlp_sat;
     p.gumbel = pol->kind == PIC_POLICY_GUMBEL;
     p.seed = pol->seed;

@@ -283,13 +283,20 @@ __device__ __forceinline__ void chain_prefixes(const KArgs& a, int it, const int
 // GROUP > 1: work units go to groups of GROUP consecutive warps of a CTA (each
 // warp of a group walks the same candidates and calls replay for the same
 // segment; the replay shares its decisions); the group's first warp counts.
-template <int NPL, int WARPS, class Replay, int GROUP = 1>
+// CTA: phase R is one call for the whole CTA, replay(fc_prev, fc_cur, it, whi,
+// wprev, replays, ucalls, uorders), which deals the pass's work units itself
+// and returns whether it changed a cached action (CTA-uniform); its counts are
+// kept by thread 0 (calls, replays, the largest unit's calls and orders), and
+// phase S stages its segments in ext_meta / ext_fcp (WARPS x 32 entries, e.g.
+// dynamic shared memory that phase R uses otherwise).
+template <int NPL, int WARPS, class Replay, int GROUP = 1, bool CTA = false>
 __device__ __forceinline__ void picard_passes(const KArgs& a, unsigned long long& calls,
-                                              Replay&& replay) {
+                                              Replay&& replay, SegMeta* ext_meta = nullptr,
+                                              int* ext_fcp = nullptr) {
     __shared__ int s_changed;
     // per warp: the 32 segments it is examining (metadata, previous-pass first change)
-    __shared__ SegMeta s_meta[WARPS][32];
-    __shared__ int s_fcp[WARPS][32];
+    __shared__ SegMeta s_meta[CTA ? 1 : WARPS][32];
+    __shared__ int s_fcp[CTA ? 1 : WARPS][32];
     const int lane = lane_id();
     const int wib = threadIdx.x >> 5;
     const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -327,14 +334,18 @@ __device__ __forceinline__ void picard_passes(const KArgs& a, unsigned long long
             a.ctrl->win_hi_prev = wprev;
         }
         if (it > 1 || a.first_dirty)
-            chain_prefixes<NPL>(a, it, fc_prev, tag_base + (unsigned)it, deadline, s_meta[wib],
-                                s_fcp[wib]);
+            chain_prefixes<NPL>(a, it, fc_prev, tag_base + (unsigned)it, deadline,
+                                CTA ? ext_meta + 32 * wib : s_meta[wib],
+                                CTA ? ext_fcp + 32 * wib : s_fcp[wib]);
         if (!grid_sync(a.ctrl, deadline)) { ok = false; break; }
         if (tr && gtid == 0) tr[0] = (long long)(globaltimer_ns() - t_start);
         // ---- phase R
         bool chg = false;
         unsigned long long ucalls = 0, uorders = 0;  // largest unit of this warp (lane 0)
         const int unit = gwarp / GROUP, nunits = nwarps / GROUP;
+        if constexpr (CTA) {
+            chg = replay(fc_prev, fc_cur, it, whi, wprev, replays, ucalls, uorders);
+        } else {
         for (int j0 = 0; j0 * nunits < nseg; j0 += 32) {
             const int j = j0 + lane;
             const int pos = j * nunits + ((j & 1) ? nunits - 1 - unit : unit);
@@ -367,6 +378,7 @@ __device__ __forceinline__ void picard_passes(const KArgs& a, unsigned long long
                 if ((unsigned long long)(mm.jend - mm.j0) > uorders) uorders = mm.jend - mm.j0;
             }
             __syncwarp();
+        }
         }
         if (tr && lane == 0 && replays != replays0) {
             atomicAdd((unsigned long long*)&tr[2], calls - calls0);
@@ -413,6 +425,8 @@ __device__ __forceinline__ void picard_passes(const KArgs& a, unsigned long long
 
 // MLP Picard kernel (pic_mlp.cu).
 cudaError_t picard_mlp(Instance* I, const picard::KArgs& a, const pic_policy* pol, cudaStream_t st);
+
+
 
 // Group-per-segment Picard kernel (pic_grp.cu).
 int grp_lanes(int N);

@@ -87,6 +87,10 @@ def parse():
     p.add_argument("--workload", default="dual_large",
                    choices=["dual_large", "greedy_small", "mlp_medium", "batch_uneven",
                             "pg_large", "capacity_large", "owmr_base"])
+    p.add_argument("--shard", default="none", choices=["none", "products"],
+                   help="single-trajectory workloads under torchrun: products (one trajectory's "
+                        "products over the ranks, balanced by demand; strong scaling) or none "
+                        "(every rank its own trajectory; weak scaling)")
     p.add_argument("--chunk-sweep", default="",
                    help="comma-separated chunk counts: one JSON line per count (single-trajectory "
                         "workloads), e.g. 256,1024,4096,16384,65536")
@@ -659,6 +663,9 @@ def run_pg(args, dev, world, rank):
         e2 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         J, res = rf.step(master, grad, actions_out=acts)
+        if world > 1:  # each rank holds its own trajectories: the batch's gradient and J
+            from paper_2406_01939_b300.shard import gradient_all_reduce
+            _, J = gradient_all_reduce(grad, J, device=dev)
         e2.record(stream)
         return J, res, (e0, e2)
 
@@ -982,7 +989,16 @@ def run_single(args, dev, world, rank):
     from paper_2406_01939_b300 import synth as synth_mod
     from paper_2406_01939_b300.session import DeviceInstance, DevicePolicy
 
-    inst, hpol, _ = make_workload(args, rank_seed(args.seed, rank))
+    sharded = args.shard == "products"
+    if sharded and (getattr(args, "partition", "chunks") != "chunks" or args.workload == "capacity_large"):
+        raise SystemExit("--shard products: contiguous chunks, no node capacity")
+    # sharded: every rank builds the same trajectory and keeps its products' orders
+    inst, hpol, _ = make_workload(args, args.seed if sharded else rank_seed(args.seed, rank))
+    T_job = inst.T
+    if sharded:
+        from paper_2406_01939_b300 import shard as shard_mod
+        owner = shard_mod.product_shards(inst.prod, inst.K, world)
+        inst, shard_times, _ = shard_mod.shard_instance(inst, owner, rank)
     di = DeviceInstance(inst, device=dev)
     pol = DevicePolicy(hpol, dev)
     T = inst.T
@@ -1004,10 +1020,14 @@ def run_single(args, dev, world, rank):
     proc_dev = torch.as_tensor(proc_host).to(dev) if rand else None
 
     def step(out):
-        return di.simulate(pol, fo_mode, num_chunks=fo_chunks, seg_window=args.seg_window,
-                           proc=proc_dev,
-                           flags=pic.PIC_FLAG_TIMING | args.flags, want_stock=False, out=out,
-                           max_steps=max_steps)
+        r = di.simulate(pol, fo_mode, num_chunks=fo_chunks, seg_window=args.seg_window,
+                        proc=proc_dev,
+                        flags=pic.PIC_FLAG_TIMING | args.flags, want_stock=False, out=out,
+                        max_steps=max_steps)
+        if sharded and world > 1:  # the trajectory's totals: one all-reduce per step
+            r["total_cost"], r["lost"], r["iters"] = shard_mod.join_scalars(
+                r["total_cost"], r["lost"], r["iters"], device=dev)
+        return r
 
     act = torch.empty(T, dtype=torch.int8, device=dev)
     for _ in range(max(3, args.warmup)):
@@ -1034,7 +1054,7 @@ def run_single(args, dev, world, rank):
         dist.barrier()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    value, t_ms = job_rate(T, args.steps, sum(step_ms), world, dev)
+    value, t_ms = job_rate(T, args.steps, sum(step_ms), world, dev)  # sharded: sum of T = T_job
     last = results[-1]
     # one extra (untimed) call with the per-pass trace (contiguous chunks)
     pass_trace = None
@@ -1156,9 +1176,12 @@ def run_single(args, dev, world, rank):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+        "scaling": "strong" if sharded else "weak", "vs_baseline": None,
         "dtype": "f32" if args.workload == "mlp_medium" else "int32", "data": "synthetic",
-        "config": workload_config(args, inst),
+        "config": dict(workload_config(args, inst),
+                       **({"T": T_job, "parallelism": f"products of one trajectory over {world} "
+                           "ranks (balanced by demand); cost, lost and passes all-reduced each step"}
+                          if sharded else {"parallelism": f"one trajectory per rank ({world})"})),
         "iters": iters,
         "seq_gpu": {"value": T / (seq_ms / 1000.0), "unit": UNIT, "ms": seq_ms} if seq_ms else None,
         "speedup_vs_seq_gpu": seq_ms / (t_ms / args.steps) if seq_ms else None,

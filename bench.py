@@ -100,7 +100,8 @@ def parse():
     p.add_argument("--partition", default="chunks", choices=["chunks", "products", "random"],
                    help="FO workloads: Algorithm 1 on contiguous time chunks (default), the "
                         "product partition of Sec. 3 (one processor per product), or the uniform "
-                        "random assignment of Sec. 4.1 over --chunks processes (no capacity)")
+                        "random assignment of Sec. 4.1 over --chunks processes (with node capacity every "
+                        "process replays the horizon in its own state: give few processes)")
     p.add_argument("--skew", type=float, default=0.0,
                    help="owmr_base: store weights (1 - skew)^n (App. B.3 ablation; 0 = uniform)")
     p.add_argument("--B", type=int, default=0,
@@ -1012,8 +1013,6 @@ def run_single(args, dev, world, rank):
     rand = args.partition == "random"
     if (products or rand) and (args.workload == "mlp_medium" or max_steps):
         raise SystemExit("--partition products/random: greedy / bid-price workloads, no max_steps")
-    if rand and getattr(inst, "cap", None) is not None:
-        raise SystemExit("--partition random: no node capacity")
     fo_mode = {"chunks": "picard", "products": "products", "random": "assigned"}[args.partition]
     fo_chunks = 0 if products else chunks_of(args)
     proc_host = synth_mod.uniform_assignment(T, fo_chunks, seed=args.seed) if rand else None
@@ -1134,14 +1133,26 @@ def run_single(args, dev, world, rank):
         # low by design.
         per = 14 + 4 * N + (4 if getattr(inst, "cap", None) is not None else 0)
         alg_bytes = last["policy_calls"] * per
+        acap = rand and getattr(inst, "cap", None) is not None
+        if acap:
+            # every process replays the horizon up to its last own order: per
+            # order-step its product, owner and cached action (4 + 4 + 1 B); per own
+            # order its region, cost and lambda rows and the new action (5 + 8 N B)
+            lastm = np.full(int(proc_host.max()) + 1, -1, np.int64)
+            np.maximum.at(lastm, proc_host.astype(np.int64), np.arange(T, dtype=np.int64))
+            walk = int((lastm + 1).sum())
+            alg_bytes = last["iters"] * walk * 9 + last["policy_calls"] * (5 + 8 * N)
         achieved = alg_bytes / (sim_ms / 1000.0) / 1e9
         peak, peak_kind = load_peaks()
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "traffic": None,
-                    "kernel": ("k_part_walk" if products else "k_assign_walk") +
-                              " plus the per-pass sorts (all passes)",
+                    "kernel": ("k_part_walk plus the per-pass sorts (all passes)" if products else
+                               "k_acap_pass (every process replays its view; all passes)"
+                               if getattr(inst, "cap", None) is not None else
+                               "k_assign_walk plus the per-pass sorts (all passes)"),
                     "peak_kind": peak_kind, "algorithmic_bytes": alg_bytes,
                     "critical_path_orders_per_pass": int(np.bincount(inst.prod).max()) if products
+                    else int(lastm.max() + 1) if acap
                     else int(np.unique(proc_host.astype(np.int64) * inst.K + inst.prod,
                                        return_counts=True)[1].max())}
     elif args.workload == "mlp_medium":

@@ -270,11 +270,17 @@ void pic_destroy_instance(pic_instance* inst);
  * max_steps (else UNSUPPORTED); device memory for the per-pass sorts is taken
  * with cudaMallocAsync on the call's stream.
  * PIC_MODE_PICARD_ASSIGNED runs Algorithm 1 with process proc[t] owning order t
- * (no capacity): in a process's view the stock of (k, n) before its order t is
- * max(0, x0[k][n] - attempts), the attempts being the cached actions naming
- * (k, n) at other processes' orders and its own fresh ones, so each (product,
- * process) pair is walked as an independent chain.  Same restrictions and
- * allocation as PIC_MODE_PICARD_PRODUCTS, plus node capacity UNSUPPORTED.
+ * (Sec. 4.1's uniform random partition, Table 1).  Without capacity, in a
+ * process's view the stock of (k, n) before its order t is max(0, x0[k][n] -
+ * attempts), the attempts being the cached actions naming (k, n) at other
+ * processes' orders and its own fresh ones, so each (product, process) pair is
+ * walked as an independent chain.  With node capacity no such closed form
+ * exists (a foreign cached action's success depends on every earlier success
+ * at its node in the process's own view), and every process replays the
+ * horizon up to its last own order in its own state, one warp each: a pass
+ * costs about num_chunks * T order-steps, and the scratch holds num_chunks * K *
+ * N stock entries.  Same restrictions and allocation as
+ * PIC_MODE_PICARD_PRODUCTS.
  *   actions_out  [T] int8 in opts.out_mem memory (required);
  *   final_stock  [K][N] int32 in opts.out_mem memory, or NULL;
  *   res          host struct, or NULL.

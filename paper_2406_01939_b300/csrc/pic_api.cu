@@ -429,9 +429,9 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
     if (opts->mode == PIC_MODE_PICARD_PRODUCTS && (mlp || opts->max_steps > 0))
         return fail(PIC_ERR_UNSUPPORTED, "product partition: greedy and bid-price policies, no window");
     if (opts->mode == PIC_MODE_PICARD_ASSIGNED) {
-        if (mlp || opts->max_steps > 0 || I.has_cap)
+        if (mlp || opts->max_steps > 0)
             return fail(PIC_ERR_UNSUPPORTED,
-                        "assigned partition: greedy and bid-price policies, no window, no capacity");
+                        "assigned partition: greedy and bid-price policies, no window");
         if (opts->num_chunks < 1 || (long long)opts->num_chunks * I.K >= (1LL << 31))
             return fail(PIC_ERR_INVALID_ARG, "assigned partition: need 1 <= num_chunks and num_chunks * K < 2^31");
         if (I.T && !opts->proc) return fail(PIC_ERR_INVALID_ARG, "assigned partition: proc is NULL");
@@ -487,7 +487,8 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
         if (opts->mode == PIC_MODE_PICARD_PRODUCTS)
             CU(picard_products(&I, pol, M, iters_cap, st));
         else
-            CU(picard_assigned(&I, pol, opts->proc, M, iters_cap, st));
+            CU(I.has_cap ? picard_assigned_cap(&I, pol, opts->proc, M, iters_cap, st)
+                         : picard_assigned(&I, pol, opts->proc, M, iters_cap, st));
         if (timing) CU(cudaEventRecord(I.ev[2], st));
         if (T) {
             CU(reduce_costs(&I, I.act_t, I.reg, st));

@@ -227,6 +227,10 @@ cudaError_t picard_products(Instance* I, const pic_policy* pol, int P, int iters
 // Ctrl::pad0 bit 128.
 cudaError_t picard_assigned(Instance* I, const pic_policy* pol, const int32_t* proc, int P,
                             int iters_cap, cudaStream_t st);
+// The same with node capacity (pic_acap.cu): every process replays the horizon
+// up to its last own order in its own state, one warp each.
+cudaError_t picard_assigned_cap(Instance* I, const pic_policy* pol, const int32_t* proc, int P,
+                                int iters_cap, cudaStream_t st);
 // Flag (Ctrl::pad0 bit 64) an initial cache holding a value outside [-1, N).
 cudaError_t check_alpha_init(Instance* I, const int8_t* alpha, cudaStream_t st);
 // Node capacity (pic_cap.cu): Algorithm 1 on M contiguous chunks of at most

@@ -1,8 +1,8 @@
 """GPU parity of Algorithm 1 for a caller's assignment of orders to processes
 (uniform random as in Sec. 4.1 / Table 1, contiguous, by product), greedy and
-bid-price policies without capacity, against the CPU oracle's Algorithm 1 for
-the same assignment: every iterate, the pass count, the path, its cost and the
-final stock bit for bit."""
+bid-price policies, without and with node capacity, against the CPU oracle's
+Algorithm 1 for the same assignment: every iterate, the pass count, the path,
+its cost and the final stock bit for bit."""
 import numpy as np
 import pytest
 
@@ -115,11 +115,6 @@ def test_invalid_inputs():
     with pytest.raises(pic.PicError) as e:
         d.simulate(Policy("greedy"), "assigned", num_chunks=4)
     assert e.value.status == pic.PIC_ERR_INVALID_ARG
-    capped = make(5, 300, 8, 5)
-    capped.cap = synth.node_capacity(300, 8, seed=1)
-    with pytest.raises(pic.PicError) as e:
-        DeviceInstance(capped).simulate(Policy("greedy"), "assigned", num_chunks=4, proc=proc)
-    assert e.value.status == pic.PIC_ERR_UNSUPPORTED
     mlp = synth.make_mlp(inst.N, inst.R, seed=1)
     with pytest.raises(pic.PicError) as e:
         d.simulate(Policy("mlp", mlp=mlp), "assigned", num_chunks=4, proc=proc)
@@ -137,3 +132,27 @@ def test_full_size_uniform_assignment():
     np.testing.assert_array_equal(got["actions"].cpu().numpy(), seq["actions"])
     assert got["total_cost"] == seq["total_cost"] and got["lost"] == seq["lost"]
     np.testing.assert_array_equal(got["final_stock"].cpu().numpy(), seq["x_final"])
+
+
+@pytest.mark.parametrize("N", [8, 33, 64])
+def test_uniform_random_assignment_with_capacity(N):
+    """Node capacity (the Sec. 3 state (x, c)) under uniform random assignments,
+    the setting of Table 1: every process replays its own view of the horizon.
+    Scarce and ample stock and capacity, 1 to 40 processes, every iterate."""
+    rng = np.random.default_rng(100 + N)
+    for trial in range(3):
+        T = int(rng.integers(50, 1500))
+        K = int(rng.integers(2, 12))
+        inst = make(1000 + 10 * N + trial, T, N, K, fill=float(rng.uniform(0.4, 1.5)))
+        inst.cap = synth.node_capacity(T, N, seed=trial, frac=float(rng.uniform(0.3, 0.9)))
+        d = DeviceInstance(inst)
+        for P in (1, 7, 40):
+            proc = synth.uniform_assignment(T, P, seed=trial)
+            for kind in ("greedy", "dual"):
+                check(inst, kind, proc, P, dev=d)
+        proc = synth.uniform_assignment(T, 9, seed=5)
+        rec = oracle.picard_partition(inst, Policy("dual"), proc, record=True)
+        for k in sorted({1, 2, rec["iters"]}):
+            g = d.simulate(Policy("dual"), "assigned", num_chunks=9, proc=proc, max_iters=k,
+                           raise_on_error=False)
+            np.testing.assert_array_equal(g["actions"].cpu().numpy(), rec["iterates"][k - 1])

@@ -188,11 +188,16 @@ def workload_config(args, inst):
     }
 
 
-def load_bf16_peak():
+def load_bf16_peak(sustained=False):
+    """Measured dense BF16 TFLOP/s: the burst figure for a kernel timed alone,
+    the sustained one for a kernel timed inside a long step."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
-        return float(json.load(open(p))["bf16_tflops"]), "measured"
-    return 1800.0, "fallback"
+        d = json.load(open(p))
+        if sustained and "bf16_tflops_sustained" in d:
+            return float(d["bf16_tflops_sustained"]), "measured (sustained)"
+        return float(d["bf16_tflops"]), "measured"
+    return (1400.0, "fallback (sustained)") if sustained else (1800.0, "fallback")
 
 
 def chunks_of(args):
@@ -210,8 +215,17 @@ def load_peaks():
 _KERNEL_FILES = {
     "int": ("pic_int.cu", "pic_replay.cuh", "pic_picard.cuh", "pic_device.cuh", "pic_internal.h"),
     "capacity": ("pic_cap.cu", "pic_picard.cuh", "pic_device.cuh", "pic_internal.h"),
+    "mlp": ("pic_mlp.cu", "pic_mlp.cuh", "pic_picard.cuh", "pic_device.cuh", "pic_internal.h"),
+    "batch": ("pic_batch.cu", "pic_mlp.cuh", "pic_replay.cuh", "pic_picard.cuh", "pic_device.cuh",
+              "pic_internal.h"),
+    "wave": ("pic_wave.cu", "pic_tc.cuh", "pic_mlp.cuh", "pic_device.cuh", "pic_internal.h"),
+    "pg": ("pic_pg.cu", "pic_tc.cuh", "pic_device.cuh", "pic_internal.h"),
+    "owmr": ("pic_owmr.cu", "pic_device.cuh"),
 }
-_PROFILES = {"int": "picard_int_dual_large.md", "capacity": "picard_cap_capacity_large.md"}
+_PROFILES = {"int": "picard_int_dual_large.md", "capacity": "picard_cap_capacity_large.md",
+             "mlp": "picard_mlp_mlp_medium.md", "batch": "picard_batch_batch_uneven.md",
+             "wave": "picard_wave_pg_large.md", "pg": "pg_grad_pg_large.md",
+             "owmr": "owmr_picard_owmr_base.md"}
 
 
 def kernel_source_hash(kind="int"):
@@ -473,6 +487,28 @@ def mlp_roofline(mlp_calls, N, ms, kernel):
             "algorithmic_flops": flops}
 
 
+def sim_roofline(r, N, ms):
+    """Roofline of a batch simulation launch (r: the result's counters).  With
+    tensor-core waves: the rows whose scores the tensor cores produced (kept or
+    re-scored as near ties) against the sustained BF16 peak (the launch runs
+    inside a long step); with the warp kernel: the FP32-scored decisions
+    against the FP32 ALU peak."""
+    if r["wave"]:
+        flops = (r["tc_decisions"] + r["rescored"]) * mlp_flops_per_call(N)
+        peak, kind = load_bf16_peak(sustained=True)
+        ach = flops / (ms / 1000.0) / 1e12
+        return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": profiled_traffic("wave"),
+                "kernel": "k_picard_wave (tcgen05 waves of 128 rows; all passes)",
+                "peak_kind": kind + " BF16 dense", "algorithmic_flops": flops,
+                "rows": "tensor-core rows kept or re-scored; table and FP32-scorer decisions "
+                        "excluded"}
+    roof = mlp_roofline(fp32_scored(r), N, ms,
+                        "k_picard_batch (warp per work unit; all passes; MLP scorer FP32 FMA)")
+    roof["traffic"] = profiled_traffic("batch")
+    return roof
+
+
 def run_batch(args, dev, world, rank):
     """Batch workload: every step simulates all trajectories of the batch in one
     persistent launch (CUDA graph)."""
@@ -598,8 +634,7 @@ def run_batch(args, dev, world, rank):
         "tc_decisions": last["tc_decisions"], "sat_decisions": last["sat_decisions"],
         "near_ties": last["near_ties"],
         "segment_replays": last["seg_replays"],
-        "roofline": mlp_roofline(fp32_scored(last), insts[0].N, sim_ms,
-                                 "k_picard_batch (persistent, all passes; MLP scorer FP32 FMA)"),
+        "roofline": sim_roofline(last, insts[0].N, sim_ms),
         "critical_path": cp,
         "pass_trace": pass_trace,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -744,6 +779,10 @@ def run_pg(args, dev, world, rank):
     achieved = flops / (bwd_ms / 1000.0) / 1e12
     tc = not (args.flags & pic.PIC_FLAG_NO_TC)
     bf16_peak, bf16_kind = load_bf16_peak()
+    # the dominant kernel is the simulation (all passes in one persistent launch)
+    sim_roof = sim_roofline({"wave": res.wave, "mlp_calls": res.mlp_calls,
+                             "tc_decisions": res.tc_decisions, "rescored": res.rescored,
+                             "sat_decisions": res.sat_decisions}, N, res.sim_ms)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
@@ -767,8 +806,9 @@ def run_pg(args, dev, world, rank):
         "policy_calls": res.policy_calls, "tc_decisions": res.tc_decisions,
         "sat_decisions": res.sat_decisions, "rescored": res.rescored,
         "near_ties": res.near_ties,
-        "roofline": ({"bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
-                      "frac": achieved / bf16_peak, "traffic": None,
+        "roofline": sim_roof,
+        "roofline_gradient": ({"bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
+                      "frac": achieved / bf16_peak, "traffic": profiled_traffic("pg"),
                       "kernel": "k_pg_tc (tcgen05, BF16 split products, FP32 accumulation in TMEM)",
                       "peak_kind": bf16_kind + " BF16 dense (burst: the gradient call timed alone)",
                       "algorithmic_flops": flops} if tc else
@@ -910,7 +950,8 @@ def run_owmr(args, dev, world, rank):
         "speedup_vs_seq_gpu": (seq["ms_full_horizon_est"] / (t_ms / args.steps)) if seq else None,
         "phases_ms": {"call": sim_ms, "step_device": t_ms / args.steps},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                     "traffic": profiled_traffic("owmr"),
                      "kernel": "k_owmr_picard (persistent, all passes; FP32 network rounds)",
                      "peak_kind": "derived: 148 SMs x 128 FP32 lanes x 2 FLOP x 2.032 GHz",
                      "algorithmic_flops": flops},
@@ -1157,6 +1198,7 @@ def run_single(args, dev, world, rank):
                                        return_counts=True)[1].max())}
     elif args.workload == "mlp_medium":
         roofline = mlp_roofline(fp32_scored(last), N, sim_ms, "k_picard_mlp (persistent, all passes)")
+        roofline["traffic"] = profiled_traffic("mlp")
     elif args.workload == "capacity_large":
         # the method's bytes: per replayed order its record (product and region,
         # 2 B each), its sorted position (4 B) and its cached action read and

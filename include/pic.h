@@ -223,6 +223,8 @@ typedef struct {
     int64_t near_ties;     /* FP32-scorer decisions whose fast layer-2 scores left a near tie
                               within their error bound, re-scored in the reference order
                               (one sequential fmaf chain per output, from the bias) */
+    int32_t wave;          /* 1 if the MLP decisions ran in tensor-core waves (PIC_FLAG_WAVE,
+                              set by the caller or chosen by the batch autotuner), else 0 */
 } pic_sim_result;
 
 /* Per-trajectory result of pic_simulate_batch. */

@@ -71,7 +71,7 @@ class pic_sim_result(C.Structure):
                 ("sim_ms", C.c_float), ("total_ms", C.c_float), ("seg_window", C.c_int32),
                 ("cta_threads", C.c_int32), ("ctas_per_sm", C.c_int32), ("mlp_calls", C.c_int64),
                 ("tc_decisions", C.c_int64), ("sat_decisions", C.c_int64),
-                ("near_ties", C.c_int64)]
+                ("near_ties", C.c_int64), ("wave", C.c_int32)]
 
 
 class pic_traj_result(C.Structure):

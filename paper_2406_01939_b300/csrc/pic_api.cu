@@ -442,6 +442,7 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
     const cudaMemcpyKind okind = host_out ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     const bool timing = (opts->flags & PIC_FLAG_TIMING) != 0;
     I.launches = 0;
+    I.ran_wave = 0;
     if (mlp) CU(mlp_alloc(&I));
     if (timing) CU(cudaEventRecord(I.ev[0], st));
     CU(cudaMemsetAsync(I.ctrl, 0, offsetof(Ctrl, nruns), st));
@@ -603,6 +604,7 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
         res->tc_decisions = (int64_t)hc.tc_rows;
         res->sat_decisions = (int64_t)hc.sat_rows;
         res->near_ties = (int64_t)hc.near_ties;
+        res->wave = I.ran_wave;
         res->seg_replays = (int64_t)hc.seg_replays;
         res->launches = I.launches;
         res->prep_ms = res->sim_ms = res->total_ms = 0.0f;

@@ -760,6 +760,7 @@ pic_status pic_simulate_batch(pic_instance* h, const pic_policy* pols, const pic
     const bool timing = (opts->flags & PIC_FLAG_TIMING) != 0;
     const size_t T = I.T, K = I.K, N = I.N;
     I.launches = 0;
+    I.ran_wave = 0;
     if (c.has_mlp) BCU(mlp_alloc(&I));
     int32_t* stock_src = I.xfin;
     if (timing) BCU(cudaEventRecord(I.ev[0], st));
@@ -858,6 +859,7 @@ pic_status pic_simulate_batch(pic_instance* h, const pic_policy* pols, const pic
         res->tc_decisions = picard ? (int64_t)hc.tc_rows : 0;
         res->sat_decisions = (int64_t)hc.sat_rows;
         res->near_ties = (int64_t)hc.near_ties;
+        res->wave = I.ran_wave;
         if (!picard)
             for (int b = 0; b < B; ++b)
                 if (bt->h_pol[b].kind >= PIC_POLICY_MLP) res->mlp_calls += bt->h_toff[b + 1] - bt->h_toff[b];

@@ -163,6 +163,7 @@ struct Instance {
     int coop_blocks;                  // persistent grid size of the last Picard launch
     int cta_threads, ctas_per_sm;     // its CTA shape
     int launches;                     // kernels launched by the current call
+    int ran_wave;                     // the current call ran the wave kernel
     cudaEvent_t ev[4];                // phase timing events (created with the instance)
     // node capacity (pic_instance_desc.cap) and the capacity kernel's tables
     int has_cap;

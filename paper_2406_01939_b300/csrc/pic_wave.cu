@@ -727,6 +727,7 @@ cudaError_t launch_wave(Instance* I, const KArgs& a, const MlpPolicy& p, const W
     I->coop_blocks = grid;
     I->cta_threads = kWThreads;
     I->ctas_per_sm = 1;
+    I->ran_wave = 1;
     KArgs args = a;
     args.perm = I->perm;  // sorted position -> time (the Gumbel counter), also for batches
     MlpPolicy pp = p;

@@ -94,7 +94,7 @@ class DeviceInstance:
                 "sim_ms": res.sim_ms, "total_ms": res.total_ms, "seg_window": res.seg_window,
                 "cta_threads": res.cta_threads, "ctas_per_sm": res.ctas_per_sm,
                 "mlp_calls": res.mlp_calls, "tc_decisions": res.tc_decisions,
-                "sat_decisions": res.sat_decisions, "near_ties": res.near_ties}
+                "sat_decisions": res.sat_decisions, "near_ties": res.near_ties, "wave": bool(res.wave)}
 
     def close(self):
         if self.handle:
@@ -187,7 +187,7 @@ class DeviceBatch:
                 "num_chunks": res.num_chunks, "seg_window": res.seg_window,
                 "cta_threads": res.cta_threads, "ctas_per_sm": res.ctas_per_sm,
                 "mlp_calls": res.mlp_calls, "tc_decisions": res.tc_decisions,
-                "sat_decisions": res.sat_decisions, "near_ties": res.near_ties,
+                "sat_decisions": res.sat_decisions, "near_ties": res.near_ties, "wave": bool(res.wave),
                 "rescored": res.rescored, "seg_replays": res.seg_replays,
                 "launches": res.launches, "prep_ms": res.prep_ms,
                 "sim_ms": res.sim_ms, "total_ms": res.total_ms,

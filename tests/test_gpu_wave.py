@@ -40,6 +40,7 @@ def test_wave_picard_matches_oracle(N):
             np.testing.assert_array_equal(got["final_stock"].cpu().numpy(), seq["x_final"])
             assert got["total_cost"] == seq["total_cost"] and got["lost"] == seq["lost"]
             assert got["iters"] == want["iters"], (M, flags, got["iters"], want["iters"])
+            assert got["wave"]  # the result names the kernel that ran
             if flags & pic.PIC_FLAG_TC:
                 assert got["tc_decisions"] > 0
             if flags & pic.PIC_FLAG_NO_TC:
@@ -97,6 +98,7 @@ def test_wave_batch_mixed_policies():
     db = DeviceBatch(insts)
     for flags in (W, W | pic.PIC_FLAG_NO_SAT):
         got = db.simulate(pols, "picard", num_chunks=24, flags=flags)
+        assert got["wave"]
         acts = db.split(got["actions"].cpu().numpy())
         xf = db.split_stock(got["final_stock"].cpu().numpy())
         for b, (inst, pol) in enumerate(zip(insts, pols)):
@@ -114,7 +116,8 @@ def test_wave_batch_uneven_full_size_equals_default_kernel():
     and pass counts, and its first MLP trajectory equals the oracle's."""
     insts, pols = synth.batch_uneven(0)
     db = DeviceBatch(insts)
-    base = db.simulate(pols, "picard", num_chunks=64)
+    base = db.simulate(pols, "picard", num_chunks=64, flags=pic.PIC_FLAG_NO_WAVE)
+    assert not base["wave"]
     for flags in (W, pic.PIC_FLAG_WAVE):
         got = db.simulate(pols, "picard", num_chunks=64, flags=flags)
         assert torch.equal(got["actions"], base["actions"])

@@ -566,8 +566,58 @@ __device__ __forceinline__ void ld_p16(const float* Pr, int c, bool valid, float
     }
 }
 
+// Column sums over the 32 lanes of a warp, V values per lane (V = 32 or 16), by
+// recursive halving: at each step a lane keeps the half of its values selected
+// by its lane bit and adds its partner's copy of that half.  V = 32: lane l ends
+// with the total of value l in v[0]; V = 16: lanes l and l ^ 1 end with the
+// total of value l >> 1.
+template <int V>
+__device__ __forceinline__ float warp_column_sum(float (&v)[V]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16, c = V; c > 1; o >>= 1, c >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < c / 2; ++i) {
+            const float send = up ? v[i] : v[i + c / 2];
+            const float keep = up ? v[i + c / 2] : v[i];
+            v[i] = keep + __shfl_xor_sync(kFull, send, o);
+        }
+    }
+    if (V == 16) v[0] += __shfl_xor_sync(kFull, v[0], 1);
+    return v[0];
+}
+
+// One tile row's inputs: sorted position, region, action, G, whether it counts,
+// and this thread's 16 stock features (column quarter cq).
+struct TileIn {
+    int jj, r, a, ok;
+    float g;
+    char4 f[4];
+};
+
+__device__ __forceinline__ TileIn load_tile_in(const PgArgs& p, int q, int cq) {
+    TileIn in;
+    in.jj = q < p.Q ? __ldg(p.jq + q) : -1;
+    in.r = -1; in.a = -1; in.ok = 0; in.g = 0.f;
+    if (in.jj >= 0 && cq == 0) {
+        in.r = __ldg(p.rq + q);
+        in.a = p.alpha_s[in.jj];
+        in.g = __ldg(p.G + in.jj);
+        in.ok = p.ok[in.jj];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        in.f[i] = in.jj >= 0 ? *reinterpret_cast<const char4*>(p.f8 + (size_t)in.jj * kPgN + 16 * cq + 4 * i)
+                             : make_char4(0, 0, 0, 0);
+    return in;
+}
+
 // Thread layout: 16 warps; warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile rows
 // = orders, or hidden units for the accumulators) and the column quarter w / 4.
+// Per tile the next tile's inputs are loaded during phase 2; db2 and the region
+// sums of dz are column sums over the rows of a warp (warp_column_sum), kept per
+// thread (quadrant of rows, column) until the region changes.
 __global__ void __launch_bounds__(kTcThreads, 1) k_pg_tc(PgArgs p, int* err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];  // 16-byte operand addresses suffice
     TcSmem& s = *reinterpret_cast<TcSmem*>(smem_raw);
@@ -584,7 +634,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pg_tc(PgArgs p, int* err) {
         *reinterpret_cast<uint16_t*>(s.w2 + lay(n, jj, kHidden)) = w2;
     }
     if (tid < kPgN) s.b2[tid] = tid < N ? lo16(p.b2[tid]) : 0.0f;
-    double db2 = 0.0;  // thread n < N: running db2[n]
+    double db2 = 0.0;  // even lanes: db2 of column 16 cq + lane / 2 over this warp's rows
     if (tid == 0) {
         s.fail = 0;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&s.mbar)));
@@ -600,8 +650,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pg_tc(PgArgs p, int* err) {
     unsigned phase = 0;
     bool acc_started = false;  // the TMEM accumulators hold this CTA's sums
     double Jw = 0.0;
-    int cur_r[2] = {-1, -1};   // per-region dz sums of column tid % 128 of each half, rows of quarter tid / 128
-    float run[2] = {0.f, 0.f};
+    // per-region dz sums of column 32 cq + lane of each half over this warp's rows
+    int cur_r0 = -1, cur_r1 = -1;
+    float run0 = 0.f, run1 = 0.f;
     const unsigned aF = su32(s.f), aW1 = su32(s.w1s), aW2 = su32(s.w2), aH = su32(s.hhi), aL = su32(s.hlo);
     const unsigned aSh = su32(s.dshi), aSl = su32(s.dslo);
     const int ntiles = (p.Q + kTcRows - 1) / kTcRows;
@@ -636,32 +687,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pg_tc(PgArgs p, int* err) {
         }
     };
     bool ok_all = true;
+    TileIn nxt = load_tile_in(p, tb0 * kTcRows + t, cq);
     for (int tile = tb0; tile < tb1 && ok_all; ++tile) {
         // ---- the tile's orders (warps 0-3: one row each) and features (16 columns per thread)
         {
-            const int q = tile * kTcRows + t;
-            const int jj = q < p.Q ? p.jq[q] : -1;
+            const TileIn& in = nxt;
             if (cq == 0) {
-                int r = -1, a = -1, okv = 0;
-                float g = 0.f;
-                if (jj >= 0) {
-                    r = p.rq[q];
-                    a = p.alpha_s[jj];
-                    g = p.G[jj];
-                    okv = p.ok[jj];
-                }
-                s.j[t] = jj; s.r[t] = r; s.a[t] = a; s.G[t] = g; s.ok[t] = okv;
+                s.j[t] = in.jj; s.r[t] = in.r; s.a[t] = in.a; s.G[t] = in.g; s.ok[t] = in.ok;
             }
             float fv[16];
-            const int c0 = 16 * cq;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const char4 c4 = jj >= 0 ? *reinterpret_cast<const char4*>(p.f8 + (size_t)jj * kPgN + c0 + 4 * i)
-                                         : make_char4(0, 0, 0, 0);
-                fv[4 * i] = c4.x / 32.0f; fv[4 * i + 1] = c4.y / 32.0f;
-                fv[4 * i + 2] = c4.z / 32.0f; fv[4 * i + 3] = c4.w / 32.0f;
+                fv[4 * i] = in.f[i].x / 32.0f; fv[4 * i + 1] = in.f[i].y / 32.0f;
+                fv[4 * i + 2] = in.f[i].z / 32.0f; fv[4 * i + 3] = in.f[i].w / 32.0f;
             }
-            st_row16(s.f, t, c0, kPgN, fv);
+            st_row16(s.f, t, 16 * cq, kPgN, fv);
         }
         tc_sync_operands();
         const int r = s.r[t];
@@ -722,20 +762,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pg_tc(PgArgs p, int* err) {
                 const float d = use && ((feas >> i) & 1u) ? G * ((n == a ? 1.0f : 0.0f) - sc[i] * inv) : 0.f;
                 dhi[i] = __bfloat162float(__float2bfloat16_rn(d));
                 dlo[i] = d - dhi[i];
+                sc[i] = d;
             }
             st_row16(s.dshi, t, n0, kPgN, dhi);
             st_row16(s.dslo, t, n0, kPgN, dlo);
+            db2 += (double)warp_column_sum<16>(sc);  // db2: the tile's column sums of ds
         }
         tc_sync_operands();
-        if (tid < N) {  // db2: this tile's column sum of ds, rows in order (deterministic)
-            float cs = 0.f;
-            for (int rr = 0; rr < kTcRows; ++rr) {
-                const int o = lay(rr, tid, kPgN);
-                cs += __uint_as_float((unsigned)*reinterpret_cast<const uint16_t*>(s.dshi + o) << 16) +
-                      __uint_as_float((unsigned)*reinterpret_cast<const uint16_t*>(s.dslo + o) << 16);
-            }
-            db2 += (double)cs;
-        }
+        // the next tile's inputs, loaded while phase 2 runs
+        if (tile + 1 < tb1) nxt = load_tile_in(p, (tile + 1) * kTcRows + t, cq);
         // ---- phase 2: gradients.  Per half: {dW2_h, dH_h}, then {dW1_h (, Z_1)}
         for (int h = 0; h < 2; ++h) {
             epi_h(h, Pr, valid);  // Z_h is in the Z columns (issued with the previous group)
@@ -762,7 +797,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pg_tc(PgArgs p, int* err) {
             }
             if (!tc_wait(&s.mbar, phase)) s.fail = 1;
             // dz = dH [h > 0] over the h buffers (hi, lo): this thread's 32 columns
-            for (int c0 = 32 * cq; c0 < 32 * cq + 32; c0 += 16) {
+            float xs[32];
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                const int c0 = 32 * cq + 16 * g;
                 float v[16], hi[16], lo[16];
                 tc_ld16(tm + lane_base + kColZ + c0, v);
 #pragma unroll
@@ -775,10 +813,35 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pg_tc(PgArgs p, int* err) {
                         const float x = hh > 0.f ? v[i + e] : 0.f;
                         hi[i + e] = __bfloat162float(__float2bfloat16_rn(x));
                         lo[i + e] = x - hi[i + e];
+                        xs[16 * g + i + e] = x;
                     }
                 }
                 st_row16(s.hhi, t, c0, 128, hi);
                 st_row16(s.hlo, t, c0, 128, lo);
+            }
+            // per-region sums of dz over this warp's rows (region-sorted: mostly one)
+            {
+                const int rt = s.r[t];
+                const int r0 = __shfl_sync(kFull, rt, 0);  // rows without an order come last
+                if (r0 >= 0) {
+                    const int col = 128 * h + 32 * cq + (tid & 31);
+                    if (__all_sync(kFull, rt == r0 || rt < 0)) {
+                        const float tot = warp_column_sum<32>(xs);
+                        int cr = h ? cur_r1 : cur_r0;
+                        float rn = h ? run1 : run0;
+                        if (cr != r0) {
+                            if (cr >= 0) atomicAdd(p.dz + (size_t)cr * kHidden + col, (double)rn);
+                            cr = r0;
+                            rn = 0.f;
+                        }
+                        rn += tot;
+                        if (h) { cur_r1 = cr; run1 = rn; } else { cur_r0 = cr; run0 = rn; }
+                    } else if (rt >= 0) {  // several regions: each row adds to its own
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            atomicAdd(p.dz + (size_t)rt * kHidden + 128 * h + 32 * cq + i, (double)xs[i]);
+                    }
+                }
             }
             tc_sync_operands();
             if (tid == 0) {
@@ -792,22 +855,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pg_tc(PgArgs p, int* err) {
                 if (h == 0) issue_z(1);  // the dz columns were read above
                 tc_commit(&s.mbar);
             }
-            // region sums of column c = tid % 128 of half h over rows 32 qq .. 32 qq + 31
-            {
-                const int c = tid & 127, qq = tid >> 7;
-                for (int rr = 32 * qq; rr < 32 * qq + 32; ++rr) {
-                    const int rg = s.r[rr];
-                    if (rg < 0) break;
-                    if (rg != cur_r[h]) {
-                        if (cur_r[h] >= 0) atomicAdd(p.dz + (size_t)cur_r[h] * kHidden + 128 * h + c, (double)run[h]);
-                        cur_r[h] = rg;
-                        run[h] = 0.f;
-                    }
-                    const float zh = __uint_as_float((unsigned)*reinterpret_cast<const uint16_t*>(s.hhi + lay(rr, c, 128)) << 16);
-                    const float zl = __uint_as_float((unsigned)*reinterpret_cast<const uint16_t*>(s.hlo + lay(rr, c, 128)) << 16);
-                    run[h] += zh + zl;
-                }
-            }
             if (!tc_wait(&s.mbar, phase)) s.fail = 1;
             __syncthreads();
         }
@@ -819,9 +866,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pg_tc(PgArgs p, int* err) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) Jw += __shfl_xor_sync(kFull, Jw, o);
     if ((tid & 31) == 0 && Jw != 0.0) atomicAdd(p.J, Jw);
-    for (int h = 0; h < 2; ++h)
-        if (cur_r[h] >= 0) atomicAdd(p.dz + (size_t)cur_r[h] * kHidden + 128 * h + (tid & 127), (double)run[h]);
-    if (tid < N && db2 != 0.0) atomicAdd(p.accb2 + tid, db2);
+    if (cur_r0 >= 0) atomicAdd(p.dz + (size_t)cur_r0 * kHidden + 32 * cq + (tid & 31), (double)run0);
+    if (cur_r1 >= 0) atomicAdd(p.dz + (size_t)cur_r1 * kHidden + 128 + 32 * cq + (tid & 31), (double)run1);
+    {
+        const int col = 16 * cq + ((tid & 31) >> 1);
+        if ((tid & 1) == 0 && col < N && db2 != 0.0) atomicAdd(p.accb2 + col, db2);
+    }
     if (acc_started && ok_all) {
         for (int h = 0; h < 2; ++h) {
             const int jj = 128 * h + t;

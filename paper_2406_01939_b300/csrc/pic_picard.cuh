@@ -272,8 +272,13 @@ __device__ __forceinline__ void chain_prefixes(const KArgs& a, int it, const int
 //            (superblock_prefix, one warp per super-block head of a chain whose
 //            product changed in the previous pass);
 //   phase R  active segments replayed, one warp each: positions of the
-//            longest-first order are dealt to warps in a snake (w, 2W-1-w,
-//            2W+w, ...), examined 32 at a time per warp, and
+//            longest-first order are dealt to CTAs in a snake (c, 2C-1-c,
+//            2C+c, ...); a CTA examines its positions with all its threads at
+//            once, lists the active ones in order in shared memory, and its
+//            warps take them one at a time (a shared-memory ticket), so that a
+//            warp that finishes early takes the next unit of its CTA (GROUP > 1:
+//            positions dealt to groups of warps in a snake, 32 at a time per
+//            group);
 //            replay(seg, meta, fcp, fc_cur, it) replays one of them and returns
 //            whether it changed a cached action (warp-uniform; it adds its
 //            policy calls to `calls` on lane 0); the trace records the pass's
@@ -294,9 +299,13 @@ __device__ __forceinline__ void picard_passes(const KArgs& a, unsigned long long
                                               Replay&& replay, SegMeta* ext_meta = nullptr,
                                               int* ext_fcp = nullptr) {
     __shared__ int s_changed;
-    // per warp: the 32 segments it is examining (metadata, previous-pass first change)
+    // per warp: the 32 segments it is examining (metadata, previous-pass first
+    // change); in phase R with GROUP == 1, the CTA's list of active units
     __shared__ SegMeta s_meta[CTA ? 1 : WARPS][32];
     __shared__ int s_fcp[CTA ? 1 : WARPS][32];
+    __shared__ int s_seg[(CTA || GROUP > 1) ? 1 : WARPS * 32];
+    __shared__ int s_wcnt[(CTA || GROUP > 1) ? 1 : WARPS];
+    __shared__ int s_ticket;
     const int lane = lane_id();
     const int wib = threadIdx.x >> 5;
     const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -345,6 +354,63 @@ __device__ __forceinline__ void picard_passes(const KArgs& a, unsigned long long
         const int unit = gwarp / GROUP, nunits = nwarps / GROUP;
         if constexpr (CTA) {
             chg = replay(fc_prev, fc_cur, it, whi, wprev, replays, ucalls, uorders);
+        } else if constexpr (GROUP == 1) {
+            // this CTA's positions j * C + (j odd ? C - 1 - b : b), a list of
+            // WARPS * 32 at a time
+            const int C = gridDim.x, b = blockIdx.x;
+            const int npos = (nseg + C - 1) / C;  // rounds j; a position past nseg is skipped
+            SegMeta* L_meta = &s_meta[0][0];
+            int* L_fcp = &s_fcp[0][0];
+            for (int base = 0; base < npos; base += WARPS * 32) {
+                const int j = base + (int)threadIdx.x;
+                bool act = false;
+                SegMeta m;
+                int sl = 0, fcp = 0;
+                if (j < npos) {
+                    const int pos = j * C + ((j & 1) ? C - 1 - b : b);
+                    if (pos < nseg) {
+                        sl = a.lpt[pos];
+                        m = load_meta(a.meta + sl);
+                        fcp = no_reset ? -1 : fc_prev[m.k];
+                        act = m.last_start > fcp;  // some run starts after the first change
+                        if (win) {  // ... or entered the window; and some run is inside it
+                            const int c0 = __ldg(a.run_chunk + m.r0), c1 = __ldg(a.run_chunk + m.r1 - 1);
+                            act = c0 < whi && (act || c1 >= wprev);
+                        }
+                    }
+                }
+                // the active units in position order: rank in the warp, then warp offsets
+                const unsigned bal = __ballot_sync(kFull, act);
+                if (lane == 0) s_wcnt[wib] = __popc(bal);
+                if (threadIdx.x == 0) s_ticket = 0;
+                __syncthreads();
+                int off = 0, total = 0;
+                for (int w = 0; w < WARPS; ++w) {
+                    const int c = s_wcnt[w];
+                    off += w < wib ? c : 0;
+                    total += c;
+                }
+                if (act) {
+                    const int idx = off + __popc(bal & ((1u << lane) - 1u));
+                    L_meta[idx] = m;
+                    L_fcp[idx] = fcp;
+                    s_seg[idx] = sl;
+                }
+                __syncthreads();
+                while (true) {
+                    int u = 0;
+                    if (lane == 0) u = atomicAdd(&s_ticket, 1);
+                    u = __shfl_sync(kFull, u, 0);
+                    if (u >= total) break;
+                    const SegMeta mm = smem_meta(&L_meta[u]);
+                    const unsigned long long cu0 = calls;
+                    chg |= replay(s_seg[u], mm, L_fcp[u], fc_cur, it);
+                    replays += 1;
+                    if (calls - cu0 > ucalls) ucalls = calls - cu0;
+                    if ((unsigned long long)(mm.jend - mm.j0) > uorders) uorders = mm.jend - mm.j0;
+                }
+                __syncthreads();  // the list is read until every warp is done
+            }
         } else {
         for (int j0 = 0; j0 * nunits < nseg; j0 += 32) {
             const int j = j0 + lane;

@@ -269,7 +269,8 @@ cudaError_t alloc_instance(Instance& I, int T_, int N_, int K_, int R_, bool has
     if (!e) e = dmalloc(&I.act_t, T);
     if (!e) e = dmalloc(&I.tmp_a, T);
     if (!e) e = dmalloc(&I.tmp_b, T);
-    if (!e) e = dmalloc(&I.scan_blk, nscan / 2048 + 2);
+    if (!e) e = dmalloc(&I.scan_blk, (size_t)scan_blk_len((int)nscan));
+    if (!e) e = cudaMemset(I.scan_blk, 0, sizeof(int32_t) * (size_t)scan_blk_len((int)nscan));
     if (!e) e = dmalloc(&I.hist, (size_t)I.hist_cap);
     if (!e) e = cudaMalloc((void**)&I.ctrl, sizeof(Ctrl));
     if (!e) e = cudaMalloc((void**)&I.trace, sizeof(long long) * kTraceCols * kTraceCap);

@@ -534,10 +534,10 @@ cudaError_t cap_tables(Instance* I, int M, cudaStream_t st) {
     const int L = (int)(((long long)T + M - 1) / M);
     k_cap_order<<<nblk(T, 256), 256, 0, st>>>(I->perm, I->run_of, I->run_start, T, I->cap_run_t,
                                               I->cap_inv, I->tmp_a);
-    if ((e = scan_exclusive(I->tmp_a, I->tmp_b, T, nullptr, I->scan_blk, st))) return e;
+    if ((e = scan_exclusive(I->tmp_a, I->tmp_b, T, nullptr, I->scan_blk, st, &I->ctrl->err))) return e;
     k_cap_info<<<nblk(T, 256), 256, 0, st>>>(I->cap_run_t, I->cap_inv, I->tmp_b, I->run_start,
                                              I->perm, I->prod, I->pstart, T, L, I->cap_info);
-    I->launches += 5;
+    I->launches += 3;
     if ((e = cudaGetLastError())) return e;
     I->cap_tables_m = M;
     return cudaSuccess;

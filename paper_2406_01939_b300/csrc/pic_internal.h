@@ -190,10 +190,11 @@ cudaError_t build_tables(Instance* I, int M, int W, cudaStream_t st);
 cudaError_t sort_pairs(Instance* I, const int32_t* keys, int n, int max_key, int32_t* keys_out,
                        int32_t* vals_out, int32_t* tmp_k, int32_t* tmp_v, cudaStream_t st);
 // The same LSD radix sort with explicit scratch: hist [sort_hist_len(n)] and
-// scan_blk [scan_blk_len(sort_hist_len(n))] (5 launches per key byte).
+// scan_blk [scan_blk_len(sort_hist_len(n))], zeroed once when allocated (3
+// launches per key byte); err as for scan_exclusive.
 cudaError_t sort_pairs_raw(const int32_t* keys, int n, int max_key, int32_t* keys_out,
                            int32_t* vals_out, int32_t* tmp_k, int32_t* tmp_v, int32_t* hist,
-                           int32_t* scan_blk, cudaStream_t st);
+                           int32_t* scan_blk, cudaStream_t st, int* err = nullptr);
 int sort_hist_len(int n);
 int scan_blk_len(int n);
 // Longest-first order of the segments by estimated work: length, times
@@ -273,9 +274,13 @@ cudaError_t take_tags(Instance& I, int iters_cap, cudaStream_t st);
 // histograms) and the per-call resets of fc and xfin.
 cudaError_t init_cache(Instance& I, const int8_t* alpha_init, cudaStream_t st);
 
-// Simple device-wide exclusive scan of int32 (n elements); total written to *total_dev.
+// Device-wide exclusive scan of int32 (n elements, one pass, decoupled
+// look-back); total written to *total_dev (if given).  blk: scan_blk_len(n)
+// ints, zeroed once when allocated (it carries an epoch counter between
+// scans); a look-back wait that runs out records PIC_ERR_TIMEOUT in *err.
+// in and out may be the same array.
 cudaError_t scan_exclusive(const int32_t* in, int32_t* out, int n, int32_t* total_dev,
-                           int32_t* blk, cudaStream_t st);
+                           int32_t* blk, cudaStream_t st, int* err = nullptr);
 
 }  // namespace pic
 

@@ -1040,13 +1040,14 @@ pic_status build_tables(pic_owmr* h, int P, int ctas, cudaStream_t st, int* laun
     A(&off, (size_t)P + 1); A(&grows, (size_t)ngroups + 1); A(&hist, hl); A(&blk, bl);
     A(&h->gbase, (size_t)ngroups + 1);
     pic_status ps = PIC_OK;
+    if (!e) e = cudaMemsetAsync(blk, 0, sizeof(int32_t) * (size_t)bl, st);  // scan epoch and words
     if (!e) e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (P + 1), st);
     if (!e && T > 0) {
         k_ow_keys<<<nblk(T, 256) < 4096 ? nblk(T, 256) : 4096, 256, 0, st>>>(T, P, h->ret, key, cnt);
         e = sort_pairs_raw(key, T, P - 1, key_s, perm, tk, tv, hist, blk, st);
         int passes = 1;
         while (passes < 4 && ((unsigned)(P - 1) >> (8 * passes)) != 0) ++passes;
-        *launches += 1 + 5 * passes;
+        *launches += 1 + 3 * passes;
     }
     if (!e) e = scan_exclusive(cnt, off, P + 1, nullptr, blk, st);
     if (!e) {
@@ -1054,7 +1055,7 @@ pic_status build_tables(pic_owmr* h, int P, int ctas, cudaStream_t st, int* laun
         e = cudaMemsetAsync(grows + ngroups, 0, sizeof(int32_t), st);
     }
     if (!e) e = scan_exclusive(grows, h->gbase, ngroups + 1, nullptr, blk, st);
-    *launches += 7;
+    *launches += 3;
     int rows_total = 0;
     if (!e) e = cudaMemcpyAsync(&rows_total, h->gbase + ngroups, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (!e) e = cudaStreamSynchronize(st);

@@ -717,27 +717,27 @@ cudaError_t picard_assigned(Instance* I, const pic_policy* pol, const int32_t* p
         e = sort_pairs(I, ukey, T, P * K - 1, uks, uord, I->tmp_a, I->tmp_b, st);
         if (!e) {
             k_assign_uflags<<<gb, 256, 0, st>>>(T, uks, flag);
-            e = scan_exclusive(flag, upos, T, total, I->scan_blk, st);
+            e = scan_exclusive(flag, upos, T, total, I->scan_blk, st, &I->ctrl->err);
         }
         if (!e) {
             k_assign_ustart<<<gb, 256, 0, st>>>(T, flag, upos, ustart);
             e = cudaMemcpyAsync(&U, total, sizeof(int), cudaMemcpyDeviceToHost, st);
         }
         if (!e) e = cudaStreamSynchronize(st);
-        I->launches += 6;
+        I->launches += 4;
     }
     // per unit: first order, product, region; the units with more than one order
     int MU = 0;
     if (!e && T > 0) {
         const int gu = (U + 255) / 256 < 4 * I->num_sms ? (U + 255) / 256 : 4 * I->num_sms;
         k_assign_units<<<gu, 256, 0, st>>>(U, ustart, uord, I->prod, I->reg, ft, fk, fr, mflag);
-        e = scan_exclusive(mflag, mpos, U, total, I->scan_blk, st);
+        e = scan_exclusive(mflag, mpos, U, total, I->scan_blk, st, &I->ctrl->err);
         if (!e) {
             k_assign_mlist<<<gu, 256, 0, st>>>(U, ustart, ft, fk, mflag, mpos, mu);
             e = cudaMemcpyAsync(&MU, total, sizeof(int), cudaMemcpyDeviceToHost, st);
         }
         if (!e) e = cudaStreamSynchronize(st);
-        I->launches += 5;
+        I->launches += 3;
     }
     // the cached actions naming (k, j), listed per (k, j) in time order
     auto tables = [&]() {

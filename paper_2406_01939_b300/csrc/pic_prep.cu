@@ -22,8 +22,6 @@ namespace pic {
 namespace {
 
 constexpr int kScanThreads = 256;
-constexpr int kScanItems = 8;
-constexpr int kScanTile = kScanThreads * kScanItems;
 
 constexpr int kRadixThreads = 256;           // 8 warps
 constexpr int kRadixPerWarp = 512;           // 16 rounds of 32
@@ -56,46 +54,111 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* total) {
     return before + x - v;
 }
 
-__global__ void k_scan_reduce(const int32_t* __restrict__ in, int n, int32_t* __restrict__ blk) {
-    const long long base = (long long)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
-    int s = 0;
-#pragma unroll
-    for (int i = 0; i < kScanItems; ++i)
-        if (base + i < n) s += in[base + i];
-    int tot;
-    block_exclusive_scan(s, &tot);
-    if (threadIdx.x == 0) blk[blockIdx.x] = tot;
+// Single-pass exclusive scan with decoupled look-back.  Tile b (= blockIdx.x)
+// scans its kScanTile1 elements, publishes its total, walks back over the tiles
+// before it (a warp reads 32 of them at a time) until it meets a published
+// inclusive prefix, adding the totals on the way, and publishes its own.  The
+// status words live in blk: blk[0] is an epoch counter, then per tile a total
+// and an inclusive prefix, each (epoch + 1) << 32 | value, so words left by an
+// earlier scan on the same scratch never match.  The last tile, which starts
+// after all others and waits until each has published, advances the epoch.
+// Waits are bounded: after kScanSpins failed polls the tile records
+// PIC_ERR_TIMEOUT in *err (if given) and goes on with what it has.
+constexpr int kScanItems1 = 32;
+constexpr int kScanTile1 = kScanThreads * kScanItems1;  // 8192
+constexpr int kScanSpins = 1 << 22;
+
+__device__ __forceinline__ unsigned long long scan_ld(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 
-__global__ void k_scan_blocks(int32_t* blk, int nb, int32_t* total) {
-    int carry = 0;
-    for (int b0 = 0; b0 < nb; b0 += kScanThreads) {
-        int i = b0 + threadIdx.x;
-        int v = i < nb ? blk[i] : 0;
-        int tot;
-        int ex = block_exclusive_scan(v, &tot);
-        if (i < nb) blk[i] = carry + ex;
-        carry += tot;
-    }
-    if (threadIdx.x == 0 && total) *total = carry;
+__device__ __forceinline__ void scan_st(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-__global__ void k_scan_down(const int32_t* __restrict__ in, int32_t* __restrict__ out, int n,
-                            const int32_t* __restrict__ blk) {
-    const long long base = (long long)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
-    int v[kScanItems];
-    int s = 0;
+__global__ void __launch_bounds__(kScanThreads) k_scan_1pass(const int32_t* __restrict__ in,
+                                                             int32_t* __restrict__ out, int n,
+                                                             int32_t* blk, int32_t* total_dev,
+                                                             int* err) {
+    __shared__ int s_prefix;
+    const int b = blockIdx.x, nb = gridDim.x;
+    const unsigned tag = (unsigned)ld_volatile(blk) + 1u;
+    unsigned long long* agg = reinterpret_cast<unsigned long long*>(blk + 2);
+    unsigned long long* incl = agg + nb;
+    const long long base = (long long)b * kScanTile1 + (long long)threadIdx.x * kScanItems1;
+    const bool vec = (reinterpret_cast<uintptr_t>(in) & 15) == 0;  // 16-byte loads allowed
+    int v[kScanItems1];
+    int sum = 0;
 #pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        v[i] = base + i < n ? in[base + i] : 0;
-        s += v[i];
+    for (int i = 0; i < kScanItems1; i += 4) {
+        if (vec && base + i + 3 < n) {
+            const int4 q = *reinterpret_cast<const int4*>(in + base + i);
+            v[i] = q.x; v[i + 1] = q.y; v[i + 2] = q.z; v[i + 3] = q.w;
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[i + u] = base + i + u < n ? in[base + i + u] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) sum += v[i + u];
     }
-    int tot;
-    int ex = block_exclusive_scan(s, &tot) + blk[blockIdx.x];
+    int tile_total;
+    const int ex = block_exclusive_scan(sum, &tile_total);
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        int prefix = 0;
+        if (b == 0) {
+            if (lane == 0) scan_st(&incl[0], ((unsigned long long)tag << 32) | (unsigned)tile_total);
+        } else {
+            if (lane == 0) scan_st(&agg[b], ((unsigned long long)tag << 32) | (unsigned)tile_total);
+            int p = b - 1, spins = 0;
+            while (p >= 0) {
+                const int q = p - lane;  // tile read by this lane (q < 0: an inclusive 0)
+                unsigned long long wi = 0, wa = 0;
+                if (q >= 0) {
+                    wi = scan_ld(&incl[q]);
+                    wa = scan_ld(&agg[q]);
+                }
+                const bool inc_ok = q < 0 || (unsigned)(wi >> 32) == tag;
+                const bool agg_ok = inc_ok || (unsigned)(wa >> 32) == tag;
+                const unsigned incm = __ballot_sync(kFull, inc_ok);
+                const unsigned aggm = __ballot_sync(kFull, agg_ok);
+                const int first = incm ? __ffs(incm) - 1 : 32;
+                const unsigned need = first == 32 ? kFull : ((1u << first) - 1u) | (1u << first);
+                if ((aggm & need) == need) {
+                    int x = 0;
+                    if (lane < first) x = (int)(unsigned)wa;
+                    else if (lane == first && q >= 0) x = (int)(unsigned)wi;
 #pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        if (base + i < n) out[base + i] = ex;
-        ex += v[i];
+                    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+                    prefix += x;
+                    if (first < 32) break;
+                    p -= 32;
+                } else if (++spins > kScanSpins) {
+                    if (lane == 0 && err) atomicCAS(err, 0, (int)PIC_ERR_TIMEOUT);
+                    break;
+                } else {
+                    __nanosleep(32);
+                }
+            }
+            if (lane == 0)
+                scan_st(&incl[b], ((unsigned long long)tag << 32) | (unsigned)(prefix + tile_total));
+        }
+        if (lane == 0) {
+            s_prefix = prefix;
+            if (b == nb - 1) {
+                if (total_dev) *total_dev = prefix + tile_total;
+                atomicAdd(blk, 1);  // every tile has read the epoch: it published
+            }
+        }
+    }
+    __syncthreads();
+    int run = s_prefix + ex;
+#pragma unroll
+    for (int i = 0; i < kScanItems1; ++i) {
+        if (base + i < n) out[base + i] = run;
+        run += v[i];
     }
 }
 
@@ -165,32 +228,27 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
 }
 
 // --------------------------------------------------------------------------- tables
-// First sorted position of every product (K+1 entries, pstart[K] = T): a
-// lower-bound search in the sorted product column.
-__global__ void k_pstart(const int32_t* __restrict__ prod_s, int T, int K, int32_t* __restrict__ pstart) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k > K) return;
-    int lo = 0, hi = T;
-    while (lo < hi) {
-        const int mid = (int)(((unsigned)lo + (unsigned)hi) >> 1);
-        if (prod_s[mid] < k) lo = mid + 1; else hi = mid;
-    }
-    pstart[k] = lo;
-}
-
-// Region gather and run-start flags: a run starts where the product or the
-// chunk changes between consecutive sorted positions.  The chunk of order t is
-// t / L, or, in a batch, (t - toff[b]) / chunk_len[b] for the trajectory b that
-// owns the product (consecutive positions of one product share b).
+// Region gather, first sorted position of every product (pstart, K + 1
+// entries, pstart[K] = T: where the product changes between consecutive sorted
+// positions, every product in between starts there) and run-start flags: a run
+// starts where the product or the chunk changes between consecutive sorted
+// positions.  The chunk of order t is t / L, or, in a batch, (t - toff[b]) /
+// chunk_len[b] for the trajectory b that owns the product (consecutive
+// positions of one product share b).
 __global__ void k_run_flags(const int32_t* __restrict__ perm, const int32_t* __restrict__ prod_s,
                             const int32_t* __restrict__ reg, int32_t* __restrict__ reg_s, int T,
-                            int L, const int32_t* __restrict__ traj_of_prod,
+                            int K, int L, const int32_t* __restrict__ traj_of_prod,
                             const int32_t* __restrict__ toff, const int32_t* __restrict__ chunk_len,
-                            int32_t* __restrict__ flag) {
+                            int32_t* __restrict__ flag, int32_t* __restrict__ pstart) {
     long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= T) return;
     int t = perm[j];
     reg_s[j] = reg[t];
+    const int kj = prod_s[j];
+    const int kp = j > 0 ? prod_s[j - 1] : -1;
+    for (int k = kp + 1; k <= kj; ++k) pstart[k] = (int)j;
+    if (j == T - 1)
+        for (int k = kj + 1; k <= K; ++k) pstart[k] = T;
     int f = 1;
     if (j > 0 && prod_s[j] == prod_s[j - 1]) {
         int tp = perm[j - 1], len = L;
@@ -365,30 +423,27 @@ inline int nblocks(long long n, int per) { return (int)((n + per - 1) / per); }
 }  // namespace
 
 cudaError_t scan_exclusive(const int32_t* in, int32_t* out, int n, int32_t* total_dev, int32_t* blk,
-                           cudaStream_t st) {
+                           cudaStream_t st, int* err) {
     if (n <= 0) return cudaSuccess;
-    int nb = nblocks(n, kScanTile);
-    k_scan_reduce<<<nb, kScanThreads, 0, st>>>(in, n, blk);
-    k_scan_blocks<<<1, kScanThreads, 0, st>>>(blk, nb, total_dev);
-    k_scan_down<<<nb, kScanThreads, 0, st>>>(in, out, n, blk);
+    k_scan_1pass<<<nblocks(n, kScanTile1), kScanThreads, 0, st>>>(in, out, n, blk, total_dev, err);
     return cudaGetLastError();
 }
 
 int sort_hist_len(int n) { return 256 * nblocks(n, kRadixTile); }
-int scan_blk_len(int n) { return nblocks(n, kScanTile); }
+int scan_blk_len(int n) { return 2 + 4 * nblocks(n > 0 ? n : 1, kScanTile1); }
 
 cudaError_t sort_pairs(Instance* I, const int32_t* keys, int n, int max_key, int32_t* keys_out,
                        int32_t* vals_out, int32_t* tmp_k, int32_t* tmp_v, cudaStream_t st) {
     int passes = 1;
     while (passes < 4 && ((unsigned)max_key >> (8 * passes)) != 0) ++passes;
-    I->launches += n > 0 ? passes * 5 : 0;
+    I->launches += n > 0 ? passes * 3 : 0;
     return sort_pairs_raw(keys, n, max_key, keys_out, vals_out, tmp_k, tmp_v, I->hist,
-                          I->scan_blk, st);
+                          I->scan_blk, st, &I->ctrl->err);
 }
 
 cudaError_t sort_pairs_raw(const int32_t* keys, int n, int max_key, int32_t* keys_out,
                            int32_t* vals_out, int32_t* tmp_k, int32_t* tmp_v, int32_t* hist,
-                           int32_t* scan_blk, cudaStream_t st) {
+                           int32_t* scan_blk, cudaStream_t st, int* err) {
     if (n <= 0) return cudaSuccess;
     // LSD radix, 8-bit digits, as many passes as max_key has bytes; the passes
     // alternate between (tmp_k, tmp_v) and (keys_out, vals_out) so that the last
@@ -405,7 +460,7 @@ cudaError_t sort_pairs_raw(const int32_t* keys, int n, int max_key, int32_t* key
         int32_t* vout = last_side ? vals_out : tmp_v;
         const int shift = 8 * p;
         k_radix_hist<<<nblk, kRadixThreads, 0, st>>>(kin, n, shift, hist, nblk);
-        if ((e = scan_exclusive(hist, hist, 256 * nblk, nullptr, scan_blk, st))) return e;
+        if ((e = scan_exclusive(hist, hist, 256 * nblk, nullptr, scan_blk, st, err))) return e;
         k_radix_scatter<<<nblk, kRadixThreads, 0, st>>>(kin, vin, n, shift, hist, nblk, kout, vout);
         kin = kout;
         vin = vout;
@@ -420,18 +475,16 @@ cudaError_t build_tables(Instance* I, int M, int W, cudaStream_t st) {
     // 1. stable sort of (product, time) by product
     // kernel launches made below besides the sort: product offsets, run flags +
     // scan + runs, segment flags + scan + segments + chains
-    I->launches += 1 + 5 + 6;
+    I->launches += 3 + 4;
     if ((e = sort_pairs(I, I->prod, T, K - 1, I->prod_s, I->perm, I->tmp_a, I->tmp_b, st))) return e;
-    // 2. first sorted position of every product
-    k_pstart<<<nblocks(K + 1, 256), 256, 0, st>>>(I->prod_s, T, K, I->pstart);
-    // 3. runs for M chunks of L orders
+    // 2. first sorted position of every product, and runs for M chunks of L orders
     const long long L = ((long long)T + M - 1) / M;
     const Batch* bt = I->batch;
-    k_run_flags<<<nblocks(T, 256), 256, 0, st>>>(I->perm, I->prod_s, I->reg, I->reg_s, T, (int)L,
+    k_run_flags<<<nblocks(T, 256), 256, 0, st>>>(I->perm, I->prod_s, I->reg, I->reg_s, T, K, (int)L,
                                                   bt ? bt->traj_of_prod : nullptr,
                                                   bt ? bt->toff : nullptr,
-                                                  bt ? bt->chunk_len : nullptr, I->tmp_a);
-    if ((e = scan_exclusive(I->tmp_a, I->tmp_b, T, nullptr, I->scan_blk, st))) return e;
+                                                  bt ? bt->chunk_len : nullptr, I->tmp_a, I->pstart);
+    if ((e = scan_exclusive(I->tmp_a, I->tmp_b, T, nullptr, I->scan_blk, st, &I->ctrl->err))) return e;
     k_runs<<<nblocks(T, 256), 256, 0, st>>>(I->tmp_a, I->tmp_b, T, I->run_of, I->run_start, I->ctrl);
     if (!bt) {  // time block of each run (the max_steps window)
         k_run_chunk<<<nblocks(T, 256), 256, 0, st>>>(I->run_start, I->perm, (int)L, I->ctrl, T,
@@ -441,7 +494,7 @@ cudaError_t build_tables(Instance* I, int M, int W, cudaStream_t st) {
     // 4. segments (window W per product) and chains
     k_seg_flags<<<nblocks(T, 256), 256, 0, st>>>(I->run_start, I->prod_s, I->pstart, W, T, I->ctrl,
                                                   I->tmp_a);
-    if ((e = scan_exclusive(I->tmp_a, I->tmp_b, T, nullptr, I->scan_blk, st))) return e;
+    if ((e = scan_exclusive(I->tmp_a, I->tmp_b, T, nullptr, I->scan_blk, st, &I->ctrl->err))) return e;
     k_segs<<<nblocks(T, 256), 256, 0, st>>>(I->tmp_a, I->tmp_b, T, I->run_start, I->prod_s,
                                              I->seg_of_run, I->seg_run, I->seg_prod, I->ctrl);
     k_chains<<<nblocks(I->smax, 256), 256, 0, st>>>(I->seg_prod, I->seg_run, I->run_start,
@@ -459,9 +512,11 @@ cudaError_t build_lpt(Instance* I, const BatchPol* pol, int mlp_weight, cudaStre
     if (e) return e;
     const int sb = nblocks(I->smax, 256);
     const int32_t* top = I->batch ? I->batch->traj_of_prod : nullptr;
-    I->launches += 5;
+    I->launches += 3;
     k_len_hist<<<sb, 256, 0, st>>>(I->seg_meta, I->ctrl, top, pol, mlp_weight, I->len_hist);
-    if ((e = scan_exclusive(I->len_hist, I->len_hist, kLenBuckets, nullptr, I->scan_blk, st))) return e;
+    if ((e = scan_exclusive(I->len_hist, I->len_hist, kLenBuckets, nullptr, I->scan_blk, st,
+                            &I->ctrl->err)))
+        return e;
     k_len_scatter<<<sb, 256, 0, st>>>(I->seg_meta, I->ctrl, top, pol, mlp_weight, I->len_hist,
                                       I->seg_lpt);
     return cudaGetLastError();

@@ -207,3 +207,34 @@ def test_pass_trace_records_every_pass():
     assert tr[0, 2] == inst.T  # every order is evaluated in the first pass
     assert (tr[:n, 4] <= tr[:n, 2]).all() and (tr[:n, 4] <= tr[:n, 5]).all()
     assert ((tr[:n, 4] > 0) == (tr[:n, 2] > 0)).all()
+
+
+def test_reused_order_tables_equal_rebuilt_ones():
+    """PIC_FLAG_REUSE_TABLES keeps the order tables of an earlier call with the
+    same chunk count and segment window: the result equals the oracle's after
+    calls in other modes, other chunkings, other policies and a reload of the
+    inputs (which invalidates the tables)."""
+    R = pic.PIC_FLAG_REUSE_TABLES
+    inst = synth.dual_large(2, T=1 << 15, K=900, R=80)
+    d = DeviceInstance(inst)
+    check_against_oracle(inst, "dual", 256, dev=d)
+    for kind in ("dual", "greedy"):
+        check_against_oracle(inst, kind, 256, dev=d, flags=R)
+    check_against_oracle(inst, "dual", 512, dev=d, flags=R)  # other chunking: rebuilt
+    check_against_oracle(inst, "dual", 512, dev=d, flags=R, seg_window=8)
+    d.simulate(Policy("dual"), "sequential")
+    d.simulate(Policy("dual"), "products", num_chunks=300)
+    d.simulate(Policy("dual"), "assigned", num_chunks=64,
+               proc=torch.as_tensor(synth.uniform_assignment(inst.T, 64, seed=1)).cuda())
+    check_against_oracle(inst, "dual", 512, dev=d, flags=R, seg_window=8)
+    # max_steps window with kept tables
+    want = oracle.picard_windowed(inst, Policy("dual"), 512, 4096)
+    got = d.simulate(Policy("dual"), "picard", num_chunks=512, seg_window=8, max_steps=4096, flags=R)
+    np.testing.assert_array_equal(got["actions"].cpu().numpy(), want["actions"])
+    assert got["iters"] == want["iters"]
+    # new inputs of the same shape: the tables are rebuilt
+    inst2 = synth.dual_large(3, T=1 << 15, K=900, R=80)
+    d.inst = inst2
+    d.load_host({k: np.ascontiguousarray(getattr(inst2, k), np.int32)
+                 for k in ("prod", "reg", "x0", "cost", "lam")})
+    check_against_oracle(inst2, "dual", 512, dev=d, flags=R, seg_window=8)

@@ -64,6 +64,9 @@ struct PgState {
     double* dz;        // [R][256] per-region sums of dz
     double* J;         // objective
     int* bad;
+    int32_t* npc;      // [K + 1] pieces of each product longer than kPgPiece orders (else 0)
+    int32_t* poff;     // [K + 1] their exclusive prefix (poff[K]: all such pieces)
+    int32_t* pcnt;     // [T / kPgPiece + K bounded: see pg_alloc][64] actions per warehouse of a piece
 };
 
 }  // namespace pic
@@ -187,40 +190,134 @@ __global__ void k_pg_G(const int32_t* __restrict__ perm, const int32_t* __restri
 }
 
 // ---------------------------------------------------------------- stock features
-// One warp per product: its orders in sorted (= time) order from x0.  Writes
-// min(stock, 32) per warehouse (row stride kPgN, zero beyond N) and whether the
-// order counts; bit 1 of *bad: a fulfilled action found no stock.
+// The stock row of every order from x0 and the actions before it (per product,
+// in sorted = time order): min(stock, 32) per warehouse (row stride kPgN, zero
+// beyond N) and whether the order counts; bit 1 of *bad: a fulfilled action
+// found no stock.  A product of at most kPgPiece orders is walked by one warp;
+// a longer one is cut into pieces of kPgPiece orders, the actions of every
+// piece but its last counted per warehouse (k_pg_pcount), and each piece walked
+// by its own warp from x0 minus the counts of the pieces before it.
+constexpr int kPgPiece = 1024;
+
+__global__ void k_pg_npieces(int K, const int32_t* __restrict__ pstart, int32_t* __restrict__ npc) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > K) return;
+    const int len = k < K ? pstart[k + 1] - pstart[k] : 0;
+    npc[k] = len > kPgPiece ? (len + kPgPiece - 1) / kPgPiece : 0;
+}
+
+// Product of piece p: the last k with poff[k] <= p (poff nondecreasing).
+__device__ __forceinline__ int piece_product(const int32_t* __restrict__ poff, int K, int p) {
+    int lo = 0, hi = K;  // poff[lo] <= p < poff[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(poff + mid) <= p) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Walk orders [j0, j1) of one product from the stock row (S0, S1) (lanes hold
+// warehouses lane and lane + 32).
+__device__ __forceinline__ bool walk_stock(int j0, int j1, int S0, int S1,
+                                           const int8_t* __restrict__ alpha_s, int8_t* __restrict__ f8,
+                                           uint8_t* __restrict__ okf) {
+    const int lane = lane_id();
+    bool err = false;
+    for (int base = j0; base < j1; base += 32) {
+        const int cnt = min(32, j1 - base);
+        const int my_a = lane < cnt ? alpha_s[base + lane] : -1;
+        int my_ok = 0;
+        for (int q = 0; q < cnt; ++q) {
+            const int a = __shfl_sync(kFull, my_a, q);
+            int8_t* row = f8 + (size_t)(base + q) * kPgN;
+            row[lane] = (int8_t)max(-128, min(S0, 32));
+            row[lane + 32] = (int8_t)max(-128, min(S1, 32));
+            const int nf = __popc(__ballot_sync(kFull, S0 > 0)) + __popc(__ballot_sync(kFull, S1 > 0));
+            if (a >= 0) {
+                if (a == lane) { err |= S0 <= 0; S0 -= 1; }
+                if (a == lane + 32) { err |= S1 <= 0; S1 -= 1; }
+            }
+            if (lane == q) my_ok = (a >= 0 && nf >= 2) ? 1 : 0;
+        }
+        if (lane < cnt) okf[base + lane] = (uint8_t)my_ok;
+    }
+    return err;
+}
+
+// Products of at most kPgPiece orders, one warp each.
 __global__ void k_pg_stock(int K, int N, const int32_t* __restrict__ pstart,
                            const int8_t* __restrict__ alpha_s, const int32_t* __restrict__ x0,
                            int8_t* __restrict__ f8, uint8_t* __restrict__ okf, int* bad) {
     const int lane = lane_id();
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
+    bool err = false;
     for (int k = gw; k < K; k += nw) {
         const int j0 = pstart[k], j1 = pstart[k + 1];
+        if (j1 - j0 > kPgPiece) continue;
+        const int S0 = lane < N ? x0[(size_t)k * N + lane] : 0;
+        const int S1 = lane + 32 < N ? x0[(size_t)k * N + lane + 32] : 0;
+        err |= walk_stock(j0, j1, S0, S1, alpha_s, f8, okf);
+    }
+    if (__any_sync(kFull, err) && lane == 0) atomicOr(bad, 1);
+}
+
+// Actions per warehouse of every piece but the last of its product, one warp
+// per piece (per-warp bins in shared memory).
+__global__ void __launch_bounds__(256) k_pg_pcount(int K, const int32_t* __restrict__ pstart,
+                                                   const int32_t* __restrict__ npc,
+                                                   const int32_t* __restrict__ poff,
+                                                   const int8_t* __restrict__ alpha_s,
+                                                   int32_t* __restrict__ pcnt) {
+    __shared__ int bins[8][kPgN];
+    const int lane = lane_id(), w = threadIdx.x >> 5;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int np = poff[K];
+    for (int p = gw; p < np; p += nw) {
+        const int k = piece_product(poff, K, p);
+        const int i = p - poff[k];
+        if (i == npc[k] - 1) continue;  // the last piece's counts are never needed
+        bins[w][lane] = 0;
+        bins[w][lane + 32] = 0;
+        __syncwarp();
+        const int j0 = pstart[k] + i * kPgPiece;
+        for (int j = j0 + lane; j < j0 + kPgPiece; j += 32) {
+            const int a = alpha_s[j];
+            if (a >= 0 && a < kPgN) atomicAdd(&bins[w][a], 1);  // a path's actions are < N
+        }
+        __syncwarp();
+        pcnt[(size_t)p * kPgN + lane] = bins[w][lane];
+        pcnt[(size_t)p * kPgN + lane + 32] = bins[w][lane + 32];
+        __syncwarp();
+    }
+}
+
+// Pieces of the longer products, one warp each: x0 minus the counts of the
+// product's earlier pieces, then the walk.
+__global__ void k_pg_stock_pieces(int K, int N, const int32_t* __restrict__ pstart,
+                                  const int32_t* __restrict__ poff, const int32_t* __restrict__ pcnt,
+                                  const int8_t* __restrict__ alpha_s, const int32_t* __restrict__ x0,
+                                  int8_t* __restrict__ f8, uint8_t* __restrict__ okf, int* bad) {
+    const int lane = lane_id();
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int np = poff[K];
+    bool err = false;
+    for (int p = gw; p < np; p += nw) {
+        const int k = piece_product(poff, K, p);
+        const int p0 = poff[k];
         int S0 = lane < N ? x0[(size_t)k * N + lane] : 0;
         int S1 = lane + 32 < N ? x0[(size_t)k * N + lane + 32] : 0;
-        bool err = false;
-        for (int base = j0; base < j1; base += 32) {
-            const int cnt = min(32, j1 - base);
-            const int my_a = lane < cnt ? alpha_s[base + lane] : -1;
-            int my_ok = 0;
-            for (int q = 0; q < cnt; ++q) {
-                const int a = __shfl_sync(kFull, my_a, q);
-                int8_t* row = f8 + (size_t)(base + q) * kPgN;
-                row[lane] = (int8_t)max(-128, min(S0, 32));
-                row[lane + 32] = (int8_t)max(-128, min(S1, 32));
-                const int nf = __popc(__ballot_sync(kFull, S0 > 0)) + __popc(__ballot_sync(kFull, S1 > 0));
-                if (a >= 0) {
-                    if (a == lane) { err |= S0 <= 0; S0 -= 1; }
-                    if (a == lane + 32) { err |= S1 <= 0; S1 -= 1; }
-                }
-                if (lane == q) my_ok = (a >= 0 && nf >= 2) ? 1 : 0;
-            }
-            if (lane < cnt) okf[base + lane] = (uint8_t)my_ok;
+        for (int q = p0; q < p; ++q) {
+            S0 -= pcnt[(size_t)q * kPgN + lane];
+            S1 -= pcnt[(size_t)q * kPgN + lane + 32];
         }
-        if (__any_sync(kFull, err) && lane == 0) atomicOr(bad, 1);
+        const int j0 = pstart[k] + (p - p0) * kPgPiece;
+        const int j1 = min(pstart[k + 1], j0 + kPgPiece);
+        err |= walk_stock(j0, j1, S0, S1, alpha_s, f8, okf);
     }
+    if (__any_sync(kFull, err) && lane == 0) atomicOr(bad, 1);
 }
 
 // ---------------------------------------------------------------- the tile kernel
@@ -1009,7 +1106,7 @@ pic_status pg_alloc(Instance& I, int e_rows, int64_t P) {
     if (g && g->P == P && g->e_rows == e_rows) return PIC_OK;
     if (g) {
         void* ptrs[] = {g->pbf, g->acts, g->cost, g->pex, g->blk, g->G, g->f8, g->ok, g->rq, g->jq,
-                        g->acc, g->dz, g->J, g->bad};
+                        g->acc, g->dz, g->J, g->bad, g->npc, g->poff, g->pcnt};
         for (void* q : ptrs)
             if (q) cudaFree(q);
         delete g;
@@ -1038,6 +1135,10 @@ pic_status pg_alloc(Instance& I, int e_rows, int64_t P) {
     PCU(cudaMalloc((void**)&g->dz, sizeof(double) * (size_t)I.R * kHidden));
     PCU(cudaMalloc((void**)&g->J, sizeof(double)));
     PCU(cudaMalloc((void**)&g->bad, sizeof(int)));
+    // pieces: a product longer than kPgPiece has ceil(len / kPgPiece) <= 2 len / kPgPiece
+    PCU(cudaMalloc((void**)&g->npc, sizeof(int32_t) * ((size_t)I.K + 1)));
+    PCU(cudaMalloc((void**)&g->poff, sizeof(int32_t) * ((size_t)I.K + 1)));
+    PCU(cudaMalloc((void**)&g->pcnt, sizeof(int32_t) * kPgN * (2 * T / kPgPiece + 1)));
     return PIC_OK;
 }
 
@@ -1048,7 +1149,7 @@ void free_pg(Instance& I) {
     PgState* g = I.pg;
     if (!g) return;
     void* ptrs[] = {g->pbf, g->acts, g->cost, g->pex, g->blk, g->G, g->f8, g->ok, g->rq, g->jq,
-                    g->acc, g->dz, g->J, g->bad};
+                    g->acc, g->dz, g->J, g->bad, g->npc, g->poff, g->pcnt};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete g;
@@ -1150,8 +1251,14 @@ extern "C" pic_status pic_policy_grad(pic_instance* h, const pic_policy* pols, c
         k_scan64_blocks<<<1, kS64Threads, 0, st>>>(g->blk, nb, g->pex + T);
         k_scan64_down<<<nb, kS64Threads, 0, st>>>(g->cost, g->pex, T, g->blk);
         k_pg_G<<<grid, 256, 0, st>>>(I.perm, I.prod_s, bt->traj_of_prod, bt->toff, g->pex, T, g->G);
-        // 4. stock features
+        // 4. stock features: short products one warp each; long ones in pieces
+        k_pg_npieces<<<nblk(I.K + 1, 256), 256, 0, st>>>(I.K, I.pstart, g->npc);
+        PCU(scan_exclusive(g->npc, g->poff, I.K + 1, nullptr, I.scan_blk, st, &I.ctrl->err));
+        k_pg_pcount<<<grid, 256, 0, st>>>(I.K, I.pstart, g->npc, g->poff, I.alpha_s, g->pcnt);
         k_pg_stock<<<grid, 256, 0, st>>>(I.K, N, I.pstart, I.alpha_s, I.x0, g->f8, g->ok, g->bad);
+        k_pg_stock_pieces<<<grid, 256, 0, st>>>(I.K, N, I.pstart, g->poff, g->pcnt, I.alpha_s, I.x0,
+                                                g->f8, g->ok, g->bad);
+        launches += 4;
         PCU(cudaGetLastError());
         // 5. region order
         const int l0 = I.launches;

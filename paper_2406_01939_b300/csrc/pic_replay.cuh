@@ -115,6 +115,7 @@ __device__ __forceinline__ bool replay_segment(const KArgs& a, const CostTable<S
 #pragma unroll
         for (int i = 0; i < NPL; ++i)
             c_n[i] = (FULL || lane + 32 * i < N) ? ct.at(rr_n, lane + 32 * i) : 0;
+#pragma unroll 4
         for (int q = 0; q < cnt; ++q) {
             const int ao = ao_n;
             int c[NPL];

@@ -128,7 +128,7 @@ __device__ __forceinline__ unsigned long long tagged(unsigned tag, int v) {
 // recorded and the pass is abandoned at the next grid barrier.
 // ROWS: histogram rows loaded per round trip (a whole super-block when
 // registers allow).
-template <int NPL, int ROWS = 8 / NPL>
+template <int NPL, int ROWS = 16 / NPL>
 __device__ __forceinline__ void superblock_prefix(const KArgs& a, int s, const SegMeta& m, int it,
                                                   unsigned tag, int fcp,
                                                   unsigned long long deadline) {
@@ -232,7 +232,7 @@ __device__ __forceinline__ void superblock_prefix(const KArgs& a, int s, const S
 // a cache started from alpha_init) are assigned to warps gwarp + j * nwarps, 32
 // at a time, and run superblock_prefix.  s_meta / s_fcp: this warp's staging
 // rows (32 entries each).
-template <int NPL, int ROWS = 8 / NPL>
+template <int NPL, int ROWS = 16 / NPL>
 __device__ __forceinline__ void chain_prefixes(const KArgs& a, int it, const int* fc_prev,
                                                unsigned tag, unsigned long long deadline,
                                                SegMeta* s_meta, int* s_fcp) {

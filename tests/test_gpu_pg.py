@@ -86,6 +86,22 @@ def test_paths_objective_and_gradient_match_oracle(N):
     assert_close_grad(g, gw)
 
 
+def test_long_products_walked_in_pieces():
+    """Products with more than 1,024 orders (K = 3 over 9,000 and 5,000 orders):
+    their stock features are walked in pieces from per-piece action counts; the
+    objective and gradient equal the oracle's, and so do the paths."""
+    insts, mlp, pols = case(12, [9000, 5000], 32, K=3, R=7, fill=1.2)
+    assert min(np.bincount(i.prod).max() for i in insts) > 2 * 1024
+    db, rf, m, acts, J, J2, g = run_gpu(insts, pols, mlp)
+    P = pg.bf16_params_f64(mlp)
+    Jw, gw, paths = oracle_batch(insts, pols, P)
+    a = acts.cpu().numpy()
+    for b in range(len(insts)):
+        np.testing.assert_array_equal(db.split(a)[b], paths[b])
+    assert abs(J - Jw) <= 1e-5 * abs(Jw) and abs(J2 - Jw) <= 1e-5 * abs(Jw)
+    assert_close_grad(g, gw)
+
+
 def test_gradient_vs_fp64_central_differences():
     """Central differences of the FP64 objective at sampled coordinates of every
     parameter tensor; each coordinate tried with two steps (a step can cross a

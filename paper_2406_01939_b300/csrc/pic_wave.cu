@@ -92,6 +92,11 @@ struct __align__(16) WaveSmem {
     // them: {unit, product, first position, end | chained << 31}
     int4 ring[kRing];
     unsigned long long acc[4];
+    // slots that finished a unit (its row's histogram to write) or started one
+    // (its start row to build) in this wave's advance: done by all warps
+    int fin_seg[kWRows], fin_row[kWRows];
+    int st_row[kWRows], st_seg[kWRows], st_k[kWRows], st_low[kWRows];
+    int n_fin, n_start;
     int n_near, fail, any_net;
     int ring_head, ring_tail, scan_i, share_done;
     unsigned long long mbar;
@@ -149,48 +154,22 @@ __device__ __forceinline__ void load_order(const KArgs& a, int j, int t_off, int
     tt = __ldg(a.perm + j) - t_off;
 }
 
-// Start the slot's new work unit seg (metadata m): S0 = max(0, x0 - D) with D
-// the cached actions of its product before it (chain prefix), S = S0, the
-// policy of its trajectory, and the first order's data.
+// Take the work unit e for the slot: its product, orders and policy, and the
+// first order's data; the start row S0 = S = max(0, x0 - D) (D the cached
+// actions of its product before it, the chain prefix) is built by rows_coop.
 template <bool BATCH>
-__device__ void slot_start(const WaveCtx<BATCH>& c, int t, Slot& sl, const int4 e) {
+__device__ void slot_take(const WaveCtx<BATCH>& c, int t, Slot& sl, const int4 e) {
     const KArgs& a = c.a;
     WaveSmem& s = c.s;
-    const int seg = e.x;
-    sl.seg = seg;
+    sl.seg = e.x;
     sl.k = e.y;
     sl.j = e.z;
     sl.jend = e.w & 0x7FFFFFFF;
     const bool chained = (e.w >> 31) & 1;
-    int low = 0;
-    const int4* x4 = reinterpret_cast<const int4*>(a.x0 + (size_t)sl.k * a.N);
-    // carry rows are NP ints (NP a multiple of 32, 16-byte aligned rows)
-    const int4* c4 = reinterpret_cast<const int4*>(a.carry + (size_t)seg * a.NP);
-    if ((a.N & 3) == 0) {
-#pragma unroll 8
-        for (int q = 0; q < a.N / 4; ++q) {
-            const int4 x = __ldg(x4 + q);
-            const int4 d = chained ? c4[q] : make_int4(0, 0, 0, 0);
-            const int v0 = max(0, x.x - d.x), v1 = max(0, x.y - d.y);
-            const int v2 = max(0, x.z - d.z), v3 = max(0, x.w - d.w);
-            s.S[t][4 * q] = v0; s.S[t][4 * q + 1] = v1; s.S[t][4 * q + 2] = v2; s.S[t][4 * q + 3] = v3;
-            s.S0[t][4 * q] = v0; s.S0[t][4 * q + 1] = v1; s.S0[t][4 * q + 2] = v2; s.S0[t][4 * q + 3] = v3;
-            low += (v0 < 32) + (v1 < 32) + (v2 < 32) + (v3 < 32);
-        }
-    } else {
-        for (int n = 0; n < a.N; ++n) {
-            const int d = chained ? a.carry[(size_t)seg * a.NP + n] : 0;
-            const int v = max(0, __ldg(a.x0 + (size_t)sl.k * a.N + n) - d);
-            s.S[t][n] = v;
-            s.S0[t][n] = v;
-            low += v < 32;
-        }
-    }
-    for (int n = a.N; n < kWN; ++n) {
-        s.S[t][n] = 0;
-        s.S0[t][n] = 0;
-    }
-    sl.low = low;
+    const int i = atomicAdd(&s.n_start, 1);
+    s.st_row[i] = t;
+    s.st_seg[i] = chained ? sl.seg : -1 - sl.seg;  // -1 - seg: no chain prefix
+    s.st_k[i] = sl.k;
     sl.first_chg = INT_MAX;
     sl.evals = 0;
     if constexpr (BATCH) {
@@ -210,20 +189,81 @@ __device__ void slot_start(const WaveCtx<BATCH>& c, int t, Slot& sl, const int4 
     load_order(a, sl.j, sl.t_off, sl.nx_ao, sl.nx_r, sl.nx_t);
 }
 
-// Close the slot's work unit: its histogram of new actions for the next pass's
-// prefix (S0 - S: every order of the unit was evaluated and each fresh action
-// took one unit) and the first-change records.  The final stock is computed
+// The rows of the slots listed by this wave's advance, one warp per row and
+// lanes over warehouses (every thread of the CTA calls it): first the
+// histograms of new actions of the finished units (S0 - S: every order of a
+// unit was evaluated and each fresh action took one unit) for the next pass's
+// prefix, then the start rows of the new units, S0 = S = max(0, x0 - D), and
+// their count of warehouses below 32 units.
+__device__ void rows_coop(const KArgs& a, WaveSmem& s) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int N = a.N, NP = a.NP;
+    for (int i = warp; i < s.n_fin; i += kWWarps) {
+        const int f = s.fin_row[i];
+        int32_t* g = a.agg + (size_t)s.fin_seg[i] * NP;
+        for (int n = lane; n < NP; n += 32) g[n] = s.S0[f][n] - s.S[f][n];
+    }
+    __syncthreads();
+    // up to 4 rows per warp at a time, their loads issued together
+    const int ns = s.n_start;
+    for (int i0 = warp; i0 < ns; i0 += 4 * kWWarps) {
+        int xv[4][kWN / 32], dv[4][kWN / 32];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * kWWarps;
+            const int sg = i < ns ? s.st_seg[i] : -1, k = i < ns ? s.st_k[i] : 0;
+            const int seg = sg >= 0 ? sg : -1 - sg;
+#pragma unroll
+            for (int h = 0; h < kWN / 32; ++h) {
+                const int n = lane + 32 * h;
+                const bool in = i < ns && n < N;
+                xv[u][h] = in ? __ldg(a.x0 + (size_t)k * N + n) : 0;
+                dv[u][h] = (in && sg >= 0) ? a.carry[(size_t)seg * NP + n] : 0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * kWWarps;
+            if (i >= ns) break;  // warp-uniform
+            const int row = s.st_row[i];
+            int low = 0;
+#pragma unroll
+            for (int h = 0; h < kWN / 32; ++h) {
+                const int n = lane + 32 * h;
+                const int v = max(0, xv[u][h] - dv[u][h]);
+                s.S[row][n] = v;
+                s.S0[row][n] = v;
+                low += __popc(__ballot_sync(kFull, n < N && v < 32));
+            }
+            if (lane == 0) s.st_low[row] = low;
+        }
+    }
+    __syncthreads();
+}
+
+// The stock features min(S, 32) / 32 of every network row, one thread per row
+// and group of 16 warehouses (every thread of the CTA calls it).
+__device__ __forceinline__ void features_coop(WaveSmem& s) {
+    const int row = threadIdx.x & (kWRows - 1), c0 = 16 * (threadIdx.x >> 7);
+    if (s.row_mode[row] == kRowNet) {
+        float fv[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) fv[i] = (float)min(s.S[row][c0 + i], 32) * 0.03125f;  // exact
+        st_row16(s.f, row, c0, kWN, fv);
+    }
+}
+
+// Close the slot's work unit: list its row for the histogram of new actions
+// (written by rows_coop) and keep the first-change records.  The final stock is computed
 // after the passes from the final cache (k_wave_xfin).  Returns whether it
 // changed a cached action.
 template <bool BATCH>
 __device__ bool slot_finish(const WaveCtx<BATCH>& c, int t, Slot& sl) {
     const KArgs& a = c.a;
     WaveSmem& s = c.s;
-    int4* g4 = reinterpret_cast<int4*>(a.agg + (size_t)sl.seg * a.NP);
-#pragma unroll 4
-    for (int q = 0; q < a.NP / 4; ++q)
-        g4[q] = make_int4(s.S0[t][4 * q] - s.S[t][4 * q], s.S0[t][4 * q + 1] - s.S[t][4 * q + 1],
-                          s.S0[t][4 * q + 2] - s.S[t][4 * q + 2], s.S0[t][4 * q + 3] - s.S[t][4 * q + 3]);
+    const int i = atomicAdd(&s.n_fin, 1);  // its row's histogram: rows_coop
+    s.fin_row[i] = t;
+    s.fin_seg[i] = sl.seg;
     const bool chg = sl.first_chg != INT_MAX;
     if (chg) {
         if (sl.first_chg < ld_volatile(&c.fc_cur[sl.k])) atomicMin(&c.fc_cur[sl.k], sl.first_chg);
@@ -289,15 +329,13 @@ __device__ void ring_refill(const WaveCtx<BATCH>& c) {
     __syncthreads();
 }
 
-// Advance the slots of one warp (warps 0-3; every lane calls it): finish the
-// units whose orders are all decided; give every lane without a unit the next
-// unit of the ring; set up each busy lane's next order as a row of the wave.
-// Returns whether this lane has a pending decision.
+// Advance the slots of one warp (warps 0-3; every lane calls it), first half:
+// finish the units whose orders are all decided; give every lane without a
+// unit the next unit of the ring.  The rows of both are listed for rows_coop.
 template <bool BATCH>
-__device__ bool slot_advance(const WaveCtx<BATCH>& c, int t, Slot& sl,
-                             bool& changed, unsigned long long& units, unsigned long long& calls,
-                             unsigned long long& ucalls, unsigned long long& uorders) {
-    const KArgs& a = c.a;
+__device__ void slot_open(const WaveCtx<BATCH>& c, int t, Slot& sl,
+                          bool& changed, unsigned long long& units, unsigned long long& calls,
+                          unsigned long long& ucalls, unsigned long long& uorders) {
     WaveSmem& s = c.s;
     const int lane = t & 31;
     if (sl.seg >= 0 && sl.j == sl.jend) {
@@ -314,9 +352,20 @@ __device__ bool slot_advance(const WaveCtx<BATCH>& c, int t, Slot& sl,
         if (lane == 0) base = atomicAdd(&s.ring_head, __popc(need));
         base = __shfl_sync(kFull, base, 0);
         const int idx = base + __popc(need & ((1u << lane) - 1u));
-        if (sl.seg < 0 && idx < ld_volatile(&s.ring_tail)) slot_start<BATCH>(c, t, sl, s.ring[idx % kRing]);
+        if (sl.seg < 0 && idx < ld_volatile(&s.ring_tail)) slot_take<BATCH>(c, t, sl, s.ring[idx % kRing]);
     }
+}
+
+// Second half, after rows_coop: set up each busy lane's next order as a row of
+// the wave (its features are written by features_coop).  started: the slot
+// took its unit in this advance (its count of low warehouses comes from
+// rows_coop).  Returns whether this lane has a pending decision.
+template <bool BATCH>
+__device__ bool slot_row(const WaveCtx<BATCH>& c, int t, Slot& sl, bool started) {
+    const KArgs& a = c.a;
+    WaveSmem& s = c.s;
     if (sl.seg < 0) return false;
+    if (started) sl.low = s.st_low[t];
     const int ao = sl.nx_ao, r = sl.nx_r, tt = sl.nx_t;
     if (sl.j + 1 < sl.jend) load_order(a, sl.j + 1, sl.t_off, sl.nx_ao, sl.nx_r, sl.nx_t);
     sl.evals += 1;
@@ -331,14 +380,6 @@ __device__ bool slot_advance(const WaveCtx<BATCH>& c, int t, Slot& sl,
     s.row_gum[t] = sl.kind == PIC_POLICY_GUMBEL;
     s.row_seed[t] = sl.seed;
     s.row_traj[t] = sl.traj;
-    if (mode == kRowNet) {
-        float fv[16];
-        for (int c0 = 0; c0 < kWN; c0 += 16) {
-#pragma unroll
-            for (int i = 0; i < 16; ++i) fv[i] = (float)min(s.S[t][c0 + i], 32) * 0.03125f;  // exact
-            st_row16(s.f, t, c0, kWN, fv);
-        }
-    }
     sl.ao = ao;
     return true;
 }
@@ -616,10 +657,20 @@ __global__ void __launch_bounds__(kWThreads, 1) k_picard_wave(KArgs a, MlpPolicy
         bool ok = s.fail == 0;
         while (ok) {
             ring_refill<BATCH>(c);
-            bool pend = false, net = false;
+            if (tid == 0) s.n_fin = s.n_start = 0;
+            __syncthreads();
+            bool started = false;
             if (tid < kWRows) {
                 s.row_mode[tid] = kRowNone;
-                pend = slot_advance<BATCH>(c, tid, sl, changed, units, scalls, umax, omax);
+                const int seg0 = sl.seg;
+                slot_open<BATCH>(c, tid, sl, changed, units, scalls, umax, omax);
+                started = sl.seg >= 0 && sl.seg != seg0;  // a unit is never taken twice
+            }
+            __syncthreads();
+            rows_coop(a, s);
+            bool pend = false, net = false;
+            if (tid < kWRows) {
+                pend = slot_row<BATCH>(c, tid, sl, started);
                 net = pend && s.row_mode[tid] == kRowNet;
             }
             if (tid == 0) s.n_near = 0;
@@ -633,6 +684,7 @@ __global__ void __launch_bounds__(kWThreads, 1) k_picard_wave(KArgs a, MlpPolicy
                 if (more) continue;
                 break;
             }
+            features_coop(s);
             // a few network rows are faster on the FP32 scorer, one warp each
             if (tid == 0) s.any_net = nnet > small;
             tc_sync_operands();  // the rows' features reach the tensor cores

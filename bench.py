@@ -113,7 +113,7 @@ def parse():
 
 # mlp_medium: the window of App. A.3 (16,384 orders = 4 chunks), short segments
 DEFAULT_MAX_STEPS = {"mlp_medium": 16384, "owmr_base": 80_000}
-DEFAULT_SEG_WINDOW = {"mlp_medium": 4}
+DEFAULT_SEG_WINDOW = {"mlp_medium": 4, "greedy_small": 16}
 
 DEFAULT_CHUNKS = {"dual_large": 4096, "greedy_small": 64, "mlp_medium": 4096, "batch_uneven": 0,
                   "pg_large": 0, "capacity_large": 16384}

@@ -564,7 +564,8 @@ def run_batch(args, dev, world, rank):
     # sequential simulator on the first orders of the first MLP trajectory
     tr = np.zeros((4096, 6), np.int64)
     db.simulate(pols, "picard", num_chunks=last["num_chunks"], seg_window=last["seg_window"],
-                flags=args.flags, want_stock=False, out=act, trace=tr)
+                flags=args.flags | (pic.PIC_FLAG_WAVE if last["wave"] else 0), want_stock=False,
+                out=act, trace=tr)
     pass_trace = pass_trace_of(tr, last["iters"])
     from paper_2406_01939_b300.session import DeviceInstance
     bm = next(b for b, p in enumerate(pols) if p.kind != "greedy")
@@ -609,6 +610,7 @@ def run_batch(args, dev, world, rank):
             t0 = time.perf_counter()
             hb = DeviceBatch(host, device=dev, mem=pic.PIC_MEM_HOST)
             hb.simulate(pols, "picard", num_chunks=last["num_chunks"], seg_window=last["seg_window"],
+                        flags=args.flags | (pic.PIC_FLAG_WAVE if last["wave"] else 0),
                         want_stock=False, out=host_act, out_mem=pic.PIC_MEM_HOST)
             hb.close()
             t1 = time.perf_counter()
@@ -766,7 +768,7 @@ def run_pg(args, dev, world, rank):
             m_dev = master_h.to(dev, non_blocking=True)
             hrf = Reinforce(hb, ["gumbel"] * B, [1000 + b for b in range(B)], list(range(B)),
                             insts[0].R, num_chunks=res.num_chunks, seg_window=res.seg_window,
-                            flags=args.flags)
+                            flags=args.flags | (pic.PIC_FLAG_WAVE if res.wave else 0))
             Jh, _ = hrf.step(m_dev, grad)
             hb.close()
             t1 = time.perf_counter()

@@ -33,13 +33,14 @@
 // trajectories' orders from the cost table (arg min, lowest index on ties).
 //
 // Slots: thread t < 128 (warps 0-3) owns slot t: it takes work units from the
-// CTA's share of the pass's longest-first order, walks their orders (run
-// starts in closed form max(0, x0 - D), cached actions of runs the pass does
-// not evaluate, the new cache, the per-segment histogram for the next pass's
-// prefix), and stops at each order that needs a decision.  The stock row S and
-// the cached-action counts D of each slot live in shared memory.  All 16 warps
-// take part in the epilogues: warp w reads TMEM lanes 32 (w % 4) .. + 31 and
-// the column quarter w / 4.
+// CTA's share of the pass's longest-first order (through a ring of active
+// units), walks their orders (the new cache, the first changes) and stops at
+// each order that needs a decision.  The stock rows S (current) and S0 (at the
+// unit's start, the closed form max(0, x0 - D)) of each slot live in shared
+// memory; all 16 warps build the start rows of the units taken in a wave, write
+// the histograms S0 - S of the units finished (the next pass's prefix) and the
+// rows' stock features.  All 16 warps take part in the epilogues: warp w reads
+// TMEM lanes 32 (w % 4) .. + 31 and the column quarter w / 4.
 #include <cstddef>
 
 #include "pic_mlp.cuh"

@@ -156,3 +156,19 @@ def test_uniform_random_assignment_with_capacity(N):
             g = d.simulate(Policy("dual"), "assigned", num_chunks=9, proc=proc, max_iters=k,
                            raise_on_error=False)
             np.testing.assert_array_equal(g["actions"].cpu().numpy(), rec["iterates"][k - 1])
+
+
+def test_capacity_replay_rejects_bad_processes_and_handles_empty_ones():
+    """With capacity: a process outside [0, P) is an error before any pass;
+    processes that own no orders (P larger than the orders) are skipped."""
+    inst = make(77, 200, 16, 4, fill=0.8)
+    inst.cap = synth.node_capacity(inst.T, inst.N, seed=1, frac=0.6)
+    d = DeviceInstance(inst)
+    proc = synth.uniform_assignment(inst.T, 5, seed=2)
+    bad = proc.copy()
+    bad[3] = 5
+    with pytest.raises(pic.PicError) as e:
+        d.simulate(Policy("dual"), "assigned", num_chunks=5, proc=bad)
+    assert e.value.status == pic.PIC_ERR_INVALID_ARG and "proc" in str(e.value)
+    sparse = np.arange(inst.T, dtype=np.int32) % 7 * 50  # processes 0, 50, ..., 300 of 350
+    check(inst, "dual", sparse, 350, dev=d)

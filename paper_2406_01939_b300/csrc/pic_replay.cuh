@@ -13,9 +13,12 @@ namespace picard {
 // changed in the previous pass (-1: every run is evaluated).
 //
 // Per run the state starts at max(0, x0 - D), D = counts of cached actions of
-// this product before the run.  D advances run by run: the run's own new
-// actions (S0 - S at the run's end) plus a correction for the orders whose new
-// action differs from the cached one (rare once the iteration settles).
+// this product before the run.  The walk keeps E = D + the run's actions so far
+// per warehouse, and the stock is max(0, x0 - E): a warehouse at or below zero
+// at the run's start is never chosen, so the clamp commutes with the run's
+// decrements, and a warehouse has stock iff E < x0.  At a run's end E takes
+// the correction for the orders whose new action differs from the cached one
+// (rare once the iteration settles) and is the next run's D.
 template <int NPL, bool DUAL, bool SMEM, bool FULL>
 __device__ __forceinline__ bool replay_segment(const KArgs& a, const CostTable<SMEM>& ct, int s,
                                                const SegMeta& m, int fcp, int* fc_cur, int it,
@@ -24,7 +27,7 @@ __device__ __forceinline__ bool replay_segment(const KArgs& a, const CostTable<S
     const int N = a.N, NP = a.NP;
     const int k = m.k;
     // key = score * 128 + n (ties to the lowest index); adj = n - 128 * lam[k][n]
-    int D[NPL], x0v[NPL], adj[NPL], S[NPL], S0[NPL], hist[NPL], corr[NPL];
+    int D0[NPL], E[NPL], x0v[NPL], adj[NPL], corr[NPL], ctot[NPL];
     // prefix counts from earlier segments of this product (exclusive chain
     // prefix); none before pass 1 of an all-a^phi cache
     const bool chained = m.ce - m.cf > 1 && (it > 1 || a.first_dirty);
@@ -32,11 +35,12 @@ __device__ __forceinline__ bool replay_segment(const KArgs& a, const CostTable<S
     for (int i = 0; i < NPL; ++i) {
         const int n = lane + 32 * i;
         const bool in = FULL || n < N;
-        hist[i] = 0;
         corr[i] = 0;
+        ctot[i] = 0;
         x0v[i] = in ? a.x0[(size_t)k * N + n] : 0;
         adj[i] = n - ((DUAL && use_lam && in) ? 128 * a.lam[(size_t)k * N + n] : 0);
-        D[i] = chained ? a.carry[(size_t)s * NP + n] : 0;
+        D0[i] = chained ? a.carry[(size_t)s * NP + n] : 0;
+        E[i] = D0[i];
     }
     const int j0 = m.j0, jend = m.jend;
     // Runs starting at or before fcp keep their cached actions (t_reset), so
@@ -72,10 +76,7 @@ __device__ __forceinline__ bool replay_segment(const KArgs& a, const CostTable<S
                 }
             }
 #pragma unroll
-            for (int i = 0; i < NPL; ++i) {
-                D[i] += cnt[i];
-                hist[i] += cnt[i];
-            }
+            for (int i = 0; i < NPL; ++i) E[i] += cnt[i];
         }
     }
     // lane i holds the end (= next start) of run rwin + i
@@ -89,11 +90,6 @@ __device__ __forceinline__ bool replay_segment(const KArgs& a, const CostTable<S
     // this run's prefix changed in the previous pass (or it entered the window)
     bool eval = run_evaluated(a, whi, wprev, r, jst > fcp);
     unsigned long long evals = eval ? (unsigned long long)(next_run - jst) : 0ull;
-#pragma unroll
-    for (int i = 0; i < NPL; ++i) {
-        S[i] = max(0, x0v[i] - D[i]);
-        S0[i] = S[i];
-    }
     int first_chg = INT_MAX;
     int nreg = 0, nold = -1;
     if (lane < jend - jst) {
@@ -131,11 +127,9 @@ __device__ __forceinline__ bool replay_segment(const KArgs& a, const CostTable<S
             if (base + q == next_run) {  // close run r, open run r+1
 #pragma unroll
                 for (int i = 0; i < NPL; ++i) {
-                    hist[i] += S0[i] - S[i];
-                    D[i] += S0[i] - S[i] + corr[i];
+                    E[i] += corr[i];
+                    ctot[i] += corr[i];
                     corr[i] = 0;
-                    S[i] = max(0, x0v[i] - D[i]);
-                    S0[i] = S[i];
                 }
                 ++r;
                 int idx = r - rwin;
@@ -154,12 +148,12 @@ __device__ __forceinline__ bool replay_segment(const KArgs& a, const CostTable<S
                 int key = INT_MAX;
 #pragma unroll
                 for (int i = 0; i < NPL; ++i)
-                    key = min(key, S[i] > 0 ? c[i] * 128 + adj[i] : INT_MAX);
+                    key = min(key, E[i] < x0v[i] ? c[i] * 128 + adj[i] : INT_MAX);
                 const int best = __reduce_min_sync(kFull, key);
                 act = best == INT_MAX ? -1 : (best & 127);
             }
 #pragma unroll
-            for (int i = 0; i < NPL; ++i) S[i] -= (act == lane + 32 * i);
+            for (int i = 0; i < NPL; ++i) E[i] += (act == lane + 32 * i);
             if (act != ao) {  // warp-uniform: the cached action was not the new one
 #pragma unroll
                 for (int i = 0; i < NPL; ++i) {
@@ -173,11 +167,10 @@ __device__ __forceinline__ bool replay_segment(const KArgs& a, const CostTable<S
         const unsigned chg = __ballot_sync(kFull, lane < cnt && my_new != my_old);
         if (chg && first_chg == INT_MAX) first_chg = base + __ffs(chg) - 1;
     }
+    // the segment's histogram of actions: skipped runs' cached ones and the
+    // evaluated runs' new ones, without the corrections applied to E
 #pragma unroll
-    for (int i = 0; i < NPL; ++i) {
-        hist[i] += S0[i] - S[i];
-        a.agg[(size_t)s * NP + lane + 32 * i] = hist[i];
-    }
+    for (int i = 0; i < NPL; ++i) a.agg[(size_t)s * NP + lane + 32 * i] = E[i] - D0[i] - ctot[i];
     if (lane == 0) {
         // many segments of a popular product change in the same pass: read before
         // the atomic so that only a new minimum contends for the word
@@ -189,7 +182,7 @@ __device__ __forceinline__ bool replay_segment(const KArgs& a, const CostTable<S
 #pragma unroll
         for (int i = 0; i < NPL; ++i) {
             const int n = lane + 32 * i;
-            if (FULL || n < N) a.xfin[(size_t)k * N + n] = S[i];
+            if (FULL || n < N) a.xfin[(size_t)k * N + n] = max(0, x0v[i] - E[i]);
         }
     }
     calls += evals;

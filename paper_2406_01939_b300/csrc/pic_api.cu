@@ -201,7 +201,7 @@ void free_instance(Instance& I) {
     free_pg(I);
     void* ptrs[] = {I.prod, I.reg, I.x0, I.cost, I.lam, I.perm, I.prod_s, I.reg_s, I.pcount,
                     I.pstart, I.run_start, I.run_of, I.run_chunk, I.seg_run, I.seg_of_run, I.seg_prod, I.seg_cf,
-                    I.seg_ce, I.seg_meta, I.seg_lpt, I.len_hist, I.alpha_s, I.agg, I.carry, I.sbagg,
+                    I.seg_ce, I.seg_meta, I.seg_lpt, I.len_hist, I.alpha_s, I.agg, I.carry, I.sbexc, I.sbagg,
                     I.sbincl, I.fc, I.xfin, I.xwork, I.act_t, I.tmp_a, I.tmp_b, I.tmp_c, I.scan_blk,
                     I.hist, I.ctrl, I.trace, I.mlp_P, I.mlp_W1p, I.mlp_W2p, I.mlp_b2, I.mlp_Emax, I.mlp_bnd, I.mlp_c2, I.mlp_sat,
                     I.cap, I.cap_run_t, I.cap_info, I.cap_inv, I.cap_qagg, I.cap_qinc};
@@ -283,13 +283,14 @@ cudaError_t prepare_picard_state(Instance& I, int W, int iters_cap, cudaStream_t
     cudaError_t e;
     if (!I.agg || smax > I.smax_agg) {
         if (I.agg) {
-            cudaFree(I.agg); cudaFree(I.carry); cudaFree(I.sbagg); cudaFree(I.sbincl);
+            cudaFree(I.agg); cudaFree(I.carry); cudaFree(I.sbexc); cudaFree(I.sbagg); cudaFree(I.sbincl);
         }
-        I.agg = I.carry = nullptr;
+        I.agg = I.carry = I.sbexc = nullptr;
         I.sbagg = I.sbincl = nullptr;
         I.smax_agg = 0;
         if ((e = dmalloc(&I.agg, (size_t)smax * I.NP))) return e;
         if ((e = dmalloc(&I.carry, (size_t)smax * I.NP))) return e;
+        if ((e = dmalloc(&I.sbexc, (size_t)smax * I.NP))) return e;
         if ((e = dmalloc(&I.sbagg, (size_t)smax * I.NP))) return e;
         if ((e = dmalloc(&I.sbincl, (size_t)smax * I.NP))) return e;
         I.smax_agg = smax;
@@ -556,6 +557,7 @@ pic_status pic_simulate(pic_instance* h, const pic_policy* pol, const pic_sim_op
             const size_t bytes = sizeof(int32_t) * (size_t)I.smax_agg * I.NP;
             CU(cudaMemsetAsync(I.agg, 0, bytes, st));
             CU(cudaMemsetAsync(I.carry, 0, bytes, st));
+            CU(cudaMemsetAsync(I.sbexc, 0, bytes, st));
         }
         if (T) {
             if (timing) CU(cudaEventRecord(I.ev[1], st));

@@ -391,7 +391,7 @@ pic_status enqueue_picard(Instance& I, const CallCfg& c, cudaStream_t st) {
     a.reg_s = I.reg_s; a.run_start = I.run_start; a.seg_run = I.seg_run;
     a.seg_prod = I.seg_prod; a.seg_cf = I.seg_cf; a.seg_ce = I.seg_ce;
     a.x0 = I.x0; a.cost = I.cost; a.lam = I.lam;
-    a.alpha_s = I.alpha_s; a.agg = I.agg; a.carry = I.carry;
+    a.alpha_s = I.alpha_s; a.agg = I.agg; a.carry = I.carry; a.sbexc = I.sbexc;
     a.sbagg = I.sbagg; a.sbincl = I.sbincl; a.meta = I.seg_meta; a.lpt = I.seg_lpt;
     a.fc = I.fc; a.xfin = I.xfin;
     a.ctrl = I.ctrl; a.max_iters = c.iters_cap; a.flags = c.flags;
@@ -443,7 +443,7 @@ pic_status run_picard(Instance& I, const CallCfg& c, bool graph, cudaStream_t st
         return PIC_OK;
     }
     // the graph holds buffer addresses: a reallocation since capture needs a new one
-    const void* bufs[] = {I.agg, I.carry, I.sbagg, I.sbincl, I.mlp_P};
+    const void* bufs[] = {I.agg, I.carry, I.sbexc, I.sbagg, I.sbincl, I.mlp_P};
     const unsigned long long sig = fnv(cfg_sig(c), bufs, sizeof(bufs));
     if (!bt->gexec || bt->gsig != sig) {
         if (bt->gexec) {

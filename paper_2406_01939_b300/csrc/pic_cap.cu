@@ -205,12 +205,13 @@ __device__ bool cap_chunk(const KArgs& a, const CapArgs& c, int m, int it, bool 
     for (int s = 0; s < nslots; ++s) {
         const int r = s_run[s], k = s_k[s];
         // segments hold one run each: the run's chain is its product's segment range
-        const bool chained = have_cache && __ldg(&a.meta[r].ce) - __ldg(&a.meta[r].cf) > 1;
+        const int cf = __ldg(&a.meta[r].cf);
+        const bool chained = have_cache && __ldg(&a.meta[r].ce) - cf > 1;
 #pragma unroll
         for (int i = 0; i < NPL; ++i) {
             const int n = lane + 32 * i;
             const int x0v = n < N ? __ldg(a.x0 + (size_t)k * N + n) : 0;
-            const int d = chained ? a.carry[(size_t)r * NP + n] : 0;
+            const int d = chained ? chain_prefix(a, r, cf, n) : 0;
             const int xs = max(0, x0v - d);
             if (have_cache) qsum[i] += min(rows[s * NP + n], xs);
             rows[s * NP + n] = xs;
@@ -608,7 +609,7 @@ cudaError_t picard_cap(Instance* I, const pic_policy* pol, int M, int max_iters,
     a.reg_s = I->reg_s; a.run_start = I->run_start; a.seg_run = I->seg_run;
     a.seg_prod = I->seg_prod; a.seg_cf = I->seg_cf; a.seg_ce = I->seg_ce;
     a.x0 = I->x0; a.cost = I->cost; a.lam = I->lam;
-    a.alpha_s = I->alpha_s; a.agg = I->agg; a.carry = I->carry;
+    a.alpha_s = I->alpha_s; a.agg = I->agg; a.carry = I->carry; a.sbexc = I->sbexc;
     a.sbagg = I->sbagg; a.sbincl = I->sbincl; a.meta = I->seg_meta; a.lpt = I->seg_lpt;
     a.fc = I->fc; a.xfin = I->xfin;
     a.ctrl = I->ctrl; a.max_iters = max_iters; a.flags = flags;

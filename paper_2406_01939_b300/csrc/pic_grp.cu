@@ -63,7 +63,7 @@ __device__ __forceinline__ bool replay_group(const KArgs& a, const int16_t* __re
         const bool in = n < N;
         x0v[i] = in ? a.x0[(size_t)k * N + n] : 0;
         adj[i] = n - ((DUAL && in) ? 128 * a.lam[(size_t)k * N + n] : 0);  // key = score*128 + n
-        D[i] = (chained && in) ? a.carry[(size_t)s * NP + n] : 0;
+        D[i] = (chained && in) ? chain_prefix(a, s, m.cf, n) : 0;
         hist[i] = 0;
         corr[i] = 0;
     }

@@ -149,7 +149,7 @@ cudaError_t picard_run(Instance* I, const pic_policy* pol, int max_iters, int fl
     a.reg_s = I->reg_s; a.run_start = I->run_start; a.seg_run = I->seg_run;
     a.seg_prod = I->seg_prod; a.seg_cf = I->seg_cf; a.seg_ce = I->seg_ce;
     a.x0 = I->x0; a.cost = I->cost; a.lam = I->lam;
-    a.alpha_s = I->alpha_s; a.agg = I->agg; a.carry = I->carry;
+    a.alpha_s = I->alpha_s; a.agg = I->agg; a.carry = I->carry; a.sbexc = I->sbexc;
     a.sbagg = I->sbagg; a.sbincl = I->sbincl; a.meta = I->seg_meta; a.lpt = I->seg_lpt;
     a.fc = I->fc; a.xfin = I->xfin;
     a.ctrl = I->ctrl; a.max_iters = max_iters; a.flags = flags;

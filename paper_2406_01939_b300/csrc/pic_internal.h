@@ -135,7 +135,10 @@ struct Instance {
     // iteration state
     int8_t *alpha_s;    // [T]  action cache in sorted order
     int32_t *agg;       // [SMAX][NP] histogram of cached actions per segment
-    int32_t *carry;     // [SMAX][NP] in-super-block exclusive prefix of agg
+    int32_t *carry;     // [SMAX][NP] exclusive prefix of agg inside the segment's super-block
+    int32_t *sbexc;     // [SMAX][NP] at a super-block's first segment: the exclusive prefix of
+                        // agg over the chain's earlier super-blocks (a segment's chain prefix
+                        // is its carry row plus its super-block's sbexc row)
     unsigned long long *sbagg;   // [SMAX][NP] super-block totals, (pass << 32) | value
     unsigned long long *sbincl;  // [SMAX][NP] inclusive chain prefix, (pass << 32) | value
     int32_t *fc;        // [2][K] first changed sorted position per product and pass parity

@@ -846,7 +846,7 @@ __device__ bool replay_segment_mlp(const KArgs& a, const MlpPolicy& p, const uin
     for (int i = 0; i < NPL; ++i) {
         const int n = lane + 32 * i;
         x0v[i] = n < N ? a.x0[(size_t)k * N + n] : 0;
-        D[i] = chained ? a.carry[(size_t)s * NP + n] : 0;
+        D[i] = chained ? chain_prefix(a, s, m.cf, n) : 0;
         S[i] = max(0, x0v[i] - D[i]);
         S0[i] = S[i];
         hist[i] = 0;

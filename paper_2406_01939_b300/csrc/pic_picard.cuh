@@ -25,6 +25,7 @@ struct KArgs {
     int8_t* alpha_s;
     int32_t* __restrict__ agg;
     int32_t* __restrict__ carry;
+    int32_t* __restrict__ sbexc;
     unsigned long long* sbagg;   // tagged super-block totals
     unsigned long long* sbincl;  // tagged inclusive prefixes
     int32_t* fc;
@@ -101,6 +102,14 @@ __device__ __forceinline__ SegMeta smem_meta(const SegMeta* p) {
     return m;
 }
 
+// The exclusive chain prefix of agg at segment s (chain from cf) for warehouse
+// n: its super-block's prefix over the earlier super-blocks plus its own prefix
+// inside the super-block.
+__device__ __forceinline__ int chain_prefix(const KArgs& a, int s, int cf, int n) {
+    const int head = s - (s - cf) % kSuperBlock;
+    return a.carry[(size_t)s * a.NP + n] + a.sbexc[(size_t)head * a.NP + n];
+}
+
 constexpr int kMaxWarpsPerCta = 32;
 
 // Look-back words carry a tag in the high half: (tag << 32) | value with tag =
@@ -149,6 +158,7 @@ __device__ __forceinline__ void superblock_prefix(const KArgs& a, int s, const S
             return;
         }
     }
+    // the super-block's total, writing every segment's prefix inside it on the way
     int tot[NPL];
 #pragma unroll
     for (int i = 0; i < NPL; ++i) tot[i] = 0;
@@ -162,7 +172,10 @@ __device__ __forceinline__ void superblock_prefix(const KArgs& a, int s, const S
 #pragma unroll
         for (int u = 0; u < kRows; ++u)
 #pragma unroll
-            for (int i = 0; i < NPL; ++i) tot[i] += v[u][i];
+            for (int i = 0; i < NPL; ++i) {
+                if (s2 + u < send) a.carry[(size_t)(s2 + u) * NP + lane + 32 * i] = tot[i];
+                tot[i] += v[u][i];
+            }
     }
     int acc[NPL];
 #pragma unroll
@@ -207,22 +220,9 @@ __device__ __forceinline__ void superblock_prefix(const KArgs& a, int s, const S
         }
     }
 #pragma unroll
-    for (int i = 0; i < NPL; ++i)
+    for (int i = 0; i < NPL; ++i) {
         a.sbincl[(size_t)s * NP + lane + 32 * i] = tagged(tag, acc[i] + tot[i]);
-    for (int s2 = s; s2 < send; s2 += kRows) {
-        int v[kRows][NPL];
-#pragma unroll
-        for (int u = 0; u < kRows; ++u)
-#pragma unroll
-            for (int i = 0; i < NPL; ++i)
-                v[u][i] = s2 + u < send ? a.agg[(size_t)(s2 + u) * NP + lane + 32 * i] : 0;
-#pragma unroll
-        for (int u = 0; u < kRows; ++u)
-#pragma unroll
-            for (int i = 0; i < NPL; ++i) {
-                if (s2 + u < send) a.carry[(size_t)(s2 + u) * NP + lane + 32 * i] = acc[i];
-                acc[i] += v[u][i];
-            }
+        a.sbexc[(size_t)s * NP + lane + 32 * i] = acc[i];
     }
 }
 

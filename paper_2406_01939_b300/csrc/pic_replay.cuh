@@ -39,7 +39,7 @@ __device__ __forceinline__ bool replay_segment(const KArgs& a, const CostTable<S
         ctot[i] = 0;
         x0v[i] = in ? a.x0[(size_t)k * N + n] : 0;
         adj[i] = n - ((DUAL && use_lam && in) ? 128 * a.lam[(size_t)k * N + n] : 0);
-        D0[i] = chained ? a.carry[(size_t)s * NP + n] : 0;
+        D0[i] = chained ? chain_prefix(a, s, m.cf, n) : 0;
         E[i] = D0[i];
     }
     const int j0 = m.j0, jend = m.jend;

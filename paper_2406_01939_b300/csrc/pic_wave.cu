@@ -96,7 +96,7 @@ struct __align__(16) WaveSmem {
     // slots that finished a unit (its row's histogram to write) or started one
     // (its start row to build) in this wave's advance: done by all warps
     int fin_seg[kWRows], fin_row[kWRows];
-    int st_row[kWRows], st_seg[kWRows], st_k[kWRows], st_low[kWRows];
+    int st_row[kWRows], st_seg[kWRows], st_k[kWRows], st_low[kWRows], st_head[kWRows];
     int n_fin, n_start;
     int n_near, fail, any_net;
     int ring_head, ring_tail, scan_i, share_done;
@@ -171,6 +171,7 @@ __device__ void slot_take(const WaveCtx<BATCH>& c, int t, Slot& sl, const int4 e
     s.st_row[i] = t;
     s.st_seg[i] = chained ? sl.seg : -1 - sl.seg;  // -1 - seg: no chain prefix
     s.st_k[i] = sl.k;
+    if (chained) s.st_head[i] = sl.seg - (sl.seg - __ldg(&a.meta[sl.seg].cf)) % kSuperBlock;
     sl.first_chg = INT_MAX;
     sl.evals = 0;
     if constexpr (BATCH) {
@@ -214,12 +215,13 @@ __device__ void rows_coop(const KArgs& a, WaveSmem& s) {
             const int i = i0 + u * kWWarps;
             const int sg = i < ns ? s.st_seg[i] : -1, k = i < ns ? s.st_k[i] : 0;
             const int seg = sg >= 0 ? sg : -1 - sg;
+            const int head = sg >= 0 ? s.st_head[i] : 0;
 #pragma unroll
             for (int h = 0; h < kWN / 32; ++h) {
                 const int n = lane + 32 * h;
                 const bool in = i < ns && n < N;
                 xv[u][h] = in ? __ldg(a.x0 + (size_t)k * N + n) : 0;
-                dv[u][h] = (in && sg >= 0) ? a.carry[(size_t)seg * NP + n] : 0;
+                dv[u][h] = (in && sg >= 0) ? a.carry[(size_t)seg * NP + n] + a.sbexc[(size_t)head * NP + n] : 0;
             }
         }
 #pragma unroll
@@ -763,6 +765,7 @@ __global__ void k_wave_xfin(int K, int N, const int32_t* __restrict__ pstart,
 
 // Shared memory of the wave kernel (dynamic: the WaveSmem block, 128-aligned).
 size_t wave_smem_bytes() { return sizeof(WaveSmem) + 128; }
+static_assert(sizeof(WaveSmem) + 128 <= 232448, "wave kernel shared memory above 227 KB");
 
 bool wave_applies(const Instance* I) { return I->N <= kWN; }
 

@@ -205,13 +205,12 @@ __device__ bool cap_chunk(const KArgs& a, const CapArgs& c, int m, int it, bool 
     for (int s = 0; s < nslots; ++s) {
         const int r = s_run[s], k = s_k[s];
         // segments hold one run each: the run's chain is its product's segment range
-        const int cf = __ldg(&a.meta[r].cf);
-        const bool chained = have_cache && __ldg(&a.meta[r].ce) - cf > 1;
+        const bool chained = have_cache && __ldg(&a.meta[r].ce) - __ldg(&a.meta[r].cf) > 1;
 #pragma unroll
         for (int i = 0; i < NPL; ++i) {
             const int n = lane + 32 * i;
             const int x0v = n < N ? __ldg(a.x0 + (size_t)k * N + n) : 0;
-            const int d = chained ? chain_prefix(a, r, cf, n) : 0;
+            const int d = chained ? a.carry[(size_t)r * NP + n] : 0;  // the whole chain prefix
             const int xs = max(0, x0v - d);
             if (have_cache) qsum[i] += min(rows[s * NP + n], xs);
             rows[s * NP + n] = xs;
@@ -414,7 +413,7 @@ __global__ void __launch_bounds__(kCapWarps * 32) k_picard_cap(KArgs a, CapArgs 
             a.ctrl->cap_fct[parity] = INT_MAX;
         }
         if (it > 1 || a.first_dirty)
-            chain_prefixes<NPL, kPrefixRows<NPL>>(a, it, fc_prev, tag, deadline, s_meta[wib],
+            chain_prefixes<NPL, kPrefixRows<NPL>, false>(a, it, fc_prev, tag, deadline, s_meta[wib],
                                                   s_fcp[wib]);
         if (!grid_sync(a.ctrl, deadline)) { ok = false; break; }
         if (tr && gtid == 0) tr[0] = (long long)(globaltimer_ns() - t_start);

@@ -137,7 +137,12 @@ __device__ __forceinline__ unsigned long long tagged(unsigned tag, int v) {
 // recorded and the pass is abandoned at the next grid barrier.
 // ROWS: histogram rows loaded per round trip (a whole super-block when
 // registers allow).
-template <int NPL, int ROWS = 16 / NPL>
+// SPLIT: carry holds the prefix inside the super-block (written while the
+// totals are summed) and sbexc the super-block's prefix over the chain (read
+// through chain_prefix); otherwise carry holds the whole chain prefix (a second
+// pass over the super-block's rows; the capacity kernel, which reads one row per
+// run).
+template <int NPL, int ROWS = 16 / NPL, bool SPLIT = true>
 __device__ __forceinline__ void superblock_prefix(const KArgs& a, int s, const SegMeta& m, int it,
                                                   unsigned tag, int fcp,
                                                   unsigned long long deadline) {
@@ -173,7 +178,7 @@ __device__ __forceinline__ void superblock_prefix(const KArgs& a, int s, const S
         for (int u = 0; u < kRows; ++u)
 #pragma unroll
             for (int i = 0; i < NPL; ++i) {
-                if (s2 + u < send) a.carry[(size_t)(s2 + u) * NP + lane + 32 * i] = tot[i];
+                if (SPLIT && s2 + u < send) a.carry[(size_t)(s2 + u) * NP + lane + 32 * i] = tot[i];
                 tot[i] += v[u][i];
             }
     }
@@ -222,7 +227,24 @@ __device__ __forceinline__ void superblock_prefix(const KArgs& a, int s, const S
 #pragma unroll
     for (int i = 0; i < NPL; ++i) {
         a.sbincl[(size_t)s * NP + lane + 32 * i] = tagged(tag, acc[i] + tot[i]);
-        a.sbexc[(size_t)s * NP + lane + 32 * i] = acc[i];
+        if (SPLIT) a.sbexc[(size_t)s * NP + lane + 32 * i] = acc[i];
+    }
+    if (!SPLIT) {
+        for (int s2 = s; s2 < send; s2 += kRows) {
+            int v[kRows][NPL];
+#pragma unroll
+            for (int u = 0; u < kRows; ++u)
+#pragma unroll
+                for (int i = 0; i < NPL; ++i)
+                    v[u][i] = s2 + u < send ? a.agg[(size_t)(s2 + u) * NP + lane + 32 * i] : 0;
+#pragma unroll
+            for (int u = 0; u < kRows; ++u)
+#pragma unroll
+                for (int i = 0; i < NPL; ++i) {
+                    if (s2 + u < send) a.carry[(size_t)(s2 + u) * NP + lane + 32 * i] = acc[i];
+                    acc[i] += v[u][i];
+                }
+        }
     }
 }
 
@@ -232,7 +254,7 @@ __device__ __forceinline__ void superblock_prefix(const KArgs& a, int s, const S
 // a cache started from alpha_init) are assigned to warps gwarp + j * nwarps, 32
 // at a time, and run superblock_prefix.  s_meta / s_fcp: this warp's staging
 // rows (32 entries each).
-template <int NPL, int ROWS = 16 / NPL>
+template <int NPL, int ROWS = 16 / NPL, bool SPLIT = true>
 __device__ __forceinline__ void chain_prefixes(const KArgs& a, int it, const int* fc_prev,
                                                unsigned tag, unsigned long long deadline,
                                                SegMeta* s_meta, int* s_fcp) {
@@ -258,7 +280,7 @@ __device__ __forceinline__ void chain_prefixes(const KArgs& a, int it, const int
             const int src = __ffs(todo) - 1;
             todo &= todo - 1;
             const SegMeta mm = smem_meta(&s_meta[src]);
-            superblock_prefix<NPL, ROWS>(a, gwarp + (j0 + src) * nwarps, mm, it, tag, s_fcp[src],
+            superblock_prefix<NPL, ROWS, SPLIT>(a, gwarp + (j0 + src) * nwarps, mm, it, tag, s_fcp[src],
                                          deadline);
         }
         __syncwarp();
@@ -294,7 +316,9 @@ __device__ __forceinline__ void chain_prefixes(const KArgs& a, int it, const int
 // kept by thread 0 (calls, replays, the largest unit's calls and orders), and
 // phase S stages its segments in ext_meta / ext_fcp (WARPS x 32 entries, e.g.
 // dynamic shared memory that phase R uses otherwise).
-template <int NPL, int WARPS, class Replay, int GROUP = 1, bool CTA = false>
+// SPLIT: the chain prefixes' layout (superblock_prefix); the replay reads them
+// accordingly.
+template <int NPL, int WARPS, class Replay, int GROUP = 1, bool CTA = false, bool SPLIT = true>
 __device__ __forceinline__ void picard_passes(const KArgs& a, unsigned long long& calls,
                                               Replay&& replay, SegMeta* ext_meta = nullptr,
                                               int* ext_fcp = nullptr) {
@@ -343,7 +367,7 @@ __device__ __forceinline__ void picard_passes(const KArgs& a, unsigned long long
             a.ctrl->win_hi_prev = wprev;
         }
         if (it > 1 || a.first_dirty)
-            chain_prefixes<NPL>(a, it, fc_prev, tag_base + (unsigned)it, deadline,
+            chain_prefixes<NPL, 16 / NPL, SPLIT>(a, it, fc_prev, tag_base + (unsigned)it, deadline,
                                 CTA ? ext_meta + 32 * wib : s_meta[wib],
                                 CTA ? ext_fcp + 32 * wib : s_fcp[wib]);
         if (!grid_sync(a.ctrl, deadline)) { ok = false; break; }

@@ -96,7 +96,8 @@ struct __align__(16) WaveSmem {
     // slots that finished a unit (its row's histogram to write) or started one
     // (its start row to build) in this wave's advance: done by all warps
     int fin_seg[kWRows], fin_row[kWRows];
-    int st_row[kWRows], st_seg[kWRows], st_k[kWRows], st_low[kWRows], st_head[kWRows];
+    int st_row[kWRows], st_seg[kWRows], st_k[kWRows];
+    unsigned char st_low[kWRows];  // warehouses below 32 units (at most 64)
     int n_fin, n_start;
     int n_near, fail, any_net;
     int ring_head, ring_tail, scan_i, share_done;
@@ -171,7 +172,6 @@ __device__ void slot_take(const WaveCtx<BATCH>& c, int t, Slot& sl, const int4 e
     s.st_row[i] = t;
     s.st_seg[i] = chained ? sl.seg : -1 - sl.seg;  // -1 - seg: no chain prefix
     s.st_k[i] = sl.k;
-    if (chained) s.st_head[i] = sl.seg - (sl.seg - __ldg(&a.meta[sl.seg].cf)) % kSuperBlock;
     sl.first_chg = INT_MAX;
     sl.evals = 0;
     if constexpr (BATCH) {
@@ -215,13 +215,12 @@ __device__ void rows_coop(const KArgs& a, WaveSmem& s) {
             const int i = i0 + u * kWWarps;
             const int sg = i < ns ? s.st_seg[i] : -1, k = i < ns ? s.st_k[i] : 0;
             const int seg = sg >= 0 ? sg : -1 - sg;
-            const int head = sg >= 0 ? s.st_head[i] : 0;
 #pragma unroll
             for (int h = 0; h < kWN / 32; ++h) {
                 const int n = lane + 32 * h;
                 const bool in = i < ns && n < N;
                 xv[u][h] = in ? __ldg(a.x0 + (size_t)k * N + n) : 0;
-                dv[u][h] = (in && sg >= 0) ? a.carry[(size_t)seg * NP + n] + a.sbexc[(size_t)head * NP + n] : 0;
+                dv[u][h] = (in && sg >= 0) ? a.carry[(size_t)seg * NP + n] : 0;
             }
         }
 #pragma unroll
@@ -238,7 +237,7 @@ __device__ void rows_coop(const KArgs& a, WaveSmem& s) {
                 s.S0[row][n] = v;
                 low += __popc(__ballot_sync(kFull, n < N && v < 32));
             }
-            if (lane == 0) s.st_low[row] = low;
+            if (lane == 0) s.st_low[row] = (unsigned char)low;
         }
     }
     __syncthreads();
@@ -722,7 +721,8 @@ __global__ void __launch_bounds__(kWThreads, 1) k_picard_wave(KArgs a, MlpPolicy
         __syncthreads();
         return any_chg > 0;
     };
-    picard_passes<NPL, kWWarps, decltype(replay)&, 1, true>(a, calls, replay,
+    // whole chain prefixes in carry: a unit's start row is one load per warehouse
+    picard_passes<NPL, kWWarps, decltype(replay)&, 1, true, false>(a, calls, replay,
                                                             reinterpret_cast<SegMeta*>(s.hhi),
                                                             reinterpret_cast<int*>(s.hlo));
     // counters: decisions by the tensor-core tile, by the saturated-state table,
@@ -765,7 +765,9 @@ __global__ void k_wave_xfin(int K, int N, const int32_t* __restrict__ pstart,
 
 // Shared memory of the wave kernel (dynamic: the WaveSmem block, 128-aligned).
 size_t wave_smem_bytes() { return sizeof(WaveSmem) + 128; }
-static_assert(sizeof(WaveSmem) + 128 <= 232448, "wave kernel shared memory above 227 KB");
+// dynamic (with the alignment slack) plus the kernel's static shared memory (the
+// pass loop's CTA words, 128 B) within the 227 KB a CTA may opt into
+static_assert(sizeof(WaveSmem) + 128 + 128 <= 232448, "wave kernel shared memory above 227 KB");
 
 bool wave_applies(const Instance* I) { return I->N <= kWN; }
 

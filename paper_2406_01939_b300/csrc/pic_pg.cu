@@ -996,6 +996,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pg_tc(PgArgs p, int* err) {
 // dW1 rows of the cost inputs (n < N), of the embedding (2N + e), and db1, from
 // DZ: acc[row][j] += sum_r coef(row, r) DZ[r][j].  Block: 256 threads = one per
 // hidden unit; blockIdx.y picks a group of 16 rows; regions strided over blockIdx.x.
+// The coefficients (cost / 128, BF16 embeddings, 1) are exact in FP32; DZ is
+// rounded to FP32 and a block's partial sums (about R / 148 regions) are FP32,
+// added to the FP64 accumulators once per block (FP64 arithmetic is slow here).
 __global__ void __launch_bounds__(256) k_pg_rows(int N, int R, const double* __restrict__ dz,
                                                   const int32_t* __restrict__ cost,
                                                   const uint16_t* __restrict__ E,
@@ -1004,46 +1007,48 @@ __global__ void __launch_bounds__(256) k_pg_rows(int N, int R, const double* __r
     const int j = threadIdx.x;
     const int nrows = N + kEmb + 1;  // cost rows, embedding rows, b1
     const int row0 = blockIdx.y * 16;
-    double acc[16];
+    float acc[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) acc[i] = 0.0;
+    for (int i = 0; i < 16; ++i) acc[i] = 0.0f;
     for (int r = blockIdx.x; r < R; r += gridDim.x) {
-        const double d = dz[(size_t)r * kHidden + j];
+        const float d = (float)dz[(size_t)r * kHidden + j];
         const int re = reg_local[r];
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
             const int row = row0 + i;
-            double c = 0.0;
-            if (row < N) c = (double)cost[(size_t)r * N + row] / 128.0;
-            else if (row < N + kEmb) c = (double)lo16(E[(size_t)re * kEmb + (row - N)]);
-            else if (row == N + kEmb) c = 1.0;
-            acc[i] = fma(c, d, acc[i]);
+            float c = 0.0f;
+            if (row < N) c = (float)cost[(size_t)r * N + row] * 0.0078125f;  // / 128, exact
+            else if (row < N + kEmb) c = lo16(E[(size_t)re * kEmb + (row - N)]);
+            else if (row == N + kEmb) c = 1.0f;
+            acc[i] = fmaf(c, d, acc[i]);
         }
     }
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
         const int row = row0 + i;
-        if (row >= nrows || acc[i] == 0.0) continue;
-        if (row < N) atomicAdd(accW1 + (size_t)row * kHidden + j, acc[i]);
-        else if (row < N + kEmb) atomicAdd(accW1 + (size_t)(2 * N + row - N) * kHidden + j, acc[i]);
-        else atomicAdd(accb1 + j, acc[i]);
+        if (row >= nrows || acc[i] == 0.0f) continue;
+        if (row < N) atomicAdd(accW1 + (size_t)row * kHidden + j, (double)acc[i]);
+        else if (row < N + kEmb) atomicAdd(accW1 + (size_t)(2 * N + row - N) * kHidden + j, (double)acc[i]);
+        else atomicAdd(accb1 + j, (double)acc[i]);
     }
 }
 
-// dE[reg_local[r]] += W1_E DZ[r]: one warp per region.
+// dE[reg_local[r]] += W1_E DZ[r]: one warp per region, FP32 products and sums
+// over the region's 256 hidden units (BF16 weights exact, DZ rounded), added to
+// the FP64 accumulators.
 __global__ void k_pg_dE(int N, int R, const double* __restrict__ dz, const uint16_t* __restrict__ W1,
                         const int32_t* __restrict__ reg_local, double* accE) {
     const int lane = lane_id();
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int r = gw; r < R; r += nw) {
-        double u[kEmb];
+        float u[kEmb];
 #pragma unroll
-        for (int e = 0; e < kEmb; ++e) u[e] = 0.0;
+        for (int e = 0; e < kEmb; ++e) u[e] = 0.0f;
         for (int j = lane; j < kHidden; j += 32) {
-            const double d = dz[(size_t)r * kHidden + j];
+            const float d = (float)dz[(size_t)r * kHidden + j];
 #pragma unroll
-            for (int e = 0; e < kEmb; ++e) u[e] = fma((double)lo16(W1[(size_t)(2 * N + e) * kHidden + j]), d, u[e]);
+            for (int e = 0; e < kEmb; ++e) u[e] = fmaf(lo16(W1[(size_t)(2 * N + e) * kHidden + j]), d, u[e]);
         }
 #pragma unroll
         for (int e = 0; e < kEmb; ++e) {
@@ -1051,11 +1056,11 @@ __global__ void k_pg_dE(int N, int R, const double* __restrict__ dz, const uint1
             for (int o = 16; o > 0; o >>= 1) u[e] += __shfl_xor_sync(kFull, u[e], o);
         }
         if (lane < kEmb) {
-            double v = 0.0;
+            float v = 0.0f;
 #pragma unroll
             for (int e = 0; e < kEmb; ++e)
                 if (e == lane) v = u[e];
-            if (v != 0.0) atomicAdd(accE + (size_t)reg_local[r] * kEmb + lane, v);
+            if (v != 0.0f) atomicAdd(accE + (size_t)reg_local[r] * kEmb + lane, (double)v);
         }
     }
 }

@@ -17,6 +17,7 @@
 // policies share one weight set staged in shared memory.  The per-call device
 // work can run as a CUDA graph (PIC_FLAG_GRAPH); the chunk count, CTA shape and
 // segment window can be picked by a timing autotuner (num_chunks = 0).
+#include <algorithm>
 #include <cstdarg>
 #include <cstddef>
 #include <cstdio>
@@ -88,8 +89,9 @@ __global__ void k_owners(int n, int B, const int32_t* __restrict__ off, int32_t*
 }
 
 // ---------------------------------------------------------------------------- per-call kernels
-// Cost and a^phi count of each trajectory from its actions in time order (one
-// CTA per trajectory); the batch totals are added to the control block.
+// Cost and a^phi count of each trajectory from its actions in time order:
+// CTA (b, s) sums slice s of gridDim.y slices of trajectory b into tres (zeroed
+// before the launch); the batch totals are added to the control block.
 constexpr int kReduceThreads = 256;
 
 __global__ void __launch_bounds__(kReduceThreads) k_traj_reduce(
@@ -98,7 +100,8 @@ __global__ void __launch_bounds__(kReduceThreads) k_traj_reduce(
     Ctrl* ctrl) {
     __shared__ long long sc[kReduceThreads / 32], sl[kReduceThreads / 32];
     const int b = blockIdx.x;
-    const int t0 = toff[b], t1 = toff[b + 1];
+    const int len = toff[b + 1] - toff[b], per = (len + (int)gridDim.y - 1) / (int)gridDim.y;
+    const int t0 = toff[b] + min(len, (int)blockIdx.y * per), t1 = toff[b] + min(len, ((int)blockIdx.y + 1) * per);
     long long c = 0, l = 0;
     for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
         const int a = act_t[t];
@@ -119,11 +122,23 @@ __global__ void __launch_bounds__(kReduceThreads) k_traj_reduce(
             c += sc[w];
             l += sl[w];
         }
-        tres[2 * b] = c;
-        tres[2 * b + 1] = l;
+        if (c) atomicAdd((unsigned long long*)&tres[2 * b], (unsigned long long)c);
+        if (l) atomicAdd((unsigned long long*)&tres[2 * b + 1], (unsigned long long)l);
         atomicAdd((unsigned long long*)&ctrl->total_cost, (unsigned long long)c);
         atomicAdd((unsigned long long*)&ctrl->lost, (unsigned long long)l);
     }
+}
+
+// Per-trajectory cost and lost count: enough slices per trajectory to give
+// every SM a few CTAs.
+inline cudaError_t traj_reduce(Instance& I, int B, cudaStream_t st) {
+    Batch* bt = I.batch;
+    cudaError_t e = cudaMemsetAsync(bt->tres, 0, sizeof(long long) * 2 * (size_t)B, st);
+    if (e) return e;
+    const int S = std::max(1, std::min(64, (4 * I.num_sms + B - 1) / B));
+    k_traj_reduce<<<dim3(B, S), kReduceThreads, 0, st>>>(I.act_t, I.reg, I.cost, I.N, bt->toff, bt->tres,
+                                                          I.ctrl);
+    return cudaGetLastError();
 }
 
 // Sequential definition (Sec. 2) for every trajectory at once: one warp per
@@ -417,8 +432,7 @@ pic_status enqueue_picard(Instance& I, const CallCfg& c, cudaStream_t st) {
         BCU(batch_dispatch(&I, c.shape, c.tc && I.N <= 64, a, p, ba, st));
     BCU(scatter_actions(&I, st));
     I.launches += 1;
-    k_traj_reduce<<<B, kReduceThreads, 0, st>>>(I.act_t, I.reg, I.cost, I.N, bt->toff, bt->tres, I.ctrl);
-    BCU(cudaGetLastError());
+    BCU(traj_reduce(I, B, st));
     unsigned char* h = bt->h_out;
     BCU(cudaMemcpyAsync(h, I.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     BCU(cudaMemcpyAsync(h + sizeof(Ctrl), bt->tres, sizeof(long long) * 2 * B, cudaMemcpyDeviceToHost, st));
@@ -782,8 +796,7 @@ pic_status pic_simulate_batch(pic_instance* h, const pic_policy* pols, const pic
         }
         BCU(cudaEventRecord(I.ev[2], st));
         I.launches += 1;
-        k_traj_reduce<<<B, kReduceThreads, 0, st>>>(I.act_t, I.reg, I.cost, I.N, bt->toff, bt->tres, I.ctrl);
-        BCU(cudaGetLastError());
+        BCU(traj_reduce(I, B, st));
         unsigned char* ho = bt->h_out;
         BCU(cudaMemcpyAsync(ho, I.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
         BCU(cudaMemcpyAsync(ho + sizeof(Ctrl), bt->tres, sizeof(long long) * 2 * B, cudaMemcpyDeviceToHost, st));

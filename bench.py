@@ -430,7 +430,9 @@ def run_reference(args):
         "steps": per, "warmup": args.warmup, "ms_per_step": 1000 * el / per * inst.T / sub.T,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.workload == "mlp_medium" else "int32",
-        "data": "synthetic", "config": workload_config(args, inst),
+        "data": "synthetic",
+        "config": dict(workload_config(args, inst),
+                       parallelism=f"one trajectory per rank ({max(1, int(args.gpus))})"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": (f"full {inst.T}-order trajectory per step" if sub.T == inst.T else
                                     f"first {sub.T} of {inst.T} orders per step") +

@@ -1028,7 +1028,8 @@ pic_status build_tables(pic_owmr* h, int P, int ctas, cudaStream_t st, int* laun
     B = B < 1 ? 1 : (B > kLanes ? kLanes : B);
     const int ngroups = (P + B - 1) / B;
     int32_t *key = nullptr, *key_s = nullptr, *perm = nullptr, *tk = nullptr, *tv = nullptr,
-            *cnt = nullptr, *off = nullptr, *grows = nullptr, *hist = nullptr, *blk = nullptr;
+            *cnt = nullptr, *off = nullptr, *grows = nullptr, *hist = nullptr, *blk = nullptr,
+            *serr = nullptr;  // set when a scan's look-back wait gives up
     const int Tn = T > 0 ? T : 1;
     const int hl = sort_hist_len(Tn);
     const int bl = scan_blk_len(hl > P + 1 ? hl : P + 1) + scan_blk_len(ngroups + 1) + 2;
@@ -1039,27 +1040,30 @@ pic_status build_tables(pic_owmr* h, int P, int ctas, cudaStream_t st, int* laun
     A(&key, Tn); A(&key_s, Tn); A(&perm, Tn); A(&tk, Tn); A(&tv, Tn); A(&cnt, (size_t)P + 1);
     A(&off, (size_t)P + 1); A(&grows, (size_t)ngroups + 1); A(&hist, hl); A(&blk, bl);
     A(&h->gbase, (size_t)ngroups + 1);
+    A(&serr, 1);
     pic_status ps = PIC_OK;
     if (!e) e = cudaMemsetAsync(blk, 0, sizeof(int32_t) * (size_t)bl, st);  // scan epoch and words
+    if (!e) e = cudaMemsetAsync(serr, 0, sizeof(int32_t), st);
     if (!e) e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (P + 1), st);
     if (!e && T > 0) {
         k_ow_keys<<<nblk(T, 256) < 4096 ? nblk(T, 256) : 4096, 256, 0, st>>>(T, P, h->ret, key, cnt);
-        e = sort_pairs_raw(key, T, P - 1, key_s, perm, tk, tv, hist, blk, st);
+        e = sort_pairs_raw(key, T, P - 1, key_s, perm, tk, tv, hist, blk, st, serr);
         int passes = 1;
         while (passes < 4 && ((unsigned)(P - 1) >> (8 * passes)) != 0) ++passes;
         *launches += 1 + 3 * passes;
     }
-    if (!e) e = scan_exclusive(cnt, off, P + 1, nullptr, blk, st);
+    if (!e) e = scan_exclusive(cnt, off, P + 1, nullptr, blk, st, serr);
     if (!e) {
         k_ow_group_rows<<<nblk(ngroups, 256), 256, 0, st>>>(P, B, ngroups, cnt, grows);
         e = cudaMemsetAsync(grows + ngroups, 0, sizeof(int32_t), st);
     }
-    if (!e) e = scan_exclusive(grows, h->gbase, ngroups + 1, nullptr, blk, st);
+    if (!e) e = scan_exclusive(grows, h->gbase, ngroups + 1, nullptr, blk, st, serr);
     *launches += 3;
-    int rows_total = 0;
+    int rows_total = 0, scan_err = 0;
     if (!e) e = cudaMemcpyAsync(&rows_total, h->gbase + ngroups, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaMemcpyAsync(&scan_err, serr, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (!e) e = cudaStreamSynchronize(st);
-    if (!e) {
+    if (!e && !scan_err) {  // rows_total sizes the record tables: only from a completed scan
         const size_t nrec = (size_t)(rows_total > 0 ? rows_total : 1) * kLanes;
         const size_t nchunk = nrec / ((size_t)kCh * kLanes) + 1;
         e = cudaMalloc(&h->rec, nrec * sizeof(int4));
@@ -1081,7 +1085,11 @@ pic_status build_tables(pic_owmr* h, int P, int ctas, cudaStream_t st, int* laun
     }
     if (!e) e = cudaStreamSynchronize(st);
     cudaFree(key); cudaFree(key_s); cudaFree(perm); cudaFree(tk); cudaFree(tv); cudaFree(cnt);
-    cudaFree(off); cudaFree(grows); cudaFree(hist); cudaFree(blk);
+    cudaFree(off); cudaFree(grows); cudaFree(hist); cudaFree(blk); cudaFree(serr);
+    if (!e && scan_err) {
+        free_tables(h);
+        return fail(PIC_ERR_TIMEOUT, "OWMR tables: a prefix scan's wait for an earlier tile exceeded its bound");
+    }
     if (e) {
         free_tables(h);
         return fail(e == cudaErrorMemoryAllocation ? PIC_ERR_OOM : PIC_ERR_CUDA,

@@ -66,3 +66,25 @@ def test_owmr_null_and_shape_arguments_rejected_without_gpu():
     d = owmr.pic_owmr_desc(10, 0)  # N = 0
     assert L.pic_owmr_create(ctypes.byref(d), ctypes.byref(h)) == pic.PIC_ERR_INVALID_ARG
     assert "N" in pic.pic_last_error()
+
+
+def test_no_cpu_fallback_without_a_device():
+    """Without a CUDA device the library and the session fail with an error:
+    nothing behind the C-ABI or the Python binding simulates on the host."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    import paper_2406_01939_b300 as pic
+    from paper_2406_01939_b300 import synth
+    from paper_2406_01939_b300.session import DeviceInstance
+    inst = synth.greedy_small(0, T=64)
+    d = pic.make_desc(inst.T, inst.N, inst.K, inst.R, inst.prod, inst.reg, inst.x0, inst.cost,
+                      mem=pic.PIC_MEM_HOST)
+    with pytest.raises(pic.PicError) as e:
+        pic.pic_create_instance(d)
+    assert e.value.status == pic.PIC_ERR_CUDA and pic.pic_last_error()
+    with pytest.raises(pic.PicError) as e:
+        pic.pic_create_batch([d, d])
+    assert e.value.status == pic.PIC_ERR_CUDA
+    with pytest.raises(RuntimeError):
+        DeviceInstance(inst)

@@ -325,6 +325,22 @@ pic_status pic_simulate_sequential_static(const pic_instance_desc* desc, int32_t
  * (a desc with cap), OOM, CUDA. */
 pic_status pic_create_batch(const pic_instance_desc* descs, int32_t B, pic_instance** out);
 
+/* Replace every trajectory's inputs of a batch instance with new arrays of the
+ * same shapes, reusing its device memory: the batch analogue of
+ * pic_instance_load, for a policy-gradient loop that samples new demand streams
+ * each step (Sec. 4.2 estimates the gradient over such sampled trajectories).
+ *   descs  HOST [B], B as at creation; desc b must have trajectory b's T, N, K,
+ *          R and lam present iff it was at creation (no cap); its arrays are
+ *          read (HOST or DEVICE per desc->mem) before the call returns, on
+ *          descs[0].stream, which the call synchronises.
+ * The same range checks as pic_create_batch run on the new inputs.  The order
+ * tables and any captured per-call graph are rebuilt by the next call; the
+ * autotuner's choice is kept.  Errors: INVALID_ARG (a shape mismatch or a
+ * failed range check, naming it), UNSUPPORTED (cap), CUDA.  After a failed
+ * check the batch's inputs are undefined: pic_simulate_batch and
+ * pic_policy_grad return INVALID_ARG until a load succeeds. */
+pic_status pic_batch_load(pic_instance* batch, const pic_instance_desc* descs, int32_t B);
+
 /* Simulate every trajectory of a batch instance, each under its own policy,
  * in one persistent launch (PIC_MODE_PICARD) or one warp per trajectory
  * (PIC_MODE_SEQUENTIAL).

@@ -108,6 +108,8 @@ def lib():
             L.pic_simulate.restype = C.c_int
             L.pic_create_batch.argtypes = [C.POINTER(pic_instance_desc), C.c_int32, C.POINTER(P)]
             L.pic_create_batch.restype = C.c_int
+            L.pic_batch_load.argtypes = [P, C.POINTER(pic_instance_desc), C.c_int32]
+            L.pic_batch_load.restype = C.c_int
             L.pic_simulate_batch.argtypes = [P, C.POINTER(pic_policy), C.POINTER(pic_sim_opts), P, P,
                                              C.POINTER(pic_traj_result), C.POINTER(pic_sim_result)]
             L.pic_simulate_batch.restype = C.c_int
@@ -216,6 +218,13 @@ def pic_create_batch(descs) -> int:
     h = C.c_void_p()
     _check(lib().pic_create_batch(arr, len(descs), C.byref(h)))
     return h.value
+
+
+def pic_batch_load(handle: int, descs) -> None:
+    """Replace every trajectory's inputs of a batch instance (same shapes as at
+    creation) with the arrays of a list of pic_instance_desc."""
+    arr = (pic_instance_desc * len(descs))(*descs)
+    _check(lib().pic_batch_load(C.c_void_p(handle), arr, len(descs)))
 
 
 def pic_simulate_batch(handle: int, policies, opts: pic_sim_opts, actions_out, final_stock=None,

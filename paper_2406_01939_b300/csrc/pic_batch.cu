@@ -592,10 +592,62 @@ pic_status create_fail(pic_instance* h, pic_status s) {
     return s;
 }
 
+// Copy every trajectory's inputs into the combined arrays (orders at toff[b],
+// products at koff[b], regions at roff[b]; lam rows of trajectories without lam
+// zero), shift its local product and region ids into its ranges, and check the
+// ranges (ids, x0 >= 0, |cost|, |lam|, |cost - lam| < 2^23).  The descriptors'
+// shapes must match the batch's.  Synchronises the stream.
+pic_status load_inputs(Instance& I, const pic_instance_desc* descs, cudaStream_t st) {
+    Batch* bt = I.batch;
+    const int B = bt->B;
+    const size_t N = I.N;
+    int* bad = &I.ctrl->pad0;
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int), st);
+    for (int b = 0; b < B && !e; ++b) {
+        const pic_instance_desc* d = descs + b;
+        const cudaMemcpyKind kind = d->mem == PIC_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+        const size_t t0 = bt->h_toff[b], k0 = bt->h_koff[b], r0 = bt->h_roff[b];
+        if (d->T) {
+            e = cudaMemcpyAsync(I.prod + t0, d->prod, sizeof(int32_t) * d->T, kind, st);
+            if (!e) e = cudaMemcpyAsync(I.reg + t0, d->reg, sizeof(int32_t) * d->T, kind, st);
+        }
+        if (!e) e = cudaMemcpyAsync(I.x0 + k0 * N, d->x0, sizeof(int32_t) * d->K * N, kind, st);
+        if (!e) e = cudaMemcpyAsync(I.cost + r0 * N, d->cost, sizeof(int32_t) * d->R * N, kind, st);
+        if (!e && I.has_lam) {
+            e = d->lam ? cudaMemcpyAsync(I.lam + k0 * N, d->lam, sizeof(int32_t) * d->K * N, kind, st)
+                       : cudaMemsetAsync(I.lam + k0 * N, 0, sizeof(int32_t) * d->K * N, st);
+        }
+    }
+    if (e) return cuda_fail(e, "input copy", __LINE__);
+    k_batch_ids<<<4 * I.num_sms, 256, 0, st>>>(I.T, B, bt->toff, bt->koff, bt->roff, I.prod, I.reg, bad);
+    e = cudaGetLastError();
+    int hb_ids = 0;
+    if (!e) e = cudaMemcpyAsync(&hb_ids, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    // range checks of x0, cost, lam on the combined arrays (ids were checked above)
+    if (!e) e = launch_validate(I, st);
+    int hb = 0;
+    if (!e) e = cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    if (e) return cuda_fail(e, "validation", __LINE__);
+    hb |= hb_ids;
+    if (hb & 1) return fail(PIC_ERR_INVALID_ARG, "a trajectory has prod[t] outside [0, K)");
+    if (hb & 2) return fail(PIC_ERR_INVALID_ARG, "a trajectory has reg[t] outside [0, R)");
+    if (hb & 4) return fail(PIC_ERR_INVALID_ARG, "a trajectory's x0 has a negative entry");
+    if (hb & (8 | 16 | 32))
+        return fail(PIC_ERR_INVALID_ARG,
+                    "|cost|, |lam| or |cost - lam| not below 2^23 (cost - lam is checked "
+                    "over all trajectories' rows together)");
+    return PIC_OK;
+}
+
 }  // namespace
 
 namespace pic {
-pic_status batch_tables(Instance& I, int M, int W, cudaStream_t st) { return ensure_tables(I, M, W, st); }
+pic_status batch_tables(Instance& I, int M, int W, cudaStream_t st) {
+    if (I.batch->invalid)
+        return fail(PIC_ERR_INVALID_ARG, "the batch's last pic_batch_load failed: load valid inputs first");
+    return ensure_tables(I, M, W, st);
+}
 }  // namespace pic
 
 extern "C" {
@@ -675,47 +727,45 @@ pic_status pic_create_batch(const pic_instance_desc* descs, int32_t B, pic_insta
     if (!e) e = cudaMemcpyAsync(bt->toff, off.data(), sizeof(int32_t) * (B + 1), cudaMemcpyHostToDevice, st);
     if (!e) e = cudaMemcpyAsync(bt->koff, off.data() + B + 1, sizeof(int32_t) * (B + 1), cudaMemcpyHostToDevice, st);
     if (!e) e = cudaMemcpyAsync(bt->roff, off.data() + 2 * (B + 1), sizeof(int32_t) * (B + 1), cudaMemcpyHostToDevice, st);
-    for (int b = 0; b < B && !e; ++b) {
-        const pic_instance_desc* d = descs + b;
-        const cudaMemcpyKind kind = d->mem == PIC_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-        const size_t t0 = bt->h_toff[b], k0 = bt->h_koff[b], r0 = bt->h_roff[b];
-        if (d->T) {
-            e = cudaMemcpyAsync(I.prod + t0, d->prod, sizeof(int32_t) * d->T, kind, st);
-            if (!e) e = cudaMemcpyAsync(I.reg + t0, d->reg, sizeof(int32_t) * d->T, kind, st);
-        }
-        if (!e) e = cudaMemcpyAsync(I.x0 + k0 * N, d->x0, sizeof(int32_t) * d->K * N, kind, st);
-        if (!e) e = cudaMemcpyAsync(I.cost + r0 * N, d->cost, sizeof(int32_t) * d->R * N, kind, st);
-        if (!e && any_lam) {
-            e = d->lam ? cudaMemcpyAsync(I.lam + k0 * N, d->lam, sizeof(int32_t) * d->K * N, kind, st)
-                       : cudaMemsetAsync(I.lam + k0 * N, 0, sizeof(int32_t) * d->K * N, st);
-        }
-    }
-    if (e) return create_fail(h, cuda_fail(e, "input copy", __LINE__));
-    int* bad = &I.ctrl->pad0;
+    if (e) return create_fail(h, cuda_fail(e, "offset copy", __LINE__));
     const int grid = 4 * I.num_sms;
-    k_batch_ids<<<grid, 256, 0, st>>>((int)T, B, bt->toff, bt->koff, bt->roff, I.prod, I.reg, bad);
     k_owners<<<grid, 256, 0, st>>>((int)K, B, bt->koff, bt->traj_of_prod, nullptr);
     k_owners<<<grid, 256, 0, st>>>((int)R, B, bt->roff, nullptr, bt->reg_local);
-    e = cudaGetLastError();
-    int hb_ids = 0;
-    if (!e) e = cudaMemcpyAsync(&hb_ids, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
-    // range checks of x0, cost, lam on the combined arrays (ids were checked above)
-    if (!e) e = launch_validate(I, st);
-    int hb = 0;
-    if (!e) e = cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (!e) e = cudaStreamSynchronize(st);
-    if (e) return create_fail(h, cuda_fail(e, "validation", __LINE__));
-    hb |= hb_ids;
-    if (hb & 1) return create_fail(h, fail(PIC_ERR_INVALID_ARG, "a trajectory has prod[t] outside [0, K)"));
-    if (hb & 2) return create_fail(h, fail(PIC_ERR_INVALID_ARG, "a trajectory has reg[t] outside [0, R)"));
-    if (hb & 4) return create_fail(h, fail(PIC_ERR_INVALID_ARG, "a trajectory's x0 has a negative entry"));
-    if (hb & (8 | 16 | 32))
-        return create_fail(h, fail(PIC_ERR_INVALID_ARG,
-                                   "|cost|, |lam| or |cost - lam| not below 2^23 (cost - lam is checked "
-                                   "over all trajectories' rows together)"));
+    if ((e = cudaGetLastError())) return create_fail(h, cuda_fail(e, "owner tables", __LINE__));
+    const pic_status ls = load_inputs(I, descs, st);
+    if (ls != PIC_OK) return create_fail(h, ls);
     I.cost16 = 0;  // the combined cost table is read from global memory
     *out = h;
     return PIC_OK;
+}
+
+pic_status pic_batch_load(pic_instance* h, const pic_instance_desc* descs, int32_t B) {
+    clear_error();
+    if (!h || !h->I.batch) return fail(PIC_ERR_INVALID_ARG, "not a batch instance (use pic_create_batch)");
+    Instance& I = h->I;
+    Batch* bt = I.batch;
+    if (!descs || B != bt->B) return fail(PIC_ERR_INVALID_ARG, "descs is NULL or B differs from the batch's %d", bt->B);
+    for (int b = 0; b < B; ++b) {
+        const pic_instance_desc* d = descs + b;
+        if (!desc_ok(d))
+            return fail(PIC_ERR_INVALID_ARG, "trajectory %d: invalid descriptor (sizes, pointers or mem)", b);
+        if (d->cap) return fail(PIC_ERR_UNSUPPORTED, "trajectory %d: node capacity is not supported in a batch", b);
+        if (d->N != I.N || d->T != bt->h_toff[b + 1] - bt->h_toff[b] || d->K != bt->h_koff[b + 1] - bt->h_koff[b] ||
+            d->R != bt->h_roff[b + 1] - bt->h_roff[b] || (d->lam != nullptr) != (bt->h_has_lam[b] != 0))
+            return fail(PIC_ERR_INVALID_ARG, "trajectory %d: shape (T, N, K, R, lam) differs from the batch's", b);
+    }
+    // the order tables and the captured per-call graph describe the old inputs
+    I.tables_m = 0;
+    I.tables_w = 0;
+    if (bt->gexec) {
+        cudaGraphExecDestroy(bt->gexec);
+        bt->gexec = nullptr;
+        bt->gsig = 0;
+    }
+    bt->invalid = 1;
+    const pic_status s = load_inputs(I, descs, (cudaStream_t)descs[0].stream);
+    if (s == PIC_OK) bt->invalid = 0;
+    return s;
 }
 
 pic_status pic_simulate_batch(pic_instance* h, const pic_policy* pols, const pic_sim_opts* opts,
@@ -726,6 +776,8 @@ pic_status pic_simulate_batch(pic_instance* h, const pic_policy* pols, const pic
     Instance& I = h->I;
     Batch* bt = I.batch;
     const int B = bt->B;
+    if (bt->invalid)
+        return fail(PIC_ERR_INVALID_ARG, "the batch's last pic_batch_load failed: load valid inputs first");
     if (!pols || !opts || (!actions_out && I.T > 0))
         return fail(PIC_ERR_INVALID_ARG, "pols, opts and actions_out are required");
     if (opts->mode == PIC_MODE_PICARD_PRODUCTS || opts->mode == PIC_MODE_PICARD_ASSIGNED)

@@ -98,6 +98,7 @@ struct Batch {
     // autotuner result and the policy signature it was tuned for
     unsigned long long tune_sig;
     int tune_m, tune_w, tune_shape, tune_tc, tune_wave;
+    int invalid;  // the last pic_batch_load failed: its inputs are undefined
 };
 
 struct PgState;  // buffers of the policy gradient (pic_pg.cu)

@@ -6,8 +6,8 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from . import (PIC_MEM_DEVICE, PIC_MEM_HOST, make_desc, make_opts, make_policy, pic_create_batch,
-               pic_create_instance, pic_destroy_instance, pic_instance_load, pic_simulate,
+from . import (PIC_MEM_DEVICE, PIC_MEM_HOST, make_desc, make_opts, make_policy, pic_batch_load,
+               pic_create_batch, pic_create_instance, pic_destroy_instance, pic_instance_load, pic_simulate,
                pic_simulate_batch)
 
 
@@ -122,8 +122,16 @@ class DeviceBatch:
         self.N = int(self.insts[0].N)
         self.offsets = np.concatenate([[0], np.cumsum([i.T for i in self.insts])]).astype(np.int64)
         self.koffsets = np.concatenate([[0], np.cumsum([i.K for i in self.insts])]).astype(np.int64)
+        keep, descs = self._descs(self.insts, mem)
+        self.handle = pic_create_batch(descs)
+        del keep  # the batch holds its own device copies
+
+    def _descs(self, insts, mem):
+        """Descriptors of insts' arrays (device copies for PIC_MEM_DEVICE, the
+        host arrays themselves for PIC_MEM_HOST) and the arrays to keep alive."""
+        device, stream = self.device, self.stream
         keep, descs = [], []
-        for i in self.insts:
+        for i in insts:
             if mem == PIC_MEM_DEVICE:
                 a = {k: _dev(getattr(i, k).astype(np.int32), device) for k in ("prod", "reg", "x0", "cost")}
                 a["lam"] = None if i.lam is None else _dev(i.lam.astype(np.int32), device)
@@ -138,8 +146,17 @@ class DeviceBatch:
             keep.append(a)
             descs.append(make_desc(i.T, i.N, i.K, i.R, a["prod"], a["reg"], a["x0"], a["cost"],
                                    a["lam"], mem=mem, stream=stream, cap=a.get("cap")))
-        self.handle = pic_create_batch(descs)
-        del keep  # the batch holds its own device copies
+        return keep, descs
+
+    def load(self, insts, mem=PIC_MEM_DEVICE):
+        """Replace every trajectory's inputs with those of insts (the same shapes,
+        lam present where it was), reusing the batch's device memory
+        (pic_batch_load); PIC_MEM_HOST copies C-contiguous host arrays."""
+        insts = list(insts)
+        keep, descs = self._descs(insts, mem)
+        pic_batch_load(self.handle, descs)
+        del keep
+        self.insts = insts
 
     def simulate(self, policies, mode="picard", num_chunks=0, max_iters=0, flags=0, alpha_init=None,
                  timeout_ns=0, seg_window=0, want_stock=True, raise_on_error=True, out=None,

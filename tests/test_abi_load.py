@@ -54,6 +54,8 @@ def test_null_arguments_rejected_without_gpu():
     assert L.pic_simulate_batch(None, None, None, None, None, None, None) == pic.PIC_ERR_INVALID_ARG
     assert "batch" in pic.pic_last_error()
     assert L.pic_policy_grad(None, None, None, None, None, None) == pic.PIC_ERR_INVALID_ARG
+    assert L.pic_batch_load(None, None, 2) == pic.PIC_ERR_INVALID_ARG
+    assert "batch" in pic.pic_last_error()
 
 
 def test_owmr_null_and_shape_arguments_rejected_without_gpu():

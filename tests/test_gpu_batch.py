@@ -211,3 +211,39 @@ def test_batch_saturated_table_exact():
             got = db.simulate(pols, mode, num_chunks=9, flags=flags)
             check_against_oracle(db, insts, pols, got, 9 if mode == "picard" else None)
             assert (got["sat_decisions"] > 0) == (flags == 0)
+
+
+def test_batch_load_replaces_the_inputs():
+    """pic_batch_load: a batch created from one set of trajectories and then
+    loaded with a second set of the same shapes simulates the second set as the
+    oracle does, through rebuilt order tables and a recaptured graph; a load
+    that fails a range check leaves the batch refusing calls until a valid one."""
+    N = 32
+    insts, pols = mixed_batch(5, [300, 1200, 50, 900, 700], N)
+    fresh = [synth.make_instance(i.T, N, i.K, i.R, seed=4242 + b, stock="poisson", fill=0.9,
+                                 with_lam=True) for b, i in enumerate(insts)]
+    db = DeviceBatch(insts)
+    for flags in (0, pic.PIC_FLAG_GRAPH):  # tables (and a graph) of the first set
+        check_against_oracle(db, insts, pols, db.simulate(pols, "picard", num_chunks=16, flags=flags))
+    db.load(fresh, mem=pic.PIC_MEM_HOST)
+    for flags in (pic.PIC_FLAG_GRAPH, 0):
+        check_against_oracle(db, fresh, pols, db.simulate(pols, "picard", num_chunks=16, flags=flags), M=16)
+    bad = [synth.make_instance(i.T, N, i.K, i.R, seed=77 + b, with_lam=True) for b, i in enumerate(insts)]
+    bad[3].prod = bad[3].prod.copy()
+    bad[3].prod[5] = bad[3].K  # out of range
+    with pytest.raises(pic.PicError) as e:
+        db.load(bad)
+    assert e.value.status == pic.PIC_ERR_INVALID_ARG and "prod" in str(e.value)
+    with pytest.raises(pic.PicError) as e:
+        db.simulate(pols, "picard", num_chunks=16)
+    assert e.value.status == pic.PIC_ERR_INVALID_ARG and "pic_batch_load" in str(e.value)
+    with pytest.raises(pic.PicError) as e:
+        db.load(fresh[:-1])  # one trajectory short
+    assert e.value.status == pic.PIC_ERR_INVALID_ARG
+    other = list(fresh)
+    other[1] = synth.make_instance(fresh[1].T + 1, N, fresh[1].K, fresh[1].R, seed=3, with_lam=True)
+    with pytest.raises(pic.PicError) as e:
+        db.load(other)
+    assert e.value.status == pic.PIC_ERR_INVALID_ARG and "trajectory 1" in str(e.value)
+    db.load(insts)  # device arrays; back to the first set
+    check_against_oracle(db, insts, pols, db.simulate(pols, "picard", num_chunks=16), M=16)

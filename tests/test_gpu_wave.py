@@ -96,18 +96,18 @@ def test_wave_batch_mixed_policies():
         insts.append(synth.make_instance(T, N, K, R, seed=100 + b, stock="poisson", with_lam=True))
         pols.append(Policy(kind, mlp=mlp if kind in ("mlp", "gumbel") else None, seed=7 + b, traj=b))
     db = DeviceBatch(insts)
+    wants = [oracle.seq_sim(inst, pol) for inst, pol in zip(insts, pols)]
+    iters = [oracle.picard_chunked(inst, pol, min(24, inst.T))["iters"] for inst, pol in zip(insts, pols)]
     for flags in (W, W | pic.PIC_FLAG_NO_SAT):
         got = db.simulate(pols, "picard", num_chunks=24, flags=flags)
         assert got["wave"]
         acts = db.split(got["actions"].cpu().numpy())
         xf = db.split_stock(got["final_stock"].cpu().numpy())
-        for b, (inst, pol) in enumerate(zip(insts, pols)):
-            want = oracle.seq_sim(inst, pol)
+        for b, want in enumerate(wants):
             np.testing.assert_array_equal(acts[b], want["actions"], err_msg=f"trajectory {b}")
             np.testing.assert_array_equal(xf[b], want["x_final"])
             assert got["traj"][b]["total_cost"] == want["total_cost"]
-            Mb = min(24, inst.T)
-            assert got["traj"][b]["iters"] == oracle.picard_chunked(inst, pol, Mb)["iters"], b
+            assert got["traj"][b]["iters"] == iters[b], b
 
 
 def test_wave_batch_uneven_full_size_equals_default_kernel():

@@ -22,9 +22,16 @@ def rand_inst(rng, T, N, K, R):
                     rng.integers(0, 4, (K, N)).astype(np.int32))
 
 
-def check(d, inst, pol, M, ms, **kw):
-    want = oracle.picard_windowed(inst, pol, M, ms)
-    seq = oracle.seq_sim(inst, pol)
+def check(d, inst, pol, M, ms, cache=None, **kw):
+    """cache: a dict living no longer than inst, holding the oracle's results
+    for repeated checks of the same instance and policy."""
+    cache = {} if cache is None else cache
+    pk = (id(inst), pol.kind, pol.seed, pol.traj, id(pol.mlp))
+    if pk + (M, ms) not in cache:
+        cache[pk + (M, ms)] = oracle.picard_windowed(inst, pol, M, ms)
+    if pk not in cache:
+        cache[pk] = oracle.seq_sim(inst, pol)
+    want, seq = cache[pk + (M, ms)], cache[pk]
     got = d.simulate(pol, "picard", num_chunks=M, max_steps=ms, **kw)
     np.testing.assert_array_equal(got["actions"].cpu().numpy(), seq["actions"])
     assert got["iters"] == want["iters"], (M, ms, got["iters"], want["iters"])
@@ -39,12 +46,13 @@ def test_window_integer_policies(N):
     for T, K, R in ((1, 1, 1), (37, 4, 5), (1000, 40, 7), (5000, 17, 40)):
         inst = rand_inst(rng, T, N, K, R)
         d = DeviceInstance(inst)
+        cache = {}
         for kind in ("greedy", "dual"):
             for M in sorted({1, 7, max(1, T // 16), T}):
                 L = -(-T // M)
                 for ms in sorted({1, L, 3 * L + 5, T}):
                     for W in (1, 64):
-                        check(d, inst, Policy(kind), M, ms, seg_window=W)
+                        check(d, inst, Policy(kind), M, ms, cache=cache, seg_window=W)
         # t_reset off: same iterates (t_reset only skips replays that reproduce the cache)
         check(d, inst, Policy("dual"), max(1, T // 16), max(1, T // 5), flags=pic.PIC_FLAG_NO_RESET)
 
@@ -67,9 +75,10 @@ def test_window_mlp_policies(N):
     inst = synth.make_instance(2500, N, 12, 9, seed=N, stock="poisson", fill=0.9)
     mlp = synth.make_mlp(N, 9, seed=N)
     d = DeviceInstance(inst)
+    cache = {}
     for pol in (Policy("mlp", mlp=mlp), Policy("gumbel", mlp=mlp, seed=5, traj=1)):
         for M, ms in ((50, 1), (50, 120), (100, 700), (25, 2500)):
-            check(d, inst, pol, M, ms)
+            check(d, inst, pol, M, ms, cache=cache)
         want = oracle.picard_windowed(inst, pol, 50, 300, record=True)
         for k in (1, 2, 5):
             got = d.simulate(pol, "picard", num_chunks=50, max_steps=300, max_iters=k,
